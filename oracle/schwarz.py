@@ -1,0 +1,186 @@
+"""Weighted overlapping additive Schwarz smoother on element-centred subdomains.
+
+Section 3.1: each subdomain Omega_s is element s plus an overlap strip adopted
+from the surrounding elements (N_O node layers, or a width delta_O).  With the
+restriction R_s, the local problem is A_ss du_s = r_s, A_ss = R_s A R_s^T,
+r_s = R_s r (Eq. subproblem); one additive Schwarz step adds
+sum_s R_s^T (W_s du_s) (Eq. correction:global), W_s = W_z (x) W_y (x) W_x built
+from the hat-shaped weight function w_H (Fig. wH).
+
+This oracle solves each A_ss DIRECTLY (dense Cholesky, or sparse LU for large
+subdomains), i.e. it does not use the fast diagonalisation the method uses; the
+two agree up to rounding because fast diagonalisation is an exact
+factorisation of A_ss^{-1}.
+
+Test infrastructure only (see ``oracle/__init__``).
+"""
+import numpy as np
+import scipy.linalg as sla
+import scipy.sparse as sp
+import scipy.sparse.linalg as spl
+
+from .gll import gll_nodes
+
+
+def max_layers(P):
+    """Largest admissible N_O at order P: floor(P/2) + 1, the layer count of
+    delta_O = dx/2, the widest overlap the paper uses (Table 1, rows 5-6).
+
+    Reading: the paper states the limit only geometrically (delta_O may not
+    exceed the width of the adjoining element, Section 3.1); a node may lie in at
+    most two subdomains per direction for the weights to sum to one, so N_O is
+    clamped to this value on every level."""
+    return P // 2 + 1
+
+
+def layers_from_width(P, delta_rel):
+    """N_O for a geometric overlap delta_O = delta_rel * dx: the number of
+    neighbour GLL nodes whose distance from the interface is <= delta_O.
+
+    In reference units the distance of neighbour node k is 1 + xi_k and the
+    overlap half-width is 2 delta_O / dx.  Inclusive comparison (a node exactly on
+    the strip boundary counts) reproduces the GLL N_O column of Table 1."""
+    xi = gll_nodes(P)
+    return int(np.sum(1.0 + xi <= 2.0 * delta_rel + 1e-12))
+
+
+def quintic(t):
+    """q(t) = 10 t^3 - 15 t^4 + 6 t^5: the quintic transition from 0 to 1 with
+    q(t) + q(1-t) = 1 (reading of 'piece-wise quintic transition', Fig. wH)."""
+    return t ** 3 * (10.0 - 15.0 * t + 6.0 * t ** 2)
+
+
+def hat_weight(xi_h, delta, profile="quintic"):
+    """w_H(xi_H) for overlap half-width ``delta`` in reference units (Fig. wH).
+
+    Reading (the full definition is deferred to an earlier paper): w = 1 for
+    |xi_H| <= 1 - delta, w = 0 for |xi_H| >= 1 + delta, and
+    w = 1 - q((|xi_H| - 1 + delta) / (2 delta)) in between, so w = 1/2 on the
+    interface and neighbouring subdomains' weights sum to one.  ``profile``
+    selects q: "quintic" (the paper's wording) or "linear" (q(t) = t).  Both give
+    the same weights whenever only the interface node lies in the strip
+    (N_O = 1)."""
+    a = abs(float(xi_h))
+    if delta <= 0.0:
+        return 1.0 if a < 1.0 else (0.5 if a == 1.0 else 0.0)
+    if a <= 1.0 - delta:
+        return 1.0
+    if a >= 1.0 + delta:
+        return 0.0
+    t = (a - 1.0 + delta) / (2.0 * delta)
+    if profile == "linear":
+        return 1.0 - t
+    if profile != "quintic":
+        raise ValueError(profile)
+    return 1.0 - quintic(t)
+
+
+def layer_delta(P, n_o):
+    """Overlap half-width (reference units) used for the weights when the
+    overlap is prescribed as N_O node layers.
+
+    Reading (parity unpinned for N_O >= 2): the midpoint between the distances
+    of the last included (k = N_O - 1) and the first excluded (k = N_O)
+    neighbour node, capped at 1 (delta_O = dx/2).  Every choice between those two
+    nodes gives the same weights for N_O = 1: face nodes 1/2, the rest of the core
+    1 (this is the only case Table 1 pins, rows 1 vs 3 at P = 4)."""
+    xi = gll_nodes(P)
+    d = 1.0 + xi
+    if n_o <= 0:
+        return 0.0
+    if n_o >= len(d):
+        return 1.0
+    return min(0.5 * (d[n_o - 1] + d[n_o]), 1.0)
+
+
+def subdomain_1d(P, n_o, delta, profile="quintic"):
+    """One direction of an element-centred subdomain.
+
+    Returns (de, i, w): for each of the m = P + 1 + 2 N_O subdomain nodes, the
+    element offset (-1, 0, +1), the node index inside that element and the 1D
+    weight.  The left strip is the last N_O nodes of the left neighbour, the
+    right strip the first N_O nodes of the right neighbour; xi_H = xi - 2 on the
+    left, xi on the core, xi + 2 on the right (Fig. wH).  N_O = 0 gives the
+    element alone with weight 1 (block Jacobi)."""
+    xi = gll_nodes(P)
+    n = P + 1
+    de, ii, w = [], [], []
+    for i in range(n - n_o, n):
+        de.append(-1)
+        ii.append(i)
+        w.append(hat_weight(xi[i] - 2.0, delta, profile))
+    for i in range(n):
+        de.append(0)
+        ii.append(i)
+        w.append(1.0 if n_o == 0 else hat_weight(xi[i], delta, profile))
+    for i in range(n_o):
+        de.append(1)
+        ii.append(i)
+        w.append(hat_weight(xi[i] + 2.0, delta, profile))
+    return np.array(de), np.array(ii), np.array(w)
+
+
+def subdomain_indices(mesh, P, n_o, delta, profile="quintic"):
+    """Global indices (Ns x m^3, subdomain node (a, b, c) at a + m (b + m c))
+    and the weights W_s = W_z (x) W_y (x) W_x (length m^3) of all subdomains."""
+    n = P + 1
+    B = n ** 3
+    dx, ix, wx = subdomain_1d(P, n_o, delta, profile)
+    m = len(dx)
+    c, b, a = np.meshgrid(np.arange(m), np.arange(m), np.arange(m), indexing="ij")
+    a, b, c = a.ravel(), b.ravel(), c.ravel()
+    ex, ey, ez = mesh.element_coords()
+    el = mesh.element(ex[:, None] + dx[a][None, :], ey[:, None] + dx[b][None, :],
+                      ez[:, None] + dx[c][None, :])
+    local = ix[a] + n * (ix[b] + n * ix[c])
+    idx = el * B + local[None, :]
+    W = wx[a] * wx[b] * wx[c]
+    return idx, W
+
+
+class SchwarzSmoother:
+    """u <- u + sum_s R_s^T W_s A_ss^{-1} R_s (f - A u), repeated nsteps times.
+
+    A_ss = A[I_s, I_s] is extracted from the assembled A.  On the uniform
+    periodic mesh it is the same matrix for every s (checked on all subdomains,
+    or a sample of ``check`` of them, to 1e-13 relative), so one factorisation
+    serves all subdomains."""
+
+    def __init__(self, A, mesh, P, n_o, delta, profile="quintic", check=64, dense_limit=7000):
+        self.idx, self.W = subdomain_indices(mesh, P, n_o, delta, profile)
+        self.N = A.shape[0]
+        Ns = self.idx.shape[0]
+        I0 = self.idx[0]
+        Ass = A[I0][:, I0]
+        sample = np.arange(Ns) if Ns <= check else np.random.default_rng(0).choice(Ns, check, replace=False)
+        ref = abs(Ass).max()
+        for s in sample:
+            Is = self.idx[s]
+            diff = abs(A[Is][:, Is] - Ass).max()
+            if diff > 1e-13 * ref:
+                raise AssertionError("A_ss differs between subdomains: %g" % diff)
+        self.m3 = len(I0)
+        if self.m3 <= dense_limit:
+            self.chol = sla.cho_factor(Ass.toarray(), lower=True)
+            self.lu = None
+        else:
+            self.chol = None
+            self.lu = spl.splu(sp.csc_matrix(Ass))
+        self.Ass = Ass
+
+    def local_solve(self, rs):
+        """A_ss^{-1} applied to the columns of rs (m^3 x k)."""
+        if self.chol is not None:
+            return sla.cho_solve(self.chol, rs)
+        return self.lu.solve(rs)
+
+    def correction(self, r):
+        """sum_s R_s^T (W_s A_ss^{-1} R_s r)."""
+        rs = r[self.idx]
+        du = self.local_solve(rs.T).T
+        return np.bincount(self.idx.ravel(), weights=(du * self.W[None, :]).ravel(), minlength=self.N)
+
+    def smooth(self, A, u, f, nsteps=1):
+        for _ in range(nsteps):
+            u = u + self.correction(f - A @ u)
+        return u

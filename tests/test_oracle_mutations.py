@@ -1,0 +1,67 @@
+"""Plant plausible mistakes in the oracle (on the CPU) and check that a pin fails.
+
+Each case patches one oracle function with a wrong variant and re-runs a pin
+from the other test modules; the pin must raise AssertionError."""
+import numpy as np
+import pytest
+
+import oracle.schwarz as schwarz
+import oracle.sipg as sipg
+import test_oracle_mg as tmg
+import test_oracle_schwarz as tsch
+import test_oracle_sipg as tsipg
+
+
+def _flip_consistency(P, h, d, mu):
+    F = _orig_face(P, h, d, mu).tocsr()
+    # wrong sign of the consistency/symmetry terms: mu J^T W J + (J^T W G + G^T W J)
+    Fmu = _orig_face(P, h, d, 0.0).tocsr()
+    return (F - 2 * Fmu).tocoo()
+
+
+_orig_face = sipg.face_matrix
+
+
+def test_wrong_face_sign_is_caught(monkeypatch):
+    monkeypatch.setattr(sipg, "face_matrix", _flip_consistency)
+    with pytest.raises(AssertionError):
+        tsipg.test_kronecker_form_eq_A(2)
+
+
+def test_literal_penalty_formula_is_caught(monkeypatch):
+    monkeypatch.setattr(sipg, "stability_threshold", lambda P, h: P * (P + 1) / h)
+    with pytest.raises(AssertionError):
+        tsipg.test_coercivity_threshold_is_half_of_quoted_formula(4)
+
+
+def test_interface_weight_one_is_caught(monkeypatch):
+    orig = schwarz.hat_weight
+
+    def bad(xi_h, delta, profile="quintic"):
+        return 1.0 if abs(abs(xi_h) - 1.0) < 1e-12 else orig(xi_h, delta, profile)
+    monkeypatch.setattr(schwarz, "hat_weight", bad)
+    with pytest.raises(AssertionError):
+        tsch.test_partition_of_unity_node_layers(4, 1, "quintic")
+
+
+def test_wrong_strip_nodes_are_caught(monkeypatch):
+    orig = schwarz.subdomain_1d
+
+    def bad(P, n_o, delta, profile="quintic"):
+        de, ii, w = orig(P, n_o, delta, profile)
+        ii = np.where(de == 1, P - ii, ii)  # right strip taken from the far side
+        return de, ii, w
+    monkeypatch.setattr(schwarz, "subdomain_1d", bad)
+    with pytest.raises(AssertionError):
+        tsch.test_direct_subdomain_inverse_equals_fast_diagonalisation(3, 1)
+
+
+def test_dropped_volume_direction_is_caught(monkeypatch):
+    orig = sipg.volume_matrix
+
+    def bad(P, h):
+        K = orig(P, (h[0], h[1], 1e9)).tocsr()  # z-derivative term effectively dropped
+        return K.tocoo()
+    monkeypatch.setattr(sipg, "volume_matrix", bad)
+    with pytest.raises(AssertionError):
+        tsipg.test_kronecker_form_eq_A(2)
