@@ -1,0 +1,205 @@
+/*
+ * mgdg.h -- C ABI of the GB300 polynomial multigrid solver for the nodal
+ * symmetric interior penalty DG (SIPG) Poisson equation on periodic 3D
+ * Cartesian grids (Stiller, "Robust Multigrid for Cartesian Interior Penalty
+ * DG Formulations of the Poisson Equation in 3D", arXiv 1612.04796).
+ *
+ * Problem (Section 2, Eq. poisson): -lap u = f on the periodic box
+ * [0,lx] x [0,ly] x [0,lz], nx*ny*nz equal cuboid elements, tensor-product
+ * Lagrange basis of order P on the Gauss-Lobatto-Legendre (GLL) points
+ * (Eq. u_h), SIPG form with GLL quadrature (Eq. ip), A u = f (Eq. discrete)
+ * with A = Mz(x)My(x)Lx + Mz(x)Ly(x)Mx + Lz(x)My(x)Mx (Eq. A).
+ *
+ * Conventions shared by every entry point
+ * ----------------------------------------
+ * Vectors are DEVICE pointers (unless a name says _host) to element-blocked
+ * coefficient vectors: element e = ex + nx*(ey + ny*ez), node (i,j,k) of an
+ * element of order p at index e*(p+1)^3 + i + (p+1)*(j + (p+1)*k).  Level l
+ * has order P_l = 2^l (level L = log2 P is the fine level, level 0 has P_0 = 1);
+ * its vectors have mg_num_dofs(ctx, l) entries.  Right-hand sides are weak
+ * (assembled) vectors b = M f_nodal with 1^T b = 0 (see mg_rhs).
+ *
+ * Ownership: the library allocates NO device memory.  The caller allocates
+ * one workspace of mg_workspace_size() bytes (256-byte aligned) and binds it
+ * with mg_bind_workspace(); the caller owns all vectors it passes.  Every call
+ * is ordered on the CUDA stream given in mg_opts.stream (NULL = legacy default
+ * stream); calls that return host scalars synchronise that stream.
+ *
+ * Errors: every entry point returns an mg_status (no exceptions cross the
+ * ABI, nothing aborts); mg_last_error() gives a message.  Device-side loops
+ * have iteration limits that end in a status, never in a hang or trap.
+ */
+#ifndef MGDG_H
+#define MGDG_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mg_ctx mg_ctx;
+
+typedef enum {
+  MG_OK = 0,
+  MG_EINVAL = 1,     /* invalid argument (sizes, pointers, level index, ...) */
+  MG_ENOMEM = 2,     /* host allocation failed or workspace too small */
+  MG_ECUDA = 3,      /* a CUDA runtime call failed (message in mg_last_error) */
+  MG_ENOCONV = 4,    /* an iteration limit was reached (setup eigensolver, solve) */
+  MG_ENOTREADY = 5   /* workspace not bound yet */
+} mg_status;
+
+/* Arithmetic of the solve (Section 3.2 method, precision is this library's choice). */
+typedef enum {
+  MG_FP64 = 0,  /* every kernel in FP64 */
+  MG_MIXED = 1  /* FP32 multigrid (smoother, transfers, operator on the levels)
+                   inside an FP64 outer iteration; FP64 outer residual, inner
+                   products, updates, 1D setup and coarsest solve */
+} mg_precision;
+
+/* How the subdomain overlap is given (Section 3.1, Table 1). */
+typedef enum {
+  MG_OVERLAP_LAYERS = 0, /* N_O node layers (argument `overlap` of mg_setup) */
+  MG_OVERLAP_WIDTH = 1   /* delta_O = overlap_frac * dx on every level (Table 1 rows 3-6) */
+} mg_overlap_mode;
+
+/* Transition profile of the hat-shaped weight function w_H (Fig. wH). */
+typedef enum {
+  MG_WEIGHT_QUINTIC = 0, /* 10t^3 - 15t^4 + 6t^5 */
+  MG_WEIGHT_LINEAR = 1   /* t */
+} mg_weight_profile;
+
+typedef struct {
+  int overlap_mode;      /* mg_overlap_mode, default MG_OVERLAP_LAYERS */
+  double overlap_frac;   /* delta_O / dx for MG_OVERLAP_WIDTH (paper: 0.08, 0.5) */
+  int weight_profile;    /* mg_weight_profile, default MG_WEIGHT_QUINTIC */
+  int ns_pre, ns_post;   /* smoothing steps N_s1, N_s2 on the fine level (default 1, 1) */
+  int ns_growth;         /* N_s,l = N_s * ns_growth^(L-l): 1 fixed V-cycle, 3 variable (Table 2) */
+  int precision;         /* mg_precision, default MG_FP64 */
+  void* stream;          /* cudaStream_t; NULL = default stream */
+} mg_opts;
+
+/* Fill *o with the defaults above. */
+void mg_default_opts(mg_opts* o);
+
+/*
+ * mg_setup -- describe a problem and its multigrid hierarchy (host only).
+ * Section 2 (domain, mesh, order), Section 3.1 (overlap), Section 3.2
+ * (levels P_l = 2^l), Section 4 (penalty mu = 2 mu_min).
+ *   lx, ly, lz   box lengths (> 0)
+ *   nx, ny, nz   elements per direction (3 .. 512)
+ *   P            polynomial order, a power of two, 2 <= P <= 32
+ *   penalty      mu / mu_min per direction, mu_min = P_l (P_l+1) / (2 dx) the
+ *                coercivity threshold of the form; the paper's choice is 2
+ *   overlap      N_O node layers (>= 0) for MG_OVERLAP_LAYERS; clamped on
+ *                each level to floor(P_l/2) + 1; ignored for MG_OVERLAP_WIDTH
+ *   opts         NULL for defaults
+ *   out          receives the new context (host memory owned by the library;
+ *                release with mg_destroy)
+ * Returns MG_EINVAL for out-of-range arguments.  No CUDA call is made.
+ */
+mg_status mg_setup(double lx, double ly, double lz, int nx, int ny, int nz, int P, double penalty,
+                   int overlap, const mg_opts* opts, mg_ctx** out);
+
+/* Bytes of device workspace the context needs (256-byte aligned base required). */
+mg_status mg_workspace_size(const mg_ctx* ctx, size_t* bytes);
+
+/*
+ * mg_bind_workspace -- bind caller-owned device memory and run the per-level
+ * 1D setup on the device (Section 3.1: GLL tables, the restricted 1D
+ * generalised eigenproblems L_s S = M_s S Lambda with S^T M_s S = I, the
+ * weights; Section 3.2: interpolation; coarse level eigenbases).  Synchronises
+ * the stream.  Returns MG_ENOCONV if an eigensolver hit its sweep limit.
+ */
+mg_status mg_bind_workspace(mg_ctx* ctx, void* dptr, size_t bytes);
+
+/* Number of levels L+1, DOFs and overlap layers of a level (host, no CUDA). */
+int mg_num_levels(const mg_ctx* ctx);
+long long mg_num_dofs(const mg_ctx* ctx, int level);
+int mg_level_layers(const mg_ctx* ctx, int level);
+
+/* Physical coordinates of the nodes of `level` into x, y, z (device, N_l each). */
+mg_status mg_node_coords(mg_ctx* ctx, int level, double* x, double* y, double* z);
+
+/*
+ * mg_rhs -- weak right-hand side of the fine level from nodal values (Section 2:
+ * GLL quadrature of int v f): b = M (f - (1^T M f)/(1^T M 1)) and then the
+ * rounding-level Euclidean mean of b is removed, so 1^T b = 0.  Device pointers,
+ * N_L values each; f_nodal and b may not alias.
+ */
+mg_status mg_rhs(mg_ctx* ctx, const double* f_nodal, double* b);
+
+/* Au = A_l u: sum-factorised SIPG operator of level l (Eq. A). */
+mg_status mg_apply_sipg(mg_ctx* ctx, int level, const double* u, double* Au);
+/* r = f - A_l u (Eq. discrete, residual form). r may not alias u or f. */
+mg_status mg_residual(mg_ctx* ctx, int level, const double* u, const double* f, double* r);
+
+/*
+ * mg_smooth -- nsteps weighted additive Schwarz steps on level l (Section 3.1):
+ * u <- u + sum_s R_s^T W_s A_ss^{-1} R_s (f - A_l u), with A_ss^{-1} applied by
+ * fast diagonalisation (Sz(x)Sy(x)Sx)(Lambda sum)^{-1}(Sz^T(x)Sy^T(x)Sx^T).
+ * In place on u.  Uses the level's scratch vectors in the workspace.
+ */
+mg_status mg_smooth(mg_ctx* ctx, int level, double* u, const double* f, int nsteps);
+
+/* f_c = I_l^T (f - A_l u): residual restriction to level l-1 (Algorithm 1). level >= 1. */
+mg_status mg_restrict_residual(mg_ctx* ctx, int level, const double* u, const double* f, double* f_c);
+/* u += I_l u_c: correction prolongation from level l-1 (Algorithm 1). level >= 1. */
+mg_status mg_prolongate(mg_ctx* ctx, int level, const double* u_c, double* u);
+/*
+ * mg_coarse_solve -- u0 = A_0^+ f0 on level 0 (Algorithm 1, coarse grid
+ * solution): f0 is projected onto the range of A_0 (zero mean) and the
+ * minimum-norm solution is returned (zero mean).  Computed directly by fast
+ * diagonalisation of the whole periodic coarse problem.
+ */
+mg_status mg_coarse_solve(mg_ctx* ctx, const double* f0, double* u0);
+
+/* One multigrid V-cycle (Algorithm 1) on the fine level, in place on u. */
+mg_status mg_vcycle(mg_ctx* ctx, double* u, const double* f);
+
+/*
+ * mg_solve -- solve A u = f to ||f - A u||_2 <= tol ||f - A u_0||_2 (Section 4).
+ * u holds the initial guess on entry and the solution (zero Euclidean mean) on
+ * return.  use_cg = 0: repeated V-cycles (MG); use_cg = 1: inexact
+ * preconditioned CG with one V-cycle from zero as preconditioner (MG-CG,
+ * Section 3.2).  With MG_MIXED the V-cycle runs in FP32.  iters, relres (host)
+ * receive the iteration count and final relative residual; history (host, may be
+ * NULL) receives maxit+1 residual norms.  Returns MG_ENOCONV if maxit is reached.
+ */
+mg_status mg_solve(mg_ctx* ctx, double* u, const double* f, double tol, int maxit, int use_cg, int* iters,
+                   double* relres, double* history);
+
+/* mg_solve with HOST buffers u_host, f_host (N_L doubles; pinned memory is
+ * fastest): copies f (and the initial u) in, solves, copies u out. */
+mg_status mg_solve_host(mg_ctx* ctx, double* u_host, const double* f_host, double tol, int maxit, int use_cg,
+                        int* iters, double* relres, double* history);
+
+/* FP32 versions of the level kernels used by the MG_MIXED preconditioner
+ * (same semantics as the FP64 entry points; FP32 tables and arithmetic). */
+mg_status mg_apply_sipg_f32(mg_ctx* ctx, int level, const float* u, float* Au);
+mg_status mg_smooth_f32(mg_ctx* ctx, int level, float* u, const float* f, int nsteps);
+mg_status mg_vcycle_f32(mg_ctx* ctx, float* u, const float* f);
+
+/*
+ * mg_get_table -- copy a 1D setup table of level l, direction dir (0 x, 1 y,
+ * 2 z) to host memory, for inspection and tests.  what:
+ *   0 GLL nodes (n)       1 GLL weights (n)      2 mass diag (h/2) w (n)
+ *   3 element block of L (n*n, row-major)        4 eigenvalues Lambda (m)
+ *   5 eigenvectors S (m*m, S[a*m + p] = entry a of eigenvector p)
+ *   6 weights w (m)       7 interpolation J_l (n * n_c, row-major; level >= 1)
+ *   8 coarse eigenvalues (2 n_d; level 0)  9 coarse eigenvectors (4 n_d^2; level 0)
+ * *count receives the number of values; fails with MG_EINVAL if capacity is too small.
+ */
+mg_status mg_get_table(mg_ctx* ctx, int level, int dir, int what, double* host_out, int capacity, int* count);
+
+/* Message of the last failed call on ctx (never NULL). */
+const char* mg_last_error(const mg_ctx* ctx);
+
+/* Release the context (host memory only; the workspace belongs to the caller). */
+void mg_destroy(mg_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MGDG_H */

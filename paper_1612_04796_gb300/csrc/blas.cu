@@ -1,0 +1,261 @@
+// Vector kernels of the outer iteration and helpers (FP64 unless noted):
+// inner products and sums with a fixed two-stage reduction order (so repeated
+// runs give identical bits), the CG updates of the inexact preconditioned CG
+// (Section 3.2) with their scalars kept on the device, mean projections onto
+// the range of the singular periodic operator, FP64 <-> FP32 conversions with
+// scaling for the FP32 preconditioner, the weak right-hand side b = M f
+// (Section 2, GLL quadrature) and the node coordinates.
+#include "mg_internal.h"
+
+namespace mgdg {
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ double block_reduce(double v, double* sh) {
+  const int t = threadIdx.x;
+  sh[t] = v;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (t < s) sh[t] += sh[t + s];
+    __syncthreads();
+  }
+  return sh[0];
+}
+
+// mode 0: sum x*y   mode 1: sum x   (T = double | float input)
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_partial(const T* __restrict__ x, const T* __restrict__ y, int64_t n,
+                                                      int mode, double* partial) {
+  __shared__ double sh[kThreads];
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    acc += mode == 0 ? (double)x[i] * (double)y[i] : (double)x[i];
+  double r = block_reduce(acc, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = r;
+}
+
+__global__ void __launch_bounds__(kThreads) k_final(const double* partial, int nb, double* scal, int slot) {
+  __shared__ double sh[kThreads];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) acc += partial[i];
+  double r = block_reduce(acc, sh);
+  if (threadIdx.x == 0) scal[slot] = r;
+}
+
+template <typename T>
+__global__ void k_sub_mean(T* x, int64_t n, const double* scal, int slot) {
+  const T mean = (T)(scal[slot] / (double)n);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] -= mean;
+}
+
+// alpha = scal[num] / scal[den]; x += alpha p; r -= alpha q
+__global__ void k_axpy2(double* __restrict__ x, const double* __restrict__ p, double* __restrict__ r,
+                        const double* __restrict__ q, int64_t n, double* scal, int num, int den) {
+  const double alpha = scal[num] / scal[den];
+  if (blockIdx.x == 0 && threadIdx.x == 0) scal[kSlotAlpha] = alpha;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    x[i] += alpha * p[i];
+    r[i] -= alpha * q[i];
+  }
+}
+
+__global__ void k_add(double* __restrict__ y, const double* __restrict__ x, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] += x[i];
+}
+
+// beta = -scal[alpha] * scal[num] / scal[den]; p = z + beta p
+__global__ void k_xpby(double* __restrict__ p, const double* __restrict__ z, int64_t n, const double* scal, int num,
+                       int den, int aslot) {
+  const double beta = -scal[aslot] * scal[num] / scal[den];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = z[i] + beta * p[i];
+}
+
+__global__ void k_to_f32(const double* __restrict__ x, float* __restrict__ y, int64_t n, const double* scal,
+                         int slot) {
+  double s = 1.0;
+  if (slot >= 0) {
+    double nrm = sqrt(scal[slot]);
+    s = nrm > 0.0 ? 1.0 / nrm : 1.0;
+  }
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = (float)(x[i] * s);
+}
+
+__global__ void k_from_f32(const float* __restrict__ x, double* __restrict__ y, int64_t n, const double* scal,
+                           int slot) {
+  double s = 1.0;
+  if (slot >= 0) {
+    double nrm = sqrt(scal[slot]);
+    s = nrm > 0.0 ? nrm : 1.0;
+  }
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = (double)x[i] * s;
+}
+
+struct MassArgs {
+  const double* tab;
+  int64_t mass[3];
+  int n;
+  int64_t Ne;
+};
+
+__device__ __forceinline__ double mass_at(const MassArgs& a, int64_t dof) {
+  const int n = a.n, n3 = n * n * n;
+  const int loc = (int)(dof % n3);
+  const int i = loc % n, j = (loc / n) % n, k = loc / (n * n);
+  return a.tab[a.mass[0] + i] * a.tab[a.mass[1] + j] * a.tab[a.mass[2] + k];
+}
+
+// partial sums of M f (slot 0) and M (slot 1)
+__global__ void __launch_bounds__(kThreads) k_mass_partial(MassArgs a, const double* __restrict__ f,
+                                                           double* partial) {
+  __shared__ double sh[kThreads];
+  const int64_t total = a.Ne * a.n * a.n * a.n;
+  double s0 = 0.0, s1 = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    double m = mass_at(a, i);
+    s0 += m * f[i];
+    s1 += m;
+  }
+  double r0 = block_reduce(s0, sh);
+  __syncthreads();
+  double r1 = block_reduce(s1, sh);
+  if (threadIdx.x == 0) {
+    partial[blockIdx.x] = r0;
+    partial[gridDim.x + blockIdx.x] = r1;
+  }
+}
+
+__global__ void k_rhs(MassArgs a, const double* __restrict__ f, double* __restrict__ b, const double* scal) {
+  const double fbar = scal[kSlotMassF] / scal[kSlotMass];
+  const int64_t total = a.Ne * a.n * a.n * a.n;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = mass_at(a, i) * (f[i] - fbar);
+}
+
+__global__ void k_coords(const double* tab, int64_t nodes, int n, int64_t Ne, int nx, int ny, double hx, double hy,
+                         double hz, double* x, double* y, double* z) {
+  const int n3 = n * n * n;
+  const int64_t total = Ne * n3;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = idx / n3;
+    const int loc = (int)(idx - e * n3);
+    const int i = loc % n, j = (loc / n) % n, k = loc / (n * n);
+    const int64_t ex = e % nx, ey = (e / nx) % ny, ez = e / ((int64_t)nx * ny);
+    x[idx] = ex * hx + (tab[nodes + i] + 1.0) * 0.5 * hx;
+    y[idx] = ey * hy + (tab[nodes + j] + 1.0) * 0.5 * hy;
+    z[idx] = ez * hz + (tab[nodes + k] + 1.0) * 0.5 * hz;
+  }
+}
+
+template <typename T>
+__global__ void k_zero(T* x, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] = (T)0;
+}
+
+inline int grid_for(int64_t n) {
+  int64_t b = (n + kThreads - 1) / kThreads;
+  if (b > 152 * 8) b = 152 * 8;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+template <typename T>
+cudaError_t reduce(const mg_ctx* c, const T* x, const T* y, int64_t n, int mode, int slot) {
+  k_partial<T><<<kRedBlocks, kThreads, 0, c->stream>>>(x, y, n, mode, c->ws.red);
+  k_final<<<1, kThreads, 0, c->stream>>>(c->ws.red, kRedBlocks, c->ws.scal, slot);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_dot(const mg_ctx* c, const double* x, const double* y, int64_t n, int slot) {
+  return reduce<double>(c, x, y, n, 0, slot);
+}
+
+cudaError_t launch_sum(const mg_ctx* c, const double* x, int64_t n, int slot) {
+  return reduce<double>(c, x, x, n, 1, slot);
+}
+
+cudaError_t launch_sub_mean(const mg_ctx* c, double* x, int64_t n, int sum_slot) {
+  k_sub_mean<double><<<grid_for(n), kThreads, 0, c->stream>>>(x, n, c->ws.scal, sum_slot);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_sub_mean_t(const mg_ctx* c, T* x, int64_t n) {
+  cudaError_t e = reduce<T>(c, x, x, n, 1, kSlotSumT);
+  if (e != cudaSuccess) return e;
+  k_sub_mean<T><<<grid_for(n), kThreads, 0, c->stream>>>(x, n, c->ws.scal, kSlotSumT);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_axpy2(const mg_ctx* c, double* x, const double* p, double* r, const double* q, int64_t n,
+                         int num_slot, int den_slot) {
+  k_axpy2<<<grid_for(n), kThreads, 0, c->stream>>>(x, p, r, q, n, c->ws.scal, num_slot, den_slot);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_add(const mg_ctx* c, double* y, const double* x, int64_t n) {
+  k_add<<<grid_for(n), kThreads, 0, c->stream>>>(y, x, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_xpby(const mg_ctx* c, double* p, const double* z, int64_t n, int num_slot, int den_slot,
+                        int alpha_slot) {
+  k_xpby<<<grid_for(n), kThreads, 0, c->stream>>>(p, z, n, c->ws.scal, num_slot, den_slot, alpha_slot);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_to_f32(const mg_ctx* c, const double* x, float* y, int64_t n, int norm_slot) {
+  k_to_f32<<<grid_for(n), kThreads, 0, c->stream>>>(x, y, n, c->ws.scal, norm_slot);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_from_f32(const mg_ctx* c, const float* x, double* y, int64_t n, int norm_slot) {
+  k_from_f32<<<grid_for(n), kThreads, 0, c->stream>>>(x, y, n, c->ws.scal, norm_slot);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rhs(const mg_ctx* c, const double* f, double* b) {
+  const LevelInfo& lv = c->lev[c->L];
+  MassArgs a;
+  a.tab = c->ws.tab64;
+  for (int d = 0; d < 3; ++d) a.mass[d] = lv.t[d].mass;
+  a.n = lv.n;
+  a.Ne = c->Ne;
+  k_mass_partial<<<kRedBlocks, kThreads, 0, c->stream>>>(a, f, c->ws.red);
+  k_final<<<1, kThreads, 0, c->stream>>>(c->ws.red, kRedBlocks, c->ws.scal, kSlotMassF);
+  k_final<<<1, kThreads, 0, c->stream>>>(c->ws.red + kRedBlocks, kRedBlocks, c->ws.scal, kSlotMass);
+  k_rhs<<<grid_for(lv.N), kThreads, 0, c->stream>>>(a, f, b, c->ws.scal);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if ((e = launch_sum(c, b, lv.N, kSlotSum)) != cudaSuccess) return e;
+  return launch_sub_mean(c, b, lv.N, kSlotSum);
+}
+
+cudaError_t launch_coords(const mg_ctx* c, int l, double* x, double* y, double* z) {
+  const LevelInfo& lv = c->lev[l];
+  k_coords<<<grid_for(lv.N), kThreads, 0, c->stream>>>(c->ws.tab64, lv.t[0].nodes, lv.n, c->Ne, c->ne[0], c->ne[1],
+                                                        lv.h[0], lv.h[1], lv.h[2], x, y, z);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_zero(const mg_ctx* c, T* x, int64_t n) {
+  k_zero<T><<<grid_for(n), kThreads, 0, c->stream>>>(x, n);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_sub_mean_t<double>(const mg_ctx*, double*, int64_t);
+template cudaError_t launch_sub_mean_t<float>(const mg_ctx*, float*, int64_t);
+template cudaError_t launch_zero<double>(const mg_ctx*, double*, int64_t);
+template cudaError_t launch_zero<float>(const mg_ctx*, float*, int64_t);
+
+}  // namespace mgdg

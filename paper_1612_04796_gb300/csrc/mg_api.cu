@@ -1,0 +1,691 @@
+// C ABI entry points and host orchestration of the multigrid solver.
+//
+// mg_setup derives the level hierarchy P_l = 2^l (Section 3.2), the overlap of
+// every level (Section 3.1, Table 1) and the workspace layout; the device
+// builds all tables at mg_bind_workspace.  mg_vcycle follows Algorithm 1,
+// mg_solve repeats it (MG) or uses it as the preconditioner of the inexact
+// preconditioned CG (MG-CG, Section 3.2); residual norms are Euclidean
+// (Section 4).
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "mg_internal.h"
+
+using namespace mgdg;
+
+namespace {
+
+mg_status fail(mg_ctx* c, mg_status st, const std::string& msg) {
+  if (c) c->err = msg;
+  return st;
+}
+
+mg_status cuda_fail(mg_ctx* c, cudaError_t e, const char* what) {
+  return fail(c, MG_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                            \
+  do {                                                      \
+    cudaError_t e_ = (call);                                \
+    if (e_ != cudaSuccess) return cuda_fail(c, e_, #call);  \
+  } while (0)
+
+// ---- host-side GLL nodes, used only to size the hierarchy (overlap layers) ----
+double legendre_host(int P, double x, double* dl) {
+  double l0 = 1.0, l1 = x;
+  for (int k = 1; k < P; ++k) {
+    double l2 = ((2.0 * k + 1.0) * x * l1 - k * l0) / (k + 1.0);
+    l0 = l1;
+    l1 = l2;
+  }
+  *dl = P * (x * l1 - l0) / (x * x - 1.0);
+  return l1;
+}
+
+std::vector<double> gll_host(int P) {
+  const double pi = 3.14159265358979323846;
+  std::vector<double> x(P + 1);
+  x[0] = -1.0;
+  x[P] = 1.0;
+  for (int k = 1; k < P; ++k) {
+    double t = -cos(pi * k / P);
+    for (int it = 0; it < 100; ++it) {
+      double dl;
+      double lp = legendre_host(P, t, &dl);
+      double d2 = (2.0 * t * dl - P * (P + 1.0) * lp) / (1.0 - t * t);
+      double dt = dl / d2;
+      t -= dt;
+      if (fabs(dt) < 1e-16) break;
+    }
+    x[k] = t;
+  }
+  for (int k = 0; k <= P / 2; ++k) {
+    double s = 0.5 * (x[P - k] - x[k]);
+    x[k] = -s;
+    x[P - k] = s;
+  }
+  if (P % 2 == 0) x[P / 2] = 0.0;
+  return x;
+}
+
+// N_O of a geometric overlap delta_O = frac * dx: neighbour nodes with
+// distance 1 + xi_k <= 2 frac from the interface (inclusive; Table 1).
+int layers_from_width(int P, double frac) {
+  std::vector<double> x = gll_host(P);
+  int cnt = 0;
+  for (double v : x)
+    if (1.0 + v <= 2.0 * frac + 1e-12) ++cnt;
+  return cnt;
+}
+
+// Hat-weight half-width for N_O prescribed layers: midpoint between the last
+// included and the first excluded neighbour node, capped at 1.
+double layer_delta(int P, int no) {
+  if (no <= 0) return 0.0;
+  std::vector<double> x = gll_host(P);
+  if (no >= P + 1) return 1.0;
+  double d = 0.5 * ((1.0 + x[no - 1]) + (1.0 + x[no]));
+  return d < 1.0 ? d : 1.0;
+}
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// ---- workspace layout ----
+struct Layout {
+  size_t tab64, tab32, lev_u[kMaxLevels], lev_f[kMaxLevels], lev_r[kMaxLevels], corr, ca, cb, cf, cu, cg[8], red,
+      scal, status, jac, total;
+  int64_t jac_count;
+};
+
+Layout make_layout(const mg_ctx* c) {
+  Layout ly;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off = align_up(off + bytes, 256);
+    return o;
+  };
+  ly.tab64 = take(c->ws.tab_count * sizeof(double));
+  ly.tab32 = take(c->ws.tab_count * sizeof(float));
+  int64_t corr = 0;
+  for (int l = 0; l <= c->L; ++l) {
+    const LevelInfo& lv = c->lev[l];
+    ly.lev_u[l] = take(lv.N * sizeof(double));
+    ly.lev_f[l] = take(lv.N * sizeof(double));
+    ly.lev_r[l] = take(lv.N * sizeof(double));
+    if (l >= 1) corr = std::max<int64_t>(corr, c->Ne * (int64_t)lv.m * lv.m * lv.m);
+  }
+  corr = std::max<int64_t>(corr, 2 * c->lev[c->L].N);
+  ly.corr = take(corr * sizeof(double));
+  const int64_t N0 = c->lev[0].N, NL = c->lev[c->L].N;
+  ly.ca = take(N0 * sizeof(double));
+  ly.cb = take(N0 * sizeof(double));
+  ly.cf = take(N0 * sizeof(double));
+  ly.cu = take(N0 * sizeof(double));
+  for (int k = 0; k < 8; ++k) ly.cg[k] = take(NL * sizeof(double));
+  ly.red = take(2 * kRedBlocks * sizeof(double));
+  ly.scal = take(kNumSlots * sizeof(double));
+  ly.status = take(256);
+  int nmax = 8;
+  for (int l = 1; l <= c->L; ++l) nmax = std::max(nmax, c->lev[l].m);
+  for (int d = 0; d < 3; ++d) nmax = std::max(nmax, c->Ng[d]);
+  int64_t per_block = 4 * (int64_t)nmax * nmax + 4 * nmax + 64;
+  ly.jac_count = per_block * 3 * (c->L + 1);
+  ly.jac = take(ly.jac_count * sizeof(double));
+  ly.total = off;
+  return ly;
+}
+
+bool check_level(mg_ctx* c, int level, bool need_smoother) {
+  if (level < 0 || level > c->L) {
+    fail(c, MG_EINVAL, "level out of range");
+    return false;
+  }
+  if (need_smoother && level < 1) {
+    fail(c, MG_EINVAL, "level 0 has no smoother / transfer");
+    return false;
+  }
+  return true;
+}
+
+mg_status need_ready(mg_ctx* c) {
+  if (!c) return MG_EINVAL;
+  if (!c->ready) return fail(c, MG_ENOTREADY, "workspace not bound");
+  return MG_OK;
+}
+
+double read_scalar(mg_ctx* c, int slot, cudaError_t* err) {
+  double v = 0.0;
+  *err = cudaMemcpyAsync(&v, c->ws.scal + slot, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  if (*err == cudaSuccess) *err = cudaStreamSynchronize(c->stream);
+  return v;
+}
+
+// ---- level vector views ----
+template <typename T>
+T* lvec(void* p) {
+  return static_cast<T*>(p);
+}
+
+template <typename T>
+cudaError_t coarse_solve_t(const mg_ctx* c, const T* f0, T* u0);
+template <>
+cudaError_t coarse_solve_t<double>(const mg_ctx* c, const double* f0, double* u0) {
+  return launch_coarse_solve(c, f0, u0);
+}
+template <>
+cudaError_t coarse_solve_t<float>(const mg_ctx* c, const float* f0, float* u0) {
+  return launch_coarse_solve_f32(c, f0, u0);
+}
+
+int steps_on_level(const mg_ctx* c, int ns, int l) {
+  int s = ns;
+  for (int k = l; k < c->L; ++k) s *= c->opts.ns_growth;
+  return s;
+}
+
+// One smoothing step on level l: u <- u + sum_s R_s^T W_s A_ss^{-1} R_s (f - A u).
+// u_is_zero: u == 0 on entry (the residual is f; u is overwritten).
+// r_ready: lev[l].r already holds f - A u.
+template <typename T>
+cudaError_t smooth_step(const mg_ctx* c, int l, T* u, const T* f, bool u_is_zero, bool r_ready) {
+  cudaError_t e;
+  if (u_is_zero) {
+    if ((e = launch_fdm<T>(c, l, f)) != cudaSuccess) return e;
+    return launch_scatter<T>(c, l, u, 0);
+  }
+  T* r = lvec<T>(c->lev[l].r);
+  if (!r_ready && (e = launch_sipg<T>(c, l, u, f, r, 1)) != cudaSuccess) return e;
+  if ((e = launch_fdm<T>(c, l, r)) != cudaSuccess) return e;
+  return launch_scatter<T>(c, l, u, 1);
+}
+
+// Algorithm 1 (MultigridCycle).  uL, fL: fine-level vectors.
+// u_zero: uL == 0 on entry; r_ready: lev[L].r == fL - A uL on entry.
+template <typename T>
+cudaError_t vcycle_t(const mg_ctx* c, T* uL, const T* fL, bool u_zero, bool r_ready) {
+  const int L = c->L;
+  T* u[kMaxLevels];
+  const T* f[kMaxLevels];
+  for (int l = 0; l <= L; ++l) {
+    u[l] = (l == L) ? uL : lvec<T>(c->lev[l].u);
+    f[l] = (l == L) ? fL : lvec<T>(c->lev[l].f);
+  }
+  cudaError_t e;
+  for (int l = L; l >= 1; --l) {
+    const int ns = steps_on_level(c, c->opts.ns_pre, l);
+    const bool zero = (l < L) || u_zero;  // u_l <- 0 on the lower levels
+    for (int st = 0; st < ns; ++st) {
+      if ((e = smooth_step<T>(c, l, u[l], f[l], zero && st == 0, l == L && st == 0 && r_ready && !zero)) !=
+          cudaSuccess)
+        return e;
+    }
+    if (ns == 0 && zero && (e = launch_zero<T>(c, u[l], c->lev[l].N)) != cudaSuccess) return e;
+    // f_{l-1} = I_l^T (f_l - A_l u_l)
+    T* r = lvec<T>(c->lev[l].r);
+    if ((e = launch_sipg<T>(c, l, u[l], f[l], r, 1)) != cudaSuccess) return e;
+    if ((e = launch_restrict<T>(c, l, r, lvec<T>(c->lev[l - 1].f))) != cudaSuccess) return e;
+  }
+  if ((e = coarse_solve_t<T>(c, f[0], u[0])) != cudaSuccess) return e;
+  for (int l = 1; l <= L; ++l) {
+    if ((e = launch_prolong<T>(c, l, u[l - 1], u[l])) != cudaSuccess) return e;
+    const int ns = steps_on_level(c, c->opts.ns_post, l);
+    for (int st = 0; st < ns; ++st)
+      if ((e = smooth_step<T>(c, l, u[l], f[l], false, false)) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// z = B r: one V-cycle from a zero guess, in FP64 or (mixed) in FP32 with the
+// input scaled by 1/||r|| (kSlotRR must hold r.r).
+cudaError_t precond(const mg_ctx* c, const double* r, double* z) {
+  const int L = c->L;
+  const int64_t N = c->lev[L].N;
+  if (c->opts.precision == MG_MIXED) {
+    float* f32 = lvec<float>(c->lev[L].f);
+    float* u32 = lvec<float>(c->lev[L].u);
+    cudaError_t e;
+    if ((e = launch_to_f32(c, r, f32, N, kSlotRR)) != cudaSuccess) return e;
+    if ((e = vcycle_t<float>(c, u32, f32, true, false)) != cudaSuccess) return e;
+    return launch_from_f32(c, u32, z, N, kSlotRR);
+  }
+  return vcycle_t<double>(c, z, r, true, false);
+}
+
+mg_status solve_impl(mg_ctx* c, double* u, const double* f, double tol, int maxit, int use_cg, int* iters,
+                     double* relres, double* history) {
+  const int L = c->L;
+  const int64_t N = c->lev[L].N;
+  cudaError_t err;
+  int it = 0;
+  double r0 = 0.0, rn = 0.0;
+  bool converged = false;
+  if (!use_cg) {
+    double* r = lvec<double>(c->lev[L].r);
+    if (c->opts.precision == MG_MIXED) r = c->ws.cg[1];
+    CK(launch_sipg<double>(c, L, u, f, r, 1));
+    CK(launch_dot(c, r, r, N, kSlotRR));
+    double rr = read_scalar(c, kSlotRR, &err);
+    CK(err);
+    r0 = rn = sqrt(rr);
+    if (history) history[0] = r0;
+    converged = r0 == 0.0;
+    while (!converged && it < maxit) {
+      ++it;
+      if (c->opts.precision == MG_MIXED) {
+        // defect correction: u += B r with the FP32 V-cycle
+        double* z = c->ws.cg[2];
+        CK(precond(c, r, z));
+        CK(launch_add(c, u, z, N));
+      } else {
+        CK((vcycle_t<double>(c, u, f, false, true)));
+      }
+      CK(launch_sipg<double>(c, L, u, f, r, 1));
+      CK(launch_dot(c, r, r, N, kSlotRR));
+      double v = read_scalar(c, kSlotRR, &err);
+      CK(err);
+      rn = sqrt(v);
+      if (history) history[it] = rn;
+      if (rn <= tol * r0) converged = true;
+    }
+  } else {
+    double* x = u;
+    double* r = c->ws.cg[1];
+    double* z = c->ws.cg[2];
+    double* p = c->ws.cg[3];
+    double* q = c->ws.cg[4];
+    CK(launch_sipg<double>(c, L, x, f, r, 1));
+    CK(launch_sum(c, r, N, kSlotSum));
+    CK(launch_sub_mean(c, r, N, kSlotSum));
+    CK(launch_dot(c, r, r, N, kSlotRR));
+    double rr = read_scalar(c, kSlotRR, &err);
+    CK(err);
+    r0 = rn = sqrt(rr);
+    if (history) history[0] = r0;
+    converged = r0 == 0.0;
+    if (!converged) {
+      CK(precond(c, r, z));
+      CK(launch_sum(c, z, N, kSlotSum));
+      CK(launch_sub_mean(c, z, N, kSlotSum));
+      CK(cudaMemcpyAsync(p, z, N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+      CK(launch_dot(c, r, z, N, kSlotRZ));
+    }
+    while (!converged && it < maxit) {
+      ++it;
+      CK(launch_sipg<double>(c, L, p, nullptr, q, 0));
+      CK(launch_dot(c, p, q, N, kSlotPQ));
+      CK(launch_axpy2(c, x, p, r, q, N, kSlotRZ, kSlotPQ));  // alpha = rz / pq
+      CK(launch_sum(c, r, N, kSlotSum));
+      CK(launch_sub_mean(c, r, N, kSlotSum));
+      CK(launch_dot(c, r, r, N, kSlotRR));
+      double v = read_scalar(c, kSlotRR, &err);
+      CK(err);
+      rn = sqrt(v);
+      if (history) history[it] = rn;
+      if (rn <= tol * r0) {
+        converged = true;
+        break;
+      }
+      CK(precond(c, r, z));
+      CK(launch_sum(c, z, N, kSlotSum));
+      CK(launch_sub_mean(c, z, N, kSlotSum));
+      // beta = z_new . (r_new - r_old) / (z_old . r_old) = -alpha (z_new . q) / rz_old
+      CK(launch_dot(c, z, q, N, kSlotZQ));
+      CK(launch_xpby(c, p, z, N, kSlotZQ, kSlotRZ, kSlotAlpha));
+      CK(launch_dot(c, r, z, N, kSlotRZ));
+    }
+  }
+  CK(launch_sum(c, u, N, kSlotSum));
+  CK(launch_sub_mean(c, u, N, kSlotSum));
+  CK(cudaStreamSynchronize(c->stream));
+  if (iters) *iters = it;
+  if (relres) *relres = r0 > 0.0 ? rn / r0 : 0.0;
+  if (!converged) return fail(c, MG_ENOCONV, "maximum number of iterations reached");
+  return MG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void mg_default_opts(mg_opts* o) {
+  if (!o) return;
+  o->overlap_mode = MG_OVERLAP_LAYERS;
+  o->overlap_frac = 0.08;
+  o->weight_profile = MG_WEIGHT_QUINTIC;
+  o->ns_pre = 1;
+  o->ns_post = 1;
+  o->ns_growth = 1;
+  o->precision = MG_FP64;
+  o->stream = nullptr;
+}
+
+mg_status mg_setup(double lx, double ly, double lz, int nx, int ny, int nz, int P, double penalty, int overlap,
+                   const mg_opts* opts, mg_ctx** out) {
+  if (!out) return MG_EINVAL;
+  *out = nullptr;
+  if (!(lx > 0 && ly > 0 && lz > 0) || nx < 3 || ny < 3 || nz < 3 || !(penalty > 0) || overlap < 0) return MG_EINVAL;
+  if (nx > 512 || ny > 512 || nz > 512) return MG_EINVAL;  // coarse eigensolver pairs fit one block
+  if (P < 2 || P > kMaxP || (P & (P - 1)) != 0) return MG_EINVAL;
+  mg_opts o;
+  mg_default_opts(&o);
+  if (opts) o = *opts;
+  if (o.ns_pre < 0 || o.ns_post < 0 || o.ns_growth < 1 || o.ns_pre + o.ns_post < 1) return MG_EINVAL;
+  if (o.precision != MG_FP64 && o.precision != MG_MIXED) return MG_EINVAL;
+  if (o.weight_profile != MG_WEIGHT_QUINTIC && o.weight_profile != MG_WEIGHT_LINEAR) return MG_EINVAL;
+  if (o.overlap_mode != MG_OVERLAP_LAYERS && o.overlap_mode != MG_OVERLAP_WIDTH) return MG_EINVAL;
+  if (o.overlap_mode == MG_OVERLAP_WIDTH && !(o.overlap_frac >= 0.0 && o.overlap_frac <= 0.5)) return MG_EINVAL;
+  if ((int64_t)nx * ny * nz > (int64_t)1 << 31) return MG_EINVAL;
+  mg_ctx* c = new (std::nothrow) mg_ctx();
+  if (!c) return MG_ENOMEM;
+  c->len[0] = lx;
+  c->len[1] = ly;
+  c->len[2] = lz;
+  c->ne[0] = nx;
+  c->ne[1] = ny;
+  c->ne[2] = nz;
+  c->Ne = (int64_t)nx * ny * nz;
+  c->P = P;
+  c->L = 0;
+  while ((1 << c->L) < P) ++c->L;
+  c->penalty = penalty;
+  c->overlap = overlap;
+  c->opts = o;
+  c->stream = static_cast<cudaStream_t>(o.stream);
+  c->ready = false;
+  for (int d = 0; d < 3; ++d) c->Ng[d] = 2 * c->ne[d];
+  int64_t off = 0;
+  auto tab = [&](int64_t count) {
+    int64_t o2 = off;
+    off += (count + 31) / 32 * 32;
+    return o2;
+  };
+  for (int l = 0; l <= c->L; ++l) {
+    LevelInfo& lv = c->lev[l];
+    lv.P = 1 << l;
+    lv.n = lv.P + 1;
+    lv.N = c->Ne * (int64_t)lv.n * lv.n * lv.n;
+    if (l >= 1) {
+      int maxno = lv.P / 2 + 1;
+      int no = (o.overlap_mode == MG_OVERLAP_LAYERS) ? overlap : layers_from_width(lv.P, o.overlap_frac);
+      lv.no = std::min(no, maxno);
+      lv.m = lv.n + 2 * lv.no;
+      lv.delta = (o.overlap_mode == MG_OVERLAP_LAYERS) ? layer_delta(lv.P, lv.no)
+                                                       : std::min(2.0 * o.overlap_frac, 1.0);
+    } else {
+      lv.no = 0;
+      lv.m = 0;
+      lv.delta = 0.0;
+    }
+    for (int d = 0; d < 3; ++d) {
+      lv.h[d] = c->len[d] / c->ne[d];
+      lv.g[d] = 2.0 / lv.h[d];
+      lv.mu[d] = penalty * lv.P * (lv.P + 1.0) / (2.0 * lv.h[d]);
+      DirTables& t = lv.t[d];
+      t.nodes = tab(lv.n);
+      t.weights = tab(lv.n);
+      t.mass = tab(lv.n);
+      t.lee = tab((int64_t)lv.n * lv.n);
+      t.d0 = tab(lv.n);
+      t.dp = tab(lv.n);
+      if (l >= 1) {
+        t.S = tab((int64_t)lv.m * lv.m);
+        t.SW = tab((int64_t)lv.m * lv.m);
+        t.lam = tab(lv.m);
+        t.w = tab(lv.m);
+        t.Q = t.qlam = -1;
+      } else {
+        t.S = t.SW = t.lam = t.w = -1;
+        t.Q = tab((int64_t)c->Ng[d] * c->Ng[d]);
+        t.qlam = tab(c->Ng[d]);
+      }
+    }
+    lv.dinv = (l >= 1) ? tab((int64_t)lv.m * lv.m * lv.m) : -1;
+    lv.J = (l >= 1) ? tab((int64_t)lv.n * (c->lev[l - 1].n)) : -1;
+    lv.u = lv.f = lv.r = nullptr;
+  }
+  c->ws.tab_count = off;
+  c->ws_bytes = make_layout(c).total;
+  *out = c;
+  return MG_OK;
+}
+
+mg_status mg_workspace_size(const mg_ctx* c, size_t* bytes) {
+  if (!c || !bytes) return MG_EINVAL;
+  *bytes = c->ws_bytes;
+  return MG_OK;
+}
+
+mg_status mg_bind_workspace(mg_ctx* c, void* dptr, size_t bytes) {
+  if (!c) return MG_EINVAL;
+  if (!dptr || (reinterpret_cast<uintptr_t>(dptr) & 255) != 0) return fail(c, MG_EINVAL, "workspace must be 256-byte aligned");
+  if (bytes < c->ws_bytes) return fail(c, MG_ENOMEM, "workspace too small");
+  Layout ly = make_layout(c);
+  char* b = static_cast<char*>(dptr);
+  Workspace& w = c->ws;
+  w.base = b;
+  w.bytes = bytes;
+  w.tab64 = reinterpret_cast<double*>(b + ly.tab64);
+  w.tab32 = reinterpret_cast<float*>(b + ly.tab32);
+  for (int l = 0; l <= c->L; ++l) {
+    c->lev[l].u = b + ly.lev_u[l];
+    c->lev[l].f = b + ly.lev_f[l];
+    c->lev[l].r = b + ly.lev_r[l];
+  }
+  w.corr = b + ly.corr;
+  w.coarse_a = reinterpret_cast<double*>(b + ly.ca);
+  w.coarse_b = reinterpret_cast<double*>(b + ly.cb);
+  w.coarse_f = reinterpret_cast<double*>(b + ly.cf);
+  w.coarse_u = reinterpret_cast<double*>(b + ly.cu);
+  for (int k = 0; k < 8; ++k) w.cg[k] = reinterpret_cast<double*>(b + ly.cg[k]);
+  w.red = reinterpret_cast<double*>(b + ly.red);
+  w.scal = reinterpret_cast<double*>(b + ly.scal);
+  w.status = reinterpret_cast<int*>(b + ly.status);
+  w.jac = reinterpret_cast<double*>(b + ly.jac);
+  w.jac_count = ly.jac_count;
+  CK(cudaMemsetAsync(w.status, 0, 256, c->stream));
+  CK(cudaMemsetAsync(w.scal, 0, kNumSlots * sizeof(double), c->stream));
+  CK(launch_setup(c));
+  int st = 0;
+  CK(cudaMemcpyAsync(&st, w.status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  // null mode of the coarse eigenbases: the smallest eigenvalue per direction
+  for (int d = 0; d < 3; ++d) {
+    std::vector<double> lam(c->Ng[d]);
+    CK(cudaMemcpyAsync(lam.data(), w.tab64 + c->lev[0].t[d].qlam, lam.size() * sizeof(double),
+                       cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->coarse_null[d] = (int)(std::min_element(lam.begin(), lam.end()) - lam.begin());
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  if (st != kDevOk) return fail(c, MG_ENOCONV, "setup eigensolver did not converge");
+  c->ready = true;
+  return MG_OK;
+}
+
+int mg_num_levels(const mg_ctx* c) { return c ? c->L + 1 : 0; }
+
+long long mg_num_dofs(const mg_ctx* c, int level) {
+  if (!c || level < 0 || level > c->L) return -1;
+  return c->lev[level].N;
+}
+
+int mg_level_layers(const mg_ctx* c, int level) {
+  if (!c || level < 0 || level > c->L) return -1;
+  return c->lev[level].no;
+}
+
+mg_status mg_node_coords(mg_ctx* c, int level, double* x, double* y, double* z) {
+  mg_status s = need_ready(c);
+  if (s != MG_OK) return s;
+  if (!check_level(c, level, false)) return MG_EINVAL;
+  if (!x || !y || !z) return fail(c, MG_EINVAL, "null pointer");
+  CK(launch_coords(c, level, x, y, z));
+  return MG_OK;
+}
+
+mg_status mg_rhs(mg_ctx* c, const double* f, double* b) {
+  mg_status s = need_ready(c);
+  if (s != MG_OK) return s;
+  if (!f || !b || f == b) return fail(c, MG_EINVAL, "bad pointers");
+  CK(launch_rhs(c, f, b));
+  return MG_OK;
+}
+
+mg_status mg_apply_sipg(mg_ctx* c, int level, const double* u, double* Au) {
+  mg_status s = need_ready(c);
+  if (s != MG_OK) return s;
+  if (!check_level(c, level, false)) return MG_EINVAL;
+  if (!u || !Au || u == Au) return fail(c, MG_EINVAL, "bad pointers");
+  CK(launch_sipg<double>(c, level, u, nullptr, Au, 0));
+  return MG_OK;
+}
+
+mg_status mg_apply_sipg_f32(mg_ctx* c, int level, const float* u, float* Au) {
+  mg_status s = need_ready(c);
+  if (s != MG_OK) return s;
+  if (!check_level(c, level, false)) return MG_EINVAL;
+  if (!u || !Au || u == Au) return fail(c, MG_EINVAL, "bad pointers");
+  CK(launch_sipg<float>(c, level, u, nullptr, Au, 0));
+  return MG_OK;
+}
+
+mg_status mg_residual(mg_ctx* c, int level, const double* u, const double* f, double* r) {
+  mg_status s = need_ready(c);
+  if (s != MG_OK) return s;
+  if (!check_level(c, level, false)) return MG_EINVAL;
+  if (!u || !f || !r || r == u || r == f) return fail(c, MG_EINVAL, "bad pointers");
+  CK(launch_sipg<double>(c, level, u, f, r, 1));
+  return MG_OK;
+}
+
+mg_status mg_smooth(mg_ctx* c, int level, double* u, const double* f, int nsteps) {
+  mg_status s = need_ready(c);
+  if (s != MG_OK) return s;
+  if (!check_level(c, level, true)) return MG_EINVAL;
+  if (!u || !f || u == f || nsteps < 0) return fail(c, MG_EINVAL, "bad arguments");
+  for (int k = 0; k < nsteps; ++k) CK(smooth_step<double>(c, level, u, f, false, false));
+  return MG_OK;
+}
+
+mg_status mg_smooth_f32(mg_ctx* c, int level, float* u, const float* f, int nsteps) {
+  mg_status s = need_ready(c);
+  if (s != MG_OK) return s;
+  if (!check_level(c, level, true)) return MG_EINVAL;
+  if (!u || !f || u == f || nsteps < 0) return fail(c, MG_EINVAL, "bad arguments");
+  for (int k = 0; k < nsteps; ++k) CK(smooth_step<float>(c, level, u, f, false, false));
+  return MG_OK;
+}
+
+mg_status mg_restrict_residual(mg_ctx* c, int level, const double* u, const double* f, double* fc) {
+  mg_status s = need_ready(c);
+  if (s != MG_OK) return s;
+  if (!check_level(c, level, true)) return MG_EINVAL;
+  if (!u || !f || !fc) return fail(c, MG_EINVAL, "null pointer");
+  double* r = lvec<double>(c->lev[level].r);
+  CK(launch_sipg<double>(c, level, u, f, r, 1));
+  CK(launch_restrict<double>(c, level, r, fc));
+  return MG_OK;
+}
+
+mg_status mg_prolongate(mg_ctx* c, int level, const double* uc, double* u) {
+  mg_status s = need_ready(c);
+  if (s != MG_OK) return s;
+  if (!check_level(c, level, true)) return MG_EINVAL;
+  if (!uc || !u) return fail(c, MG_EINVAL, "null pointer");
+  CK(launch_prolong<double>(c, level, uc, u));
+  return MG_OK;
+}
+
+mg_status mg_coarse_solve(mg_ctx* c, const double* f0, double* u0) {
+  mg_status s = need_ready(c);
+  if (s != MG_OK) return s;
+  if (!f0 || !u0 || f0 == u0) return fail(c, MG_EINVAL, "bad pointers");
+  CK(launch_coarse_solve(c, f0, u0));
+  return MG_OK;
+}
+
+mg_status mg_vcycle(mg_ctx* c, double* u, const double* f) {
+  mg_status s = need_ready(c);
+  if (s != MG_OK) return s;
+  if (!u || !f || u == f) return fail(c, MG_EINVAL, "bad pointers");
+  CK((vcycle_t<double>(c, u, f, false, false)));
+  return MG_OK;
+}
+
+mg_status mg_vcycle_f32(mg_ctx* c, float* u, const float* f) {
+  mg_status s = need_ready(c);
+  if (s != MG_OK) return s;
+  if (!u || !f || u == f) return fail(c, MG_EINVAL, "bad pointers");
+  CK((vcycle_t<float>(c, u, f, false, false)));
+  return MG_OK;
+}
+
+mg_status mg_solve(mg_ctx* c, double* u, const double* f, double tol, int maxit, int use_cg, int* iters,
+                   double* relres, double* history) {
+  mg_status s = need_ready(c);
+  if (s != MG_OK) return s;
+  if (!u || !f || u == f || maxit < 0 || !(tol >= 0.0)) return fail(c, MG_EINVAL, "bad arguments");
+  return solve_impl(c, u, f, tol, maxit, use_cg ? 1 : 0, iters, relres, history);
+}
+
+mg_status mg_solve_host(mg_ctx* c, double* u_host, const double* f_host, double tol, int maxit, int use_cg,
+                        int* iters, double* relres, double* history) {
+  mg_status s = need_ready(c);
+  if (s != MG_OK) return s;
+  if (!u_host || !f_host || maxit < 0 || !(tol >= 0.0)) return fail(c, MG_EINVAL, "bad arguments");
+  const int64_t N = c->lev[c->L].N;
+  double* u = c->ws.cg[5];
+  double* f = c->ws.cg[6];
+  CK(cudaMemcpyAsync(f, f_host, N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(u, u_host, N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  mg_status st = solve_impl(c, u, f, tol, maxit, use_cg ? 1 : 0, iters, relres, history);
+  if (st != MG_OK && st != MG_ENOCONV) return st;
+  CK(cudaMemcpyAsync(u_host, u, N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return st;
+}
+
+mg_status mg_get_table(mg_ctx* c, int level, int dir, int what, double* host_out, int capacity, int* count) {
+  mg_status s = need_ready(c);
+  if (s != MG_OK) return s;
+  if (!check_level(c, level, false) || dir < 0 || dir > 2 || !host_out || !count)
+    return fail(c, MG_EINVAL, "bad arguments");
+  const LevelInfo& lv = c->lev[level];
+  const DirTables& t = lv.t[dir];
+  int64_t off = -1, cnt = 0;
+  const int n = lv.n, m = lv.m, Ng = c->Ng[dir];
+  switch (what) {
+    case 0: off = t.nodes; cnt = n; break;
+    case 1: off = t.weights; cnt = n; break;
+    case 2: off = t.mass; cnt = n; break;
+    case 3: off = t.lee; cnt = (int64_t)n * n; break;
+    case 4: off = t.lam; cnt = m; break;
+    case 5: off = t.S; cnt = (int64_t)m * m; break;
+    case 6: off = t.w; cnt = m; break;
+    case 7: off = lv.J; cnt = level >= 1 ? (int64_t)n * c->lev[level - 1].n : 0; break;
+    case 8: off = t.qlam; cnt = Ng; break;
+    case 9: off = t.Q; cnt = (int64_t)Ng * Ng; break;
+    default: return fail(c, MG_EINVAL, "unknown table");
+  }
+  if (off < 0 || cnt <= 0) return fail(c, MG_EINVAL, "table not present on this level");
+  if (cnt > capacity) return fail(c, MG_EINVAL, "capacity too small");
+  CK(cudaMemcpyAsync(host_out, c->ws.tab64 + off, cnt * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  *count = (int)cnt;
+  return MG_OK;
+}
+
+const char* mg_last_error(const mg_ctx* c) {
+  if (!c) return "null context";
+  return c->err.c_str();
+}
+
+void mg_destroy(mg_ctx* c) { delete c; }
+
+}  // extern "C"

@@ -1,0 +1,147 @@
+// Internal declarations of the GB300 multigrid library: context, device table
+// layout and the host-side launchers of every kernel.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/mgdg.h"
+
+namespace mgdg {
+
+constexpr int kMaxLevels = 6;   // P <= 32
+constexpr int kMaxP = 32;
+constexpr int kMaxN = kMaxP + 1;        // nodes per element and direction
+constexpr int kMaxM = kMaxN + 2 * (kMaxP / 2 + 1);  // widest subdomain line
+constexpr int kRedBlocks = 304;         // fixed grid of the two-stage reductions (2 per SM)
+
+// Slots of the device scalar array ws.scal.
+enum Slot : int {
+  kSlotRZ = 0,      // r . z
+  kSlotPQ = 1,      // p . q
+  kSlotAlpha = 2,   // alpha
+  kSlotZQ = 3,      // z . q
+  kSlotRR = 4,      // r . r
+  kSlotSum = 5,     // scratch sum for mean projections
+  kSlotMassF = 6,   // sum M f
+  kSlotMass = 7,    // sum M
+  kSlotScale = 8,   // norm used to scale FP32 preconditioner input
+  kSlotCoarse = 60, // coarse-solve mean
+  kSlotSumT = 61,   // mean projection of FP32 vectors
+  kNumSlots = 64
+};
+
+// Status word written by device code (setup eigensolvers) and read by the host.
+enum DevStatus : int { kDevOk = 0, kDevNoConv = 1 };
+
+// Offsets (in values) of the 1D tables of one level and direction inside the
+// table arrays tab64 / tab32 (same offsets in both).
+struct DirTables {
+  int64_t nodes, weights, mass, lee, d0, dp;  // n, n, n, n*n, n, n
+  int64_t S, SW, lam, w;                      // m*m, m*m, m, m  (level >= 1)
+  int64_t Q, qlam;                            // Ng*Ng, Ng       (level 0)
+};
+
+struct LevelInfo {
+  int P, n, m, no;       // order, nodes per direction, subdomain width, overlap layers
+  double delta;          // hat-weight half-width (reference units)
+  int64_t N;             // DOFs
+  double h[3], g[3], mu[3];
+  DirTables t[3];
+  int64_t dinv;          // m^3: 1 / (lam_x[a] + lam_y[b] + lam_z[c])
+  int64_t J;             // n * n_c interpolation from level l-1 (level >= 1)
+  // device vectors (bytes sized for FP64; FP32 code uses the first half)
+  void* u;
+  void* f;
+  void* r;
+};
+
+struct Workspace {
+  char* base = nullptr;
+  size_t bytes = 0;
+  double* tab64 = nullptr;
+  float* tab32 = nullptr;
+  int64_t tab_count = 0;
+  void* corr = nullptr;        // smoother corrections, Ne * m^3 (largest level)
+  double* coarse_a = nullptr;  // coarse FDM scratch, N_0 each
+  double* coarse_b = nullptr;
+  double* coarse_f = nullptr;  // FP64 coarse rhs / solution for the FP32 hierarchy
+  double* coarse_u = nullptr;
+  double* cg[8] = {nullptr};   // FP64 outer vectors: x, r, z, p, q, u_io, f_io, spare
+  double* red = nullptr;       // reduction partials (kRedBlocks * 2)
+  double* scal = nullptr;      // device scalars (64)
+  int* status = nullptr;       // device status word
+  double* jac = nullptr;       // eigensolver scratch
+  int64_t jac_count = 0;
+};
+
+}  // namespace mgdg
+
+struct mg_ctx {
+  double len[3];
+  int ne[3];
+  int64_t Ne;
+  int P, L;
+  double penalty;
+  int overlap;
+  mg_opts opts;
+  cudaStream_t stream;
+  mgdg::LevelInfo lev[mgdg::kMaxLevels];
+  int Ng[3];               // coarse 1D sizes 2 n_d
+  int coarse_null[3];      // index of the constant eigenvector per direction
+  mgdg::Workspace ws;
+  size_t ws_bytes;
+  bool ready;
+  std::string err;
+};
+
+namespace mgdg {
+
+// ---- setup (setup.cu) ----
+cudaError_t launch_setup(mg_ctx* c);
+
+// ---- operator (sipg.cu) ----
+// out = mode==0 ? A u : f - A u, on level l, T = double | float.
+template <typename T>
+cudaError_t launch_sipg(const mg_ctx* c, int l, const T* u, const T* f, T* out, int residual);
+
+// ---- smoother (schwarz.cu) ----
+// Corrections of all subdomains from residual r into ws.corr, then
+// u = beta*u + scatter(corr).  beta is 0 (u := correction) or 1.
+template <typename T>
+cudaError_t launch_fdm(const mg_ctx* c, int l, const T* r);
+template <typename T>
+cudaError_t launch_scatter(const mg_ctx* c, int l, T* u, int accumulate);
+
+// ---- transfers (transfer.cu) ----
+template <typename T>
+cudaError_t launch_restrict(const mg_ctx* c, int l, const T* r_fine, T* f_coarse);
+template <typename T>
+cudaError_t launch_prolong(const mg_ctx* c, int l, const T* u_coarse, T* u_fine);
+
+// ---- coarse solve (coarse.cu) ----
+cudaError_t launch_coarse_solve(const mg_ctx* c, const double* f0, double* u0);
+cudaError_t launch_coarse_solve_f32(const mg_ctx* c, const float* f0, float* u0);
+
+// ---- vectors (blas.cu) ----
+// dot products: result into device scalar slot `slot` of ws.scal
+cudaError_t launch_dot(const mg_ctx* c, const double* x, const double* y, int64_t n, int slot);
+cudaError_t launch_sum(const mg_ctx* c, const double* x, int64_t n, int slot);
+cudaError_t launch_sub_mean(const mg_ctx* c, double* x, int64_t n, int sum_slot);
+template <typename T>
+cudaError_t launch_sub_mean_t(const mg_ctx* c, T* x, int64_t n);
+cudaError_t launch_axpy2(const mg_ctx* c, double* x, const double* p, double* r, const double* q, int64_t n,
+                         int num_slot, int den_slot);
+cudaError_t launch_add(const mg_ctx* c, double* y, const double* x, int64_t n);  // y += x
+cudaError_t launch_xpby(const mg_ctx* c, double* p, const double* z, int64_t n, int num_slot, int den_slot,
+                        int alpha_slot);
+cudaError_t launch_to_f32(const mg_ctx* c, const double* x, float* y, int64_t n, int norm_slot);
+cudaError_t launch_from_f32(const mg_ctx* c, const float* x, double* y, int64_t n, int norm_slot);
+cudaError_t launch_rhs(const mg_ctx* c, const double* f, double* b);
+cudaError_t launch_coords(const mg_ctx* c, int l, double* x, double* y, double* z);
+template <typename T>
+cudaError_t launch_zero(const mg_ctx* c, T* x, int64_t n);
+
+}  // namespace mgdg

@@ -1,0 +1,469 @@
+// Per-level 1D setup on the device (FP64), one thread block per level and
+// direction.
+//
+// Section 2: GLL nodes, weights and differentiation matrix; 1D mass
+// M = (h/2) diag(w) and SIPG stiffness L (element block K + face terms, face
+// couplings to the neighbours), Eq. (A).
+// Section 3.1: restricted 1D matrices L_s = R L R^T, M_s = R M R^T of the
+// element-centred subdomain, the generalised eigenproblem L_s S = M_s S Lambda
+// with S^T M_s S = I (solved as the symmetric problem
+// M_s^{-1/2} L_s M_s^{-1/2} V = V Lambda, S = M_s^{-1/2} V), the hat weights w
+// (Fig. wH), and the table 1/(lam_x + lam_y + lam_z) of the fast diagonalisation.
+// Section 3.2: embedded interpolation J from order P_{l-1} to P_l; the
+// eigenbasis of the whole periodic 1D problem on the coarsest level (used to
+// apply A_0^+ directly).
+//
+// Both the subdomain problem and the periodic coarse problem are symmetric
+// under reflection of the line, so the eigenproblem is split into its even and
+// odd halves before the cyclic Jacobi iteration; every eigenvector is then
+// exactly even or odd (the first ne columns of S are even, the rest odd).
+#include <math.h>
+
+#include "mg_internal.h"
+
+namespace mgdg {
+namespace {
+
+constexpr int kSetupThreads = 256;
+constexpr int kMaxSweeps = 60;
+
+// Legendre polynomial L_P(x) and its first two derivatives (three-term
+// recurrence; derivatives from (x^2-1) L_P' = P (x L_P - L_{P-1}) and the
+// Legendre equation (1-x^2) L'' - 2x L' + P(P+1) L = 0), for |x| < 1.
+__device__ void legendre(int P, double x, double* lp, double* dlp, double* d2lp) {
+  double l0 = 1.0, l1 = x;
+  for (int k = 1; k < P; ++k) {
+    double l2 = ((2.0 * k + 1.0) * x * l1 - k * l0) / (k + 1.0);
+    l0 = l1;
+    l1 = l2;
+  }
+  *lp = l1;
+  double d = P * (x * l1 - l0) / (x * x - 1.0);
+  *dlp = d;
+  *d2lp = (2.0 * x * d - P * (P + 1.0) * l1) / (1.0 - x * x);
+}
+
+__device__ double legendre_value(int P, double x) {
+  if (P == 0) return 1.0;
+  double l0 = 1.0, l1 = x;
+  for (int k = 1; k < P; ++k) {
+    double l2 = ((2.0 * k + 1.0) * x * l1 - k * l0) / (k + 1.0);
+    l0 = l1;
+    l1 = l2;
+  }
+  return l1;
+}
+
+// GLL nodes of order P by Newton's method on L_P'(x) = 0 from the
+// Chebyshev-Gauss-Lobatto points, then symmetrised.  Single thread.
+__device__ void gll_nodes_dev(int P, double* x) {
+  const double pi = 3.14159265358979323846;
+  x[0] = -1.0;
+  x[P] = 1.0;
+  for (int k = 1; k < P; ++k) {
+    double t = -cos(pi * k / P);
+    for (int it = 0; it < 100; ++it) {
+      double lp, dlp, d2lp;
+      legendre(P, t, &lp, &dlp, &d2lp);
+      double dt = dlp / d2lp;
+      t -= dt;
+      if (fabs(dt) < 1e-16) break;
+    }
+    x[k] = t;
+  }
+  for (int k = 0; k <= P / 2; ++k) {
+    double s = 0.5 * (x[P - k] - x[k]);
+    x[k] = -s;
+    x[P - k] = s;
+  }
+  if (P % 2 == 0) x[P / 2] = 0.0;
+}
+
+// Block-wide sum of one double per thread (kSetupThreads threads).
+__device__ double block_sum(double v, double* sh) {
+  int t = threadIdx.x;
+  sh[t] = v;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (t < s) sh[t] += sh[t + s];
+    __syncthreads();
+  }
+  double r = sh[0];
+  __syncthreads();
+  return r;
+}
+
+// Cyclic Jacobi eigensolver for a symmetric n x n matrix A (row-major, global
+// scratch), parallel round-robin ordering: n/2 disjoint rotations per step.
+// On return the diagonal of A holds the eigenvalues and V (n x n) the
+// eigenvectors as columns.  Returns false if kMaxSweeps sweeps did not bring
+// the off-diagonal norm below 1e-15 of the diagonal norm.
+__device__ bool jacobi(double* A, double* V, int n, double* sh_red, int* sh_p, int* sh_q, double* sh_c,
+                       double* sh_s) {
+  const int t = threadIdx.x, nt = blockDim.x;
+  for (int i = t; i < n * n; i += nt) V[i] = (i / n == i % n) ? 1.0 : 0.0;
+  __syncthreads();
+  if (n <= 1) return true;
+  const int np = n + (n & 1);
+  const int half = np / 2;
+  bool converged = false;
+  for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
+    double off = 0.0, dia = 0.0;
+    for (int i = t; i < n * n; i += nt) {
+      double v = A[i];
+      if (i / n == i % n) dia += v * v; else off += v * v;
+    }
+    off = block_sum(off, sh_red);
+    dia = block_sum(dia, sh_red);
+    if (off <= 1e-30 * dia) {
+      converged = true;
+      break;
+    }
+    for (int round = 0; round < np - 1; ++round) {
+      for (int k = t; k < half; k += nt) {
+        int a = (k == 0) ? 0 : 1 + ((k - 1 + round) % (np - 1));
+        int b = 1 + ((np - 2 - k + round) % (np - 1));
+        int p = a < b ? a : b, q = a < b ? b : a;
+        double c = 1.0, s = 0.0;
+        if (q < n) {
+          double apq = A[p * n + q];
+          if (apq != 0.0) {
+            double tau = (A[q * n + q] - A[p * n + p]) / (2.0 * apq);
+            double tt = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+            c = 1.0 / sqrt(1.0 + tt * tt);
+            s = tt * c;
+          }
+        }
+        sh_p[k] = p;
+        sh_q[k] = q;
+        sh_c[k] = c;
+        sh_s[k] = s;
+      }
+      __syncthreads();
+      for (int idx = t; idx < half * n; idx += nt) {  // rows: A <- J^T A
+        int k = idx / n, j = idx % n;
+        int p = sh_p[k], q = sh_q[k];
+        if (q >= n) continue;
+        double c = sh_c[k], s = sh_s[k];
+        double apj = A[p * n + j], aqj = A[q * n + j];
+        A[p * n + j] = c * apj - s * aqj;
+        A[q * n + j] = s * apj + c * aqj;
+      }
+      __syncthreads();
+      for (int idx = t; idx < half * n; idx += nt) {  // columns: A <- A J, V <- V J
+        int k = idx / n, i = idx % n;
+        int p = sh_p[k], q = sh_q[k];
+        if (q >= n) continue;
+        double c = sh_c[k], s = sh_s[k];
+        double aip = A[i * n + p], aiq = A[i * n + q];
+        A[i * n + p] = c * aip - s * aiq;
+        A[i * n + q] = s * aip + c * aiq;
+        double vip = V[i * n + p], viq = V[i * n + q];
+        V[i * n + p] = c * vip - s * viq;
+        V[i * n + q] = s * vip + c * viq;
+      }
+      __syncthreads();
+    }
+  }
+  return converged;
+}
+
+// Symmetric generalised eigenproblem L S = M S Lambda (M diagonal > 0, L and M
+// centro-symmetric, size m) by even/odd splitting and Jacobi.
+// scratch: >= 4 m^2 doubles.  Writes S (m x m, column p = eigenvector p, even
+// modes first) and lam (m).  Returns false on non-convergence.
+__device__ bool gen_eig_centro(const double* L, const double* M, int m, double* S, double* lam, double* scratch,
+                               double* sh_red, int* sh_p, int* sh_q, double* sh_c, double* sh_s) {
+  const int t = threadIdx.x, nt = blockDim.x;
+  const int hm = m / 2, odd_m = m & 1;
+  const int ne = hm + odd_m, no = hm;
+  const double r2 = 0.70710678118654752440;
+  double* E = scratch;
+  double* VE = E + ne * ne;
+  double* O = VE + ne * ne;
+  double* VO = O + (no > 0 ? no * no : 1);
+  // C = M^{-1/2} L M^{-1/2}
+  auto C = [&](int a, int b) { return L[a * m + b] / sqrt(M[a] * M[b]); };
+  for (int idx = t; idx < ne * ne; idx += nt) {
+    int a = idx / ne, b = idx % ne;
+    double v;
+    if (a < hm && b < hm) v = C(a, b) + C(a, m - 1 - b);
+    else if (a < hm) v = 2.0 * r2 * C(a, hm);
+    else if (b < hm) v = 2.0 * r2 * C(hm, b);
+    else v = C(hm, hm);
+    E[idx] = v;
+  }
+  for (int idx = t; idx < no * no; idx += nt) {
+    int a = idx / no, b = idx % no;
+    O[idx] = C(a, b) - C(a, m - 1 - b);
+  }
+  __syncthreads();
+  bool ok = jacobi(E, VE, ne, sh_red, sh_p, sh_q, sh_c, sh_s);
+  ok = jacobi(O, VO, no, sh_red, sh_p, sh_q, sh_c, sh_s) && ok;
+  for (int idx = t; idx < m * m; idx += nt) {
+    int a = idx / m, p = idx % m;  // entry a of eigenvector p
+    double v;
+    if (p < ne) {
+      int aa = a < hm ? a : (a >= m - hm ? m - 1 - a : hm);
+      v = (aa < hm) ? VE[aa * ne + p] * r2 : VE[aa * ne + p];
+    } else {
+      int q = p - ne;
+      if (a < hm) v = VO[a * no + q] * r2;
+      else if (a >= m - hm) v = -VO[(m - 1 - a) * no + q] * r2;
+      else v = 0.0;
+    }
+    S[idx] = v / sqrt(M[a]);
+  }
+  for (int p = t; p < m; p += nt) lam[p] = (p < ne) ? E[p * ne + p] : O[(p - ne) * no + (p - ne)];
+  __syncthreads();
+  return ok;
+}
+
+__device__ double hat_weight(double xi_h, double delta, int profile) {
+  double a = fabs(xi_h);
+  if (delta <= 0.0) return a < 1.0 ? 1.0 : (a == 1.0 ? 0.5 : 0.0);
+  if (a <= 1.0 - delta) return 1.0;
+  if (a >= 1.0 + delta) return 0.0;
+  double tt = (a - 1.0 + delta) / (2.0 * delta);
+  double q = (profile == MG_WEIGHT_LINEAR) ? tt : tt * tt * tt * (10.0 - 15.0 * tt + 6.0 * tt * tt);
+  return 1.0 - q;
+}
+
+struct SetupParams {
+  int P, n, m, no, profile, level, Pc;
+  double delta, h, g, mu;
+  DirTables t;
+  int64_t J;
+  int Ng;        // coarse: 2 * elements in this direction
+};
+
+struct SetupBatch {
+  SetupParams p[kMaxLevels * 3];
+};
+
+// Shared part of every block: GLL nodes/weights/D of order P in shared memory
+// and the element block of L.
+struct BasisSmem {
+  double x[kMaxN], w[kMaxN], D[kMaxN * kMaxN], Lee[kMaxN * kMaxN];
+  double xc[kMaxN], lamc[kMaxN];
+  double red[kSetupThreads];
+  int sp[kSetupThreads], sq[kSetupThreads];
+  double sc[kSetupThreads], ss[kSetupThreads];
+};
+
+__device__ void build_basis(const SetupParams& q, BasisSmem& sm) {
+  const int t = threadIdx.x, nt = blockDim.x;
+  const int P = q.P, n = q.n;
+  if (t == 0) gll_nodes_dev(P, sm.x);
+  __syncthreads();
+  for (int i = t; i < n; i += nt) {
+    double lp = legendre_value(P, sm.x[i]);
+    sm.w[i] = 2.0 / (P * (P + 1.0) * lp * lp);
+  }
+  for (int idx = t; idx < n * n; idx += nt) {
+    int i = idx / n, j = idx % n;
+    double v;
+    if (i != j) v = legendre_value(P, sm.x[i]) / (legendre_value(P, sm.x[j]) * (sm.x[i] - sm.x[j]));
+    else if (i == 0) v = -P * (P + 1.0) / 4.0;
+    else if (i == P) v = P * (P + 1.0) / 4.0;
+    else v = 0.0;
+    sm.D[idx] = v;
+  }
+  __syncthreads();
+  // element block: g D^T W D + mu (e_0 e_0^T + e_P e_P^T)
+  //   - g/2 (e_P D_P + D_P^T e_P^T) + g/2 (e_0 D_0 + D_0^T e_0^T)
+  const double g = q.g, mu = q.mu;
+  for (int idx = t; idx < n * n; idx += nt) {
+    int i = idx / n, j = idx % n;
+    double k = 0.0;
+    for (int a = 0; a < n; ++a) k += sm.w[a] * sm.D[a * n + i] * sm.D[a * n + j];
+    double v = g * k;
+    if (i == j && (i == 0 || i == P)) v += mu;
+    if (i == P) v -= 0.5 * g * sm.D[P * n + j];
+    if (j == P) v -= 0.5 * g * sm.D[P * n + i];
+    if (i == 0) v += 0.5 * g * sm.D[0 * n + j];
+    if (j == 0) v += 0.5 * g * sm.D[0 * n + i];
+    sm.Lee[idx] = v;
+  }
+  __syncthreads();
+}
+
+// 1D global-L entry between node i of element offset da and node j of element
+// offset db (|da - db| <= 1, infinite or periodic line with >= 3 elements).
+__device__ double line_entry(const BasisSmem& sm, const SetupParams& q, int da, int i, int db, int j) {
+  const int n = q.n, P = q.P;
+  const double g = q.g, mu = q.mu;
+  if (da == db) return sm.Lee[i * n + j];
+  if (db == da + 1) {  // row in the left element, column in the right one
+    double v = 0.0;
+    if (i == P && j == 0) v -= mu;
+    if (i == P) v -= 0.5 * g * sm.D[0 * n + j];
+    if (j == 0) v += 0.5 * g * sm.D[P * n + i];
+    return v;
+  }
+  if (db == da - 1) {  // row in the right element, column in the left one
+    double v = 0.0;
+    if (i == 0 && j == P) v -= mu;
+    if (i == 0) v += 0.5 * g * sm.D[P * n + j];
+    if (j == P) v -= 0.5 * g * sm.D[0 * n + i];
+    return v;
+  }
+  return 0.0;
+}
+
+__global__ void __launch_bounds__(kSetupThreads) k_setup_level(SetupBatch batch, double* tab, double* scratch,
+                                                             int64_t scratch_per_block, int* status) {
+  __shared__ BasisSmem sm;
+  const SetupParams q = batch.p[blockIdx.x];
+  const int t = threadIdx.x, nt = blockDim.x;
+  const int n = q.n;
+  build_basis(q, sm);
+  for (int i = t; i < n; i += nt) {
+    tab[q.t.nodes + i] = sm.x[i];
+    tab[q.t.weights + i] = sm.w[i];
+    tab[q.t.mass + i] = 0.5 * q.h * sm.w[i];
+    tab[q.t.d0 + i] = sm.D[0 * n + i];
+    tab[q.t.dp + i] = sm.D[q.P * n + i];
+  }
+  for (int i = t; i < n * n; i += nt) tab[q.t.lee + i] = sm.Lee[i];
+  double* scr = scratch + blockIdx.x * scratch_per_block;
+
+  if (q.level == 0) {
+    // periodic coarse line of Ng = 2 * elements nodes, index 2 e + i
+    const int Ng = q.Ng, ne = Ng / n;
+    double* Lg = scr;
+    double* Mg = Lg + Ng * Ng;
+    double* wk = Mg + Ng;
+    for (int idx = t; idx < Ng * Ng; idx += nt) {
+      int r = idx / Ng, c = idx % Ng;
+      int er = r / n, ir = r % n, ec = c / n, ic = c % n;
+      int d = ec - er;
+      if (d == ne - 1) d = -1;
+      if (d == -(ne - 1)) d = 1;
+      Lg[idx] = (d >= -1 && d <= 1) ? line_entry(sm, q, 0, ir, d, ic) : 0.0;
+    }
+    for (int i = t; i < Ng; i += nt) Mg[i] = 0.5 * q.h * sm.w[i % n];
+    __syncthreads();
+    bool ok = gen_eig_centro(Lg, Mg, Ng, tab + q.t.Q, tab + q.t.qlam, wk, sm.red, sm.sp, sm.sq, sm.sc, sm.ss);
+    if (!ok && t == 0) atomicExch(status, kDevNoConv);
+    return;
+  }
+
+  // element-centred subdomain line: last `no` nodes of the left neighbour, the
+  // element, first `no` nodes of the right neighbour
+  const int m = q.m, no = q.no;
+  double* Ls = scr;
+  double* Ms = Ls + m * m;
+  double* wk = Ms + m;
+  auto node_of = [&](int a, int* de, int* ii) {
+    if (a < no) { *de = -1; *ii = n - no + a; }
+    else if (a < no + n) { *de = 0; *ii = a - no; }
+    else { *de = 1; *ii = a - no - n; }
+  };
+  for (int idx = t; idx < m * m; idx += nt) {
+    int a = idx / m, b = idx % m, da, ia, db, ib;
+    node_of(a, &da, &ia);
+    node_of(b, &db, &ib);
+    Ls[idx] = line_entry(sm, q, da, ia, db, ib);
+  }
+  for (int a = t; a < m; a += nt) {
+    int da, ia;
+    node_of(a, &da, &ia);
+    Ms[a] = 0.5 * q.h * sm.w[ia];
+    double xi_h = sm.x[ia] + 2.0 * da;
+    tab[q.t.w + a] = (no == 0) ? 1.0 : hat_weight(xi_h, q.delta, q.profile);
+  }
+  __syncthreads();
+  bool ok = gen_eig_centro(Ls, Ms, m, tab + q.t.S, tab + q.t.lam, wk, sm.red, sm.sp, sm.sq, sm.sc, sm.ss);
+  if (!ok && t == 0) atomicExch(status, kDevNoConv);
+  __syncthreads();
+  // S with the weights folded in: SW[a][p] = w[a] S[a][p]
+  for (int idx = t; idx < m * m; idx += nt) tab[q.t.SW + idx] = tab[q.t.w + idx / m] * tab[q.t.S + idx];
+  // interpolation from order Pc (barycentric form), written by the x block only
+  if (q.J >= 0) {
+    const int Pc = q.Pc, nc = Pc + 1;
+    if (t == 0) gll_nodes_dev(Pc, sm.xc);
+    __syncthreads();
+    for (int i = t; i < nc; i += nt) {
+      double prod = 1.0;
+      for (int k = 0; k < nc; ++k)
+        if (k != i) prod *= (sm.xc[i] - sm.xc[k]);
+      sm.lamc[i] = 1.0 / prod;
+    }
+    __syncthreads();
+    for (int idx = t; idx < n * nc; idx += nt) {
+      int a = idx / nc, i = idx % nc;
+      double xa = sm.x[a];
+      int hit = -1;
+      for (int k = 0; k < nc; ++k)
+        if (fabs(xa - sm.xc[k]) < 1e-14) hit = k;
+      double v;
+      if (hit >= 0) {
+        v = (hit == i) ? 1.0 : 0.0;
+      } else {
+        double den = 0.0;
+        for (int k = 0; k < nc; ++k) den += sm.lamc[k] / (xa - sm.xc[k]);
+        v = (sm.lamc[i] / (xa - sm.xc[i])) / den;
+      }
+      tab[q.J + idx] = v;
+    }
+  }
+}
+
+__global__ void k_setup_dinv(double* tab, int64_t dinv, int64_t lx, int64_t ly, int64_t lz, int m) {
+  int64_t total = (int64_t)m * m * m;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    int a = (int)(i % m), b = (int)((i / m) % m), c = (int)(i / ((int64_t)m * m));
+    tab[dinv + i] = 1.0 / (tab[lx + a] + tab[ly + b] + tab[lz + c]);
+  }
+}
+
+__global__ void k_cast_tables(const double* src, float* dst, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = (float)src[i];
+}
+
+}  // namespace
+
+cudaError_t launch_setup(mg_ctx* c) {
+  SetupBatch batch;
+  int nb = 0;
+  for (int l = 0; l <= c->L; ++l) {
+    const LevelInfo& lv = c->lev[l];
+    for (int d = 0; d < 3; ++d) {
+      SetupParams& q = batch.p[nb++];
+      q.P = lv.P;
+      q.n = lv.n;
+      q.m = lv.m;
+      q.no = lv.no;
+      q.profile = c->opts.weight_profile;
+      q.level = l;
+      q.Pc = l > 0 ? c->lev[l - 1].P : 0;
+      q.delta = lv.delta;
+      q.h = lv.h[d];
+      q.g = lv.g[d];
+      q.mu = lv.mu[d];
+      q.t = lv.t[d];
+      q.J = (l > 0 && d == 0) ? lv.J : -1;
+      q.Ng = (l == 0) ? c->Ng[d] : 0;
+    }
+  }
+  int64_t per_block = c->ws.jac_count / nb;
+  cudaStream_t s = c->stream;
+  k_setup_level<<<nb, kSetupThreads, 0, s>>>(batch, c->ws.tab64, c->ws.jac, per_block, c->ws.status);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  for (int l = 1; l <= c->L; ++l) {
+    const LevelInfo& lv = c->lev[l];
+    int64_t total = (int64_t)lv.m * lv.m * lv.m;
+    int blocks = (int)((total + 255) / 256);
+    if (blocks > 1024) blocks = 1024;
+    k_setup_dinv<<<blocks, 256, 0, s>>>(c->ws.tab64, lv.dinv, lv.t[0].lam, lv.t[1].lam, lv.t[2].lam, lv.m);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  k_cast_tables<<<256, 256, 0, s>>>(c->ws.tab64, c->ws.tab32, c->ws.tab_count);
+  return cudaGetLastError();
+}
+
+}  // namespace mgdg

@@ -1,0 +1,95 @@
+"""CPU checks of the C-ABI library: it loads, exports every symbol that
+include/mgdg.h declares, and its host-only logic (argument validation, level
+sizes, overlap layers, workspace sizing, not-ready errors) behaves.  No
+compute call is made: there is no GPU here."""
+import ctypes
+import json
+import os
+
+import pytest
+
+import paper_1612_04796_gb300 as pkg
+from paper_1612_04796_gb300._lib import MgOpts
+
+HERE = os.path.dirname(__file__)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    pkg.build()
+    return pkg.load_library()
+
+
+def test_exports_every_declared_symbol(lib):
+    names = pkg.header_symbols()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def _setup(lib, P=4, counts=(4, 4, 4), overlap=1, lengths=(1.0, 1.0, 1.0), **kw):
+    opts = MgOpts()
+    lib.mg_default_opts(ctypes.byref(opts))
+    for k, v in kw.items():
+        setattr(opts, k, v)
+    ctx = ctypes.c_void_p()
+    st = lib.mg_setup(lengths[0], lengths[1], lengths[2], counts[0], counts[1], counts[2], P, 2.0, overlap,
+                      ctypes.byref(opts), ctypes.byref(ctx))
+    return st, ctx
+
+
+def test_defaults(lib):
+    o = MgOpts()
+    lib.mg_default_opts(ctypes.byref(o))
+    assert (o.ns_pre, o.ns_post, o.ns_growth, o.precision, o.overlap_mode, o.weight_profile) == (1, 1, 1, 0, 0, 0)
+
+
+@pytest.mark.parametrize("bad", [dict(P=3), dict(P=1), dict(P=64), dict(counts=(2, 4, 4)), dict(counts=(4, 4, 513)),
+                                 dict(overlap=-1), dict(lengths=(0.0, 1.0, 1.0)), dict(ns_pre=0, ns_post=0),
+                                 dict(precision=7), dict(overlap_mode=1, overlap_frac=0.75)])
+def test_rejects_bad_arguments(lib, bad):
+    st, ctx = _setup(lib, **bad)
+    assert st == 1 and not ctx.value
+
+
+@pytest.mark.parametrize("P", [2, 4, 8, 16, 32])
+def test_levels_and_sizes(lib, P):
+    st, ctx = _setup(lib, P=P, counts=(3, 4, 5), overlap=4)
+    assert st == 0
+    L = P.bit_length() - 1
+    assert lib.mg_num_levels(ctx) == L + 1
+    for l in range(L + 1):
+        assert lib.mg_num_dofs(ctx, l) == 60 * (2 ** l + 1) ** 3
+        if l >= 1:
+            assert lib.mg_level_layers(ctx, l) == min(4, 2 ** (l - 1) + 1)
+    assert lib.mg_num_dofs(ctx, L + 1) == -1
+    sz = ctypes.c_size_t()
+    assert lib.mg_workspace_size(ctx, ctypes.byref(sz)) == 0
+    assert sz.value > 8 * 60 * (P + 1) ** 3 * 10
+    lib.mg_destroy(ctx)
+
+
+def test_width_overlap_reproduces_table1_layers(lib):
+    table = json.load(open(os.path.join(HERE, "golden", "table1_gll.json")))
+    for row in table["rows"]:
+        if not row["overlap"].startswith("delta_O"):
+            continue
+        frac = float(row["overlap"].split("=")[1])
+        st, ctx = _setup(lib, P=32, overlap_mode=1, overlap_frac=frac)
+        assert st == 0
+        got = [lib.mg_level_layers(ctx, l) for l in range(1, 6)]
+        assert got == row["n_o"], (frac, got)
+        lib.mg_destroy(ctx)
+
+
+def test_calls_before_binding_are_not_ready(lib):
+    st, ctx = _setup(lib)
+    assert st == 0
+    dummy = ctypes.c_void_p(256)
+    assert lib.mg_apply_sipg(ctx, 2, dummy, dummy) == 5
+    assert lib.mg_vcycle(ctx, dummy, dummy) == 5
+    assert b"not bound" in lib.mg_last_error(ctx)
+    # misaligned / too small workspace is rejected before any CUDA call
+    assert lib.mg_bind_workspace(ctx, ctypes.c_void_p(257), ctypes.c_size_t(1 << 40)) == 1
+    assert lib.mg_bind_workspace(ctx, ctypes.c_void_p(256), ctypes.c_size_t(16)) == 2
+    lib.mg_destroy(ctx)
