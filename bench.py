@@ -1,0 +1,348 @@
+#!/usr/bin/env python
+"""Benchmark: DOF/s solved to 1e-10 relative residual on one or more GB300s.
+
+Workload (one step = one full solve): periodic unit cube, 16^3 elements, P = 8
+(2,985,984 DOFs), nodal f ~ N(0, 1) from seed 2 made compatible (zero integral
+mean), weak rhs b = M f, standalone V(1,1) multigrid with N_O = 1 node-layer
+overlap, FP64, from u = 0 to ||b - A u|| <= 1e-10 ||b||.  Inputs are resident
+in HBM when timing starts; L2 is flushed (256 MiB write) between steps.
+
+Also reported: the same solves through the host-buffer API (e2e), the
+mixed-precision solver (FP32 V-cycle inside FP64 CG) on the same problem, the
+smoother kernel against its FP64 roofline, and the FP64 CPU oracle timed on
+the host cores on a bounded sample of the workload.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mg|reference]
+Multi-GPU (N > 1, launched with torch.distributed.run): every rank solves its
+own replica of the problem (weak scaling, no collective on the data path).
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "DOF/s solved to 1e-10 rel. residual, mixed vs FP64 on GB300; p50/p99 latency"
+WORKLOAD = {
+    "workload": "periodic unit cube, 16^3 elements, P=8 (2,985,984 DOFs), nodal f ~ N(0,1) seed 2 with zero mean, "
+                "standalone V(1,1) multigrid, N_O=1 node layer, FP64, u0 = 0, tol 1e-10",
+    "lengths": [1.0, 1.0, 1.0],
+    "elements": [16, 16, 16],
+    "P": 8,
+    "overlap_layers": 1,
+    "penalty": "2 x stability threshold",
+    "tol": 1e-10,
+    "solver": "MG V(1,1)",
+    "seed": 2,
+}
+# bounded sample of the workload for the CPU oracle (same P, overlap, tol; smaller mesh)
+ORACLE_SAMPLE = {"elements": [6, 6, 6], "P": 8}
+FLUSH_BYTES = 256 << 20
+FP64_FLOP_PER_CLK_PER_SM = 4      # 2 FP64 FMA per clock per SM (1.25 TFLOP/s nominal at 2070 MHz, 152 SMs)
+NUM_SMS = 152
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mg", choices=["mg", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip e2e / mixed / roofline legs")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            return json.load(fh), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.proc = None
+        self.lines = []
+        try:
+            import torch
+            uuid = str(torch.cuda.get_device_properties(device_index).uuid)
+            sel = ["-i", uuid if uuid.startswith("GPU-") else "GPU-" + uuid]
+        except Exception:
+            sel = []
+        self.cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits", "-lms", "200"] + sel
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(self.cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": max(power)}
+
+
+def oracle_sample_solve(seed=2):
+    """The FP64 CPU oracle on the bounded sample: returns (DOFs, solve seconds,
+    setup seconds, iterations)."""
+    from oracle.multigrid import Hierarchy, solve_mg
+    from oracle.sipg import Mesh, weak_rhs
+    from paper_1612_04796_gb300 import inputs
+    counts, P = ORACLE_SAMPLE["elements"], ORACLE_SAMPLE["P"]
+    t0 = time.perf_counter()
+    mesh = Mesh(WORKLOAD["lengths"], counts)
+    H = Hierarchy(mesh, P, n_o=WORKLOAD["overlap_layers"])
+    N = H.A.shape[0]
+    b = weak_rhs(mesh, P, inputs.gaussian(N, seed))
+    t1 = time.perf_counter()
+    _, its, _ = solve_mg(H, b, tol=WORKLOAD["tol"])
+    t2 = time.perf_counter()
+    return N, t2 - t1, t1 - t0, its
+
+
+def sample_text(N, its):
+    c = ORACLE_SAMPLE["elements"]
+    return ("FP64 oracle (numpy/scipy, assembled SIPG matrix, direct subdomain solves) solving the same problem "
+            "class on %dx%dx%d elements, P=%d (%d DOFs, %d V(1,1) cycles to 1e-10), solve time only"
+            % (c[0], c[1], c[2], ORACLE_SAMPLE["P"], N, its))
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle, on the host cores, each step one solve of
+    the bounded sample.  Rank 0 only."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    times = []
+    N = its = 0
+    for step in range(args.warmup + args.steps):
+        N, t, _, its = oracle_sample_solve()
+        if step >= args.warmup:
+            times.append(t)
+    total = sum(times)
+    value = N * len(times) / total
+    cores = os.cpu_count()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": dict(WORKLOAD, sample=ORACLE_SAMPLE),
+        "cpu_baseline": {"value": value, "unit": "DOF/s", "cores": cores, "kind": "oracle",
+                         "sample": sample_text(N, its)},
+        "e2e": {"value": value, "unit": "DOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_mg(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_1612_04796_gb300 as pkg
+    from paper_1612_04796_gb300 import inputs
+
+    rank, world, local = dist_env()
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local if world > 1 else torch.cuda.current_device())
+    torch.cuda.set_device(dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    pkg.load_library()
+    W = WORKLOAD
+    s = pkg.MGSolver(W["lengths"], W["elements"], W["P"], overlap=W["overlap_layers"], device=dev)
+    N = s.num_dofs()
+    f_nodal = torch.tensor(inputs.gaussian(N, W["seed"]), device=dev)
+    b = s.rhs(f_nodal)
+    u = torch.zeros(N, dtype=torch.float64, device=dev)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    for _ in range(args.warmup):
+        u.zero_()
+        s.solve(b, u, tol=W["tol"])
+    barrier()
+
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    s.profile(True)
+    launches0 = s.kernel_launches()
+    step_ms = []
+    iters = []
+    barrier()
+    for step in range(args.steps):
+        flush.fill_(step & 0xFF)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        u.zero_()
+        _, its, rel, _ = s.solve(b, u, tol=W["tol"])
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        iters.append(its)
+    barrier()
+    launches = s.kernel_launches() - launches0
+    s.profile(False)
+    clock_info = clocks.stop()
+    total_s = max_over_ranks(sum(step_ms) / 1e3)
+    value = world * N * args.steps / total_s
+
+    # roofline of the dominant kernel: the smoother's fast diagonalisation on the
+    # fine level, FP64-pipe bound; algorithmic flops per launch = Ne (12 m^4 + m^3)
+    lev = s.L
+    m = s.P + 1 + 2 * s.layers(lev)
+    Ne = int(np.prod(W["elements"]))
+    fdm_ms, fdm_n = s.profile_result("fdm", lev)
+    algo_flop = Ne * (12.0 * m ** 4 + m ** 3)
+    pk, pk_kind = peaks()
+    sm_max = float(pk.get("sm_max_mhz", 2070.0))
+    fp64_peak = NUM_SMS * FP64_FLOP_PER_CLK_PER_SM * sm_max * 1e6
+    achieved = algo_flop / (fdm_ms / fdm_n / 1e3) if fdm_n else None
+    roofline = {
+        "kernel": "k_fdm<double> (fine-level gather + fast diagonalisation)",
+        "bound": "alu", "achieved": achieved / 1e12 if achieved else None, "peak": fp64_peak / 1e12,
+        "unit": "TFLOP/s", "frac": (achieved / fp64_peak) if achieved else None, "traffic": None,
+        "algorithmic_flop_per_launch": algo_flop, "launches_timed": fdm_n,
+        "avg_launch_ms": fdm_ms / fdm_n if fdm_n else None,
+        "peak_basis": "FP64 pipe: %d SMs x %d flop/clk x %.0f MHz (derived; %s peaks file has no FP64 entry)"
+                      % (NUM_SMS, FP64_FLOP_PER_CLK_PER_SM, sm_max, pk_kind),
+    }
+    shares = {}
+    for kind in ("fdm", "scatter", "sipg", "restrict", "prolong", "coarse"):
+        ms, cnt = s.profile_result(kind)
+        shares[kind] = round(ms / max(sum(step_ms), 1e-9), 4)
+    roofline["time_share_of_step"] = shares
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": sum(step_ms) / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": dict(W, dofs=N, iterations=int(statistics.median(iters)),
+                       l2="flushed (256 MiB write) between steps", parallelism="replicas" if world > 1 else "1 GPU"),
+        "gpu_launches": launches, "clocks": clock_info, "roofline": roofline,
+    }
+
+    if not args.no_extras:
+        # e2e: the same solves through the host-buffer entry point (pinned memory)
+        f_host = b.cpu().pin_memory()
+        u_host = torch.zeros(N, dtype=torch.float64).pin_memory()
+        s.solve_host(f_host, u_host, tol=W["tol"])
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(max(3, args.steps // 3)):
+            u_host.zero_()
+            s.solve_host(f_host, u_host, tol=W["tol"])
+        k_e2e = max(3, args.steps // 3)
+        e2e_s = max_over_ranks(time.perf_counter() - t0)
+        line["e2e"] = {"value": world * N * k_e2e / e2e_s, "unit": "DOF/s", "h2d_bytes_per_step": 2 * N * 8,
+                       "d2h_bytes_per_step": N * 8, "steps": k_e2e}
+
+        # mixed precision: FP32 V(1,1) preconditioner inside FP64 inexact PCG
+        sm_ = pkg.MGSolver(W["lengths"], W["elements"], W["P"], overlap=W["overlap_layers"], precision="mixed",
+                           device=dev)
+        um = torch.zeros(N, dtype=torch.float64, device=dev)
+        for _ in range(args.warmup):
+            um.zero_()
+            sm_.solve(b, um, tol=W["tol"], use_cg=True)
+        barrier()
+        mix_ms = []
+        for step in range(args.steps):
+            flush.fill_(step & 0xFF)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            um.zero_()
+            _, its_m, rel_m, _ = sm_.solve(b, um, tol=W["tol"], use_cg=True)
+            e1.record(stream)
+            e1.synchronize()
+            mix_ms.append(e0.elapsed_time(e1))
+        barrier()
+        true_rel = float(torch.linalg.norm(s.residual(um, b)) / torch.linalg.norm(b))
+        err = float(torch.max(torch.abs(um - u)) / torch.max(torch.abs(u)))
+        mix_total = max_over_ranks(sum(mix_ms) / 1e3)
+        line["mixed"] = {"value": world * N * args.steps / mix_total, "unit": "DOF/s",
+                         "ms_per_step": sum(mix_ms) / args.steps, "iterations": its_m,
+                         "solver": "MG-CG: FP32 V(1,1) preconditioner, FP64 inexact PCG",
+                         "true_relres": true_rel, "max_rel_diff_vs_fp64_solution": err}
+
+    if rank == 0 and not args.no_cpu_baseline:
+        Ns, ts, _, its_s = oracle_sample_solve()
+        line["cpu_baseline"] = {"value": Ns / ts, "unit": "DOF/s", "cores": os.cpu_count(), "kind": "oracle",
+                                "sample": sample_text(Ns, its_s)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_mg(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -192,6 +192,20 @@ mg_status mg_vcycle_f32(mg_ctx* ctx, float* u, const float* f);
  */
 mg_status mg_get_table(mg_ctx* ctx, int level, int dir, int what, double* host_out, int capacity, int* count);
 
+/* Instrumentation (not part of the method).
+ * mg_kernel_launches: number of kernels this context has launched since
+ *   mg_setup (host-side count; mg_bind_workspace's setup kernels included).
+ * mg_profile: enable = 1 starts recording a CUDA event pair on the context's
+ *   stream around every kernel group (clearing earlier records); 0 stops.
+ * mg_profile_result: summed device time in ms and number of recorded groups
+ *   of one kind on one level (level -1: all levels).  kind: 0 smoother fast
+ *   diagonalisation (gather + contractions), 1 smoother scatter, 2 operator /
+ *   residual, 3 restriction, 4 prolongation, 5 coarse solve.  Synchronises
+ *   the stream. */
+long long mg_kernel_launches(const mg_ctx* ctx);
+mg_status mg_profile(mg_ctx* ctx, int enable);
+mg_status mg_profile_result(mg_ctx* ctx, int kind, int level, double* total_ms, long long* count);
+
 /* Message of the last failed call on ctx (never NULL). */
 const char* mg_last_error(const mg_ctx* ctx);
 

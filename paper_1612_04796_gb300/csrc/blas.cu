@@ -169,7 +169,9 @@ inline int grid_for(int64_t n) {
 template <typename T>
 cudaError_t reduce(const mg_ctx* c, const T* x, const T* y, int64_t n, int mode, int slot) {
   k_partial<T><<<kRedBlocks, kThreads, 0, c->stream>>>(x, y, n, mode, c->ws.red);
+  c->nlaunch += 1;
   k_final<<<1, kThreads, 0, c->stream>>>(c->ws.red, kRedBlocks, c->ws.scal, slot);
+  c->nlaunch += 1;
   return cudaGetLastError();
 }
 
@@ -185,6 +187,7 @@ cudaError_t launch_sum(const mg_ctx* c, const double* x, int64_t n, int slot) {
 
 cudaError_t launch_sub_mean(const mg_ctx* c, double* x, int64_t n, int sum_slot) {
   k_sub_mean<double><<<grid_for(n), kThreads, 0, c->stream>>>(x, n, c->ws.scal, sum_slot);
+  c->nlaunch += 1;
   return cudaGetLastError();
 }
 
@@ -193,33 +196,39 @@ cudaError_t launch_sub_mean_t(const mg_ctx* c, T* x, int64_t n) {
   cudaError_t e = reduce<T>(c, x, x, n, 1, kSlotSumT);
   if (e != cudaSuccess) return e;
   k_sub_mean<T><<<grid_for(n), kThreads, 0, c->stream>>>(x, n, c->ws.scal, kSlotSumT);
+  c->nlaunch += 1;
   return cudaGetLastError();
 }
 
 cudaError_t launch_axpy2(const mg_ctx* c, double* x, const double* p, double* r, const double* q, int64_t n,
                          int num_slot, int den_slot) {
   k_axpy2<<<grid_for(n), kThreads, 0, c->stream>>>(x, p, r, q, n, c->ws.scal, num_slot, den_slot);
+  c->nlaunch += 1;
   return cudaGetLastError();
 }
 
 cudaError_t launch_add(const mg_ctx* c, double* y, const double* x, int64_t n) {
   k_add<<<grid_for(n), kThreads, 0, c->stream>>>(y, x, n);
+  c->nlaunch += 1;
   return cudaGetLastError();
 }
 
 cudaError_t launch_xpby(const mg_ctx* c, double* p, const double* z, int64_t n, int num_slot, int den_slot,
                         int alpha_slot) {
   k_xpby<<<grid_for(n), kThreads, 0, c->stream>>>(p, z, n, c->ws.scal, num_slot, den_slot, alpha_slot);
+  c->nlaunch += 1;
   return cudaGetLastError();
 }
 
 cudaError_t launch_to_f32(const mg_ctx* c, const double* x, float* y, int64_t n, int norm_slot) {
   k_to_f32<<<grid_for(n), kThreads, 0, c->stream>>>(x, y, n, c->ws.scal, norm_slot);
+  c->nlaunch += 1;
   return cudaGetLastError();
 }
 
 cudaError_t launch_from_f32(const mg_ctx* c, const float* x, double* y, int64_t n, int norm_slot) {
   k_from_f32<<<grid_for(n), kThreads, 0, c->stream>>>(x, y, n, c->ws.scal, norm_slot);
+  c->nlaunch += 1;
   return cudaGetLastError();
 }
 
@@ -231,9 +240,13 @@ cudaError_t launch_rhs(const mg_ctx* c, const double* f, double* b) {
   a.n = lv.n;
   a.Ne = c->Ne;
   k_mass_partial<<<kRedBlocks, kThreads, 0, c->stream>>>(a, f, c->ws.red);
+  c->nlaunch += 1;
   k_final<<<1, kThreads, 0, c->stream>>>(c->ws.red, kRedBlocks, c->ws.scal, kSlotMassF);
+  c->nlaunch += 1;
   k_final<<<1, kThreads, 0, c->stream>>>(c->ws.red + kRedBlocks, kRedBlocks, c->ws.scal, kSlotMass);
+  c->nlaunch += 1;
   k_rhs<<<grid_for(lv.N), kThreads, 0, c->stream>>>(a, f, b, c->ws.scal);
+  c->nlaunch += 1;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if ((e = launch_sum(c, b, lv.N, kSlotSum)) != cudaSuccess) return e;
@@ -244,12 +257,14 @@ cudaError_t launch_coords(const mg_ctx* c, int l, double* x, double* y, double* 
   const LevelInfo& lv = c->lev[l];
   k_coords<<<grid_for(lv.N), kThreads, 0, c->stream>>>(c->ws.tab64, lv.t[0].nodes, lv.n, c->Ne, c->ne[0], c->ne[1],
                                                         lv.h[0], lv.h[1], lv.h[2], x, y, z);
+  c->nlaunch += 1;
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_zero(const mg_ctx* c, T* x, int64_t n) {
   k_zero<T><<<grid_for(n), kThreads, 0, c->stream>>>(x, n);
+  c->nlaunch += 1;
   return cudaGetLastError();
 }
 

@@ -96,6 +96,7 @@ cudaError_t launch_coarse_solve(const mg_ctx* c, const double* f0, double* u0) {
   k_coarse_axis<<<(int)blocks, 256, 0, s>>>(A, B, Q[2], d, 2, 1, 0, 0, sc, -1, 0, 0, 0, 0, 0, 0, 0);
   k_coarse_axis<<<(int)blocks, 256, 0, s>>>(B, A, Q[1], d, 1, 1, 0, 0, sc, -1, 0, 0, 0, 0, 0, 0, 0);
   k_coarse_axis<<<(int)blocks, 256, 0, s>>>(A, u0, Q[0], d, 0, 1, 0, 1, sc, -1, 0, 0, 0, 0, 0, 0, 0);
+  c->nlaunch += 6;
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = launch_sum(c, u0, N0, sum_slot)) != cudaSuccess) return e;
   return launch_sub_mean(c, u0, N0, sum_slot);

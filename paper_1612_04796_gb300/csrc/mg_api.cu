@@ -167,6 +167,27 @@ double read_scalar(mg_ctx* c, int slot, cudaError_t* err) {
   return v;
 }
 
+// CUDA events around one kernel group when profiling is on (mg_profile).
+struct ProfScope {
+  const mg_ctx* c;
+  long idx = -1;
+  ProfScope(const mg_ctx* c_, int kind, int level) : c(c_) {
+    if (!c->prof_on) return;
+    if (c->prof_used == c->prof.size()) {
+      mg_ctx::ProfRec r{kind, level, nullptr, nullptr};
+      if (cudaEventCreate(&r.a) != cudaSuccess || cudaEventCreate(&r.b) != cudaSuccess) return;
+      c->prof.push_back(r);
+    }
+    idx = (long)c->prof_used++;
+    c->prof[idx].kind = kind;
+    c->prof[idx].level = level;
+    cudaEventRecord(c->prof[idx].a, c->stream);
+  }
+  ~ProfScope() {
+    if (idx >= 0) cudaEventRecord(c->prof[idx].b, c->stream);
+  }
+};
+
 // ---- level vector views ----
 template <typename T>
 T* lvec(void* p) {
@@ -196,14 +217,21 @@ int steps_on_level(const mg_ctx* c, int ns, int l) {
 template <typename T>
 cudaError_t smooth_step(const mg_ctx* c, int l, T* u, const T* f, bool u_is_zero, bool r_ready) {
   cudaError_t e;
-  if (u_is_zero) {
-    if ((e = launch_fdm<T>(c, l, f)) != cudaSuccess) return e;
-    return launch_scatter<T>(c, l, u, 0);
+  const T* rin = f;
+  if (!u_is_zero) {
+    T* r = lvec<T>(c->lev[l].r);
+    if (!r_ready) {
+      ProfScope ps(c, kProfSipg, l);
+      if ((e = launch_sipg<T>(c, l, u, f, r, 1)) != cudaSuccess) return e;
+    }
+    rin = r;
   }
-  T* r = lvec<T>(c->lev[l].r);
-  if (!r_ready && (e = launch_sipg<T>(c, l, u, f, r, 1)) != cudaSuccess) return e;
-  if ((e = launch_fdm<T>(c, l, r)) != cudaSuccess) return e;
-  return launch_scatter<T>(c, l, u, 1);
+  {
+    ProfScope ps(c, kProfFdm, l);
+    if ((e = launch_fdm<T>(c, l, rin)) != cudaSuccess) return e;
+  }
+  ProfScope ps(c, kProfScatter, l);
+  return launch_scatter<T>(c, l, u, u_is_zero ? 0 : 1);
 }
 
 // Algorithm 1 (MultigridCycle).  uL, fL: fine-level vectors.
@@ -229,12 +257,22 @@ cudaError_t vcycle_t(const mg_ctx* c, T* uL, const T* fL, bool u_zero, bool r_re
     if (ns == 0 && zero && (e = launch_zero<T>(c, u[l], c->lev[l].N)) != cudaSuccess) return e;
     // f_{l-1} = I_l^T (f_l - A_l u_l)
     T* r = lvec<T>(c->lev[l].r);
-    if ((e = launch_sipg<T>(c, l, u[l], f[l], r, 1)) != cudaSuccess) return e;
+    {
+      ProfScope ps(c, kProfSipg, l);
+      if ((e = launch_sipg<T>(c, l, u[l], f[l], r, 1)) != cudaSuccess) return e;
+    }
+    ProfScope ps(c, kProfRestrict, l);
     if ((e = launch_restrict<T>(c, l, r, lvec<T>(c->lev[l - 1].f))) != cudaSuccess) return e;
   }
-  if ((e = coarse_solve_t<T>(c, f[0], u[0])) != cudaSuccess) return e;
+  {
+    ProfScope ps(c, kProfCoarse, 0);
+    if ((e = coarse_solve_t<T>(c, f[0], u[0])) != cudaSuccess) return e;
+  }
   for (int l = 1; l <= L; ++l) {
-    if ((e = launch_prolong<T>(c, l, u[l - 1], u[l])) != cudaSuccess) return e;
+    {
+      ProfScope ps(c, kProfProlong, l);
+      if ((e = launch_prolong<T>(c, l, u[l - 1], u[l])) != cudaSuccess) return e;
+    }
     const int ns = steps_on_level(c, c->opts.ns_post, l);
     for (int st = 0; st < ns; ++st)
       if ((e = smooth_step<T>(c, l, u[l], f[l], false, false)) != cudaSuccess) return e;
@@ -286,7 +324,10 @@ mg_status solve_impl(mg_ctx* c, double* u, const double* f, double tol, int maxi
       } else {
         CK((vcycle_t<double>(c, u, f, false, true)));
       }
-      CK(launch_sipg<double>(c, L, u, f, r, 1));
+      {
+        ProfScope ps(c, kProfSipg, L);
+        CK(launch_sipg<double>(c, L, u, f, r, 1));
+      }
       CK(launch_dot(c, r, r, N, kSlotRR));
       double v = read_scalar(c, kSlotRR, &err);
       CK(err);
@@ -318,7 +359,10 @@ mg_status solve_impl(mg_ctx* c, double* u, const double* f, double tol, int maxi
     }
     while (!converged && it < maxit) {
       ++it;
-      CK(launch_sipg<double>(c, L, p, nullptr, q, 0));
+      {
+        ProfScope ps(c, kProfSipg, L);
+        CK(launch_sipg<double>(c, L, p, nullptr, q, 0));
+      }
       CK(launch_dot(c, p, q, N, kSlotPQ));
       CK(launch_axpy2(c, x, p, r, q, N, kSlotRZ, kSlotPQ));  // alpha = rz / pq
       CK(launch_sum(c, r, N, kSlotSum));
@@ -686,6 +730,40 @@ const char* mg_last_error(const mg_ctx* c) {
   return c->err.c_str();
 }
 
-void mg_destroy(mg_ctx* c) { delete c; }
+long long mg_kernel_launches(const mg_ctx* c) { return c ? c->nlaunch : -1; }
+
+mg_status mg_profile(mg_ctx* c, int enable) {
+  if (!c) return MG_EINVAL;
+  c->prof_on = enable != 0;
+  if (enable) c->prof_used = 0;
+  return MG_OK;
+}
+
+mg_status mg_profile_result(mg_ctx* c, int kind, int level, double* total_ms, long long* count) {
+  if (!c || !total_ms || !count || kind < 0 || kind >= kProfKinds) return MG_EINVAL;
+  CK(cudaStreamSynchronize(c->stream));
+  double tot = 0.0;
+  long long n = 0;
+  for (size_t i = 0; i < c->prof_used; ++i) {
+    const mg_ctx::ProfRec& r = c->prof[i];
+    if (r.kind != kind || (level >= 0 && r.level != level)) continue;
+    float ms = 0.0f;
+    CK(cudaEventElapsedTime(&ms, r.a, r.b));
+    tot += ms;
+    ++n;
+  }
+  *total_ms = tot;
+  *count = n;
+  return MG_OK;
+}
+
+void mg_destroy(mg_ctx* c) {
+  if (!c) return;
+  for (auto& r : c->prof) {
+    if (r.a) cudaEventDestroy(r.a);
+    if (r.b) cudaEventDestroy(r.b);
+  }
+  delete c;
+}
 
 }  // extern "C"

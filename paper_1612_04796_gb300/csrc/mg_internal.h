@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/mgdg.h"
 
@@ -95,9 +96,23 @@ struct mg_ctx {
   size_t ws_bytes;
   bool ready;
   std::string err;
+  // instrumentation: kernel launch count and optional per-group CUDA events
+  // (mutable: the launchers take a const context)
+  struct ProfRec {
+    int kind, level;
+    cudaEvent_t a, b;
+  };
+  mutable long long nlaunch = 0;
+  mutable bool prof_on = false;
+  mutable std::vector<ProfRec> prof;
+  mutable size_t prof_used = 0;
 };
 
 namespace mgdg {
+
+// Kernel groups timed by the profiler (mg_profile_result kinds).
+enum ProfKind : int { kProfFdm = 0, kProfScatter, kProfSipg, kProfRestrict, kProfProlong, kProfCoarse, kProfVector,
+                      kProfKinds };
 
 // ---- setup (setup.cu) ----
 cudaError_t launch_setup(mg_ctx* c);

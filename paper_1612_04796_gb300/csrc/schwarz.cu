@@ -181,6 +181,7 @@ cudaError_t launch_fdm(const mg_ctx* c, int l, const T* r) {
   int threads = lv.m * lv.m >= 256 ? 256 : 128;
   int64_t blocks = c->Ne < 152 * 8 ? c->Ne : 152 * 8;
   k_fdm<T><<<(int)blocks, threads, smem, c->stream>>>(a);
+  c->nlaunch += 1;
   return cudaGetLastError();
 }
 
@@ -192,6 +193,7 @@ cudaError_t launch_scatter(const mg_ctx* c, int l, T* u, int accumulate) {
   if (blocks > 152 * 16) blocks = 152 * 16;
   k_scatter<T><<<(int)blocks, 256, 0, c->stream>>>(static_cast<const T*>(c->ws.corr), u, c->Ne, c->ne[0], c->ne[1],
                                                     c->ne[2], lv.n, lv.m, lv.no, accumulate);
+  c->nlaunch += 1;
   return cudaGetLastError();
 }
 

@@ -451,6 +451,7 @@ cudaError_t launch_setup(mg_ctx* c) {
   int64_t per_block = c->ws.jac_count / nb;
   cudaStream_t s = c->stream;
   k_setup_level<<<nb, kSetupThreads, 0, s>>>(batch, c->ws.tab64, c->ws.jac, per_block, c->ws.status);
+  c->nlaunch += 1;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   for (int l = 1; l <= c->L; ++l) {
@@ -459,10 +460,12 @@ cudaError_t launch_setup(mg_ctx* c) {
     int blocks = (int)((total + 255) / 256);
     if (blocks > 1024) blocks = 1024;
     k_setup_dinv<<<blocks, 256, 0, s>>>(c->ws.tab64, lv.dinv, lv.t[0].lam, lv.t[1].lam, lv.t[2].lam, lv.m);
+    c->nlaunch += 1;
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
   k_cast_tables<<<256, 256, 0, s>>>(c->ws.tab64, c->ws.tab32, c->ws.tab_count);
+  c->nlaunch += 1;
   return cudaGetLastError();
 }
 

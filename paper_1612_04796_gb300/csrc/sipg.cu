@@ -172,6 +172,7 @@ cudaError_t launch_sipg(const mg_ctx* c, int l, const T* u, const T* f, T* out, 
     if (e != cudaSuccess) return e;
   }
   k_sipg<T><<<(int)blocks, 256, smem, c->stream>>>(a);
+  c->nlaunch += 1;
   return cudaGetLastError();
 }
 

@@ -50,6 +50,7 @@ cudaError_t contract(const mg_ctx* c, const T* in, T* out, const T* J, int d0, i
   if (blocks > 152 * 16) blocks = 152 * 16;
   k_contract_axis<T><<<(int)blocks, 256, 0, c->stream>>>(in, out, J, c->Ne, d0, d1, d2, axis, nout, ldj, transpose,
                                                          accumulate);
+  c->nlaunch += 1;
   return cudaGetLastError();
 }
 

@@ -221,6 +221,23 @@ class MGSolver:
         self._check(st)
         return u_host, its.value, rel.value, hist[:its.value + 1]
 
+    # -- instrumentation ------------------------------------------------------
+    def kernel_launches(self):
+        return int(self.lib.mg_kernel_launches(self.ctx))
+
+    def profile(self, enable=True):
+        self._check(self.lib.mg_profile(self.ctx, int(bool(enable))))
+
+    PROFILE_KINDS = {"fdm": 0, "scatter": 1, "sipg": 2, "restrict": 3, "prolong": 4, "coarse": 5}
+
+    def profile_result(self, kind, level=-1):
+        """(total ms, number of kernel groups) recorded for one kind / level."""
+        ms = ctypes.c_double()
+        cnt = ctypes.c_longlong()
+        self._check(self.lib.mg_profile_result(self.ctx, self.PROFILE_KINDS[kind], int(level), ctypes.byref(ms),
+                                               ctypes.byref(cnt)))
+        return ms.value, cnt.value
+
     def get_table(self, level, direction, what):
         """Copy a 1D setup table to a numpy array (see mg_get_table)."""
         cap = 1 << 16
