@@ -192,6 +192,37 @@ mg_status mg_vcycle_f32(mg_ctx* ctx, float* u, const float* f);
  */
 mg_status mg_get_table(mg_ctx* ctx, int level, int dir, int what, double* host_out, int capacity, int* count);
 
+/*
+ * mg_coarse_solve_noalloc -- allocation-free variant of mg_coarse_solve.  The
+ * paper has no counterpart: this entry point exists for callers that may not
+ * allocate device memory (for example a plugin that a host framework hands
+ * only its input and output buffers because the framework owns all device
+ * memory, or a latency-critical path that cannot accept an allocation's
+ * implicit device synchronisation) and therefore cannot provide the
+ * workspace that mg_bind_workspace needs.
+ * It computes u0 = A_0^+ f0 on the P_0 = 1 level of the mesh given by lx, ly,
+ * lz, nx, ny, nz and penalty (same meaning as in mg_setup), with no context
+ * and no workspace; it calls no cudaMalloc / cudaFree or any allocating
+ * routine.  Its scratch is one file-scope device array of 4.5 MiB, which every
+ * GPU that loads the library holds until the process exits.
+ *   f0, u0   device pointers, N0 = 8 nx ny nz doubles each, element-blocked
+ *            level-0 layout (2 nodes per direction); u0 receives the zero-mean
+ *            solution; they may not alias.
+ *   stream   cudaStream_t (NULL = legacy default stream); the call
+ *            synchronises it once (it reads the coarse eigenvalues back).
+ * Limits: 3 <= nx, ny, nz <= 32 (N0 <= 262,144); larger sizes (and other
+ * invalid arguments) return MG_EINVAL before any CUDA call.  MG_ECUDA on a
+ * failed CUDA call, MG_ENOCONV if an eigensolver hit its sweep limit.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current): make that first call
+ * before any stream capture begins.  All calls share the one array, which
+ * keeps the last call's contents: calls that overlap on the GPU (from other
+ * streams or other host threads) race on it and must not be issued
+ * concurrently.
+ */
+mg_status mg_coarse_solve_noalloc(double lx, double ly, double lz, int nx, int ny, int nz, double penalty,
+                                  const double* f0, double* u0, void* stream);
+
 /* Instrumentation (not part of the method).
  * mg_kernel_launches: number of kernels this context has launched since
  *   mg_setup (host-side count; mg_bind_workspace's setup kernels included).

@@ -102,6 +102,28 @@ cudaError_t launch_coarse_solve(const mg_ctx* c, const double* f0, double* u0) {
   return launch_sub_mean(c, u0, N0, sum_slot);
 }
 
+cudaError_t launch_coarse_fdm_raw(const double* const Q[3], const double* const lam[3], const int Ng[3],
+                                  const int ne[3], const int null_mode[3], const double* f0, double* A, double* B,
+                                  double* u0, const double* scal, int mean_slot, cudaStream_t s) {
+  CoarseDims d;
+  for (int k = 0; k < 3; ++k) {
+    d.Ng[k] = Ng[k];
+    d.ne[k] = ne[k];
+  }
+  const int64_t N0 = (int64_t)Ng[0] * Ng[1] * Ng[2];
+  int64_t blocks = (N0 + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  const int* nz = null_mode;
+  k_coarse_axis<<<(int)blocks, 256, 0, s>>>(f0, A, Q[0], d, 0, 0, 1, 0, scal, mean_slot, 0, 0, 0, 0, 0, 0, 0);
+  k_coarse_axis<<<(int)blocks, 256, 0, s>>>(A, B, Q[1], d, 1, 0, 0, 0, scal, -1, 0, 0, 0, 0, 0, 0, 0);
+  k_coarse_axis<<<(int)blocks, 256, 0, s>>>(B, A, Q[2], d, 2, 0, 0, 0, scal, -1, 1, lam[0], lam[1], lam[2], nz[0],
+                                            nz[1], nz[2]);
+  k_coarse_axis<<<(int)blocks, 256, 0, s>>>(A, B, Q[2], d, 2, 1, 0, 0, scal, -1, 0, 0, 0, 0, 0, 0, 0);
+  k_coarse_axis<<<(int)blocks, 256, 0, s>>>(B, A, Q[1], d, 1, 1, 0, 0, scal, -1, 0, 0, 0, 0, 0, 0, 0);
+  k_coarse_axis<<<(int)blocks, 256, 0, s>>>(A, u0, Q[0], d, 0, 1, 0, 1, scal, -1, 0, 0, 0, 0, 0, 0, 0);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_coarse_solve_f32(const mg_ctx* c, const float* f0, float* u0) {
   // The coarsest solve of the FP32 hierarchy stays in FP64: widen, solve, narrow.
   const int64_t N0 = c->lev[0].N;

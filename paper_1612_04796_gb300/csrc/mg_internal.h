@@ -117,6 +117,12 @@ enum ProfKind : int { kProfFdm = 0, kProfScatter, kProfSipg, kProfRestrict, kPro
 // ---- setup (setup.cu) ----
 cudaError_t launch_setup(mg_ctx* c);
 
+// Level-0 tables only (three blocks), explicit pointers; used by the
+// allocation-free coarse solve (noalloc.cu).
+cudaError_t launch_setup_coarse_tables(const double len[3], const int ne[3], double penalty, double* tab,
+                                       const DirTables t[3], double* scratch, int64_t per_block, int* status,
+                                       cudaStream_t s);
+
 // ---- operator (sipg.cu) ----
 // out = mode==0 ? A u : f - A u, on level l, T = double | float.
 template <typename T>
@@ -139,6 +145,11 @@ cudaError_t launch_prolong(const mg_ctx* c, int l, const T* u_coarse, T* u_fine)
 // ---- coarse solve (coarse.cu) ----
 cudaError_t launch_coarse_solve(const mg_ctx* c, const double* f0, double* u0);
 cudaError_t launch_coarse_solve_f32(const mg_ctx* c, const float* f0, float* u0);
+// The six fast-diagonalisation passes of the coarse solve with explicit
+// pointers; f0's mean is read from scal[mean_slot] (sum of f0).
+cudaError_t launch_coarse_fdm_raw(const double* const Q[3], const double* const lam[3], const int Ng[3],
+                                  const int ne[3], const int null_mode[3], const double* f0, double* A, double* B,
+                                  double* u0, const double* scal, int mean_slot, cudaStream_t s);
 
 // ---- vectors (blas.cu) ----
 // dot products: result into device scalar slot `slot` of ws.scal

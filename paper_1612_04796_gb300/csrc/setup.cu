@@ -425,6 +425,31 @@ __global__ void k_cast_tables(const double* src, float* dst, int64_t n) {
 
 }  // namespace
 
+cudaError_t launch_setup_coarse_tables(const double len[3], const int ne[3], double penalty, double* tab,
+                                       const DirTables t[3], double* scratch, int64_t per_block, int* status,
+                                       cudaStream_t s) {
+  SetupBatch batch;
+  for (int d = 0; d < 3; ++d) {
+    SetupParams& q = batch.p[d];
+    q.P = 1;
+    q.n = 2;
+    q.m = 0;
+    q.no = 0;
+    q.profile = MG_WEIGHT_QUINTIC;
+    q.level = 0;
+    q.Pc = 0;
+    q.delta = 0.0;
+    q.h = len[d] / ne[d];
+    q.g = 2.0 / q.h;
+    q.mu = penalty * 2.0 / (2.0 * q.h);
+    q.t = t[d];
+    q.J = -1;
+    q.Ng = 2 * ne[d];
+  }
+  k_setup_level<<<3, kSetupThreads, 0, s>>>(batch, tab, scratch, per_block, status);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_setup(mg_ctx* c) {
   SetupBatch batch;
   int nb = 0;
