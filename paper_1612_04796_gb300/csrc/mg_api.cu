@@ -478,6 +478,11 @@ mg_status mg_setup(double lx, double ly, double lz, int nx, int ny, int nz, int 
       t.lee = tab((int64_t)lv.n * lv.n);
       t.d0 = tab(lv.n);
       t.dp = tab(lv.n);
+      t.ce = tab((int64_t)((lv.n + 1) / 2) * ((lv.n + 1) / 2));
+      t.co = tab((int64_t)(lv.n / 2) * (lv.n / 2) + 1);
+      t.fe = tab((lv.n + 1) / 2);
+      t.fo = tab(lv.n / 2 + 1);
+      t.fsc = tab(2);
       if (l >= 1) {
         t.S = tab((int64_t)lv.m * lv.m);
         t.SW = tab((int64_t)lv.m * lv.m);
@@ -491,6 +496,7 @@ mg_status mg_setup(double lx, double ly, double lz, int nx, int ny, int nz, int 
       }
     }
     lv.dinv = (l >= 1) ? tab((int64_t)lv.m * lv.m * lv.m) : -1;
+    lv.mass3 = tab((int64_t)lv.n * lv.n * lv.n);
     lv.J = (l >= 1) ? tab((int64_t)lv.n * (c->lev[l - 1].n)) : -1;
     lv.u = lv.f = lv.r = nullptr;
   }

@@ -41,6 +41,9 @@ enum DevStatus : int { kDevOk = 0, kDevNoConv = 1 };
 // table arrays tab64 / tab32 (same offsets in both).
 struct DirTables {
   int64_t nodes, weights, mass, lee, d0, dp;  // n, n, n, n*n, n, n
+  // even/odd form of M^{-1} L_ee (ne = (n+1)/2, no = n/2): ce ne*ne, co no*no,
+  // face vectors fe (ne), fo (no) and the scalars fsc = {mu / m_0, g / (2 m_0)}
+  int64_t ce, co, fe, fo, fsc;
   int64_t S, SW, lam, w;                      // m*m, m*m, m, m  (level >= 1)
   int64_t Q, qlam;                            // Ng*Ng, Ng       (level 0)
 };
@@ -52,6 +55,7 @@ struct LevelInfo {
   double h[3], g[3], mu[3];
   DirTables t[3];
   int64_t dinv;          // m^3: 1 / (lam_x[a] + lam_y[b] + lam_z[c])
+  int64_t mass3;         // n^3: mass_x[i] mass_y[j] mass_z[k]
   int64_t J;             // n * n_c interpolation from level l-1 (level >= 1)
   // device vectors (bytes sized for FP64; FP32 code uses the first half)
   void* u;

@@ -110,6 +110,7 @@ extern "C" mg_status mg_coarse_solve_noalloc(double lx, double ly, double lz, in
     t[d].Q = o + 6 * kNaSmall;
     t[d].qlam = o + 6 * kNaSmall + (int64_t)kNaMaxNg * kNaMaxNg;
     t[d].S = t[d].SW = t[d].lam = t[d].w = -1;
+    t[d].ce = t[d].co = t[d].fe = t[d].fo = t[d].fsc = -1;
   }
   double* tab = base + kNaTab;
   double* scal = base + kNaScal;

@@ -36,29 +36,48 @@ __device__ __forceinline__ void sub_node(int a, int n, int no, int* de, int* ii)
 
 __device__ __forceinline__ int wrap(int x, int n) { return x < 0 ? x + n : (x >= n ? x - n : x); }
 
-// In-place 1D contraction of all m^2 lines of the tile along `axis`:
-// forward  (backward == 0): v[p] = sum_a S[a][p] x[a]      (S^T)
-// backward (backward == 1): v[a] = sum_p SW[a][p] x[p]     (diag(w) S)
+// Even/odd 1D transforms of one subdomain line (m = 2h+1, odd).  The
+// eigenvectors of the reflection-symmetric line problem are even (columns
+// p < h+1 of S) or odd (columns h+1 .. 2h), so with e_a = x_a + x_{m-1-a},
+// o_a = x_a - x_{m-1-a} (a < h) and e_h = x_h:
+//   forward  v_p     = sum_{a<=h} S[a][p] e_a          (p <= h)
+//            v_{h+1+q} = sum_{a<h} S[a][h+1+q] o_a     (q < h)
+//   backward x_a, x_{m-1-a} = E_a +- O_a, E_a = sum_{p<=h} SW[a][p] v_p,
+//            O_a = sum_{q<h} SW[a][h+1+q] v_{h+1+q},  x_h = E_h.
+// (h+1)^2 + h^2 multiply-adds and 2h additions instead of m^2.
 template <typename T>
-__device__ void contract_lines(T* tile, const T* mat, int m, int axis, int backward) {
-  const int m2 = m * m;
-  const int stride = axis == 0 ? 1 : (axis == 1 ? m : m2);
-  T line[kMaxM];
-  for (int ln = threadIdx.x; ln < m2; ln += blockDim.x) {
-    const int u = ln % m, v = ln / m;
-    int base;
-    if (axis == 0) base = m * (u + m * v);
-    else if (axis == 1) base = u + m2 * v;
-    else base = u + m * v;
-    for (int a = 0; a < m; ++a) line[a] = tile[base + a * stride];
-    for (int p = 0; p < m; ++p) {
-      T acc = 0;
-      if (!backward) {
-        for (int a = 0; a < m; ++a) acc += mat[a * m + p] * line[a];
-      } else {
-        for (int q = 0; q < m; ++q) acc += mat[p * m + q] * line[q];
-      }
-      tile[base + p * stride] = acc;
+__device__ __forceinline__ void fwd_eo(T* x, const T* __restrict__ S, int m, T* __restrict__ out, int ost) {
+  const int h = m >> 1, ne = h + 1;
+  for (int a = 0; a < h; ++a) {
+    const T xa = x[a], xb = x[m - 1 - a];
+    x[a] = xa + xb;          // e_a
+    x[m - 1 - a] = xa - xb;  // o_a stored at m-1-a
+  }
+  for (int p = 0; p < ne; ++p) {
+    T acc = 0;
+    for (int a = 0; a <= h; ++a) acc += S[a * m + p] * x[a];
+    out[p * ost] = acc;
+  }
+  for (int q = 0; q < h; ++q) {
+    T acc = 0;
+    for (int a = 0; a < h; ++a) acc += S[a * m + ne + q] * x[m - 1 - a];
+    out[(ne + q) * ost] = acc;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void bwd_eo(const T* v, const T* __restrict__ SW, int m, T* __restrict__ out, int ost) {
+  const int h = m >> 1, ne = h + 1;
+  for (int a = 0; a <= h; ++a) {
+    T E = 0;
+    for (int p = 0; p < ne; ++p) E += SW[a * m + p] * v[p];
+    if (a < h) {
+      T O = 0;
+      for (int q = 0; q < h; ++q) O += SW[a * m + ne + q] * v[ne + q];
+      out[a * ost] = E + O;
+      out[(m - 1 - a) * ost] = E - O;
+    } else {
+      out[a * ost] = E;
     }
   }
 }
@@ -77,33 +96,60 @@ __global__ void __launch_bounds__(256) k_fdm(FdmArgs<T> a) {
     }
   }
   __syncthreads();
+  const T* __restrict__ dinv = a.tab + a.dinv;
+  T x[kMaxM], v[kMaxM];
   for (int64_t s = blockIdx.x; s < a.Ne; s += gridDim.x) {
     const int sx = (int)(s % a.nx), sy = (int)((s / a.nx) % a.ny), sz = (int)(s / ((int64_t)a.nx * a.ny));
     T* tile = a.corr + s * (int64_t)m3;
-    // gather r_s = R_s r
-    for (int idx = threadIdx.x; idx < m3; idx += blockDim.x) {
-      const int ia = idx % m, ib = (idx / m) % m, ic = idx / m2;
-      int dx, ix, dy, iy, dz, iz;
-      sub_node(ia, n, no, &dx, &ix);
-      sub_node(ib, n, no, &dy, &iy);
-      sub_node(ic, n, no, &dz, &iz);
-      const int64_t e = wrap(sx + dx, a.nx) + a.nx * (wrap(sy + dy, a.ny) + (int64_t)a.ny * wrap(sz + dz, a.nz));
-      tile[idx] = a.r[e * n3 + ix + n * (iy + n * iz)];
+    const int64_t exl = wrap(sx - 1, a.nx), exr = wrap(sx + 1, a.nx);
+    // pass 1: gather the x-lines of r_s = R_s r and transform them (forward, x)
+    for (int ln = threadIdx.x; ln < m2; ln += blockDim.x) {
+      const int b = ln % m, c = ln / m;
+      int dy, iy, dz, iz;
+      sub_node(b, n, no, &dy, &iy);
+      sub_node(c, n, no, &dz, &iz);
+      const int64_t row = a.nx * (wrap(sy + dy, a.ny) + (int64_t)a.ny * wrap(sz + dz, a.nz));
+      const int loc = n * (iy + n * iz);
+      const T* rl = a.r + (exl + row) * n3 + loc;
+      const T* rc = a.r + (sx + row) * n3 + loc;
+      const T* rr = a.r + (exr + row) * n3 + loc;
+      for (int t = 0; t < no; ++t) x[t] = rl[n - no + t];
+      for (int t = 0; t < n; ++t) x[no + t] = rc[t];
+      for (int t = 0; t < no; ++t) x[no + n + t] = rr[t];
+      fwd_eo(x, sS, m, tile + m * ln, 1);
     }
     __syncthreads();
-    contract_lines(tile, sS, m, 0, 0);
+    // pass 2: forward, y
+    for (int ln = threadIdx.x; ln < m2; ln += blockDim.x) {
+      const int ia = ln % m, c = ln / m;
+      T* line = tile + ia + m2 * c;
+      for (int t = 0; t < m; ++t) x[t] = line[t * m];
+      fwd_eo(x, sS + m2, m, line, m);
+    }
     __syncthreads();
-    contract_lines(tile, sS + m2, m, 1, 0);
+    // pass 3: forward z, divide by lam_x + lam_y + lam_z, backward z
+    for (int ln = threadIdx.x; ln < m2; ln += blockDim.x) {
+      T* line = tile + ln;
+      for (int t = 0; t < m; ++t) x[t] = line[t * m2];
+      fwd_eo(x, sS + 2 * m2, m, v, 1);
+      for (int t = 0; t < m; ++t) v[t] *= dinv[ln + t * m2];
+      bwd_eo(v, sSW + 2 * m2, m, line, m2);
+    }
     __syncthreads();
-    contract_lines(tile, sS + 2 * m2, m, 2, 0);
+    // pass 4: backward, y
+    for (int ln = threadIdx.x; ln < m2; ln += blockDim.x) {
+      const int ia = ln % m, c = ln / m;
+      T* line = tile + ia + m2 * c;
+      for (int t = 0; t < m; ++t) v[t] = line[t * m];
+      bwd_eo(v, sSW + m2, m, line, m);
+    }
     __syncthreads();
-    for (int idx = threadIdx.x; idx < m3; idx += blockDim.x) tile[idx] *= a.tab[a.dinv + idx];
-    __syncthreads();
-    contract_lines(tile, sSW + 2 * m2, m, 2, 1);
-    __syncthreads();
-    contract_lines(tile, sSW + m2, m, 1, 1);
-    __syncthreads();
-    contract_lines(tile, sSW, m, 0, 1);
+    // pass 5: backward, x (weights folded into SW)
+    for (int ln = threadIdx.x; ln < m2; ln += blockDim.x) {
+      T* line = tile + m * ln;
+      for (int t = 0; t < m; ++t) v[t] = line[t];
+      bwd_eo(v, sSW, m, line, 1);
+    }
     __syncthreads();
   }
 }

@@ -326,6 +326,33 @@ __global__ void __launch_bounds__(kSetupThreads) k_setup_level(SetupBatch batch,
     tab[q.t.dp + i] = sm.D[q.P * n + i];
   }
   for (int i = t; i < n * n; i += nt) tab[q.t.lee + i] = sm.Lee[i];
+  // even/odd form of C = M^{-1} L_ee (centro-symmetric): for output i < ne
+  //   (C u)_i = sum_{t<ne} ce[i][t] e_t + sum_{t<no} co[i][t] o_t,  (C u)_{n-1-i} = ... - ...
+  // with e_t = u_t + u_{n-1-t}, o_t = u_t - u_{n-1-t} (t < no) and e_h = u_h for odd n.
+  if (q.t.ce >= 0) {
+    const int ne = (n + 1) / 2, no = n / 2;
+    for (int idx = t; idx < ne * ne; idx += nt) {
+      int i = idx / ne, tt = idx % ne;
+      double mi = 0.5 * q.h * sm.w[i];
+      double v = (tt < no) ? 0.5 * (sm.Lee[i * n + tt] + sm.Lee[i * n + n - 1 - tt]) : sm.Lee[i * n + tt];
+      tab[q.t.ce + idx] = v / mi;
+    }
+    for (int idx = t; idx < no * no; idx += nt) {
+      int i = idx / no, tt = idx % no;
+      double mi = 0.5 * q.h * sm.w[i];
+      tab[q.t.co + idx] = 0.5 * (sm.Lee[i * n + tt] - sm.Lee[i * n + n - 1 - tt]) / mi;
+    }
+    // face rank-1 terms -g/2 (D0_i a + D0_{n-1-i} c) in even/odd form (s = a + c, t = a - c)
+    for (int i = t; i < ne; i += nt)
+      tab[q.t.fe + i] = -0.25 * q.g * (sm.D[i] + sm.D[n - 1 - i]) / (0.5 * q.h * sm.w[i]);
+    for (int i = t; i < no; i += nt)
+      tab[q.t.fo + i] = -0.25 * q.g * (sm.D[i] - sm.D[n - 1 - i]) / (0.5 * q.h * sm.w[i]);
+    if (t == 0) {
+      double m0 = 0.5 * q.h * sm.w[0];
+      tab[q.t.fsc + 0] = q.mu / m0;
+      tab[q.t.fsc + 1] = 0.5 * q.g / m0;
+    }
+  }
   double* scr = scratch + blockIdx.x * scratch_per_block;
 
   if (q.level == 0) {
@@ -418,6 +445,14 @@ __global__ void k_setup_dinv(double* tab, int64_t dinv, int64_t lx, int64_t ly, 
   }
 }
 
+__global__ void k_setup_mass3(double* tab, int64_t mass3, int64_t mx, int64_t my, int64_t mz, int n) {
+  const int total = n * n * n;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    int a = i % n, b = (i / n) % n, c = i / (n * n);
+    tab[mass3 + i] = tab[mx + a] * tab[my + b] * tab[mz + c];
+  }
+}
+
 __global__ void k_cast_tables(const double* src, float* dst, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     dst[i] = (float)src[i];
@@ -443,6 +478,7 @@ cudaError_t launch_setup_coarse_tables(const double len[3], const int ne[3], dou
     q.g = 2.0 / q.h;
     q.mu = penalty * 2.0 / (2.0 * q.h);
     q.t = t[d];
+    q.t.ce = q.t.co = q.t.fe = q.t.fo = q.t.fsc = -1;
     q.J = -1;
     q.Ng = 2 * ne[d];
   }
@@ -479,6 +515,16 @@ cudaError_t launch_setup(mg_ctx* c) {
   c->nlaunch += 1;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  for (int l = 0; l <= c->L; ++l) {
+    const LevelInfo& lv = c->lev[l];
+    if (lv.mass3 < 0) continue;
+    int total = lv.n * lv.n * lv.n;
+    k_setup_mass3<<<(total + 255) / 256, 256, 0, s>>>(c->ws.tab64, lv.mass3, lv.t[0].mass, lv.t[1].mass,
+                                                      lv.t[2].mass, lv.n);
+    c->nlaunch += 1;
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   for (int l = 1; l <= c->L; ++l) {
     const LevelInfo& lv = c->lev[l];
     int64_t total = (int64_t)lv.m * lv.m * lv.m;

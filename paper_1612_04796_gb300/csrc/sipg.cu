@@ -1,6 +1,7 @@
 // Sum-factorised SIPG operator (Section 2, Eq. A):
-//   A = Mz(x)My(x)Lx + Mz(x)Ly(x)Mx + Lz(x)My(x)Mx
-// applied element by element.  Row block e of the 1D matrix L is
+//   A = Mz(x)My(x)Lx + Mz(x)Ly(x)Mx + Lz(x)My(x)Mx = M (I(x)I(x)Cx + I(x)Cy(x)I + Cz(x)I(x)I),
+// with M = Mz(x)My(x)Mx the diagonal mass and C_d = M_d^{-1} L_d, applied
+// element by element.  Row block e of the 1D matrix L is
 //   L_ee u_e + L_e,e-1 u_e-1 + L_e,e+1 u_e+1,
 // where L_ee = (2/h) D^T W D plus the self terms of both faces and the
 // neighbour couplings are rank-2 face terms (standard SIPG reading of Eq. ip):
@@ -8,13 +9,22 @@
 //        a = u_e-1 at its node P, b = (D u_e-1) at its node P,
 //   (L_e,e+1 u_e+1)_i = delta_iP (-mu c - g/2 d) + g/2 DP_i c,
 //        c = u_e+1 at its node 0, d = (D u_e+1) at its node 0,
-// with g = 2/h, D0 / DP the first / last row of the reference
-// differentiation matrix.  One thread per output DOF; the element and its
-// face neighbours are read through L1/L2.
+// with g = 2/h and D0 / DP the first / last row of the reference
+// differentiation matrix.
+//
+// L_ee and M_d are symmetric under reflection of the element (i -> P-i) and
+// DP_i = -D0_{P-i}, so every 1D line product is evaluated in even/odd form:
+// e_t = u_t + u_{P-t}, o_t = u_t - u_{P-t}; two half-size products; the face
+// rank-1 terms fold into the even part (with a + c) and the odd part (with
+// a - c).  One thread per 1D line; the three directions are three passes over
+// the element, accumulated in the output vector; the last pass applies the
+// mass and forms f - A u.
 #include "mg_internal.h"
 
 namespace mgdg {
 namespace {
+
+constexpr int kMaxHalf = kMaxN / 2 + 1;
 
 template <typename T>
 struct OpArgs {
@@ -23,112 +33,113 @@ struct OpArgs {
   const T* f;
   T* out;
   int64_t Ne;
-  int nx, ny, nz, n, residual;
-  int64_t lee[3], mass[3], d0, dp;
-  T g[3], mu[3];
+  int nx, ny, nz, n, residual, epb;
+  int64_t ce[3], co[3], fe[3], fo[3], fsc[3], d0, dp, mass3;
 };
+
+// One direction of one line.  ue / uL / uR: the line in the element and in
+// its left / right neighbour (same stride st); o: the output line.
+// mode 0: o = C u; 1: o += C u; 2: o = residual ? f - M (o + C u) : M (o + C u).
+template <typename T>
+__device__ __forceinline__ void line_apply(const OpArgs<T>& a, int d, const T* __restrict__ ue,
+                                           const T* __restrict__ uL, const T* __restrict__ uR, int st, T* o,
+                                           const T* __restrict__ fl, const T* __restrict__ m3, int m3st, int mode) {
+  const int n = a.n, P = n - 1, ne = (n + 1) / 2, no = n / 2;
+  const T* __restrict__ ce = a.tab + a.ce[d];
+  const T* __restrict__ co = a.tab + a.co[d];
+  const T* __restrict__ fe = a.tab + a.fe[d];
+  const T* __restrict__ fo = a.tab + a.fo[d];
+  const T* __restrict__ D0 = a.tab + a.d0;
+  const T* __restrict__ DP = a.tab + a.dp;
+  const T mu_m0 = a.tab[a.fsc[d]], g2_m0 = a.tab[a.fsc[d] + 1];
+  T ev[kMaxHalf], od[kMaxHalf];
+  for (int t = 0; t < no; ++t) {
+    const T xa = ue[t * st], xb = ue[(P - t) * st];
+    ev[t] = xa + xb;
+    od[t] = xa - xb;
+  }
+  if (n & 1) ev[no] = ue[no * st];
+  const T av = uL[P * st], cv = uR[0];
+  T b = 0, dd = 0;
+  for (int t = 0; t < n; ++t) {
+    b += DP[t] * uL[t * st];
+    dd += D0[t] * uR[t * st];
+  }
+  const T s = av + cv, tm = av - cv;
+  const T lo = g2_m0 * b - mu_m0 * av;     // extra term of output 0
+  const T hi = -(mu_m0 * cv + g2_m0 * dd);  // extra term of output P
+  for (int i = 0; i < ne; ++i) {
+    T E = fe[i] * s;
+    for (int t = 0; t < ne; ++t) E += ce[i * ne + t] * ev[t];
+    T v0, v1;
+    if (i < no) {
+      T O = fo[i] * tm;
+      for (int t = 0; t < no; ++t) O += co[i * no + t] * od[t];
+      v0 = E + O;
+      v1 = E - O;
+    } else {
+      v0 = v1 = E;
+    }
+    if (i == 0) {
+      v0 += lo;
+      v1 += hi;
+    }
+    const int i1 = P - i;
+    if (mode == 0) {
+      o[i * st] = v0;
+      if (i1 != i) o[i1 * st] = v1;
+    } else if (mode == 1) {
+      o[i * st] += v0;
+      if (i1 != i) o[i1 * st] += v1;
+    } else {
+      const T w0 = m3[i * m3st] * (o[i * st] + v0);
+      o[i * st] = a.residual ? fl[i * st] - w0 : w0;
+      if (i1 != i) {
+        const T w1 = m3[i1 * m3st] * (o[i1 * st] + v1);
+        o[i1 * st] = a.residual ? fl[i1 * st] - w1 : w1;
+      }
+    }
+  }
+}
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_sipg(OpArgs<T> a) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  T* sm = reinterpret_cast<T*>(smraw);
   const int n = a.n, n2 = n * n, n3 = n2 * n, P = n - 1;
-  T* sL = sm;             // 3 n^2
-  T* sM = sL + 3 * n2;    // 3 n
-  T* sD0 = sM + 3 * n;    // n
-  T* sDP = sD0 + n;       // n
-  for (int i = threadIdx.x; i < n2; i += blockDim.x) {
-    sL[i] = a.tab[a.lee[0] + i];
-    sL[n2 + i] = a.tab[a.lee[1] + i];
-    sL[2 * n2 + i] = a.tab[a.lee[2] + i];
+  const int lines = a.epb * n2;
+  const T* m3 = a.tab + a.mass3;
+  for (int64_t e0 = (int64_t)blockIdx.x * a.epb; e0 < a.Ne; e0 += (int64_t)gridDim.x * a.epb) {
+    for (int dir = 0; dir < 3; ++dir) {
+      for (int ln = threadIdx.x; ln < lines; ln += blockDim.x) {
+        const int64_t e = e0 + ln / n2;
+        if (e >= a.Ne) continue;
+        const int l2 = ln % n2, p = l2 % n, q = l2 / n;
+        const int ex = (int)(e % a.nx), ey = (int)((e / a.nx) % a.ny), ez = (int)(e / ((int64_t)a.nx * a.ny));
+        int64_t eL, eR;
+        int base, st;
+        if (dir == 0) {
+          eL = (ex == 0 ? a.nx - 1 : ex - 1) + a.nx * (ey + (int64_t)a.ny * ez);
+          eR = (ex == a.nx - 1 ? 0 : ex + 1) + a.nx * (ey + (int64_t)a.ny * ez);
+          base = n * (p + n * q);
+          st = 1;
+        } else if (dir == 1) {
+          eL = ex + a.nx * ((ey == 0 ? a.ny - 1 : ey - 1) + (int64_t)a.ny * ez);
+          eR = ex + a.nx * ((ey == a.ny - 1 ? 0 : ey + 1) + (int64_t)a.ny * ez);
+          base = p + n2 * q;
+          st = n;
+        } else {
+          eL = ex + a.nx * (ey + (int64_t)a.ny * (ez == 0 ? a.nz - 1 : ez - 1));
+          eR = ex + a.nx * (ey + (int64_t)a.ny * (ez == a.nz - 1 ? 0 : ez + 1));
+          base = p + n * q;
+          st = n2;
+        }
+        const int64_t off = e * n3 + base;
+        line_apply<T>(a, dir, a.u + off, a.u + eL * n3 + base, a.u + eR * n3 + base, st, a.out + off,
+                      a.residual ? a.f + off : nullptr, m3 + base, st, dir);
+      }
+      __syncthreads();
+    }
   }
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    sM[i] = a.tab[a.mass[0] + i];
-    sM[n + i] = a.tab[a.mass[1] + i];
-    sM[2 * n + i] = a.tab[a.mass[2] + i];
-    sD0[i] = a.tab[a.d0 + i];
-    sDP[i] = a.tab[a.dp + i];
-  }
-  __syncthreads();
-  const int64_t total = a.Ne * n3;
-  const T half = (T)0.5;
-  for (int64_t dof = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; dof < total;
-       dof += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t e = dof / n3;
-    const int loc = (int)(dof - e * n3);
-    const int i = loc % n, j = (loc / n) % n, k = loc / n2;
-    const int ex = (int)(e % a.nx), ey = (int)((e / a.nx) % a.ny), ez = (int)(e / ((int64_t)a.nx * a.ny));
-    const T* ue = a.u + e * n3;
-    T sx = 0, sy = 0, sz = 0;
-    for (int t = 0; t < n; ++t) {
-      sx += sL[i * n + t] * ue[t + n * (j + n * k)];
-      sy += sL[n2 + j * n + t] * ue[i + n * (t + n * k)];
-      sz += sL[2 * n2 + k * n + t] * ue[i + n * (j + n * t)];
-    }
-    // x faces
-    {
-      const int64_t eL = (ex == 0 ? ex + a.nx - 1 : ex - 1) + a.nx * (ey + (int64_t)a.ny * ez);
-      const int64_t eR = (ex == a.nx - 1 ? 0 : ex + 1) + a.nx * (ey + (int64_t)a.ny * ez);
-      const T* uL = a.u + eL * n3 + n * (j + n * k);
-      const T* uR = a.u + eR * n3 + n * (j + n * k);
-      const T av = uL[P], cv = uR[0];
-      const T g = a.g[0], mu = a.mu[0];
-      sx += g * half * (sDP[i] * cv - sD0[i] * av);
-      if (i == 0) {
-        T b = 0;
-        for (int t = 0; t < n; ++t) b += sDP[t] * uL[t];
-        sx += g * half * b - mu * av;
-      }
-      if (i == P) {
-        T d = 0;
-        for (int t = 0; t < n; ++t) d += sD0[t] * uR[t];
-        sx -= mu * cv + g * half * d;
-      }
-    }
-    // y faces
-    {
-      const int64_t eL = ex + a.nx * ((ey == 0 ? ey + a.ny - 1 : ey - 1) + (int64_t)a.ny * ez);
-      const int64_t eR = ex + a.nx * ((ey == a.ny - 1 ? 0 : ey + 1) + (int64_t)a.ny * ez);
-      const T* uL = a.u + eL * n3 + i + n2 * k;
-      const T* uR = a.u + eR * n3 + i + n2 * k;
-      const T av = uL[n * P], cv = uR[0];
-      const T g = a.g[1], mu = a.mu[1];
-      sy += g * half * (sDP[j] * cv - sD0[j] * av);
-      if (j == 0) {
-        T b = 0;
-        for (int t = 0; t < n; ++t) b += sDP[t] * uL[n * t];
-        sy += g * half * b - mu * av;
-      }
-      if (j == P) {
-        T d = 0;
-        for (int t = 0; t < n; ++t) d += sD0[t] * uR[n * t];
-        sy -= mu * cv + g * half * d;
-      }
-    }
-    // z faces
-    {
-      const int64_t eL = ex + a.nx * (ey + (int64_t)a.ny * (ez == 0 ? ez + a.nz - 1 : ez - 1));
-      const int64_t eR = ex + a.nx * (ey + (int64_t)a.ny * (ez == a.nz - 1 ? 0 : ez + 1));
-      const T* uL = a.u + eL * n3 + i + n * j;
-      const T* uR = a.u + eR * n3 + i + n * j;
-      const T av = uL[n2 * P], cv = uR[0];
-      const T g = a.g[2], mu = a.mu[2];
-      sz += g * half * (sDP[k] * cv - sD0[k] * av);
-      if (k == 0) {
-        T b = 0;
-        for (int t = 0; t < n; ++t) b += sDP[t] * uL[n2 * t];
-        sz += g * half * b - mu * av;
-      }
-      if (k == P) {
-        T d = 0;
-        for (int t = 0; t < n; ++t) d += sD0[t] * uR[n2 * t];
-        sz -= mu * cv + g * half * d;
-      }
-    }
-    const T mx = sM[i], my = sM[n + j], mz = sM[2 * n + k];
-    const T Au = mz * (my * sx + mx * sy) + my * mx * sz;
-    a.out[dof] = a.residual ? a.f[dof] - Au : Au;
-  }
+  (void)P;
 }
 
 template <typename T>
@@ -155,23 +166,23 @@ cudaError_t launch_sipg(const mg_ctx* c, int l, const T* u, const T* f, T* out, 
   a.n = lv.n;
   a.residual = residual;
   for (int d = 0; d < 3; ++d) {
-    a.lee[d] = lv.t[d].lee;
-    a.mass[d] = lv.t[d].mass;
-    a.g[d] = (T)lv.g[d];
-    a.mu[d] = (T)lv.mu[d];
+    a.ce[d] = lv.t[d].ce;
+    a.co[d] = lv.t[d].co;
+    a.fe[d] = lv.t[d].fe;
+    a.fo[d] = lv.t[d].fo;
+    a.fsc[d] = lv.t[d].fsc;
   }
   a.d0 = lv.t[0].d0;
   a.dp = lv.t[0].dp;
-  const int n = lv.n;
-  size_t smem = sizeof(T) * (3 * n * n + 5 * n);
-  int64_t total = c->Ne * (int64_t)n * n * n;
-  int64_t blocks = (total + 255) / 256;
-  if (blocks > 152 * 16) blocks = 152 * 16;
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_sipg<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-  }
-  k_sipg<T><<<(int)blocks, 256, smem, c->stream>>>(a);
+  a.mass3 = lv.mass3;
+  const int n2 = lv.n * lv.n;
+  a.epb = n2 >= 128 ? 1 : 128 / n2;
+  int threads = a.epb * n2;
+  threads = (threads + 31) / 32 * 32;
+  if (threads > 256) threads = 256;
+  int64_t groups = (c->Ne + a.epb - 1) / a.epb;
+  int64_t blocks = groups < 152 * 16 ? groups : 152 * 16;
+  k_sipg<T><<<(int)blocks, threads, 0, c->stream>>>(a);
   c->nlaunch += 1;
   return cudaGetLastError();
 }

@@ -262,6 +262,7 @@ def test_solve_c1_manufactured_matches_oracle(solver_cache):
     assert itg == ito
     # residual norms agree to 6 digits or down to the rounding floor of the
     # FP64 residual f - A u (~1e-16 of the initial residual)
+    ho = np.asarray(ho)
     assert np.all(np.abs(hg - ho) <= 1e-6 * ho + 1e-15 * ho[0])
     assert rel_err(host(ug), uo) < 1e-9
     assert np.max(np.abs(host(ug) - (u_ex - u_ex.mean()))) < 5e-3
@@ -276,6 +277,7 @@ def test_solve_cg_matches_oracle(solver_cache):
     uo, ito, ho = solve_mgcg(H, b, tol=1e-10)
     ug, itg, rel, hg = s.solve(cuda(b), tol=1e-10, use_cg=True)
     assert itg == ito
+    ho = np.asarray(ho)
     assert np.all(np.abs(hg - ho) <= 1e-6 * ho + 1e-15 * ho[0])
     assert rel_err(host(ug), uo) < 1e-9
 
