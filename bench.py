@@ -129,6 +129,25 @@ class ClockSampler:
                 "samples": len(sm), "power_w_max": max(power)}
 
 
+def profile_shares(s, total_ms):
+    out = {}
+    for kind in s.PROFILE_KINDS:
+        ms, _ = s.profile_result(kind)
+        out[kind] = round(ms / max(total_ms, 1e-9), 4)
+    return out
+
+
+def profile_levels(s, steps):
+    """Device ms per step for every kernel group and level (CUDA events)."""
+    out = {}
+    for kind in s.PROFILE_KINDS:
+        for lev in range(s.L + 1):
+            ms, cnt = s.profile_result(kind, lev)
+            if cnt:
+                out["%s@%d" % (kind, lev)] = round(ms / steps, 4)
+    return out
+
+
 def oracle_sample_solve(seed=2):
     """The FP64 CPU oracle on the bounded sample: returns (DOFs, solve seconds,
     setup seconds, iterations)."""
@@ -267,11 +286,8 @@ def run_mg(args):
         "peak_basis": "FP64 pipe: %d SMs x %d flop/clk x %.0f MHz (derived; %s peaks file has no FP64 entry)"
                       % (NUM_SMS, FP64_FLOP_PER_CLK_PER_SM, sm_max, pk_kind),
     }
-    shares = {}
-    for kind in ("fdm", "scatter", "sipg", "restrict", "prolong", "coarse"):
-        ms, cnt = s.profile_result(kind)
-        shares[kind] = round(ms / max(sum(step_ms), 1e-9), 4)
-    roofline["time_share_of_step"] = shares
+    roofline["time_share_of_step"] = profile_shares(s, sum(step_ms))
+    roofline["ms_per_step_by_kernel_level"] = profile_levels(s, args.steps)
 
     line = {
         "metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": world, "steps": args.steps,
@@ -306,6 +322,7 @@ def run_mg(args):
             sm_.solve(b, um, tol=W["tol"], use_cg=True)
         barrier()
         mix_ms = []
+        sm_.profile(True)
         for step in range(args.steps):
             flush.fill_(step & 0xFF)
             e0 = torch.cuda.Event(enable_timing=True)
@@ -317,13 +334,16 @@ def run_mg(args):
             e1.synchronize()
             mix_ms.append(e0.elapsed_time(e1))
         barrier()
+        sm_.profile(False)
         true_rel = float(torch.linalg.norm(s.residual(um, b)) / torch.linalg.norm(b))
         err = float(torch.max(torch.abs(um - u)) / torch.max(torch.abs(u)))
         mix_total = max_over_ranks(sum(mix_ms) / 1e3)
         line["mixed"] = {"value": world * N * args.steps / mix_total, "unit": "DOF/s",
                          "ms_per_step": sum(mix_ms) / args.steps, "iterations": its_m,
                          "solver": "MG-CG: FP32 V(1,1) preconditioner, FP64 inexact PCG",
-                         "true_relres": true_rel, "max_rel_diff_vs_fp64_solution": err}
+                         "true_relres": true_rel, "max_rel_diff_vs_fp64_solution": err,
+                         "time_share_of_step": profile_shares(sm_, sum(mix_ms)),
+                         "ms_per_step_by_kernel_level": profile_levels(sm_, args.steps)}
 
     if rank == 0 and not args.no_cpu_baseline:
         Ns, ts, _, its_s = oracle_sample_solve()

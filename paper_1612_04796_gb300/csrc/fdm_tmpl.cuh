@@ -1,0 +1,199 @@
+// Fast-diagonalisation smoother kernel with the subdomain width m as a
+// compile-time constant (Section 3.1): the 1D lines live in registers and the
+// even/odd products are fully unrolled.  Same algorithm, same memory layout
+// and same results as the run-time-size kernel in schwarz.cu; included only by
+// the instantiation units fdm_m_*.cu.
+#pragma once
+
+#include "mg_internal.h"
+
+namespace mgdg {
+
+template <typename T>
+struct FdmArgs {
+  const T* tab;
+  const T* r;
+  T* corr;
+  int64_t Ne;
+  int nx, ny, nz, n, m, no, spb;
+  int64_t S[3], SW[3], dinv;
+};
+
+__device__ __forceinline__ void fdm_sub_node(int a, int n, int no, int* de, int* ii) {
+  if (a < no) { *de = -1; *ii = n - no + a; }
+  else if (a < no + n) { *de = 0; *ii = a - no; }
+  else { *de = 1; *ii = a - no - n; }
+}
+
+__device__ __forceinline__ int fdm_wrap(int x, int n) { return x < 0 ? x + n : (x >= n ? x - n : x); }
+
+// y = S^T x for a reflection-symmetric line (even modes first); x is overwritten.
+template <typename T, int M>
+__device__ __forceinline__ void fdm_fwd(T (&x)[M], const T* __restrict__ S, T (&y)[M]) {
+  constexpr int h = M / 2, ne = h + 1;
+#pragma unroll
+  for (int a = 0; a < h; ++a) {
+    const T xa = x[a], xb = x[M - 1 - a];
+    x[a] = xa + xb;
+    x[M - 1 - a] = xa - xb;
+  }
+#pragma unroll
+  for (int p = 0; p < ne; ++p) {
+    T acc = S[p] * x[0];
+#pragma unroll
+    for (int a = 1; a <= h; ++a) acc += S[a * M + p] * x[a];
+    y[p] = acc;
+  }
+#pragma unroll
+  for (int q = 0; q < h; ++q) {
+    T acc = S[ne + q] * x[M - 1];
+#pragma unroll
+    for (int a = 1; a < h; ++a) acc += S[a * M + ne + q] * x[M - 1 - a];
+    y[ne + q] = acc;
+  }
+}
+
+// x = SW v (weights folded into SW).
+template <typename T, int M>
+__device__ __forceinline__ void fdm_bwd(const T (&v)[M], const T* __restrict__ SW, T (&x)[M]) {
+  constexpr int h = M / 2, ne = h + 1;
+#pragma unroll
+  for (int a = 0; a <= h; ++a) {
+    T E = SW[a * M] * v[0];
+#pragma unroll
+    for (int p = 1; p < ne; ++p) E += SW[a * M + p] * v[p];
+    if (a < h) {
+      T O = SW[a * M + ne] * v[ne];
+#pragma unroll
+      for (int q = 1; q < h; ++q) O += SW[a * M + ne + q] * v[ne + q];
+      x[a] = E + O;
+      x[M - 1 - a] = E - O;
+    } else {
+      x[a] = E;
+    }
+  }
+}
+
+template <typename T, int M>
+__global__ void __launch_bounds__(256) k_fdm_m(FdmArgs<T> a) {
+  constexpr int M2 = M * M, M3 = M2 * M;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* sS = reinterpret_cast<T*>(smraw);  // 3 M^2
+  T* sSW = sS + 3 * M2;                 // 3 M^2
+  for (int i = threadIdx.x; i < M2; i += blockDim.x) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      sS[d * M2 + i] = a.tab[a.S[d] + i];
+      sSW[d * M2 + i] = a.tab[a.SW[d] + i];
+    }
+  }
+  __syncthreads();
+  const T* __restrict__ dinv = a.tab + a.dinv;
+  const int n = a.n, no = a.no, n3 = n * n * n, spb = a.spb;
+  const int lines = spb * M2;
+  for (int64_t s0 = (int64_t)blockIdx.x * spb; s0 < a.Ne; s0 += (int64_t)gridDim.x * spb) {
+    // pass 1: gather x-lines of r_s and transform (forward, x)
+    for (int ln = threadIdx.x; ln < lines; ln += blockDim.x) {
+      const int64_t s = s0 + ln / M2;
+      if (s >= a.Ne) continue;
+      const int l2 = ln % M2, b = l2 % M, c = l2 / M;
+      const int sx = (int)(s % a.nx), sy = (int)((s / a.nx) % a.ny), sz = (int)(s / ((int64_t)a.nx * a.ny));
+      int dy, iy, dz, iz;
+      fdm_sub_node(b, n, no, &dy, &iy);
+      fdm_sub_node(c, n, no, &dz, &iz);
+      const int64_t row = a.nx * (fdm_wrap(sy + dy, a.ny) + (int64_t)a.ny * fdm_wrap(sz + dz, a.nz));
+      const int loc = n * (iy + n * iz);
+      // offsets of position t of the line in the left / centre / right element
+      const int64_t ol = (fdm_wrap(sx - 1, a.nx) + row) * n3 + loc + (n - no);
+      const int64_t oc = (sx + row) * n3 + loc - no;
+      const int64_t orr = (fdm_wrap(sx + 1, a.nx) + row) * n3 + loc - (no + n);
+      T x[M], y[M];
+#pragma unroll
+      for (int t = 0; t < M; ++t) x[t] = a.r[(t < no ? ol : (t < no + n ? oc : orr)) + t];
+      fdm_fwd<T, M>(x, sS, y);
+      T* tile = a.corr + s * (int64_t)M3 + M * l2;
+#pragma unroll
+      for (int p = 0; p < M; ++p) tile[p] = y[p];
+    }
+    __syncthreads();
+    // pass 2: forward, y
+    for (int ln = threadIdx.x; ln < lines; ln += blockDim.x) {
+      const int64_t s = s0 + ln / M2;
+      if (s >= a.Ne) continue;
+      const int l2 = ln % M2;
+      T* line = a.corr + s * (int64_t)M3 + (l2 % M) + M2 * (l2 / M);
+      T x[M], y[M];
+#pragma unroll
+      for (int t = 0; t < M; ++t) x[t] = line[t * M];
+      fdm_fwd<T, M>(x, sS + M2, y);
+#pragma unroll
+      for (int t = 0; t < M; ++t) line[t * M] = y[t];
+    }
+    __syncthreads();
+    // pass 3: forward z, scale by 1 / (lam_x + lam_y + lam_z), backward z
+    for (int ln = threadIdx.x; ln < lines; ln += blockDim.x) {
+      const int64_t s = s0 + ln / M2;
+      if (s >= a.Ne) continue;
+      const int l2 = ln % M2;
+      T* line = a.corr + s * (int64_t)M3 + l2;
+      T x[M], y[M];
+#pragma unroll
+      for (int t = 0; t < M; ++t) x[t] = line[t * M2];
+      fdm_fwd<T, M>(x, sS + 2 * M2, y);
+#pragma unroll
+      for (int t = 0; t < M; ++t) y[t] *= dinv[l2 + t * M2];
+      fdm_bwd<T, M>(y, sSW + 2 * M2, x);
+#pragma unroll
+      for (int t = 0; t < M; ++t) line[t * M2] = x[t];
+    }
+    __syncthreads();
+    // pass 4: backward, y
+    for (int ln = threadIdx.x; ln < lines; ln += blockDim.x) {
+      const int64_t s = s0 + ln / M2;
+      if (s >= a.Ne) continue;
+      const int l2 = ln % M2;
+      T* line = a.corr + s * (int64_t)M3 + (l2 % M) + M2 * (l2 / M);
+      T x[M], y[M];
+#pragma unroll
+      for (int t = 0; t < M; ++t) y[t] = line[t * M];
+      fdm_bwd<T, M>(y, sSW + M2, x);
+#pragma unroll
+      for (int t = 0; t < M; ++t) line[t * M] = x[t];
+    }
+    __syncthreads();
+    // pass 5: backward, x (weights folded into SW)
+    for (int ln = threadIdx.x; ln < lines; ln += blockDim.x) {
+      const int64_t s = s0 + ln / M2;
+      if (s >= a.Ne) continue;
+      const int l2 = ln % M2;
+      T* line = a.corr + s * (int64_t)M3 + M * l2;
+      T x[M], y[M];
+#pragma unroll
+      for (int t = 0; t < M; ++t) y[t] = line[t];
+      fdm_bwd<T, M>(y, sSW, x);
+#pragma unroll
+      for (int t = 0; t < M; ++t) line[t] = x[t];
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T, int M>
+cudaError_t launch_fdm_m(const FdmArgs<T>& a, int blocks, int threads, size_t smem, cudaStream_t s) {
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_fdm_m<T, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_fdm_m<T, M><<<blocks, threads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+#define MGDG_FDM_EXTERN(M)                                                                                   \
+  extern template cudaError_t launch_fdm_m<double, M>(const FdmArgs<double>&, int, int, size_t, cudaStream_t); \
+  extern template cudaError_t launch_fdm_m<float, M>(const FdmArgs<float>&, int, int, size_t, cudaStream_t);
+
+#define MGDG_FDM_INSTANTIATE(M)                                                                              \
+  template cudaError_t launch_fdm_m<double, M>(const FdmArgs<double>&, int, int, size_t, cudaStream_t);     \
+  template cudaError_t launch_fdm_m<float, M>(const FdmArgs<float>&, int, int, size_t, cudaStream_t);
+
+}  // namespace mgdg

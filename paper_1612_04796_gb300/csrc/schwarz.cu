@@ -12,29 +12,21 @@
 // output DOF: every DOF sums the <= 8 (<= 27 at the widest overlap) subdomain
 // values that cover it in a fixed order, so the result is deterministic and
 // no atomics are needed.
-#include "mg_internal.h"
+#include "fdm_tmpl.cuh"
 
 namespace mgdg {
+
+MGDG_FDM_EXTERN(3) MGDG_FDM_EXTERN(5) MGDG_FDM_EXTERN(7) MGDG_FDM_EXTERN(9) MGDG_FDM_EXTERN(11)
+MGDG_FDM_EXTERN(13) MGDG_FDM_EXTERN(15) MGDG_FDM_EXTERN(17) MGDG_FDM_EXTERN(19) MGDG_FDM_EXTERN(21)
+MGDG_FDM_EXTERN(23) MGDG_FDM_EXTERN(25) MGDG_FDM_EXTERN(27) MGDG_FDM_EXTERN(29) MGDG_FDM_EXTERN(31)
+MGDG_FDM_EXTERN(33) MGDG_FDM_EXTERN(35)
+
 namespace {
 
-template <typename T>
-struct FdmArgs {
-  const T* tab;
-  const T* r;
-  T* corr;
-  int64_t Ne;
-  int nx, ny, nz, n, m, no;
-  int64_t S[3], SW[3], dinv;
-};
+using mgdg::FdmArgs;
 
-// Subdomain line position a -> (element offset, node index).
-__device__ __forceinline__ void sub_node(int a, int n, int no, int* de, int* ii) {
-  if (a < no) { *de = -1; *ii = n - no + a; }
-  else if (a < no + n) { *de = 0; *ii = a - no; }
-  else { *de = 1; *ii = a - no - n; }
-}
-
-__device__ __forceinline__ int wrap(int x, int n) { return x < 0 ? x + n : (x >= n ? x - n : x); }
+__device__ __forceinline__ void sub_node(int a, int n, int no, int* de, int* ii) { fdm_sub_node(a, n, no, de, ii); }
+__device__ __forceinline__ int wrap(int x, int n) { return fdm_wrap(x, n); }
 
 // Even/odd 1D transforms of one subdomain line (m = 2h+1, odd).  The
 // eigenvectors of the reflection-symmetric line problem are even (columns
@@ -220,11 +212,30 @@ cudaError_t launch_fdm(const mg_ctx* c, int l, const T* r) {
   }
   a.dinv = lv.dinv;
   size_t smem = sizeof(T) * 6 * lv.m * lv.m;
+  const int m2 = lv.m * lv.m;
+  if ((lv.m & 1) && lv.m >= 3 && lv.m <= 35) {
+    // compile-time width: several subdomains per block when m^2 is small
+    a.spb = m2 >= 128 ? 1 : 128 / m2;
+    int threads = a.spb * m2;
+    threads = threads > 256 ? 256 : (threads + 31) / 32 * 32;
+    int64_t groups = (c->Ne + a.spb - 1) / a.spb;
+    int blocks = (int)(groups < 152 * 8 ? groups : 152 * 8);
+    c->nlaunch += 1;
+    switch (lv.m) {
+#define MGDG_CASE(M) case M: return launch_fdm_m<T, M>(a, blocks, threads, smem, c->stream);
+      MGDG_CASE(3) MGDG_CASE(5) MGDG_CASE(7) MGDG_CASE(9) MGDG_CASE(11) MGDG_CASE(13) MGDG_CASE(15)
+      MGDG_CASE(17) MGDG_CASE(19) MGDG_CASE(21) MGDG_CASE(23) MGDG_CASE(25) MGDG_CASE(27) MGDG_CASE(29)
+      MGDG_CASE(31) MGDG_CASE(33) MGDG_CASE(35)
+#undef MGDG_CASE
+      default: break;
+    }
+  }
+  a.spb = 1;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_fdm<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  int threads = lv.m * lv.m >= 256 ? 256 : 128;
+  int threads = m2 >= 256 ? 256 : 128;
   int64_t blocks = c->Ne < 152 * 8 ? c->Ne : 152 * 8;
   k_fdm<T><<<(int)blocks, threads, smem, c->stream>>>(a);
   c->nlaunch += 1;

@@ -142,6 +142,114 @@ __global__ void __launch_bounds__(256) k_sipg(OpArgs<T> a) {
   (void)P;
 }
 
+// Compile-time-size version of line_apply / k_sipg (lines in registers).
+template <typename T, int N>
+__device__ __forceinline__ void line_apply_n(const OpArgs<T>& a, int d, const T* __restrict__ ue,
+                                             const T* __restrict__ uL, const T* __restrict__ uR, int st, T* o,
+                                             const T* __restrict__ fl, const T* __restrict__ m3, int mode) {
+  constexpr int P = N - 1, ne = (N + 1) / 2, no = N / 2;
+  const T* __restrict__ ce = a.tab + a.ce[d];
+  const T* __restrict__ co = a.tab + a.co[d];
+  const T* __restrict__ fe = a.tab + a.fe[d];
+  const T* __restrict__ fo = a.tab + a.fo[d];
+  const T* __restrict__ D0 = a.tab + a.d0;
+  const T* __restrict__ DP = a.tab + a.dp;
+  const T mu_m0 = a.tab[a.fsc[d]], g2_m0 = a.tab[a.fsc[d] + 1];
+  T ev[ne], od[no > 0 ? no : 1];
+#pragma unroll
+  for (int t = 0; t < no; ++t) {
+    const T xa = ue[t * st], xb = ue[(P - t) * st];
+    ev[t] = xa + xb;
+    od[t] = xa - xb;
+  }
+  if (N & 1) ev[ne - 1] = ue[no * st];
+  const T av = uL[P * st], cv = uR[0];
+  T b = 0, dd = 0;
+#pragma unroll
+  for (int t = 0; t < N; ++t) {
+    b += DP[t] * uL[t * st];
+    dd += D0[t] * uR[t * st];
+  }
+  const T s = av + cv, tm = av - cv;
+  const T lo = g2_m0 * b - mu_m0 * av;
+  const T hi = -(mu_m0 * cv + g2_m0 * dd);
+#pragma unroll
+  for (int i = 0; i < ne; ++i) {
+    T E = fe[i] * s;
+#pragma unroll
+    for (int t = 0; t < ne; ++t) E += ce[i * ne + t] * ev[t];
+    T v0, v1;
+    if (i < no) {
+      T O = fo[i] * tm;
+#pragma unroll
+      for (int t = 0; t < no; ++t) O += co[i * no + t] * od[t];
+      v0 = E + O;
+      v1 = E - O;
+    } else {
+      v0 = v1 = E;
+    }
+    if (i == 0) {
+      v0 += lo;
+      v1 += hi;
+    }
+    const int i1 = P - i;
+    if (mode == 0) {
+      o[i * st] = v0;
+      if (i1 != i) o[i1 * st] = v1;
+    } else if (mode == 1) {
+      o[i * st] += v0;
+      if (i1 != i) o[i1 * st] += v1;
+    } else {
+      const T w0 = m3[i * st] * (o[i * st] + v0);
+      o[i * st] = a.residual ? fl[i * st] - w0 : w0;
+      if (i1 != i) {
+        const T w1 = m3[i1 * st] * (o[i1 * st] + v1);
+        o[i1 * st] = a.residual ? fl[i1 * st] - w1 : w1;
+      }
+    }
+  }
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(256) k_sipg_n(OpArgs<T> a) {
+  constexpr int n2 = N * N, n3 = n2 * N;
+  const int lines = a.epb * n2;
+  const T* m3 = a.tab + a.mass3;
+  for (int64_t e0 = (int64_t)blockIdx.x * a.epb; e0 < a.Ne; e0 += (int64_t)gridDim.x * a.epb) {
+#pragma unroll 1
+    for (int dir = 0; dir < 3; ++dir) {
+      for (int ln = threadIdx.x; ln < lines; ln += blockDim.x) {
+        const int64_t e = e0 + ln / n2;
+        if (e >= a.Ne) continue;
+        const int l2 = ln % n2, p = l2 % N, q = l2 / N;
+        const int ex = (int)(e % a.nx), ey = (int)((e / a.nx) % a.ny), ez = (int)(e / ((int64_t)a.nx * a.ny));
+        int64_t eL, eR;
+        int base, st;
+        if (dir == 0) {
+          eL = (ex == 0 ? a.nx - 1 : ex - 1) + a.nx * (ey + (int64_t)a.ny * ez);
+          eR = (ex == a.nx - 1 ? 0 : ex + 1) + a.nx * (ey + (int64_t)a.ny * ez);
+          base = N * (p + N * q);
+          st = 1;
+        } else if (dir == 1) {
+          eL = ex + a.nx * ((ey == 0 ? a.ny - 1 : ey - 1) + (int64_t)a.ny * ez);
+          eR = ex + a.nx * ((ey == a.ny - 1 ? 0 : ey + 1) + (int64_t)a.ny * ez);
+          base = p + n2 * q;
+          st = N;
+        } else {
+          eL = ex + a.nx * (ey + (int64_t)a.ny * (ez == 0 ? a.nz - 1 : ez - 1));
+          eR = ex + a.nx * (ey + (int64_t)a.ny * (ez == a.nz - 1 ? 0 : ez + 1));
+          base = p + N * q;
+          st = n2;
+        }
+        const int64_t off = e * n3 + base;
+        line_apply_n<T, N>(a, dir, a.u + off, a.u + eL * n3 + base, a.u + eR * n3 + base, st, a.out + off,
+                           a.residual ? a.f + off : nullptr, m3 + base, dir);
+      }
+      __syncthreads();
+    }
+  }
+}
+
 template <typename T>
 const T* table_of(const mg_ctx* c);
 template <>
@@ -182,8 +290,16 @@ cudaError_t launch_sipg(const mg_ctx* c, int l, const T* u, const T* f, T* out, 
   if (threads > 256) threads = 256;
   int64_t groups = (c->Ne + a.epb - 1) / a.epb;
   int64_t blocks = groups < 152 * 16 ? groups : 152 * 16;
-  k_sipg<T><<<(int)blocks, threads, 0, c->stream>>>(a);
   c->nlaunch += 1;
+  switch (lv.n) {
+    case 2: k_sipg_n<T, 2><<<(int)blocks, threads, 0, c->stream>>>(a); break;
+    case 3: k_sipg_n<T, 3><<<(int)blocks, threads, 0, c->stream>>>(a); break;
+    case 5: k_sipg_n<T, 5><<<(int)blocks, threads, 0, c->stream>>>(a); break;
+    case 9: k_sipg_n<T, 9><<<(int)blocks, threads, 0, c->stream>>>(a); break;
+    case 17: k_sipg_n<T, 17><<<(int)blocks, threads, 0, c->stream>>>(a); break;
+    case 33: k_sipg_n<T, 33><<<(int)blocks, threads, 0, c->stream>>>(a); break;
+    default: k_sipg<T><<<(int)blocks, threads, 0, c->stream>>>(a); break;
+  }
   return cudaGetLastError();
 }
 
