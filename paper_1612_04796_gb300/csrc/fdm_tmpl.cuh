@@ -74,12 +74,25 @@ __device__ __forceinline__ void fdm_bwd(const T (&v)[M], const T* __restrict__ S
   }
 }
 
+// Subdomains per block and whether their tiles fit in shared memory (the
+// last pass always writes the corrections to the global buffer).
+template <typename T, int M>
+struct FdmShape {
+  static constexpr int spb = M * M >= 128 ? 1 : 128 / (M * M);
+  static constexpr size_t table_bytes = sizeof(T) * 6 * M * M;
+  static constexpr size_t tile_bytes = sizeof(T) * spb * M * M * M;
+  static constexpr bool smem_tile = table_bytes + tile_bytes <= 210 * 1024;
+  static constexpr size_t smem = table_bytes + (smem_tile ? tile_bytes : 0);
+};
+
 template <typename T, int M>
 __global__ void __launch_bounds__(256) k_fdm_m(FdmArgs<T> a) {
   constexpr int M2 = M * M, M3 = M2 * M;
+  constexpr bool kSmemTile = FdmShape<T, M>::smem_tile;
   extern __shared__ __align__(16) unsigned char smraw[];
   T* sS = reinterpret_cast<T*>(smraw);  // 3 M^2
   T* sSW = sS + 3 * M2;                 // 3 M^2
+  T* sTile = sSW + 3 * M2;              // spb M^3 (if kSmemTile)
   for (int i = threadIdx.x; i < M2; i += blockDim.x) {
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
@@ -111,7 +124,7 @@ __global__ void __launch_bounds__(256) k_fdm_m(FdmArgs<T> a) {
 #pragma unroll
       for (int t = 0; t < M; ++t) x[t] = a.r[(t < no ? ol : (t < no + n ? oc : orr)) + t];
       fdm_fwd<T, M>(x, sS, y);
-      T* tile = a.corr + s * (int64_t)M3 + M * l2;
+      T* tile = (kSmemTile ? sTile + (ln / M2) * M3 : a.corr + s * (int64_t)M3) + M * l2;
 #pragma unroll
       for (int p = 0; p < M; ++p) tile[p] = y[p];
     }
@@ -121,7 +134,7 @@ __global__ void __launch_bounds__(256) k_fdm_m(FdmArgs<T> a) {
       const int64_t s = s0 + ln / M2;
       if (s >= a.Ne) continue;
       const int l2 = ln % M2;
-      T* line = a.corr + s * (int64_t)M3 + (l2 % M) + M2 * (l2 / M);
+      T* line = (kSmemTile ? sTile + (ln / M2) * M3 : a.corr + s * (int64_t)M3) + (l2 % M) + M2 * (l2 / M);
       T x[M], y[M];
 #pragma unroll
       for (int t = 0; t < M; ++t) x[t] = line[t * M];
@@ -135,7 +148,7 @@ __global__ void __launch_bounds__(256) k_fdm_m(FdmArgs<T> a) {
       const int64_t s = s0 + ln / M2;
       if (s >= a.Ne) continue;
       const int l2 = ln % M2;
-      T* line = a.corr + s * (int64_t)M3 + l2;
+      T* line = (kSmemTile ? sTile + (ln / M2) * M3 : a.corr + s * (int64_t)M3) + l2;
       T x[M], y[M];
 #pragma unroll
       for (int t = 0; t < M; ++t) x[t] = line[t * M2];
@@ -152,7 +165,7 @@ __global__ void __launch_bounds__(256) k_fdm_m(FdmArgs<T> a) {
       const int64_t s = s0 + ln / M2;
       if (s >= a.Ne) continue;
       const int l2 = ln % M2;
-      T* line = a.corr + s * (int64_t)M3 + (l2 % M) + M2 * (l2 / M);
+      T* line = (kSmemTile ? sTile + (ln / M2) * M3 : a.corr + s * (int64_t)M3) + (l2 % M) + M2 * (l2 / M);
       T x[M], y[M];
 #pragma unroll
       for (int t = 0; t < M; ++t) y[t] = line[t * M];
@@ -166,20 +179,22 @@ __global__ void __launch_bounds__(256) k_fdm_m(FdmArgs<T> a) {
       const int64_t s = s0 + ln / M2;
       if (s >= a.Ne) continue;
       const int l2 = ln % M2;
-      T* line = a.corr + s * (int64_t)M3 + M * l2;
+      const T* line = (kSmemTile ? sTile + (ln / M2) * M3 : a.corr + s * (int64_t)M3) + M * l2;
+      T* outl = a.corr + s * (int64_t)M3 + M * l2;
       T x[M], y[M];
 #pragma unroll
       for (int t = 0; t < M; ++t) y[t] = line[t];
       fdm_bwd<T, M>(y, sSW, x);
 #pragma unroll
-      for (int t = 0; t < M; ++t) line[t] = x[t];
+      for (int t = 0; t < M; ++t) outl[t] = x[t];
     }
     __syncthreads();
   }
 }
 
 template <typename T, int M>
-cudaError_t launch_fdm_m(const FdmArgs<T>& a, int blocks, int threads, size_t smem, cudaStream_t s) {
+cudaError_t launch_fdm_m(const FdmArgs<T>& a, int blocks, int threads, size_t /*smem*/, cudaStream_t s) {
+  const size_t smem = FdmShape<T, M>::smem;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_fdm_m<T, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

@@ -188,6 +188,53 @@ struct ProfScope {
   }
 };
 
+// Run `body` (stream-ordered launches on c->stream, no host synchronisation)
+// through a cached CUDA graph: captured once on an internal stream, replayed
+// on the caller's stream.  Eager when graphs are off or profiling is on.
+template <typename F>
+cudaError_t run_graph(mg_ctx* c, int kind, const void* a, const void* b, F body) {
+  if (!c->use_graphs || c->prof_on) return body();
+  for (auto& g : c->graphs) {
+    if (g.kind == kind && g.a == a && g.b == b) {
+      c->nlaunch += g.kernels;
+      return cudaGraphLaunch(g.exec, c->stream);
+    }
+  }
+  cudaError_t e;
+  if (!c->cap_stream && (e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
+    return e;
+  cudaStream_t user = c->stream;
+  const long long n0 = c->nlaunch;
+  c->stream = c->cap_stream;
+  if ((e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeRelaxed)) != cudaSuccess) {
+    c->stream = user;
+    return e;
+  }
+  cudaError_t eb = body();
+  cudaGraph_t graph = nullptr;
+  cudaError_t ee = cudaStreamEndCapture(c->cap_stream, &graph);
+  c->stream = user;
+  const long long kernels = c->nlaunch - n0;
+  c->nlaunch = n0;
+  if (eb != cudaSuccess || ee != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return eb != cudaSuccess ? eb : ee;
+  }
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return e;
+  if (c->graphs.size() >= 16) {
+    cudaGraphExecDestroy(c->graphs.front().exec);
+    c->graphs.erase(c->graphs.begin());
+  }
+  c->graphs.push_back({kind, a, b, exec, kernels});
+  c->nlaunch += kernels;
+  return cudaGraphLaunch(exec, c->stream);
+}
+
+enum GraphKind : int { kGraphMgCycle = 1, kGraphPrecond, kGraphVcycle, kGraphVcycle32, kGraphCgA, kGraphCgB };
+
 // ---- level vector views ----
 template <typename T>
 T* lvec(void* p) {
@@ -306,7 +353,8 @@ mg_status solve_impl(mg_ctx* c, double* u, const double* f, double tol, int maxi
   bool converged = false;
   if (!use_cg) {
     double* r = lvec<double>(c->lev[L].r);
-    if (c->opts.precision == MG_MIXED) r = c->ws.cg[1];
+    const bool mixed = c->opts.precision == MG_MIXED;
+    if (mixed) r = c->ws.cg[1];
     CK(launch_sipg<double>(c, L, u, f, r, 1));
     CK(launch_dot(c, r, r, N, kSlotRR));
     double rr = read_scalar(c, kSlotRR, &err);
@@ -316,19 +364,22 @@ mg_status solve_impl(mg_ctx* c, double* u, const double* f, double tol, int maxi
     converged = r0 == 0.0;
     while (!converged && it < maxit) {
       ++it;
-      if (c->opts.precision == MG_MIXED) {
-        // defect correction: u += B r with the FP32 V-cycle
-        double* z = c->ws.cg[2];
-        CK(precond(c, r, z));
-        CK(launch_add(c, u, z, N));
-      } else {
-        CK((vcycle_t<double>(c, u, f, false, true)));
-      }
-      {
-        ProfScope ps(c, kProfSipg, L);
-        CK(launch_sipg<double>(c, L, u, f, r, 1));
-      }
-      CK(launch_dot(c, r, r, N, kSlotRR));
+      // one cycle (FP64 V-cycle, or mixed defect correction u += B r) and the new residual norm
+      CK(run_graph(c, kGraphMgCycle, u, f, [&]() -> cudaError_t {
+        cudaError_t e;
+        if (mixed) {
+          double* z = c->ws.cg[2];
+          if ((e = precond(c, r, z)) != cudaSuccess) return e;
+          if ((e = launch_add(c, u, z, N)) != cudaSuccess) return e;
+        } else if ((e = vcycle_t<double>(c, u, f, false, true)) != cudaSuccess) {
+          return e;
+        }
+        {
+          ProfScope ps(c, kProfSipg, L);
+          if ((e = launch_sipg<double>(c, L, u, f, r, 1)) != cudaSuccess) return e;
+        }
+        return launch_dot(c, r, r, N, kSlotRR);
+      }));
       double v = read_scalar(c, kSlotRR, &err);
       CK(err);
       rn = sqrt(v);
@@ -359,15 +410,19 @@ mg_status solve_impl(mg_ctx* c, double* u, const double* f, double tol, int maxi
     }
     while (!converged && it < maxit) {
       ++it;
-      {
-        ProfScope ps(c, kProfSipg, L);
-        CK(launch_sipg<double>(c, L, p, nullptr, q, 0));
-      }
-      CK(launch_dot(c, p, q, N, kSlotPQ));
-      CK(launch_axpy2(c, x, p, r, q, N, kSlotRZ, kSlotPQ));  // alpha = rz / pq
-      CK(launch_sum(c, r, N, kSlotSum));
-      CK(launch_sub_mean(c, r, N, kSlotSum));
-      CK(launch_dot(c, r, r, N, kSlotRR));
+      // q = A p, alpha = rz / pq, x += alpha p, r -= alpha q, r projected, rr = r.r
+      CK(run_graph(c, kGraphCgA, x, f, [&]() -> cudaError_t {
+        cudaError_t e;
+        {
+          ProfScope ps(c, kProfSipg, L);
+          if ((e = launch_sipg<double>(c, L, p, nullptr, q, 0)) != cudaSuccess) return e;
+        }
+        if ((e = launch_dot(c, p, q, N, kSlotPQ)) != cudaSuccess) return e;
+        if ((e = launch_axpy2(c, x, p, r, q, N, kSlotRZ, kSlotPQ)) != cudaSuccess) return e;
+        if ((e = launch_sum(c, r, N, kSlotSum)) != cudaSuccess) return e;
+        if ((e = launch_sub_mean(c, r, N, kSlotSum)) != cudaSuccess) return e;
+        return launch_dot(c, r, r, N, kSlotRR);
+      }));
       double v = read_scalar(c, kSlotRR, &err);
       CK(err);
       rn = sqrt(v);
@@ -376,13 +431,17 @@ mg_status solve_impl(mg_ctx* c, double* u, const double* f, double tol, int maxi
         converged = true;
         break;
       }
-      CK(precond(c, r, z));
-      CK(launch_sum(c, z, N, kSlotSum));
-      CK(launch_sub_mean(c, z, N, kSlotSum));
-      // beta = z_new . (r_new - r_old) / (z_old . r_old) = -alpha (z_new . q) / rz_old
-      CK(launch_dot(c, z, q, N, kSlotZQ));
-      CK(launch_xpby(c, p, z, N, kSlotZQ, kSlotRZ, kSlotAlpha));
-      CK(launch_dot(c, r, z, N, kSlotRZ));
+      // z = B r projected; beta = z_new . (r_new - r_old) / (z_old . r_old) = -alpha (z_new . q) / rz_old;
+      // p = z + beta p; rz = r . z
+      CK(run_graph(c, kGraphCgB, x, f, [&]() -> cudaError_t {
+        cudaError_t e;
+        if ((e = precond(c, r, z)) != cudaSuccess) return e;
+        if ((e = launch_sum(c, z, N, kSlotSum)) != cudaSuccess) return e;
+        if ((e = launch_sub_mean(c, z, N, kSlotSum)) != cudaSuccess) return e;
+        if ((e = launch_dot(c, z, q, N, kSlotZQ)) != cudaSuccess) return e;
+        if ((e = launch_xpby(c, p, z, N, kSlotZQ, kSlotRZ, kSlotAlpha)) != cudaSuccess) return e;
+        return launch_dot(c, r, z, N, kSlotRZ);
+      }));
     }
   }
   CK(launch_sum(c, u, N, kSlotSum));
@@ -664,7 +723,7 @@ mg_status mg_vcycle(mg_ctx* c, double* u, const double* f) {
   mg_status s = need_ready(c);
   if (s != MG_OK) return s;
   if (!u || !f || u == f) return fail(c, MG_EINVAL, "bad pointers");
-  CK((vcycle_t<double>(c, u, f, false, false)));
+  CK(run_graph(c, kGraphVcycle, u, f, [&]() { return vcycle_t<double>(c, u, f, false, false); }));
   return MG_OK;
 }
 
@@ -672,7 +731,7 @@ mg_status mg_vcycle_f32(mg_ctx* c, float* u, const float* f) {
   mg_status s = need_ready(c);
   if (s != MG_OK) return s;
   if (!u || !f || u == f) return fail(c, MG_EINVAL, "bad pointers");
-  CK((vcycle_t<float>(c, u, f, false, false)));
+  CK(run_graph(c, kGraphVcycle32, u, f, [&]() { return vcycle_t<float>(c, u, f, false, false); }));
   return MG_OK;
 }
 
@@ -765,6 +824,8 @@ mg_status mg_profile_result(mg_ctx* c, int kind, int level, double* total_ms, lo
 
 void mg_destroy(mg_ctx* c) {
   if (!c) return;
+  for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   for (auto& r : c->prof) {
     if (r.a) cudaEventDestroy(r.a);
     if (r.b) cudaEventDestroy(r.b);

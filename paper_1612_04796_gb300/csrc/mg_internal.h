@@ -107,6 +107,18 @@ struct mg_ctx {
     cudaEvent_t a, b;
   };
   mutable long long nlaunch = 0;
+  // CUDA graphs of recurring launch sequences (V-cycle, CG steps), keyed by
+  // kind and the two vector pointers they were captured with.
+  struct GraphEntry {
+    int kind;
+    const void* a;
+    const void* b;
+    cudaGraphExec_t exec;
+    long long kernels;
+  };
+  std::vector<GraphEntry> graphs;
+  cudaStream_t cap_stream = nullptr;
+  bool use_graphs = true;
   mutable bool prof_on = false;
   mutable std::vector<ProfRec> prof;
   mutable size_t prof_used = 0;

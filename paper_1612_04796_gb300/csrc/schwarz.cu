@@ -183,6 +183,50 @@ __global__ void k_scatter(const T* __restrict__ corr, T* __restrict__ u, int64_t
   }
 }
 
+// Same sum as k_scatter with compile-time n: one thread per DOF, the 27
+// possible covering subdomains visited in the same fixed order (-1, 0, +1 per
+// direction, x fastest) with predicates instead of per-DOF lists.
+template <typename T, int N>
+__global__ void __launch_bounds__(256) k_scatter_n(const T* __restrict__ corr, T* __restrict__ u, int64_t Ne, int nx,
+                                                   int ny, int nz, int m, int no, int accumulate) {
+  constexpr int N3 = N * N * N;
+  const int64_t m3 = (int64_t)m * m * m;
+  const int64_t total = Ne * N3;
+  for (int64_t dof = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; dof < total;
+       dof += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = dof / N3;
+    const int loc = (int)(dof - e * N3);
+    const int i = loc % N, j = (loc / N) % N, k = loc / (N * N);
+    const int ex = (int)(e % nx), ey = (int)((e / nx) % ny), ez = (int)(e / ((int64_t)nx * ny));
+    // per direction and offset o (0: subdomain to the left, 1: own, 2: to the right):
+    // covered?  position in that subdomain's line
+    const bool vx0 = i < no, vx2 = i >= N - no, vy0 = j < no, vy2 = j >= N - no, vz0 = k < no, vz2 = k >= N - no;
+    const int px[3] = {no + N + i, no + i, i - (N - no)};
+    const int py[3] = {no + N + j, no + j, j - (N - no)};
+    const int pz[3] = {no + N + k, no + k, k - (N - no)};
+    const int sxs[3] = {ex == 0 ? nx - 1 : ex - 1, ex, ex == nx - 1 ? 0 : ex + 1};
+    const int sys[3] = {ey == 0 ? ny - 1 : ey - 1, ey, ey == ny - 1 ? 0 : ey + 1};
+    const int szs[3] = {ez == 0 ? nz - 1 : ez - 1, ez, ez == nz - 1 ? 0 : ez + 1};
+    T sum = 0;
+#pragma unroll
+    for (int oz = 0; oz < 3; ++oz) {
+      if ((oz == 0 && !vz0) || (oz == 2 && !vz2)) continue;
+#pragma unroll
+      for (int oy = 0; oy < 3; ++oy) {
+        if ((oy == 0 && !vy0) || (oy == 2 && !vy2)) continue;
+        const int64_t row = nx * (sys[oy] + (int64_t)ny * szs[oz]);
+        const int pyz = m * (py[oy] + m * pz[oz]);
+#pragma unroll
+        for (int ox = 0; ox < 3; ++ox) {
+          if ((ox == 0 && !vx0) || (ox == 2 && !vx2)) continue;
+          sum += corr[(sxs[ox] + row) * m3 + px[ox] + pyz];
+        }
+      }
+    }
+    u[dof] = accumulate ? u[dof] + sum : sum;
+  }
+}
+
 template <typename T>
 const T* table_of(const mg_ctx* c);
 template <>
@@ -215,7 +259,7 @@ cudaError_t launch_fdm(const mg_ctx* c, int l, const T* r) {
   const int m2 = lv.m * lv.m;
   if ((lv.m & 1) && lv.m >= 3 && lv.m <= 35) {
     // compile-time width: several subdomains per block when m^2 is small
-    a.spb = m2 >= 128 ? 1 : 128 / m2;
+    a.spb = m2 >= 128 ? 1 : 128 / m2;  // must equal FdmShape<T, m>::spb
     int threads = a.spb * m2;
     threads = threads > 256 ? 256 : (threads + 31) / 32 * 32;
     int64_t groups = (c->Ne + a.spb - 1) / a.spb;
@@ -248,9 +292,17 @@ cudaError_t launch_scatter(const mg_ctx* c, int l, T* u, int accumulate) {
   int64_t total = lv.N;
   int64_t blocks = (total + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;
-  k_scatter<T><<<(int)blocks, 256, 0, c->stream>>>(static_cast<const T*>(c->ws.corr), u, c->Ne, c->ne[0], c->ne[1],
-                                                    c->ne[2], lv.n, lv.m, lv.no, accumulate);
+  const T* corr = static_cast<const T*>(c->ws.corr);
+  const int eb = (int)blocks;
   c->nlaunch += 1;
+  switch (lv.n) {
+#define MGDG_SC(N) case N: k_scatter_n<T, N><<<eb, 256, 0, c->stream>>>(corr, u, c->Ne, c->ne[0], c->ne[1], c->ne[2], lv.m, lv.no, accumulate); return cudaGetLastError();
+    MGDG_SC(3) MGDG_SC(5) MGDG_SC(9) MGDG_SC(17) MGDG_SC(33)
+#undef MGDG_SC
+    default: break;
+  }
+  k_scatter<T><<<(int)blocks, 256, 0, c->stream>>>(corr, u, c->Ne, c->ne[0], c->ne[1], c->ne[2], lv.n, lv.m, lv.no,
+                                                    accumulate);
   return cudaGetLastError();
 }
 

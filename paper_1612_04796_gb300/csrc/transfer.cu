@@ -4,7 +4,9 @@
 // with J (n_f x n_c) the values of the order-P_{l-1} GLL Lagrange basis at the
 // order-P_l GLL nodes (embedded interpolation).  Both are applied as three
 // one-axis contractions (sum factorisation), one output value per thread,
-// through the smoother's correction buffer as scratch.
+// through the smoother's correction buffer as scratch (order 32), or in one
+// fused kernel per element with shared-memory intermediates and even/odd
+// products (orders 2..16).
 #include "mg_internal.h"
 
 namespace mgdg {
@@ -54,6 +56,141 @@ cudaError_t contract(const mg_ctx* c, const T* in, T* out, const T* J, int d0, i
   return cudaGetLastError();
 }
 
+// Even/odd product y = A x for a centro-symmetric NO x NI matrix given as its
+// even part AE ((NO+1)/2 x (NI+1)/2) and odd part AO (NO/2 x NI/2):
+//   e_t = x_t + x_{NI-1-t}, o_t = x_t - x_{NI-1-t} (t < NI/2), e_{NI/2} = x_{NI/2} (NI odd),
+//   y_a = E_a + O_a, y_{NO-1-a} = E_a - O_a, y_{NO/2} = E_{NO/2} (NO odd).
+// The interpolation matrix J (order P_l nodes x order P_{l-1} basis) is
+// centro-symmetric because both GLL point sets are symmetric about 0.
+template <typename T, int NO, int NI>
+__device__ __forceinline__ void cs_matvec(const T* __restrict__ AE, const T* __restrict__ AO, const T (&x)[NI],
+                                          T (&y)[NO]) {
+  constexpr int hi = NI / 2, ho = NO / 2, nei = (NI + 1) / 2, neo = (NO + 1) / 2;
+  T e[nei], o[hi > 0 ? hi : 1];
+#pragma unroll
+  for (int t = 0; t < hi; ++t) {
+    e[t] = x[t] + x[NI - 1 - t];
+    o[t] = x[t] - x[NI - 1 - t];
+  }
+  if (NI & 1) e[nei - 1] = x[hi];
+#pragma unroll
+  for (int a = 0; a < neo; ++a) {
+    T E = AE[a * nei] * e[0];
+#pragma unroll
+    for (int t = 1; t < nei; ++t) E += AE[a * nei + t] * e[t];
+    if (a < ho) {
+      T O = AO[a * hi] * o[0];
+#pragma unroll
+      for (int t = 1; t < hi; ++t) O += AO[a * hi + t] * o[t];
+      y[a] = E + O;
+      y[NO - 1 - a] = E - O;
+    } else {
+      y[a] = E;
+    }
+  }
+}
+
+// Even / odd parts of the centro-symmetric matrix A (NO x NI, A[o][t] = get(o, t)).
+template <typename T, int NO, int NI, typename Get>
+__device__ void cs_split(Get get, T* AE, T* AO) {
+  constexpr int hi = NI / 2, nei = (NI + 1) / 2, neo = (NO + 1) / 2, ho = NO / 2;
+  for (int idx = threadIdx.x; idx < neo * nei; idx += blockDim.x) {
+    const int a = idx / nei, t = idx % nei;
+    AE[idx] = (t < hi) ? (T)0.5 * (get(a, t) + get(a, NI - 1 - t)) : get(a, t);
+  }
+  for (int idx = threadIdx.x; idx < ho * hi; idx += blockDim.x) {
+    const int a = idx / hi, t = idx % hi;
+    AO[idx] = (T)0.5 * (get(a, t) - get(a, NI - 1 - t));
+  }
+}
+
+// Fused prolongation u_f += (J (x) J (x) J) u_c, one element per block pass,
+// intermediates in shared memory.
+template <typename T, int NF, int NC>
+__global__ void __launch_bounds__(128) k_prolong_fused(const T* __restrict__ uc, T* __restrict__ uf,
+                                                       const T* __restrict__ J, int64_t Ne) {
+  constexpr int nei = (NC + 1) / 2, neo = (NF + 1) / 2;
+  __shared__ T sE[neo * nei], sO[(NF / 2) * (NC / 2) + 1];
+  __shared__ T sB[NF * NC * NC], sC[NF * NF * NC];
+  cs_split<T, NF, NC>([&](int o, int t) { return J[o * NC + t]; }, sE, sO);
+  __syncthreads();
+  for (int64_t e = blockIdx.x; e < Ne; e += gridDim.x) {
+    const T* x0 = uc + e * (NC * NC * NC);
+    for (int ln = threadIdx.x; ln < NC * NC; ln += blockDim.x) {  // x: (j,k) lines
+      T x[NC], y[NF];
+#pragma unroll
+      for (int t = 0; t < NC; ++t) x[t] = x0[t + NC * ln];
+      cs_matvec<T, NF, NC>(sE, sO, x, y);
+#pragma unroll
+      for (int a = 0; a < NF; ++a) sB[a + NF * ln] = y[a];
+    }
+    __syncthreads();
+    for (int ln = threadIdx.x; ln < NF * NC; ln += blockDim.x) {  // y: (a,k) lines
+      const int a = ln % NF, k = ln / NF;
+      T x[NC], y[NF];
+#pragma unroll
+      for (int t = 0; t < NC; ++t) x[t] = sB[a + NF * (t + NC * k)];
+      cs_matvec<T, NF, NC>(sE, sO, x, y);
+#pragma unroll
+      for (int b = 0; b < NF; ++b) sC[a + NF * (b + NF * k)] = y[b];
+    }
+    __syncthreads();
+    T* out = uf + e * (NF * NF * NF);
+    for (int ln = threadIdx.x; ln < NF * NF; ln += blockDim.x) {  // z: (a,b) lines, accumulate
+      T x[NC], y[NF];
+#pragma unroll
+      for (int t = 0; t < NC; ++t) x[t] = sC[ln + NF * NF * t];
+      cs_matvec<T, NF, NC>(sE, sO, x, y);
+#pragma unroll
+      for (int c = 0; c < NF; ++c) out[ln + NF * NF * c] += y[c];
+    }
+    __syncthreads();
+  }
+}
+
+// Fused restriction f_c = (J^T (x) J^T (x) J^T) r_f per element.
+template <typename T, int NF, int NC>
+__global__ void __launch_bounds__(128) k_restrict_fused(const T* __restrict__ rf, T* __restrict__ fc,
+                                                        const T* __restrict__ J, int64_t Ne) {
+  constexpr int nei = (NF + 1) / 2, neo = (NC + 1) / 2;
+  __shared__ T sE[neo * nei], sO[(NC / 2) * (NF / 2) + 1];
+  __shared__ T sB[NF * NC * NC], sC[NF * NF * NC];
+  cs_split<T, NC, NF>([&](int o, int t) { return J[t * NC + o]; }, sE, sO);
+  __syncthreads();
+  for (int64_t e = blockIdx.x; e < Ne; e += gridDim.x) {
+    const T* x0 = rf + e * (NF * NF * NF);
+    for (int ln = threadIdx.x; ln < NF * NF; ln += blockDim.x) {  // z: (a,b) lines
+      T x[NF], y[NC];
+#pragma unroll
+      for (int t = 0; t < NF; ++t) x[t] = x0[ln + NF * NF * t];
+      cs_matvec<T, NC, NF>(sE, sO, x, y);
+#pragma unroll
+      for (int k = 0; k < NC; ++k) sC[ln + NF * NF * k] = y[k];
+    }
+    __syncthreads();
+    for (int ln = threadIdx.x; ln < NF * NC; ln += blockDim.x) {  // y: (a,k) lines
+      const int a = ln % NF, k = ln / NF;
+      T x[NF], y[NC];
+#pragma unroll
+      for (int t = 0; t < NF; ++t) x[t] = sC[a + NF * (t + NF * k)];
+      cs_matvec<T, NC, NF>(sE, sO, x, y);
+#pragma unroll
+      for (int j = 0; j < NC; ++j) sB[a + NF * (j + NC * k)] = y[j];
+    }
+    __syncthreads();
+    T* out = fc + e * (NC * NC * NC);
+    for (int ln = threadIdx.x; ln < NC * NC; ln += blockDim.x) {  // x: (j,k) lines
+      T x[NF], y[NC];
+#pragma unroll
+      for (int t = 0; t < NF; ++t) x[t] = sB[t + NF * ln];
+      cs_matvec<T, NC, NF>(sE, sO, x, y);
+#pragma unroll
+      for (int i = 0; i < NC; ++i) out[i + NC * ln] = y[i];
+    }
+    __syncthreads();
+  }
+}
+
 template <typename T>
 const T* table_of(const mg_ctx* c);
 template <>
@@ -63,10 +200,20 @@ const float* table_of<float>(const mg_ctx* c) { return c->ws.tab32; }
 
 }  // namespace
 
+inline int fused_blocks(int64_t Ne) { return (int)(Ne < 152 * 12 ? Ne : 152 * 12); }
+
 template <typename T>
 cudaError_t launch_restrict(const mg_ctx* c, int l, const T* r_fine, T* f_coarse) {
   const int nf = c->lev[l].n, nc = c->lev[l - 1].n;
   const T* J = table_of<T>(c) + c->lev[l].J;
+  const int nb = fused_blocks(c->Ne);
+  switch (nf) {
+    case 3: k_restrict_fused<T, 3, 2><<<nb, 128, 0, c->stream>>>(r_fine, f_coarse, J, c->Ne); c->nlaunch += 1; return cudaGetLastError();
+    case 5: k_restrict_fused<T, 5, 3><<<nb, 128, 0, c->stream>>>(r_fine, f_coarse, J, c->Ne); c->nlaunch += 1; return cudaGetLastError();
+    case 9: k_restrict_fused<T, 9, 5><<<nb, 128, 0, c->stream>>>(r_fine, f_coarse, J, c->Ne); c->nlaunch += 1; return cudaGetLastError();
+    case 17: k_restrict_fused<T, 17, 9><<<nb, 128, 0, c->stream>>>(r_fine, f_coarse, J, c->Ne); c->nlaunch += 1; return cudaGetLastError();
+    default: break;
+  }
   T* t1 = static_cast<T*>(c->ws.corr);
   T* t2 = t1 + c->Ne * (int64_t)nf * nf * nc;
   cudaError_t e;
@@ -80,6 +227,14 @@ template <typename T>
 cudaError_t launch_prolong(const mg_ctx* c, int l, const T* u_coarse, T* u_fine) {
   const int nf = c->lev[l].n, nc = c->lev[l - 1].n;
   const T* J = table_of<T>(c) + c->lev[l].J;
+  const int nb = fused_blocks(c->Ne);
+  switch (nf) {
+    case 3: k_prolong_fused<T, 3, 2><<<nb, 128, 0, c->stream>>>(u_coarse, u_fine, J, c->Ne); c->nlaunch += 1; return cudaGetLastError();
+    case 5: k_prolong_fused<T, 5, 3><<<nb, 128, 0, c->stream>>>(u_coarse, u_fine, J, c->Ne); c->nlaunch += 1; return cudaGetLastError();
+    case 9: k_prolong_fused<T, 9, 5><<<nb, 128, 0, c->stream>>>(u_coarse, u_fine, J, c->Ne); c->nlaunch += 1; return cudaGetLastError();
+    case 17: k_prolong_fused<T, 17, 9><<<nb, 128, 0, c->stream>>>(u_coarse, u_fine, J, c->Ne); c->nlaunch += 1; return cudaGetLastError();
+    default: break;
+  }
   T* t1 = static_cast<T*>(c->ws.corr);
   T* t2 = t1 + c->Ne * (int64_t)nf * nc * nc;
   cudaError_t e;
