@@ -65,8 +65,10 @@ typedef enum {
 
 /* Transition profile of the hat-shaped weight function w_H (Fig. wH). */
 typedef enum {
-  MG_WEIGHT_QUINTIC = 0, /* 10t^3 - 15t^4 + 6t^5 */
-  MG_WEIGHT_LINEAR = 1   /* t */
+  MG_WEIGHT_QUINTIC = 0,            /* q(t) = 10t^3 - 15t^4 + 6t^5 across the whole strip */
+  MG_WEIGHT_LINEAR = 1,             /* q(t) = t */
+  MG_WEIGHT_QUINTIC_HALVES = 2,     /* a quintic step on each half of the strip, 1/2 on the interface */
+  MG_WEIGHT_QUINTIC_NORMALISED = 3  /* one-sided quintic hat normalised to sum to one */
 } mg_weight_profile;
 
 typedef struct {

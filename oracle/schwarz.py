@@ -57,9 +57,11 @@ def hat_weight(xi_h, delta, profile="quintic"):
     |xi_H| <= 1 - delta, w = 0 for |xi_H| >= 1 + delta, and
     w = 1 - q((|xi_H| - 1 + delta) / (2 delta)) in between, so w = 1/2 on the
     interface and neighbouring subdomains' weights sum to one.  ``profile``
-    selects q: "quintic" (the paper's wording) or "linear" (q(t) = t).  Both give
-    the same weights whenever only the interface node lies in the strip
-    (N_O = 1)."""
+    selects q: "quintic" (the paper's wording) or "linear" (q(t) = t); or one of
+    two other readings of a "piece-wise quintic transition": "quintic_halves"
+    (a quintic step on each half of the strip) and "quintic_normalised" (a
+    one-sided quintic hat normalised to a partition of unity).  All give the
+    same weights whenever only the interface node lies in the strip (N_O = 1)."""
     a = abs(float(xi_h))
     if delta <= 0.0:
         return 1.0 if a < 1.0 else (0.5 if a == 1.0 else 0.0)
@@ -67,6 +69,16 @@ def hat_weight(xi_h, delta, profile="quintic"):
         return 1.0
     if a >= 1.0 + delta:
         return 0.0
+    if profile == "quintic_halves":
+        # a quintic step on each half of the strip, 1/2 on the interface
+        if a <= 1.0:
+            return 1.0 - 0.5 * quintic((a - 1.0 + delta) / delta)
+        return 0.5 * (1.0 - quintic((a - 1.0) / delta))
+    if profile == "quintic_normalised":
+        # one-sided hat r (1 on the element, 1 - q(d / delta) at distance d outside),
+        # divided by the sum over the two subdomains that cover the node
+        r = 1.0 - quintic(abs(a - 1.0) / delta)
+        return 1.0 / (1.0 + r) if a <= 1.0 else r / (1.0 + r)
     t = (a - 1.0 + delta) / (2.0 * delta)
     if profile == "linear":
         return 1.0 - t

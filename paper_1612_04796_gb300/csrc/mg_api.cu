@@ -481,7 +481,7 @@ mg_status mg_setup(double lx, double ly, double lz, int nx, int ny, int nz, int 
   if (opts) o = *opts;
   if (o.ns_pre < 0 || o.ns_post < 0 || o.ns_growth < 1 || o.ns_pre + o.ns_post < 1) return MG_EINVAL;
   if (o.precision != MG_FP64 && o.precision != MG_MIXED) return MG_EINVAL;
-  if (o.weight_profile != MG_WEIGHT_QUINTIC && o.weight_profile != MG_WEIGHT_LINEAR) return MG_EINVAL;
+  if (o.weight_profile < MG_WEIGHT_QUINTIC || o.weight_profile > MG_WEIGHT_QUINTIC_NORMALISED) return MG_EINVAL;
   if (o.overlap_mode != MG_OVERLAP_LAYERS && o.overlap_mode != MG_OVERLAP_WIDTH) return MG_EINVAL;
   if (o.overlap_mode == MG_OVERLAP_WIDTH && !(o.overlap_frac >= 0.0 && o.overlap_frac <= 0.5)) return MG_EINVAL;
   if ((int64_t)nx * ny * nz > (int64_t)1 << 31) return MG_EINVAL;

@@ -219,13 +219,26 @@ __device__ bool gen_eig_centro(const double* L, const double* M, int m, double* 
   return ok;
 }
 
+__device__ double quintic_step(double t) { return t * t * t * (10.0 - 15.0 * t + 6.0 * t * t); }
+
 __device__ double hat_weight(double xi_h, double delta, int profile) {
   double a = fabs(xi_h);
   if (delta <= 0.0) return a < 1.0 ? 1.0 : (a == 1.0 ? 0.5 : 0.0);
   if (a <= 1.0 - delta) return 1.0;
   if (a >= 1.0 + delta) return 0.0;
+  if (profile == MG_WEIGHT_QUINTIC_HALVES) {
+    // a quintic step on each half of the strip, w = 1/2 on the interface
+    return a <= 1.0 ? 1.0 - 0.5 * quintic_step((a - 1.0 + delta) / delta) : 0.5 * (1.0 - quintic_step((a - 1.0) / delta));
+  }
+  if (profile == MG_WEIGHT_QUINTIC_NORMALISED) {
+    // one-sided hat r = 1 on the element, 1 - q((a - 1)/delta) in the strip,
+    // normalised by the sum over the two subdomains covering the node
+    const double d = fabs(a - 1.0);
+    const double r = 1.0 - quintic_step(d / delta);
+    return a <= 1.0 ? 1.0 / (1.0 + r) : r / (1.0 + r);
+  }
   double tt = (a - 1.0 + delta) / (2.0 * delta);
-  double q = (profile == MG_WEIGHT_LINEAR) ? tt : tt * tt * tt * (10.0 - 15.0 * tt + 6.0 * tt * tt);
+  double q = (profile == MG_WEIGHT_LINEAR) ? tt : quintic_step(tt);
   return 1.0 - q;
 }
 

@@ -13,7 +13,7 @@ from ._lib import MgOpts, load_library
 
 PRECISION = {"fp64": 0, "mixed": 1}
 OVERLAP_MODE = {"layers": 0, "width": 1}
-PROFILE = {"quintic": 0, "linear": 1}
+PROFILE = {"quintic": 0, "linear": 1, "quintic_halves": 2, "quintic_normalised": 3}
 
 
 class MGError(RuntimeError):

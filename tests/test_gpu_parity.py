@@ -167,7 +167,7 @@ def test_smooth_fp64(solver_cache, P, overlap):
     assert rel_err(host(u1t) - u1, ref2) < FP64_TOL
 
 
-@pytest.mark.parametrize("profile", ["quintic", "linear"])
+@pytest.mark.parametrize("profile", ["quintic", "linear", "quintic_halves", "quintic_normalised"])
 def test_smooth_width_overlap(solver_cache, profile):
     """delta_O = 0.08 dx at P = 8: N_O = 2, weights from the transition profile."""
     lengths, counts, P = (1.0, 1.0, 1.0), (3, 3, 4), 8

@@ -32,7 +32,7 @@ def test_quintic_and_hat_properties():
     t = np.linspace(0, 1, 101)
     np.testing.assert_allclose(quintic(t) + quintic(1 - t), 1.0, atol=1e-15)
     assert quintic(0.0) == 0.0 and quintic(1.0) == 1.0
-    for prof in ("quintic", "linear"):
+    for prof in ("quintic", "linear", "quintic_halves", "quintic_normalised"):
         for delta in (0.05, 0.16, 0.5, 1.0):
             assert hat_weight(1.0, delta, prof) == pytest.approx(0.5)
             assert hat_weight(-1.0, delta, prof) == pytest.approx(0.5)
@@ -44,7 +44,7 @@ def test_quintic_and_hat_properties():
 
 @pytest.mark.parametrize("P", [2, 4, 8])
 @pytest.mark.parametrize("n_o", [0, 1, 2, 3, 5])
-@pytest.mark.parametrize("profile", ["quintic", "linear"])
+@pytest.mark.parametrize("profile", ["quintic", "linear", "quintic_halves", "quintic_normalised"])
 def test_partition_of_unity_node_layers(P, n_o, profile):
     """sum_s R_s^T W_s R_s 1 = 1 (the weighted corrections average, Eq. correction:global)."""
     n_o = min(n_o, max_layers(P))
