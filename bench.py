@@ -44,6 +44,29 @@ WORKLOAD = {
     "solver": "MG V(1,1)",
     "seed": 2,
 }
+# Other configurations (same timing code; `--workload NAME`).  The default
+# bench line is WORKLOAD above (c2).
+WORKLOADS = {
+    "c1": dict(workload="periodic unit cube, 4^3 elements, P=4 (8,000 DOFs), manufactured sines "
+                        "(f = 12 pi^2 sin 2pi x sin 2pi y sin 2pi z), standalone V(1,1) MG, N_O=1, FP64, tol 1e-10",
+               lengths=[1.0, 1.0, 1.0], elements=[4, 4, 4], P=4, overlap_layers=1, rhs="sines", precision="fp64",
+               use_cg=False),
+    "c2": dict(WORKLOAD, rhs="gaussian", precision="fp64", use_cg=False),
+    "c3": dict(workload="periodic box [0,48]x[0,1]x[0,1], 48x8x8 elements, P=16 (15,092,736 DOFs), N_O node layers, "
+                        "zero-mean Gaussian f (seed 3), FP32 V(1,1) preconditioner inside FP64 inexact PCG, tol 1e-10",
+               lengths=[48.0, 1.0, 1.0], elements=[48, 8, 8], P=16, overlap_layers=1, rhs="gaussian", seed=3,
+               precision="mixed", use_cg=True),
+    "c3ar48": dict(workload="periodic box [0,48]x[0,24]x[0,1], 8^3 elements (aspect 48:24:1), P=16 (2,515,456 DOFs), "
+                            "N_O node layers, zero-mean Gaussian f (seed 3), FP32 V(1,1) in FP64 PCG, tol 1e-10",
+                   lengths=[48.0, 24.0, 1.0], elements=[8, 8, 8], P=16, overlap_layers=1, rhs="gaussian", seed=3,
+                   precision="mixed", use_cg=True),
+    "c4": dict(workload="periodic unit cube, 4^3 elements, P=32 (2,299,968 DOFs), f = 8 random Fourier modes "
+                        "(|k|_inf <= 8, seed 4), FP32 V(1,1) preconditioner (CUDA-core FDM) in FP64 PCG, N_O=1, tol 1e-10",
+               lengths=[1.0, 1.0, 1.0], elements=[4, 4, 4], P=32, overlap_layers=1, rhs="fourier", seed=4,
+               precision="mixed", use_cg=True),
+}
+FP32_FLOP_PER_CLK_PER_SM = 256    # 128 FP32 FMA lanes per SM
+
 # bounded sample of the workload for the CPU oracle (same P, overlap, tol; smaller mesh)
 ORACLE_SAMPLE = {"elements": [6, 6, 6], "P": 8}
 FLUSH_BYTES = 256 << 20
@@ -59,11 +82,31 @@ def parse_args():
     ap.add_argument("--impl", default="mg", choices=["mg", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip e2e / mixed / roofline legs")
+    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
+    ap.add_argument("--overlap", type=int, default=None, help="override N_O of the workload")
     return ap.parse_args()
 
 
 def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def reduce_max(x, device=None):
+    """Max of a float over all ranks of the default process group (identity
+    without one); device = the tensor device the backend needs."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_scaling_value(world, dofs_per_rank, steps, max_seconds):
+    """Whole-job DOF/s: every rank solves its own replica; the job time is the
+    slowest rank's."""
+    return world * dofs_per_rank * steps / max_seconds
 
 
 def peaks():
@@ -220,11 +263,7 @@ def run_mg(args):
         torch.cuda.synchronize()
 
     def max_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_max(x, dev)
 
     pkg.load_library()
     W = WORKLOAD
@@ -265,7 +304,7 @@ def run_mg(args):
     launches = s.kernel_launches() - launches0
     clock_info = clocks.stop()
     total_s = max_over_ranks(sum(step_ms) / 1e3)
-    value = world * N * args.steps / total_s
+    value = weak_scaling_value(world, N, args.steps, total_s)
     # per-kernel device times: the same steps again with CUDA events around
     # every kernel group (eager launches instead of graph replays)
     s.profile(True)
@@ -357,10 +396,97 @@ def run_mg(args):
         dist.destroy_process_group()
 
 
+def run_workload(args):
+    """One configuration other than the default line: DOF/s of full solves,
+    per-kernel device times, fine-level smoother roofline."""
+    import torch
+
+    import paper_1612_04796_gb300 as pkg
+    from paper_1612_04796_gb300 import inputs
+
+    W = dict(WORKLOADS[args.workload])
+    if args.overlap is not None:
+        W["overlap_layers"] = args.overlap
+    dev = torch.device("cuda", torch.cuda.current_device())
+    pkg.load_library()
+    s = pkg.MGSolver(W["lengths"], W["elements"], W["P"], overlap=W["overlap_layers"], precision=W["precision"],
+                     device=dev)
+    s64 = s if W["precision"] == "fp64" else pkg.MGSolver(W["lengths"], W["elements"], W["P"],
+                                                          overlap=W["overlap_layers"], device=dev)
+    N = s.num_dofs()
+    x, y, z = (t.cpu().numpy() for t in s.node_coords())
+    if W["rhs"] == "sines":
+        f = inputs.sines(x, y, z, W["lengths"])[1]
+    elif W["rhs"] == "fourier":
+        f = inputs.eval_fourier(inputs.fourier_modes(W["seed"]), x, y, z, W["lengths"])
+    else:
+        f = inputs.gaussian(N, W.get("seed", 2))
+    b = s.rhs(torch.tensor(f, device=dev))
+    u = torch.zeros(N, dtype=torch.float64, device=dev)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def steps(k):
+        ms, its = [], []
+        for step in range(k):
+            flush.fill_(step & 0xFF)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            u.zero_()
+            _, it, _, _ = s.solve(b, u, tol=1e-10, maxit=200, use_cg=W["use_cg"])
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            its.append(it)
+        return ms, its
+
+    steps(args.warmup)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    l0 = s.kernel_launches()
+    ms, its = steps(args.steps)
+    launches = s.kernel_launches() - l0
+    clock_info = clocks.stop()
+    s.profile(True)
+    prof_ms, _ = steps(args.steps)
+    s.profile(False)
+    true_rel = float(torch.linalg.norm(s64.residual(u, b)) / torch.linalg.norm(b))
+    lev = s.L
+    m = s.P + 1 + 2 * s.layers(lev)
+    Ne = int(np.prod(W["elements"]))
+    fdm_ms, fdm_n = s.profile_result("fdm", lev)
+    algo = Ne * (12.0 * m ** 4 + m ** 3)
+    pk, _ = peaks()
+    clk = float(pk.get("sm_max_mhz", 2070.0)) * 1e6
+    fp64 = W["precision"] == "fp64"
+    peak = NUM_SMS * (FP64_FLOP_PER_CLK_PER_SM if fp64 else FP32_FLOP_PER_CLK_PER_SM) * clk
+    ach = algo / (fdm_ms / fdm_n / 1e3) if fdm_n else None
+    line = {
+        "metric": METRIC, "value": N * args.steps / (sum(ms) / 1e3), "unit": "DOF/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": sum(ms) / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if fp64 else "f32 multigrid / f64 outer",
+        "data": "synthetic",
+        "config": dict(W, dofs=N, iterations=int(statistics.median(its)), name=args.workload,
+                       true_relres=true_rel, l2="flushed (256 MiB write) between steps"),
+        "gpu_launches": launches, "clocks": clock_info,
+        "roofline": {"kernel": "fine-level smoother (m=%d)" % m, "bound": "alu", "unit": "TFLOP/s",
+                     "achieved": ach / 1e12 if ach else None, "peak": peak / 1e12,
+                     "frac": ach / peak if ach else None, "traffic": None,
+                     "avg_launch_ms": fdm_ms / fdm_n if fdm_n else None,
+                     "time_share_of_step": profile_shares(s, sum(prof_ms)),
+                     "ms_per_step_by_kernel_level": profile_levels(s, args.steps)},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload != "c2":
+        run_workload(args)
     else:
         run_mg(args)
 

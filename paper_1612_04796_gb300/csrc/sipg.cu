@@ -250,6 +250,74 @@ __global__ void __launch_bounds__(256) k_sipg_n(OpArgs<T> a) {
   }
 }
 
+// Direction-split variant for meshes with few elements: one launch per
+// direction, each element's lines spread over `chunks` blocks.
+template <typename T, int N>
+__global__ void __launch_bounds__(256) k_sipg_dir(OpArgs<T> a, int dir, int chunks) {
+  constexpr int n2 = N * N, n3 = n2 * N;
+  const T* m3 = a.tab + a.mass3;
+  const int64_t nblk = a.Ne * chunks;
+  for (int64_t bi = blockIdx.x; bi < nblk; bi += gridDim.x) {
+    const int64_t e = bi / chunks;
+    const int ln = (int)(bi % chunks) * blockDim.x + threadIdx.x;
+    if (ln >= n2) continue;
+    const int p = ln % N, q = ln / N;
+    const int ex = (int)(e % a.nx), ey = (int)((e / a.nx) % a.ny), ez = (int)(e / ((int64_t)a.nx * a.ny));
+    int64_t eL, eR;
+    int base, st;
+    if (dir == 0) {
+      eL = (ex == 0 ? a.nx - 1 : ex - 1) + a.nx * (ey + (int64_t)a.ny * ez);
+      eR = (ex == a.nx - 1 ? 0 : ex + 1) + a.nx * (ey + (int64_t)a.ny * ez);
+      base = N * (p + N * q);
+      st = 1;
+    } else if (dir == 1) {
+      eL = ex + a.nx * ((ey == 0 ? a.ny - 1 : ey - 1) + (int64_t)a.ny * ez);
+      eR = ex + a.nx * ((ey == a.ny - 1 ? 0 : ey + 1) + (int64_t)a.ny * ez);
+      base = p + n2 * q;
+      st = N;
+    } else {
+      eL = ex + a.nx * (ey + (int64_t)a.ny * (ez == 0 ? a.nz - 1 : ez - 1));
+      eR = ex + a.nx * (ey + (int64_t)a.ny * (ez == a.nz - 1 ? 0 : ez + 1));
+      base = p + N * q;
+      st = n2;
+    }
+    const int64_t off = e * n3 + base;
+    line_apply_n<T, N>(a, dir, a.u + off, a.u + eL * n3 + base, a.u + eR * n3 + base, st, a.out + off,
+                       a.residual ? a.f + off : nullptr, m3 + base, dir);
+  }
+}
+
+template <typename T, int N>
+cudaError_t launch_sipg_n(const mg_ctx* c, OpArgs<T>& a) {
+  constexpr int n2 = N * N;
+  // lines per element and direction spread evenly over <= 256 threads
+  const int iters = (n2 + 255) / 256;
+  if (iters > 1 || c->Ne < 2 * 152) {
+    const int chunks = (n2 + 255) / 256;
+    const int threads = ((n2 + chunks - 1) / chunks + 31) / 32 * 32;
+    if (c->Ne * chunks < 4 * 152 || iters > 1) {
+      const int64_t nblk = c->Ne * chunks;
+      const int blocks = (int)(nblk < 152 * 16 ? nblk : 152 * 16);
+      for (int dir = 0; dir < 3; ++dir) {
+        k_sipg_dir<T, N><<<blocks, threads, 0, c->stream>>>(a, dir, chunks);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+      }
+      c->nlaunch += 3;
+      return cudaSuccess;
+    }
+  }
+  a.epb = n2 >= 128 ? 1 : 128 / n2;
+  int threads = a.epb * n2;
+  threads = (threads + 31) / 32 * 32;
+  if (threads > 256) threads = 256;
+  int64_t groups = (c->Ne + a.epb - 1) / a.epb;
+  int64_t blocks = groups < 152 * 16 ? groups : 152 * 16;
+  k_sipg_n<T, N><<<(int)blocks, threads, 0, c->stream>>>(a);
+  c->nlaunch += 1;
+  return cudaGetLastError();
+}
+
 template <typename T>
 const T* table_of(const mg_ctx* c);
 template <>
@@ -290,16 +358,17 @@ cudaError_t launch_sipg(const mg_ctx* c, int l, const T* u, const T* f, T* out, 
   if (threads > 256) threads = 256;
   int64_t groups = (c->Ne + a.epb - 1) / a.epb;
   int64_t blocks = groups < 152 * 16 ? groups : 152 * 16;
-  c->nlaunch += 1;
   switch (lv.n) {
-    case 2: k_sipg_n<T, 2><<<(int)blocks, threads, 0, c->stream>>>(a); break;
-    case 3: k_sipg_n<T, 3><<<(int)blocks, threads, 0, c->stream>>>(a); break;
-    case 5: k_sipg_n<T, 5><<<(int)blocks, threads, 0, c->stream>>>(a); break;
-    case 9: k_sipg_n<T, 9><<<(int)blocks, threads, 0, c->stream>>>(a); break;
-    case 17: k_sipg_n<T, 17><<<(int)blocks, threads, 0, c->stream>>>(a); break;
-    case 33: k_sipg_n<T, 33><<<(int)blocks, threads, 0, c->stream>>>(a); break;
-    default: k_sipg<T><<<(int)blocks, threads, 0, c->stream>>>(a); break;
+    case 2: return launch_sipg_n<T, 2>(c, a);
+    case 3: return launch_sipg_n<T, 3>(c, a);
+    case 5: return launch_sipg_n<T, 5>(c, a);
+    case 9: return launch_sipg_n<T, 9>(c, a);
+    case 17: return launch_sipg_n<T, 17>(c, a);
+    case 33: return launch_sipg_n<T, 33>(c, a);
+    default: break;
   }
+  c->nlaunch += 1;
+  k_sipg<T><<<(int)blocks, threads, 0, c->stream>>>(a);
   return cudaGetLastError();
 }
 
