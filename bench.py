@@ -65,6 +65,10 @@ WORKLOADS = {
                lengths=[1.0, 1.0, 1.0], elements=[4, 4, 4], P=32, overlap_layers=1, rhs="fourier", seed=4,
                precision="mixed", use_cg=True),
 }
+WORKLOADS["c5"] = dict(workload="serving stream: 512 solve requests, Poisson arrivals at 200/s (seed 5), periodic box "
+                                "[0,AR]x[0,1]x[0,1], AR ~ U[1,8], n^3 elements with n in {4,8,16,24,32}, P in {2,4,8,16}, "
+                                "N_O=1, Gaussian f, FP32 V(1,1) in FP64 PCG, tol 1e-10, admitted by HBM footprint, "
+                                "one context and stream per slot")
 FP32_FLOP_PER_CLK_PER_SM = 256    # 128 FP32 FMA lanes per SM
 
 # bounded sample of the workload for the CPU oracle (same P, overlap, tol; smaller mesh)
@@ -481,10 +485,49 @@ def run_workload(args):
     print(json.dumps(line), flush=True)
 
 
+def run_serving(args):
+    """The serving stream: throughput (DOFs solved / makespan) and per-request
+    latency (arrival to result on the host) percentiles."""
+    import torch
+
+    from paper_1612_04796_gb300.serving import Server, latency_summary, request_stream
+    n_req = int(os.environ.get("MG_SERVING_REQUESTS", "512"))
+    reqs = request_stream(seed=5, n_requests=n_req)
+    srv = Server(slots=8, keep_solution=False)
+    # warm-up: one small request of every order (module loading, first captures)
+    warm = [r for r in request_stream(seed=6, n_requests=64, sizes=(4,)) if True][:8]
+    srv.serve(warm, realtime=False)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(srv.device.index)
+    clocks.start()
+    t0 = time.perf_counter()
+    res = srv.serve(reqs, realtime=True)
+    torch.cuda.synchronize()
+    makespan = time.perf_counter() - t0
+    clock_info = clocks.stop()
+    ok = [r for r, q in zip(res, reqs) if r.error is None]
+    dofs = sum(q.dofs for r, q in zip(res, reqs) if r.error is None)
+    summ = latency_summary(res)
+    line = {
+        "metric": METRIC, "value": dofs / makespan, "unit": "DOF/s", "n_gpus": 1, "steps": 1, "warmup": 1,
+        "ms_per_step": makespan * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 multigrid / f64 outer", "data": "synthetic",
+        "config": dict(WORKLOADS["c5"], name="c5", requests=len(reqs), slots=8,
+                       hbm_budget_gb=srv.scheduler.budget / 1e9, total_dofs=dofs),
+        "latency": summ, "max_concurrent": srv.max_active,
+        "iterations": {"median": float(np.median([r.iterations for r in ok])),
+                       "max": int(max(r.iterations for r in ok))},
+        "max_relres": float(max(r.relres for r in ok)), "clocks": clock_info,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "c5":
+        run_serving(args)
     elif args.workload != "c2":
         run_workload(args)
     else:
