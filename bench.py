@@ -67,7 +67,8 @@ WORKLOADS = {
 }
 WORKLOADS["c5"] = dict(workload="serving stream: 512 solve requests, Poisson arrivals at 200/s (seed 5), periodic box "
                                 "[0,AR]x[0,1]x[0,1], AR ~ U[1,8], n^3 elements with n in {4,8,16,24,32}, P in {2,4,8,16}, "
-                                "N_O=1, Gaussian f, FP32 V(1,1) in FP64 PCG, tol 1e-10, admitted by HBM footprint, "
+                                "N_O=4 (default; --overlap), Gaussian f, FP32 V(1,1) in FP64 PCG, tol 1e-10, "
+                                "admitted by HBM footprint, "
                                 "one context and stream per slot")
 FP32_FLOP_PER_CLK_PER_SM = 256    # 128 FP32 FMA lanes per SM
 
@@ -492,8 +493,10 @@ def run_serving(args):
 
     from paper_1612_04796_gb300.serving import Server, latency_summary, request_stream
     n_req = int(os.environ.get("MG_SERVING_REQUESTS", "512"))
-    reqs = request_stream(seed=5, n_requests=n_req)
-    srv = Server(slots=8, keep_solution=False)
+    overlap = 4 if args.overlap is None else args.overlap
+    slots = int(os.environ.get("MG_SERVING_SLOTS", "8"))
+    reqs = request_stream(seed=5, n_requests=n_req, overlap=overlap)
+    srv = Server(slots=slots, keep_solution=False)
     # warm-up: one small request of every order (module loading, first captures)
     warm = [r for r in request_stream(seed=6, n_requests=64, sizes=(4,)) if True][:8]
     srv.serve(warm, realtime=False)
@@ -512,7 +515,7 @@ def run_serving(args):
         "metric": METRIC, "value": dofs / makespan, "unit": "DOF/s", "n_gpus": 1, "steps": 1, "warmup": 1,
         "ms_per_step": makespan * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32 multigrid / f64 outer", "data": "synthetic",
-        "config": dict(WORKLOADS["c5"], name="c5", requests=len(reqs), slots=8,
+        "config": dict(WORKLOADS["c5"], name="c5", requests=len(reqs), slots=slots, overlap_layers=overlap,
                        hbm_budget_gb=srv.scheduler.budget / 1e9, total_dofs=dofs),
         "latency": summ, "max_concurrent": srv.max_active,
         "iterations": {"median": float(np.median([r.iterations for r in ok])),

@@ -127,13 +127,14 @@ class Scheduler:
 
 
 def request_stream(seed=5, n_requests=512, rate=200.0, sizes=(4, 8, 16, 24, 32), orders=(2, 4, 8, 16),
-                   aspect=(1.0, 8.0)):
+                   aspect=(1.0, 8.0), overlap=1):
     """The serving workload: Poisson arrivals, box [0, AR] x [0, 1] x [0, 1]
     with n^3 elements, order P, Gaussian right-hand side from a per-request
-    seed."""
+    seed; `overlap` = N_O node layers of every request's smoother."""
     reqs = []
     for i, d in enumerate(inputs.request_stream(seed, n_requests, rate, sizes, orders, aspect)):
-        reqs.append(Request(i, (d["aspect"], 1.0, 1.0), (d["n"],) * 3, d["P"], d["seed"], d["arrival"]))
+        reqs.append(Request(i, (d["aspect"], 1.0, 1.0), (d["n"],) * 3, d["P"], d["seed"], d["arrival"],
+                            overlap=overlap))
     return reqs
 
 
