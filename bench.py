@@ -177,6 +177,21 @@ class ClockSampler:
                 "samples": len(sm), "power_w_max": max(power)}
 
 
+def measured_traffic():
+    """DRAM bytes per launch of the fine-level smoother from the committed ncu
+    capture, or None if the kernel source changed since it was taken."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "fdm_fp64_16x16x16_p8_m11.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        rec = json.load(fh)
+    with open(os.path.join(ROOT, rec["source"]), "rb") as fh:
+        if hashlib.sha256(fh.read()).hexdigest() != rec["source_sha256"]:
+            return None
+    return rec["dram_bytes_read"] + rec["dram_bytes_write"]
+
+
 def profile_shares(s, total_ms):
     out = {}
     for kind in s.PROFILE_KINDS:
@@ -330,7 +345,8 @@ def run_mg(args):
     roofline = {
         "kernel": "k_fdm<double> (fine-level gather + fast diagonalisation)",
         "bound": "alu", "achieved": achieved / 1e12 if achieved else None, "peak": fp64_peak / 1e12,
-        "unit": "TFLOP/s", "frac": (achieved / fp64_peak) if achieved else None, "traffic": None,
+        "unit": "TFLOP/s", "frac": (achieved / fp64_peak) if achieved else None, "traffic": measured_traffic(),
+        "traffic_source": "profiles/fdm_fp64_16x16x16_p8_m11.md (ncu dram__bytes_read+write of one launch)",
         "algorithmic_flop_per_launch": algo_flop, "launches_timed": fdm_n,
         "avg_launch_ms": fdm_ms / fdm_n if fdm_n else None,
         "peak_basis": "FP64 pipe: %d SMs x %d flop/clk x %.0f MHz (derived; %s peaks file has no FP64 entry)"

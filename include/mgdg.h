@@ -166,7 +166,9 @@ mg_status mg_vcycle(mg_ctx* ctx, double* u, const double* f);
  * preconditioned CG with one V-cycle from zero as preconditioner (MG-CG,
  * Section 3.2).  With MG_MIXED the V-cycle runs in FP32.  iters, relres (host)
  * receive the iteration count and final relative residual; history (host, may be
- * NULL) receives maxit+1 residual norms.  Returns MG_ENOCONV if maxit is reached.
+ * NULL) receives maxit+1 residual norms.  Returns MG_ENOCONV if maxit is reached
+ * or the residual becomes non-finite, MG_EINVAL if the initial residual is not
+ * finite (NaN or Inf in u or f).
  */
 mg_status mg_solve(mg_ctx* ctx, double* u, const double* f, double tol, int maxit, int use_cg, int* iters,
                    double* relres, double* history);

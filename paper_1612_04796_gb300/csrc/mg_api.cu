@@ -7,6 +7,8 @@
 // preconditioned CG (MG-CG, Section 3.2); residual norms are Euclidean
 // (Section 4).
 #include <math.h>
+
+#include <cmath>
 #include <stdio.h>
 #include <string.h>
 
@@ -361,6 +363,7 @@ mg_status solve_impl(mg_ctx* c, double* u, const double* f, double tol, int maxi
     CK(err);
     r0 = rn = sqrt(rr);
     if (history) history[0] = r0;
+    if (!std::isfinite(r0)) return fail(c, MG_EINVAL, "initial residual is not finite (NaN or Inf in u or f)");
     converged = r0 == 0.0;
     while (!converged && it < maxit) {
       ++it;
@@ -384,6 +387,7 @@ mg_status solve_impl(mg_ctx* c, double* u, const double* f, double tol, int maxi
       CK(err);
       rn = sqrt(v);
       if (history) history[it] = rn;
+      if (!std::isfinite(rn)) return fail(c, MG_ENOCONV, "residual became non-finite");
       if (rn <= tol * r0) converged = true;
     }
   } else {
@@ -400,6 +404,7 @@ mg_status solve_impl(mg_ctx* c, double* u, const double* f, double tol, int maxi
     CK(err);
     r0 = rn = sqrt(rr);
     if (history) history[0] = r0;
+    if (!std::isfinite(r0)) return fail(c, MG_EINVAL, "initial residual is not finite (NaN or Inf in u or f)");
     converged = r0 == 0.0;
     if (!converged) {
       CK(precond(c, r, z));
@@ -427,6 +432,7 @@ mg_status solve_impl(mg_ctx* c, double* u, const double* f, double tol, int maxi
       CK(err);
       rn = sqrt(v);
       if (history) history[it] = rn;
+      if (!std::isfinite(rn)) return fail(c, MG_ENOCONV, "residual became non-finite");
       if (rn <= tol * r0) {
         converged = true;
         break;
