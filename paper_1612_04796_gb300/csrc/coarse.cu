@@ -45,9 +45,10 @@ __global__ void k_coarse_axis(const double* __restrict__ in, double* __restrict_
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
     int g[3];
-    g[0] = (int)(idx % Nx);
-    g[1] = (int)((idx / Nx) % Ny);
-    g[2] = (int)(idx / ((int64_t)Nx * Ny));
+    const int i32 = (int)idx, gyz = i32 / Nx;  // coarse sizes fit in 32 bits
+    g[0] = i32 - gyz * Nx;
+    g[1] = gyz % Ny;
+    g[2] = gyz / Ny;
     const int o = g[axis];
     double acc = 0.0;
     for (int t = 0; t < Na; ++t) {

@@ -110,7 +110,8 @@ __global__ void __launch_bounds__(256) k_fdm_m(FdmArgs<T> a) {
       const int64_t s = s0 + ln / M2;
       if (s >= a.Ne) continue;
       const int l2 = ln % M2, b = l2 % M, c = l2 / M;
-      const int sx = (int)(s % a.nx), sy = (int)((s / a.nx) % a.ny), sz = (int)(s / ((int64_t)a.nx * a.ny));
+      const int s32 = (int)s, sxy = s32 / a.nx;  // element indices fit in 32 bits
+      const int sx = s32 - sxy * a.nx, sy = sxy % a.ny, sz = sxy / a.ny;
       int dy, iy, dz, iz;
       fdm_sub_node(b, n, no, &dy, &iy);
       fdm_sub_node(c, n, no, &dz, &iz);

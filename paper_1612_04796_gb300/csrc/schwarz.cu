@@ -194,10 +194,11 @@ __global__ void __launch_bounds__(256) k_scatter_n(const T* __restrict__ corr, T
   const int64_t total = Ne * N3;
   for (int64_t dof = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; dof < total;
        dof += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t e = dof / N3;
-    const int loc = (int)(dof - e * N3);
+    const int e = (int)(dof / N3);  // element indices fit in 32 bits
+    const int loc = (int)(dof - (int64_t)e * N3);
     const int i = loc % N, j = (loc / N) % N, k = loc / (N * N);
-    const int ex = (int)(e % nx), ey = (int)((e / nx) % ny), ez = (int)(e / ((int64_t)nx * ny));
+    const int exy = e / nx;
+    const int ex = e - exy * nx, ey = exy % ny, ez = exy / ny;
     // per direction and offset o (0: subdomain to the left, 1: own, 2: to the right):
     // covered?  position in that subdomain's line
     const bool vx0 = i < no, vx2 = i >= N - no, vy0 = j < no, vy2 = j >= N - no, vz0 = k < no, vz2 = k >= N - no;

@@ -113,7 +113,8 @@ __global__ void __launch_bounds__(256) k_sipg(OpArgs<T> a) {
         const int64_t e = e0 + ln / n2;
         if (e >= a.Ne) continue;
         const int l2 = ln % n2, p = l2 % n, q = l2 / n;
-        const int ex = (int)(e % a.nx), ey = (int)((e / a.nx) % a.ny), ez = (int)(e / ((int64_t)a.nx * a.ny));
+        const int e32 = (int)e, exy = e32 / a.nx;  // element indices fit in 32 bits
+        const int ex = e32 - exy * a.nx, ey = exy % a.ny, ez = exy / a.ny;
         int64_t eL, eR;
         int base, st;
         if (dir == 0) {
@@ -222,7 +223,8 @@ __global__ void __launch_bounds__(256) k_sipg_n(OpArgs<T> a) {
         const int64_t e = e0 + ln / n2;
         if (e >= a.Ne) continue;
         const int l2 = ln % n2, p = l2 % N, q = l2 / N;
-        const int ex = (int)(e % a.nx), ey = (int)((e / a.nx) % a.ny), ez = (int)(e / ((int64_t)a.nx * a.ny));
+        const int e32 = (int)e, exy = e32 / a.nx;  // element indices fit in 32 bits
+        const int ex = e32 - exy * a.nx, ey = exy % a.ny, ez = exy / a.ny;
         int64_t eL, eR;
         int base, st;
         if (dir == 0) {
@@ -262,7 +264,8 @@ __global__ void __launch_bounds__(256) k_sipg_dir(OpArgs<T> a, int dir, int chun
     const int ln = (int)(bi % chunks) * blockDim.x + threadIdx.x;
     if (ln >= n2) continue;
     const int p = ln % N, q = ln / N;
-    const int ex = (int)(e % a.nx), ey = (int)((e / a.nx) % a.ny), ez = (int)(e / ((int64_t)a.nx * a.ny));
+    const int e32 = (int)e, exy = e32 / a.nx;  // element indices fit in 32 bits
+    const int ex = e32 - exy * a.nx, ey = exy % a.ny, ez = exy / a.ny;
     int64_t eL, eR;
     int base, st;
     if (dir == 0) {
