@@ -18,7 +18,7 @@ import scipy.sparse as sp
 import scipy.sparse.linalg as spl
 
 from .gll import gll_nodes, lagrange_eval
-from .schwarz import SchwarzSmoother, layer_delta, layers_from_width, max_layers
+from .schwarz import SchwarzSmoother, layer_delta, layers_from_width, max_layers, max_width_layers
 from .sipg import assemble
 
 
@@ -46,18 +46,31 @@ def level_layers(P_l, n_o=None, delta_rel=None):
     return min(int(n_o), max_layers(P_l))
 
 
+def max_overlap_widths(mesh, frac):
+    """The "max" overlap of Table 2: delta_O,i = min(max_j frac dx_j, dx_i), as a
+    reference half-width 2 delta_O,i / dx_i per direction (<= 2)."""
+    big = frac * max(mesh.h)
+    return tuple(2.0 * min(big, mesh.h[d]) / mesh.h[d] for d in range(3))
+
+
 class Level:
-    def __init__(self, mesh, P_l, factor, n_o=None, delta_rel=None, smoother=True, profile="quintic"):
+    def __init__(self, mesh, P_l, factor, n_o=None, delta_rel=None, smoother=True, profile="quintic",
+                 max_frac=None):
         self.P = P_l
         self.A = assemble(mesh, P_l, factor)
         self.N = self.A.shape[0]
         self.smoother = None
         if smoother:
-            self.n_o = level_layers(P_l, n_o, delta_rel)
-            if delta_rel is not None:
-                delta = min(2.0 * delta_rel, 1.0)
+            if max_frac is not None:
+                deltas = max_overlap_widths(mesh, max_frac)
+                self.n_o = tuple(max_width_layers(P_l, d) for d in deltas)
+                delta = deltas
             else:
-                delta = layer_delta(P_l, self.n_o)
+                self.n_o = level_layers(P_l, n_o, delta_rel)
+                if delta_rel is not None:
+                    delta = min(2.0 * delta_rel, 1.0)
+                else:
+                    delta = layer_delta(P_l, self.n_o)
             self.delta = delta
             self.smoother = SchwarzSmoother(self.A, mesh, P_l, self.n_o, delta, profile)
 
@@ -65,14 +78,14 @@ class Level:
 class Hierarchy:
     """All levels of the polynomial multigrid method for one mesh and order P."""
 
-    def __init__(self, mesh, P, factor=2.0, n_o=1, delta_rel=None, profile="quintic"):
+    def __init__(self, mesh, P, factor=2.0, n_o=1, delta_rel=None, profile="quintic", max_frac=None):
         L = int(round(math.log2(P)))
         if 2 ** L != P:
             raise ValueError("P must be a power of two")
         self.mesh = mesh
         self.L = L
-        self.levels = [Level(mesh, 2 ** l, factor, n_o, delta_rel, smoother=(l >= 1), profile=profile)
-                       for l in range(L + 1)]
+        self.levels = [Level(mesh, 2 ** l, factor, n_o, delta_rel, smoother=(l >= 1), profile=profile,
+                             max_frac=max_frac) for l in range(L + 1)]
         self.I3 = [None] + [interpolation_matrix(2 ** (l - 1), 2 ** l) for l in range(1, L + 1)]
         self.Ne = mesh.num_elements
 

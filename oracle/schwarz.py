@@ -22,6 +22,13 @@ import scipy.sparse.linalg as spl
 from .gll import gll_nodes
 
 
+def max_width_layers(P, delta_ref):
+    """N_O for a strip of reference half-width delta_ref that may reach the
+    whole neighbour element (delta_ref <= 2): all neighbour nodes within it."""
+    xi = gll_nodes(P)
+    return int(np.sum(1.0 + xi <= delta_ref + 1e-12))
+
+
 def max_layers(P):
     """Largest admissible N_O at order P: floor(P/2) + 1, the layer count of
     delta_O = dx/2, the widest overlap the paper uses (Table 1, rows 5-6).
@@ -132,21 +139,57 @@ def subdomain_1d(P, n_o, delta, profile="quintic"):
     return np.array(de), np.array(ii), np.array(w)
 
 
+def normalised_subdomain_1d(P, n_o, delta, profile="quintic"):
+    """subdomain_1d with each weight divided by the sum of the raw weights of
+    all subdomains that cover the node (up to three when the strip is wider
+    than half an element, as in the "max" overlap of Table 2).  For a strip
+    half-width delta <= 1 (reference units) the raw weights of the two
+    covering subdomains already sum to one and are returned unchanged.
+
+    Reading (the paper only says the overlap may reach the whole neighbour
+    element): a node of an element at reference coordinate xi is seen by the
+    subdomain centred o elements away (o = -1, 0, +1) at xi_H = xi - 2 o, and is
+    covered by it if it lies in that subdomain's strip."""
+    xi = gll_nodes(P)
+    n = P + 1
+    de, ii, w = subdomain_1d(P, n_o, delta, profile)
+    if delta <= 1.0:
+        return de, ii, w
+
+    def raw(x):
+        return 1.0 if n_o == 0 else hat_weight(x, delta, profile)
+
+    out = np.empty_like(w)
+    for a in range(len(de)):
+        i = ii[a]
+        total = raw(xi[i])                      # own element (o = 0)
+        if i >= n - n_o:                        # in the left strip of the subdomain to the right
+            total += raw(xi[i] - 2.0)
+        if i < n_o:                             # in the right strip of the subdomain to the left
+            total += raw(xi[i] + 2.0)
+        out[a] = w[a] / total if total > 0 else 0.0
+    return de, ii, out
+
+
 def subdomain_indices(mesh, P, n_o, delta, profile="quintic"):
-    """Global indices (Ns x m^3, subdomain node (a, b, c) at a + m (b + m c))
-    and the weights W_s = W_z (x) W_y (x) W_x (length m^3) of all subdomains."""
+    """Global indices (Ns x mx my mz, subdomain node (a, b, c) at a + mx (b + my c))
+    and the weights W_s = W_z (x) W_y (x) W_x of all subdomains.  n_o and delta
+    may be given per direction (tuples of three)."""
     n = P + 1
     B = n ** 3
-    dx, ix, wx = subdomain_1d(P, n_o, delta, profile)
-    m = len(dx)
-    c, b, a = np.meshgrid(np.arange(m), np.arange(m), np.arange(m), indexing="ij")
+    n_os = tuple(n_o) if np.ndim(n_o) else (n_o,) * 3
+    deltas = tuple(delta) if np.ndim(delta) else (delta,) * 3
+    lines = [normalised_subdomain_1d(P, n_os[d], deltas[d], profile) for d in range(3)]
+    (dx, ix, wx), (dy, iy, wy), (dz, iz, wz) = lines
+    mx, my, mz = len(dx), len(dy), len(dz)
+    c, b, a = np.meshgrid(np.arange(mz), np.arange(my), np.arange(mx), indexing="ij")
     a, b, c = a.ravel(), b.ravel(), c.ravel()
     ex, ey, ez = mesh.element_coords()
-    el = mesh.element(ex[:, None] + dx[a][None, :], ey[:, None] + dx[b][None, :],
-                      ez[:, None] + dx[c][None, :])
-    local = ix[a] + n * (ix[b] + n * ix[c])
+    el = mesh.element(ex[:, None] + dx[a][None, :], ey[:, None] + dy[b][None, :],
+                      ez[:, None] + dz[c][None, :])
+    local = ix[a] + n * (iy[b] + n * iz[c])
     idx = el * B + local[None, :]
-    W = wx[a] * wx[b] * wx[c]
+    W = wx[a] * wy[b] * wz[c]
     return idx, W
 
 

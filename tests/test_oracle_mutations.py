@@ -7,6 +7,7 @@ import pytest
 
 import oracle.schwarz as schwarz
 import oracle.sipg as sipg
+import test_oracle_max_overlap as tmax
 import test_oracle_mg as tmg
 import test_oracle_schwarz as tsch
 import test_oracle_sipg as tsipg
@@ -65,3 +66,30 @@ def test_dropped_volume_direction_is_caught(monkeypatch):
     monkeypatch.setattr(sipg, "volume_matrix", bad)
     with pytest.raises(AssertionError):
         tsipg.test_kronecker_form_eq_A(2)
+
+
+def _normalise_two_sided_only(P, n_o, delta, profile="quintic"):
+    # wrong: the subdomain to the left (whose right strip may also cover the
+    # node once the strip is wider than half an element) is left out of the sum
+    de, ii, w = schwarz.subdomain_1d(P, n_o, delta, profile)
+    if delta <= 1.0:
+        return de, ii, w
+    xi = schwarz.gll_nodes(P)
+    n = P + 1
+    out = np.empty_like(w)
+    for a in range(len(de)):
+        i = ii[a]
+        total = schwarz.hat_weight(xi[i], delta, profile)
+        if i >= n - n_o:
+            total += schwarz.hat_weight(xi[i] - 2.0, delta, profile)
+        out[a] = w[a] / total
+    return de, ii, out
+
+
+@pytest.mark.parametrize("bad", [_normalise_two_sided_only,
+                                 lambda P, n_o, delta, profile="quintic": schwarz.subdomain_1d(P, n_o, delta, profile)],
+                         ids=["two_sided", "unnormalised"])
+def test_wrong_max_overlap_normalisation_is_caught(monkeypatch, bad):
+    monkeypatch.setattr(schwarz, "normalised_subdomain_1d", bad)
+    with pytest.raises(AssertionError):
+        tmax.test_partition_of_unity_max_overlap(4, 48, "quintic")
