@@ -60,7 +60,11 @@ typedef enum {
 /* How the subdomain overlap is given (Section 3.1, Table 1). */
 typedef enum {
   MG_OVERLAP_LAYERS = 0, /* N_O node layers (argument `overlap` of mg_setup) */
-  MG_OVERLAP_WIDTH = 1   /* delta_O = overlap_frac * dx on every level (Table 1 rows 3-6) */
+  MG_OVERLAP_WIDTH = 1,  /* delta_O,i = overlap_frac * dx_i on every level (Table 1 rows 3-6;
+                            the "rel" overlap of Table 2) */
+  MG_OVERLAP_MAX = 2     /* delta_O,i = min(overlap_frac * max_j dx_j, dx_i): the "max" overlap
+                            of Table 2 for anisotropic meshes; the strip may cover the whole
+                            neighbour element, and every direction has its own N_O */
 } mg_overlap_mode;
 
 /* Transition profile of the hat-shaped weight function w_H (Fig. wH). */
@@ -73,7 +77,8 @@ typedef enum {
 
 typedef struct {
   int overlap_mode;      /* mg_overlap_mode, default MG_OVERLAP_LAYERS */
-  double overlap_frac;   /* delta_O / dx for MG_OVERLAP_WIDTH (paper: 0.08, 0.5) */
+  double overlap_frac;   /* delta_O / dx for MG_OVERLAP_WIDTH (0 .. 0.5; paper: 0.08, 0.5),
+                            delta_O / max_j dx_j for MG_OVERLAP_MAX (0 .. 1; paper: 0.08) */
   int weight_profile;    /* mg_weight_profile, default MG_WEIGHT_QUINTIC */
   int ns_pre, ns_post;   /* smoothing steps N_s1, N_s2 on the fine level (default 1, 1) */
   int ns_growth;         /* N_s,l = N_s * ns_growth^(L-l): 1 fixed V-cycle, 3 variable (Table 2) */
@@ -95,6 +100,11 @@ void mg_default_opts(mg_opts* o);
  *                coercivity threshold of the form; the paper's choice is 2
  *   overlap      N_O node layers (>= 0) for MG_OVERLAP_LAYERS; clamped on
  *                each level to floor(P_l/2) + 1; ignored for MG_OVERLAP_WIDTH
+ *                and MG_OVERLAP_MAX
+ * With MG_OVERLAP_MAX a direction whose strip covers the whole neighbour
+ * element (N_O = P_l + 1) needs at least 4 elements, so that the two strips of
+ * a subdomain are not coupled through the periodic boundary: MG_EINVAL
+ * otherwise.
  *   opts         NULL for defaults
  *   out          receives the new context (host memory owned by the library;
  *                release with mg_destroy)
@@ -115,10 +125,14 @@ mg_status mg_workspace_size(const mg_ctx* ctx, size_t* bytes);
  */
 mg_status mg_bind_workspace(mg_ctx* ctx, void* dptr, size_t bytes);
 
-/* Number of levels L+1, DOFs and overlap layers of a level (host, no CUDA). */
+/* Number of levels L+1, DOFs and overlap layers of a level (host, no CUDA).
+ * mg_level_layers gives N_O of the x direction; mg_level_layers_dir that of
+ * direction dir (0 x, 1 y, 2 z), which differ only with MG_OVERLAP_MAX.
+ * -1 for a bad level or direction. */
 int mg_num_levels(const mg_ctx* ctx);
 long long mg_num_dofs(const mg_ctx* ctx, int level);
 int mg_level_layers(const mg_ctx* ctx, int level);
+int mg_level_layers_dir(const mg_ctx* ctx, int level, int dir);
 
 /* Physical coordinates of the nodes of `level` into x, y, z (device, N_l each). */
 mg_status mg_node_coords(mg_ctx* ctx, int level, double* x, double* y, double* z);
@@ -192,7 +206,8 @@ mg_status mg_vcycle_f32(mg_ctx* ctx, float* u, const float* f);
  *   5 eigenvectors S (m*m, S[a*m + p] = entry a of eigenvector p)
  *   6 weights w (m)       7 interpolation J_l (n * n_c, row-major; level >= 1)
  *   8 coarse eigenvalues (2 n_d; level 0)  9 coarse eigenvectors (4 n_d^2; level 0)
- * *count receives the number of values; fails with MG_EINVAL if capacity is too small.
+ * (m = n + 2 N_O of direction dir.)  *count receives the number of values;
+ * fails with MG_EINVAL if capacity is too small.
  */
 mg_status mg_get_table(mg_ctx* ctx, int level, int dir, int what, double* host_out, int capacity, int* count);
 

@@ -39,6 +39,7 @@ SIGNATURES = {
     "mg_num_levels": (_I, [_P]),
     "mg_num_dofs": (_LL, [_P, _I]),
     "mg_level_layers": (_I, [_P, _I]),
+    "mg_level_layers_dir": (_I, [_P, _I, _I]),
     "mg_node_coords": (_S, [_P, _I, _P, _P, _P]),
     "mg_rhs": (_S, [_P, _P, _P]),
     "mg_apply_sipg": (_S, [_P, _I, _P, _P]),

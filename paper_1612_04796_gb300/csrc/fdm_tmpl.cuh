@@ -15,7 +15,9 @@ struct FdmArgs {
   const T* r;
   T* corr;
   int64_t Ne;
-  int nx, ny, nz, n, m, no, spb;
+  int nx, ny, nz, n, m, no, spb;  // m, no: cubic subdomains (compile-time kernel)
+  int md[3], nod[3];              // per-direction width and layers (run-time kernel)
+  int s_in_smem;                  // run-time kernel: 1D factors staged in shared memory
   int64_t S[3], SW[3], dinv;
 };
 

@@ -121,7 +121,7 @@ Layout make_layout(const mg_ctx* c) {
     ly.lev_u[l] = take(lv.N * sizeof(double));
     ly.lev_f[l] = take(lv.N * sizeof(double));
     ly.lev_r[l] = take(lv.N * sizeof(double));
-    if (l >= 1) corr = std::max<int64_t>(corr, c->Ne * (int64_t)lv.m * lv.m * lv.m);
+    if (l >= 1) corr = std::max<int64_t>(corr, c->Ne * (int64_t)lv.m[0] * lv.m[1] * lv.m[2]);
   }
   corr = std::max<int64_t>(corr, 2 * c->lev[c->L].N);
   ly.corr = take(corr * sizeof(double));
@@ -135,7 +135,8 @@ Layout make_layout(const mg_ctx* c) {
   ly.scal = take(kNumSlots * sizeof(double));
   ly.status = take(256);
   int nmax = 8;
-  for (int l = 1; l <= c->L; ++l) nmax = std::max(nmax, c->lev[l].m);
+  for (int l = 1; l <= c->L; ++l)
+    for (int d = 0; d < 3; ++d) nmax = std::max(nmax, c->lev[l].m[d]);
   for (int d = 0; d < 3; ++d) nmax = std::max(nmax, c->Ng[d]);
   int64_t per_block = 4 * (int64_t)nmax * nmax + 4 * nmax + 64;
   ly.jac_count = per_block * 3 * (c->L + 1);
@@ -488,8 +489,10 @@ mg_status mg_setup(double lx, double ly, double lz, int nx, int ny, int nz, int 
   if (o.ns_pre < 0 || o.ns_post < 0 || o.ns_growth < 1 || o.ns_pre + o.ns_post < 1) return MG_EINVAL;
   if (o.precision != MG_FP64 && o.precision != MG_MIXED) return MG_EINVAL;
   if (o.weight_profile < MG_WEIGHT_QUINTIC || o.weight_profile > MG_WEIGHT_QUINTIC_NORMALISED) return MG_EINVAL;
-  if (o.overlap_mode != MG_OVERLAP_LAYERS && o.overlap_mode != MG_OVERLAP_WIDTH) return MG_EINVAL;
+  if (o.overlap_mode != MG_OVERLAP_LAYERS && o.overlap_mode != MG_OVERLAP_WIDTH && o.overlap_mode != MG_OVERLAP_MAX)
+    return MG_EINVAL;
   if (o.overlap_mode == MG_OVERLAP_WIDTH && !(o.overlap_frac >= 0.0 && o.overlap_frac <= 0.5)) return MG_EINVAL;
+  if (o.overlap_mode == MG_OVERLAP_MAX && !(o.overlap_frac >= 0.0 && o.overlap_frac <= 1.0)) return MG_EINVAL;
   if ((int64_t)nx * ny * nz > (int64_t)1 << 31) return MG_EINVAL;
   mg_ctx* c = new (std::nothrow) mg_ctx();
   if (!c) return MG_ENOMEM;
@@ -520,17 +523,32 @@ mg_status mg_setup(double lx, double ly, double lz, int nx, int ny, int nz, int 
     lv.P = 1 << l;
     lv.n = lv.P + 1;
     lv.N = c->Ne * (int64_t)lv.n * lv.n * lv.n;
-    if (l >= 1) {
-      int maxno = lv.P / 2 + 1;
-      int no = (o.overlap_mode == MG_OVERLAP_LAYERS) ? overlap : layers_from_width(lv.P, o.overlap_frac);
-      lv.no = std::min(no, maxno);
-      lv.m = lv.n + 2 * lv.no;
-      lv.delta = (o.overlap_mode == MG_OVERLAP_LAYERS) ? layer_delta(lv.P, lv.no)
-                                                       : std::min(2.0 * o.overlap_frac, 1.0);
-    } else {
-      lv.no = 0;
-      lv.m = 0;
-      lv.delta = 0.0;
+    const double hmax = std::max(std::max(lx / nx, ly / ny), lz / nz);
+    for (int d = 0; d < 3; ++d) {
+      if (l == 0) {
+        lv.no[d] = 0;
+        lv.m[d] = 0;
+        lv.delta[d] = 0.0;
+        continue;
+      }
+      if (o.overlap_mode == MG_OVERLAP_MAX) {
+        // strip of width min(frac max_j dx_j, dx_d): up to the whole neighbour element
+        const double h = c->len[d] / c->ne[d];
+        const double rel = std::min(o.overlap_frac * hmax, h) / h;
+        lv.no[d] = layers_from_width(lv.P, rel);
+        lv.delta[d] = 2.0 * rel;
+        if (lv.no[d] == lv.n && c->ne[d] < 4) {
+          delete c;
+          return MG_EINVAL;
+        }
+      } else {
+        const int maxno = lv.P / 2 + 1;
+        const int no = (o.overlap_mode == MG_OVERLAP_LAYERS) ? overlap : layers_from_width(lv.P, o.overlap_frac);
+        lv.no[d] = std::min(no, maxno);
+        lv.delta[d] = (o.overlap_mode == MG_OVERLAP_LAYERS) ? layer_delta(lv.P, lv.no[d])
+                                                            : std::min(2.0 * o.overlap_frac, 1.0);
+      }
+      lv.m[d] = lv.n + 2 * lv.no[d];
     }
     for (int d = 0; d < 3; ++d) {
       lv.h[d] = c->len[d] / c->ne[d];
@@ -549,10 +567,10 @@ mg_status mg_setup(double lx, double ly, double lz, int nx, int ny, int nz, int 
       t.fo = tab(lv.n / 2 + 1);
       t.fsc = tab(2);
       if (l >= 1) {
-        t.S = tab((int64_t)lv.m * lv.m);
-        t.SW = tab((int64_t)lv.m * lv.m);
-        t.lam = tab(lv.m);
-        t.w = tab(lv.m);
+        t.S = tab((int64_t)lv.m[d] * lv.m[d]);
+        t.SW = tab((int64_t)lv.m[d] * lv.m[d]);
+        t.lam = tab(lv.m[d]);
+        t.w = tab(lv.m[d]);
         t.Q = t.qlam = -1;
       } else {
         t.S = t.SW = t.lam = t.w = -1;
@@ -560,7 +578,7 @@ mg_status mg_setup(double lx, double ly, double lz, int nx, int ny, int nz, int 
         t.qlam = tab(c->Ng[d]);
       }
     }
-    lv.dinv = (l >= 1) ? tab((int64_t)lv.m * lv.m * lv.m) : -1;
+    lv.dinv = (l >= 1) ? tab((int64_t)lv.m[0] * lv.m[1] * lv.m[2]) : -1;
     lv.mass3 = tab((int64_t)lv.n * lv.n * lv.n);
     lv.J = (l >= 1) ? tab((int64_t)lv.n * (c->lev[l - 1].n)) : -1;
     lv.u = lv.f = lv.r = nullptr;
@@ -630,9 +648,11 @@ long long mg_num_dofs(const mg_ctx* c, int level) {
   return c->lev[level].N;
 }
 
-int mg_level_layers(const mg_ctx* c, int level) {
-  if (!c || level < 0 || level > c->L) return -1;
-  return c->lev[level].no;
+int mg_level_layers(const mg_ctx* c, int level) { return mg_level_layers_dir(c, level, 0); }
+
+int mg_level_layers_dir(const mg_ctx* c, int level, int dir) {
+  if (!c || level < 0 || level > c->L || dir < 0 || dir > 2) return -1;
+  return c->lev[level].no[dir];
 }
 
 mg_status mg_node_coords(mg_ctx* c, int level, double* x, double* y, double* z) {
@@ -774,7 +794,7 @@ mg_status mg_get_table(mg_ctx* c, int level, int dir, int what, double* host_out
   const LevelInfo& lv = c->lev[level];
   const DirTables& t = lv.t[dir];
   int64_t off = -1, cnt = 0;
-  const int n = lv.n, m = lv.m, Ng = c->Ng[dir];
+  const int n = lv.n, m = lv.m[dir], Ng = c->Ng[dir];
   switch (what) {
     case 0: off = t.nodes; cnt = n; break;
     case 1: off = t.weights; cnt = n; break;

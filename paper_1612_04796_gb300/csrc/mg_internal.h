@@ -15,7 +15,7 @@ namespace mgdg {
 constexpr int kMaxLevels = 6;   // P <= 32
 constexpr int kMaxP = 32;
 constexpr int kMaxN = kMaxP + 1;        // nodes per element and direction
-constexpr int kMaxM = kMaxN + 2 * (kMaxP / 2 + 1);  // widest subdomain line
+constexpr int kMaxM = 3 * kMaxN;         // widest subdomain line (strips of whole neighbour elements)
 constexpr int kRedBlocks = 304;         // fixed grid of the two-stage reductions (2 per SM)
 
 // Slots of the device scalar array ws.scal.
@@ -49,12 +49,13 @@ struct DirTables {
 };
 
 struct LevelInfo {
-  int P, n, m, no;       // order, nodes per direction, subdomain width, overlap layers
-  double delta;          // hat-weight half-width (reference units)
+  int P, n;              // order, nodes per direction
+  int m[3], no[3];       // subdomain width and overlap layers per direction
+  double delta[3];       // hat-weight half-width per direction (reference units, <= 2)
   int64_t N;             // DOFs
   double h[3], g[3], mu[3];
   DirTables t[3];
-  int64_t dinv;          // m^3: 1 / (lam_x[a] + lam_y[b] + lam_z[c])
+  int64_t dinv;          // m_x m_y m_z: 1 / (lam_x[a] + lam_y[b] + lam_z[c])
   int64_t mass3;         // n^3: mass_x[i] mass_y[j] mass_z[k]
   int64_t J;             // n * n_c interpolation from level l-1 (level >= 1)
   // device vectors (bytes sized for FP64; FP32 code uses the first half)
@@ -69,7 +70,7 @@ struct Workspace {
   double* tab64 = nullptr;
   float* tab32 = nullptr;
   int64_t tab_count = 0;
-  void* corr = nullptr;        // smoother corrections, Ne * m^3 (largest level)
+  void* corr = nullptr;        // smoother corrections, Ne * m_x m_y m_z (largest level)
   double* coarse_a = nullptr;  // coarse FDM scratch, N_0 each
   double* coarse_b = nullptr;
   double* coarse_f = nullptr;  // FP64 coarse rhs / solution for the FP32 hierarchy

@@ -12,6 +12,8 @@
 // output DOF: every DOF sums the <= 8 (<= 27 at the widest overlap) subdomain
 // values that cover it in a fixed order, so the result is deterministic and
 // no atomics are needed.
+#include <algorithm>
+
 #include "fdm_tmpl.cuh"
 
 namespace mgdg {
@@ -74,100 +76,126 @@ __device__ __forceinline__ void bwd_eo(const T* v, const T* __restrict__ SW, int
   }
 }
 
+// Run-time widths m_x, m_y, m_z (subdomains need not be cubic: with the "max"
+// overlap of Table 2 every direction has its own N_O).  The tile of subdomain s
+// is stored at corr + s m_x m_y m_z, node (a, b, c) at a + m_x (b + m_y c).
+// The six 1D factors are staged in shared memory when they fit, else read
+// through the cache from the table array.
 template <typename T>
 __global__ void __launch_bounds__(256) k_fdm(FdmArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   T* sm = reinterpret_cast<T*>(smraw);
-  const int m = a.m, m2 = m * m, m3 = m2 * m, n = a.n, n3 = n * n * n, no = a.no;
-  T* sS = sm;              // 3 m^2
-  T* sSW = sS + 3 * m2;    // 3 m^2
-  for (int i = threadIdx.x; i < m2; i += blockDim.x) {
+  const int mx = a.md[0], my = a.md[1], mz = a.md[2], mxy = mx * my, mxyz = mxy * mz;
+  const int n = a.n, n3 = n * n * n, nox = a.nod[0], noy = a.nod[1], noz = a.nod[2];
+  const T* S[3];
+  const T* SW[3];
+  if (a.s_in_smem) {
+    T* p = sm;
     for (int d = 0; d < 3; ++d) {
-      sS[d * m2 + i] = a.tab[a.S[d] + i];
-      sSW[d * m2 + i] = a.tab[a.SW[d] + i];
+      const int md2 = a.md[d] * a.md[d];
+      for (int i = threadIdx.x; i < md2; i += blockDim.x) {
+        p[i] = a.tab[a.S[d] + i];
+        p[md2 + i] = a.tab[a.SW[d] + i];
+      }
+      S[d] = p;
+      SW[d] = p + md2;
+      p += 2 * md2;
+    }
+    __syncthreads();
+  } else {
+    for (int d = 0; d < 3; ++d) {
+      S[d] = a.tab + a.S[d];
+      SW[d] = a.tab + a.SW[d];
     }
   }
-  __syncthreads();
   const T* __restrict__ dinv = a.tab + a.dinv;
   T x[kMaxM], v[kMaxM];
   for (int64_t s = blockIdx.x; s < a.Ne; s += gridDim.x) {
-    const int sx = (int)(s % a.nx), sy = (int)((s / a.nx) % a.ny), sz = (int)(s / ((int64_t)a.nx * a.ny));
-    T* tile = a.corr + s * (int64_t)m3;
+    const int s32 = (int)s, sxy = s32 / a.nx;
+    const int sx = s32 - sxy * a.nx, sy = sxy % a.ny, sz = sxy / a.ny;
+    T* tile = a.corr + s * (int64_t)mxyz;
     const int64_t exl = wrap(sx - 1, a.nx), exr = wrap(sx + 1, a.nx);
     // pass 1: gather the x-lines of r_s = R_s r and transform them (forward, x)
-    for (int ln = threadIdx.x; ln < m2; ln += blockDim.x) {
-      const int b = ln % m, c = ln / m;
+    for (int ln = threadIdx.x; ln < my * mz; ln += blockDim.x) {
+      const int b = ln % my, c = ln / my;
       int dy, iy, dz, iz;
-      sub_node(b, n, no, &dy, &iy);
-      sub_node(c, n, no, &dz, &iz);
+      sub_node(b, n, noy, &dy, &iy);
+      sub_node(c, n, noz, &dz, &iz);
       const int64_t row = a.nx * (wrap(sy + dy, a.ny) + (int64_t)a.ny * wrap(sz + dz, a.nz));
       const int loc = n * (iy + n * iz);
       const T* rl = a.r + (exl + row) * n3 + loc;
       const T* rc = a.r + (sx + row) * n3 + loc;
       const T* rr = a.r + (exr + row) * n3 + loc;
-      for (int t = 0; t < no; ++t) x[t] = rl[n - no + t];
-      for (int t = 0; t < n; ++t) x[no + t] = rc[t];
-      for (int t = 0; t < no; ++t) x[no + n + t] = rr[t];
-      fwd_eo(x, sS, m, tile + m * ln, 1);
+      for (int t = 0; t < nox; ++t) x[t] = rl[n - nox + t];
+      for (int t = 0; t < n; ++t) x[nox + t] = rc[t];
+      for (int t = 0; t < nox; ++t) x[nox + n + t] = rr[t];
+      fwd_eo(x, S[0], mx, tile + mx * ln, 1);
     }
     __syncthreads();
     // pass 2: forward, y
-    for (int ln = threadIdx.x; ln < m2; ln += blockDim.x) {
-      const int ia = ln % m, c = ln / m;
-      T* line = tile + ia + m2 * c;
-      for (int t = 0; t < m; ++t) x[t] = line[t * m];
-      fwd_eo(x, sS + m2, m, line, m);
+    for (int ln = threadIdx.x; ln < mx * mz; ln += blockDim.x) {
+      const int ia = ln % mx, c = ln / mx;
+      T* line = tile + ia + mxy * c;
+      for (int t = 0; t < my; ++t) x[t] = line[t * mx];
+      fwd_eo(x, S[1], my, line, mx);
     }
     __syncthreads();
     // pass 3: forward z, divide by lam_x + lam_y + lam_z, backward z
-    for (int ln = threadIdx.x; ln < m2; ln += blockDim.x) {
+    for (int ln = threadIdx.x; ln < mxy; ln += blockDim.x) {
       T* line = tile + ln;
-      for (int t = 0; t < m; ++t) x[t] = line[t * m2];
-      fwd_eo(x, sS + 2 * m2, m, v, 1);
-      for (int t = 0; t < m; ++t) v[t] *= dinv[ln + t * m2];
-      bwd_eo(v, sSW + 2 * m2, m, line, m2);
+      for (int t = 0; t < mz; ++t) x[t] = line[t * mxy];
+      fwd_eo(x, S[2], mz, v, 1);
+      for (int t = 0; t < mz; ++t) v[t] *= dinv[ln + t * mxy];
+      bwd_eo(v, SW[2], mz, line, mxy);
     }
     __syncthreads();
     // pass 4: backward, y
-    for (int ln = threadIdx.x; ln < m2; ln += blockDim.x) {
-      const int ia = ln % m, c = ln / m;
-      T* line = tile + ia + m2 * c;
-      for (int t = 0; t < m; ++t) v[t] = line[t * m];
-      bwd_eo(v, sSW + m2, m, line, m);
+    for (int ln = threadIdx.x; ln < mx * mz; ln += blockDim.x) {
+      const int ia = ln % mx, c = ln / mx;
+      T* line = tile + ia + mxy * c;
+      for (int t = 0; t < my; ++t) v[t] = line[t * mx];
+      bwd_eo(v, SW[1], my, line, mx);
     }
     __syncthreads();
     // pass 5: backward, x (weights folded into SW)
-    for (int ln = threadIdx.x; ln < m2; ln += blockDim.x) {
-      T* line = tile + m * ln;
-      for (int t = 0; t < m; ++t) v[t] = line[t];
-      bwd_eo(v, sSW, m, line, 1);
+    for (int ln = threadIdx.x; ln < my * mz; ln += blockDim.x) {
+      T* line = tile + mx * ln;
+      for (int t = 0; t < mx; ++t) v[t] = line[t];
+      bwd_eo(v, SW[0], mx, line, 1);
     }
     __syncthreads();
   }
 }
 
+// Subdomain geometry of the scatter: widths and layers per direction.
+struct SubShape {
+  int mx, my, mz, nox, noy, noz;
+};
+
 template <typename T>
 __global__ void k_scatter(const T* __restrict__ corr, T* __restrict__ u, int64_t Ne, int nx, int ny, int nz, int n,
-                          int m, int no, int accumulate) {
-  const int n3 = n * n * n, m2 = m * m, m3 = m2 * m;
+                          SubShape g, int accumulate) {
+  const int n3 = n * n * n;
+  const int64_t mxyz = (int64_t)g.mx * g.my * g.mz;
   const int64_t total = Ne * n3;
   for (int64_t dof = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; dof < total;
        dof += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t e = dof / n3;
-    const int loc = (int)(dof - e * n3);
+    const int e = (int)(dof / n3);
+    const int loc = (int)(dof - (int64_t)e * n3);
     const int i = loc % n, j = (loc / n) % n, k = loc / (n * n);
-    const int ex = (int)(e % nx), ey = (int)((e / nx) % ny), ez = (int)(e / ((int64_t)nx * ny));
+    const int exy = e / nx;
+    const int ex = e - exy * nx, ey = exy % ny, ez = exy / ny;
     // per direction: covering subdomains (offset, position), fixed order -1, 0, +1
     int ox[3], px[3], cx = 0, oy[3], py[3], cy = 0, oz[3], pz[3], cz = 0;
-    if (i < no) { ox[cx] = -1; px[cx++] = no + n + i; }
-    ox[cx] = 0; px[cx++] = no + i;
-    if (i >= n - no) { ox[cx] = 1; px[cx++] = i - (n - no); }
-    if (j < no) { oy[cy] = -1; py[cy++] = no + n + j; }
-    oy[cy] = 0; py[cy++] = no + j;
-    if (j >= n - no) { oy[cy] = 1; py[cy++] = j - (n - no); }
-    if (k < no) { oz[cz] = -1; pz[cz++] = no + n + k; }
-    oz[cz] = 0; pz[cz++] = no + k;
-    if (k >= n - no) { oz[cz] = 1; pz[cz++] = k - (n - no); }
+    if (i < g.nox) { ox[cx] = -1; px[cx++] = g.nox + n + i; }
+    ox[cx] = 0; px[cx++] = g.nox + i;
+    if (i >= n - g.nox) { ox[cx] = 1; px[cx++] = i - (n - g.nox); }
+    if (j < g.noy) { oy[cy] = -1; py[cy++] = g.noy + n + j; }
+    oy[cy] = 0; py[cy++] = g.noy + j;
+    if (j >= n - g.noy) { oy[cy] = 1; py[cy++] = j - (n - g.noy); }
+    if (k < g.noz) { oz[cz] = -1; pz[cz++] = g.noz + n + k; }
+    oz[cz] = 0; pz[cz++] = g.noz + k;
+    if (k >= n - g.noz) { oz[cz] = 1; pz[cz++] = k - (n - g.noz); }
     T sum = 0;
     for (int c = 0; c < cz; ++c) {
       const int64_t zz = wrap(ez + oz[c], nz);
@@ -175,7 +203,7 @@ __global__ void k_scatter(const T* __restrict__ corr, T* __restrict__ u, int64_t
         const int64_t yy = wrap(ey + oy[b], ny);
         for (int q = 0; q < cx; ++q) {
           const int64_t s = wrap(ex + ox[q], nx) + nx * (yy + ny * zz);
-          sum += corr[s * m3 + px[q] + m * (py[b] + m * pz[c])];
+          sum += corr[s * mxyz + px[q] + g.mx * (py[b] + g.my * pz[c])];
         }
       }
     }
@@ -188,9 +216,9 @@ __global__ void k_scatter(const T* __restrict__ corr, T* __restrict__ u, int64_t
 // direction, x fastest) with predicates instead of per-DOF lists.
 template <typename T, int N>
 __global__ void __launch_bounds__(256) k_scatter_n(const T* __restrict__ corr, T* __restrict__ u, int64_t Ne, int nx,
-                                                   int ny, int nz, int m, int no, int accumulate) {
+                                                   int ny, int nz, SubShape g, int accumulate) {
   constexpr int N3 = N * N * N;
-  const int64_t m3 = (int64_t)m * m * m;
+  const int64_t mxyz = (int64_t)g.mx * g.my * g.mz;
   const int64_t total = Ne * N3;
   for (int64_t dof = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; dof < total;
        dof += (int64_t)gridDim.x * blockDim.x) {
@@ -201,10 +229,11 @@ __global__ void __launch_bounds__(256) k_scatter_n(const T* __restrict__ corr, T
     const int ex = e - exy * nx, ey = exy % ny, ez = exy / ny;
     // per direction and offset o (0: subdomain to the left, 1: own, 2: to the right):
     // covered?  position in that subdomain's line
-    const bool vx0 = i < no, vx2 = i >= N - no, vy0 = j < no, vy2 = j >= N - no, vz0 = k < no, vz2 = k >= N - no;
-    const int px[3] = {no + N + i, no + i, i - (N - no)};
-    const int py[3] = {no + N + j, no + j, j - (N - no)};
-    const int pz[3] = {no + N + k, no + k, k - (N - no)};
+    const bool vx0 = i < g.nox, vx2 = i >= N - g.nox, vy0 = j < g.noy, vy2 = j >= N - g.noy, vz0 = k < g.noz,
+               vz2 = k >= N - g.noz;
+    const int px[3] = {g.nox + N + i, g.nox + i, i - (N - g.nox)};
+    const int py[3] = {g.noy + N + j, g.noy + j, j - (N - g.noy)};
+    const int pz[3] = {g.noz + N + k, g.noz + k, k - (N - g.noz)};
     const int sxs[3] = {ex == 0 ? nx - 1 : ex - 1, ex, ex == nx - 1 ? 0 : ex + 1};
     const int sys[3] = {ey == 0 ? ny - 1 : ey - 1, ey, ey == ny - 1 ? 0 : ey + 1};
     const int szs[3] = {ez == 0 ? nz - 1 : ez - 1, ez, ez == nz - 1 ? 0 : ez + 1};
@@ -216,11 +245,11 @@ __global__ void __launch_bounds__(256) k_scatter_n(const T* __restrict__ corr, T
       for (int oy = 0; oy < 3; ++oy) {
         if ((oy == 0 && !vy0) || (oy == 2 && !vy2)) continue;
         const int64_t row = nx * (sys[oy] + (int64_t)ny * szs[oz]);
-        const int pyz = m * (py[oy] + m * pz[oz]);
+        const int pyz = g.mx * (py[oy] + g.my * pz[oz]);
 #pragma unroll
         for (int ox = 0; ox < 3; ++ox) {
           if ((ox == 0 && !vx0) || (ox == 2 && !vx2)) continue;
-          sum += corr[(sxs[ox] + row) * m3 + px[ox] + pyz];
+          sum += corr[(sxs[ox] + row) * mxyz + px[ox] + pyz];
         }
       }
     }
@@ -249,24 +278,28 @@ cudaError_t launch_fdm(const mg_ctx* c, int l, const T* r) {
   a.ny = c->ne[1];
   a.nz = c->ne[2];
   a.n = lv.n;
-  a.m = lv.m;
-  a.no = lv.no;
+  a.m = lv.m[0];
+  a.no = lv.no[0];
   for (int d = 0; d < 3; ++d) {
+    a.md[d] = lv.m[d];
+    a.nod[d] = lv.no[d];
     a.S[d] = lv.t[d].S;
     a.SW[d] = lv.t[d].SW;
   }
   a.dinv = lv.dinv;
-  size_t smem = sizeof(T) * 6 * lv.m * lv.m;
-  const int m2 = lv.m * lv.m;
-  if ((lv.m & 1) && lv.m >= 3 && lv.m <= 35) {
+  const bool cubic = lv.m[0] == lv.m[1] && lv.m[0] == lv.m[2];
+  const int m = lv.m[0], m2 = m * m;
+  if (cubic && (m & 1) && m >= 3 && m <= 35) {
     // compile-time width: several subdomains per block when m^2 is small
+    const size_t smem = sizeof(T) * 6 * m2;
     a.spb = m2 >= 128 ? 1 : 128 / m2;  // must equal FdmShape<T, m>::spb
+    a.s_in_smem = 1;
     int threads = a.spb * m2;
     threads = threads > 256 ? 256 : (threads + 31) / 32 * 32;
     int64_t groups = (c->Ne + a.spb - 1) / a.spb;
     int blocks = (int)(groups < 152 * 8 ? groups : 152 * 8);
     c->nlaunch += 1;
-    switch (lv.m) {
+    switch (m) {
 #define MGDG_CASE(M) case M: return launch_fdm_m<T, M>(a, blocks, threads, smem, c->stream);
       MGDG_CASE(3) MGDG_CASE(5) MGDG_CASE(7) MGDG_CASE(9) MGDG_CASE(11) MGDG_CASE(13) MGDG_CASE(15)
       MGDG_CASE(17) MGDG_CASE(19) MGDG_CASE(21) MGDG_CASE(23) MGDG_CASE(25) MGDG_CASE(27) MGDG_CASE(29)
@@ -274,13 +307,19 @@ cudaError_t launch_fdm(const mg_ctx* c, int l, const T* r) {
 #undef MGDG_CASE
       default: break;
     }
+    c->nlaunch -= 1;
   }
   a.spb = 1;
+  size_t smem = 0;
+  for (int d = 0; d < 3; ++d) smem += sizeof(T) * 2 * lv.m[d] * lv.m[d];
+  a.s_in_smem = smem <= 160 * 1024;
+  if (!a.s_in_smem) smem = 0;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_fdm<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  int threads = m2 >= 256 ? 256 : 128;
+  const int lines = std::max(lv.m[1] * lv.m[2], std::max(lv.m[0] * lv.m[2], lv.m[0] * lv.m[1]));
+  int threads = lines >= 256 ? 256 : 128;
   int64_t blocks = c->Ne < 152 * 8 ? c->Ne : 152 * 8;
   k_fdm<T><<<(int)blocks, threads, smem, c->stream>>>(a);
   c->nlaunch += 1;
@@ -295,14 +334,15 @@ cudaError_t launch_scatter(const mg_ctx* c, int l, T* u, int accumulate) {
   if (blocks > 152 * 16) blocks = 152 * 16;
   const T* corr = static_cast<const T*>(c->ws.corr);
   const int eb = (int)blocks;
+  const SubShape g{lv.m[0], lv.m[1], lv.m[2], lv.no[0], lv.no[1], lv.no[2]};
   c->nlaunch += 1;
   switch (lv.n) {
-#define MGDG_SC(N) case N: k_scatter_n<T, N><<<eb, 256, 0, c->stream>>>(corr, u, c->Ne, c->ne[0], c->ne[1], c->ne[2], lv.m, lv.no, accumulate); return cudaGetLastError();
+#define MGDG_SC(N) case N: k_scatter_n<T, N><<<eb, 256, 0, c->stream>>>(corr, u, c->Ne, c->ne[0], c->ne[1], c->ne[2], g, accumulate); return cudaGetLastError();
     MGDG_SC(3) MGDG_SC(5) MGDG_SC(9) MGDG_SC(17) MGDG_SC(33)
 #undef MGDG_SC
     default: break;
   }
-  k_scatter<T><<<(int)blocks, 256, 0, c->stream>>>(corr, u, c->Ne, c->ne[0], c->ne[1], c->ne[2], lv.n, lv.m, lv.no,
+  k_scatter<T><<<(int)blocks, 256, 0, c->stream>>>(corr, u, c->Ne, c->ne[0], c->ne[1], c->ne[2], lv.n, g,
                                                     accumulate);
   return cudaGetLastError();
 }

@@ -411,7 +411,19 @@ __global__ void __launch_bounds__(kSetupThreads) k_setup_level(SetupBatch batch,
     node_of(a, &da, &ia);
     Ms[a] = 0.5 * q.h * sm.w[ia];
     double xi_h = sm.x[ia] + 2.0 * da;
-    tab[q.t.w + a] = (no == 0) ? 1.0 : hat_weight(xi_h, q.delta, q.profile);
+    double w = (no == 0) ? 1.0 : hat_weight(xi_h, q.delta, q.profile);
+    if (no > 0 && q.delta > 1.0) {
+      // A strip wider than half an element: the node of the neighbour element
+      // may also lie in a third subdomain, so the weight is divided by the sum
+      // of the raw weights of all subdomains covering it (xi_h - 2 o for the
+      // subdomain centred o elements further on, o = -1, 0, +1).
+      const double xi = sm.x[ia];
+      double total = hat_weight(xi, q.delta, q.profile);
+      if (ia >= n - no) total += hat_weight(xi - 2.0, q.delta, q.profile);
+      if (ia < no) total += hat_weight(xi + 2.0, q.delta, q.profile);
+      w = total > 0.0 ? w / total : 0.0;
+    }
+    tab[q.t.w + a] = w;
   }
   __syncthreads();
   bool ok = gen_eig_centro(Ls, Ms, m, tab + q.t.S, tab + q.t.lam, wk, sm.red, sm.sp, sm.sq, sm.sc, sm.ss);
@@ -450,10 +462,10 @@ __global__ void __launch_bounds__(kSetupThreads) k_setup_level(SetupBatch batch,
   }
 }
 
-__global__ void k_setup_dinv(double* tab, int64_t dinv, int64_t lx, int64_t ly, int64_t lz, int m) {
-  int64_t total = (int64_t)m * m * m;
+__global__ void k_setup_dinv(double* tab, int64_t dinv, int64_t lx, int64_t ly, int64_t lz, int mx, int my, int mz) {
+  int64_t total = (int64_t)mx * my * mz;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    int a = (int)(i % m), b = (int)((i / m) % m), c = (int)(i / ((int64_t)m * m));
+    int a = (int)(i % mx), b = (int)((i / mx) % my), c = (int)(i / ((int64_t)mx * my));
     tab[dinv + i] = 1.0 / (tab[lx + a] + tab[ly + b] + tab[lz + c]);
   }
 }
@@ -508,12 +520,12 @@ cudaError_t launch_setup(mg_ctx* c) {
       SetupParams& q = batch.p[nb++];
       q.P = lv.P;
       q.n = lv.n;
-      q.m = lv.m;
-      q.no = lv.no;
+      q.m = lv.m[d];
+      q.no = lv.no[d];
       q.profile = c->opts.weight_profile;
       q.level = l;
       q.Pc = l > 0 ? c->lev[l - 1].P : 0;
-      q.delta = lv.delta;
+      q.delta = lv.delta[d];
       q.h = lv.h[d];
       q.g = lv.g[d];
       q.mu = lv.mu[d];
@@ -540,10 +552,11 @@ cudaError_t launch_setup(mg_ctx* c) {
   }
   for (int l = 1; l <= c->L; ++l) {
     const LevelInfo& lv = c->lev[l];
-    int64_t total = (int64_t)lv.m * lv.m * lv.m;
+    int64_t total = (int64_t)lv.m[0] * lv.m[1] * lv.m[2];
     int blocks = (int)((total + 255) / 256);
     if (blocks > 1024) blocks = 1024;
-    k_setup_dinv<<<blocks, 256, 0, s>>>(c->ws.tab64, lv.dinv, lv.t[0].lam, lv.t[1].lam, lv.t[2].lam, lv.m);
+    k_setup_dinv<<<blocks, 256, 0, s>>>(c->ws.tab64, lv.dinv, lv.t[0].lam, lv.t[1].lam, lv.t[2].lam, lv.m[0],
+                                        lv.m[1], lv.m[2]);
     c->nlaunch += 1;
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;

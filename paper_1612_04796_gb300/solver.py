@@ -12,7 +12,7 @@ from . import _lib
 from ._lib import MgOpts, load_library
 
 PRECISION = {"fp64": 0, "mixed": 1}
-OVERLAP_MODE = {"layers": 0, "width": 1}
+OVERLAP_MODE = {"layers": 0, "width": 1, "max": 2}
 PROFILE = {"quintic": 0, "linear": 1, "quintic_halves": 2, "quintic_normalised": 3}
 
 
@@ -97,8 +97,11 @@ class MGSolver:
     def num_dofs(self, level=None):
         return int(self.lib.mg_num_dofs(self.ctx, self.L if level is None else level))
 
-    def layers(self, level):
-        return int(self.lib.mg_level_layers(self.ctx, level))
+    def layers(self, level, direction=None):
+        """N_O of a level: of the x direction, or of `direction` (0, 1, 2)."""
+        if direction is None:
+            return int(self.lib.mg_level_layers(self.ctx, level))
+        return int(self.lib.mg_level_layers_dir(self.ctx, level, int(direction)))
 
     def _vec(self, t, level, dtype=torch.float64, name="vector"):
         n = self.num_dofs(level)

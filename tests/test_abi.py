@@ -93,3 +93,37 @@ def test_calls_before_binding_are_not_ready(lib):
     assert lib.mg_bind_workspace(ctx, ctypes.c_void_p(257), ctypes.c_size_t(1 << 40)) == 1
     assert lib.mg_bind_workspace(ctx, ctypes.c_void_p(256), ctypes.c_size_t(16)) == 2
     lib.mg_destroy(ctx)
+
+
+@pytest.mark.parametrize("ar", [1, 3, 8, 12, 48])
+@pytest.mark.parametrize("P", [4, 16])
+def test_max_overlap_layers_per_direction(lib, ar, P):
+    """MG_OVERLAP_MAX: N_O of every level and direction equals the oracle's
+    count for delta_O,i = min(0.08 max_j dx_j, dx_i) (Table 2)."""
+    import math
+
+    from oracle.schwarz import max_width_layers
+    from oracle.multigrid import max_overlap_widths
+    from oracle.sipg import Mesh
+    lengths = (2 * math.pi * ar, 2 * math.pi * math.ceil(ar / 2), 2 * math.pi)
+    st, ctx = _setup(lib, P=P, counts=(8, 8, 8), lengths=lengths, overlap_mode=2, overlap_frac=0.08)
+    assert st == 0
+    deltas = max_overlap_widths(Mesh(lengths, (8, 8, 8)), 0.08)
+    for l in range(1, P.bit_length()):
+        got = [lib.mg_level_layers_dir(ctx, l, d) for d in range(3)]
+        assert got == [max_width_layers(2 ** l, dd) for dd in deltas], (l, got)
+        assert lib.mg_level_layers(ctx, l) == got[0]
+    assert lib.mg_level_layers_dir(ctx, 1, 3) == -1
+    lib.mg_destroy(ctx)
+
+
+def test_max_overlap_rejections(lib):
+    import math
+    lengths = (2 * math.pi * 48, 2 * math.pi * 24, 2 * math.pi)
+    # whole-element strips in z with only three elements there
+    st, ctx = _setup(lib, P=4, counts=(4, 4, 3), lengths=lengths, overlap_mode=2, overlap_frac=0.08)
+    assert st == 1 and not ctx.value
+    st, ctx = _setup(lib, P=4, counts=(4, 4, 4), lengths=lengths, overlap_mode=2, overlap_frac=1.5)
+    assert st == 1 and not ctx.value
+    st, ctx = _setup(lib, P=4, counts=(4, 4, 4), lengths=lengths, overlap_mode=3, overlap_frac=0.08)
+    assert st == 1 and not ctx.value
