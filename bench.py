@@ -32,6 +32,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "DOF/s solved to 1e-10 rel. residual, mixed vs FP64 on GB300; p50/p99 latency"
+TC_MODE = {"off": False, "on": True, "auto": "auto"}
 WORKLOAD = {
     "workload": "periodic unit cube, 16^3 elements, P=8 (2,985,984 DOFs), nodal f ~ N(0,1) seed 2 with zero mean, "
                 "standalone V(1,1) multigrid, N_O=1 node layer, FP64, u0 = 0, tol 1e-10",
@@ -96,6 +97,9 @@ def parse_args():
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
     ap.add_argument("--overlap", type=int, default=None, help="override N_O of the workload")
     ap.add_argument("--precision", default=None, choices=["fp64", "mixed"], help="override the workload's precision")
+    ap.add_argument("--tensor-cores", default="off", choices=["off", "on", "auto"],
+                    help="FP32 smoother contractions in the mixed runs: CUDA cores, tensor cores (tcgen05, "
+                         "TF32) where the tiles fit, or per level the faster of the two (timed at setup)")
     return ap.parse_args()
 
 
@@ -391,7 +395,7 @@ def run_mg(args):
 
         # mixed precision: FP32 V(1,1) preconditioner inside FP64 inexact PCG
         sm_ = pkg.MGSolver(W["lengths"], W["elements"], W["P"], overlap=W["overlap_layers"], precision="mixed",
-                           device=dev)
+                           device=dev, tensor_cores=TC_MODE[args.tensor_cores])
         um = torch.zeros(N, dtype=torch.float64, device=dev)
         for _ in range(args.warmup):
             um.zero_()
@@ -409,6 +413,8 @@ def run_mg(args):
         line["mixed"] = {"value": world * N * args.steps / mix_total, "unit": "DOF/s",
                          "ms_per_step": sum(mix_ms) / args.steps, "iterations": its_m,
                          "solver": "MG-CG: FP32 V(1,1) preconditioner, FP64 inexact PCG",
+                         "fdm_tensor_cores": args.tensor_cores,
+                         "fdm_tensor_cores_by_level": [sm_.fdm_tensor_cores(l) for l in range(1, sm_.L + 1)],
                          "true_relres": true_rel, "max_rel_diff_vs_fp64_solution": err,
                          "time_share_of_step": profile_shares(sm_, sum(mix_prof_ms)),
                          "ms_per_step_by_kernel_level": profile_levels(sm_, args.steps)}
@@ -440,8 +446,9 @@ def run_workload(args):
     dev = torch.device("cuda", torch.cuda.current_device())
     pkg.load_library()
     extra = {k: W[k] for k in ("overlap_mode", "overlap_frac", "ns_growth") if k in W}
+    extra_mixed = dict(extra, tensor_cores=TC_MODE[args.tensor_cores])
     s = pkg.MGSolver(W["lengths"], W["elements"], W["P"], overlap=W["overlap_layers"], precision=W["precision"],
-                     device=dev, **extra)
+                     device=dev, **(extra_mixed if W["precision"] == "mixed" else extra))
     s64 = s if W["precision"] == "fp64" else pkg.MGSolver(W["lengths"], W["elements"], W["P"],
                                                           overlap=W["overlap_layers"], device=dev, **extra)
     N = s.num_dofs()
@@ -484,6 +491,9 @@ def run_workload(args):
     prof_ms, _ = steps(args.steps)
     s.profile(False)
     true_rel = float(torch.linalg.norm(s64.residual(u, b)) / torch.linalg.norm(b))
+    if W["precision"] == "mixed":
+        W["fdm_tensor_cores"] = args.tensor_cores
+        W["fdm_tensor_cores_by_level"] = [s.fdm_tensor_cores(l) for l in range(1, s.L + 1)]
     lev = s.L
     md = [s.P + 1 + 2 * s.layers(lev, d) for d in range(3)]
     m = md[0] if md[0] == md[1] == md[2] else "x".join(str(v) for v in md)

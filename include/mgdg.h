@@ -83,6 +83,12 @@ typedef struct {
   int ns_pre, ns_post;   /* smoothing steps N_s1, N_s2 on the fine level (default 1, 1) */
   int ns_growth;         /* N_s,l = N_s * ns_growth^(L-l): 1 fixed V-cycle, 3 variable (Table 2) */
   int precision;         /* mg_precision, default MG_FP64 */
+  int fdm_tensor_cores;  /* MG_MIXED, subdomain contractions of the FP32 smoother: 0 = FP32 CUDA
+                            cores (default); 1 = tensor cores (tcgen05, TF32 inputs rounded to
+                            nearest, FP32 accumulation) on every level whose tiles fit the
+                            kernel; 2 = per level whichever of the two mg_bind_workspace
+                            measures faster (the choice, and so the rounding, may differ
+                            between contexts) */
   void* stream;          /* cudaStream_t; NULL = default stream */
 } mg_opts;
 
@@ -133,6 +139,10 @@ int mg_num_levels(const mg_ctx* ctx);
 long long mg_num_dofs(const mg_ctx* ctx, int level);
 int mg_level_layers(const mg_ctx* ctx, int level);
 int mg_level_layers_dir(const mg_ctx* ctx, int level, int dir);
+
+/* Kernel of the FP32 smoother contractions on a level after mg_bind_workspace:
+ * 1 tensor cores, 0 CUDA cores, -1 bad level. */
+int mg_level_fdm_tensor_cores(const mg_ctx* ctx, int level);
 
 /* Physical coordinates of the nodes of `level` into x, y, z (device, N_l each). */
 mg_status mg_node_coords(mg_ctx* ctx, int level, double* x, double* y, double* z);

@@ -20,6 +20,7 @@ class MgOpts(ctypes.Structure):
         ("ns_post", ctypes.c_int),
         ("ns_growth", ctypes.c_int),
         ("precision", ctypes.c_int),
+        ("fdm_tensor_cores", ctypes.c_int),
         ("stream", ctypes.c_void_p),
     ]
 
@@ -40,6 +41,7 @@ SIGNATURES = {
     "mg_num_dofs": (_LL, [_P, _I]),
     "mg_level_layers": (_I, [_P, _I]),
     "mg_level_layers_dir": (_I, [_P, _I, _I]),
+    "mg_level_fdm_tensor_cores": (_I, [_P, _I]),
     "mg_node_coords": (_S, [_P, _I, _P, _P, _P]),
     "mg_rhs": (_S, [_P, _P, _P]),
     "mg_apply_sipg": (_S, [_P, _I, _P, _P]),

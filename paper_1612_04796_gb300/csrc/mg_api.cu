@@ -346,6 +346,41 @@ cudaError_t precond(const mg_ctx* c, const double* r, double* z) {
   return vcycle_t<double>(c, z, r, true, false);
 }
 
+// FP32 smoother kernel per level.  fdm_tensor_cores = 1: the tensor-core
+// kernel wherever the tiles fit it.  2: both kernels are timed on the level
+// (CUDA events, a zero residual, after one warm-up launch each) and the
+// faster one is kept.
+cudaError_t choose_fdm_kernels(mg_ctx* c) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaSuccess;
+  for (int l = 1; l <= c->L && e == cudaSuccess; ++l) {
+    LevelInfo& lv = c->lev[l];
+    lv.fdm_tc = 0;
+    if (!fdm_tc_fits(c, l)) continue;
+    if (c->opts.fdm_tensor_cores == 1) {
+      lv.fdm_tc = 1;
+      continue;
+    }
+    if (!e0 && ((e = cudaEventCreate(&e0)) != cudaSuccess || (e = cudaEventCreate(&e1)) != cudaSuccess)) break;
+    float* r = lvec<float>(lv.r);
+    if ((e = launch_zero<float>(c, r, lv.N)) != cudaSuccess) break;
+    float best[2] = {0.f, 0.f};
+    for (int kind = 0; kind < 2 && e == cudaSuccess; ++kind) {
+      lv.fdm_tc = kind;
+      if ((e = launch_fdm<float>(c, l, r)) != cudaSuccess) break;
+      if ((e = cudaEventRecord(e0, c->stream)) != cudaSuccess) break;
+      for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = launch_fdm<float>(c, l, r);
+      if (e != cudaSuccess || (e = cudaEventRecord(e1, c->stream)) != cudaSuccess) break;
+      if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
+      e = cudaEventElapsedTime(&best[kind], e0, e1);
+    }
+    lv.fdm_tc = (e == cudaSuccess && best[1] < best[0]) ? 1 : 0;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  return e;
+}
+
 mg_status solve_impl(mg_ctx* c, double* u, const double* f, double tol, int maxit, int use_cg, int* iters,
                      double* relres, double* history) {
   const int L = c->L;
@@ -453,8 +488,11 @@ mg_status solve_impl(mg_ctx* c, double* u, const double* f, double tol, int maxi
   }
   CK(launch_sum(c, u, N, kSlotSum));
   CK(launch_sub_mean(c, u, N, kSlotSum));
+  int waits = 0;
+  CK(cudaMemcpyAsync(&waits, c->ws.status + 1, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   if (iters) *iters = it;
+  if (waits != kDevOk) return fail(c, MG_ECUDA, "a tensor-core kernel gave up waiting for its MMAs");
   if (relres) *relres = r0 > 0.0 ? rn / r0 : 0.0;
   if (!converged) return fail(c, MG_ENOCONV, "maximum number of iterations reached");
   return MG_OK;
@@ -473,6 +511,7 @@ void mg_default_opts(mg_opts* o) {
   o->ns_post = 1;
   o->ns_growth = 1;
   o->precision = MG_FP64;
+  o->fdm_tensor_cores = 0;
   o->stream = nullptr;
 }
 
@@ -488,6 +527,7 @@ mg_status mg_setup(double lx, double ly, double lz, int nx, int ny, int nz, int 
   if (opts) o = *opts;
   if (o.ns_pre < 0 || o.ns_post < 0 || o.ns_growth < 1 || o.ns_pre + o.ns_post < 1) return MG_EINVAL;
   if (o.precision != MG_FP64 && o.precision != MG_MIXED) return MG_EINVAL;
+  if (o.fdm_tensor_cores < 0 || o.fdm_tensor_cores > 2) return MG_EINVAL;
   if (o.weight_profile < MG_WEIGHT_QUINTIC || o.weight_profile > MG_WEIGHT_QUINTIC_NORMALISED) return MG_EINVAL;
   if (o.overlap_mode != MG_OVERLAP_LAYERS && o.overlap_mode != MG_OVERLAP_WIDTH && o.overlap_mode != MG_OVERLAP_MAX)
     return MG_EINVAL;
@@ -579,9 +619,11 @@ mg_status mg_setup(double lx, double ly, double lz, int nx, int ny, int nz, int 
       }
     }
     lv.dinv = (l >= 1) ? tab((int64_t)lv.m[0] * lv.m[1] * lv.m[2]) : -1;
+    lv.dinvp = (l >= 1) ? tab((int64_t)lv.m[0] * ((lv.m[1] + 3) / 4 * 4) * ((lv.m[2] + 3) / 4 * 4)) : -1;
     lv.mass3 = tab((int64_t)lv.n * lv.n * lv.n);
     lv.J = (l >= 1) ? tab((int64_t)lv.n * (c->lev[l - 1].n)) : -1;
     lv.u = lv.f = lv.r = nullptr;
+    lv.fdm_tc = 0;
   }
   c->ws.tab_count = off;
   c->ws_bytes = make_layout(c).total;
@@ -637,6 +679,7 @@ mg_status mg_bind_workspace(mg_ctx* c, void* dptr, size_t bytes) {
   }
   CK(cudaStreamSynchronize(c->stream));
   if (st != kDevOk) return fail(c, MG_ENOCONV, "setup eigensolver did not converge");
+  if (c->opts.precision == MG_MIXED && c->opts.fdm_tensor_cores != 0) CK(choose_fdm_kernels(c));
   c->ready = true;
   return MG_OK;
 }
@@ -649,6 +692,11 @@ long long mg_num_dofs(const mg_ctx* c, int level) {
 }
 
 int mg_level_layers(const mg_ctx* c, int level) { return mg_level_layers_dir(c, level, 0); }
+
+int mg_level_fdm_tensor_cores(const mg_ctx* c, int level) {
+  if (!c || level < 0 || level > c->L) return -1;
+  return c->lev[level].fdm_tc;
+}
 
 int mg_level_layers_dir(const mg_ctx* c, int level, int dir) {
   if (!c || level < 0 || level > c->L || dir < 0 || dir > 2) return -1;

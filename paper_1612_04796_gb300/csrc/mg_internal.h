@@ -35,7 +35,8 @@ enum Slot : int {
 };
 
 // Status word written by device code (setup eigensolvers) and read by the host.
-enum DevStatus : int { kDevOk = 0, kDevNoConv = 1 };
+// Word 0: setup eigensolvers; word 1: bounded waits of the tensor-core kernels.
+enum DevStatus : int { kDevOk = 0, kDevNoConv = 1, kDevTimeout = 2 };
 
 // Offsets (in values) of the 1D tables of one level and direction inside the
 // table arrays tab64 / tab32 (same offsets in both).
@@ -56,7 +57,10 @@ struct LevelInfo {
   double h[3], g[3], mu[3];
   DirTables t[3];
   int64_t dinv;          // m_x m_y m_z: 1 / (lam_x[a] + lam_y[b] + lam_z[c])
+  int64_t dinvp;         // the same values at (b + ru4(m_y) a) ru4(m_z) + c, zero padded
+                         // (ru4 = rounded up to a multiple of 4; tensor-core smoother)
   int64_t mass3;         // n^3: mass_x[i] mass_y[j] mass_z[k]
+  int fdm_tc;            // FP32 smoother contractions on the tensor cores (1) or CUDA cores (0)
   int64_t J;             // n * n_c interpolation from level l-1 (level >= 1)
   // device vectors (bytes sized for FP64; FP32 code uses the first half)
   void* u;
@@ -152,6 +156,10 @@ template <typename T>
 cudaError_t launch_fdm(const mg_ctx* c, int l, const T* r);
 template <typename T>
 cudaError_t launch_scatter(const mg_ctx* c, int l, T* u, int accumulate);
+// FP32 corrections on the tensor cores (fdm_tc.cu); cudaErrorNotSupported if
+// the level's subdomain tiles do not fit the kernel's shared/tensor memory.
+cudaError_t launch_fdm_tc(const mg_ctx* c, int l, const float* r);
+bool fdm_tc_fits(const mg_ctx* c, int l);
 
 // ---- transfers (transfer.cu) ----
 template <typename T>

@@ -13,6 +13,7 @@
 // values that cover it in a fixed order, so the result is deterministic and
 // no atomics are needed.
 #include <algorithm>
+#include <type_traits>
 
 #include "fdm_tmpl.cuh"
 
@@ -269,6 +270,12 @@ const float* table_of<float>(const mg_ctx* c) { return c->ws.tab32; }
 template <typename T>
 cudaError_t launch_fdm(const mg_ctx* c, int l, const T* r) {
   const LevelInfo& lv = c->lev[l];
+  if constexpr (std::is_same<T, float>::value) {
+    if (lv.fdm_tc) {
+      const cudaError_t e = launch_fdm_tc(c, l, r);
+      if (e != cudaErrorNotSupported) return e;
+    }
+  }
   FdmArgs<T> a;
   a.tab = table_of<T>(c);
   a.r = r;

@@ -470,6 +470,17 @@ __global__ void k_setup_dinv(double* tab, int64_t dinv, int64_t lx, int64_t ly, 
   }
 }
 
+// 1 / (lam_x[a] + lam_y[b] + lam_z[c]) at (b + myp a) mzp + c, zero where b >= my or c >= mz.
+__global__ void k_setup_dinvp(double* tab, int64_t dinvp, int64_t lx, int64_t ly, int64_t lz, int mx, int my, int mz) {
+  const int myp = (my + 3) / 4 * 4, mzp = (mz + 3) / 4 * 4;
+  const int64_t total = (int64_t)mx * myp * mzp;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(i % mzp), row = (int)(i / mzp);
+    const int b = row % myp, a = row / myp;
+    tab[dinvp + i] = (b < my && c < mz) ? 1.0 / (tab[lx + a] + tab[ly + b] + tab[lz + c]) : 0.0;
+  }
+}
+
 __global__ void k_setup_mass3(double* tab, int64_t mass3, int64_t mx, int64_t my, int64_t mz, int n) {
   const int total = n * n * n;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
@@ -557,6 +568,9 @@ cudaError_t launch_setup(mg_ctx* c) {
     if (blocks > 1024) blocks = 1024;
     k_setup_dinv<<<blocks, 256, 0, s>>>(c->ws.tab64, lv.dinv, lv.t[0].lam, lv.t[1].lam, lv.t[2].lam, lv.m[0],
                                         lv.m[1], lv.m[2]);
+    k_setup_dinvp<<<blocks, 256, 0, s>>>(c->ws.tab64, lv.dinvp, lv.t[0].lam, lv.t[1].lam, lv.t[2].lam, lv.m[0],
+                                         lv.m[1], lv.m[2]);
+    c->nlaunch += 1;
     c->nlaunch += 1;
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;

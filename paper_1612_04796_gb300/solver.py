@@ -34,7 +34,7 @@ class MGSolver:
 
     def __init__(self, lengths, counts, P, penalty=2.0, overlap=1, precision="fp64", overlap_mode="layers",
                  overlap_frac=0.08, weight_profile="quintic", ns_pre=1, ns_post=1, ns_growth=1, device="cuda",
-                 stream=None):
+                 stream=None, tensor_cores=False):
         self.lib = load_library()
         self.device = torch.device(device)
         if self.device.type == "cuda" and self.device.index is None:
@@ -46,6 +46,7 @@ class MGSolver:
         opts.weight_profile = PROFILE[weight_profile]
         opts.ns_pre, opts.ns_post, opts.ns_growth = int(ns_pre), int(ns_post), int(ns_growth)
         opts.precision = PRECISION[precision]
+        opts.fdm_tensor_cores = {False: 0, True: 1, "auto": 2}[tensor_cores]
         with torch.cuda.device(self.device):
             self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         opts.stream = ctypes.c_void_p(self.stream.cuda_stream)
@@ -96,6 +97,10 @@ class MGSolver:
 
     def num_dofs(self, level=None):
         return int(self.lib.mg_num_dofs(self.ctx, self.L if level is None else level))
+
+    def fdm_tensor_cores(self, level):
+        """1 if the FP32 smoother of `level` runs its contractions on the tensor cores."""
+        return int(self.lib.mg_level_fdm_tensor_cores(self.ctx, level))
 
     def layers(self, level, direction=None):
         """N_O of a level: of the x direction, or of `direction` (0, 1, 2)."""

@@ -46,7 +46,8 @@ def test_defaults(lib):
 
 @pytest.mark.parametrize("bad", [dict(P=3), dict(P=1), dict(P=64), dict(counts=(2, 4, 4)), dict(counts=(4, 4, 513)),
                                  dict(overlap=-1), dict(lengths=(0.0, 1.0, 1.0)), dict(ns_pre=0, ns_post=0),
-                                 dict(precision=7), dict(overlap_mode=1, overlap_frac=0.75)])
+                                 dict(precision=7), dict(overlap_mode=1, overlap_frac=0.75),
+                                 dict(precision=1, fdm_tensor_cores=3)])
 def test_rejects_bad_arguments(lib, bad):
     st, ctx = _setup(lib, **bad)
     assert st == 1 and not ctx.value
