@@ -140,6 +140,17 @@ long long mg_num_dofs(const mg_ctx* ctx, int level);
 int mg_level_layers(const mg_ctx* ctx, int level);
 int mg_level_layers_dir(const mg_ctx* ctx, int level, int dir);
 
+/*
+ * mg_selftest_bounded_wait -- check the bounded wait of the tensor-core
+ * smoother kernel on `level` (MG_MIXED context, level whose tiles fit the
+ * kernel): launches it so that nothing ever arrives on its mbarrier (no MMA is
+ * issued), lets its wait run out (about 10 ms), reads the status word back and
+ * clears it.  *timed_out = 1 if the kernel reported the timeout.  The context
+ * stays usable.  Not part of the method; a check of the failure path.
+ * MG_EINVAL if the level cannot run the kernel.
+ */
+mg_status mg_selftest_bounded_wait(mg_ctx* ctx, int level, int* timed_out);
+
 /* Kernel of the FP32 smoother contractions on a level after mg_bind_workspace:
  * 1 tensor cores, 0 CUDA cores, -1 bad level. */
 int mg_level_fdm_tensor_cores(const mg_ctx* ctx, int level);

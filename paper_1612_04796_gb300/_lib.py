@@ -42,6 +42,7 @@ SIGNATURES = {
     "mg_level_layers": (_I, [_P, _I]),
     "mg_level_layers_dir": (_I, [_P, _I, _I]),
     "mg_level_fdm_tensor_cores": (_I, [_P, _I]),
+    "mg_selftest_bounded_wait": (_S, [_P, _I, ctypes.POINTER(ctypes.c_int)]),
     "mg_node_coords": (_S, [_P, _I, _P, _P, _P]),
     "mg_rhs": (_S, [_P, _P, _P]),
     "mg_apply_sipg": (_S, [_P, _I, _P, _P]),

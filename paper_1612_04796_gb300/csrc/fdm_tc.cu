@@ -35,7 +35,8 @@
 // finite garbage into padded K positions only.  Values are rounded to TF32
 // (to nearest) when stored as MMA inputs.  Every wait is bounded in time; on a
 // timeout the kernel sets the status word, leaves its loops and still frees
-// its tensor memory.
+// its tensor memory (mg_selftest_bounded_wait runs the kernel with a barrier
+// that nothing arrives on to check exactly that).
 #include <stdint.h>
 
 #include <algorithm>
@@ -48,6 +49,7 @@ namespace {
 constexpr int kTcThreads = 256;  // eight warps; warp w reads tensor-memory lanes 32 (w % 4) ..
 constexpr int kTcRows = 128;     // MMA tile height M (quads)
 constexpr long long kTcWaitCycles = 4000000000LL;  // about 2 s at the maximum SM clock
+constexpr long long kTcSelfTestWaitCycles = 20000000LL;  // about 10 ms
 constexpr int kPassDir[6] = {0, 1, 2, 2, 1, 0};
 
 struct TcPass {
@@ -76,6 +78,8 @@ struct TcArgs {
   int lbo_a;           // bytes between K-adjacent core matrices of A (144: bank spread, or 128)
   int b_resident;      // 1: all six factors loaded once; 0: reloaded per pass at offset 0
   uint32_t tmem_cols;  // power of two >= 32
+  long long wait_cycles;  // limit of each mbarrier wait
+  int self_test;          // 1: issue no MMA and no commit, so the first wait runs out
 };
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
@@ -102,7 +106,7 @@ __device__ __forceinline__ void tc_mma(uint32_t tmem, uint64_t da, uint64_t db, 
 }
 
 // Wait for completion `phase` of the mbarrier, bounded in time.
-__device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t phase) {
+__device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t phase, long long limit) {
   const long long t0 = clock64();
   uint32_t done = 0;
   while (true) {
@@ -112,7 +116,7 @@ __device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t phase) {
         : "=r"(done)
         : "r"(mbar), "r"(phase));
     if (done) return true;
-    if (clock64() - t0 > kTcWaitCycles) return false;
+    if (clock64() - t0 > limit) return false;
   }
 }
 
@@ -318,7 +322,7 @@ __global__ void __launch_bounds__(kTcThreads) k_fdm_tc(TcArgs a) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       asm volatile("tcgen05.fence::before_thread_sync;");
       __syncthreads();
-      if (tid == 0) {
+      if (tid == 0 && !a.self_test) {
         asm volatile("tcgen05.fence::after_thread_sync;");
         const uint32_t idesc = tc_idesc(ps.np);
         const uint32_t lbo = (uint32_t)a.lbo_a, sbo = (uint32_t)ps.kp * lbo, sbo_b = 32u * ps.kp;
@@ -333,7 +337,7 @@ __global__ void __launch_bounds__(kTcThreads) k_fdm_tc(TcArgs a) {
                      : "memory");
       }
       // one thread waits for the MMAs (the others sleep in the barrier, issuing nothing)
-      if (tid == 0 && !tc_wait(mb, phase)) {
+      if (tid == 0 && !tc_wait(mb, phase, a.wait_cycles)) {
         atomicExch(a.status + 1, kDevTimeout);
         abort_flag = 1;
       }
@@ -470,11 +474,13 @@ bool fdm_tc_fits(const mg_ctx* c, int l) {
   return l >= 1 && l <= c->L && tc_configure(c, l, nullptr, a, per_sm, smem);
 }
 
-cudaError_t launch_fdm_tc(const mg_ctx* c, int l, const float* r) {
+cudaError_t launch_fdm_tc(const mg_ctx* c, int l, const float* r, int self_test) {
   TcArgs a;
   int per_sm = 0;
   uint32_t smem = 0;
   if (!tc_configure(c, l, r, a, per_sm, smem)) return cudaErrorNotSupported;
+  a.self_test = self_test;
+  a.wait_cycles = self_test ? kTcSelfTestWaitCycles : kTcWaitCycles;
   const int G = a.G;
   cudaError_t e = cudaFuncSetAttribute(k_fdm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

@@ -693,6 +693,23 @@ long long mg_num_dofs(const mg_ctx* c, int level) {
 
 int mg_level_layers(const mg_ctx* c, int level) { return mg_level_layers_dir(c, level, 0); }
 
+mg_status mg_selftest_bounded_wait(mg_ctx* c, int level, int* timed_out) {
+  mg_status s = need_ready(c);
+  if (s != MG_OK) return s;
+  if (!timed_out || c->opts.precision != MG_MIXED || level < 1 || level > c->L || !fdm_tc_fits(c, level))
+    return fail(c, MG_EINVAL, "the level cannot run the tensor-core smoother");
+  *timed_out = 0;
+  float* r = lvec<float>(c->lev[level].r);
+  CK(launch_zero<float>(c, r, c->lev[level].N));
+  CK(launch_fdm_tc(c, level, r, 1));
+  int st = 0;
+  CK(cudaMemcpyAsync(&st, c->ws.status + 1, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemsetAsync(c->ws.status + 1, 0, sizeof(int), c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  *timed_out = st == kDevTimeout ? 1 : 0;
+  return MG_OK;
+}
+
 int mg_level_fdm_tensor_cores(const mg_ctx* c, int level) {
   if (!c || level < 0 || level > c->L) return -1;
   return c->lev[level].fdm_tc;

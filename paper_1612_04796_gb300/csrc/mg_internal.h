@@ -158,7 +158,9 @@ template <typename T>
 cudaError_t launch_scatter(const mg_ctx* c, int l, T* u, int accumulate);
 // FP32 corrections on the tensor cores (fdm_tc.cu); cudaErrorNotSupported if
 // the level's subdomain tiles do not fit the kernel's shared/tensor memory.
-cudaError_t launch_fdm_tc(const mg_ctx* c, int l, const float* r);
+// self_test = 1: no MMA is issued and nothing arrives on the barrier, so the
+// kernel's first (shortened) wait runs out and it reports kDevTimeout.
+cudaError_t launch_fdm_tc(const mg_ctx* c, int l, const float* r, int self_test = 0);
 bool fdm_tc_fits(const mg_ctx* c, int l);
 
 // ---- transfers (transfer.cu) ----

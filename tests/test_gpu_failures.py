@@ -1,6 +1,7 @@
 """Failure handling on the GPU without faulting it: iteration limits end in a
 status, bad arguments are rejected before any kernel runs, a NaN right-hand
-side ends after maxit cycles (no hang)."""
+side ends after maxit cycles (no hang), and the tensor-core kernel's bounded
+mbarrier wait runs out on a barrier that nothing arrives on and reports it."""
 import ctypes
 
 import numpy as np
@@ -48,3 +49,24 @@ def test_nan_rhs_is_rejected_and_context_stays_usable(small, mg):
     assert ei.value.status == 1  # MG_EINVAL: non-finite initial residual
     u2, its2, rel2, _ = s.solve(b, tol=1e-10)
     assert rel2 <= 1e-10
+
+
+def test_tensor_core_wait_runs_out_and_context_stays_usable(mg):
+    """The tensor-core smoother's mbarrier wait is bounded: with nothing ever
+    arriving on the barrier (no MMA issued) the kernel gives up after its limit,
+    reports the timeout in the status word and frees its tensor memory; the
+    same context then solves normally."""
+    import torch
+    s = mg.MGSolver((1.0, 1.0, 1.0), (4, 4, 4), 8, precision="mixed", tensor_cores=True)
+    assert s.fdm_tensor_cores(s.L) == 1
+    flag = ctypes.c_int(-1)
+    assert s.lib.mg_selftest_bounded_wait(s.ctx, s.L, ctypes.byref(flag)) == 0
+    assert flag.value == 1
+    b = s.rhs(torch.tensor(inputs.gaussian(s.num_dofs(), 9), device=s.device))
+    u, its, rel, _ = s.solve(b, tol=1e-10, use_cg=True)
+    assert rel <= 1e-10
+    # a level that cannot run the kernel (FP64 context) is refused
+    s64 = mg.MGSolver((1.0, 1.0, 1.0), (4, 4, 4), 4)
+    assert s64.lib.mg_selftest_bounded_wait(s64.ctx, 1, ctypes.byref(flag)) == 1
+    s.close()
+    s64.close()
