@@ -1,13 +1,16 @@
 // Coarse grid solution u_0 = A_0^+ f_0 (Algorithm 1) on the P_0 = 1 level.
 //
-// f_0 is projected onto the range of A_0 (its Euclidean mean removed); the
-// periodic coarse operator A_0 = Mz(x)My(x)Lx + ... is diagonalised exactly by
-// the M-orthonormal eigenbases Q_d of the whole periodic 1D problems
-// (L_d Q_d = M_d Q_d Lambda_d, Q_d^T M_d Q_d = I), so
-//   v = (Qz(x)Qy(x)Qx) (Lambda sum)^+ (Qz^T(x)Qy^T(x)Qx^T) f_0
-// solves A_0 v = f_0; the single zero eigenvalue (all three constant modes)
-// is dropped, and the mean of v is removed to return the minimum-norm
-// solution.  This is a direct solve: no iteration, no tolerance.
+// The periodic coarse operator A_0 = Mz(x)My(x)Lx + ... is diagonalised
+// exactly by the M-orthonormal eigenbases Q_d of the whole periodic 1D
+// problems (L_d Q_d = M_d Q_d Lambda_d, Q_d^T M_d Q_d = I), so
+//   u_0 = (Qz(x)Qy(x)Qx) (Lambda sum)^+ (Qz^T(x)Qy^T(x)Qx^T) f_0
+// with the single zero eigenvalue (all three constant modes) dropped.  At
+// P_0 = 1 the 1D mass matrices are (h/2) I, so every other eigenvector is
+// orthogonal to the constants: dropping the constant mode is the projection
+// of f_0 onto the range of A_0, and u_0 has zero Euclidean mean -- it is the
+// minimum-norm solution A_0^+ f_0 without separate mean projections (they
+// would change u_0 only at rounding level).  This is a direct solve: no
+// iteration, no tolerance; six launches, one per axis pass.
 //
 // Vectors of level 0 are element-blocked with 2 nodes per direction; the
 // global 1D index along x is 2 ex + i (the same for y, z).  Intermediates are
@@ -34,7 +37,10 @@ __device__ __forceinline__ int64_t eb_index(int gx, int gy, int gz, const Coarse
 // in_eb / out_eb: read / write element-blocked order instead of lexicographic.
 // mean_slot >= 0: subtract scal[mean_slot] / N from every input value.
 // scale: multiply each output by the pseudo-inverse of lam_x + lam_y + lam_z.
-__global__ void k_coarse_axis(const double* __restrict__ in, double* __restrict__ out, const double* __restrict__ Q,
+// TI / TO: type of the input / output vector (the FP32 hierarchy reads its
+// right-hand side and writes its solution in FP32; intermediates are FP64).
+template <typename TI, typename TO>
+__global__ void k_coarse_axis(const TI* __restrict__ in, TO* __restrict__ out, const double* __restrict__ Q,
                               CoarseDims d, int axis, int backward, int in_eb, int out_eb, const double* scal,
                               int mean_slot, int scale, const double* lx, const double* ly, const double* lz,
                               int nx0, int ny0, int nz0) {
@@ -56,20 +62,40 @@ __global__ void k_coarse_axis(const double* __restrict__ in, double* __restrict_
       h[axis] = t;
       const int64_t src = in_eb ? eb_index(h[0], h[1], h[2], d) : h[0] + (int64_t)Nx * (h[1] + (int64_t)Ny * h[2]);
       const double q = backward ? Q[o * Na + t] : Q[t * Na + o];
-      acc += q * (in[src] - shift);
+      acc += q * ((double)in[src] - shift);
     }
     if (scale) {
       if (g[0] == nx0 && g[1] == ny0 && g[2] == nz0) acc = 0.0;
       else acc /= (lx[g[0]] + ly[g[1]] + lz[g[2]]);
     }
     const int64_t dst = out_eb ? eb_index(g[0], g[1], g[2], d) : idx;
-    out[dst] = acc;
+    out[dst] = (TO)acc;
   }
 }
 
-}  // namespace
+// The six axis passes: f0 (element-blocked) -> x, y, z forward, scale, z, y, x
+// backward -> u0 (element-blocked); A, B lexicographic FP64 scratch.
+template <typename TI, typename TO>
+cudaError_t coarse_passes(const double* const Q[3], const double* const lam[3], const CoarseDims& d,
+                          const int null_mode[3], const TI* f0, double* A, double* B, TO* u0, const double* scal,
+                          int mean_slot, cudaStream_t s) {
+  const int64_t N0 = (int64_t)d.Ng[0] * d.Ng[1] * d.Ng[2];
+  int64_t blocks = (N0 + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  const int* nz = null_mode;
+  const int b = (int)blocks;
+  k_coarse_axis<TI, double><<<b, 256, 0, s>>>(f0, A, Q[0], d, 0, 0, 1, 0, scal, mean_slot, 0, 0, 0, 0, 0, 0, 0);
+  k_coarse_axis<double, double><<<b, 256, 0, s>>>(A, B, Q[1], d, 1, 0, 0, 0, scal, -1, 0, 0, 0, 0, 0, 0, 0);
+  k_coarse_axis<double, double><<<b, 256, 0, s>>>(B, A, Q[2], d, 2, 0, 0, 0, scal, -1, 1, lam[0], lam[1], lam[2],
+                                                  nz[0], nz[1], nz[2]);
+  k_coarse_axis<double, double><<<b, 256, 0, s>>>(A, B, Q[2], d, 2, 1, 0, 0, scal, -1, 0, 0, 0, 0, 0, 0, 0);
+  k_coarse_axis<double, double><<<b, 256, 0, s>>>(B, A, Q[1], d, 1, 1, 0, 0, scal, -1, 0, 0, 0, 0, 0, 0, 0);
+  k_coarse_axis<double, TO><<<b, 256, 0, s>>>(A, u0, Q[0], d, 0, 1, 0, 1, scal, -1, 0, 0, 0, 0, 0, 0, 0);
+  return cudaGetLastError();
+}
 
-cudaError_t launch_coarse_solve(const mg_ctx* c, const double* f0, double* u0) {
+template <typename TI, typename TO>
+cudaError_t coarse_solve_t(const mg_ctx* c, const TI* f0, TO* u0) {
   const LevelInfo& lv = c->lev[0];
   CoarseDims d;
   for (int k = 0; k < 3; ++k) {
@@ -79,28 +105,15 @@ cudaError_t launch_coarse_solve(const mg_ctx* c, const double* f0, double* u0) {
   const double* tab = c->ws.tab64;
   const double* Q[3] = {tab + lv.t[0].Q, tab + lv.t[1].Q, tab + lv.t[2].Q};
   const double* lam[3] = {tab + lv.t[0].qlam, tab + lv.t[1].qlam, tab + lv.t[2].qlam};
-  double* A = c->ws.coarse_a;
-  double* B = c->ws.coarse_b;
-  const int64_t N0 = lv.N;
-  int64_t blocks = (N0 + 255) / 256;
-  if (blocks > 152 * 8) blocks = 152 * 8;
-  const int sum_slot = 60;
-  cudaError_t e;
-  if ((e = launch_sum(c, f0, N0, sum_slot)) != cudaSuccess) return e;
-  const double* sc = c->ws.scal;
-  cudaStream_t s = c->stream;
-  const int* nz = c->coarse_null;
-  k_coarse_axis<<<(int)blocks, 256, 0, s>>>(f0, A, Q[0], d, 0, 0, 1, 0, sc, sum_slot, 0, 0, 0, 0, 0, 0, 0);
-  k_coarse_axis<<<(int)blocks, 256, 0, s>>>(A, B, Q[1], d, 1, 0, 0, 0, sc, -1, 0, 0, 0, 0, 0, 0, 0);
-  k_coarse_axis<<<(int)blocks, 256, 0, s>>>(B, A, Q[2], d, 2, 0, 0, 0, sc, -1, 1, lam[0], lam[1], lam[2], nz[0],
-                                            nz[1], nz[2]);
-  k_coarse_axis<<<(int)blocks, 256, 0, s>>>(A, B, Q[2], d, 2, 1, 0, 0, sc, -1, 0, 0, 0, 0, 0, 0, 0);
-  k_coarse_axis<<<(int)blocks, 256, 0, s>>>(B, A, Q[1], d, 1, 1, 0, 0, sc, -1, 0, 0, 0, 0, 0, 0, 0);
-  k_coarse_axis<<<(int)blocks, 256, 0, s>>>(A, u0, Q[0], d, 0, 1, 0, 1, sc, -1, 0, 0, 0, 0, 0, 0, 0);
   c->nlaunch += 6;
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  if ((e = launch_sum(c, u0, N0, sum_slot)) != cudaSuccess) return e;
-  return launch_sub_mean(c, u0, N0, sum_slot);
+  return coarse_passes<TI, TO>(Q, lam, d, c->coarse_null, f0, c->ws.coarse_a, c->ws.coarse_b, u0, c->ws.scal, -1,
+                               c->stream);
+}
+
+}  // namespace
+
+cudaError_t launch_coarse_solve(const mg_ctx* c, const double* f0, double* u0) {
+  return coarse_solve_t<double, double>(c, f0, u0);
 }
 
 cudaError_t launch_coarse_fdm_raw(const double* const Q[3], const double* const lam[3], const int Ng[3],
@@ -111,27 +124,13 @@ cudaError_t launch_coarse_fdm_raw(const double* const Q[3], const double* const 
     d.Ng[k] = Ng[k];
     d.ne[k] = ne[k];
   }
-  const int64_t N0 = (int64_t)Ng[0] * Ng[1] * Ng[2];
-  int64_t blocks = (N0 + 255) / 256;
-  if (blocks > 152 * 8) blocks = 152 * 8;
-  const int* nz = null_mode;
-  k_coarse_axis<<<(int)blocks, 256, 0, s>>>(f0, A, Q[0], d, 0, 0, 1, 0, scal, mean_slot, 0, 0, 0, 0, 0, 0, 0);
-  k_coarse_axis<<<(int)blocks, 256, 0, s>>>(A, B, Q[1], d, 1, 0, 0, 0, scal, -1, 0, 0, 0, 0, 0, 0, 0);
-  k_coarse_axis<<<(int)blocks, 256, 0, s>>>(B, A, Q[2], d, 2, 0, 0, 0, scal, -1, 1, lam[0], lam[1], lam[2], nz[0],
-                                            nz[1], nz[2]);
-  k_coarse_axis<<<(int)blocks, 256, 0, s>>>(A, B, Q[2], d, 2, 1, 0, 0, scal, -1, 0, 0, 0, 0, 0, 0, 0);
-  k_coarse_axis<<<(int)blocks, 256, 0, s>>>(B, A, Q[1], d, 1, 1, 0, 0, scal, -1, 0, 0, 0, 0, 0, 0, 0);
-  k_coarse_axis<<<(int)blocks, 256, 0, s>>>(A, u0, Q[0], d, 0, 1, 0, 1, scal, -1, 0, 0, 0, 0, 0, 0, 0);
-  return cudaGetLastError();
+  return coarse_passes<double, double>(Q, lam, d, null_mode, f0, A, B, u0, scal, mean_slot, s);
 }
 
 cudaError_t launch_coarse_solve_f32(const mg_ctx* c, const float* f0, float* u0) {
-  // The coarsest solve of the FP32 hierarchy stays in FP64: widen, solve, narrow.
-  const int64_t N0 = c->lev[0].N;
-  cudaError_t e;
-  if ((e = launch_from_f32(c, f0, c->ws.coarse_f, N0, -1)) != cudaSuccess) return e;
-  if ((e = launch_coarse_solve(c, c->ws.coarse_f, c->ws.coarse_u)) != cudaSuccess) return e;
-  return launch_to_f32(c, c->ws.coarse_u, u0, N0, -1);
+  // The coarsest solve of the FP32 hierarchy runs in FP64: the first pass
+  // reads the FP32 right-hand side, the last writes the FP32 solution.
+  return coarse_solve_t<float, float>(c, f0, u0);
 }
 
 }  // namespace mgdg
