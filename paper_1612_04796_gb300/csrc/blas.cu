@@ -61,6 +61,104 @@ __global__ void k_axpy2(double* __restrict__ x, const double* __restrict__ p, do
   }
 }
 
+// The CG update with the partial sums of the new r and r^2 (columns 0, 1).
+__global__ void __launch_bounds__(kThreads) k_cg_update(double* __restrict__ x, const double* __restrict__ p,
+                                                        double* __restrict__ r, const double* __restrict__ q,
+                                                        int64_t n, double* scal, double* partial) {
+  __shared__ double sh[kThreads];
+  const double alpha = scal[kSlotRZ] / scal[kSlotPQ];
+  if (blockIdx.x == 0 && threadIdx.x == 0) scal[kSlotAlpha] = alpha;
+  double s1 = 0.0, s2 = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    x[i] += alpha * p[i];
+    const double ri = r[i] - alpha * q[i];
+    r[i] = ri;
+    s1 += ri;
+    s2 += ri * ri;
+  }
+  const double b1 = block_reduce(s1, sh);
+  __syncthreads();
+  const double b2 = block_reduce(s2, sh);
+  if (threadIdx.x == 0) {
+    partial[blockIdx.x] = b1;
+    partial[gridDim.x + blockIdx.x] = b2;
+  }
+}
+
+// Sum `cols` columns of nb partials each, in a fixed order, into v[0 .. cols).
+__device__ void final_columns(const double* partial, int nb, int cols, double* v, double* sh) {
+  for (int k = 0; k < cols; ++k) {
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) acc += partial[k * nb + i];
+    v[k] = block_reduce(acc, sh);
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_cg_update_final(const double* partial, int nb, double* scal,
+                                                              int64_t n) {
+  __shared__ double sh[kThreads];
+  double v[2];
+  final_columns(partial, nb, 2, v, sh);
+  if (threadIdx.x == 0) {
+    scal[kSlotSum] = v[0];
+    scal[kSlotRR] = fmax(v[1] - v[0] * v[0] / (double)n, 0.0);
+  }
+}
+
+template <typename TZ>
+__device__ __forceinline__ double z_scale(const double* scal) {
+  if (sizeof(TZ) == sizeof(double)) return 1.0;
+  const double nrm = sqrt(scal[kSlotRR]);
+  return nrm > 0.0 ? nrm : 1.0;
+}
+
+// Partial sums of z, z.q, z.r, q, r (columns 0 .. 4).
+template <typename TZ>
+__global__ void __launch_bounds__(kThreads) k_cg_sums(const TZ* __restrict__ zs, const double* __restrict__ q,
+                                                      const double* __restrict__ r, int64_t n, const double* scal,
+                                                      double* partial) {
+  __shared__ double sh[kThreads];
+  const double zsc = z_scale<TZ>(scal);
+  double a[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double z = (double)zs[i] * zsc, qi = q[i], ri = r[i];
+    a[0] += z;
+    a[1] += z * qi;
+    a[2] += z * ri;
+    a[3] += qi;
+    a[4] += ri;
+  }
+  for (int k = 0; k < 5; ++k) {
+    const double b = block_reduce(a[k], sh);
+    __syncthreads();
+    if (threadIdx.x == 0) partial[k * gridDim.x + blockIdx.x] = b;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_cg_sums_final(const double* partial, int nb, double* scal, int64_t n) {
+  __shared__ double sh[kThreads];
+  double v[5];
+  final_columns(partial, nb, 5, v, sh);
+  if (threadIdx.x == 0) {
+    const double inv = 1.0 / (double)n;
+    const double zq = v[1] - v[0] * v[3] * inv;  // z'.q'
+    const double zr = v[2] - v[0] * v[4] * inv;  // z'.r'
+    scal[kSlotZQ] = zq;
+    scal[kSlotBeta] = -scal[kSlotAlpha] * zq / scal[kSlotRZ];
+    scal[kSlotMuZ] = v[0] * inv;
+    scal[kSlotRZ] = zr;
+  }
+}
+
+// p = (z - mean(z)) + beta p
+template <typename TZ>
+__global__ void k_cg_newdir(double* __restrict__ p, const TZ* __restrict__ zs, int64_t n, const double* scal) {
+  const double zsc = z_scale<TZ>(scal), muz = scal[kSlotMuZ], beta = scal[kSlotBeta];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = ((double)zs[i] * zsc - muz) + beta * p[i];
+}
+
 __global__ void k_add(double* __restrict__ y, const double* __restrict__ x, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     y[i] += x[i];
@@ -206,6 +304,28 @@ cudaError_t launch_axpy2(const mg_ctx* c, double* x, const double* p, double* r,
   c->nlaunch += 1;
   return cudaGetLastError();
 }
+
+cudaError_t launch_cg_update(const mg_ctx* c, double* x, const double* p, double* r, const double* q, int64_t n) {
+  k_cg_update<<<kRedBlocks, kThreads, 0, c->stream>>>(x, p, r, q, n, c->ws.scal, c->ws.red);
+  k_cg_update_final<<<1, kThreads, 0, c->stream>>>(c->ws.red, kRedBlocks, c->ws.scal, n);
+  c->nlaunch += 2;
+  return cudaGetLastError();
+}
+
+template <typename TZ>
+cudaError_t launch_cg_direction(const mg_ctx* c, double* p, const TZ* z, const double* q, const double* r,
+                                int64_t n) {
+  k_cg_sums<TZ><<<kRedBlocks, kThreads, 0, c->stream>>>(z, q, r, n, c->ws.scal, c->ws.red);
+  k_cg_sums_final<<<1, kThreads, 0, c->stream>>>(c->ws.red, kRedBlocks, c->ws.scal, n);
+  k_cg_newdir<TZ><<<grid_for(n), kThreads, 0, c->stream>>>(p, z, n, c->ws.scal);
+  c->nlaunch += 3;
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_cg_direction<double>(const mg_ctx*, double*, const double*, const double*,
+                                                 const double*, int64_t);
+template cudaError_t launch_cg_direction<float>(const mg_ctx*, double*, const float*, const double*, const double*,
+                                                int64_t);
 
 cudaError_t launch_add(const mg_ctx* c, double* y, const double* x, int64_t n) {
   k_add<<<grid_for(n), kThreads, 0, c->stream>>>(y, x, n);

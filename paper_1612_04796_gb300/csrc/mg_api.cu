@@ -131,7 +131,7 @@ Layout make_layout(const mg_ctx* c) {
   ly.cf = take(N0 * sizeof(double));
   ly.cu = take(N0 * sizeof(double));
   for (int k = 0; k < 8; ++k) ly.cg[k] = take(NL * sizeof(double));
-  ly.red = take(2 * kRedBlocks * sizeof(double));
+  ly.red = take(8 * kRedBlocks * sizeof(double));  // up to 5 partial-sum columns
   ly.scal = take(kNumSlots * sizeof(double));
   ly.status = take(256);
   int nmax = 8;
@@ -451,7 +451,8 @@ mg_status solve_impl(mg_ctx* c, double* u, const double* f, double tol, int maxi
     }
     while (!converged && it < maxit) {
       ++it;
-      // q = A p, alpha = rz / pq, x += alpha p, r -= alpha q, r projected, rr = r.r
+      // q = A p, alpha = rz / pq, x += alpha p, r -= alpha q, rr = |r - mean(r)|^2.  The mean of r
+      // (zero up to rounding: 1^T q = 0) is taken out where r is used, not stored.
       CK(run_graph(c, kGraphCgA, x, f, [&]() -> cudaError_t {
         cudaError_t e;
         {
@@ -459,10 +460,7 @@ mg_status solve_impl(mg_ctx* c, double* u, const double* f, double tol, int maxi
           if ((e = launch_sipg<double>(c, L, p, nullptr, q, 0)) != cudaSuccess) return e;
         }
         if ((e = launch_dot(c, p, q, N, kSlotPQ)) != cudaSuccess) return e;
-        if ((e = launch_axpy2(c, x, p, r, q, N, kSlotRZ, kSlotPQ)) != cudaSuccess) return e;
-        if ((e = launch_sum(c, r, N, kSlotSum)) != cudaSuccess) return e;
-        if ((e = launch_sub_mean(c, r, N, kSlotSum)) != cudaSuccess) return e;
-        return launch_dot(c, r, r, N, kSlotRR);
+        return launch_cg_update(c, x, p, r, q, N);
       }));
       double v = read_scalar(c, kSlotRR, &err);
       CK(err);
@@ -474,15 +472,18 @@ mg_status solve_impl(mg_ctx* c, double* u, const double* f, double tol, int maxi
         break;
       }
       // z = B r projected; beta = z_new . (r_new - r_old) / (z_old . r_old) = -alpha (z_new . q) / rz_old;
-      // p = z + beta p; rz = r . z
+      // p = z + beta p; rz = r . z (one pass for the five sums, one for p)
       CK(run_graph(c, kGraphCgB, x, f, [&]() -> cudaError_t {
         cudaError_t e;
-        if ((e = precond(c, r, z)) != cudaSuccess) return e;
-        if ((e = launch_sum(c, z, N, kSlotSum)) != cudaSuccess) return e;
-        if ((e = launch_sub_mean(c, z, N, kSlotSum)) != cudaSuccess) return e;
-        if ((e = launch_dot(c, z, q, N, kSlotZQ)) != cudaSuccess) return e;
-        if ((e = launch_xpby(c, p, z, N, kSlotZQ, kSlotRZ, kSlotAlpha)) != cudaSuccess) return e;
-        return launch_dot(c, r, z, N, kSlotRZ);
+        if (c->opts.precision == MG_MIXED) {
+          float* f32 = lvec<float>(c->lev[L].f);
+          float* u32 = lvec<float>(c->lev[L].u);
+          if ((e = launch_to_f32(c, r, f32, N, kSlotRR)) != cudaSuccess) return e;
+          if ((e = vcycle_t<float>(c, u32, f32, true, false)) != cudaSuccess) return e;
+          return launch_cg_direction<float>(c, p, u32, q, r, N);
+        }
+        if ((e = vcycle_t<double>(c, z, r, true, false)) != cudaSuccess) return e;
+        return launch_cg_direction<double>(c, p, z, q, r, N);
       }));
     }
   }

@@ -29,6 +29,8 @@ enum Slot : int {
   kSlotMassF = 6,   // sum M f
   kSlotMass = 7,    // sum M
   kSlotScale = 8,   // norm used to scale FP32 preconditioner input
+  kSlotBeta = 9,    // CG beta
+  kSlotMuZ = 10,    // mean of the preconditioned residual z
   kSlotCoarse = 60, // coarse-solve mean
   kSlotSumT = 61,   // mean projection of FP32 vectors
   kNumSlots = 64
@@ -187,6 +189,15 @@ template <typename T>
 cudaError_t launch_sub_mean_t(const mg_ctx* c, T* x, int64_t n);
 cudaError_t launch_axpy2(const mg_ctx* c, double* x, const double* p, double* r, const double* q, int64_t n,
                          int num_slot, int den_slot);
+// Fused CG steps (one pass each plus a one-block finish):
+//  cg_update: alpha = scal[RZ] / scal[PQ]; x += alpha p; r -= alpha q;
+//             scal[Sum] = sum r, scal[RR] = |r - mean(r)|^2.
+//  cg_direction: z = zscale * zsrc (zscale = sqrt(scal[RR]) for an FP32 z, else 1);
+//             with z' = z - mean(z) and q' = q - mean(q), r' = r - mean(r):
+//             beta = -alpha z'.q' / scal[RZ]; scal[RZ] = z'.r'; p = z' + beta p.
+cudaError_t launch_cg_update(const mg_ctx* c, double* x, const double* p, double* r, const double* q, int64_t n);
+template <typename TZ>
+cudaError_t launch_cg_direction(const mg_ctx* c, double* p, const TZ* z, const double* q, const double* r, int64_t n);
 cudaError_t launch_add(const mg_ctx* c, double* y, const double* x, int64_t n);  // y += x
 cudaError_t launch_xpby(const mg_ctx* c, double* p, const double* z, int64_t n, int num_slot, int den_slot,
                         int alpha_slot);
