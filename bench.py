@@ -97,6 +97,8 @@ def parse_args():
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
     ap.add_argument("--overlap", type=int, default=None, help="override N_O of the workload")
     ap.add_argument("--precision", default=None, choices=["fp64", "mixed"], help="override the workload's precision")
+    ap.add_argument("--outer-df64", action="store_true",
+                    help="mixed runs: outer operator products q = A p in double-float (FP32-pair) arithmetic")
     ap.add_argument("--tensor-cores", default="off", choices=["off", "on", "auto"],
                     help="FP32 smoother contractions in the mixed runs: CUDA cores, tensor cores (tcgen05, "
                          "TF32) where the tiles fit, or per level the faster of the two (timed at setup)")
@@ -393,31 +395,39 @@ def run_mg(args):
         line["e2e"] = {"value": world * N * k_e2e / e2e_s, "unit": "DOF/s", "h2d_bytes_per_step": 2 * N * 8,
                        "d2h_bytes_per_step": N * 8, "steps": k_e2e}
 
-        # mixed precision: FP32 V(1,1) preconditioner inside FP64 inexact PCG
-        sm_ = pkg.MGSolver(W["lengths"], W["elements"], W["P"], overlap=W["overlap_layers"], precision="mixed",
-                           device=dev, tensor_cores=TC_MODE[args.tensor_cores])
-        um = torch.zeros(N, dtype=torch.float64, device=dev)
-        for _ in range(args.warmup):
-            um.zero_()
-            sm_.solve(b, um, tol=W["tol"], use_cg=True)
-        barrier()
-        mix_ms, its_ml = timed_steps(sm_, um, use_cg=True)
-        its_m = its_ml[-1]
-        barrier()
-        sm_.profile(True)
-        mix_prof_ms, _ = timed_steps(sm_, um, use_cg=True)
-        sm_.profile(False)
-        true_rel = float(torch.linalg.norm(s.residual(um, b)) / torch.linalg.norm(b))
-        err = float(torch.max(torch.abs(um - u)) / torch.max(torch.abs(u)))
-        mix_total = max_over_ranks(sum(mix_ms) / 1e3)
-        line["mixed"] = {"value": world * N * args.steps / mix_total, "unit": "DOF/s",
-                         "ms_per_step": sum(mix_ms) / args.steps, "iterations": its_m,
-                         "solver": "MG-CG: FP32 V(1,1) preconditioner, FP64 inexact PCG",
-                         "fdm_tensor_cores": args.tensor_cores,
-                         "fdm_tensor_cores_by_level": [sm_.fdm_tensor_cores(l) for l in range(1, sm_.L + 1)],
-                         "true_relres": true_rel, "max_rel_diff_vs_fp64_solution": err,
-                         "time_share_of_step": profile_shares(sm_, sum(mix_prof_ms)),
-                         "ms_per_step_by_kernel_level": profile_levels(sm_, args.steps)}
+        # mixed precision: FP32 V(1,1) preconditioner inside FP64 inexact PCG, with the outer
+        # products q = A p in FP64 ("mixed") and in double-float pairs ("mixed_df64")
+        def mixed_leg(outer_df64):
+            sm_ = pkg.MGSolver(W["lengths"], W["elements"], W["P"], overlap=W["overlap_layers"], precision="mixed",
+                               device=dev, tensor_cores=TC_MODE[args.tensor_cores], outer_df64=outer_df64)
+            um = torch.zeros(N, dtype=torch.float64, device=dev)
+            for _ in range(args.warmup):
+                um.zero_()
+                sm_.solve(b, um, tol=W["tol"], use_cg=True)
+            barrier()
+            mix_ms, its_ml = timed_steps(sm_, um, use_cg=True)
+            barrier()
+            sm_.profile(True)
+            mix_prof_ms, _ = timed_steps(sm_, um, use_cg=True)
+            sm_.profile(False)
+            true_rel = float(torch.linalg.norm(s.residual(um, b)) / torch.linalg.norm(b))
+            err = float(torch.max(torch.abs(um - u)) / torch.max(torch.abs(u)))
+            mix_total = max_over_ranks(sum(mix_ms) / 1e3)
+            leg = {"value": world * N * args.steps / mix_total, "unit": "DOF/s",
+                   "ms_per_step": sum(mix_ms) / args.steps, "iterations": its_ml[-1],
+                   "solver": "MG-CG: FP32 V(1,1) preconditioner, FP64 inexact PCG",
+                   "outer_operator": "double-float (FP32 pairs, ~48-bit)" if outer_df64 else "FP64",
+                   "fdm_tensor_cores": args.tensor_cores,
+                   "fdm_tensor_cores_by_level": [sm_.fdm_tensor_cores(l) for l in range(1, sm_.L + 1)],
+                   "true_relres_fp64": true_rel, "max_rel_diff_vs_fp64_solution": err,
+                   "time_share_of_step": profile_shares(sm_, sum(mix_prof_ms)),
+                   "ms_per_step_by_kernel_level": profile_levels(sm_, args.steps)}
+            sm_.close()
+            return leg
+
+        line["mixed"] = mixed_leg(args.outer_df64)
+        if not args.outer_df64:
+            line["mixed_df64"] = mixed_leg(True)
 
     if rank == 0 and not args.no_cpu_baseline:
         Ns, ts, _, its_s = oracle_sample_solve()
@@ -446,7 +456,7 @@ def run_workload(args):
     dev = torch.device("cuda", torch.cuda.current_device())
     pkg.load_library()
     extra = {k: W[k] for k in ("overlap_mode", "overlap_frac", "ns_growth") if k in W}
-    extra_mixed = dict(extra, tensor_cores=TC_MODE[args.tensor_cores])
+    extra_mixed = dict(extra, tensor_cores=TC_MODE[args.tensor_cores], outer_df64=args.outer_df64)
     s = pkg.MGSolver(W["lengths"], W["elements"], W["P"], overlap=W["overlap_layers"], precision=W["precision"],
                      device=dev, **(extra_mixed if W["precision"] == "mixed" else extra))
     s64 = s if W["precision"] == "fp64" else pkg.MGSolver(W["lengths"], W["elements"], W["P"],
@@ -493,6 +503,7 @@ def run_workload(args):
     true_rel = float(torch.linalg.norm(s64.residual(u, b)) / torch.linalg.norm(b))
     if W["precision"] == "mixed":
         W["fdm_tensor_cores"] = args.tensor_cores
+        W["outer_operator"] = "double-float (FP32 pairs)" if args.outer_df64 else "FP64"
         W["fdm_tensor_cores_by_level"] = [s.fdm_tensor_cores(l) for l in range(1, s.L + 1)]
     lev = s.L
     md = [s.P + 1 + 2 * s.layers(lev, d) for d in range(3)]

@@ -89,6 +89,9 @@ typedef struct {
                             kernel; 2 = per level whichever of the two mg_bind_workspace
                             measures faster (the choice, and so the rounding, may differ
                             between contexts) */
+  int outer_df64;        /* MG_MIXED with use_cg: 1 = the outer products q = A p in double-float
+                            arithmetic (pairs of FP32, about 48 significant bits; FP64 vectors,
+                            inner products and updates); 0 = FP64 (default) */
   void* stream;          /* cudaStream_t; NULL = default stream */
 } mg_opts;
 
@@ -212,6 +215,12 @@ mg_status mg_solve(mg_ctx* ctx, double* u, const double* f, double tol, int maxi
  * fastest): copies f (and the initial u) in, solves, copies u out. */
 mg_status mg_solve_host(mg_ctx* ctx, double* u_host, const double* f_host, double tol, int maxit, int use_cg,
                         int* iters, double* relres, double* history);
+
+/* mg_apply_sipg_df64 -- Au = A_l u like mg_apply_sipg (FP64 vectors), with the
+ * arithmetic in double-float (about 48 significant bits); the operator of the
+ * outer iteration when mg_opts.outer_df64 = 1.  Uses the smoother's
+ * correction buffer as scratch. */
+mg_status mg_apply_sipg_df64(mg_ctx* ctx, int level, const double* u, double* Au);
 
 /* FP32 versions of the level kernels used by the MG_MIXED preconditioner
  * (same semantics as the FP64 entry points; FP32 tables and arithmetic). */

@@ -151,12 +151,35 @@ __global__ void __launch_bounds__(kThreads) k_cg_sums_final(const double* partia
   }
 }
 
-// p = (z - mean(z)) + beta p
+// p = (z - mean(z)) + beta p; pdf (if given) receives p split into double-float pairs
 template <typename TZ>
-__global__ void k_cg_newdir(double* __restrict__ p, const TZ* __restrict__ zs, int64_t n, const double* scal) {
+__global__ void k_cg_newdir(double* __restrict__ p, const TZ* __restrict__ zs, int64_t n, const double* scal,
+                            df64* __restrict__ pdf) {
   const double zsc = z_scale<TZ>(scal), muz = scal[kSlotMuZ], beta = scal[kSlotBeta];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = ((double)zs[i] * zsc - muz) + beta * p[i];
+    p[i] = v;
+    if (pdf) pdf[i] = df_from_double(v);
+  }
+}
+
+__global__ void k_split_df64(const double* __restrict__ x, df64* __restrict__ y, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    p[i] = ((double)zs[i] * zsc - muz) + beta * p[i];
+    y[i] = df_from_double(x[i]);
+}
+
+// q = qdf as FP64 and the partial sums of p . q
+__global__ void __launch_bounds__(kThreads) k_dot_dfq(const double* __restrict__ p, const df64* __restrict__ qdf,
+                                                      double* __restrict__ q, int64_t n, double* partial) {
+  __shared__ double sh[kThreads];
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double qi = df_to_double(qdf[i]);
+    q[i] = qi;
+    acc += p[i] * qi;
+  }
+  const double b = block_reduce(acc, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = b;
 }
 
 __global__ void k_add(double* __restrict__ y, const double* __restrict__ x, int64_t n) {
@@ -313,19 +336,32 @@ cudaError_t launch_cg_update(const mg_ctx* c, double* x, const double* p, double
 }
 
 template <typename TZ>
-cudaError_t launch_cg_direction(const mg_ctx* c, double* p, const TZ* z, const double* q, const double* r,
-                                int64_t n) {
+cudaError_t launch_cg_direction(const mg_ctx* c, double* p, const TZ* z, const double* q, const double* r, int64_t n,
+                                df64* pdf) {
   k_cg_sums<TZ><<<kRedBlocks, kThreads, 0, c->stream>>>(z, q, r, n, c->ws.scal, c->ws.red);
   k_cg_sums_final<<<1, kThreads, 0, c->stream>>>(c->ws.red, kRedBlocks, c->ws.scal, n);
-  k_cg_newdir<TZ><<<grid_for(n), kThreads, 0, c->stream>>>(p, z, n, c->ws.scal);
+  k_cg_newdir<TZ><<<grid_for(n), kThreads, 0, c->stream>>>(p, z, n, c->ws.scal, pdf);
   c->nlaunch += 3;
   return cudaGetLastError();
 }
 
 template cudaError_t launch_cg_direction<double>(const mg_ctx*, double*, const double*, const double*,
-                                                 const double*, int64_t);
+                                                 const double*, int64_t, df64*);
 template cudaError_t launch_cg_direction<float>(const mg_ctx*, double*, const float*, const double*, const double*,
-                                                int64_t);
+                                                int64_t, df64*);
+
+cudaError_t launch_split_df64(const mg_ctx* c, const double* x, df64* y, int64_t n) {
+  k_split_df64<<<grid_for(n), kThreads, 0, c->stream>>>(x, y, n);
+  c->nlaunch += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dot_dfq(const mg_ctx* c, const double* p, const df64* qdf, double* q, int64_t n, int slot) {
+  k_dot_dfq<<<kRedBlocks, kThreads, 0, c->stream>>>(p, qdf, q, n, c->ws.red);
+  k_final<<<1, kThreads, 0, c->stream>>>(c->ws.red, kRedBlocks, c->ws.scal, slot);
+  c->nlaunch += 2;
+  return cudaGetLastError();
+}
 
 cudaError_t launch_add(const mg_ctx* c, double* y, const double* x, int64_t n) {
   k_add<<<grid_for(n), kThreads, 0, c->stream>>>(y, x, n);

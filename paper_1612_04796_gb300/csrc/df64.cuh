@@ -1,0 +1,72 @@
+// Double-float arithmetic: a value is the unevaluated sum hi + lo of two FP32
+// numbers with |lo| <= ulp(hi) / 2, about 48 significant bits.  On this GPU
+// FP32 runs 61 times faster than FP64, so pipe-bound FP64 kernels can run
+// their arithmetic in pairs of FP32 instead.
+//
+// The operations are the classical error-free transformations: Knuth's
+// TwoSum (the rounding error of a + b, exact for any a, b), Dekker's
+// Fast-TwoSum renormalisation (exact when |a| >= |b|) and the FMA form of the
+// product error (fma(a, b, -fl(a b)) is the exact rounding error of a b).
+// Every step uses the explicitly rounded intrinsics, so the compiler cannot
+// contract or reassociate them.  Addition ("sloppy" variant: the two low
+// parts are added once) and multiplication each cost 8-10 FP32 operations;
+// their relative error is a small multiple of 2^-48 except when the high
+// parts of a sum cancel, where the error stays a small multiple of 2^-48
+// times the operands.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace mgdg {
+
+struct df64 {
+  float hi, lo;
+  __host__ __device__ df64() {}
+  __host__ __device__ df64(float h, float l) : hi(h), lo(l) {}
+  __device__ df64(int v) : hi((float)v), lo(0.f) {}
+  __device__ df64(float v) : hi(v), lo(0.f) {}
+};
+
+// s + e = a + b exactly (Knuth).
+__device__ __forceinline__ df64 df_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return df64(s, e);
+}
+
+// s + e = a + b exactly when |a| >= |b| (Dekker).
+__device__ __forceinline__ df64 df_fast_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return df64(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+
+__device__ __forceinline__ df64 operator+(df64 a, df64 b) {
+  const df64 s = df_two_sum(a.hi, b.hi);
+  return df_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+
+__device__ __forceinline__ df64 operator-(df64 a) { return df64(-a.hi, -a.lo); }
+
+__device__ __forceinline__ df64 operator-(df64 a, df64 b) { return a + (-b); }
+
+__device__ __forceinline__ df64 operator*(df64 a, df64 b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return df_fast_two_sum(p, e);
+}
+
+__device__ __forceinline__ df64& operator+=(df64& a, df64 b) { return a = a + b; }
+__device__ __forceinline__ df64& operator-=(df64& a, df64 b) { return a = a - b; }
+
+// Nearest double-float to x and back (these conversions use the FP64 pipe).
+__device__ __forceinline__ df64 df_from_double(double x) {
+  const float h = __double2float_rn(x);
+  return df64(h, __double2float_rn(x - (double)h));
+}
+
+__device__ __forceinline__ double df_to_double(df64 a) { return (double)a.hi + (double)a.lo; }
+
+}  // namespace mgdg

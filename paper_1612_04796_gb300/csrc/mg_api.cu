@@ -100,7 +100,7 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 // ---- workspace layout ----
 struct Layout {
-  size_t tab64, tab32, lev_u[kMaxLevels], lev_f[kMaxLevels], lev_r[kMaxLevels], corr, ca, cb, cf, cu, cg[8], red,
+  size_t tab64, tab32, tabdf, lev_u[kMaxLevels], lev_f[kMaxLevels], lev_r[kMaxLevels], corr, ca, cb, cf, cu, cg[8], red,
       scal, status, jac, total;
   int64_t jac_count;
 };
@@ -115,6 +115,7 @@ Layout make_layout(const mg_ctx* c) {
   };
   ly.tab64 = take(c->ws.tab_count * sizeof(double));
   ly.tab32 = take(c->ws.tab_count * sizeof(float));
+  ly.tabdf = take(c->ws.tab_count * sizeof(df64));
   int64_t corr = 0;
   for (int l = 0; l <= c->L; ++l) {
     const LevelInfo& lv = c->lev[l];
@@ -442,12 +443,18 @@ mg_status solve_impl(mg_ctx* c, double* u, const double* f, double tol, int maxi
     if (history) history[0] = r0;
     if (!std::isfinite(r0)) return fail(c, MG_EINVAL, "initial residual is not finite (NaN or Inf in u or f)");
     converged = r0 == 0.0;
+    // double-float copies of p and q for the outer operator (mg_opts.outer_df64), in the
+    // smoother's correction buffer: written after each preconditioner, read before the next
+    const bool df = c->opts.outer_df64 && c->opts.precision == MG_MIXED;
+    df64* pdf = df ? static_cast<df64*>(c->ws.corr) : nullptr;
+    df64* qdf = df ? pdf + N : nullptr;
     if (!converged) {
       CK(precond(c, r, z));
       CK(launch_sum(c, z, N, kSlotSum));
       CK(launch_sub_mean(c, z, N, kSlotSum));
       CK(cudaMemcpyAsync(p, z, N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
       CK(launch_dot(c, r, z, N, kSlotRZ));
+      if (df) CK(launch_split_df64(c, p, pdf, N));
     }
     while (!converged && it < maxit) {
       ++it;
@@ -455,11 +462,19 @@ mg_status solve_impl(mg_ctx* c, double* u, const double* f, double tol, int maxi
       // (zero up to rounding: 1^T q = 0) is taken out where r is used, not stored.
       CK(run_graph(c, kGraphCgA, x, f, [&]() -> cudaError_t {
         cudaError_t e;
-        {
-          ProfScope ps(c, kProfSipg, L);
-          if ((e = launch_sipg<double>(c, L, p, nullptr, q, 0)) != cudaSuccess) return e;
+        if (df) {
+          {
+            ProfScope ps(c, kProfSipg, L);
+            if ((e = launch_sipg<df64>(c, L, pdf, nullptr, qdf, 0)) != cudaSuccess) return e;
+          }
+          if ((e = launch_dot_dfq(c, p, qdf, q, N, kSlotPQ)) != cudaSuccess) return e;
+        } else {
+          {
+            ProfScope ps(c, kProfSipg, L);
+            if ((e = launch_sipg<double>(c, L, p, nullptr, q, 0)) != cudaSuccess) return e;
+          }
+          if ((e = launch_dot(c, p, q, N, kSlotPQ)) != cudaSuccess) return e;
         }
-        if ((e = launch_dot(c, p, q, N, kSlotPQ)) != cudaSuccess) return e;
         return launch_cg_update(c, x, p, r, q, N);
       }));
       double v = read_scalar(c, kSlotRR, &err);
@@ -480,7 +495,7 @@ mg_status solve_impl(mg_ctx* c, double* u, const double* f, double tol, int maxi
           float* u32 = lvec<float>(c->lev[L].u);
           if ((e = launch_to_f32(c, r, f32, N, kSlotRR)) != cudaSuccess) return e;
           if ((e = vcycle_t<float>(c, u32, f32, true, false)) != cudaSuccess) return e;
-          return launch_cg_direction<float>(c, p, u32, q, r, N);
+          return launch_cg_direction<float>(c, p, u32, q, r, N, pdf);
         }
         if ((e = vcycle_t<double>(c, z, r, true, false)) != cudaSuccess) return e;
         return launch_cg_direction<double>(c, p, z, q, r, N);
@@ -513,6 +528,7 @@ void mg_default_opts(mg_opts* o) {
   o->ns_growth = 1;
   o->precision = MG_FP64;
   o->fdm_tensor_cores = 0;
+  o->outer_df64 = 0;
   o->stream = nullptr;
 }
 
@@ -529,6 +545,7 @@ mg_status mg_setup(double lx, double ly, double lz, int nx, int ny, int nz, int 
   if (o.ns_pre < 0 || o.ns_post < 0 || o.ns_growth < 1 || o.ns_pre + o.ns_post < 1) return MG_EINVAL;
   if (o.precision != MG_FP64 && o.precision != MG_MIXED) return MG_EINVAL;
   if (o.fdm_tensor_cores < 0 || o.fdm_tensor_cores > 2) return MG_EINVAL;
+  if (o.outer_df64 < 0 || o.outer_df64 > 1) return MG_EINVAL;
   if (o.weight_profile < MG_WEIGHT_QUINTIC || o.weight_profile > MG_WEIGHT_QUINTIC_NORMALISED) return MG_EINVAL;
   if (o.overlap_mode != MG_OVERLAP_LAYERS && o.overlap_mode != MG_OVERLAP_WIDTH && o.overlap_mode != MG_OVERLAP_MAX)
     return MG_EINVAL;
@@ -649,6 +666,7 @@ mg_status mg_bind_workspace(mg_ctx* c, void* dptr, size_t bytes) {
   w.bytes = bytes;
   w.tab64 = reinterpret_cast<double*>(b + ly.tab64);
   w.tab32 = reinterpret_cast<float*>(b + ly.tab32);
+  w.tabdf = reinterpret_cast<df64*>(b + ly.tabdf);
   for (int l = 0; l <= c->L; ++l) {
     c->lev[l].u = b + ly.lev_u[l];
     c->lev[l].f = b + ly.lev_f[l];
@@ -693,6 +711,21 @@ long long mg_num_dofs(const mg_ctx* c, int level) {
 }
 
 int mg_level_layers(const mg_ctx* c, int level) { return mg_level_layers_dir(c, level, 0); }
+
+mg_status mg_apply_sipg_df64(mg_ctx* c, int level, const double* u, double* Au) {
+  mg_status s = need_ready(c);
+  if (s != MG_OK) return s;
+  if (!check_level(c, level, false)) return MG_EINVAL;
+  if (!u || !Au || u == Au) return fail(c, MG_EINVAL, "null or aliased vector");
+  const int64_t N = c->lev[level].N;
+  df64* udf = static_cast<df64*>(c->ws.corr);
+  df64* adf = udf + N;
+  if ((int64_t)(2 * N) > c->lev[c->L].N * 2) return fail(c, MG_EINVAL, "level too large for the scratch");
+  CK(launch_split_df64(c, u, udf, N));
+  CK(launch_sipg<df64>(c, level, udf, nullptr, adf, 0));
+  CK(launch_dot_dfq(c, u, adf, Au, N, kSlotSum));
+  return MG_OK;
+}
 
 mg_status mg_selftest_bounded_wait(mg_ctx* c, int level, int* timed_out) {
   mg_status s = need_ready(c);

@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "../../include/mgdg.h"
+#include "df64.cuh"
 
 namespace mgdg {
 
@@ -75,6 +76,7 @@ struct Workspace {
   size_t bytes = 0;
   double* tab64 = nullptr;
   float* tab32 = nullptr;
+  df64* tabdf = nullptr;       // the FP64 tables split into double-float pairs
   int64_t tab_count = 0;
   void* corr = nullptr;        // smoother corrections, Ne * m_x m_y m_z (largest level)
   double* coarse_a = nullptr;  // coarse FDM scratch, N_0 each
@@ -149,7 +151,7 @@ cudaError_t launch_setup_coarse_tables(const double len[3], const int ne[3], dou
 // ---- operator (sipg.cu) ----
 // out = mode==0 ? A u : f - A u, on level l, T = double | float.
 template <typename T>
-cudaError_t launch_sipg(const mg_ctx* c, int l, const T* u, const T* f, T* out, int residual);
+cudaError_t launch_sipg(const mg_ctx* c, int l, const T* u, const T* f, T* out, int residual);  // T: double, float, df64
 
 // ---- smoother (schwarz.cu) ----
 // Corrections of all subdomains from residual r into ws.corr, then
@@ -197,7 +199,12 @@ cudaError_t launch_axpy2(const mg_ctx* c, double* x, const double* p, double* r,
 //             beta = -alpha z'.q' / scal[RZ]; scal[RZ] = z'.r'; p = z' + beta p.
 cudaError_t launch_cg_update(const mg_ctx* c, double* x, const double* p, double* r, const double* q, int64_t n);
 template <typename TZ>
-cudaError_t launch_cg_direction(const mg_ctx* c, double* p, const TZ* z, const double* q, const double* r, int64_t n);
+cudaError_t launch_cg_direction(const mg_ctx* c, double* p, const TZ* z, const double* q, const double* r, int64_t n,
+                                df64* pdf = nullptr);
+// Double-float support of the outer operator: y = x split into pairs; and
+// q = to_double(qdf) with scal[slot] = p . q in the same pass.
+cudaError_t launch_split_df64(const mg_ctx* c, const double* x, df64* y, int64_t n);
+cudaError_t launch_dot_dfq(const mg_ctx* c, const double* p, const df64* qdf, double* q, int64_t n, int slot);
 cudaError_t launch_add(const mg_ctx* c, double* y, const double* x, int64_t n);  // y += x
 cudaError_t launch_xpby(const mg_ctx* c, double* p, const double* z, int64_t n, int num_slot, int den_slot,
                         int alpha_slot);

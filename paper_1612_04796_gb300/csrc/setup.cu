@@ -489,9 +489,11 @@ __global__ void k_setup_mass3(double* tab, int64_t mass3, int64_t mx, int64_t my
   }
 }
 
-__global__ void k_cast_tables(const double* src, float* dst, int64_t n) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+__global__ void k_cast_tables(const double* src, float* dst, df64* dst_df, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     dst[i] = (float)src[i];
+    dst_df[i] = df_from_double(src[i]);
+  }
 }
 
 }  // namespace
@@ -575,7 +577,7 @@ cudaError_t launch_setup(mg_ctx* c) {
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  k_cast_tables<<<256, 256, 0, s>>>(c->ws.tab64, c->ws.tab32, c->ws.tab_count);
+  k_cast_tables<<<256, 256, 0, s>>>(c->ws.tab64, c->ws.tab32, c->ws.tabdf, c->ws.tab_count);
   c->nlaunch += 1;
   return cudaGetLastError();
 }

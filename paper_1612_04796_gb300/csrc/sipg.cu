@@ -18,7 +18,9 @@
 // rank-1 terms fold into the even part (with a + c) and the odd part (with
 // a - c).  One thread per 1D line; the three directions are three passes over
 // the element, accumulated in the output vector; the last pass applies the
-// mass and forms f - A u.
+// mass and forms f - A u.  The kernels are templates on the arithmetic type:
+// FP64, FP32 (the multigrid of the mixed solve) or double-float pairs
+// (df64.cuh; the outer operator of the mixed solve on request).
 #include "mg_internal.h"
 
 namespace mgdg {
@@ -144,10 +146,13 @@ __global__ void __launch_bounds__(256) k_sipg(OpArgs<T> a) {
 }
 
 // Compile-time-size version of line_apply / k_sipg (lines in registers).
-template <typename T, int N>
+// NP > 1: the line's output pairs (i, P - i) are shared by NP threads, thread
+// `part` taking i = part, part + NP, ...; each reads the whole line.
+template <typename T, int N, int NP = 1>
 __device__ __forceinline__ void line_apply_n(const OpArgs<T>& a, int d, const T* __restrict__ ue,
                                              const T* __restrict__ uL, const T* __restrict__ uR, int st, T* o,
-                                             const T* __restrict__ fl, const T* __restrict__ m3, int mode) {
+                                             const T* __restrict__ fl, const T* __restrict__ m3, int mode,
+                                             int part = 0) {
   constexpr int P = N - 1, ne = (N + 1) / 2, no = N / 2;
   const T* __restrict__ ce = a.tab + a.ce[d];
   const T* __restrict__ co = a.tab + a.co[d];
@@ -175,7 +180,9 @@ __device__ __forceinline__ void line_apply_n(const OpArgs<T>& a, int d, const T*
   const T lo = g2_m0 * b - mu_m0 * av;
   const T hi = -(mu_m0 * cv + g2_m0 * dd);
 #pragma unroll
-  for (int i = 0; i < ne; ++i) {
+  for (int ii = 0; ii < (ne + NP - 1) / NP; ++ii) {
+    const int i = NP == 1 ? ii : part + ii * NP;
+    if (NP > 1 && i >= ne) break;
     T E = fe[i] * s;
 #pragma unroll
     for (int t = 0; t < ne; ++t) E += ce[i * ne + t] * ev[t];
@@ -253,16 +260,18 @@ __global__ void __launch_bounds__(256) k_sipg_n(OpArgs<T> a) {
 }
 
 // Direction-split variant for meshes with few elements: one launch per
-// direction, each element's lines spread over `chunks` blocks.
-template <typename T, int N>
+// direction, each element's lines (times NP threads per line) spread over
+// `chunks` blocks.
+template <typename T, int N, int NP>
 __global__ void __launch_bounds__(256) k_sipg_dir(OpArgs<T> a, int dir, int chunks) {
   constexpr int n2 = N * N, n3 = n2 * N;
   const T* m3 = a.tab + a.mass3;
   const int64_t nblk = a.Ne * chunks;
   for (int64_t bi = blockIdx.x; bi < nblk; bi += gridDim.x) {
     const int64_t e = bi / chunks;
-    const int ln = (int)(bi % chunks) * blockDim.x + threadIdx.x;
-    if (ln >= n2) continue;
+    const int lt = (int)(bi % chunks) * blockDim.x + threadIdx.x;
+    if (lt >= n2 * NP) continue;
+    const int ln = lt / NP, part = lt - ln * NP;
     const int p = ln % N, q = ln / N;
     const int e32 = (int)e, exy = e32 / a.nx;  // element indices fit in 32 bits
     const int ex = e32 - exy * a.nx, ey = exy % a.ny, ez = exy / a.ny;
@@ -285,24 +294,26 @@ __global__ void __launch_bounds__(256) k_sipg_dir(OpArgs<T> a, int dir, int chun
       st = n2;
     }
     const int64_t off = e * n3 + base;
-    line_apply_n<T, N>(a, dir, a.u + off, a.u + eL * n3 + base, a.u + eR * n3 + base, st, a.out + off,
-                       a.residual ? a.f + off : nullptr, m3 + base, dir);
+    line_apply_n<T, N, NP>(a, dir, a.u + off, a.u + eL * n3 + base, a.u + eR * n3 + base, st, a.out + off,
+                           a.residual ? a.f + off : nullptr, m3 + base, dir, part);
   }
 }
 
 template <typename T, int N>
 cudaError_t launch_sipg_n(const mg_ctx* c, OpArgs<T>& a) {
   constexpr int n2 = N * N;
+  // the long lines of high orders are shared by 4 threads (4 times the parallelism on small meshes)
+  constexpr int NP = N >= 17 ? 4 : 1;
   // lines per element and direction spread evenly over <= 256 threads
   const int iters = (n2 + 255) / 256;
   if (iters > 1 || c->Ne < 2 * 152) {
-    const int chunks = (n2 + 255) / 256;
-    const int threads = ((n2 + chunks - 1) / chunks + 31) / 32 * 32;
+    const int chunks = (n2 * NP + 255) / 256;
+    const int threads = ((n2 * NP + chunks - 1) / chunks + 31) / 32 * 32;
     if (c->Ne * chunks < 4 * 152 || iters > 1) {
       const int64_t nblk = c->Ne * chunks;
       const int blocks = (int)(nblk < 152 * 16 ? nblk : 152 * 16);
       for (int dir = 0; dir < 3; ++dir) {
-        k_sipg_dir<T, N><<<blocks, threads, 0, c->stream>>>(a, dir, chunks);
+        k_sipg_dir<T, N, NP><<<blocks, threads, 0, c->stream>>>(a, dir, chunks);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
       }
@@ -327,6 +338,8 @@ template <>
 const double* table_of<double>(const mg_ctx* c) { return c->ws.tab64; }
 template <>
 const float* table_of<float>(const mg_ctx* c) { return c->ws.tab32; }
+template <>
+const df64* table_of<df64>(const mg_ctx* c) { return c->ws.tabdf; }
 
 }  // namespace
 
@@ -377,5 +390,6 @@ cudaError_t launch_sipg(const mg_ctx* c, int l, const T* u, const T* f, T* out, 
 
 template cudaError_t launch_sipg<double>(const mg_ctx*, int, const double*, const double*, double*, int);
 template cudaError_t launch_sipg<float>(const mg_ctx*, int, const float*, const float*, float*, int);
+template cudaError_t launch_sipg<df64>(const mg_ctx*, int, const df64*, const df64*, df64*, int);
 
 }  // namespace mgdg

@@ -34,7 +34,7 @@ class MGSolver:
 
     def __init__(self, lengths, counts, P, penalty=2.0, overlap=1, precision="fp64", overlap_mode="layers",
                  overlap_frac=0.08, weight_profile="quintic", ns_pre=1, ns_post=1, ns_growth=1, device="cuda",
-                 stream=None, tensor_cores=False):
+                 stream=None, tensor_cores=False, outer_df64=False):
         self.lib = load_library()
         self.device = torch.device(device)
         if self.device.type == "cuda" and self.device.index is None:
@@ -47,6 +47,7 @@ class MGSolver:
         opts.ns_pre, opts.ns_post, opts.ns_growth = int(ns_pre), int(ns_post), int(ns_growth)
         opts.precision = PRECISION[precision]
         opts.fdm_tensor_cores = {False: 0, True: 1, "auto": 2}[tensor_cores]
+        opts.outer_df64 = 1 if outer_df64 else 0
         with torch.cuda.device(self.device):
             self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         opts.stream = ctypes.c_void_p(self.stream.cuda_stream)
@@ -144,6 +145,14 @@ class MGSolver:
         self._vec(u, level, name="u")
         out = self.empty(level) if out is None else self._vec(out, level, name="out")
         self._check(self.lib.mg_apply_sipg(self.ctx, level, _ptr(u), _ptr(out)))
+        return out
+
+    def apply_sipg_df64(self, u, level=None, out=None):
+        """A_l u with double-float arithmetic (FP64 vectors); see mg_apply_sipg_df64."""
+        level = self.L if level is None else level
+        self._vec(u, level, name="u")
+        out = self.empty(level) if out is None else self._vec(out, level, name="out")
+        self._check(self.lib.mg_apply_sipg_df64(self.ctx, level, _ptr(u), _ptr(out)))
         return out
 
     def residual(self, u, f, level=None, out=None):

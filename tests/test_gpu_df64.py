@@ -1,0 +1,64 @@
+"""The outer operator in double-float arithmetic (pairs of FP32, about 48
+significant bits): parity with the FP64 oracle and solves that reach the FP64
+tolerance.
+
+Tolerance: each double-float operation has a relative error of a few 2^-48
+(~4e-15) of its operands; an application of A sums about 3 (n + 4) such terms
+per node of sizes up to |A| |u|, so the result is within ~1e-13 of the
+largest entry -- the test allows 1e-12, the FP64 path's own bound."""
+import numpy as np
+import pytest
+
+from oracle.multigrid import Hierarchy, solve_mgcg
+from oracle.sipg import Mesh, assemble, weak_rhs
+from paper_1612_04796_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def rel_err(got, ref):
+    return np.max(np.abs(np.asarray(got) - ref)) / np.max(np.abs(ref))
+
+
+def cuda(x):
+    import torch
+    return torch.tensor(np.asarray(x), dtype=torch.float64, device="cuda")
+
+
+@pytest.mark.parametrize("P,counts", [(2, (3, 4, 5)), (4, (3, 4, 3)), (8, (3, 3, 4)), (16, (3, 3, 3))])
+def test_apply_sipg_df64_matches_oracle(mg, P, counts):
+    lengths = (1.0, 1.5, 0.7)
+    s = mg.MGSolver(lengths, counts, P, precision="mixed", outer_df64=True)
+    A = assemble(Mesh(lengths, counts), P)
+    u = inputs.gaussian(A.shape[0], 21)
+    got = s.apply_sipg_df64(cuda(u)).cpu().numpy()
+    s.close()
+    assert rel_err(got, A @ u) < 1e-12
+
+
+def test_apply_sipg_df64_all_levels(mg):
+    lengths, counts = (1.0, 1.0, 1.0), (3, 3, 3)
+    s = mg.MGSolver(lengths, counts, 8, precision="mixed", outer_df64=True)
+    for l in range(s.L + 1):
+        A = assemble(Mesh(lengths, counts), 2 ** l)
+        u = inputs.gaussian(A.shape[0], 22 + l)
+        assert rel_err(s.apply_sipg_df64(cuda(u), level=l).cpu().numpy(), A @ u) < 1e-12
+    s.close()
+
+
+def test_mixed_solve_with_df64_outer_operator(mg):
+    """FP32 V-cycle inside the FP64 CG whose q = A p is double-float: the true
+    FP64 residual reaches 1e-10 and the iteration count matches the oracle's
+    MG-CG within one."""
+    lengths, counts, P = (1.0, 1.0, 1.0), (4, 4, 4), 8
+    s = mg.MGSolver(lengths, counts, P, precision="mixed", outer_df64=True)
+    mesh = Mesh(lengths, counts)
+    H = Hierarchy(mesh, P)
+    b = weak_rhs(mesh, P, inputs.gaussian(H.A.shape[0], 19))
+    uo, ito, _ = solve_mgcg(H, b, tol=1e-10)
+    ug, itg, rel, hg = s.solve(cuda(b), tol=1e-10, use_cg=True)
+    u = ug.cpu().numpy()
+    s.close()
+    assert np.linalg.norm(b - H.A @ u) <= 1.01e-10 * np.linalg.norm(b)
+    assert abs(itg - ito) <= 1
+    assert rel_err(u, uo) < 1e-7
