@@ -425,6 +425,29 @@ def run_mg(args):
             sm_.close()
             return leg
 
+        # the standalone MG of the main line with the multigrid in double-float arithmetic
+        sd = pkg.MGSolver(W["lengths"], W["elements"], W["P"], overlap=W["overlap_layers"], precision="df64",
+                          device=dev)
+        ud = torch.zeros(N, dtype=torch.float64, device=dev)
+        for _ in range(args.warmup):
+            ud.zero_()
+            sd.solve(b, ud, tol=W["tol"])
+        barrier()
+        df_ms, its_d = timed_steps(sd, ud, use_cg=False)
+        barrier()
+        sd.profile(True)
+        df_prof_ms, _ = timed_steps(sd, ud, use_cg=False)
+        sd.profile(False)
+        line["df64"] = {"value": world * N * args.steps / max_over_ranks(sum(df_ms) / 1e3), "unit": "DOF/s",
+                        "ms_per_step": sum(df_ms) / args.steps, "iterations": its_d[-1],
+                        "solver": "MG V(1,1), multigrid in double-float (FP32 pairs, ~48-bit), FP64 residual",
+                        "dtype": "f32x2",
+                        "true_relres_fp64": float(torch.linalg.norm(s.residual(ud, b)) / torch.linalg.norm(b)),
+                        "max_rel_diff_vs_fp64_solution": float(torch.max(torch.abs(ud - u)) / torch.max(torch.abs(u))),
+                        "time_share_of_step": profile_shares(sd, sum(df_prof_ms)),
+                        "ms_per_step_by_kernel_level": profile_levels(sd, args.steps)}
+        sd.close()
+
         line["mixed"] = mixed_leg(args.outer_df64)
         if not args.outer_df64:
             line["mixed_df64"] = mixed_leg(True)

@@ -52,9 +52,12 @@ typedef enum {
 /* Arithmetic of the solve (Section 3.2 method, precision is this library's choice). */
 typedef enum {
   MG_FP64 = 0,  /* every kernel in FP64 */
-  MG_MIXED = 1  /* FP32 multigrid (smoother, transfers, operator on the levels)
+  MG_MIXED = 1, /* FP32 multigrid (smoother, transfers, operator on the levels)
                    inside an FP64 outer iteration; FP64 outer residual, inner
                    products, updates, 1D setup and coarsest solve */
+  MG_DF64 = 2   /* the same split with the multigrid in double-float arithmetic
+                   (pairs of FP32, about 48 significant bits: FP64-class accuracy
+                   on the FP32 pipes); the coarsest solve stays FP64 */
 } mg_precision;
 
 /* How the subdomain overlap is given (Section 3.1, Table 1). */
@@ -215,6 +218,11 @@ mg_status mg_solve(mg_ctx* ctx, double* u, const double* f, double tol, int maxi
  * fastest): copies f (and the initial u) in, solves, copies u out. */
 mg_status mg_solve_host(mg_ctx* ctx, double* u_host, const double* f_host, double tol, int maxit, int use_cg,
                         int* iters, double* relres, double* history);
+
+/* mg_vcycle_df64 -- one V-cycle (Algorithm 1) like mg_vcycle on FP64 vectors u,
+ * f of the finest level, with the multigrid arithmetic in double-float (the
+ * preconditioner of MG_DF64).  Uses two of the outer-iteration work vectors. */
+mg_status mg_vcycle_df64(mg_ctx* ctx, double* u, const double* f);
 
 /* mg_apply_sipg_df64 -- Au = A_l u like mg_apply_sipg (FP64 vectors), with the
  * arithmetic in double-float (about 48 significant bits); the operator of the

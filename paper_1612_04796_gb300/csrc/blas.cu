@@ -163,6 +163,12 @@ __global__ void k_cg_newdir(double* __restrict__ p, const TZ* __restrict__ zs, i
   }
 }
 
+// y = x (accumulate = 0) or y += x (accumulate = 1), x double-float, y FP64
+__global__ void k_join_df64(const df64* __restrict__ x, double* __restrict__ y, int64_t n, int accumulate) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = accumulate ? y[i] + df_to_double(x[i]) : df_to_double(x[i]);
+}
+
 __global__ void k_split_df64(const double* __restrict__ x, df64* __restrict__ y, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     y[i] = df_from_double(x[i]);
@@ -349,9 +355,17 @@ template cudaError_t launch_cg_direction<double>(const mg_ctx*, double*, const d
                                                  const double*, int64_t, df64*);
 template cudaError_t launch_cg_direction<float>(const mg_ctx*, double*, const float*, const double*, const double*,
                                                 int64_t, df64*);
+template cudaError_t launch_cg_direction<df64>(const mg_ctx*, double*, const df64*, const double*, const double*,
+                                               int64_t, df64*);
 
 cudaError_t launch_split_df64(const mg_ctx* c, const double* x, df64* y, int64_t n) {
   k_split_df64<<<grid_for(n), kThreads, 0, c->stream>>>(x, y, n);
+  c->nlaunch += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_join_df64(const mg_ctx* c, const df64* x, double* y, int64_t n, int accumulate) {
+  k_join_df64<<<grid_for(n), kThreads, 0, c->stream>>>(x, y, n, accumulate);
   c->nlaunch += 1;
   return cudaGetLastError();
 }
@@ -428,5 +442,6 @@ template cudaError_t launch_sub_mean_t<double>(const mg_ctx*, double*, int64_t);
 template cudaError_t launch_sub_mean_t<float>(const mg_ctx*, float*, int64_t);
 template cudaError_t launch_zero<double>(const mg_ctx*, double*, int64_t);
 template cudaError_t launch_zero<float>(const mg_ctx*, float*, int64_t);
+template cudaError_t launch_zero<df64>(const mg_ctx*, df64*, int64_t);
 
 }  // namespace mgdg

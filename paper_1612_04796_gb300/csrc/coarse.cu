@@ -127,6 +127,10 @@ cudaError_t launch_coarse_fdm_raw(const double* const Q[3], const double* const 
   return coarse_passes<double, double>(Q, lam, d, null_mode, f0, A, B, u0, scal, mean_slot, s);
 }
 
+cudaError_t launch_coarse_solve_df64(const mg_ctx* c, const df64* f0, df64* u0) {
+  return coarse_solve_t<df64, df64>(c, f0, u0);
+}
+
 cudaError_t launch_coarse_solve_f32(const mg_ctx* c, const float* f0, float* u0) {
   // The coarsest solve of the FP32 hierarchy runs in FP64: the first pass
   // reads the FP32 right-hand side, the last writes the FP32 solution.

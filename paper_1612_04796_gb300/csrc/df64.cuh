@@ -25,6 +25,14 @@ struct df64 {
   __host__ __device__ df64(float h, float l) : hi(h), lo(l) {}
   __device__ df64(int v) : hi((float)v), lo(0.f) {}
   __device__ df64(float v) : hi(v), lo(0.f) {}
+  // nearest pair to an FP64 value (FP64 arithmetic; constants fold at compile time)
+  __device__ df64(double v) {
+#ifdef __CUDA_ARCH__
+    hi = __double2float_rn(v);
+    lo = __double2float_rn(v - (double)hi);
+#endif
+  }
+  __device__ explicit operator double() const { return (double)hi + (double)lo; }
 };
 
 // s + e = a + b exactly (Knuth).
@@ -60,13 +68,11 @@ __device__ __forceinline__ df64 operator*(df64 a, df64 b) {
 
 __device__ __forceinline__ df64& operator+=(df64& a, df64 b) { return a = a + b; }
 __device__ __forceinline__ df64& operator-=(df64& a, df64 b) { return a = a - b; }
+__device__ __forceinline__ df64& operator*=(df64& a, df64 b) { return a = a * b; }
 
 // Nearest double-float to x and back (these conversions use the FP64 pipe).
-__device__ __forceinline__ df64 df_from_double(double x) {
-  const float h = __double2float_rn(x);
-  return df64(h, __double2float_rn(x - (double)h));
-}
+__device__ __forceinline__ df64 df_from_double(double x) { return df64(x); }
 
-__device__ __forceinline__ double df_to_double(df64 a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ double df_to_double(df64 a) { return (double)a; }
 
 }  // namespace mgdg

@@ -214,4 +214,12 @@ cudaError_t launch_fdm_m(const FdmArgs<T>& a, int blocks, int threads, size_t /*
   template cudaError_t launch_fdm_m<double, M>(const FdmArgs<double>&, int, int, size_t, cudaStream_t);     \
   template cudaError_t launch_fdm_m<float, M>(const FdmArgs<float>&, int, int, size_t, cudaStream_t);
 
+// Double-float instantiations exist for the widths of N_O = 1, 2 up to P = 16
+// (other widths use the run-time-size kernel).
+#define MGDG_FDM_DF_WIDTHS(X) X(3) X(5) X(7) X(9) X(11) X(13) X(17) X(19) X(21)
+#define MGDG_FDM_EXTERN_DF(M) \
+  extern template cudaError_t launch_fdm_m<df64, M>(const FdmArgs<df64>&, int, int, size_t, cudaStream_t);
+#define MGDG_FDM_INSTANTIATE_DF(M) \
+  template cudaError_t launch_fdm_m<df64, M>(const FdmArgs<df64>&, int, int, size_t, cudaStream_t);
+
 }  // namespace mgdg

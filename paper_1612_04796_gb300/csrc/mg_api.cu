@@ -255,6 +255,10 @@ template <>
 cudaError_t coarse_solve_t<float>(const mg_ctx* c, const float* f0, float* u0) {
   return launch_coarse_solve_f32(c, f0, u0);
 }
+template <>
+cudaError_t coarse_solve_t<df64>(const mg_ctx* c, const df64* f0, df64* u0) {
+  return launch_coarse_solve_df64(c, f0, u0);
+}
 
 int steps_on_level(const mg_ctx* c, int ns, int l) {
   int s = ns;
@@ -344,6 +348,14 @@ cudaError_t precond(const mg_ctx* c, const double* r, double* z) {
     if ((e = vcycle_t<float>(c, u32, f32, true, false)) != cudaSuccess) return e;
     return launch_from_f32(c, u32, z, N, kSlotRR);
   }
+  if (c->opts.precision == MG_DF64) {
+    df64* fd = lvec<df64>(c->lev[L].f);
+    df64* ud = lvec<df64>(c->lev[L].u);
+    cudaError_t e;
+    if ((e = launch_split_df64(c, r, fd, N)) != cudaSuccess) return e;
+    if ((e = vcycle_t<df64>(c, ud, fd, true, false)) != cudaSuccess) return e;
+    return launch_join_df64(c, ud, z, N, 0);
+  }
   return vcycle_t<double>(c, z, r, true, false);
 }
 
@@ -392,7 +404,7 @@ mg_status solve_impl(mg_ctx* c, double* u, const double* f, double tol, int maxi
   bool converged = false;
   if (!use_cg) {
     double* r = lvec<double>(c->lev[L].r);
-    const bool mixed = c->opts.precision == MG_MIXED;
+    const bool mixed = c->opts.precision != MG_FP64;  // defect correction u += B r (B in FP32 or double-float)
     if (mixed) r = c->ws.cg[1];
     CK(launch_sipg<double>(c, L, u, f, r, 1));
     CK(launch_dot(c, r, r, N, kSlotRR));
@@ -445,7 +457,7 @@ mg_status solve_impl(mg_ctx* c, double* u, const double* f, double tol, int maxi
     converged = r0 == 0.0;
     // double-float copies of p and q for the outer operator (mg_opts.outer_df64), in the
     // smoother's correction buffer: written after each preconditioner, read before the next
-    const bool df = c->opts.outer_df64 && c->opts.precision == MG_MIXED;
+    const bool df = c->opts.outer_df64 && c->opts.precision != MG_FP64;
     df64* pdf = df ? static_cast<df64*>(c->ws.corr) : nullptr;
     df64* qdf = df ? pdf + N : nullptr;
     if (!converged) {
@@ -497,6 +509,13 @@ mg_status solve_impl(mg_ctx* c, double* u, const double* f, double tol, int maxi
           if ((e = vcycle_t<float>(c, u32, f32, true, false)) != cudaSuccess) return e;
           return launch_cg_direction<float>(c, p, u32, q, r, N, pdf);
         }
+        if (c->opts.precision == MG_DF64) {
+          df64* fd = lvec<df64>(c->lev[L].f);
+          df64* ud = lvec<df64>(c->lev[L].u);
+          if ((e = launch_split_df64(c, r, fd, N)) != cudaSuccess) return e;
+          if ((e = vcycle_t<df64>(c, ud, fd, true, false)) != cudaSuccess) return e;
+          return launch_cg_direction<df64>(c, p, ud, q, r, N, pdf);
+        }
         if ((e = vcycle_t<double>(c, z, r, true, false)) != cudaSuccess) return e;
         return launch_cg_direction<double>(c, p, z, q, r, N);
       }));
@@ -543,7 +562,7 @@ mg_status mg_setup(double lx, double ly, double lz, int nx, int ny, int nz, int 
   mg_default_opts(&o);
   if (opts) o = *opts;
   if (o.ns_pre < 0 || o.ns_post < 0 || o.ns_growth < 1 || o.ns_pre + o.ns_post < 1) return MG_EINVAL;
-  if (o.precision != MG_FP64 && o.precision != MG_MIXED) return MG_EINVAL;
+  if (o.precision != MG_FP64 && o.precision != MG_MIXED && o.precision != MG_DF64) return MG_EINVAL;
   if (o.fdm_tensor_cores < 0 || o.fdm_tensor_cores > 2) return MG_EINVAL;
   if (o.outer_df64 < 0 || o.outer_df64 > 1) return MG_EINVAL;
   if (o.weight_profile < MG_WEIGHT_QUINTIC || o.weight_profile > MG_WEIGHT_QUINTIC_NORMALISED) return MG_EINVAL;
@@ -711,6 +730,21 @@ long long mg_num_dofs(const mg_ctx* c, int level) {
 }
 
 int mg_level_layers(const mg_ctx* c, int level) { return mg_level_layers_dir(c, level, 0); }
+
+mg_status mg_vcycle_df64(mg_ctx* c, double* u, const double* f) {
+  mg_status s = need_ready(c);
+  if (s != MG_OK) return s;
+  if (!u || !f || u == f) return fail(c, MG_EINVAL, "null or aliased vector");
+  const int L = c->L;
+  const int64_t N = c->lev[L].N;
+  df64* ud = reinterpret_cast<df64*>(c->ws.cg[5]);
+  df64* fd = reinterpret_cast<df64*>(c->ws.cg[6]);
+  CK(launch_split_df64(c, u, ud, N));
+  CK(launch_split_df64(c, f, fd, N));
+  CK(vcycle_t<df64>(c, ud, fd, false, false));
+  CK(launch_join_df64(c, ud, u, N, 0));
+  return MG_OK;
+}
 
 mg_status mg_apply_sipg_df64(mg_ctx* c, int level, const double* u, double* Au) {
   mg_status s = need_ready(c);

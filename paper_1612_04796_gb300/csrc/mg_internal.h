@@ -176,6 +176,7 @@ cudaError_t launch_prolong(const mg_ctx* c, int l, const T* u_coarse, T* u_fine)
 // ---- coarse solve (coarse.cu) ----
 cudaError_t launch_coarse_solve(const mg_ctx* c, const double* f0, double* u0);
 cudaError_t launch_coarse_solve_f32(const mg_ctx* c, const float* f0, float* u0);
+cudaError_t launch_coarse_solve_df64(const mg_ctx* c, const df64* f0, df64* u0);
 // The six fast-diagonalisation passes of the coarse solve with explicit
 // pointers; f0's mean is read from scal[mean_slot] (sum of f0).
 cudaError_t launch_coarse_fdm_raw(const double* const Q[3], const double* const lam[3], const int Ng[3],
@@ -204,6 +205,7 @@ cudaError_t launch_cg_direction(const mg_ctx* c, double* p, const TZ* z, const d
 // Double-float support of the outer operator: y = x split into pairs; and
 // q = to_double(qdf) with scal[slot] = p . q in the same pass.
 cudaError_t launch_split_df64(const mg_ctx* c, const double* x, df64* y, int64_t n);
+cudaError_t launch_join_df64(const mg_ctx* c, const df64* x, double* y, int64_t n, int accumulate);
 cudaError_t launch_dot_dfq(const mg_ctx* c, const double* p, const df64* qdf, double* q, int64_t n, int slot);
 cudaError_t launch_add(const mg_ctx* c, double* y, const double* x, int64_t n);  // y += x
 cudaError_t launch_xpby(const mg_ctx* c, double* p, const double* z, int64_t n, int num_slot, int den_slot,

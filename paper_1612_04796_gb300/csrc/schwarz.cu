@@ -23,6 +23,7 @@ MGDG_FDM_EXTERN(3) MGDG_FDM_EXTERN(5) MGDG_FDM_EXTERN(7) MGDG_FDM_EXTERN(9) MGDG
 MGDG_FDM_EXTERN(13) MGDG_FDM_EXTERN(15) MGDG_FDM_EXTERN(17) MGDG_FDM_EXTERN(19) MGDG_FDM_EXTERN(21)
 MGDG_FDM_EXTERN(23) MGDG_FDM_EXTERN(25) MGDG_FDM_EXTERN(27) MGDG_FDM_EXTERN(29) MGDG_FDM_EXTERN(31)
 MGDG_FDM_EXTERN(33) MGDG_FDM_EXTERN(35)
+MGDG_FDM_DF_WIDTHS(MGDG_FDM_EXTERN_DF)
 
 namespace {
 
@@ -264,6 +265,8 @@ template <>
 const double* table_of<double>(const mg_ctx* c) { return c->ws.tab64; }
 template <>
 const float* table_of<float>(const mg_ctx* c) { return c->ws.tab32; }
+template <>
+const df64* table_of<df64>(const mg_ctx* c) { return c->ws.tabdf; }
 
 }  // namespace
 
@@ -306,14 +309,21 @@ cudaError_t launch_fdm(const mg_ctx* c, int l, const T* r) {
     int64_t groups = (c->Ne + a.spb - 1) / a.spb;
     int blocks = (int)(groups < 152 * 8 ? groups : 152 * 8);
     c->nlaunch += 1;
-    switch (m) {
 #define MGDG_CASE(M) case M: return launch_fdm_m<T, M>(a, blocks, threads, smem, c->stream);
-      MGDG_CASE(3) MGDG_CASE(5) MGDG_CASE(7) MGDG_CASE(9) MGDG_CASE(11) MGDG_CASE(13) MGDG_CASE(15)
-      MGDG_CASE(17) MGDG_CASE(19) MGDG_CASE(21) MGDG_CASE(23) MGDG_CASE(25) MGDG_CASE(27) MGDG_CASE(29)
-      MGDG_CASE(31) MGDG_CASE(33) MGDG_CASE(35)
-#undef MGDG_CASE
-      default: break;
+    if constexpr (std::is_same<T, df64>::value) {
+      switch (m) {
+        MGDG_FDM_DF_WIDTHS(MGDG_CASE)
+        default: break;
+      }
+    } else {
+      switch (m) {
+        MGDG_CASE(3) MGDG_CASE(5) MGDG_CASE(7) MGDG_CASE(9) MGDG_CASE(11) MGDG_CASE(13) MGDG_CASE(15)
+        MGDG_CASE(17) MGDG_CASE(19) MGDG_CASE(21) MGDG_CASE(23) MGDG_CASE(25) MGDG_CASE(27) MGDG_CASE(29)
+        MGDG_CASE(31) MGDG_CASE(33) MGDG_CASE(35)
+        default: break;
+      }
     }
+#undef MGDG_CASE
     c->nlaunch -= 1;
   }
   a.spb = 1;
@@ -358,5 +368,7 @@ template cudaError_t launch_fdm<double>(const mg_ctx*, int, const double*);
 template cudaError_t launch_fdm<float>(const mg_ctx*, int, const float*);
 template cudaError_t launch_scatter<double>(const mg_ctx*, int, double*, int);
 template cudaError_t launch_scatter<float>(const mg_ctx*, int, float*, int);
+template cudaError_t launch_fdm<df64>(const mg_ctx*, int, const df64*);
+template cudaError_t launch_scatter<df64>(const mg_ctx*, int, df64*, int);
 
 }  // namespace mgdg

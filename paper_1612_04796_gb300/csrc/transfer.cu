@@ -197,6 +197,8 @@ template <>
 const double* table_of<double>(const mg_ctx* c) { return c->ws.tab64; }
 template <>
 const float* table_of<float>(const mg_ctx* c) { return c->ws.tab32; }
+template <>
+const df64* table_of<df64>(const mg_ctx* c) { return c->ws.tabdf; }
 
 }  // namespace
 
@@ -248,5 +250,7 @@ template cudaError_t launch_restrict<double>(const mg_ctx*, int, const double*, 
 template cudaError_t launch_restrict<float>(const mg_ctx*, int, const float*, float*);
 template cudaError_t launch_prolong<double>(const mg_ctx*, int, const double*, double*);
 template cudaError_t launch_prolong<float>(const mg_ctx*, int, const float*, float*);
+template cudaError_t launch_restrict<df64>(const mg_ctx*, int, const df64*, df64*);
+template cudaError_t launch_prolong<df64>(const mg_ctx*, int, const df64*, df64*);
 
 }  // namespace mgdg

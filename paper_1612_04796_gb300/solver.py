@@ -11,7 +11,7 @@ import torch
 from . import _lib
 from ._lib import MgOpts, load_library
 
-PRECISION = {"fp64": 0, "mixed": 1}
+PRECISION = {"fp64": 0, "mixed": 1, "df64": 2}
 OVERLAP_MODE = {"layers": 0, "width": 1, "max": 2}
 PROFILE = {"quintic": 0, "linear": 1, "quintic_halves": 2, "quintic_normalised": 3}
 
@@ -195,6 +195,13 @@ class MGSolver:
         u0 = self.empty(0)
         self._check(self.lib.mg_coarse_solve(self.ctx, _ptr(f0), _ptr(u0)))
         return u0
+
+    def vcycle_df64(self, u, f):
+        """One V-cycle on FP64 vectors with the multigrid in double-float arithmetic."""
+        self._vec(u, self.L, name="u")
+        self._vec(f, self.L, name="f")
+        self._check(self.lib.mg_vcycle_df64(self.ctx, _ptr(u), _ptr(f)))
+        return u
 
     def vcycle(self, u, f):
         if u.dtype == torch.float32:

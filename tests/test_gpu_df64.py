@@ -62,3 +62,55 @@ def test_mixed_solve_with_df64_outer_operator(mg):
     assert np.linalg.norm(b - H.A @ u) <= 1.01e-10 * np.linalg.norm(b)
     assert abs(itg - ito) <= 1
     assert rel_err(u, uo) < 1e-7
+
+
+@pytest.mark.parametrize("P,overlap", [(4, 1), (8, 1), (8, 2)])
+def test_vcycle_df64_matches_oracle(mg, P, overlap):
+    """One V(1,1) cycle with smoother, transfers and level operators in
+    double-float: within 1e-10 of the FP64 oracle (the FP64 path's bound
+    through a cycle)."""
+    lengths, counts = (1.0, 1.5, 0.7), (3, 3, 4)
+    s = mg.MGSolver(lengths, counts, P, overlap=overlap, precision="df64")
+    mesh = Mesh(lengths, counts)
+    H = Hierarchy(mesh, P, n_o=overlap)
+    u = inputs.gaussian(H.A.shape[0], 16)
+    f = weak_rhs(mesh, P, inputs.gaussian(H.A.shape[0], 17))
+    ref = H.vcycle(u, f)
+    ut = cuda(u)
+    s.vcycle_df64(ut, cuda(f))
+    got = ut.cpu().numpy()
+    s.close()
+    assert rel_err(got, ref) < 1e-10
+
+
+def test_df64_mg_solve_reproduces_oracle_iterations(mg):
+    """Standalone MG with the double-float hierarchy (defect correction with
+    the FP64 residual): the oracle's cycle count and residual history."""
+    from oracle.multigrid import solve_mg
+    lengths, counts, P = (1.0, 1.0, 1.0), (4, 4, 4), 4
+    s = mg.MGSolver(lengths, counts, P, precision="df64")
+    mesh = Mesh(lengths, counts)
+    H = Hierarchy(mesh, P)
+    b = weak_rhs(mesh, P, inputs.gaussian(H.A.shape[0], 18))
+    uo, ito, ho = solve_mg(H, b, tol=1e-10)
+    ug, itg, rel, hg = s.solve(cuda(b), tol=1e-10)
+    s.close()
+    ho = np.asarray(ho)
+    assert itg == ito
+    assert np.all(np.abs(hg - ho) <= 1e-6 * ho + 1e-14 * ho[0])
+    assert rel_err(ug.cpu().numpy(), uo) < 1e-9
+
+
+def test_df64_mgcg_solve(mg):
+    lengths, counts, P = (1.0, 1.0, 1.0), (4, 4, 4), 8
+    s = mg.MGSolver(lengths, counts, P, precision="df64", outer_df64=True)
+    mesh = Mesh(lengths, counts)
+    H = Hierarchy(mesh, P)
+    b = weak_rhs(mesh, P, inputs.gaussian(H.A.shape[0], 19))
+    uo, ito, _ = solve_mgcg(H, b, tol=1e-10)
+    ug, itg, rel, _ = s.solve(cuda(b), tol=1e-10, use_cg=True)
+    u = ug.cpu().numpy()
+    s.close()
+    assert np.linalg.norm(b - H.A @ u) <= 1.01e-10 * np.linalg.norm(b)
+    assert abs(itg - ito) <= 1
+    assert rel_err(u, uo) < 1e-8
