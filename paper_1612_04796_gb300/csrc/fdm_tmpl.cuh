@@ -41,17 +41,19 @@ __device__ __forceinline__ void fdm_fwd(T (&x)[M], const T* __restrict__ S, T (&
   }
 #pragma unroll
   for (int p = 0; p < ne; ++p) {
-    T acc = S[p] * x[0];
+    Acc<T> acc;
+    acc.init(S[p], x[0]);
 #pragma unroll
-    for (int a = 1; a <= h; ++a) acc += S[a * M + p] * x[a];
-    y[p] = acc;
+    for (int a = 1; a <= h; ++a) acc.add(S[a * M + p], x[a]);
+    y[p] = acc.get();
   }
 #pragma unroll
   for (int q = 0; q < h; ++q) {
-    T acc = S[ne + q] * x[M - 1];
+    Acc<T> acc;
+    acc.init(S[ne + q], x[M - 1]);
 #pragma unroll
-    for (int a = 1; a < h; ++a) acc += S[a * M + ne + q] * x[M - 1 - a];
-    y[ne + q] = acc;
+    for (int a = 1; a < h; ++a) acc.add(S[a * M + ne + q], x[M - 1 - a]);
+    y[ne + q] = acc.get();
   }
 }
 
@@ -61,13 +63,17 @@ __device__ __forceinline__ void fdm_bwd(const T (&v)[M], const T* __restrict__ S
   constexpr int h = M / 2, ne = h + 1;
 #pragma unroll
   for (int a = 0; a <= h; ++a) {
-    T E = SW[a * M] * v[0];
+    Acc<T> ea;
+    ea.init(SW[a * M], v[0]);
 #pragma unroll
-    for (int p = 1; p < ne; ++p) E += SW[a * M + p] * v[p];
+    for (int p = 1; p < ne; ++p) ea.add(SW[a * M + p], v[p]);
+    const T E = ea.get();
     if (a < h) {
-      T O = SW[a * M + ne] * v[ne];
+      Acc<T> oa;
+      oa.init(SW[a * M + ne], v[ne]);
 #pragma unroll
-      for (int q = 1; q < h; ++q) O += SW[a * M + ne + q] * v[ne + q];
+      for (int q = 1; q < h; ++q) oa.add(SW[a * M + ne + q], v[ne + q]);
+      const T O = oa.get();
       x[a] = E + O;
       x[M - 1 - a] = E - O;
     } else {

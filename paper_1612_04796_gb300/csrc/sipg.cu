@@ -170,12 +170,15 @@ __device__ __forceinline__ void line_apply_n(const OpArgs<T>& a, int d, const T*
   }
   if (N & 1) ev[ne - 1] = ue[no * st];
   const T av = uL[P * st], cv = uR[0];
-  T b = 0, dd = 0;
+  Acc<T> ba, da;
+  ba.init(DP[0], uL[0]);
+  da.init(D0[0], uR[0]);
 #pragma unroll
-  for (int t = 0; t < N; ++t) {
-    b += DP[t] * uL[t * st];
-    dd += D0[t] * uR[t * st];
+  for (int t = 1; t < N; ++t) {
+    ba.add(DP[t], uL[t * st]);
+    da.add(D0[t], uR[t * st]);
   }
+  const T b = ba.get(), dd = da.get();
   const T s = av + cv, tm = av - cv;
   const T lo = g2_m0 * b - mu_m0 * av;
   const T hi = -(mu_m0 * cv + g2_m0 * dd);
@@ -183,14 +186,18 @@ __device__ __forceinline__ void line_apply_n(const OpArgs<T>& a, int d, const T*
   for (int ii = 0; ii < (ne + NP - 1) / NP; ++ii) {
     const int i = NP == 1 ? ii : part + ii * NP;
     if (NP > 1 && i >= ne) break;
-    T E = fe[i] * s;
+    Acc<T> ea;
+    ea.init(fe[i], s);
 #pragma unroll
-    for (int t = 0; t < ne; ++t) E += ce[i * ne + t] * ev[t];
+    for (int t = 0; t < ne; ++t) ea.add(ce[i * ne + t], ev[t]);
+    const T E = ea.get();
     T v0, v1;
     if (i < no) {
-      T O = fo[i] * tm;
+      Acc<T> oa;
+      oa.init(fo[i], tm);
 #pragma unroll
-      for (int t = 0; t < no; ++t) O += co[i * no + t] * od[t];
+      for (int t = 0; t < no; ++t) oa.add(co[i * no + t], od[t]);
+      const T O = oa.get();
       v0 = E + O;
       v1 = E - O;
     } else {
