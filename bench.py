@@ -74,7 +74,8 @@ WORKLOADS = {
 }
 WORKLOADS["c5"] = dict(workload="serving stream: 512 solve requests, Poisson arrivals at 200/s (seed 5), periodic box "
                                 "[0,AR]x[0,1]x[0,1], AR ~ U[1,8], n^3 elements with n in {4,8,16,24,32}, P in {2,4,8,16}, "
-                                "N_O=4 (default; --overlap), Gaussian f, FP32 V(1,1) in FP64 PCG, tol 1e-10, "
+                                "N_O=4 (default; --overlap), Gaussian f, FP32 V(1,1) in FP64 PCG (outer A p in "
+                                "double-float), tol 1e-10, "
                                 "admitted by HBM footprint, "
                                 "one context and stream per slot")
 FP32_FLOP_PER_CLK_PER_SM = 256    # 128 FP32 FMA lanes per SM
@@ -588,7 +589,8 @@ def run_serving(args):
         "ms_per_step": makespan * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32 multigrid / f64 outer", "data": "synthetic",
         "config": dict(WORKLOADS["c5"], name="c5", requests=len(reqs), slots=slots, overlap_layers=overlap,
-                       hbm_budget_gb=srv.scheduler.budget / 1e9, total_dofs=dofs),
+                       hbm_budget_gb=srv.scheduler.budget / 1e9, total_dofs=dofs,
+                       outer_operator="double-float (FP32 pairs)" if srv.outer_df64 else "FP64"),
         "latency": summ, "max_concurrent": srv.max_active,
         "iterations": {"median": float(np.median([r.iterations for r in ok])),
                        "max": int(max(r.iterations for r in ok))},

@@ -140,9 +140,11 @@ def request_stream(seed=5, n_requests=512, rate=200.0, sizes=(4, 8, 16, 24, 32),
 
 class Server:
     """Real solves: FP32 V-cycle preconditioner inside FP64 inexact PCG by
-    default; each slot owns a CUDA stream."""
+    default, the outer products q = A p in double-float (outer_df64); each
+    slot owns a CUDA stream."""
 
-    def __init__(self, slots=8, budget_bytes=None, precision="mixed", use_cg=True, device="cuda", keep_solution=True):
+    def __init__(self, slots=8, budget_bytes=None, precision="mixed", use_cg=True, device="cuda", keep_solution=True,
+                 outer_df64=True):
         import torch
 
         from ._lib import MgOpts, load_library
@@ -158,6 +160,7 @@ class Server:
             free, _ = torch.cuda.mem_get_info(self.device)
             budget_bytes = int(0.8 * free)
         self.precision = precision
+        self.outer_df64 = bool(outer_df64) and precision != "fp64"
         self.use_cg = use_cg
         self.keep = keep_solution
         self.streams = [torch.cuda.Stream(self.device) for _ in range(slots)]
@@ -183,7 +186,7 @@ class Server:
         stream = self.streams[slot]
         with torch.cuda.device(self.device), torch.cuda.stream(stream):
             s = self.MGSolver(req.lengths, req.counts, req.P, overlap=req.overlap, precision=self.precision,
-                              device=self.device, stream=stream)
+                              device=self.device, stream=stream, outer_df64=self.outer_df64)
             f = torch.tensor(inputs.gaussian(s.num_dofs(), req.seed), device=self.device)
             b = s.rhs(f)
             u, its, rel, _ = s.solve(b, tol=req.tol, use_cg=self.use_cg, maxit=400)
