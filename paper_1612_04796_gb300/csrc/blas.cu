@@ -50,17 +50,6 @@ __global__ void k_sub_mean(T* x, int64_t n, const double* scal, int slot) {
     x[i] -= mean;
 }
 
-// alpha = scal[num] / scal[den]; x += alpha p; r -= alpha q
-__global__ void k_axpy2(double* __restrict__ x, const double* __restrict__ p, double* __restrict__ r,
-                        const double* __restrict__ q, int64_t n, double* scal, int num, int den) {
-  const double alpha = scal[num] / scal[den];
-  if (blockIdx.x == 0 && threadIdx.x == 0) scal[kSlotAlpha] = alpha;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    x[i] += alpha * p[i];
-    r[i] -= alpha * q[i];
-  }
-}
-
 // The CG update with the partial sums of the new r and r^2 (columns 0, 1).
 __global__ void __launch_bounds__(kThreads) k_cg_update(double* __restrict__ x, const double* __restrict__ p,
                                                         double* __restrict__ r, const double* __restrict__ q,
@@ -193,14 +182,6 @@ __global__ void k_add(double* __restrict__ y, const double* __restrict__ x, int6
     y[i] += x[i];
 }
 
-// beta = -scal[alpha] * scal[num] / scal[den]; p = z + beta p
-__global__ void k_xpby(double* __restrict__ p, const double* __restrict__ z, int64_t n, const double* scal, int num,
-                       int den, int aslot) {
-  const double beta = -scal[aslot] * scal[num] / scal[den];
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    p[i] = z[i] + beta * p[i];
-}
-
 __global__ void k_to_f32(const double* __restrict__ x, float* __restrict__ y, int64_t n, const double* scal,
                          int slot) {
   double s = 1.0;
@@ -318,22 +299,6 @@ cudaError_t launch_sub_mean(const mg_ctx* c, double* x, int64_t n, int sum_slot)
   return cudaGetLastError();
 }
 
-template <typename T>
-cudaError_t launch_sub_mean_t(const mg_ctx* c, T* x, int64_t n) {
-  cudaError_t e = reduce<T>(c, x, x, n, 1, kSlotSumT);
-  if (e != cudaSuccess) return e;
-  k_sub_mean<T><<<grid_for(n), kThreads, 0, c->stream>>>(x, n, c->ws.scal, kSlotSumT);
-  c->nlaunch += 1;
-  return cudaGetLastError();
-}
-
-cudaError_t launch_axpy2(const mg_ctx* c, double* x, const double* p, double* r, const double* q, int64_t n,
-                         int num_slot, int den_slot) {
-  k_axpy2<<<grid_for(n), kThreads, 0, c->stream>>>(x, p, r, q, n, c->ws.scal, num_slot, den_slot);
-  c->nlaunch += 1;
-  return cudaGetLastError();
-}
-
 cudaError_t launch_cg_update(const mg_ctx* c, double* x, const double* p, double* r, const double* q, int64_t n) {
   k_cg_update<<<kRedBlocks, kThreads, 0, c->stream>>>(x, p, r, q, n, c->ws.scal, c->ws.red);
   k_cg_update_final<<<1, kThreads, 0, c->stream>>>(c->ws.red, kRedBlocks, c->ws.scal, n);
@@ -379,13 +344,6 @@ cudaError_t launch_dot_dfq(const mg_ctx* c, const double* p, const df64* qdf, do
 
 cudaError_t launch_add(const mg_ctx* c, double* y, const double* x, int64_t n) {
   k_add<<<grid_for(n), kThreads, 0, c->stream>>>(y, x, n);
-  c->nlaunch += 1;
-  return cudaGetLastError();
-}
-
-cudaError_t launch_xpby(const mg_ctx* c, double* p, const double* z, int64_t n, int num_slot, int den_slot,
-                        int alpha_slot) {
-  k_xpby<<<grid_for(n), kThreads, 0, c->stream>>>(p, z, n, c->ws.scal, num_slot, den_slot, alpha_slot);
   c->nlaunch += 1;
   return cudaGetLastError();
 }
@@ -438,8 +396,6 @@ cudaError_t launch_zero(const mg_ctx* c, T* x, int64_t n) {
   return cudaGetLastError();
 }
 
-template cudaError_t launch_sub_mean_t<double>(const mg_ctx*, double*, int64_t);
-template cudaError_t launch_sub_mean_t<float>(const mg_ctx*, float*, int64_t);
 template cudaError_t launch_zero<double>(const mg_ctx*, double*, int64_t);
 template cudaError_t launch_zero<float>(const mg_ctx*, float*, int64_t);
 template cudaError_t launch_zero<df64>(const mg_ctx*, df64*, int64_t);

@@ -33,7 +33,6 @@ enum Slot : int {
   kSlotBeta = 9,    // CG beta
   kSlotMuZ = 10,    // mean of the preconditioned residual z
   kSlotCoarse = 60, // coarse-solve mean
-  kSlotSumT = 61,   // mean projection of FP32 vectors
   kNumSlots = 64
 };
 
@@ -188,10 +187,6 @@ cudaError_t launch_coarse_fdm_raw(const double* const Q[3], const double* const 
 cudaError_t launch_dot(const mg_ctx* c, const double* x, const double* y, int64_t n, int slot);
 cudaError_t launch_sum(const mg_ctx* c, const double* x, int64_t n, int slot);
 cudaError_t launch_sub_mean(const mg_ctx* c, double* x, int64_t n, int sum_slot);
-template <typename T>
-cudaError_t launch_sub_mean_t(const mg_ctx* c, T* x, int64_t n);
-cudaError_t launch_axpy2(const mg_ctx* c, double* x, const double* p, double* r, const double* q, int64_t n,
-                         int num_slot, int den_slot);
 // Fused CG steps (one pass each plus a one-block finish):
 //  cg_update: alpha = scal[RZ] / scal[PQ]; x += alpha p; r -= alpha q;
 //             scal[Sum] = sum r, scal[RR] = |r - mean(r)|^2.
@@ -208,8 +203,6 @@ cudaError_t launch_split_df64(const mg_ctx* c, const double* x, df64* y, int64_t
 cudaError_t launch_join_df64(const mg_ctx* c, const df64* x, double* y, int64_t n, int accumulate);
 cudaError_t launch_dot_dfq(const mg_ctx* c, const double* p, const df64* qdf, double* q, int64_t n, int slot);
 cudaError_t launch_add(const mg_ctx* c, double* y, const double* x, int64_t n);  // y += x
-cudaError_t launch_xpby(const mg_ctx* c, double* p, const double* z, int64_t n, int num_slot, int den_slot,
-                        int alpha_slot);
 cudaError_t launch_to_f32(const mg_ctx* c, const double* x, float* y, int64_t n, int norm_slot);
 cudaError_t launch_from_f32(const mg_ctx* c, const float* x, double* y, int64_t n, int norm_slot);
 cudaError_t launch_rhs(const mg_ctx* c, const double* f, double* b);
