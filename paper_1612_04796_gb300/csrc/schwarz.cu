@@ -259,6 +259,70 @@ __global__ void __launch_bounds__(256) k_scatter_n(const T* __restrict__ corr, T
   }
 }
 
+// k_scatter_n when every node lies in at most two subdomains per direction
+// (2 N_O <= n): the two candidates of each direction in increasing offset,
+// all eight loads issued unconditionally (an absent candidate repeats the own
+// address and its value is replaced by zero), then summed in the same order
+// as k_scatter_n, so the two kernels give identical bits.
+template <typename T, int N>
+__global__ void __launch_bounds__(256) k_scatter_n2(const T* __restrict__ corr, T* __restrict__ u, int64_t Ne,
+                                                    int nx, int ny, int nz, SubShape g, int accumulate) {
+  constexpr int N3 = N * N * N;
+  const int64_t mxyz = (int64_t)g.mx * g.my * g.mz;
+  const int64_t total = Ne * N3;
+  for (int64_t dof = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; dof < total;
+       dof += (int64_t)gridDim.x * blockDim.x) {
+    const int e = (int)(dof / N3);  // element indices fit in 32 bits
+    const int loc = (int)(dof - (int64_t)e * N3);
+    const int i = loc % N, j = (loc / N) % N, k = loc / (N * N);
+    const int exy = e / nx;
+    const int ex = e - exy * nx, ey = exy % ny, ez = exy / ny;
+    int sx[2], px[2], sy[2], py[2], sz[2], pz[2];
+    bool vx, vy, vz;
+    auto cand = [&](int t, int no, int ec, int ne, int* sc, int* pc, bool* v) {
+      if (t < no) {
+        sc[0] = ec == 0 ? ne - 1 : ec - 1;
+        pc[0] = no + N + t;
+        sc[1] = ec;
+        pc[1] = no + t;
+        *v = true;
+      } else if (t >= N - no) {
+        sc[0] = ec;
+        pc[0] = no + t;
+        sc[1] = ec == ne - 1 ? 0 : ec + 1;
+        pc[1] = t - (N - no);
+        *v = true;
+      } else {
+        sc[0] = sc[1] = ec;
+        pc[0] = pc[1] = no + t;
+        *v = false;
+      }
+    };
+    cand(i, g.nox, ex, nx, sx, px, &vx);
+    cand(j, g.noy, ey, ny, sy, py, &vy);
+    cand(k, g.noz, ez, nz, sz, pz, &vz);
+    T val[8];
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+      for (int b = 0; b < 2; ++b)
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+          const int64_t sub = sx[a] + (int64_t)nx * (sy[b] + (int64_t)ny * sz[c]);
+          val[a + 2 * (b + 2 * c)] = corr[sub * mxyz + px[a] + g.mx * (py[b] + g.my * pz[c])];
+        }
+    T sum = 0;
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+      for (int b = 0; b < 2; ++b)
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+          if ((a == 0 || vx) && (b == 0 || vy) && (c == 0 || vz)) sum += val[a + 2 * (b + 2 * c)];
+    u[dof] = accumulate ? u[dof] + sum : sum;
+  }
+}
+
 template <typename T>
 const T* table_of(const mg_ctx* c);
 template <>
@@ -353,6 +417,15 @@ cudaError_t launch_scatter(const mg_ctx* c, int l, T* u, int accumulate) {
   const int eb = (int)blocks;
   const SubShape g{lv.m[0], lv.m[1], lv.m[2], lv.no[0], lv.no[1], lv.no[2]};
   c->nlaunch += 1;
+  const bool two = 2 * lv.no[0] <= lv.n && 2 * lv.no[1] <= lv.n && 2 * lv.no[2] <= lv.n;
+  if (two) {
+    switch (lv.n) {
+#define MGDG_SC2(N) case N: k_scatter_n2<T, N><<<eb, 256, 0, c->stream>>>(corr, u, c->Ne, c->ne[0], c->ne[1], c->ne[2], g, accumulate); return cudaGetLastError();
+      MGDG_SC2(3) MGDG_SC2(5) MGDG_SC2(9) MGDG_SC2(17) MGDG_SC2(33)
+#undef MGDG_SC2
+      default: break;
+    }
+  }
   switch (lv.n) {
 #define MGDG_SC(N) case N: k_scatter_n<T, N><<<eb, 256, 0, c->stream>>>(corr, u, c->Ne, c->ne[0], c->ne[1], c->ne[2], g, accumulate); return cudaGetLastError();
     MGDG_SC(3) MGDG_SC(5) MGDG_SC(9) MGDG_SC(17) MGDG_SC(33)
