@@ -46,33 +46,33 @@ WORKLOAD = {
     "seed": 2,
 }
 # Other configurations (same timing code; `--workload NAME`).  The default
-# bench line is WORKLOAD above (c2).
+# bench line is WORKLOAD above (cube16_p8).
 WORKLOADS = {
-    "c1": dict(workload="periodic unit cube, 4^3 elements, P=4 (8,000 DOFs), manufactured sines "
+    "sines4_p4": dict(workload="periodic unit cube, 4^3 elements, P=4 (8,000 DOFs), manufactured sines "
                         "(f = 12 pi^2 sin 2pi x sin 2pi y sin 2pi z), standalone V(1,1) MG, N_O=1, FP64, tol 1e-10",
                lengths=[1.0, 1.0, 1.0], elements=[4, 4, 4], P=4, overlap_layers=1, rhs="sines", precision="fp64",
                use_cg=False),
-    "c2": dict(WORKLOAD, rhs="gaussian", precision="fp64", use_cg=False),
-    "c3": dict(workload="periodic box [0,48]x[0,1]x[0,1], 48x8x8 elements, P=16 (15,092,736 DOFs), N_O node layers, "
+    "cube16_p8": dict(WORKLOAD, rhs="gaussian", precision="fp64", use_cg=False),
+    "box48x8x8_p16": dict(workload="periodic box [0,48]x[0,1]x[0,1], 48x8x8 elements, P=16 (15,092,736 DOFs), N_O node layers, "
                         "zero-mean Gaussian f (seed 3), FP32 V(1,1) preconditioner inside FP64 inexact PCG, tol 1e-10",
                lengths=[48.0, 1.0, 1.0], elements=[48, 8, 8], P=16, overlap_layers=1, rhs="gaussian", seed=3,
                precision="mixed", use_cg=True),
-    "c3ar48": dict(workload="periodic box [0,48]x[0,24]x[0,1], 8^3 elements (aspect 48:24:1), P=16 (2,515,456 DOFs), "
+    "ar48_p16": dict(workload="periodic box [0,48]x[0,24]x[0,1], 8^3 elements (aspect 48:24:1), P=16 (2,515,456 DOFs), "
                             "N_O node layers, zero-mean Gaussian f (seed 3), FP32 V(1,1) in FP64 PCG, tol 1e-10",
                    lengths=[48.0, 24.0, 1.0], elements=[8, 8, 8], P=16, overlap_layers=1, rhs="gaussian", seed=3,
                    precision="mixed", use_cg=True),
-    "ar48max": dict(workload="Table 2 robust method at AR = 48: periodic box [0,48]x[0,24]x[0,1], 8^3 elements, "
+    "ar48max_p16": dict(workload="Table 2 robust method at AR = 48: periodic box [0,48]x[0,24]x[0,1], 8^3 elements, "
                              "P=16 (2,515,456 DOFs), delta_O,i = min(0.08 max_j dx_j, dx_i) (N_O = 4, 6, 17 in x, y, z "
                              "on the finest level), variable V-cycle N_s,l = (1,1) x 3^(L-l), zero-mean Gaussian f "
                              "(seed 3), MG-CG, tol 1e-10",
                     lengths=[48.0, 24.0, 1.0], elements=[8, 8, 8], P=16, overlap_layers=1, overlap_mode="max",
                     overlap_frac=0.08, ns_growth=3, rhs="gaussian", seed=3, precision="fp64", use_cg=True),
-    "c4": dict(workload="periodic unit cube, 4^3 elements, P=32 (2,299,968 DOFs), f = 8 random Fourier modes "
+    "cube4_p32": dict(workload="periodic unit cube, 4^3 elements, P=32 (2,299,968 DOFs), f = 8 random Fourier modes "
                         "(|k|_inf <= 8, seed 4), FP32 V(1,1) preconditioner (CUDA-core FDM) in FP64 PCG, N_O=1, tol 1e-10",
                lengths=[1.0, 1.0, 1.0], elements=[4, 4, 4], P=32, overlap_layers=1, rhs="fourier", seed=4,
                precision="mixed", use_cg=True),
 }
-WORKLOADS["c5"] = dict(workload="serving stream: 512 solve requests, Poisson arrivals at 200/s (seed 5), periodic box "
+WORKLOADS["serving512"] = dict(workload="serving stream: 512 solve requests, Poisson arrivals at 200/s (seed 5), periodic box "
                                 "[0,AR]x[0,1]x[0,1], AR ~ U[1,8], n^3 elements with n in {4,8,16,24,32}, P in {2,4,8,16}, "
                                 "N_O=4 (default; --overlap), Gaussian f, FP32 V(1,1) in FP64 PCG (outer A p in "
                                 "double-float), tol 1e-10, "
@@ -95,7 +95,7 @@ def parse_args():
     ap.add_argument("--impl", default="mg", choices=["mg", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip e2e / mixed / roofline legs")
-    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="cube16_p8", choices=sorted(WORKLOADS))
     ap.add_argument("--overlap", type=int, default=None, help="override N_O of the workload")
     ap.add_argument("--precision", default=None, choices=["fp64", "mixed"], help="override the workload's precision")
     ap.add_argument("--outer-df64", action="store_true",
@@ -588,7 +588,7 @@ def run_serving(args):
         "metric": METRIC, "value": dofs / makespan, "unit": "DOF/s", "n_gpus": 1, "steps": 1, "warmup": 1,
         "ms_per_step": makespan * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32 multigrid / f64 outer", "data": "synthetic",
-        "config": dict(WORKLOADS["c5"], name="c5", requests=len(reqs), slots=slots, overlap_layers=overlap,
+        "config": dict(WORKLOADS["serving512"], name="serving512", requests=len(reqs), slots=slots, overlap_layers=overlap,
                        hbm_budget_gb=srv.scheduler.budget / 1e9, total_dofs=dofs,
                        outer_operator="double-float (FP32 pairs)" if srv.outer_df64 else "FP64"),
         "latency": summ, "max_concurrent": srv.max_active,
@@ -603,9 +603,9 @@ def main():
     args = parse_args()
     if args.impl == "reference":
         run_reference(args)
-    elif args.workload == "c5":
+    elif args.workload == "serving512":
         run_serving(args)
-    elif args.workload != "c2":
+    elif args.workload != "cube16_p8":
         run_workload(args)
     else:
         run_mg(args)

@@ -10,8 +10,8 @@ from patches import oracle_operator_at, oracle_smooth_at
 
 pytestmark = pytest.mark.gpu
 
-C2 = dict(lengths=(1.0, 1.0, 1.0), counts=(16, 16, 16), P=8)      # the bench workload
-C4 = dict(lengths=(1.0, 1.0, 1.0), counts=(4, 4, 4), P=32)
+CUBE16_P8 = dict(lengths=(1.0, 1.0, 1.0), counts=(16, 16, 16), P=8)      # 16^3 elements, P = 8: the bench workload
+CUBE4_P32 = dict(lengths=(1.0, 1.0, 1.0), counts=(4, 4, 4), P=32)
 
 
 def _cuda(x):
@@ -20,8 +20,8 @@ def _cuda(x):
 
 
 @pytest.fixture(scope="module")
-def c2(mg):
-    s = mg.MGSolver(C2["lengths"], C2["counts"], C2["P"])
+def cube16(mg):
+    s = mg.MGSolver(CUBE16_P8["lengths"], CUBE16_P8["counts"], CUBE16_P8["P"])
     N = s.num_dofs()
     u = inputs.gaussian(N, 41)
     f = inputs.gaussian(N, 42)
@@ -34,34 +34,34 @@ def _elements(counts, k, seed):
     return [0, Ne - 1] + list(rng.choice(Ne, k, replace=False))
 
 
-def test_c2_operator_sampled(c2):
-    s, u, _ = c2
+def test_cube16_p8_operator_sampled(cube16):
+    s, u, _ = cube16
     Au = s.apply_sipg(_cuda(u)).cpu().numpy()
     n3 = 9 ** 3
-    for e in _elements(C2["counts"], 3, 1):
-        ref = oracle_operator_at(u, C2["lengths"], C2["counts"], 8, e)
+    for e in _elements(CUBE16_P8["counts"], 3, 1):
+        ref = oracle_operator_at(u, CUBE16_P8["lengths"], CUBE16_P8["counts"], 8, e)
         got = Au[e * n3:(e + 1) * n3]
         assert np.max(np.abs(got - ref)) / np.max(np.abs(ref)) < 1e-12, e
 
 
-def test_c2_smoother_sampled(c2):
-    s, u, f = c2
+def test_cube16_p8_smoother_sampled(cube16):
+    s, u, f = cube16
     ut = _cuda(u)
     s.smooth(ut, _cuda(f))
     corr = ut.cpu().numpy() - u
     n3 = 9 ** 3
-    for e in _elements(C2["counts"], 1, 2):
-        ref = oracle_smooth_at(u, f, C2["lengths"], C2["counts"], 8, 1, e)
+    for e in _elements(CUBE16_P8["counts"], 1, 2):
+        ref = oracle_smooth_at(u, f, CUBE16_P8["lengths"], CUBE16_P8["counts"], 8, 1, e)
         got = corr[e * n3:(e + 1) * n3]
         assert np.max(np.abs(got - ref)) / np.max(np.abs(ref)) < 1e-12, e
 
 
-def test_c2_solve_properties(c2, mg):
+def test_cube16_p8_solve_properties(cube16, mg):
     """The bench solve: 12 V(1,1) cycles (Table 1 row 1, P = 8: rbar = 0.89,
     n10 = ceil(10 / 0.89) = 12), true FP64 residual <= 1e-10, zero mean, and
     bitwise identical on a rerun."""
     import torch
-    s, _, _ = c2
+    s, _, _ = cube16
     N = s.num_dofs()
     b = s.rhs(_cuda(inputs.gaussian(N, 2)))
     u1, it1, rel1, hist = s.solve(b, tol=1e-10)
@@ -74,30 +74,30 @@ def test_c2_solve_properties(c2, mg):
     u2, it2, _, _ = s.solve(b, tol=1e-10)
     assert it2 == it1 and torch.equal(u1, u2)
     # the mixed path on the same problem reaches the same tolerance
-    sm = mg.MGSolver(C2["lengths"], C2["counts"], C2["P"], precision="mixed")
+    sm = mg.MGSolver(CUBE16_P8["lengths"], CUBE16_P8["counts"], CUBE16_P8["P"], precision="mixed")
     um, itm, _, _ = sm.solve(b, tol=1e-10, use_cg=True)
     assert float(torch.linalg.norm(s.residual(um, b)) / torch.linalg.norm(b)) <= 1.01e-10
     assert float((um - u1).abs().max() / u1.abs().max()) < 1e-8
 
 
-def test_c4_operator_sampled(mg):
-    s = mg.MGSolver(C4["lengths"], C4["counts"], C4["P"])
+def test_cube4_p32_operator_sampled(mg):
+    s = mg.MGSolver(CUBE4_P32["lengths"], CUBE4_P32["counts"], CUBE4_P32["P"])
     u = inputs.gaussian(s.num_dofs(), 43)
     Au = s.apply_sipg(_cuda(u)).cpu().numpy()
     n3 = 33 ** 3
     for e in (0, 37):
-        ref = oracle_operator_at(u, C4["lengths"], C4["counts"], 32, e)
+        ref = oracle_operator_at(u, CUBE4_P32["lengths"], CUBE4_P32["counts"], 32, e)
         got = Au[e * n3:(e + 1) * n3]
         assert np.max(np.abs(got - ref)) / np.max(np.abs(ref)) < 1e-12, e
 
 
-def test_c4_mixed_solve_reaches_tolerance(mg):
+def test_cube4_p32_mixed_solve_reaches_tolerance(mg):
     """High order (P = 32): FP32 V-cycle inside FP64 CG reaches 1e-10 on the
     true FP64 residual; MG-CG takes about ceil(10 / 0.52) = 20 iterations
     (Table 1 row 2, P = 32)."""
     import torch
-    s = mg.MGSolver(C4["lengths"], C4["counts"], C4["P"], precision="mixed")
-    s64 = mg.MGSolver(C4["lengths"], C4["counts"], C4["P"])
+    s = mg.MGSolver(CUBE4_P32["lengths"], CUBE4_P32["counts"], CUBE4_P32["P"], precision="mixed")
+    s64 = mg.MGSolver(CUBE4_P32["lengths"], CUBE4_P32["counts"], CUBE4_P32["P"])
     N = s.num_dofs()
     x, y, z = (t.cpu().numpy() for t in s.node_coords())
     f = inputs.eval_fourier(inputs.fourier_modes(4), x, y, z)

@@ -244,7 +244,7 @@ def test_vcycle_fp64(solver_cache, P, overlap):
 
 
 def test_solve_c1_manufactured_matches_oracle(solver_cache):
-    """Configuration C1: unit cube, 4^3 elements, P = 4, N_O = 1, sines."""
+    """Unit cube, 4^3 elements, P = 4, N_O = 1, manufactured sines."""
     lengths, counts, P = (1.0, 1.0, 1.0), (4, 4, 4), 4
     s = solver_cache(lengths, counts, P)
     mesh = Mesh(lengths, counts)

@@ -81,8 +81,9 @@ def test_pcg_with_jacobi_preconditioner_is_textbook_pcg():
 
 
 def test_manufactured_solution_solve():
-    """BASELINE-shaped case C1 at reduced size: V(1,1) cycles reach the
-    tolerance and the solution approximates the exact sines."""
+    """The manufactured-solution case (unit cube, 4^3 elements, P = 4, sines):
+    V(1,1) cycles reach the tolerance and the solution approximates the exact
+    sines."""
     mesh = Mesh((1, 1, 1), (4, 4, 4))
     P = 4
     H = Hierarchy(mesh, P)
