@@ -76,7 +76,8 @@ WORKLOADS["serving512"] = dict(workload="serving stream: 512 solve requests, Poi
                                 "[0,AR]x[0,1]x[0,1], AR ~ U[1,8], n^3 elements with n in {4,8,16,24,32}, P in {2,4,8,16}, "
                                 "N_O=4 (default; --overlap), Gaussian f, FP32 V(1,1) in FP64 PCG (outer A p in "
                                 "double-float), tol 1e-10, "
-                                "admitted by HBM footprint, "
+                                "admitted by HBM footprint (smallest work first with aging; MG_SERVING_POLICY=fcfs "
+                                "for first come first served), "
                                 "one context and stream per slot")
 FP32_FLOP_PER_CLK_PER_SM = 256    # 128 FP32 FMA lanes per SM
 
@@ -568,8 +569,9 @@ def run_serving(args):
     n_req = int(os.environ.get("MG_SERVING_REQUESTS", "512"))
     overlap = 4 if args.overlap is None else args.overlap
     slots = int(os.environ.get("MG_SERVING_SLOTS", "8"))
+    policy = os.environ.get("MG_SERVING_POLICY", "smallest")
     reqs = request_stream(seed=5, n_requests=n_req, overlap=overlap)
-    srv = Server(slots=slots, keep_solution=False)
+    srv = Server(slots=slots, keep_solution=False, policy=policy)
     # warm-up: one small request of every order (module loading, first captures)
     warm = [r for r in request_stream(seed=6, n_requests=64, sizes=(4,)) if True][:8]
     srv.serve(warm, realtime=False)
@@ -590,6 +592,8 @@ def run_serving(args):
         "dtype": "f32 multigrid / f64 outer", "data": "synthetic",
         "config": dict(WORKLOADS["serving512"], name="serving512", requests=len(reqs), slots=slots, overlap_layers=overlap,
                        hbm_budget_gb=srv.scheduler.budget / 1e9, total_dofs=dofs,
+                       admission=policy + (" (aging after %.0f s)" % srv.scheduler.max_wait
+                                           if policy == "smallest" else ""),
                        outer_operator="double-float (FP32 pairs)" if srv.outer_df64 else "FP64"),
         "latency": summ, "max_concurrent": srv.max_active,
         "iterations": {"median": float(np.median([r.iterations for r in ok])),

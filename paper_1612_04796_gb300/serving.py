@@ -57,17 +57,30 @@ class Result:
 
 
 class Scheduler:
-    """First-come first-served admission under a slot limit and a memory
-    budget.  ``footprint(req)`` gives the bytes a request holds while it runs;
-    ``run(req, slot)`` does the work (on a worker thread) and returns a dict
-    that is stored on the Result."""
+    """Admission under a slot limit and a memory budget.  ``footprint(req)``
+    gives the bytes a request holds while it runs; ``run(req, slot)`` does the
+    work (on a worker thread) and returns a dict that is stored on the Result.
 
-    def __init__(self, run, footprint, slots, budget_bytes, clock=time.perf_counter):
+    policy "fcfs": strictly in arrival order (a request that does not fit
+    blocks the ones behind it).  policy "smallest": among the requests that
+    have arrived, the one with the least work (``work(req)``, default its DOF
+    count) that fits is admitted first; a request that has waited longer than
+    ``max_wait`` seconds is aged: the aged ones go first, in arrival order and
+    without being overtaken, so no request waits much longer than max_wait
+    for its turn."""
+
+    def __init__(self, run, footprint, slots, budget_bytes, clock=time.perf_counter, policy="fcfs", work=None,
+                 max_wait=10.0):
+        if policy not in ("fcfs", "smallest"):
+            raise ValueError("unknown policy %r" % policy)
         self.run = run
         self.footprint = footprint
         self.slots = int(slots)
         self.budget = int(budget_bytes)
         self.clock = clock
+        self.policy = policy
+        self.work = work if work is not None else (lambda r: r.dofs)
+        self.max_wait = float(max_wait)
         self.cv = threading.Condition()
         self.used = 0
         self.active = 0
@@ -88,32 +101,51 @@ class Scheduler:
             self.free_slots.append(slot)
             self.cv.notify_all()
 
+    def _pick(self, waiting, now, realtime):
+        """The request to admit next among `waiting` (arrived, not admitted),
+        or None to wait for resources.  Called with self.cv held."""
+        fits = lambda r: self.used + self.footprint(r) <= self.budget
+        if self.policy == "fcfs":
+            return waiting[0] if fits(waiting[0]) else None
+        aged = [r for r in waiting if realtime and now - r.arrival > self.max_wait]
+        if aged:
+            return aged[0] if fits(aged[0]) else None
+        best = None
+        for r in waiting:
+            if fits(r) and (best is None or self.work(r) < self.work(best)):
+                best = r
+        return best
+
     def serve(self, requests, realtime=True):
-        """Serve `requests` (sorted by arrival, seconds from the start).
-        Returns results in request order."""
+        """Serve `requests` (arrival in seconds from the start).  Returns
+        results in request order."""
         pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
+        waiting = []
         results = {r.id: Result(r.id) for r in requests}
         t0 = self.clock()
         threads = []
         for r in requests:
             if self.footprint(r) > self.budget:
                 raise ValueError("request %s needs more memory than the whole budget" % r.id)
-        while pending:
-            req = pending[0]
+        while pending or waiting:
             now = self.clock() - t0
-            if realtime and req.arrival > now:
-                time.sleep(min(req.arrival - now, 0.005))
+            while pending and (not realtime or pending[0].arrival <= now):
+                waiting.append(pending.popleft())
+            if not waiting:
+                time.sleep(min(pending[0].arrival - now, 0.005))
                 continue
-            need = self.footprint(req)
             with self.cv:
-                while not (self.free_slots and self.used + need <= self.budget):
-                    self.cv.wait(timeout=0.05)
+                req = self._pick(waiting, self.clock() - t0, realtime) if self.free_slots else None
+                if req is None:
+                    self.cv.wait(timeout=0.005 if pending else 0.05)
+                    continue
+                need = self.footprint(req)
                 slot = self.free_slots.pop(0)
                 self.used += need
                 self.active += 1
                 self.max_active = max(self.max_active, self.active)
                 active_now = self.active
-            pending.popleft()
+            waiting.remove(req)
             res = results[req.id]
             res.t_arrival = t0 + (req.arrival if realtime else 0.0)
             res.t_admit = self.clock()
@@ -144,7 +176,7 @@ class Server:
     slot owns a CUDA stream."""
 
     def __init__(self, slots=8, budget_bytes=None, precision="mixed", use_cg=True, device="cuda", keep_solution=True,
-                 outer_df64=True):
+                 outer_df64=True, policy="fcfs", max_wait=10.0):
         import torch
 
         from ._lib import MgOpts, load_library
@@ -164,7 +196,7 @@ class Server:
         self.use_cg = use_cg
         self.keep = keep_solution
         self.streams = [torch.cuda.Stream(self.device) for _ in range(slots)]
-        self.scheduler = Scheduler(self._run, self.footprint, slots, budget_bytes)
+        self.scheduler = Scheduler(self._run, self.footprint, slots, budget_bytes, policy=policy, max_wait=max_wait)
 
     def footprint(self, req):
         """Workspace plus the request's own vectors (f, b, u), from the

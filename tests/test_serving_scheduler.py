@@ -79,3 +79,42 @@ def test_request_stream_shape():
     assert all(1.0 <= r.lengths[0] <= 8.0 for r in reqs)
     arr = [r.arrival for r in reqs]
     assert arr == sorted(arr) and 1.5 < arr[-1] < 4.0  # ~512 / 200 per second
+
+
+def test_smallest_first_admits_small_requests_first():
+    """policy "smallest": with one slot and everything arrived, the requests
+    run in increasing work order."""
+    reqs = [Request(i, (1, 1, 1), (n, n, n), 2, i, arrival=0.0) for i, n in enumerate([16, 4, 8, 32, 4])]
+    log = []
+    sched = Scheduler(_fake({i: 0.005 for i in range(5)}, log), lambda r: 1, slots=1, budget_bytes=10,
+                      policy="smallest")
+    sched.serve(reqs, realtime=False)
+    starts = [rid for kind, rid, _ in log if kind == "start"]
+    assert starts == [1, 4, 2, 0, 3]
+
+
+def test_smallest_first_skips_what_does_not_fit_and_ages():
+    """A large request that does not fit does not block smaller ones; once it
+    has waited longer than max_wait it goes first and is not overtaken."""
+    big = Request(0, (1, 1, 1), (32, 32, 32), 2, 0, arrival=0.0)
+    small = [Request(i, (1, 1, 1), (4, 4, 4), 2, i, arrival=0.0) for i in range(1, 9)]
+    log = []
+    size = {0: 10}
+    size.update({i: 4 for i in range(1, 9)})
+    sched = Scheduler(_fake({i: 0.03 for i in range(9)}, log), lambda r: size[r.id], slots=3, budget_bytes=10,
+                      policy="smallest", max_wait=0.05)
+    sched.serve([big] + small, realtime=True)
+    starts = [rid for kind, rid, _ in log if kind == "start"]
+    assert starts[0] != 0                       # small ones first while nothing aged
+    i_big = starts.index(0)
+    assert i_big < len(starts) - 1              # aged: admitted before the small ones are exhausted
+    used, peak = 0, 0
+    for kind, rid, _ in log:
+        used += size[rid] if kind == "start" else -size[rid]
+        peak = max(peak, used)
+    assert peak <= 10
+
+
+def test_unknown_policy_is_rejected():
+    with pytest.raises(ValueError):
+        Scheduler(lambda r, s: {}, lambda r: 1, slots=1, budget_bytes=1, policy="lifo")
