@@ -105,3 +105,30 @@ def test_cube4_p32_mixed_solve_reaches_tolerance(mg):
     u, its, rel, _ = s.solve(b, tol=1e-10, use_cg=True, maxit=60)
     assert float(torch.linalg.norm(s64.residual(u, b)) / torch.linalg.norm(b)) <= 1.01e-10
     assert 14 <= its <= 26
+
+
+def test_cube16_p8_double_float_solves(cube16, mg):
+    """The bench problem with the multigrid in double-float: the FP64 path's
+    12 cycles and a solution within 1e-12 of the FP64 one; and the mixed
+    solve with the double-float outer operator: the true FP64 residual
+    reaches 1e-10 in the same 9 iterations as with the FP64 outer operator."""
+    import torch
+    s, _, _ = cube16
+    N = s.num_dofs()
+    b = s.rhs(_cuda(inputs.gaussian(N, 2)))
+    u64, it64, _, _ = s.solve(b, tol=1e-10)
+    sd = mg.MGSolver(CUBE16_P8["lengths"], CUBE16_P8["counts"], CUBE16_P8["P"], precision="df64")
+    ud, itd, _, _ = sd.solve(b, tol=1e-10)
+    assert itd == it64
+    assert float(torch.linalg.norm(s.residual(ud, b)) / torch.linalg.norm(b)) <= 1e-10
+    assert float((ud - u64).abs().max() / u64.abs().max()) < 1e-12
+    sd.close()
+    its = []
+    for df in (False, True):
+        sm = mg.MGSolver(CUBE16_P8["lengths"], CUBE16_P8["counts"], CUBE16_P8["P"], precision="mixed",
+                         outer_df64=df)
+        um, itm, _, _ = sm.solve(b, tol=1e-10, use_cg=True)
+        assert float(torch.linalg.norm(s.residual(um, b)) / torch.linalg.norm(b)) <= 1.01e-10
+        its.append(itm)
+        sm.close()
+    assert its[0] == its[1]
