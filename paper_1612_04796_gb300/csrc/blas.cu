@@ -27,6 +27,7 @@ __device__ double block_reduce(double v, double* sh) {
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_partial(const T* __restrict__ x, const T* __restrict__ y, int64_t n,
                                                       int mode, double* partial) {
+  pdl_entry();
   __shared__ double sh[kThreads];
   double acc = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -36,6 +37,7 @@ __global__ void __launch_bounds__(kThreads) k_partial(const T* __restrict__ x, c
 }
 
 __global__ void __launch_bounds__(kThreads) k_final(const double* partial, int nb, double* scal, int slot) {
+  pdl_entry();
   __shared__ double sh[kThreads];
   double acc = 0.0;
   for (int i = threadIdx.x; i < nb; i += blockDim.x) acc += partial[i];
@@ -45,6 +47,7 @@ __global__ void __launch_bounds__(kThreads) k_final(const double* partial, int n
 
 template <typename T>
 __global__ void k_sub_mean(T* x, int64_t n, const double* scal, int slot) {
+  pdl_entry();
   const T mean = (T)(scal[slot] / (double)n);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     x[i] -= mean;
@@ -54,6 +57,7 @@ __global__ void k_sub_mean(T* x, int64_t n, const double* scal, int slot) {
 __global__ void __launch_bounds__(kThreads) k_cg_update(double* __restrict__ x, const double* __restrict__ p,
                                                         double* __restrict__ r, const double* __restrict__ q,
                                                         int64_t n, double* scal, double* partial) {
+  pdl_entry();
   __shared__ double sh[kThreads];
   const double alpha = scal[kSlotRZ] / scal[kSlotPQ];
   if (blockIdx.x == 0 && threadIdx.x == 0) scal[kSlotAlpha] = alpha;
@@ -86,6 +90,7 @@ __device__ void final_columns(const double* partial, int nb, int cols, double* v
 
 __global__ void __launch_bounds__(kThreads) k_cg_update_final(const double* partial, int nb, double* scal,
                                                               int64_t n) {
+  pdl_entry();
   __shared__ double sh[kThreads];
   double v[2];
   final_columns(partial, nb, 2, v, sh);
@@ -107,6 +112,7 @@ template <typename TZ>
 __global__ void __launch_bounds__(kThreads) k_cg_sums(const TZ* __restrict__ zs, const double* __restrict__ q,
                                                       const double* __restrict__ r, int64_t n, const double* scal,
                                                       double* partial) {
+  pdl_entry();
   __shared__ double sh[kThreads];
   const double zsc = z_scale<TZ>(scal);
   double a[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
@@ -126,6 +132,7 @@ __global__ void __launch_bounds__(kThreads) k_cg_sums(const TZ* __restrict__ zs,
 }
 
 __global__ void __launch_bounds__(kThreads) k_cg_sums_final(const double* partial, int nb, double* scal, int64_t n) {
+  pdl_entry();
   __shared__ double sh[kThreads];
   double v[5];
   final_columns(partial, nb, 5, v, sh);
@@ -144,6 +151,7 @@ __global__ void __launch_bounds__(kThreads) k_cg_sums_final(const double* partia
 template <typename TZ>
 __global__ void k_cg_newdir(double* __restrict__ p, const TZ* __restrict__ zs, int64_t n, const double* scal,
                             df64* __restrict__ pdf) {
+  pdl_entry();
   const double zsc = z_scale<TZ>(scal), muz = scal[kSlotMuZ], beta = scal[kSlotBeta];
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const double v = ((double)zs[i] * zsc - muz) + beta * p[i];
@@ -154,11 +162,13 @@ __global__ void k_cg_newdir(double* __restrict__ p, const TZ* __restrict__ zs, i
 
 // y = x (accumulate = 0) or y += x (accumulate = 1), x double-float, y FP64
 __global__ void k_join_df64(const df64* __restrict__ x, double* __restrict__ y, int64_t n, int accumulate) {
+  pdl_entry();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     y[i] = accumulate ? y[i] + df_to_double(x[i]) : df_to_double(x[i]);
 }
 
 __global__ void k_split_df64(const double* __restrict__ x, df64* __restrict__ y, int64_t n) {
+  pdl_entry();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     y[i] = df_from_double(x[i]);
 }
@@ -166,6 +176,7 @@ __global__ void k_split_df64(const double* __restrict__ x, df64* __restrict__ y,
 // q = qdf as FP64 and the partial sums of p . q
 __global__ void __launch_bounds__(kThreads) k_dot_dfq(const double* __restrict__ p, const df64* __restrict__ qdf,
                                                       double* __restrict__ q, int64_t n, double* partial) {
+  pdl_entry();
   __shared__ double sh[kThreads];
   double acc = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -178,12 +189,14 @@ __global__ void __launch_bounds__(kThreads) k_dot_dfq(const double* __restrict__
 }
 
 __global__ void k_add(double* __restrict__ y, const double* __restrict__ x, int64_t n) {
+  pdl_entry();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     y[i] += x[i];
 }
 
 __global__ void k_to_f32(const double* __restrict__ x, float* __restrict__ y, int64_t n, const double* scal,
                          int slot) {
+  pdl_entry();
   double s = 1.0;
   if (slot >= 0) {
     double nrm = sqrt(scal[slot]);
@@ -195,6 +208,7 @@ __global__ void k_to_f32(const double* __restrict__ x, float* __restrict__ y, in
 
 __global__ void k_from_f32(const float* __restrict__ x, double* __restrict__ y, int64_t n, const double* scal,
                            int slot) {
+  pdl_entry();
   double s = 1.0;
   if (slot >= 0) {
     double nrm = sqrt(scal[slot]);
@@ -221,6 +235,7 @@ __device__ __forceinline__ double mass_at(const MassArgs& a, int64_t dof) {
 // partial sums of M f (slot 0) and M (slot 1)
 __global__ void __launch_bounds__(kThreads) k_mass_partial(MassArgs a, const double* __restrict__ f,
                                                            double* partial) {
+  pdl_entry();
   __shared__ double sh[kThreads];
   const int64_t total = a.Ne * a.n * a.n * a.n;
   double s0 = 0.0, s1 = 0.0;
@@ -239,6 +254,7 @@ __global__ void __launch_bounds__(kThreads) k_mass_partial(MassArgs a, const dou
 }
 
 __global__ void k_rhs(MassArgs a, const double* __restrict__ f, double* __restrict__ b, const double* scal) {
+  pdl_entry();
   const double fbar = scal[kSlotMassF] / scal[kSlotMass];
   const int64_t total = a.Ne * a.n * a.n * a.n;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x)
@@ -247,6 +263,7 @@ __global__ void k_rhs(MassArgs a, const double* __restrict__ f, double* __restri
 
 __global__ void k_coords(const double* tab, int64_t nodes, int n, int64_t Ne, int nx, int ny, double hx, double hy,
                          double hz, double* x, double* y, double* z) {
+  pdl_entry();
   const int n3 = n * n * n;
   const int64_t total = Ne * n3;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
@@ -263,6 +280,7 @@ __global__ void k_coords(const double* tab, int64_t nodes, int n, int64_t Ne, in
 
 template <typename T>
 __global__ void k_zero(T* x, int64_t n) {
+  pdl_entry();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     x[i] = (T)0;
 }
@@ -276,9 +294,9 @@ inline int grid_for(int64_t n) {
 
 template <typename T>
 cudaError_t reduce(const mg_ctx* c, const T* x, const T* y, int64_t n, int mode, int slot) {
-  k_partial<T><<<kRedBlocks, kThreads, 0, c->stream>>>(x, y, n, mode, c->ws.red);
+  launch_pdl(k_partial<T>, kRedBlocks, kThreads, 0, c->stream, x, y, n, mode, c->ws.red);
   c->nlaunch += 1;
-  k_final<<<1, kThreads, 0, c->stream>>>(c->ws.red, kRedBlocks, c->ws.scal, slot);
+  launch_pdl(k_final, 1, kThreads, 0, c->stream, c->ws.red, kRedBlocks, c->ws.scal, slot);
   c->nlaunch += 1;
   return cudaGetLastError();
 }
@@ -294,14 +312,14 @@ cudaError_t launch_sum(const mg_ctx* c, const double* x, int64_t n, int slot) {
 }
 
 cudaError_t launch_sub_mean(const mg_ctx* c, double* x, int64_t n, int sum_slot) {
-  k_sub_mean<double><<<grid_for(n), kThreads, 0, c->stream>>>(x, n, c->ws.scal, sum_slot);
+  launch_pdl(k_sub_mean<double>, grid_for(n), kThreads, 0, c->stream, x, n, c->ws.scal, sum_slot);
   c->nlaunch += 1;
   return cudaGetLastError();
 }
 
 cudaError_t launch_cg_update(const mg_ctx* c, double* x, const double* p, double* r, const double* q, int64_t n) {
-  k_cg_update<<<kRedBlocks, kThreads, 0, c->stream>>>(x, p, r, q, n, c->ws.scal, c->ws.red);
-  k_cg_update_final<<<1, kThreads, 0, c->stream>>>(c->ws.red, kRedBlocks, c->ws.scal, n);
+  launch_pdl(k_cg_update, kRedBlocks, kThreads, 0, c->stream, x, p, r, q, n, c->ws.scal, c->ws.red);
+  launch_pdl(k_cg_update_final, 1, kThreads, 0, c->stream, c->ws.red, kRedBlocks, c->ws.scal, n);
   c->nlaunch += 2;
   return cudaGetLastError();
 }
@@ -309,9 +327,9 @@ cudaError_t launch_cg_update(const mg_ctx* c, double* x, const double* p, double
 template <typename TZ>
 cudaError_t launch_cg_direction(const mg_ctx* c, double* p, const TZ* z, const double* q, const double* r, int64_t n,
                                 df64* pdf) {
-  k_cg_sums<TZ><<<kRedBlocks, kThreads, 0, c->stream>>>(z, q, r, n, c->ws.scal, c->ws.red);
-  k_cg_sums_final<<<1, kThreads, 0, c->stream>>>(c->ws.red, kRedBlocks, c->ws.scal, n);
-  k_cg_newdir<TZ><<<grid_for(n), kThreads, 0, c->stream>>>(p, z, n, c->ws.scal, pdf);
+  launch_pdl(k_cg_sums<TZ>, kRedBlocks, kThreads, 0, c->stream, z, q, r, n, c->ws.scal, c->ws.red);
+  launch_pdl(k_cg_sums_final, 1, kThreads, 0, c->stream, c->ws.red, kRedBlocks, c->ws.scal, n);
+  launch_pdl(k_cg_newdir<TZ>, grid_for(n), kThreads, 0, c->stream, p, z, n, c->ws.scal, pdf);
   c->nlaunch += 3;
   return cudaGetLastError();
 }
@@ -324,38 +342,38 @@ template cudaError_t launch_cg_direction<df64>(const mg_ctx*, double*, const df6
                                                int64_t, df64*);
 
 cudaError_t launch_split_df64(const mg_ctx* c, const double* x, df64* y, int64_t n) {
-  k_split_df64<<<grid_for(n), kThreads, 0, c->stream>>>(x, y, n);
+  launch_pdl(k_split_df64, grid_for(n), kThreads, 0, c->stream, x, y, n);
   c->nlaunch += 1;
   return cudaGetLastError();
 }
 
 cudaError_t launch_join_df64(const mg_ctx* c, const df64* x, double* y, int64_t n, int accumulate) {
-  k_join_df64<<<grid_for(n), kThreads, 0, c->stream>>>(x, y, n, accumulate);
+  launch_pdl(k_join_df64, grid_for(n), kThreads, 0, c->stream, x, y, n, accumulate);
   c->nlaunch += 1;
   return cudaGetLastError();
 }
 
 cudaError_t launch_dot_dfq(const mg_ctx* c, const double* p, const df64* qdf, double* q, int64_t n, int slot) {
-  k_dot_dfq<<<kRedBlocks, kThreads, 0, c->stream>>>(p, qdf, q, n, c->ws.red);
-  k_final<<<1, kThreads, 0, c->stream>>>(c->ws.red, kRedBlocks, c->ws.scal, slot);
+  launch_pdl(k_dot_dfq, kRedBlocks, kThreads, 0, c->stream, p, qdf, q, n, c->ws.red);
+  launch_pdl(k_final, 1, kThreads, 0, c->stream, c->ws.red, kRedBlocks, c->ws.scal, slot);
   c->nlaunch += 2;
   return cudaGetLastError();
 }
 
 cudaError_t launch_add(const mg_ctx* c, double* y, const double* x, int64_t n) {
-  k_add<<<grid_for(n), kThreads, 0, c->stream>>>(y, x, n);
+  launch_pdl(k_add, grid_for(n), kThreads, 0, c->stream, y, x, n);
   c->nlaunch += 1;
   return cudaGetLastError();
 }
 
 cudaError_t launch_to_f32(const mg_ctx* c, const double* x, float* y, int64_t n, int norm_slot) {
-  k_to_f32<<<grid_for(n), kThreads, 0, c->stream>>>(x, y, n, c->ws.scal, norm_slot);
+  launch_pdl(k_to_f32, grid_for(n), kThreads, 0, c->stream, x, y, n, c->ws.scal, norm_slot);
   c->nlaunch += 1;
   return cudaGetLastError();
 }
 
 cudaError_t launch_from_f32(const mg_ctx* c, const float* x, double* y, int64_t n, int norm_slot) {
-  k_from_f32<<<grid_for(n), kThreads, 0, c->stream>>>(x, y, n, c->ws.scal, norm_slot);
+  launch_pdl(k_from_f32, grid_for(n), kThreads, 0, c->stream, x, y, n, c->ws.scal, norm_slot);
   c->nlaunch += 1;
   return cudaGetLastError();
 }
@@ -367,13 +385,13 @@ cudaError_t launch_rhs(const mg_ctx* c, const double* f, double* b) {
   for (int d = 0; d < 3; ++d) a.mass[d] = lv.t[d].mass;
   a.n = lv.n;
   a.Ne = c->Ne;
-  k_mass_partial<<<kRedBlocks, kThreads, 0, c->stream>>>(a, f, c->ws.red);
+  launch_pdl(k_mass_partial, kRedBlocks, kThreads, 0, c->stream, a, f, c->ws.red);
   c->nlaunch += 1;
-  k_final<<<1, kThreads, 0, c->stream>>>(c->ws.red, kRedBlocks, c->ws.scal, kSlotMassF);
+  launch_pdl(k_final, 1, kThreads, 0, c->stream, c->ws.red, kRedBlocks, c->ws.scal, kSlotMassF);
   c->nlaunch += 1;
-  k_final<<<1, kThreads, 0, c->stream>>>(c->ws.red + kRedBlocks, kRedBlocks, c->ws.scal, kSlotMass);
+  launch_pdl(k_final, 1, kThreads, 0, c->stream, c->ws.red + kRedBlocks, kRedBlocks, c->ws.scal, kSlotMass);
   c->nlaunch += 1;
-  k_rhs<<<grid_for(lv.N), kThreads, 0, c->stream>>>(a, f, b, c->ws.scal);
+  launch_pdl(k_rhs, grid_for(lv.N), kThreads, 0, c->stream, a, f, b, c->ws.scal);
   c->nlaunch += 1;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -383,7 +401,7 @@ cudaError_t launch_rhs(const mg_ctx* c, const double* f, double* b) {
 
 cudaError_t launch_coords(const mg_ctx* c, int l, double* x, double* y, double* z) {
   const LevelInfo& lv = c->lev[l];
-  k_coords<<<grid_for(lv.N), kThreads, 0, c->stream>>>(c->ws.tab64, lv.t[0].nodes, lv.n, c->Ne, c->ne[0], c->ne[1],
+  launch_pdl(k_coords, grid_for(lv.N), kThreads, 0, c->stream, c->ws.tab64, lv.t[0].nodes, lv.n, c->Ne, c->ne[0], c->ne[1],
                                                         lv.h[0], lv.h[1], lv.h[2], x, y, z);
   c->nlaunch += 1;
   return cudaGetLastError();
@@ -391,7 +409,7 @@ cudaError_t launch_coords(const mg_ctx* c, int l, double* x, double* y, double* 
 
 template <typename T>
 cudaError_t launch_zero(const mg_ctx* c, T* x, int64_t n) {
-  k_zero<T><<<grid_for(n), kThreads, 0, c->stream>>>(x, n);
+  launch_pdl(k_zero<T>, grid_for(n), kThreads, 0, c->stream, x, n);
   c->nlaunch += 1;
   return cudaGetLastError();
 }

@@ -44,6 +44,7 @@ __global__ void k_coarse_axis(const TI* __restrict__ in, TO* __restrict__ out, c
                               CoarseDims d, int axis, int backward, int in_eb, int out_eb, const double* scal,
                               int mean_slot, int scale, const double* lx, const double* ly, const double* lz,
                               int nx0, int ny0, int nz0) {
+  pdl_entry();
   const int Nx = d.Ng[0], Ny = d.Ng[1], Nz = d.Ng[2];
   const int64_t total = (int64_t)Nx * Ny * Nz;
   const int Na = d.Ng[axis];
@@ -84,13 +85,13 @@ cudaError_t coarse_passes(const double* const Q[3], const double* const lam[3], 
   if (blocks > 152 * 8) blocks = 152 * 8;
   const int* nz = null_mode;
   const int b = (int)blocks;
-  k_coarse_axis<TI, double><<<b, 256, 0, s>>>(f0, A, Q[0], d, 0, 0, 1, 0, scal, mean_slot, 0, 0, 0, 0, 0, 0, 0);
-  k_coarse_axis<double, double><<<b, 256, 0, s>>>(A, B, Q[1], d, 1, 0, 0, 0, scal, -1, 0, 0, 0, 0, 0, 0, 0);
-  k_coarse_axis<double, double><<<b, 256, 0, s>>>(B, A, Q[2], d, 2, 0, 0, 0, scal, -1, 1, lam[0], lam[1], lam[2],
+  launch_pdl(k_coarse_axis<TI, double>, b, 256, 0, s, f0, A, Q[0], d, 0, 0, 1, 0, scal, mean_slot, 0, nullptr, nullptr, nullptr, 0, 0, 0);
+  launch_pdl(k_coarse_axis<double, double>, b, 256, 0, s, A, B, Q[1], d, 1, 0, 0, 0, scal, -1, 0, nullptr, nullptr, nullptr, 0, 0, 0);
+  launch_pdl(k_coarse_axis<double, double>, b, 256, 0, s, B, A, Q[2], d, 2, 0, 0, 0, scal, -1, 1, lam[0], lam[1], lam[2],
                                                   nz[0], nz[1], nz[2]);
-  k_coarse_axis<double, double><<<b, 256, 0, s>>>(A, B, Q[2], d, 2, 1, 0, 0, scal, -1, 0, 0, 0, 0, 0, 0, 0);
-  k_coarse_axis<double, double><<<b, 256, 0, s>>>(B, A, Q[1], d, 1, 1, 0, 0, scal, -1, 0, 0, 0, 0, 0, 0, 0);
-  k_coarse_axis<double, TO><<<b, 256, 0, s>>>(A, u0, Q[0], d, 0, 1, 0, 1, scal, -1, 0, 0, 0, 0, 0, 0, 0);
+  launch_pdl(k_coarse_axis<double, double>, b, 256, 0, s, A, B, Q[2], d, 2, 1, 0, 0, scal, -1, 0, nullptr, nullptr, nullptr, 0, 0, 0);
+  launch_pdl(k_coarse_axis<double, double>, b, 256, 0, s, B, A, Q[1], d, 1, 1, 0, 0, scal, -1, 0, nullptr, nullptr, nullptr, 0, 0, 0);
+  launch_pdl(k_coarse_axis<double, TO>, b, 256, 0, s, A, u0, Q[0], d, 0, 1, 0, 1, scal, -1, 0, nullptr, nullptr, nullptr, 0, 0, 0);
   return cudaGetLastError();
 }
 

@@ -250,6 +250,7 @@ __device__ __forceinline__ void tc_writeback(const TcArgs& a, float* A, uint32_t
 }
 
 __global__ void __launch_bounds__(kTcThreads) k_fdm_tc(TcArgs a) {
+  pdl_entry();
   extern __shared__ __align__(128) unsigned char tc_smem[];
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tmem_slot;
@@ -486,7 +487,7 @@ cudaError_t launch_fdm_tc(const mg_ctx* c, int l, const float* r, int self_test)
   if (e != cudaSuccess) return e;
   const int64_t groups = (c->Ne + G - 1) / G;
   const int blocks = (int)std::min<int64_t>(groups, 152LL * per_sm);
-  k_fdm_tc<<<blocks, kTcThreads, smem, c->stream>>>(a);
+  launch_pdl(k_fdm_tc, blocks, kTcThreads, smem, c->stream, a);
   c->nlaunch += 1;
   return cudaGetLastError();
 }

@@ -95,6 +95,7 @@ struct FdmShape {
 
 template <typename T, int M>
 __global__ void __launch_bounds__(256) k_fdm_m(FdmArgs<T> a) {
+  pdl_entry();
   constexpr int M2 = M * M, M3 = M2 * M;
   constexpr bool kSmemTile = FdmShape<T, M>::smem_tile;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -208,7 +209,7 @@ cudaError_t launch_fdm_m(const FdmArgs<T>& a, int blocks, int threads, size_t /*
     cudaError_t e = cudaFuncSetAttribute(k_fdm_m<T, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  k_fdm_m<T, M><<<blocks, threads, smem, s>>>(a);
+  launch_pdl(k_fdm_m<T, M>, blocks, threads, smem, s, a);
   return cudaGetLastError();
 }
 

@@ -13,6 +13,32 @@
 
 namespace mgdg {
 
+// Programmatic dependent launch.  Hot-path kernels are launched with
+// launch_pdl, which lets a kernel be launched as soon as the blocks of its
+// predecessor in the stream (or graph) have exited, before that grid has
+// formally completed; every such kernel starts with pdl_entry(), which waits
+// until the predecessor has completed and its writes are visible, before
+// touching memory.  (Triggering the successor early, at the start of each
+// kernel, was measured slower: its waiting blocks compete for the SMs.)  A
+// kernel launched without the attribute passes the wait at once.
+__device__ __forceinline__ void pdl_entry() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<Args&&>(args)...);
+}
+
 constexpr int kMaxLevels = 6;   // P <= 32
 constexpr int kMaxP = 32;
 constexpr int kMaxN = kMaxP + 1;        // nodes per element and direction

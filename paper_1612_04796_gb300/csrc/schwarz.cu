@@ -85,6 +85,7 @@ __device__ __forceinline__ void bwd_eo(const T* v, const T* __restrict__ SW, int
 // through the cache from the table array.
 template <typename T>
 __global__ void __launch_bounds__(256) k_fdm(FdmArgs<T> a) {
+  pdl_entry();
   extern __shared__ __align__(16) unsigned char smraw[];
   T* sm = reinterpret_cast<T*>(smraw);
   const int mx = a.md[0], my = a.md[1], mz = a.md[2], mxy = mx * my, mxyz = mxy * mz;
@@ -177,6 +178,7 @@ struct SubShape {
 template <typename T>
 __global__ void k_scatter(const T* __restrict__ corr, T* __restrict__ u, int64_t Ne, int nx, int ny, int nz, int n,
                           SubShape g, int accumulate) {
+  pdl_entry();
   const int n3 = n * n * n;
   const int64_t mxyz = (int64_t)g.mx * g.my * g.mz;
   const int64_t total = Ne * n3;
@@ -219,6 +221,7 @@ __global__ void k_scatter(const T* __restrict__ corr, T* __restrict__ u, int64_t
 template <typename T, int N>
 __global__ void __launch_bounds__(256) k_scatter_n(const T* __restrict__ corr, T* __restrict__ u, int64_t Ne, int nx,
                                                    int ny, int nz, SubShape g, int accumulate) {
+  pdl_entry();
   constexpr int N3 = N * N * N;
   const int64_t mxyz = (int64_t)g.mx * g.my * g.mz;
   const int64_t total = Ne * N3;
@@ -267,6 +270,7 @@ __global__ void __launch_bounds__(256) k_scatter_n(const T* __restrict__ corr, T
 template <typename T, int N>
 __global__ void __launch_bounds__(256) k_scatter_n2(const T* __restrict__ corr, T* __restrict__ u, int64_t Ne,
                                                     int nx, int ny, int nz, SubShape g, int accumulate) {
+  pdl_entry();
   constexpr int N3 = N * N * N;
   const int64_t mxyz = (int64_t)g.mx * g.my * g.mz;
   const int64_t total = Ne * N3;
@@ -402,7 +406,7 @@ cudaError_t launch_fdm(const mg_ctx* c, int l, const T* r) {
   const int lines = std::max(lv.m[1] * lv.m[2], std::max(lv.m[0] * lv.m[2], lv.m[0] * lv.m[1]));
   int threads = lines >= 256 ? 256 : 128;
   int64_t blocks = c->Ne < 152 * 8 ? c->Ne : 152 * 8;
-  k_fdm<T><<<(int)blocks, threads, smem, c->stream>>>(a);
+  launch_pdl(k_fdm<T>, (int)blocks, threads, smem, c->stream, a);
   c->nlaunch += 1;
   return cudaGetLastError();
 }
@@ -420,19 +424,19 @@ cudaError_t launch_scatter(const mg_ctx* c, int l, T* u, int accumulate) {
   const bool two = 2 * lv.no[0] <= lv.n && 2 * lv.no[1] <= lv.n && 2 * lv.no[2] <= lv.n;
   if (two) {
     switch (lv.n) {
-#define MGDG_SC2(N) case N: k_scatter_n2<T, N><<<eb, 256, 0, c->stream>>>(corr, u, c->Ne, c->ne[0], c->ne[1], c->ne[2], g, accumulate); return cudaGetLastError();
+#define MGDG_SC2(N) case N: launch_pdl(k_scatter_n2<T, N>, eb, 256, 0, c->stream, corr, u, c->Ne, c->ne[0], c->ne[1], c->ne[2], g, accumulate); return cudaGetLastError();
       MGDG_SC2(3) MGDG_SC2(5) MGDG_SC2(9) MGDG_SC2(17) MGDG_SC2(33)
 #undef MGDG_SC2
       default: break;
     }
   }
   switch (lv.n) {
-#define MGDG_SC(N) case N: k_scatter_n<T, N><<<eb, 256, 0, c->stream>>>(corr, u, c->Ne, c->ne[0], c->ne[1], c->ne[2], g, accumulate); return cudaGetLastError();
+#define MGDG_SC(N) case N: launch_pdl(k_scatter_n<T, N>, eb, 256, 0, c->stream, corr, u, c->Ne, c->ne[0], c->ne[1], c->ne[2], g, accumulate); return cudaGetLastError();
     MGDG_SC(3) MGDG_SC(5) MGDG_SC(9) MGDG_SC(17) MGDG_SC(33)
 #undef MGDG_SC
     default: break;
   }
-  k_scatter<T><<<(int)blocks, 256, 0, c->stream>>>(corr, u, c->Ne, c->ne[0], c->ne[1], c->ne[2], lv.n, g,
+  launch_pdl(k_scatter<T>, (int)blocks, 256, 0, c->stream, corr, u, c->Ne, c->ne[0], c->ne[1], c->ne[2], lv.n, g,
                                                     accumulate);
   return cudaGetLastError();
 }

@@ -106,6 +106,7 @@ __device__ __forceinline__ void line_apply(const OpArgs<T>& a, int d, const T* _
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_sipg(OpArgs<T> a) {
+  pdl_entry();
   const int n = a.n, n2 = n * n, n3 = n2 * n, P = n - 1;
   const int lines = a.epb * n2;
   const T* m3 = a.tab + a.mass3;
@@ -227,6 +228,7 @@ __device__ __forceinline__ void line_apply_n(const OpArgs<T>& a, int d, const T*
 
 template <typename T, int N>
 __global__ void __launch_bounds__(256) k_sipg_n(OpArgs<T> a) {
+  pdl_entry();
   constexpr int n2 = N * N, n3 = n2 * N;
   const int lines = a.epb * n2;
   const T* m3 = a.tab + a.mass3;
@@ -271,6 +273,7 @@ __global__ void __launch_bounds__(256) k_sipg_n(OpArgs<T> a) {
 // `chunks` blocks.
 template <typename T, int N, int NP>
 __global__ void __launch_bounds__(256) k_sipg_dir(OpArgs<T> a, int dir, int chunks) {
+  pdl_entry();
   constexpr int n2 = N * N, n3 = n2 * N;
   const T* m3 = a.tab + a.mass3;
   const int64_t nblk = a.Ne * chunks;
@@ -320,7 +323,7 @@ cudaError_t launch_sipg_n(const mg_ctx* c, OpArgs<T>& a) {
       const int64_t nblk = c->Ne * chunks;
       const int blocks = (int)(nblk < 152 * 16 ? nblk : 152 * 16);
       for (int dir = 0; dir < 3; ++dir) {
-        k_sipg_dir<T, N, NP><<<blocks, threads, 0, c->stream>>>(a, dir, chunks);
+        launch_pdl(k_sipg_dir<T, N, NP>, blocks, threads, 0, c->stream, a, dir, chunks);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
       }
@@ -334,7 +337,7 @@ cudaError_t launch_sipg_n(const mg_ctx* c, OpArgs<T>& a) {
   if (threads > 256) threads = 256;
   int64_t groups = (c->Ne + a.epb - 1) / a.epb;
   int64_t blocks = groups < 152 * 16 ? groups : 152 * 16;
-  k_sipg_n<T, N><<<(int)blocks, threads, 0, c->stream>>>(a);
+  launch_pdl(k_sipg_n<T, N>, (int)blocks, threads, 0, c->stream, a);
   c->nlaunch += 1;
   return cudaGetLastError();
 }
@@ -391,7 +394,7 @@ cudaError_t launch_sipg(const mg_ctx* c, int l, const T* u, const T* f, T* out, 
     default: break;
   }
   c->nlaunch += 1;
-  k_sipg<T><<<(int)blocks, threads, 0, c->stream>>>(a);
+  launch_pdl(k_sipg<T>, (int)blocks, threads, 0, c->stream, a);
   return cudaGetLastError();
 }
 

@@ -18,6 +18,7 @@ namespace {
 template <typename T>
 __global__ void k_contract_axis(const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ J, int64_t Ne,
                                 int d0, int d1, int d2, int axis, int nout, int ldj, int transpose, int accumulate) {
+  pdl_entry();
   int o0 = d0, o1 = d1, o2 = d2;
   if (axis == 0) o0 = nout; else if (axis == 1) o1 = nout; else o2 = nout;
   const int64_t in_sz = (int64_t)d0 * d1 * d2, out_sz = (int64_t)o0 * o1 * o2;
@@ -50,7 +51,7 @@ cudaError_t contract(const mg_ctx* c, const T* in, T* out, const T* J, int d0, i
   int64_t total = c->Ne * (int64_t)o0 * o1 * o2;
   int64_t blocks = (total + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;
-  k_contract_axis<T><<<(int)blocks, 256, 0, c->stream>>>(in, out, J, c->Ne, d0, d1, d2, axis, nout, ldj, transpose,
+  launch_pdl(k_contract_axis<T>, (int)blocks, 256, 0, c->stream, in, out, J, c->Ne, d0, d1, d2, axis, nout, ldj, transpose,
                                                          accumulate);
   c->nlaunch += 1;
   return cudaGetLastError();
@@ -109,6 +110,7 @@ __device__ void cs_split(Get get, T* AE, T* AO) {
 template <typename T, int NF, int NC>
 __global__ void __launch_bounds__(128) k_prolong_fused(const T* __restrict__ uc, T* __restrict__ uf,
                                                        const T* __restrict__ J, int64_t Ne) {
+  pdl_entry();
   constexpr int nei = (NC + 1) / 2, neo = (NF + 1) / 2;
   __shared__ T sE[neo * nei], sO[(NF / 2) * (NC / 2) + 1];
   __shared__ T sB[NF * NC * NC], sC[NF * NF * NC];
@@ -152,6 +154,7 @@ __global__ void __launch_bounds__(128) k_prolong_fused(const T* __restrict__ uc,
 template <typename T, int NF, int NC>
 __global__ void __launch_bounds__(128) k_restrict_fused(const T* __restrict__ rf, T* __restrict__ fc,
                                                         const T* __restrict__ J, int64_t Ne) {
+  pdl_entry();
   constexpr int nei = (NF + 1) / 2, neo = (NC + 1) / 2;
   __shared__ T sE[neo * nei], sO[(NC / 2) * (NF / 2) + 1];
   __shared__ T sB[NF * NC * NC], sC[NF * NF * NC];
@@ -210,10 +213,10 @@ cudaError_t launch_restrict(const mg_ctx* c, int l, const T* r_fine, T* f_coarse
   const T* J = table_of<T>(c) + c->lev[l].J;
   const int nb = fused_blocks(c->Ne);
   switch (nf) {
-    case 3: k_restrict_fused<T, 3, 2><<<nb, 128, 0, c->stream>>>(r_fine, f_coarse, J, c->Ne); c->nlaunch += 1; return cudaGetLastError();
-    case 5: k_restrict_fused<T, 5, 3><<<nb, 128, 0, c->stream>>>(r_fine, f_coarse, J, c->Ne); c->nlaunch += 1; return cudaGetLastError();
-    case 9: k_restrict_fused<T, 9, 5><<<nb, 128, 0, c->stream>>>(r_fine, f_coarse, J, c->Ne); c->nlaunch += 1; return cudaGetLastError();
-    case 17: k_restrict_fused<T, 17, 9><<<nb, 128, 0, c->stream>>>(r_fine, f_coarse, J, c->Ne); c->nlaunch += 1; return cudaGetLastError();
+    case 3: launch_pdl(k_restrict_fused<T, 3, 2>, nb, 128, 0, c->stream, r_fine, f_coarse, J, c->Ne); c->nlaunch += 1; return cudaGetLastError();
+    case 5: launch_pdl(k_restrict_fused<T, 5, 3>, nb, 128, 0, c->stream, r_fine, f_coarse, J, c->Ne); c->nlaunch += 1; return cudaGetLastError();
+    case 9: launch_pdl(k_restrict_fused<T, 9, 5>, nb, 128, 0, c->stream, r_fine, f_coarse, J, c->Ne); c->nlaunch += 1; return cudaGetLastError();
+    case 17: launch_pdl(k_restrict_fused<T, 17, 9>, nb, 128, 0, c->stream, r_fine, f_coarse, J, c->Ne); c->nlaunch += 1; return cudaGetLastError();
     default: break;
   }
   T* t1 = static_cast<T*>(c->ws.corr);
@@ -231,10 +234,10 @@ cudaError_t launch_prolong(const mg_ctx* c, int l, const T* u_coarse, T* u_fine)
   const T* J = table_of<T>(c) + c->lev[l].J;
   const int nb = fused_blocks(c->Ne);
   switch (nf) {
-    case 3: k_prolong_fused<T, 3, 2><<<nb, 128, 0, c->stream>>>(u_coarse, u_fine, J, c->Ne); c->nlaunch += 1; return cudaGetLastError();
-    case 5: k_prolong_fused<T, 5, 3><<<nb, 128, 0, c->stream>>>(u_coarse, u_fine, J, c->Ne); c->nlaunch += 1; return cudaGetLastError();
-    case 9: k_prolong_fused<T, 9, 5><<<nb, 128, 0, c->stream>>>(u_coarse, u_fine, J, c->Ne); c->nlaunch += 1; return cudaGetLastError();
-    case 17: k_prolong_fused<T, 17, 9><<<nb, 128, 0, c->stream>>>(u_coarse, u_fine, J, c->Ne); c->nlaunch += 1; return cudaGetLastError();
+    case 3: launch_pdl(k_prolong_fused<T, 3, 2>, nb, 128, 0, c->stream, u_coarse, u_fine, J, c->Ne); c->nlaunch += 1; return cudaGetLastError();
+    case 5: launch_pdl(k_prolong_fused<T, 5, 3>, nb, 128, 0, c->stream, u_coarse, u_fine, J, c->Ne); c->nlaunch += 1; return cudaGetLastError();
+    case 9: launch_pdl(k_prolong_fused<T, 9, 5>, nb, 128, 0, c->stream, u_coarse, u_fine, J, c->Ne); c->nlaunch += 1; return cudaGetLastError();
+    case 17: launch_pdl(k_prolong_fused<T, 17, 9>, nb, 128, 0, c->stream, u_coarse, u_fine, J, c->Ne); c->nlaunch += 1; return cudaGetLastError();
     default: break;
   }
   T* t1 = static_cast<T*>(c->ws.corr);
