@@ -99,6 +99,7 @@ def parse_args():
     ap.add_argument("--workload", default="cube16_p8", choices=sorted(WORKLOADS))
     ap.add_argument("--overlap", type=int, default=None, help="override N_O of the workload")
     ap.add_argument("--precision", default=None, choices=["fp64", "mixed"], help="override the workload's precision")
+    ap.add_argument("--cg", action="store_true", help="solve the workload with MG-CG instead of its default solver")
     ap.add_argument("--outer-df64", action="store_true",
                     help="mixed runs: outer operator products q = A p in double-float (FP32-pair) arithmetic")
     ap.add_argument("--tensor-cores", default="off", choices=["off", "on", "auto"],
@@ -478,6 +479,8 @@ def run_workload(args):
         W["overlap_layers"] = args.overlap
     if args.precision is not None:
         W["precision"] = args.precision
+    if args.cg:
+        W["use_cg"] = True
     dev = torch.device("cuda", torch.cuda.current_device())
     pkg.load_library()
     extra = {k: W[k] for k in ("overlap_mode", "overlap_frac", "ns_growth") if k in W}
@@ -609,7 +612,7 @@ def main():
         run_reference(args)
     elif args.workload == "serving512":
         run_serving(args)
-    elif args.workload != "cube16_p8":
+    elif args.workload != "cube16_p8" or args.precision is not None or args.cg:
         run_workload(args)
     else:
         run_mg(args)

@@ -107,42 +107,42 @@ __device__ __forceinline__ double z_scale(const double* scal) {
   return nrm > 0.0 ? nrm : 1.0;
 }
 
-// Partial sums of z, z.q, z.r, q, r (columns 0 .. 4).
+// Partial sums of z, z.q, z.r (columns 0 .. 2), z taken unscaled (the FP32
+// preconditioner's scale is applied to the totals).
 template <typename TZ>
 __global__ void __launch_bounds__(kThreads) k_cg_sums(const TZ* __restrict__ zs, const double* __restrict__ q,
-                                                      const double* __restrict__ r, int64_t n, const double* scal,
-                                                      double* partial) {
+                                                      const double* __restrict__ r, int64_t n, double* partial) {
   pdl_entry();
   __shared__ double sh[kThreads];
-  const double zsc = z_scale<TZ>(scal);
-  double a[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  double a[3] = {0.0, 0.0, 0.0};
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const double z = (double)zs[i] * zsc, qi = q[i], ri = r[i];
+    const double z = (double)zs[i];
     a[0] += z;
-    a[1] += z * qi;
-    a[2] += z * ri;
-    a[3] += qi;
-    a[4] += ri;
+    a[1] += z * q[i];
+    a[2] += z * r[i];
   }
-  for (int k = 0; k < 5; ++k) {
+  for (int k = 0; k < 3; ++k) {
     const double b = block_reduce(a[k], sh);
     __syncthreads();
     if (threadIdx.x == 0) partial[k * gridDim.x + blockIdx.x] = b;
   }
 }
 
+// With z' = z - mean(z): z'.q' = z.q (1^T q = 1^T A p = 0) and
+// z'.r' = z.r - sum(z) sum(r) / n (sum(r) from the update pass).
+template <typename TZ>
 __global__ void __launch_bounds__(kThreads) k_cg_sums_final(const double* partial, int nb, double* scal, int64_t n) {
   pdl_entry();
   __shared__ double sh[kThreads];
-  double v[5];
-  final_columns(partial, nb, 5, v, sh);
+  double v[3];
+  final_columns(partial, nb, 3, v, sh);
   if (threadIdx.x == 0) {
-    const double inv = 1.0 / (double)n;
-    const double zq = v[1] - v[0] * v[3] * inv;  // z'.q'
-    const double zr = v[2] - v[0] * v[4] * inv;  // z'.r'
+    const double zsc = z_scale<TZ>(scal), inv = 1.0 / (double)n;
+    const double sz = zsc * v[0], zq = zsc * v[1];
+    const double zr = zsc * v[2] - sz * scal[kSlotSum] * inv;
     scal[kSlotZQ] = zq;
     scal[kSlotBeta] = -scal[kSlotAlpha] * zq / scal[kSlotRZ];
-    scal[kSlotMuZ] = v[0] * inv;
+    scal[kSlotMuZ] = sz * inv;
     scal[kSlotRZ] = zr;
   }
 }
@@ -327,8 +327,8 @@ cudaError_t launch_cg_update(const mg_ctx* c, double* x, const double* p, double
 template <typename TZ>
 cudaError_t launch_cg_direction(const mg_ctx* c, double* p, const TZ* z, const double* q, const double* r, int64_t n,
                                 df64* pdf) {
-  launch_pdl(k_cg_sums<TZ>, kRedBlocks, kThreads, 0, c->stream, z, q, r, n, c->ws.scal, c->ws.red);
-  launch_pdl(k_cg_sums_final, 1, kThreads, 0, c->stream, c->ws.red, kRedBlocks, c->ws.scal, n);
+  launch_pdl(k_cg_sums<TZ>, kRedBlocks, kThreads, 0, c->stream, z, q, r, n, c->ws.red);
+  launch_pdl(k_cg_sums_final<TZ>, 1, kThreads, 0, c->stream, c->ws.red, kRedBlocks, c->ws.scal, n);
   launch_pdl(k_cg_newdir<TZ>, grid_for(n), kThreads, 0, c->stream, p, z, n, c->ws.scal, pdf);
   c->nlaunch += 3;
   return cudaGetLastError();

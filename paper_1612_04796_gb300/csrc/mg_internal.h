@@ -43,7 +43,7 @@ constexpr int kMaxLevels = 6;   // P <= 32
 constexpr int kMaxP = 32;
 constexpr int kMaxN = kMaxP + 1;        // nodes per element and direction
 constexpr int kMaxM = 3 * kMaxN;         // widest subdomain line (strips of whole neighbour elements)
-constexpr int kRedBlocks = 304;         // fixed grid of the two-stage reductions (2 per SM)
+constexpr int kRedBlocks = 1216;        // fixed grid of the two-stage reductions (8 per SM)
 
 // Slots of the device scalar array ws.scal.
 enum Slot : int {
@@ -217,8 +217,9 @@ cudaError_t launch_sub_mean(const mg_ctx* c, double* x, int64_t n, int sum_slot)
 //  cg_update: alpha = scal[RZ] / scal[PQ]; x += alpha p; r -= alpha q;
 //             scal[Sum] = sum r, scal[RR] = |r - mean(r)|^2.
 //  cg_direction: z = zscale * zsrc (zscale = sqrt(scal[RR]) for an FP32 z, else 1);
-//             with z' = z - mean(z) and q' = q - mean(q), r' = r - mean(r):
-//             beta = -alpha z'.q' / scal[RZ]; scal[RZ] = z'.r'; p = z' + beta p.
+//             with z' = z - mean(z), r' = r - mean(r) (sum r in scal[Sum]) and
+//             q of zero sum (1^T A = 0): beta = -alpha z'.q / scal[RZ];
+//             scal[RZ] = z'.r'; p = z' + beta p.
 cudaError_t launch_cg_update(const mg_ctx* c, double* x, const double* p, double* r, const double* q, int64_t n);
 template <typename TZ>
 cudaError_t launch_cg_direction(const mg_ctx* c, double* p, const TZ* z, const double* q, const double* r, int64_t n,
