@@ -18,7 +18,9 @@
 // 16-byte core matrices, K-adjacent core matrices LBO bytes apart, 8-row
 // groups SBO = K_pad LBO bytes apart).  Per 128-quad tile and line i of the
 // quad one MMA (M = 128, N = N_pad, K = 8 per step) writes the outputs of
-// that line to tensor-memory columns (4 t + i) N_pad ..; one thread issues
+// that line to tensor-memory columns (4 t + i) N_pad .. (the last tile is
+// anchored at the end of the quads, overlapping its predecessor, whose rows
+// it does not write back, so no padding tile is stored); one thread issues
 // them and waits on the commit mbarrier while the others sleep in a block
 // barrier.  Every warp then reads its 32 lanes (quads) back with tcgen05.ld:
 // a thread holds, for each output index o, the four values of its quad's
@@ -60,6 +62,8 @@ struct TcPass {
   int np;         // N padded to a multiple of 16
   int quads;      // G * lines / 4
   int tiles;      // 128-quad tiles
+  int last0;      // first quad of the last tile: anchored at the end of the quads (rounded up
+                  // to 8) when there are several tiles, so the buffer needs no padding tile
   uint32_t boff;  // byte offset of this pass's factor in the B region
 };
 
@@ -194,11 +198,12 @@ __device__ __forceinline__ void tc_writeback(const TcArgs& a, float* A, uint32_t
   const int Ln = P < 5 ? a.pass[P + 1].lines : 0;
   const uint32_t lanes = (uint32_t)((warp & 3) * 32) << 16;
   for (int t = warp >> 2; t < ps.tiles; t += 2) {
-    const int quad = t * kTcRows + (warp & 3) * 32 + lane;
+    const int t0 = t == ps.tiles - 1 ? ps.last0 : t * kTcRows;  // rows below t * 128 belong to earlier tiles
+    const int quad = t0 + (warp & 3) * 32 + lane;
     const int line0 = 4 * quad;
     const int g = line0 / ps.lines, l0 = line0 - g * ps.lines;
     const int f0 = l0 % ps.fast, sl = l0 / ps.fast;
-    const bool valid = ok && quad < ps.quads && s0 + g < a.Ne;
+    const bool valid = ok && quad < ps.quads && quad >= t * kTcRows && s0 + g < a.Ne;
     for (int c0 = 0; c0 < ps.np; c0 += 16) {
       float v[4][16];
 #pragma unroll
@@ -328,12 +333,14 @@ __global__ void __launch_bounds__(kTcThreads) k_fdm_tc(TcArgs a) {
         const uint32_t idesc = tc_idesc(ps.np);
         const uint32_t lbo = (uint32_t)a.lbo_a, sbo = (uint32_t)ps.kp * lbo, sbo_b = 32u * ps.kp;
         const uint32_t bp = baseB + (a.b_resident ? ps.boff : 0u);
-        for (int t = 0; t < ps.tiles; ++t)
+        for (int t = 0; t < ps.tiles; ++t) {
+          const uint32_t t0 = (uint32_t)(t == ps.tiles - 1 ? ps.last0 : t * kTcRows);
           for (int i = 0; i < 4; ++i)
             for (int j = 0; j < ps.kp / 8; ++j)
               tc_mma(tmem + (uint32_t)((4 * t + i) * ps.np),
-                     tc_desc(baseA + (uint32_t)t * 16u * sbo + (uint32_t)(i * ps.kp / 4 + 2 * j) * lbo, lbo, sbo),
+                     tc_desc(baseA + (t0 / 8u) * sbo + (uint32_t)(i * ps.kp / 4 + 2 * j) * lbo, lbo, sbo),
                      tc_desc(bp + 256u * j, 128, sbo_b), idesc, j > 0 ? 1u : 0u);
+        }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb)
                      : "memory");
       }
@@ -390,8 +397,10 @@ uint32_t make_plan(TcArgs& a, int G, int lbo, uint32_t limit) {
     ps.np = round_up(m, 16);
     ps.quads = G * ps.lines / 4;
     ps.tiles = (ps.quads + kTcRows - 1) / kTcRows;
+    const int rows = std::max(round_up(ps.quads, 8), kTcRows);  // quad rows the buffer holds
+    ps.last0 = rows - kTcRows;
     ps.boff = btot;
-    abytes = std::max<uint32_t>(abytes, (uint32_t)ps.tiles * 16u * (uint32_t)ps.kp * (uint32_t)lbo);
+    abytes = std::max<uint32_t>(abytes, (uint32_t)(rows / 8) * (uint32_t)ps.kp * (uint32_t)lbo);
     const uint32_t fb = (uint32_t)ps.np * ps.kp * 4u;
     bmax = std::max(bmax, fb);
     btot += fb;
