@@ -594,8 +594,8 @@ def run_serving(args):
         "ms_per_step": makespan * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32 multigrid / f64 outer", "data": "synthetic",
         "config": dict(WORKLOADS["serving512"], name="serving512", requests=len(reqs), slots=slots, overlap_layers=overlap,
-                       hbm_budget_gb=srv.scheduler.budget / 1e9, total_dofs=dofs,
-                       admission=policy + (" (aging after %.0f s)" % srv.scheduler.max_wait
+                       hbm_budget_gb=srv.budget / 1e9, total_dofs=dofs,
+                       admission=policy + (" (aging after %.0f s)" % srv.max_wait
                                            if policy == "smallest" else ""),
                        outer_operator="double-float (FP32 pairs)" if srv.outer_df64 else "FP64"),
         "latency": summ, "max_concurrent": srv.max_active,

@@ -9,7 +9,7 @@ from ._lib import LIB_PATH, header_symbols, load_library  # noqa: F401
 
 
 def build(force=False, verbose=False):
-    from .build import build as _build
+    from .libbuild import build as _build
     return _build(force=force, verbose=verbose)
 
 

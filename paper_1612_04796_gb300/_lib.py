@@ -1,11 +1,13 @@
-"""ctypes declarations of the C ABI in include/mgdg.h (argument marshalling only)."""
+"""ctypes declarations of the C ABI in include/mgdg.h and include/mgdg_server.h
+(argument marshalling only)."""
 import ctypes
+import glob
 import os
 import re
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "lib", "libmgdg.so")
-HEADER = os.path.join(os.path.dirname(HERE), "include", "mgdg.h")
+INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 MG_OK, MG_EINVAL, MG_ENOMEM, MG_ECUDA, MG_ENOCONV, MG_ENOTREADY = range(6)
 STATUS_NAMES = {0: "MG_OK", 1: "MG_EINVAL", 2: "MG_ENOMEM", 3: "MG_ECUDA", 4: "MG_ENOCONV", 5: "MG_ENOTREADY"}
@@ -25,6 +27,68 @@ class MgOpts(ctypes.Structure):
         ("stream", ctypes.c_void_p),
     ]
 
+
+FILL_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_longlong, ctypes.POINTER(ctypes.c_double),
+                           ctypes.c_size_t)
+
+
+class MgRequest(ctypes.Structure):
+    _fields_ = [
+        ("lx", ctypes.c_double), ("ly", ctypes.c_double), ("lz", ctypes.c_double),
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+        ("P", ctypes.c_int),
+        ("overlap", ctypes.c_int),
+        ("penalty", ctypes.c_double),
+        ("tol", ctypes.c_double),
+        ("f", ctypes.c_void_p),
+        ("fill", FILL_FN),
+        ("user", ctypes.c_void_p),
+        ("u", ctypes.c_void_p),
+        ("footprint", ctypes.c_size_t),
+    ]
+
+
+EXECUTE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_longlong, ctypes.POINTER(MgRequest),
+                              ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double))
+
+
+class MgServerOpts(ctypes.Structure):
+    _fields_ = [
+        ("slots", ctypes.c_int),
+        ("budget", ctypes.c_size_t),
+        ("policy", ctypes.c_int),
+        ("max_wait", ctypes.c_double),
+        ("device", ctypes.c_int),
+        ("use_cg", ctypes.c_int),
+        ("maxit", ctypes.c_int),
+        ("opts", MgOpts),
+        ("execute", EXECUTE_FN),
+        ("execute_user", ctypes.c_void_p),
+    ]
+
+
+class MgResult(ctypes.Structure):
+    _fields_ = [
+        ("status", ctypes.c_int),
+        ("iterations", ctypes.c_int),
+        ("relres", ctypes.c_double),
+        ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double),
+        ("concurrency", ctypes.c_int),
+        ("slot", ctypes.c_int),
+        ("footprint", ctypes.c_size_t),
+        ("error", ctypes.c_char * 160),
+    ]
+
+
+class MgServerStats(ctypes.Structure):
+    _fields_ = [
+        ("submitted", ctypes.c_longlong), ("completed", ctypes.c_longlong),
+        ("queued", ctypes.c_int), ("running", ctypes.c_int), ("max_running", ctypes.c_int),
+        ("budget", ctypes.c_size_t), ("used", ctypes.c_size_t), ("peak_used", ctypes.c_size_t),
+    ]
+
+
+MG_SCHED_FCFS, MG_SCHED_SMALLEST = 0, 1
 
 _c = ctypes
 _P = ctypes.c_void_p
@@ -65,6 +129,15 @@ SIGNATURES = {
     "mg_kernel_launches": (_LL, [_P]),
     "mg_profile": (_S, [_P, _I]),
     "mg_profile_result": (_S, [_P, _I, _I, ctypes.POINTER(_D), ctypes.POINTER(_LL)]),
+    "mg_server_default_opts": (None, [ctypes.POINTER(MgServerOpts)]),
+    "mg_server_create": (_S, [ctypes.POINTER(MgServerOpts), ctypes.POINTER(_P)]),
+    "mg_request_footprint": (_S, [ctypes.POINTER(MgRequest), ctypes.POINTER(MgOpts), ctypes.POINTER(ctypes.c_size_t)]),
+    "mg_submit": (_S, [_P, ctypes.POINTER(MgRequest), ctypes.POINTER(_LL)]),
+    "mg_poll": (_S, [_P, _LL, ctypes.POINTER(MgResult)]),
+    "mg_wait": (_S, [_P, _LL, _D, ctypes.POINTER(MgResult)]),
+    "mg_server_get_stats": (_S, [_P, ctypes.POINTER(MgServerStats)]),
+    "mg_server_destroy": (None, [_P]),
+    "mg_sched_pick": (_I, [_I, _D, _D, ctypes.c_size_t, ctypes.c_size_t, _I, _P, _P, _P]),
     "mg_last_error": (ctypes.c_char_p, [_P]),
     "mg_destroy": (None, [_P]),
 }
@@ -72,21 +145,25 @@ SIGNATURES = {
 _lib = None
 
 
-def header_symbols(path=HEADER):
-    """Names of the functions declared in include/mgdg.h."""
-    text = open(path).read()
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(mg_[a-z0-9_]+)\s*\(", text)))
+def header_symbols(include=INCLUDE):
+    """Names of the functions declared in the headers under include/."""
+    names = set()
+    for path in sorted(glob.glob(os.path.join(include, "*.h"))):
+        text = open(path).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"\(\s*\*\s*\w+\s*\)\s*\(", "(", text)  # function-pointer members
+        names.update(re.findall(r"\b(mg_[a-z0-9_]+)\s*\(", text))
+    return sorted(names)
 
 
 def load_library(path=LIB_PATH):
-    """Load libmgdg.so (built by build.py) and declare every entry point.
+    """Load libmgdg.so (built by libbuild.py) and declare every entry point.
     Raises if the library is missing: there is no fallback implementation."""
     global _lib
     if _lib is not None:
         return _lib
     if not os.path.exists(path):
-        raise RuntimeError("libmgdg.so not found at %s; run paper_1612_04796_gb300.build.build()" % path)
+        raise RuntimeError("libmgdg.so not found at %s; run paper_1612_04796_gb300.build()" % path)
     lib = ctypes.CDLL(path)
     for name, (res, args) in SIGNATURES.items():
         fn = getattr(lib, name)

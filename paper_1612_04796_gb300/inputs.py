@@ -15,9 +15,14 @@ import math
 import numpy as np
 
 
-def gaussian(n, seed):
-    """n i.i.d. N(0, 1) values (nodal right-hand side, element-blocked order)."""
-    return np.random.default_rng(seed).standard_normal(int(n))
+def gaussian(n, seed, out=None):
+    """n i.i.d. N(0, 1) values (nodal right-hand side, element-blocked order);
+    written into `out` (float64, n values) when given."""
+    rng = np.random.default_rng(seed)
+    if out is None:
+        return rng.standard_normal(int(n))
+    assert out.shape == (int(n),) and out.dtype == np.float64
+    return rng.standard_normal(out=out)
 
 
 def uniform_guess(n, seed):

@@ -1,21 +1,19 @@
-"""Serving loop: continuous batching of independent Poisson solves.
+"""Serving: continuous batching of independent Poisson solves.
 
-Requests (periodic box, mesh, order P, right-hand side) arrive over time.  A
-request is admitted as soon as a worker slot is free and its device-memory
-footprint fits into the HBM budget (first come, first served: a request that
-does not fit blocks the ones behind it, so large requests are not starved).
-Every admitted request gets its own solver context, workspace and CUDA
-stream on a worker thread; the solves of different requests therefore
-overlap on the GPU, and each result is independent of what else runs (the
-kernels are deterministic and share no state), so a request gives the same
-answer alone and in the mix.
+Requests (periodic box, mesh, order P, right-hand side) arrive over time.
+The native runtime (include/mgdg_server.h) admits a request as soon as a
+worker slot is free and its device-memory footprint fits into the HBM budget
+(first come first served, or smallest work first with aging).  Every
+admitted request gets its own solver context, pool memory and CUDA stream on
+a worker thread; the solves of different requests therefore overlap on the
+GPU, and each result is independent of what else runs (the kernels are
+deterministic and share no state), so a request gives the same answer alone
+and in the mix.
 
-The scheduling logic (``Scheduler``) is separate from the GPU work so that it
-can be tested with fake solves; ``Server`` plugs in the real solver.
+``Server`` binds the runtime; with an ``executor`` in place of the GPU solve
+the same admission code runs without a GPU (tests).
 """
-import collections
 import ctypes
-import threading
 import time
 
 import numpy as np
@@ -23,8 +21,11 @@ import numpy as np
 from . import inputs
 
 
+POLICY = {"fcfs": 0, "smallest": 1}
+
+
 class Request:
-    def __init__(self, rid, lengths, counts, P, seed, arrival=0.0, tol=1e-10, overlap=1):
+    def __init__(self, rid, lengths, counts, P, seed, arrival=0.0, tol=1e-10, overlap=1, footprint=0):
         self.id = rid
         self.lengths = tuple(float(v) for v in lengths)
         self.counts = tuple(int(v) for v in counts)
@@ -33,6 +34,7 @@ class Request:
         self.arrival = float(arrival)
         self.tol = float(tol)
         self.overlap = int(overlap)
+        self.footprint = int(footprint)  # bytes; 0 = the library's sizing
 
     @property
     def dofs(self):
@@ -50,112 +52,11 @@ class Result:
         self.t_done = None
         self.error = None
         self.concurrency = 0
+        self.slot = -1
 
     @property
     def latency(self):
         return self.t_done - self.t_arrival
-
-
-class Scheduler:
-    """Admission under a slot limit and a memory budget.  ``footprint(req)``
-    gives the bytes a request holds while it runs; ``run(req, slot)`` does the
-    work (on a worker thread) and returns a dict that is stored on the Result.
-
-    policy "fcfs": strictly in arrival order (a request that does not fit
-    blocks the ones behind it).  policy "smallest": among the requests that
-    have arrived, the one with the least work (``work(req)``, default its DOF
-    count) that fits is admitted first; a request that has waited longer than
-    ``max_wait`` seconds is aged: the aged ones go first, in arrival order and
-    without being overtaken, so no request waits much longer than max_wait
-    for its turn."""
-
-    def __init__(self, run, footprint, slots, budget_bytes, clock=time.perf_counter, policy="fcfs", work=None,
-                 max_wait=10.0):
-        if policy not in ("fcfs", "smallest"):
-            raise ValueError("unknown policy %r" % policy)
-        self.run = run
-        self.footprint = footprint
-        self.slots = int(slots)
-        self.budget = int(budget_bytes)
-        self.clock = clock
-        self.policy = policy
-        self.work = work if work is not None else (lambda r: r.dofs)
-        self.max_wait = float(max_wait)
-        self.cv = threading.Condition()
-        self.used = 0
-        self.active = 0
-        self.max_active = 0
-        self.free_slots = list(range(self.slots))
-
-    def _worker(self, req, slot, res, need):
-        try:
-            out = self.run(req, slot)
-            for k, v in out.items():
-                setattr(res, k, v)
-        except Exception as exc:  # recorded on the result, the loop goes on
-            res.error = repr(exc)
-        res.t_done = self.clock()
-        with self.cv:
-            self.used -= need
-            self.active -= 1
-            self.free_slots.append(slot)
-            self.cv.notify_all()
-
-    def _pick(self, waiting, now, realtime):
-        """The request to admit next among `waiting` (arrived, not admitted),
-        or None to wait for resources.  Called with self.cv held."""
-        fits = lambda r: self.used + self.footprint(r) <= self.budget
-        if self.policy == "fcfs":
-            return waiting[0] if fits(waiting[0]) else None
-        aged = [r for r in waiting if realtime and now - r.arrival > self.max_wait]
-        if aged:
-            return aged[0] if fits(aged[0]) else None
-        best = None
-        for r in waiting:
-            if fits(r) and (best is None or self.work(r) < self.work(best)):
-                best = r
-        return best
-
-    def serve(self, requests, realtime=True):
-        """Serve `requests` (arrival in seconds from the start).  Returns
-        results in request order."""
-        pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
-        waiting = []
-        results = {r.id: Result(r.id) for r in requests}
-        t0 = self.clock()
-        threads = []
-        for r in requests:
-            if self.footprint(r) > self.budget:
-                raise ValueError("request %s needs more memory than the whole budget" % r.id)
-        while pending or waiting:
-            now = self.clock() - t0
-            while pending and (not realtime or pending[0].arrival <= now):
-                waiting.append(pending.popleft())
-            if not waiting:
-                time.sleep(min(pending[0].arrival - now, 0.005))
-                continue
-            with self.cv:
-                req = self._pick(waiting, self.clock() - t0, realtime) if self.free_slots else None
-                if req is None:
-                    self.cv.wait(timeout=0.005 if pending else 0.05)
-                    continue
-                need = self.footprint(req)
-                slot = self.free_slots.pop(0)
-                self.used += need
-                self.active += 1
-                self.max_active = max(self.max_active, self.active)
-                active_now = self.active
-            waiting.remove(req)
-            res = results[req.id]
-            res.t_arrival = t0 + (req.arrival if realtime else 0.0)
-            res.t_admit = self.clock()
-            res.concurrency = active_now
-            th = threading.Thread(target=self._worker, args=(req, slot, res, need), daemon=True)
-            th.start()
-            threads.append(th)
-        for th in threads:
-            th.join()
-        return [results[r.id] for r in requests]
 
 
 def request_stream(seed=5, n_requests=512, rate=200.0, sizes=(4, 8, 16, 24, 32), orders=(2, 4, 8, 16),
@@ -171,69 +72,177 @@ def request_stream(seed=5, n_requests=512, rate=200.0, sizes=(4, 8, 16, 24, 32),
 
 
 class Server:
-    """Real solves: FP32 V-cycle preconditioner inside FP64 inexact PCG by
-    default, the outer products q = A p in double-float (outer_df64); each
-    slot owns a CUDA stream."""
+    """Binding of the native serving runtime (include/mgdg_server.h): the
+    admission, the worker threads, the streams and the device memory are the
+    library's; this class marshals requests in and results out.
+
+    Real solves by default: FP32 V-cycle preconditioner inside FP64 inexact
+    PCG, the outer products q = A p in double-float (outer_df64).  Each
+    request's nodal right-hand side is drawn from its seed when the runtime
+    admits it (the fill callback), so queued requests hold no host buffer.
+
+    ``executor(req, slot) -> {"iterations": .., "relres": ..}`` replaces the
+    GPU solve (host-only use of the scheduler, e.g. tests); the runtime then
+    makes no CUDA call, and ``req.footprint`` (bytes) is the request's size."""
 
     def __init__(self, slots=8, budget_bytes=None, precision="mixed", use_cg=True, device="cuda", keep_solution=True,
-                 outer_df64=True, policy="fcfs", max_wait=10.0):
-        import torch
-
-        from ._lib import MgOpts, load_library
-        from .solver import MGSolver
-        self.torch = torch
-        self.MGSolver = MGSolver
-        self.lib = load_library()
-        self.MgOpts = MgOpts
-        self.device = torch.device(device)
-        if self.device.index is None:
-            self.device = torch.device("cuda", torch.cuda.current_device())
-        if budget_bytes is None:
-            free, _ = torch.cuda.mem_get_info(self.device)
-            budget_bytes = int(0.8 * free)
+                 outer_df64=True, policy="fcfs", max_wait=10.0, executor=None, maxit=400):
+        from . import _lib
+        from .solver import PRECISION
+        if policy not in POLICY:
+            raise ValueError("unknown policy %r" % policy)
+        self._lib = _lib
+        self.lib = _lib.load_library()
         self.precision = precision
         self.outer_df64 = bool(outer_df64) and precision != "fp64"
         self.use_cg = use_cg
-        self.keep = keep_solution
-        self.streams = [torch.cuda.Stream(self.device) for _ in range(slots)]
-        self.scheduler = Scheduler(self._run, self.footprint, slots, budget_bytes, policy=policy, max_wait=max_wait)
+        self.keep = keep_solution and executor is None
+        self.policy = policy
+        self.max_wait = float(max_wait)
+        self.executor = executor
+        o = _lib.MgServerOpts()
+        self.lib.mg_server_default_opts(ctypes.byref(o))
+        o.slots = int(slots)
+        o.policy = POLICY[policy]
+        o.max_wait = self.max_wait
+        o.use_cg = 1 if use_cg else 0
+        o.maxit = int(maxit)
+        o.opts.precision = PRECISION[precision]
+        o.opts.outer_df64 = 1 if self.outer_df64 else 0
+        o.budget = 0 if budget_bytes is None else int(budget_bytes)
+        self._records = {}
+        self._next_key = 1
+        self._errors = {}
+        if executor is None:
+            import torch
+            dev = torch.device(device)
+            if dev.index is None:
+                dev = torch.device("cuda", torch.cuda.current_device())
+            self.device = dev
+            o.device = dev.index
+            self._execute_cb = None
+        else:
+            self.device = None
+            self._execute_cb = _lib.EXECUTE_FN(self._execute)
+            o.execute = self._execute_cb
+        self._fill_cb = _lib.FILL_FN(self._fill)
+        self.opts = o
+        h = ctypes.c_void_p()
+        st = self.lib.mg_server_create(ctypes.byref(o), ctypes.byref(h))
+        if st != 0:
+            raise RuntimeError("mg_server_create failed: %s" % _lib.STATUS_NAMES.get(st, st))
+        self.handle = h
+
+    # callbacks, run on the runtime's worker threads
+    def _fill(self, user, ticket, ptr, n):
+        req = self._records[user][0]
+        out = np.ctypeslib.as_array(ptr, shape=(n,))
+        inputs.gaussian(n, req.seed, out=out)
+
+    def _execute(self, user, ticket, reqp, slot, itp, relp):
+        key = reqp.contents.user
+        try:
+            out = self.executor(self._records[key][0], slot)
+            itp[0] = int(out.get("iterations", 0))
+            relp[0] = float(out.get("relres", 0.0))
+            return 0
+        except Exception as exc:  # recorded on the result, the runtime goes on
+            self._errors[key] = repr(exc)
+            return 1
+
+    def _request(self, req, key, u):
+        q = self._lib.MgRequest()
+        q.lx, q.ly, q.lz = req.lengths
+        q.nx, q.ny, q.nz = req.counts
+        q.P = req.P
+        q.overlap = req.overlap
+        q.penalty = 2.0
+        q.tol = req.tol
+        q.f = None
+        q.fill = self._fill_cb
+        q.user = key
+        q.u = u.ctypes.data if u is not None else None
+        q.footprint = int(getattr(req, "footprint", 0) or 0)
+        return q
 
     def footprint(self, req):
-        """Workspace plus the request's own vectors (f, b, u), from the
-        library's host-only sizing."""
-        opts = self.MgOpts()
-        self.lib.mg_default_opts(ctypes.byref(opts))
-        ctx = ctypes.c_void_p()
-        st = self.lib.mg_setup(req.lengths[0], req.lengths[1], req.lengths[2], req.counts[0], req.counts[1],
-                               req.counts[2], req.P, 2.0, req.overlap, ctypes.byref(opts), ctypes.byref(ctx))
+        """Bytes the runtime reserves for `req` (host only)."""
+        out = ctypes.c_size_t()
+        st = self.lib.mg_request_footprint(ctypes.byref(self._request(req, 0, None)), ctypes.byref(self.opts.opts),
+                                           ctypes.byref(out))
         if st != 0:
             raise ValueError("invalid request %s" % req.id)
-        size = ctypes.c_size_t()
-        self.lib.mg_workspace_size(ctx, ctypes.byref(size))
-        self.lib.mg_destroy(ctx)
-        return size.value + 3 * 8 * req.dofs + (1 << 20)
-
-    def _run(self, req, slot):
-        torch = self.torch
-        stream = self.streams[slot]
-        with torch.cuda.device(self.device), torch.cuda.stream(stream):
-            s = self.MGSolver(req.lengths, req.counts, req.P, overlap=req.overlap, precision=self.precision,
-                              device=self.device, stream=stream, outer_df64=self.outer_df64)
-            f = torch.tensor(inputs.gaussian(s.num_dofs(), req.seed), device=self.device)
-            b = s.rhs(f)
-            u, its, rel, _ = s.solve(b, tol=req.tol, use_cg=self.use_cg, maxit=400)
-            out = u.cpu().numpy() if self.keep else None
-            stream.synchronize()
-            s.close()
-            del s, f, b, u
-        return {"u": out, "iterations": its, "relres": rel}
+        return out.value
 
     def serve(self, requests, realtime=True):
-        return self.scheduler.serve(requests, realtime)
+        """Submit `requests` (at their arrival times, in seconds from now, when
+        `realtime`; all at once otherwise) and wait for every result.
+        Returns results in request order."""
+        keys = []
+        for r in requests:
+            u = np.empty(r.dofs) if self.keep else None
+            keys.append(self._next_key)
+            self._records[self._next_key] = (r, u)
+            self._next_key += 1
+        order = sorted(range(len(requests)), key=lambda i: requests[i].arrival)
+        tickets = {}
+        t0 = time.perf_counter()
+        try:
+            for i in order:
+                r = requests[i]
+                if realtime:
+                    delay = r.arrival - (time.perf_counter() - t0)
+                    if delay > 0:
+                        time.sleep(delay)
+                q = self._request(r, keys[i], self._records[keys[i]][1])
+                t = ctypes.c_longlong()
+                st = self.lib.mg_submit(self.handle, ctypes.byref(q), ctypes.byref(t))
+                if st != 0:
+                    raise ValueError("request %s rejected (%s): invalid, or larger than the whole budget"
+                                     % (r.id, self._lib.STATUS_NAMES.get(st, st)))
+                tickets[i] = t.value
+        finally:
+            results = []
+            for i, r in enumerate(requests):
+                res = Result(r.id)
+                if i in tickets:
+                    out = self._lib.MgResult()
+                    self.lib.mg_wait(self.handle, tickets[i], -1.0, ctypes.byref(out))
+                    res.iterations, res.relres = out.iterations, out.relres
+                    res.t_arrival, res.t_admit, res.t_done = out.t_submit, out.t_admit, out.t_done
+                    res.concurrency = out.concurrency
+                    res.slot = out.slot
+                    if out.status != 0:
+                        res.error = self._errors.pop(keys[i], None) or "%s: %s" % (
+                            self._lib.STATUS_NAMES.get(out.status, out.status), out.error.decode())
+                    res.u = self._records[keys[i]][1]
+                self._records.pop(keys[i], None)
+                results.append(res)
+        return results
+
+    def stats(self):
+        st = self._lib.MgServerStats()
+        self.lib.mg_server_get_stats(self.handle, ctypes.byref(st))
+        return st
 
     @property
     def max_active(self):
-        return self.scheduler.max_active
+        return self.stats().max_running
+
+    @property
+    def budget(self):
+        return self.stats().budget
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.mg_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def latency_summary(results):

@@ -33,8 +33,44 @@ def test_memory_budget_limits_concurrency(mg):
     at a time even with free slots."""
     from paper_1612_04796_gb300.serving import Request, Server
     reqs = [Request(i, (1.0, 1.0, 1.0), (4, 4, 4), 4, seed=200 + i) for i in range(4)]
-    srv = Server(slots=4)
-    srv.scheduler.budget = srv.footprint(reqs[0])
+    probe = Server(slots=1)
+    fp = probe.footprint(reqs[0])
+    probe.close()
+    srv = Server(slots=4, budget_bytes=fp)
     res = srv.serve(reqs, realtime=False)
     assert all(r.error is None for r in res)
     assert srv.max_active == 1
+    assert srv.stats().peak_used == fp
+    srv.close()
+
+
+def test_served_solution_equals_a_direct_solve(mg):
+    """The runtime's path (right-hand side drawn at admission, copied in,
+    assembled by mg_rhs, solved from zero, copied out) gives bitwise the
+    solution of the same solve made directly through MGSolver."""
+    import torch
+    from paper_1612_04796_gb300 import inputs
+    from paper_1612_04796_gb300.serving import Request, Server
+    req = Request(0, (2.0, 1.0, 1.0), (5, 5, 5), 4, seed=77)
+    srv = Server(slots=2)
+    res = srv.serve([req], realtime=False)[0]
+    srv.close()
+    assert res.error is None and res.relres <= 1e-10
+    s = mg.MGSolver(req.lengths, req.counts, req.P, overlap=req.overlap, precision="mixed", outer_df64=True)
+    b = s.rhs(torch.tensor(inputs.gaussian(s.num_dofs(), req.seed), device="cuda"))
+    u, its, rel, _ = s.solve(b, tol=req.tol, use_cg=True, maxit=400)
+    assert its == res.iterations and rel == res.relres
+    np.testing.assert_array_equal(u.cpu().numpy(), res.u)
+    s.close()
+
+
+def test_fp64_standalone_server(mg):
+    """Solver options reach every request: an FP64 standalone-V-cycle server
+    reproduces the 12 cycles of the 16^3-element, P = 8 problem class on a
+    smaller mesh of the same order (Table 1 row 1: about 11-12 cycles)."""
+    from paper_1612_04796_gb300.serving import Request, Server
+    srv = Server(slots=1, precision="fp64", use_cg=False)
+    res = srv.serve([Request(0, (1.0, 1.0, 1.0), (6, 6, 6), 8, seed=5)], realtime=False)[0]
+    srv.close()
+    assert res.error is None and res.relres <= 1e-10
+    assert 10 <= res.iterations <= 13
