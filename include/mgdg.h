@@ -219,6 +219,34 @@ mg_status mg_solve(mg_ctx* ctx, double* u, const double* f, double tol, int maxi
 mg_status mg_solve_host(mg_ctx* ctx, double* u_host, const double* f_host, double tol, int maxit, int use_cg,
                         int* iters, double* relres, double* history);
 
+/*
+ * mg_solve_batch -- MG-CG solves (mg_solve with use_cg = 1) of `count`
+ * independent problems advanced together: every sweep of their iterations
+ * (operator, smoother, scatter, transfers, coarse passes, CG vector passes)
+ * is issued as one launch for all of them, each problem keeping its own
+ * blocks, tables and vectors, so that small problems share the GPU instead
+ * of each paying for its own launches.  The problems may differ in box, mesh,
+ * order and options; launches merge where their kernel sequences agree
+ * (same order and level structure), the rest run one by one.
+ *   ctxs     count distinct contexts, each with its workspace bound
+ *   u, f     per problem: device vectors as in mg_solve (u: initial guess in,
+ *            zero-mean solution out)
+ *   count    1 .. 16
+ *   tol, maxit  as in mg_solve, the same for every problem
+ *   iters, relres, status  (host, count entries each, may be NULL) per problem:
+ *            its iteration count, relative residual and mg_status (MG_OK,
+ *            MG_ENOCONV at maxit or on a non-finite residual, MG_EINVAL on a
+ *            non-finite initial residual, MG_ECUDA if a tensor-core wait ran out)
+ * Every launch goes to the stream of ctxs[0] (the other contexts' streams are
+ * not used); the call synchronises it once per half iteration.  Each problem
+ * gets the same kernels, block decomposition and reduction order as its own
+ * mg_solve, hence bitwise the same result.  Returns MG_EINVAL / MG_ENOTREADY
+ * for bad arguments, MG_ECUDA if a CUDA call failed (message on ctxs[0]),
+ * else MG_OK (per-problem outcomes in status).
+ */
+mg_status mg_solve_batch(mg_ctx* const* ctxs, int count, double* const* u, const double* const* f, double tol,
+                         int maxit, int* iters, double* relres, int* status);
+
 /* mg_vcycle_df64 -- one V-cycle (Algorithm 1) like mg_vcycle on FP64 vectors u,
  * f of the finest level, with the multigrid arithmetic in double-float (the
  * preconditioner of MG_DF64).  Uses two of the outer-iteration work vectors. */

@@ -14,7 +14,7 @@ def build(force=False, verbose=False):
 
 
 def __getattr__(name):
-    if name in ("MGSolver", "MGError"):
+    if name in ("MGSolver", "MGError", "solve_batch"):
         from . import solver
         return getattr(solver, name)
     raise AttributeError(name)

@@ -120,6 +120,7 @@ SIGNATURES = {
     "mg_coarse_solve": (_S, [_P, _P, _P]),
     "mg_vcycle": (_S, [_P, _P, _P]),
     "mg_solve": (_S, [_P, _P, _P, _D, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_D), _P]),
+    "mg_solve_batch": (_S, [_P, _I, _P, _P, _D, _I, _P, _P, _P]),
     "mg_solve_host": (_S, [_P, _P, _P, _D, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_D), _P]),
     "mg_apply_sipg_f32": (_S, [_P, _I, _P, _P]),
     "mg_smooth_f32": (_S, [_P, _I, _P, _P, _I]),

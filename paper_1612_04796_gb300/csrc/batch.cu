@@ -1,0 +1,96 @@
+// Batched execution: several independent problems advance together, each
+// sweep of the solver (operator, smoother, scatter, transfer, coarse pass,
+// vector pass) issued as one grouped launch for all of them.
+//
+// The solver's launch sequence for one problem is recorded (launch_pdl with a
+// recorder installed) instead of launched; the sequences of the problems are
+// then merged: the records of one problem keep their order, and at each step
+// the kernel found at the head of the most sequences is launched once through
+// its grouped twin (k_grouped), every problem getting its own block range and
+// parameters.  Problems of different sizes, aspect ratios and even kernel
+// variants (a small mesh takes the direction-split operator) merge as far as
+// their sequences agree.
+#include "mg_internal.h"
+
+#include <algorithm>
+
+namespace mgdg {
+
+LaunchRecorder*& launch_recorder() {
+  static thread_local LaunchRecorder* rec = nullptr;
+  return rec;
+}
+
+namespace {
+
+struct ScalarPtrs {
+  const double* p[kMaxBatch];
+};
+
+__global__ void k_gather_scalars(ScalarPtrs src, int n, double* out) {
+  const int i = threadIdx.x;
+  if (i < n) out[i] = *src.p[i];
+}
+
+bool same_kernel(const LaunchRec& a, const LaunchRec& b) {
+  return a.key == b.key && a.block.x == b.block.x && a.block.y == b.block.y && a.block.z == b.block.z &&
+         a.smem == b.smem;
+}
+
+}  // namespace
+
+cudaError_t launch_merged(const std::vector<LaunchRecorder>& seqs, cudaStream_t s, long long* launches) {
+  const int B = (int)seqs.size();
+  std::vector<size_t> head(B, 0);
+  long long n_launch = 0;
+  for (;;) {
+    // the kernel at the head of the most sequences (ties: the lowest problem index)
+    int best = -1, best_count = 0;
+    for (int i = 0; i < B; ++i) {
+      if (head[i] >= seqs[i].recs.size()) continue;
+      const LaunchRec& r = seqs[i].recs[head[i]];
+      int count = 0;
+      for (int j = 0; j < B; ++j)
+        if (head[j] < seqs[j].recs.size() && same_kernel(seqs[j].recs[head[j]], r)) ++count;
+      if (count > best_count) {
+        best = i;
+        best_count = count;
+      }
+    }
+    if (best < 0) break;
+    const LaunchRec& ref = seqs[best].recs[head[best]];
+    const LaunchRec* group[kMaxBatch];
+    int n = 0;
+    for (int j = 0; j < B; ++j) {
+      if (head[j] < seqs[j].recs.size() && same_kernel(seqs[j].recs[head[j]], ref)) {
+        group[n++] = &seqs[j].recs[head[j]];
+        ++head[j];
+      }
+    }
+    cudaError_t e = cudaSuccess;
+    if (n > 1 && ref.grouped) {
+      for (int k = 0; k < n && e == cudaSuccess; k += kMaxBatch) {
+        e = ref.grouped(group + k, std::min(kMaxBatch, n - k), s);
+        ++n_launch;
+      }
+    } else {
+      for (int k = 0; k < n && e == cudaSuccess; ++k) {
+        e = group[k]->plain(*group[k], s);
+        ++n_launch;
+      }
+    }
+    if (e != cudaSuccess) return e;
+  }
+  if (launches) *launches += n_launch;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_scalars(const double* const* src, int n, double* out, cudaStream_t s) {
+  if (n < 1 || n > kMaxBatch) return cudaErrorInvalidValue;
+  ScalarPtrs p{};
+  for (int i = 0; i < n; ++i) p.p[i] = src[i];
+  k_gather_scalars<<<1, 32, 0, s>>>(p, n, out);
+  return cudaGetLastError();
+}
+
+}  // namespace mgdg

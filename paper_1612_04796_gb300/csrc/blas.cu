@@ -25,19 +25,24 @@ __device__ double block_reduce(double v, double* sh) {
 
 // mode 0: sum x*y   mode 1: sum x   (T = double | float input)
 template <typename T>
+__device__ __forceinline__ void partial_body(BlockIdx bi_, const T* __restrict__ x, const T* __restrict__ y, int64_t n,
+                                                      int mode, double* partial) {
+  __shared__ double sh[kThreads];
+  double acc = 0.0;
+  for (int64_t i = bi_.b * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)bi_.g * blockDim.x)
+    acc += mode == 0 ? (double)x[i] * (double)y[i] : (double)x[i];
+  double r = block_reduce(acc, sh);
+  if (threadIdx.x == 0) partial[bi_.b] = r;
+}
+
+template <typename T>
 __global__ void __launch_bounds__(kThreads) k_partial(const T* __restrict__ x, const T* __restrict__ y, int64_t n,
                                                       int mode, double* partial) {
   pdl_entry();
-  __shared__ double sh[kThreads];
-  double acc = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    acc += mode == 0 ? (double)x[i] * (double)y[i] : (double)x[i];
-  double r = block_reduce(acc, sh);
-  if (threadIdx.x == 0) partial[blockIdx.x] = r;
+  partial_body<T>(plain_block(), x, y, n, mode, partial);
 }
 
-__global__ void __launch_bounds__(kThreads) k_final(const double* partial, int nb, double* scal, int slot) {
-  pdl_entry();
+__device__ __forceinline__ void final_body(BlockIdx bi_, const double* partial, int nb, double* scal, int slot) {
   __shared__ double sh[kThreads];
   double acc = 0.0;
   for (int i = threadIdx.x; i < nb; i += blockDim.x) acc += partial[i];
@@ -45,24 +50,33 @@ __global__ void __launch_bounds__(kThreads) k_final(const double* partial, int n
   if (threadIdx.x == 0) scal[slot] = r;
 }
 
-template <typename T>
-__global__ void k_sub_mean(T* x, int64_t n, const double* scal, int slot) {
+__global__ void __launch_bounds__(kThreads) k_final(const double* partial, int nb, double* scal, int slot) {
   pdl_entry();
+  final_body(plain_block(), partial, nb, scal, slot);
+}
+
+template <typename T>
+__device__ __forceinline__ void sub_mean_body(BlockIdx bi_, T* x, int64_t n, const double* scal, int slot) {
   const T mean = (T)(scal[slot] / (double)n);
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+  for (int64_t i = bi_.b * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)bi_.g * blockDim.x)
     x[i] -= mean;
 }
 
+template <typename T>
+__global__ void k_sub_mean(T* x, int64_t n, const double* scal, int slot) {
+  pdl_entry();
+  sub_mean_body<T>(plain_block(), x, n, scal, slot);
+}
+
 // The CG update with the partial sums of the new r and r^2 (columns 0, 1).
-__global__ void __launch_bounds__(kThreads) k_cg_update(double* __restrict__ x, const double* __restrict__ p,
+__device__ __forceinline__ void cg_update_body(BlockIdx bi_, double* __restrict__ x, const double* __restrict__ p,
                                                         double* __restrict__ r, const double* __restrict__ q,
                                                         int64_t n, double* scal, double* partial) {
-  pdl_entry();
   __shared__ double sh[kThreads];
   const double alpha = scal[kSlotRZ] / scal[kSlotPQ];
-  if (blockIdx.x == 0 && threadIdx.x == 0) scal[kSlotAlpha] = alpha;
+  if (bi_.b == 0 && threadIdx.x == 0) scal[kSlotAlpha] = alpha;
   double s1 = 0.0, s2 = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t i = bi_.b * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)bi_.g * blockDim.x) {
     x[i] += alpha * p[i];
     const double ri = r[i] - alpha * q[i];
     r[i] = ri;
@@ -73,9 +87,16 @@ __global__ void __launch_bounds__(kThreads) k_cg_update(double* __restrict__ x, 
   __syncthreads();
   const double b2 = block_reduce(s2, sh);
   if (threadIdx.x == 0) {
-    partial[blockIdx.x] = b1;
-    partial[gridDim.x + blockIdx.x] = b2;
+    partial[bi_.b] = b1;
+    partial[bi_.g + bi_.b] = b2;
   }
+}
+
+__global__ void __launch_bounds__(kThreads) k_cg_update(double* __restrict__ x, const double* __restrict__ p,
+                                                        double* __restrict__ r, const double* __restrict__ q,
+                                                        int64_t n, double* scal, double* partial) {
+  pdl_entry();
+  cg_update_body(plain_block(), x, p, r, q, n, scal, partial);
 }
 
 // Sum `cols` columns of nb partials each, in a fixed order, into v[0 .. cols).
@@ -88,9 +109,8 @@ __device__ void final_columns(const double* partial, int nb, int cols, double* v
   }
 }
 
-__global__ void __launch_bounds__(kThreads) k_cg_update_final(const double* partial, int nb, double* scal,
+__device__ __forceinline__ void cg_update_final_body(BlockIdx bi_, const double* partial, int nb, double* scal,
                                                               int64_t n) {
-  pdl_entry();
   __shared__ double sh[kThreads];
   double v[2];
   final_columns(partial, nb, 2, v, sh);
@@ -98,6 +118,12 @@ __global__ void __launch_bounds__(kThreads) k_cg_update_final(const double* part
     scal[kSlotSum] = v[0];
     scal[kSlotRR] = fmax(v[1] - v[0] * v[0] / (double)n, 0.0);
   }
+}
+
+__global__ void __launch_bounds__(kThreads) k_cg_update_final(const double* partial, int nb, double* scal,
+                                                              int64_t n) {
+  pdl_entry();
+  cg_update_final_body(plain_block(), partial, nb, scal, n);
 }
 
 template <typename TZ>
@@ -110,12 +136,11 @@ __device__ __forceinline__ double z_scale(const double* scal) {
 // Partial sums of z, z.q, z.r (columns 0 .. 2), z taken unscaled (the FP32
 // preconditioner's scale is applied to the totals).
 template <typename TZ>
-__global__ void __launch_bounds__(kThreads) k_cg_sums(const TZ* __restrict__ zs, const double* __restrict__ q,
+__device__ __forceinline__ void cg_sums_body(BlockIdx bi_, const TZ* __restrict__ zs, const double* __restrict__ q,
                                                       const double* __restrict__ r, int64_t n, double* partial) {
-  pdl_entry();
   __shared__ double sh[kThreads];
   double a[3] = {0.0, 0.0, 0.0};
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t i = bi_.b * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)bi_.g * blockDim.x) {
     const double z = (double)zs[i];
     a[0] += z;
     a[1] += z * q[i];
@@ -124,15 +149,21 @@ __global__ void __launch_bounds__(kThreads) k_cg_sums(const TZ* __restrict__ zs,
   for (int k = 0; k < 3; ++k) {
     const double b = block_reduce(a[k], sh);
     __syncthreads();
-    if (threadIdx.x == 0) partial[k * gridDim.x + blockIdx.x] = b;
+    if (threadIdx.x == 0) partial[k * bi_.g + bi_.b] = b;
   }
+}
+
+template <typename TZ>
+__global__ void __launch_bounds__(kThreads) k_cg_sums(const TZ* __restrict__ zs, const double* __restrict__ q,
+                                                      const double* __restrict__ r, int64_t n, double* partial) {
+  pdl_entry();
+  cg_sums_body<TZ>(plain_block(), zs, q, r, n, partial);
 }
 
 // With z' = z - mean(z): z'.q' = z.q (1^T q = 1^T A p = 0) and
 // z'.r' = z.r - sum(z) sum(r) / n (sum(r) from the update pass).
 template <typename TZ>
-__global__ void __launch_bounds__(kThreads) k_cg_sums_final(const double* partial, int nb, double* scal, int64_t n) {
-  pdl_entry();
+__device__ __forceinline__ void cg_sums_final_body(BlockIdx bi_, const double* partial, int nb, double* scal, int64_t n) {
   __shared__ double sh[kThreads];
   double v[3];
   final_columns(partial, nb, 3, v, sh);
@@ -147,75 +178,114 @@ __global__ void __launch_bounds__(kThreads) k_cg_sums_final(const double* partia
   }
 }
 
+template <typename TZ>
+__global__ void __launch_bounds__(kThreads) k_cg_sums_final(const double* partial, int nb, double* scal, int64_t n) {
+  pdl_entry();
+  cg_sums_final_body<TZ>(plain_block(), partial, nb, scal, n);
+}
+
 // p = (z - mean(z)) + beta p; pdf (if given) receives p split into double-float pairs
 template <typename TZ>
-__global__ void k_cg_newdir(double* __restrict__ p, const TZ* __restrict__ zs, int64_t n, const double* scal,
+__device__ __forceinline__ void cg_newdir_body(BlockIdx bi_, double* __restrict__ p, const TZ* __restrict__ zs, int64_t n, const double* scal,
                             df64* __restrict__ pdf) {
-  pdl_entry();
   const double zsc = z_scale<TZ>(scal), muz = scal[kSlotMuZ], beta = scal[kSlotBeta];
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t i = bi_.b * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)bi_.g * blockDim.x) {
     const double v = ((double)zs[i] * zsc - muz) + beta * p[i];
     p[i] = v;
     if (pdf) pdf[i] = df_from_double(v);
   }
 }
 
+template <typename TZ>
+__global__ void k_cg_newdir(double* __restrict__ p, const TZ* __restrict__ zs, int64_t n, const double* scal,
+                            df64* __restrict__ pdf) {
+  pdl_entry();
+  cg_newdir_body<TZ>(plain_block(), p, zs, n, scal, pdf);
+}
+
 // y = x (accumulate = 0) or y += x (accumulate = 1), x double-float, y FP64
+__device__ __forceinline__ void join_df64_body(BlockIdx bi_, const df64* __restrict__ x, double* __restrict__ y, int64_t n, int accumulate) {
+  for (int64_t i = bi_.b * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)bi_.g * blockDim.x)
+    y[i] = accumulate ? y[i] + df_to_double(x[i]) : df_to_double(x[i]);
+}
+
 __global__ void k_join_df64(const df64* __restrict__ x, double* __restrict__ y, int64_t n, int accumulate) {
   pdl_entry();
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    y[i] = accumulate ? y[i] + df_to_double(x[i]) : df_to_double(x[i]);
+  join_df64_body(plain_block(), x, y, n, accumulate);
+}
+
+__device__ __forceinline__ void split_df64_body(BlockIdx bi_, const double* __restrict__ x, df64* __restrict__ y, int64_t n) {
+  for (int64_t i = bi_.b * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)bi_.g * blockDim.x)
+    y[i] = df_from_double(x[i]);
 }
 
 __global__ void k_split_df64(const double* __restrict__ x, df64* __restrict__ y, int64_t n) {
   pdl_entry();
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    y[i] = df_from_double(x[i]);
+  split_df64_body(plain_block(), x, y, n);
 }
 
 // q = qdf as FP64 and the partial sums of p . q
-__global__ void __launch_bounds__(kThreads) k_dot_dfq(const double* __restrict__ p, const df64* __restrict__ qdf,
+__device__ __forceinline__ void dot_dfq_body(BlockIdx bi_, const double* __restrict__ p, const df64* __restrict__ qdf,
                                                       double* __restrict__ q, int64_t n, double* partial) {
-  pdl_entry();
   __shared__ double sh[kThreads];
   double acc = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t i = bi_.b * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)bi_.g * blockDim.x) {
     const double qi = df_to_double(qdf[i]);
     q[i] = qi;
     acc += p[i] * qi;
   }
   const double b = block_reduce(acc, sh);
-  if (threadIdx.x == 0) partial[blockIdx.x] = b;
+  if (threadIdx.x == 0) partial[bi_.b] = b;
+}
+
+__global__ void __launch_bounds__(kThreads) k_dot_dfq(const double* __restrict__ p, const df64* __restrict__ qdf,
+                                                      double* __restrict__ q, int64_t n, double* partial) {
+  pdl_entry();
+  dot_dfq_body(plain_block(), p, qdf, q, n, partial);
+}
+
+__device__ __forceinline__ void add_body(BlockIdx bi_, double* __restrict__ y, const double* __restrict__ x, int64_t n) {
+  for (int64_t i = bi_.b * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)bi_.g * blockDim.x)
+    y[i] += x[i];
 }
 
 __global__ void k_add(double* __restrict__ y, const double* __restrict__ x, int64_t n) {
   pdl_entry();
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    y[i] += x[i];
+  add_body(plain_block(), y, x, n);
 }
 
-__global__ void k_to_f32(const double* __restrict__ x, float* __restrict__ y, int64_t n, const double* scal,
+__device__ __forceinline__ void to_f32_body(BlockIdx bi_, const double* __restrict__ x, float* __restrict__ y, int64_t n, const double* scal,
                          int slot) {
-  pdl_entry();
   double s = 1.0;
   if (slot >= 0) {
     double nrm = sqrt(scal[slot]);
     s = nrm > 0.0 ? 1.0 / nrm : 1.0;
   }
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+  for (int64_t i = bi_.b * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)bi_.g * blockDim.x)
     y[i] = (float)(x[i] * s);
 }
 
-__global__ void k_from_f32(const float* __restrict__ x, double* __restrict__ y, int64_t n, const double* scal,
-                           int slot) {
+__global__ void k_to_f32(const double* __restrict__ x, float* __restrict__ y, int64_t n, const double* scal,
+                         int slot) {
   pdl_entry();
+  to_f32_body(plain_block(), x, y, n, scal, slot);
+}
+
+__device__ __forceinline__ void from_f32_body(BlockIdx bi_, const float* __restrict__ x, double* __restrict__ y, int64_t n, const double* scal,
+                           int slot) {
   double s = 1.0;
   if (slot >= 0) {
     double nrm = sqrt(scal[slot]);
     s = nrm > 0.0 ? nrm : 1.0;
   }
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+  for (int64_t i = bi_.b * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)bi_.g * blockDim.x)
     y[i] = (double)x[i] * s;
+}
+
+__global__ void k_from_f32(const float* __restrict__ x, double* __restrict__ y, int64_t n, const double* scal,
+                           int slot) {
+  pdl_entry();
+  from_f32_body(plain_block(), x, y, n, scal, slot);
 }
 
 struct MassArgs {
@@ -279,10 +349,15 @@ __global__ void k_coords(const double* tab, int64_t nodes, int n, int64_t Ne, in
 }
 
 template <typename T>
+__device__ __forceinline__ void zero_body(BlockIdx bi_, T* x, int64_t n) {
+  for (int64_t i = bi_.b * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)bi_.g * blockDim.x)
+    x[i] = (T)0;
+}
+
+template <typename T>
 __global__ void k_zero(T* x, int64_t n) {
   pdl_entry();
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    x[i] = (T)0;
+  zero_body<T>(plain_block(), x, n);
 }
 
 inline int grid_for(int64_t n) {
@@ -294,9 +369,9 @@ inline int grid_for(int64_t n) {
 
 template <typename T>
 cudaError_t reduce(const mg_ctx* c, const T* x, const T* y, int64_t n, int mode, int slot) {
-  launch_pdl(k_partial<T>, kRedBlocks, kThreads, 0, c->stream, x, y, n, mode, c->ws.red);
+  launch_pdl<partial_body<T>>(k_partial<T>, kRedBlocks, kThreads, 0, c->stream, x, y, n, mode, c->ws.red);
   c->nlaunch += 1;
-  launch_pdl(k_final, 1, kThreads, 0, c->stream, c->ws.red, kRedBlocks, c->ws.scal, slot);
+  launch_pdl<final_body>(k_final, 1, kThreads, 0, c->stream, c->ws.red, kRedBlocks, c->ws.scal, slot);
   c->nlaunch += 1;
   return cudaGetLastError();
 }
@@ -312,14 +387,14 @@ cudaError_t launch_sum(const mg_ctx* c, const double* x, int64_t n, int slot) {
 }
 
 cudaError_t launch_sub_mean(const mg_ctx* c, double* x, int64_t n, int sum_slot) {
-  launch_pdl(k_sub_mean<double>, grid_for(n), kThreads, 0, c->stream, x, n, c->ws.scal, sum_slot);
+  launch_pdl<sub_mean_body<double>>(k_sub_mean<double>, grid_for(n), kThreads, 0, c->stream, x, n, c->ws.scal, sum_slot);
   c->nlaunch += 1;
   return cudaGetLastError();
 }
 
 cudaError_t launch_cg_update(const mg_ctx* c, double* x, const double* p, double* r, const double* q, int64_t n) {
-  launch_pdl(k_cg_update, kRedBlocks, kThreads, 0, c->stream, x, p, r, q, n, c->ws.scal, c->ws.red);
-  launch_pdl(k_cg_update_final, 1, kThreads, 0, c->stream, c->ws.red, kRedBlocks, c->ws.scal, n);
+  launch_pdl<cg_update_body>(k_cg_update, kRedBlocks, kThreads, 0, c->stream, x, p, r, q, n, c->ws.scal, c->ws.red);
+  launch_pdl<cg_update_final_body>(k_cg_update_final, 1, kThreads, 0, c->stream, c->ws.red, kRedBlocks, c->ws.scal, n);
   c->nlaunch += 2;
   return cudaGetLastError();
 }
@@ -327,9 +402,9 @@ cudaError_t launch_cg_update(const mg_ctx* c, double* x, const double* p, double
 template <typename TZ>
 cudaError_t launch_cg_direction(const mg_ctx* c, double* p, const TZ* z, const double* q, const double* r, int64_t n,
                                 df64* pdf) {
-  launch_pdl(k_cg_sums<TZ>, kRedBlocks, kThreads, 0, c->stream, z, q, r, n, c->ws.red);
-  launch_pdl(k_cg_sums_final<TZ>, 1, kThreads, 0, c->stream, c->ws.red, kRedBlocks, c->ws.scal, n);
-  launch_pdl(k_cg_newdir<TZ>, grid_for(n), kThreads, 0, c->stream, p, z, n, c->ws.scal, pdf);
+  launch_pdl<cg_sums_body<TZ>>(k_cg_sums<TZ>, kRedBlocks, kThreads, 0, c->stream, z, q, r, n, c->ws.red);
+  launch_pdl<cg_sums_final_body<TZ>>(k_cg_sums_final<TZ>, 1, kThreads, 0, c->stream, c->ws.red, kRedBlocks, c->ws.scal, n);
+  launch_pdl<cg_newdir_body<TZ>>(k_cg_newdir<TZ>, grid_for(n), kThreads, 0, c->stream, p, z, n, c->ws.scal, pdf);
   c->nlaunch += 3;
   return cudaGetLastError();
 }
@@ -342,38 +417,38 @@ template cudaError_t launch_cg_direction<df64>(const mg_ctx*, double*, const df6
                                                int64_t, df64*);
 
 cudaError_t launch_split_df64(const mg_ctx* c, const double* x, df64* y, int64_t n) {
-  launch_pdl(k_split_df64, grid_for(n), kThreads, 0, c->stream, x, y, n);
+  launch_pdl<split_df64_body>(k_split_df64, grid_for(n), kThreads, 0, c->stream, x, y, n);
   c->nlaunch += 1;
   return cudaGetLastError();
 }
 
 cudaError_t launch_join_df64(const mg_ctx* c, const df64* x, double* y, int64_t n, int accumulate) {
-  launch_pdl(k_join_df64, grid_for(n), kThreads, 0, c->stream, x, y, n, accumulate);
+  launch_pdl<join_df64_body>(k_join_df64, grid_for(n), kThreads, 0, c->stream, x, y, n, accumulate);
   c->nlaunch += 1;
   return cudaGetLastError();
 }
 
 cudaError_t launch_dot_dfq(const mg_ctx* c, const double* p, const df64* qdf, double* q, int64_t n, int slot) {
-  launch_pdl(k_dot_dfq, kRedBlocks, kThreads, 0, c->stream, p, qdf, q, n, c->ws.red);
-  launch_pdl(k_final, 1, kThreads, 0, c->stream, c->ws.red, kRedBlocks, c->ws.scal, slot);
+  launch_pdl<dot_dfq_body>(k_dot_dfq, kRedBlocks, kThreads, 0, c->stream, p, qdf, q, n, c->ws.red);
+  launch_pdl<final_body>(k_final, 1, kThreads, 0, c->stream, c->ws.red, kRedBlocks, c->ws.scal, slot);
   c->nlaunch += 2;
   return cudaGetLastError();
 }
 
 cudaError_t launch_add(const mg_ctx* c, double* y, const double* x, int64_t n) {
-  launch_pdl(k_add, grid_for(n), kThreads, 0, c->stream, y, x, n);
+  launch_pdl<add_body>(k_add, grid_for(n), kThreads, 0, c->stream, y, x, n);
   c->nlaunch += 1;
   return cudaGetLastError();
 }
 
 cudaError_t launch_to_f32(const mg_ctx* c, const double* x, float* y, int64_t n, int norm_slot) {
-  launch_pdl(k_to_f32, grid_for(n), kThreads, 0, c->stream, x, y, n, c->ws.scal, norm_slot);
+  launch_pdl<to_f32_body>(k_to_f32, grid_for(n), kThreads, 0, c->stream, x, y, n, c->ws.scal, norm_slot);
   c->nlaunch += 1;
   return cudaGetLastError();
 }
 
 cudaError_t launch_from_f32(const mg_ctx* c, const float* x, double* y, int64_t n, int norm_slot) {
-  launch_pdl(k_from_f32, grid_for(n), kThreads, 0, c->stream, x, y, n, c->ws.scal, norm_slot);
+  launch_pdl<from_f32_body>(k_from_f32, grid_for(n), kThreads, 0, c->stream, x, y, n, c->ws.scal, norm_slot);
   c->nlaunch += 1;
   return cudaGetLastError();
 }
@@ -387,9 +462,9 @@ cudaError_t launch_rhs(const mg_ctx* c, const double* f, double* b) {
   a.Ne = c->Ne;
   launch_pdl(k_mass_partial, kRedBlocks, kThreads, 0, c->stream, a, f, c->ws.red);
   c->nlaunch += 1;
-  launch_pdl(k_final, 1, kThreads, 0, c->stream, c->ws.red, kRedBlocks, c->ws.scal, kSlotMassF);
+  launch_pdl<final_body>(k_final, 1, kThreads, 0, c->stream, c->ws.red, kRedBlocks, c->ws.scal, kSlotMassF);
   c->nlaunch += 1;
-  launch_pdl(k_final, 1, kThreads, 0, c->stream, c->ws.red + kRedBlocks, kRedBlocks, c->ws.scal, kSlotMass);
+  launch_pdl<final_body>(k_final, 1, kThreads, 0, c->stream, c->ws.red + kRedBlocks, kRedBlocks, c->ws.scal, kSlotMass);
   c->nlaunch += 1;
   launch_pdl(k_rhs, grid_for(lv.N), kThreads, 0, c->stream, a, f, b, c->ws.scal);
   c->nlaunch += 1;
@@ -409,7 +484,7 @@ cudaError_t launch_coords(const mg_ctx* c, int l, double* x, double* y, double* 
 
 template <typename T>
 cudaError_t launch_zero(const mg_ctx* c, T* x, int64_t n) {
-  launch_pdl(k_zero<T>, grid_for(n), kThreads, 0, c->stream, x, n);
+  launch_pdl<zero_body<T>>(k_zero<T>, grid_for(n), kThreads, 0, c->stream, x, n);
   c->nlaunch += 1;
   return cudaGetLastError();
 }

@@ -40,17 +40,16 @@ __device__ __forceinline__ int64_t eb_index(int gx, int gy, int gz, const Coarse
 // TI / TO: type of the input / output vector (the FP32 hierarchy reads its
 // right-hand side and writes its solution in FP32; intermediates are FP64).
 template <typename TI, typename TO>
-__global__ void k_coarse_axis(const TI* __restrict__ in, TO* __restrict__ out, const double* __restrict__ Q,
+__device__ __forceinline__ void coarse_axis_body(BlockIdx bi_, const TI* __restrict__ in, TO* __restrict__ out, const double* __restrict__ Q,
                               CoarseDims d, int axis, int backward, int in_eb, int out_eb, const double* scal,
                               int mean_slot, int scale, const double* lx, const double* ly, const double* lz,
                               int nx0, int ny0, int nz0) {
-  pdl_entry();
   const int Nx = d.Ng[0], Ny = d.Ng[1], Nz = d.Ng[2];
   const int64_t total = (int64_t)Nx * Ny * Nz;
   const int Na = d.Ng[axis];
   const double shift = mean_slot >= 0 ? scal[mean_slot] / (double)total : 0.0;
-  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
-       idx += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t idx = bi_.b * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)bi_.g * blockDim.x) {
     int g[3];
     const int i32 = (int)idx, gyz = i32 / Nx;  // coarse sizes fit in 32 bits
     g[0] = i32 - gyz * Nx;
@@ -74,6 +73,15 @@ __global__ void k_coarse_axis(const TI* __restrict__ in, TO* __restrict__ out, c
   }
 }
 
+template <typename TI, typename TO>
+__global__ void k_coarse_axis(const TI* __restrict__ in, TO* __restrict__ out, const double* __restrict__ Q,
+                              CoarseDims d, int axis, int backward, int in_eb, int out_eb, const double* scal,
+                              int mean_slot, int scale, const double* lx, const double* ly, const double* lz,
+                              int nx0, int ny0, int nz0) {
+  pdl_entry();
+  coarse_axis_body<TI, TO>(plain_block(), in, out, Q, d, axis, backward, in_eb, out_eb, scal, mean_slot, scale, lx, ly, lz, nx0, ny0, nz0);
+}
+
 // The six axis passes: f0 (element-blocked) -> x, y, z forward, scale, z, y, x
 // backward -> u0 (element-blocked); A, B lexicographic FP64 scratch.
 template <typename TI, typename TO>
@@ -85,13 +93,13 @@ cudaError_t coarse_passes(const double* const Q[3], const double* const lam[3], 
   if (blocks > 152 * 8) blocks = 152 * 8;
   const int* nz = null_mode;
   const int b = (int)blocks;
-  launch_pdl(k_coarse_axis<TI, double>, b, 256, 0, s, f0, A, Q[0], d, 0, 0, 1, 0, scal, mean_slot, 0, nullptr, nullptr, nullptr, 0, 0, 0);
-  launch_pdl(k_coarse_axis<double, double>, b, 256, 0, s, A, B, Q[1], d, 1, 0, 0, 0, scal, -1, 0, nullptr, nullptr, nullptr, 0, 0, 0);
-  launch_pdl(k_coarse_axis<double, double>, b, 256, 0, s, B, A, Q[2], d, 2, 0, 0, 0, scal, -1, 1, lam[0], lam[1], lam[2],
+  launch_pdl<coarse_axis_body<TI, double>>(k_coarse_axis<TI, double>, b, 256, 0, s, f0, A, Q[0], d, 0, 0, 1, 0, scal, mean_slot, 0, nullptr, nullptr, nullptr, 0, 0, 0);
+  launch_pdl<coarse_axis_body<double, double>>(k_coarse_axis<double, double>, b, 256, 0, s, A, B, Q[1], d, 1, 0, 0, 0, scal, -1, 0, nullptr, nullptr, nullptr, 0, 0, 0);
+  launch_pdl<coarse_axis_body<double, double>>(k_coarse_axis<double, double>, b, 256, 0, s, B, A, Q[2], d, 2, 0, 0, 0, scal, -1, 1, lam[0], lam[1], lam[2],
                                                   nz[0], nz[1], nz[2]);
-  launch_pdl(k_coarse_axis<double, double>, b, 256, 0, s, A, B, Q[2], d, 2, 1, 0, 0, scal, -1, 0, nullptr, nullptr, nullptr, 0, 0, 0);
-  launch_pdl(k_coarse_axis<double, double>, b, 256, 0, s, B, A, Q[1], d, 1, 1, 0, 0, scal, -1, 0, nullptr, nullptr, nullptr, 0, 0, 0);
-  launch_pdl(k_coarse_axis<double, TO>, b, 256, 0, s, A, u0, Q[0], d, 0, 1, 0, 1, scal, -1, 0, nullptr, nullptr, nullptr, 0, 0, 0);
+  launch_pdl<coarse_axis_body<double, double>>(k_coarse_axis<double, double>, b, 256, 0, s, A, B, Q[2], d, 2, 1, 0, 0, scal, -1, 0, nullptr, nullptr, nullptr, 0, 0, 0);
+  launch_pdl<coarse_axis_body<double, double>>(k_coarse_axis<double, double>, b, 256, 0, s, B, A, Q[1], d, 1, 1, 0, 0, scal, -1, 0, nullptr, nullptr, nullptr, 0, 0, 0);
+  launch_pdl<coarse_axis_body<double, TO>>(k_coarse_axis<double, TO>, b, 256, 0, s, A, u0, Q[0], d, 0, 1, 0, 1, scal, -1, 0, nullptr, nullptr, nullptr, 0, 0, 0);
   return cudaGetLastError();
 }
 

@@ -1,11 +1,8 @@
-// Instantiations of the compile-time-size smoother kernel, m = 25 27 29 31 33 35.
+// Instantiations of the compile-time-size smoother kernel, m = 25 27 29.
 #include "fdm_tmpl.cuh"
 
 namespace mgdg {
 MGDG_FDM_INSTANTIATE(25)
 MGDG_FDM_INSTANTIATE(27)
 MGDG_FDM_INSTANTIATE(29)
-MGDG_FDM_INSTANTIATE(31)
-MGDG_FDM_INSTANTIATE(33)
-MGDG_FDM_INSTANTIATE(35)
 }  // namespace mgdg

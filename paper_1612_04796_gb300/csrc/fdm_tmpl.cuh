@@ -94,8 +94,7 @@ struct FdmShape {
 };
 
 template <typename T, int M>
-__global__ void __launch_bounds__(256) k_fdm_m(FdmArgs<T> a) {
-  pdl_entry();
+__device__ __forceinline__ void fdm_m_body(BlockIdx bi_, FdmArgs<T> a) {
   constexpr int M2 = M * M, M3 = M2 * M;
   constexpr bool kSmemTile = FdmShape<T, M>::smem_tile;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -113,7 +112,7 @@ __global__ void __launch_bounds__(256) k_fdm_m(FdmArgs<T> a) {
   const T* __restrict__ dinv = a.tab + a.dinv;
   const int n = a.n, no = a.no, n3 = n * n * n, spb = a.spb;
   const int lines = spb * M2;
-  for (int64_t s0 = (int64_t)blockIdx.x * spb; s0 < a.Ne; s0 += (int64_t)gridDim.x * spb) {
+  for (int64_t s0 = (int64_t)bi_.b * spb; s0 < a.Ne; s0 += (int64_t)bi_.g * spb) {
     // pass 1: gather x-lines of r_s and transform (forward, x)
     for (int ln = threadIdx.x; ln < lines; ln += blockDim.x) {
       const int64_t s = s0 + ln / M2;
@@ -203,13 +202,24 @@ __global__ void __launch_bounds__(256) k_fdm_m(FdmArgs<T> a) {
 }
 
 template <typename T, int M>
+__global__ void __launch_bounds__(256) k_fdm_m(FdmArgs<T> a) {
+  pdl_entry();
+  fdm_m_body<T, M>(plain_block(), a);
+}
+
+template <typename T, int M>
 cudaError_t launch_fdm_m(const FdmArgs<T>& a, int blocks, int threads, size_t /*smem*/, cudaStream_t s) {
   const size_t smem = FdmShape<T, M>::smem;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_fdm_m<T, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  launch_pdl(k_fdm_m<T, M>, blocks, threads, smem, s, a);
+  // grouped twin (batched solves) for the FP32 smoother only: the FP64 and
+  // double-float hierarchies are not batched by the serving path
+  if constexpr (std::is_same<T, float>::value)
+    launch_pdl<fdm_m_body<T, M>>(k_fdm_m<T, M>, blocks, threads, smem, s, a);
+  else
+    launch_pdl(k_fdm_m<T, M>, blocks, threads, smem, s, a);
   return cudaGetLastError();
 }
 

@@ -394,6 +394,68 @@ cudaError_t choose_fdm_kernels(mg_ctx* c) {
   return e;
 }
 
+// The first direction of the PCG iteration: z = B r projected to zero mean,
+// p = z, rz = r . z (and p in double-float for the outer operator).
+cudaError_t cg_start(const mg_ctx* c, double* r, double* z, double* p, df64* pdf) {
+  const int64_t N = c->lev[c->L].N;
+  cudaError_t e;
+  if ((e = precond(c, r, z)) != cudaSuccess) return e;
+  if ((e = launch_sum(c, z, N, kSlotSum)) != cudaSuccess) return e;
+  if ((e = launch_sub_mean(c, z, N, kSlotSum)) != cudaSuccess) return e;
+  if ((e = cudaMemcpyAsync(p, z, N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream)) != cudaSuccess) return e;
+  if ((e = launch_dot(c, r, z, N, kSlotRZ)) != cudaSuccess) return e;
+  if (pdf) e = launch_split_df64(c, p, pdf, N);
+  return e;
+}
+
+// First half of a PCG iteration: q = A p (in double-float when pdf is given),
+// alpha = rz / pq, x += alpha p, r -= alpha q, rr = |r - mean(r)|^2.  The mean
+// of r (zero up to rounding: 1^T q = 0) is taken out where r is used, not
+// stored.  Kernel launches only (no host synchronisation).
+cudaError_t cg_step_a(const mg_ctx* c, double* x, double* p, double* r, double* q, df64* pdf, df64* qdf) {
+  const int L = c->L;
+  const int64_t N = c->lev[L].N;
+  cudaError_t e;
+  if (pdf) {
+    {
+      ProfScope ps(c, kProfSipg, L);
+      if ((e = launch_sipg<df64>(c, L, pdf, nullptr, qdf, 0)) != cudaSuccess) return e;
+    }
+    if ((e = launch_dot_dfq(c, p, qdf, q, N, kSlotPQ)) != cudaSuccess) return e;
+  } else {
+    {
+      ProfScope ps(c, kProfSipg, L);
+      if ((e = launch_sipg<double>(c, L, p, nullptr, q, 0)) != cudaSuccess) return e;
+    }
+    if ((e = launch_dot(c, p, q, N, kSlotPQ)) != cudaSuccess) return e;
+  }
+  return launch_cg_update(c, x, p, r, q, N);
+}
+
+// Second half: z = B r projected; beta = z_new . (r_new - r_old) / (z_old . r_old)
+// = -alpha (z_new . q) / rz_old; p = z + beta p; rz = r . z.  Kernel launches only.
+cudaError_t cg_step_b(const mg_ctx* c, double* p, double* r, double* q, double* z, df64* pdf) {
+  const int L = c->L;
+  const int64_t N = c->lev[L].N;
+  cudaError_t e;
+  if (c->opts.precision == MG_MIXED) {
+    float* f32 = lvec<float>(c->lev[L].f);
+    float* u32 = lvec<float>(c->lev[L].u);
+    if ((e = launch_to_f32(c, r, f32, N, kSlotRR)) != cudaSuccess) return e;
+    if ((e = vcycle_t<float>(c, u32, f32, true, false)) != cudaSuccess) return e;
+    return launch_cg_direction<float>(c, p, u32, q, r, N, pdf);
+  }
+  if (c->opts.precision == MG_DF64) {
+    df64* fd = lvec<df64>(c->lev[L].f);
+    df64* ud = lvec<df64>(c->lev[L].u);
+    if ((e = launch_split_df64(c, r, fd, N)) != cudaSuccess) return e;
+    if ((e = vcycle_t<df64>(c, ud, fd, true, false)) != cudaSuccess) return e;
+    return launch_cg_direction<df64>(c, p, ud, q, r, N, pdf);
+  }
+  if ((e = vcycle_t<double>(c, z, r, true, false)) != cudaSuccess) return e;
+  return launch_cg_direction<double>(c, p, z, q, r, N);
+}
+
 mg_status solve_impl(mg_ctx* c, double* u, const double* f, double tol, int maxit, int use_cg, int* iters,
                      double* relres, double* history) {
   const int L = c->L;
@@ -460,35 +522,10 @@ mg_status solve_impl(mg_ctx* c, double* u, const double* f, double tol, int maxi
     const bool df = c->opts.outer_df64 && c->opts.precision != MG_FP64;
     df64* pdf = df ? static_cast<df64*>(c->ws.corr) : nullptr;
     df64* qdf = df ? pdf + N : nullptr;
-    if (!converged) {
-      CK(precond(c, r, z));
-      CK(launch_sum(c, z, N, kSlotSum));
-      CK(launch_sub_mean(c, z, N, kSlotSum));
-      CK(cudaMemcpyAsync(p, z, N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
-      CK(launch_dot(c, r, z, N, kSlotRZ));
-      if (df) CK(launch_split_df64(c, p, pdf, N));
-    }
+    if (!converged) CK(cg_start(c, r, z, p, pdf));
     while (!converged && it < maxit) {
       ++it;
-      // q = A p, alpha = rz / pq, x += alpha p, r -= alpha q, rr = |r - mean(r)|^2.  The mean of r
-      // (zero up to rounding: 1^T q = 0) is taken out where r is used, not stored.
-      CK(run_graph(c, kGraphCgA, x, f, [&]() -> cudaError_t {
-        cudaError_t e;
-        if (df) {
-          {
-            ProfScope ps(c, kProfSipg, L);
-            if ((e = launch_sipg<df64>(c, L, pdf, nullptr, qdf, 0)) != cudaSuccess) return e;
-          }
-          if ((e = launch_dot_dfq(c, p, qdf, q, N, kSlotPQ)) != cudaSuccess) return e;
-        } else {
-          {
-            ProfScope ps(c, kProfSipg, L);
-            if ((e = launch_sipg<double>(c, L, p, nullptr, q, 0)) != cudaSuccess) return e;
-          }
-          if ((e = launch_dot(c, p, q, N, kSlotPQ)) != cudaSuccess) return e;
-        }
-        return launch_cg_update(c, x, p, r, q, N);
-      }));
+      CK(run_graph(c, kGraphCgA, x, f, [&]() { return cg_step_a(c, x, p, r, q, pdf, qdf); }));
       double v = read_scalar(c, kSlotRR, &err);
       CK(err);
       rn = sqrt(v);
@@ -498,27 +535,7 @@ mg_status solve_impl(mg_ctx* c, double* u, const double* f, double tol, int maxi
         converged = true;
         break;
       }
-      // z = B r projected; beta = z_new . (r_new - r_old) / (z_old . r_old) = -alpha (z_new . q) / rz_old;
-      // p = z + beta p; rz = r . z (one pass for the five sums, one for p)
-      CK(run_graph(c, kGraphCgB, x, f, [&]() -> cudaError_t {
-        cudaError_t e;
-        if (c->opts.precision == MG_MIXED) {
-          float* f32 = lvec<float>(c->lev[L].f);
-          float* u32 = lvec<float>(c->lev[L].u);
-          if ((e = launch_to_f32(c, r, f32, N, kSlotRR)) != cudaSuccess) return e;
-          if ((e = vcycle_t<float>(c, u32, f32, true, false)) != cudaSuccess) return e;
-          return launch_cg_direction<float>(c, p, u32, q, r, N, pdf);
-        }
-        if (c->opts.precision == MG_DF64) {
-          df64* fd = lvec<df64>(c->lev[L].f);
-          df64* ud = lvec<df64>(c->lev[L].u);
-          if ((e = launch_split_df64(c, r, fd, N)) != cudaSuccess) return e;
-          if ((e = vcycle_t<df64>(c, ud, fd, true, false)) != cudaSuccess) return e;
-          return launch_cg_direction<df64>(c, p, ud, q, r, N, pdf);
-        }
-        if ((e = vcycle_t<double>(c, z, r, true, false)) != cudaSuccess) return e;
-        return launch_cg_direction<double>(c, p, z, q, r, N);
-      }));
+      CK(run_graph(c, kGraphCgB, x, f, [&]() { return cg_step_b(c, p, r, q, z, pdf); }));
     }
   }
   CK(launch_sum(c, u, N, kSlotSum));
@@ -530,6 +547,136 @@ mg_status solve_impl(mg_ctx* c, double* u, const double* f, double tol, int maxi
   if (waits != kDevOk) return fail(c, MG_ECUDA, "a tensor-core kernel gave up waiting for its MMAs");
   if (relres) *relres = r0 > 0.0 ? rn / r0 : 0.0;
   if (!converged) return fail(c, MG_ENOCONV, "maximum number of iterations reached");
+  return MG_OK;
+}
+
+// Batched MG-CG (mg_solve_batch).  Every problem's launches are recorded and
+// merged into grouped launches on the first problem's stream; host
+// synchronisation once per half iteration for all problems together.
+struct BatchMember {
+  mg_ctx* c;
+  double *x, *r, *z, *p, *q;
+  const double* f;
+  df64 *pdf, *qdf;
+  double r0 = 0.0, rn = 0.0;
+  int it = 0;
+  int status = MG_OK;
+  bool active = true;
+};
+
+// Record `step(member)` for every active member, then launch the merged sequence.
+template <typename F>
+cudaError_t batch_step(std::vector<BatchMember>& ms, cudaStream_t s, long long* launches, F step) {
+  std::vector<LaunchRecorder> seqs;
+  seqs.reserve(ms.size());
+  LaunchRecorder*& rec = launch_recorder();
+  for (auto& m : ms) {
+    if (!m.active) continue;
+    seqs.emplace_back();
+    rec = &seqs.back();
+    const cudaError_t e = step(m);
+    rec = nullptr;
+    if (e != cudaSuccess) return e;
+  }
+  if (seqs.empty()) return cudaSuccess;
+  return launch_merged(seqs, s, launches);
+}
+
+// Host copies of scalar slot `slot` of every active member (one gather
+// launch, one copy, one synchronisation).
+cudaError_t batch_read(std::vector<BatchMember>& ms, int slot, cudaStream_t s, std::vector<double>& out) {
+  const double* src[kMaxBatch];
+  int idx[kMaxBatch], n = 0;
+  for (int i = 0; i < (int)ms.size(); ++i)
+    if (ms[i].active) {
+      src[n] = ms[i].c->ws.scal + slot;
+      idx[n++] = i;
+    }
+  out.assign(ms.size(), 0.0);
+  if (n == 0) return cudaSuccess;
+  double* dst = ms[0].c->ws.scal + kSlotBatch;
+  double host[kMaxBatch];
+  cudaError_t e;
+  if ((e = launch_gather_scalars(src, n, dst, s)) != cudaSuccess) return e;
+  if ((e = cudaMemcpyAsync(host, dst, n * sizeof(double), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+  for (int k = 0; k < n; ++k) out[idx[k]] = host[k];
+  return cudaSuccess;
+}
+
+mg_status solve_batch_impl(std::vector<BatchMember>& ms, cudaStream_t s, double tol, int maxit, long long* launches,
+                           std::string* err) {
+  cudaError_t e;
+  std::vector<double> v;
+#define BCK(x)                                   \
+  do {                                           \
+    if ((e = (x)) != cudaSuccess) {              \
+      *err = cudaGetErrorString(e);              \
+      return MG_ECUDA;                           \
+    }                                            \
+  } while (0)
+  // r = f - A x projected to zero mean, |r|
+  BCK(batch_step(ms, s, launches, [&](BatchMember& m) -> cudaError_t {
+    const int64_t N = m.c->lev[m.c->L].N;
+    cudaError_t e2;
+    if ((e2 = launch_sipg<double>(m.c, m.c->L, m.x, m.f, m.r, 1)) != cudaSuccess) return e2;
+    if ((e2 = launch_sum(m.c, m.r, N, kSlotSum)) != cudaSuccess) return e2;
+    if ((e2 = launch_sub_mean(m.c, m.r, N, kSlotSum)) != cudaSuccess) return e2;
+    return launch_dot(m.c, m.r, m.r, N, kSlotRR);
+  }));
+  BCK(batch_read(ms, kSlotRR, s, v));
+  for (int i = 0; i < (int)ms.size(); ++i) {
+    BatchMember& m = ms[i];
+    m.r0 = m.rn = sqrt(v[i]);
+    if (!std::isfinite(m.r0)) {
+      m.status = MG_EINVAL;
+      m.active = false;
+    } else if (m.r0 == 0.0) {
+      m.active = false;
+    }
+  }
+  // The cudaMemcpyAsync of cg_start is not a kernel: the first direction runs per problem.
+  for (auto& m : ms)
+    if (m.active) BCK(cg_start(m.c, m.r, m.z, m.p, m.pdf));
+  for (int it = 1; it <= maxit; ++it) {
+    bool any = false;
+    for (auto& m : ms) any = any || m.active;
+    if (!any) break;
+    BCK(batch_step(ms, s, launches,
+                   [&](BatchMember& m) { return cg_step_a(m.c, m.x, m.p, m.r, m.q, m.pdf, m.qdf); }));
+    BCK(batch_read(ms, kSlotRR, s, v));
+    for (int i = 0; i < (int)ms.size(); ++i) {
+      BatchMember& m = ms[i];
+      if (!m.active) continue;
+      m.it = it;
+      m.rn = sqrt(v[i]);
+      if (!std::isfinite(m.rn)) {
+        m.status = MG_ENOCONV;
+        m.active = false;
+      } else if (m.rn <= tol * m.r0) {
+        m.active = false;
+      } else if (it == maxit) {
+        m.status = MG_ENOCONV;
+        m.active = false;
+      }
+    }
+    BCK(batch_step(ms, s, launches, [&](BatchMember& m) { return cg_step_b(m.c, m.p, m.r, m.q, m.z, m.pdf); }));
+  }
+  // zero-mean solutions and the tensor-core wait flags
+  for (auto& m : ms) m.active = true;
+  BCK(batch_step(ms, s, launches, [&](BatchMember& m) -> cudaError_t {
+    const int64_t N = m.c->lev[m.c->L].N;
+    cudaError_t e2;
+    if ((e2 = launch_sum(m.c, m.x, N, kSlotSum)) != cudaSuccess) return e2;
+    return launch_sub_mean(m.c, m.x, N, kSlotSum);
+  }));
+  std::vector<int> waits(ms.size(), 0);
+  for (int i = 0; i < (int)ms.size(); ++i)
+    BCK(cudaMemcpyAsync(&waits[i], ms[i].c->ws.status + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+  BCK(cudaStreamSynchronize(s));
+  for (int i = 0; i < (int)ms.size(); ++i)
+    if (waits[i] != kDevOk && ms[i].status == MG_OK) ms[i].status = MG_ECUDA;
+#undef BCK
   return MG_OK;
 }
 
@@ -946,6 +1093,54 @@ mg_status mg_get_table(mg_ctx* c, int level, int dir, int what, double* host_out
   CK(cudaMemcpyAsync(host_out, c->ws.tab64 + off, cnt * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   *count = (int)cnt;
+  return MG_OK;
+}
+
+mg_status mg_solve_batch(mg_ctx* const* ctxs, int count, double* const* u, const double* const* f, double tol,
+                         int maxit, int* iters, double* relres, int* status) {
+  if (!ctxs || !u || !f || count < 1 || count > kMaxBatch || !(tol > 0.0) || maxit < 1) return MG_EINVAL;
+  for (int i = 0; i < count; ++i) {
+    if (!ctxs[i] || !u[i] || !f[i]) return MG_EINVAL;
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == ctxs[i]) return fail(ctxs[0], MG_EINVAL, "a context appears twice in the batch");
+    if (!ctxs[i]->ready) return fail(ctxs[0], MG_ENOTREADY, "workspace not bound");
+  }
+  mg_ctx* c0 = ctxs[0];
+  const cudaStream_t s = c0->stream;
+  std::vector<BatchMember> ms(count);
+  std::vector<cudaStream_t> saved(count);
+  std::vector<bool> prof(count);
+  for (int i = 0; i < count; ++i) {
+    mg_ctx* c = ctxs[i];
+    const int64_t N = c->lev[c->L].N;
+    BatchMember& m = ms[i];
+    m.c = c;
+    m.x = u[i];
+    m.f = f[i];
+    m.r = c->ws.cg[1];
+    m.z = c->ws.cg[2];
+    m.p = c->ws.cg[3];
+    m.q = c->ws.cg[4];
+    const bool df = c->opts.outer_df64 && c->opts.precision != MG_FP64;
+    m.pdf = df ? static_cast<df64*>(c->ws.corr) : nullptr;
+    m.qdf = df ? m.pdf + N : nullptr;
+    saved[i] = c->stream;
+    prof[i] = c->prof_on;
+    c->stream = s;  // every launch of the batch goes to the first problem's stream
+    c->prof_on = false;
+  }
+  std::string err;
+  long long launches = 0;
+  const mg_status st = solve_batch_impl(ms, s, tol, maxit, &launches, &err);
+  for (int i = 0; i < count; ++i) {
+    ctxs[i]->stream = saved[i];
+    ctxs[i]->prof_on = prof[i];
+    if (iters) iters[i] = ms[i].it;
+    if (relres) relres[i] = ms[i].r0 > 0.0 ? ms[i].rn / ms[i].r0 : 0.0;
+    if (status) status[i] = st != MG_OK ? st : ms[i].status;
+  }
+  c0->batch_launches += launches;
+  if (st != MG_OK) return fail(c0, st, err);
   return MG_OK;
 }
 

@@ -4,8 +4,11 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
+#include <cuda/std/tuple>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/mgdg.h"
@@ -23,9 +26,61 @@ namespace mgdg {
 // kernel launched without the attribute passes the wait at once.
 __device__ __forceinline__ void pdl_entry() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
-template <typename... KArgs, typename... Args>
-inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
-                              Args&&... args) {
+// ---- batched execution: kernel bodies, grouped launches, launch recording ----
+//
+// A kernel body is a __device__ function that takes the block index and the
+// number of blocks it may assume (BlockIdx) in place of blockIdx.x and
+// gridDim.x.  Its plain kernel passes the real ones; its grouped twin
+// (k_grouped) runs the bodies of several independent problems in one launch:
+// the launch's blocks are split into consecutive ranges, one per problem,
+// each range running the body with that problem's parameters and its own
+// block numbering, exactly as the plain kernel would (same per-block work,
+// same reduction order, so the same bits).
+struct BlockIdx {
+  int b, g;  // block index, number of blocks
+};
+__device__ __forceinline__ BlockIdx plain_block() { return BlockIdx{(int)blockIdx.x, (int)gridDim.x}; }
+
+constexpr int kMaxBatch = 16;  // problems per grouped launch
+
+template <typename A>
+struct Grouped {
+  int count;
+  int start[kMaxBatch + 1];  // first block of each problem; start[count] = the launch's blocks
+  A a[kMaxBatch];            // each problem's kernel parameters
+};
+
+template <int LB, auto Body, typename... Ps>
+__global__ void __launch_bounds__(LB) k_grouped(const __grid_constant__ Grouped<cuda::std::tuple<Ps...>> g) {
+  pdl_entry();
+  int r = 0;
+  while (r + 1 < g.count && (int)blockIdx.x >= g.start[r + 1]) ++r;
+  const BlockIdx bi{(int)blockIdx.x - g.start[r], g.start[r + 1] - g.start[r]};
+  cuda::std::apply([&](const Ps&... ps) { Body(bi, ps...); }, g.a[r]);
+}
+
+// One recorded launch: the plain kernel (its identity), the launch shape, its
+// parameters packed as cuda::std::tuple<kernel parameter types...>, how to
+// replay it alone and (if the kernel has a body) how to launch the grouped
+// twin for several records of the same kernel.
+struct LaunchRec {
+  const void* key = nullptr;
+  dim3 grid, block;
+  size_t smem = 0;
+  std::vector<unsigned char> args;
+  cudaError_t (*plain)(const LaunchRec&, cudaStream_t) = nullptr;
+  cudaError_t (*grouped)(const LaunchRec* const*, int, cudaStream_t) = nullptr;
+};
+
+// While a host thread has a recorder installed, launch_pdl appends to it
+// instead of launching (batched execution, batch.cu).
+struct LaunchRecorder {
+  std::vector<LaunchRec> recs;
+};
+LaunchRecorder*& launch_recorder();
+
+inline cudaError_t launch_pdl_now(const void* kernel, dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                                  void** args) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = grid;
   cfg.blockDim = block;
@@ -36,7 +91,69 @@ inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, s
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kernel, static_cast<Args&&>(args)...);
+  return cudaLaunchKernelExC(&cfg, kernel, args);
+}
+
+template <typename... KArgs>
+cudaError_t launch_tuple(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                         cuda::std::tuple<KArgs...>& t) {
+  void* ptrs[sizeof...(KArgs) > 0 ? sizeof...(KArgs) : 1];
+  int i = 0;
+  cuda::std::apply([&](KArgs&... v) { ((ptrs[i++] = (void*)&v), ...); }, t);
+  return launch_pdl_now((const void*)kernel, grid, block, smem, s, ptrs);
+}
+
+template <typename... KArgs>
+cudaError_t replay_plain(const LaunchRec& r, cudaStream_t s) {
+  using Tup = cuda::std::tuple<KArgs...>;
+  Tup t;
+  memcpy((void*)&t, r.args.data(), sizeof(Tup));
+  return launch_tuple(reinterpret_cast<void (*)(KArgs...)>(const_cast<void*>(r.key)), r.grid, r.block, r.smem, s,
+                      t);
+}
+
+template <int LB, auto Body, typename... KArgs>
+cudaError_t launch_grouped(const LaunchRec* const* r, int n, cudaStream_t s) {
+  using Tup = cuda::std::tuple<KArgs...>;
+  Grouped<Tup> g;
+  g.count = n;
+  g.start[0] = 0;
+  for (int i = 0; i < n; ++i) {
+    memcpy((void*)&g.a[i], r[i]->args.data(), sizeof(Tup));
+    g.start[i + 1] = g.start[i] + (int)r[i]->grid.x;
+  }
+  auto* twin = k_grouped<LB, Body, KArgs...>;
+  if (r[0]->smem > 48 * 1024) {
+    const cudaError_t e = cudaFuncSetAttribute(twin, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)r[0]->smem);
+    if (e != cudaSuccess) return e;
+  }
+  void* ptrs[1] = {(void*)&g};
+  return launch_pdl_now((const void*)twin, dim3(g.start[n]), r[0]->block, r[0]->smem, s, ptrs);
+}
+
+// Launch `kernel` with programmatic dependent launch (or record it, see
+// LaunchRecorder).  Body (optional): the kernel's body, for a grouped twin
+// with launch bounds LB.
+template <auto Body = nullptr, int LB = 256, typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args&&... args) {
+  cuda::std::tuple<KArgs...> t(static_cast<KArgs>(args)...);
+  if (LaunchRecorder* rec = launch_recorder()) {
+    LaunchRec r;
+    r.key = (const void*)kernel;
+    r.grid = grid;
+    r.block = block;
+    r.smem = smem;
+    r.args.resize(sizeof(t));
+    memcpy(r.args.data(), (const void*)&t, sizeof(t));
+    r.plain = &replay_plain<KArgs...>;
+    if constexpr (!std::is_same<decltype(Body), std::nullptr_t>::value) {
+      if (grid.y == 1 && grid.z == 1) r.grouped = &launch_grouped<LB, Body, KArgs...>;
+    }
+    rec->recs.push_back(std::move(r));
+    return cudaSuccess;
+  }
+  return launch_tuple(kernel, grid, block, smem, s, t);
 }
 
 constexpr int kMaxLevels = 6;   // P <= 32
@@ -58,6 +175,7 @@ enum Slot : int {
   kSlotScale = 8,   // norm used to scale FP32 preconditioner input
   kSlotBeta = 9,    // CG beta
   kSlotMuZ = 10,    // mean of the preconditioned residual z
+  kSlotBatch = 16,  // 16 .. 16 + kMaxBatch - 1: scalars gathered from a batch's problems
   kSlotCoarse = 60, // coarse-solve mean
   kNumSlots = 64
 };
@@ -141,6 +259,7 @@ struct mg_ctx {
     cudaEvent_t a, b;
   };
   mutable long long nlaunch = 0;
+  long long batch_launches = 0;  // launches of batched solves led by this context
   // CUDA graphs of recurring launch sequences (V-cycle, CG steps), keyed by
   // kind and the two vector pointers they were captured with.
   struct GraphEntry {
@@ -163,6 +282,13 @@ namespace mgdg {
 // Kernel groups timed by the profiler (mg_profile_result kinds).
 enum ProfKind : int { kProfFdm = 0, kProfScatter, kProfSipg, kProfRestrict, kProfProlong, kProfCoarse, kProfVector,
                       kProfKinds };
+
+// ---- batched execution (batch.cu) ----
+// Launch the recorded sequences of several problems on stream s, merged into
+// grouped launches; *launches += the number of launches made.
+cudaError_t launch_merged(const std::vector<LaunchRecorder>& seqs, cudaStream_t s, long long* launches);
+// out[i] = *src[i] (device scalars of up to kMaxBatch problems), one launch.
+cudaError_t launch_gather_scalars(const double* const* src, int n, double* out, cudaStream_t s);
 
 // ---- setup (setup.cu) ----
 cudaError_t launch_setup(mg_ctx* c);

@@ -84,8 +84,7 @@ __device__ __forceinline__ void bwd_eo(const T* v, const T* __restrict__ SW, int
 // The six 1D factors are staged in shared memory when they fit, else read
 // through the cache from the table array.
 template <typename T>
-__global__ void __launch_bounds__(256) k_fdm(FdmArgs<T> a) {
-  pdl_entry();
+__device__ __forceinline__ void fdm_body(BlockIdx bi_, FdmArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   T* sm = reinterpret_cast<T*>(smraw);
   const int mx = a.md[0], my = a.md[1], mz = a.md[2], mxy = mx * my, mxyz = mxy * mz;
@@ -113,7 +112,7 @@ __global__ void __launch_bounds__(256) k_fdm(FdmArgs<T> a) {
   }
   const T* __restrict__ dinv = a.tab + a.dinv;
   T x[kMaxM], v[kMaxM];
-  for (int64_t s = blockIdx.x; s < a.Ne; s += gridDim.x) {
+  for (int64_t s = bi_.b; s < a.Ne; s += bi_.g) {
     const int s32 = (int)s, sxy = s32 / a.nx;
     const int sx = s32 - sxy * a.nx, sy = sxy % a.ny, sz = sxy / a.ny;
     T* tile = a.corr + s * (int64_t)mxyz;
@@ -170,20 +169,25 @@ __global__ void __launch_bounds__(256) k_fdm(FdmArgs<T> a) {
   }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(256) k_fdm(FdmArgs<T> a) {
+  pdl_entry();
+  fdm_body<T>(plain_block(), a);
+}
+
 // Subdomain geometry of the scatter: widths and layers per direction.
 struct SubShape {
   int mx, my, mz, nox, noy, noz;
 };
 
 template <typename T>
-__global__ void k_scatter(const T* __restrict__ corr, T* __restrict__ u, int64_t Ne, int nx, int ny, int nz, int n,
-                          SubShape g, int accumulate) {
-  pdl_entry();
+__device__ __forceinline__ void scatter_body(BlockIdx bi_, const T* __restrict__ corr, T* __restrict__ u, int64_t Ne,
+                                             int nx, int ny, int nz, int n, SubShape g, int accumulate) {
   const int n3 = n * n * n;
   const int64_t mxyz = (int64_t)g.mx * g.my * g.mz;
   const int64_t total = Ne * n3;
-  for (int64_t dof = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; dof < total;
-       dof += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t dof = bi_.b * (int64_t)blockDim.x + threadIdx.x; dof < total;
+       dof += (int64_t)bi_.g * blockDim.x) {
     const int e = (int)(dof / n3);
     const int loc = (int)(dof - (int64_t)e * n3);
     const int i = loc % n, j = (loc / n) % n, k = loc / (n * n);
@@ -215,18 +219,24 @@ __global__ void k_scatter(const T* __restrict__ corr, T* __restrict__ u, int64_t
   }
 }
 
+template <typename T>
+__global__ void k_scatter(const T* __restrict__ corr, T* __restrict__ u, int64_t Ne, int nx, int ny, int nz, int n,
+                          SubShape g, int accumulate) {
+  pdl_entry();
+  scatter_body<T>(plain_block(), corr, u, Ne, nx, ny, nz, n, g, accumulate);
+}
+
 // Same sum as k_scatter with compile-time n: one thread per DOF, the 27
 // possible covering subdomains visited in the same fixed order (-1, 0, +1 per
 // direction, x fastest) with predicates instead of per-DOF lists.
 template <typename T, int N>
-__global__ void __launch_bounds__(256) k_scatter_n(const T* __restrict__ corr, T* __restrict__ u, int64_t Ne, int nx,
-                                                   int ny, int nz, SubShape g, int accumulate) {
-  pdl_entry();
+__device__ __forceinline__ void scatter_n_body(BlockIdx bi_, const T* __restrict__ corr, T* __restrict__ u,
+                                               int64_t Ne, int nx, int ny, int nz, SubShape g, int accumulate) {
   constexpr int N3 = N * N * N;
   const int64_t mxyz = (int64_t)g.mx * g.my * g.mz;
   const int64_t total = Ne * N3;
-  for (int64_t dof = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; dof < total;
-       dof += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t dof = bi_.b * (int64_t)blockDim.x + threadIdx.x; dof < total;
+       dof += (int64_t)bi_.g * blockDim.x) {
     const int e = (int)(dof / N3);  // element indices fit in 32 bits
     const int loc = (int)(dof - (int64_t)e * N3);
     const int i = loc % N, j = (loc / N) % N, k = loc / (N * N);
@@ -262,20 +272,26 @@ __global__ void __launch_bounds__(256) k_scatter_n(const T* __restrict__ corr, T
   }
 }
 
+template <typename T, int N>
+__global__ void __launch_bounds__(256) k_scatter_n(const T* __restrict__ corr, T* __restrict__ u, int64_t Ne, int nx,
+                                                   int ny, int nz, SubShape g, int accumulate) {
+  pdl_entry();
+  scatter_n_body<T, N>(plain_block(), corr, u, Ne, nx, ny, nz, g, accumulate);
+}
+
 // k_scatter_n when every node lies in at most two subdomains per direction
 // (2 N_O <= n): the two candidates of each direction in increasing offset,
 // all eight loads issued unconditionally (an absent candidate repeats the own
 // address and its value is replaced by zero), then summed in the same order
 // as k_scatter_n, so the two kernels give identical bits.
 template <typename T, int N>
-__global__ void __launch_bounds__(256) k_scatter_n2(const T* __restrict__ corr, T* __restrict__ u, int64_t Ne,
+__device__ __forceinline__ void scatter_n2_body(BlockIdx bi_, const T* __restrict__ corr, T* __restrict__ u, int64_t Ne,
                                                     int nx, int ny, int nz, SubShape g, int accumulate) {
-  pdl_entry();
   constexpr int N3 = N * N * N;
   const int64_t mxyz = (int64_t)g.mx * g.my * g.mz;
   const int64_t total = Ne * N3;
-  for (int64_t dof = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; dof < total;
-       dof += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t dof = bi_.b * (int64_t)blockDim.x + threadIdx.x; dof < total;
+       dof += (int64_t)bi_.g * blockDim.x) {
     const int e = (int)(dof / N3);  // element indices fit in 32 bits
     const int loc = (int)(dof - (int64_t)e * N3);
     const int i = loc % N, j = (loc / N) % N, k = loc / (N * N);
@@ -325,6 +341,13 @@ __global__ void __launch_bounds__(256) k_scatter_n2(const T* __restrict__ corr, 
           if ((a == 0 || vx) && (b == 0 || vy) && (c == 0 || vz)) sum += val[a + 2 * (b + 2 * c)];
     u[dof] = accumulate ? u[dof] + sum : sum;
   }
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(256) k_scatter_n2(const T* __restrict__ corr, T* __restrict__ u, int64_t Ne,
+                                                    int nx, int ny, int nz, SubShape g, int accumulate) {
+  pdl_entry();
+  scatter_n2_body<T, N>(plain_block(), corr, u, Ne, nx, ny, nz, g, accumulate);
 }
 
 template <typename T>
@@ -406,7 +429,7 @@ cudaError_t launch_fdm(const mg_ctx* c, int l, const T* r) {
   const int lines = std::max(lv.m[1] * lv.m[2], std::max(lv.m[0] * lv.m[2], lv.m[0] * lv.m[1]));
   int threads = lines >= 256 ? 256 : 128;
   int64_t blocks = c->Ne < 152 * 8 ? c->Ne : 152 * 8;
-  launch_pdl(k_fdm<T>, (int)blocks, threads, smem, c->stream, a);
+  launch_pdl<fdm_body<T>>(k_fdm<T>, (int)blocks, threads, smem, c->stream, a);
   c->nlaunch += 1;
   return cudaGetLastError();
 }
@@ -424,19 +447,19 @@ cudaError_t launch_scatter(const mg_ctx* c, int l, T* u, int accumulate) {
   const bool two = 2 * lv.no[0] <= lv.n && 2 * lv.no[1] <= lv.n && 2 * lv.no[2] <= lv.n;
   if (two) {
     switch (lv.n) {
-#define MGDG_SC2(N) case N: launch_pdl(k_scatter_n2<T, N>, eb, 256, 0, c->stream, corr, u, c->Ne, c->ne[0], c->ne[1], c->ne[2], g, accumulate); return cudaGetLastError();
+#define MGDG_SC2(N) case N: launch_pdl<scatter_n2_body<T, N>>(k_scatter_n2<T, N>, eb, 256, 0, c->stream, corr, u, c->Ne, c->ne[0], c->ne[1], c->ne[2], g, accumulate); return cudaGetLastError();
       MGDG_SC2(3) MGDG_SC2(5) MGDG_SC2(9) MGDG_SC2(17) MGDG_SC2(33)
 #undef MGDG_SC2
       default: break;
     }
   }
   switch (lv.n) {
-#define MGDG_SC(N) case N: launch_pdl(k_scatter_n<T, N>, eb, 256, 0, c->stream, corr, u, c->Ne, c->ne[0], c->ne[1], c->ne[2], g, accumulate); return cudaGetLastError();
+#define MGDG_SC(N) case N: launch_pdl<scatter_n_body<T, N>>(k_scatter_n<T, N>, eb, 256, 0, c->stream, corr, u, c->Ne, c->ne[0], c->ne[1], c->ne[2], g, accumulate); return cudaGetLastError();
     MGDG_SC(3) MGDG_SC(5) MGDG_SC(9) MGDG_SC(17) MGDG_SC(33)
 #undef MGDG_SC
     default: break;
   }
-  launch_pdl(k_scatter<T>, (int)blocks, 256, 0, c->stream, corr, u, c->Ne, c->ne[0], c->ne[1], c->ne[2], lv.n, g,
+  launch_pdl<scatter_body<T>>(k_scatter<T>, (int)blocks, 256, 0, c->stream, corr, u, c->Ne, c->ne[0], c->ne[1], c->ne[2], lv.n, g,
                                                     accumulate);
   return cudaGetLastError();
 }

@@ -20,7 +20,10 @@
 // the element, accumulated in the output vector; the last pass applies the
 // mass and forms f - A u.  The kernels are templates on the arithmetic type:
 // FP64, FP32 (the multigrid of the mixed solve) or double-float pairs
-// (df64.cuh; the outer operator of the mixed solve on request).
+// (df64.cuh; the outer operator of the mixed solve on request).  Included by
+// sipg_f64.cu, sipg_f32.cu and sipg_df64.cu, one arithmetic type each.
+#pragma once
+
 #include "mg_internal.h"
 
 namespace mgdg {
@@ -227,12 +230,11 @@ __device__ __forceinline__ void line_apply_n(const OpArgs<T>& a, int d, const T*
 }
 
 template <typename T, int N>
-__global__ void __launch_bounds__(256) k_sipg_n(OpArgs<T> a) {
-  pdl_entry();
+__device__ __forceinline__ void sipg_n_body(BlockIdx bi, OpArgs<T> a) {
   constexpr int n2 = N * N, n3 = n2 * N;
   const int lines = a.epb * n2;
   const T* m3 = a.tab + a.mass3;
-  for (int64_t e0 = (int64_t)blockIdx.x * a.epb; e0 < a.Ne; e0 += (int64_t)gridDim.x * a.epb) {
+  for (int64_t e0 = (int64_t)bi.b * a.epb; e0 < a.Ne; e0 += (int64_t)bi.g * a.epb) {
 #pragma unroll 1
     for (int dir = 0; dir < 3; ++dir) {
       for (int ln = threadIdx.x; ln < lines; ln += blockDim.x) {
@@ -268,16 +270,21 @@ __global__ void __launch_bounds__(256) k_sipg_n(OpArgs<T> a) {
   }
 }
 
+template <typename T, int N>
+__global__ void __launch_bounds__(256) k_sipg_n(OpArgs<T> a) {
+  pdl_entry();
+  sipg_n_body<T, N>(plain_block(), a);
+}
+
 // Direction-split variant for meshes with few elements: one launch per
 // direction, each element's lines (times NP threads per line) spread over
 // `chunks` blocks.
 template <typename T, int N, int NP>
-__global__ void __launch_bounds__(256) k_sipg_dir(OpArgs<T> a, int dir, int chunks) {
-  pdl_entry();
+__device__ __forceinline__ void sipg_dir_body(BlockIdx blk, OpArgs<T> a, int dir, int chunks) {
   constexpr int n2 = N * N, n3 = n2 * N;
   const T* m3 = a.tab + a.mass3;
   const int64_t nblk = a.Ne * chunks;
-  for (int64_t bi = blockIdx.x; bi < nblk; bi += gridDim.x) {
+  for (int64_t bi = blk.b; bi < nblk; bi += blk.g) {
     const int64_t e = bi / chunks;
     const int lt = (int)(bi % chunks) * blockDim.x + threadIdx.x;
     if (lt >= n2 * NP) continue;
@@ -309,6 +316,12 @@ __global__ void __launch_bounds__(256) k_sipg_dir(OpArgs<T> a, int dir, int chun
   }
 }
 
+template <typename T, int N, int NP>
+__global__ void __launch_bounds__(256) k_sipg_dir(OpArgs<T> a, int dir, int chunks) {
+  pdl_entry();
+  sipg_dir_body<T, N, NP>(plain_block(), a, dir, chunks);
+}
+
 template <typename T, int N>
 cudaError_t launch_sipg_n(const mg_ctx* c, OpArgs<T>& a) {
   constexpr int n2 = N * N;
@@ -323,7 +336,7 @@ cudaError_t launch_sipg_n(const mg_ctx* c, OpArgs<T>& a) {
       const int64_t nblk = c->Ne * chunks;
       const int blocks = (int)(nblk < 152 * 16 ? nblk : 152 * 16);
       for (int dir = 0; dir < 3; ++dir) {
-        launch_pdl(k_sipg_dir<T, N, NP>, blocks, threads, 0, c->stream, a, dir, chunks);
+        launch_pdl<sipg_dir_body<T, N, NP>>(k_sipg_dir<T, N, NP>, blocks, threads, 0, c->stream, a, dir, chunks);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
       }
@@ -337,7 +350,7 @@ cudaError_t launch_sipg_n(const mg_ctx* c, OpArgs<T>& a) {
   if (threads > 256) threads = 256;
   int64_t groups = (c->Ne + a.epb - 1) / a.epb;
   int64_t blocks = groups < 152 * 16 ? groups : 152 * 16;
-  launch_pdl(k_sipg_n<T, N>, (int)blocks, threads, 0, c->stream, a);
+  launch_pdl<sipg_n_body<T, N>>(k_sipg_n<T, N>, (int)blocks, threads, 0, c->stream, a);
   c->nlaunch += 1;
   return cudaGetLastError();
 }
@@ -397,9 +410,5 @@ cudaError_t launch_sipg(const mg_ctx* c, int l, const T* u, const T* f, T* out, 
   launch_pdl(k_sipg<T>, (int)blocks, threads, 0, c->stream, a);
   return cudaGetLastError();
 }
-
-template cudaError_t launch_sipg<double>(const mg_ctx*, int, const double*, const double*, double*, int);
-template cudaError_t launch_sipg<float>(const mg_ctx*, int, const float*, const float*, float*, int);
-template cudaError_t launch_sipg<df64>(const mg_ctx*, int, const df64*, const df64*, df64*, int);
 
 }  // namespace mgdg

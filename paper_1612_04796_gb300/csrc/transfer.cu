@@ -16,16 +16,15 @@ namespace {
 // per-element tensor with extents (d0, d1, d2), x fastest.
 // Mat(o, t) = transpose ? J[t * ldj + o] : J[o * ldj + t].
 template <typename T>
-__global__ void k_contract_axis(const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ J, int64_t Ne,
+__device__ __forceinline__ void contract_axis_body(BlockIdx bi_, const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ J, int64_t Ne,
                                 int d0, int d1, int d2, int axis, int nout, int ldj, int transpose, int accumulate) {
-  pdl_entry();
   int o0 = d0, o1 = d1, o2 = d2;
   if (axis == 0) o0 = nout; else if (axis == 1) o1 = nout; else o2 = nout;
   const int64_t in_sz = (int64_t)d0 * d1 * d2, out_sz = (int64_t)o0 * o1 * o2;
   const int64_t total = Ne * out_sz;
   const int nin = axis == 0 ? d0 : (axis == 1 ? d1 : d2);
-  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
-       idx += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t idx = bi_.b * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)bi_.g * blockDim.x) {
     const int64_t e = idx / out_sz;
     const int loc = (int)(idx - e * out_sz);
     const int a = loc % o0, b = (loc / o0) % o1, c = loc / (o0 * o1);
@@ -44,6 +43,13 @@ __global__ void k_contract_axis(const T* __restrict__ in, T* __restrict__ out, c
 }
 
 template <typename T>
+__global__ void k_contract_axis(const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ J, int64_t Ne,
+                                int d0, int d1, int d2, int axis, int nout, int ldj, int transpose, int accumulate) {
+  pdl_entry();
+  contract_axis_body<T>(plain_block(), in, out, J, Ne, d0, d1, d2, axis, nout, ldj, transpose, accumulate);
+}
+
+template <typename T>
 cudaError_t contract(const mg_ctx* c, const T* in, T* out, const T* J, int d0, int d1, int d2, int axis, int nout,
                      int ldj, int transpose, int accumulate) {
   int o0 = d0, o1 = d1, o2 = d2;
@@ -51,7 +57,7 @@ cudaError_t contract(const mg_ctx* c, const T* in, T* out, const T* J, int d0, i
   int64_t total = c->Ne * (int64_t)o0 * o1 * o2;
   int64_t blocks = (total + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;
-  launch_pdl(k_contract_axis<T>, (int)blocks, 256, 0, c->stream, in, out, J, c->Ne, d0, d1, d2, axis, nout, ldj, transpose,
+  launch_pdl<contract_axis_body<T>>(k_contract_axis<T>, (int)blocks, 256, 0, c->stream, in, out, J, c->Ne, d0, d1, d2, axis, nout, ldj, transpose,
                                                          accumulate);
   c->nlaunch += 1;
   return cudaGetLastError();
@@ -108,15 +114,14 @@ __device__ void cs_split(Get get, T* AE, T* AO) {
 // Fused prolongation u_f += (J (x) J (x) J) u_c, one element per block pass,
 // intermediates in shared memory.
 template <typename T, int NF, int NC>
-__global__ void __launch_bounds__(128) k_prolong_fused(const T* __restrict__ uc, T* __restrict__ uf,
+__device__ __forceinline__ void prolong_fused_body(BlockIdx bi_, const T* __restrict__ uc, T* __restrict__ uf,
                                                        const T* __restrict__ J, int64_t Ne) {
-  pdl_entry();
   constexpr int nei = (NC + 1) / 2, neo = (NF + 1) / 2;
   __shared__ T sE[neo * nei], sO[(NF / 2) * (NC / 2) + 1];
   __shared__ T sB[NF * NC * NC], sC[NF * NF * NC];
   cs_split<T, NF, NC>([&](int o, int t) { return J[o * NC + t]; }, sE, sO);
   __syncthreads();
-  for (int64_t e = blockIdx.x; e < Ne; e += gridDim.x) {
+  for (int64_t e = bi_.b; e < Ne; e += bi_.g) {
     const T* x0 = uc + e * (NC * NC * NC);
     for (int ln = threadIdx.x; ln < NC * NC; ln += blockDim.x) {  // x: (j,k) lines
       T x[NC], y[NF];
@@ -150,17 +155,23 @@ __global__ void __launch_bounds__(128) k_prolong_fused(const T* __restrict__ uc,
   }
 }
 
+template <typename T, int NF, int NC>
+__global__ void __launch_bounds__(128) k_prolong_fused(const T* __restrict__ uc, T* __restrict__ uf,
+                                                       const T* __restrict__ J, int64_t Ne) {
+  pdl_entry();
+  prolong_fused_body<T, NF, NC>(plain_block(), uc, uf, J, Ne);
+}
+
 // Fused restriction f_c = (J^T (x) J^T (x) J^T) r_f per element.
 template <typename T, int NF, int NC>
-__global__ void __launch_bounds__(128) k_restrict_fused(const T* __restrict__ rf, T* __restrict__ fc,
+__device__ __forceinline__ void restrict_fused_body(BlockIdx bi_, const T* __restrict__ rf, T* __restrict__ fc,
                                                         const T* __restrict__ J, int64_t Ne) {
-  pdl_entry();
   constexpr int nei = (NF + 1) / 2, neo = (NC + 1) / 2;
   __shared__ T sE[neo * nei], sO[(NC / 2) * (NF / 2) + 1];
   __shared__ T sB[NF * NC * NC], sC[NF * NF * NC];
   cs_split<T, NC, NF>([&](int o, int t) { return J[t * NC + o]; }, sE, sO);
   __syncthreads();
-  for (int64_t e = blockIdx.x; e < Ne; e += gridDim.x) {
+  for (int64_t e = bi_.b; e < Ne; e += bi_.g) {
     const T* x0 = rf + e * (NF * NF * NF);
     for (int ln = threadIdx.x; ln < NF * NF; ln += blockDim.x) {  // z: (a,b) lines
       T x[NF], y[NC];
@@ -194,6 +205,13 @@ __global__ void __launch_bounds__(128) k_restrict_fused(const T* __restrict__ rf
   }
 }
 
+template <typename T, int NF, int NC>
+__global__ void __launch_bounds__(128) k_restrict_fused(const T* __restrict__ rf, T* __restrict__ fc,
+                                                        const T* __restrict__ J, int64_t Ne) {
+  pdl_entry();
+  restrict_fused_body<T, NF, NC>(plain_block(), rf, fc, J, Ne);
+}
+
 template <typename T>
 const T* table_of(const mg_ctx* c);
 template <>
@@ -213,10 +231,10 @@ cudaError_t launch_restrict(const mg_ctx* c, int l, const T* r_fine, T* f_coarse
   const T* J = table_of<T>(c) + c->lev[l].J;
   const int nb = fused_blocks(c->Ne);
   switch (nf) {
-    case 3: launch_pdl(k_restrict_fused<T, 3, 2>, nb, 128, 0, c->stream, r_fine, f_coarse, J, c->Ne); c->nlaunch += 1; return cudaGetLastError();
-    case 5: launch_pdl(k_restrict_fused<T, 5, 3>, nb, 128, 0, c->stream, r_fine, f_coarse, J, c->Ne); c->nlaunch += 1; return cudaGetLastError();
-    case 9: launch_pdl(k_restrict_fused<T, 9, 5>, nb, 128, 0, c->stream, r_fine, f_coarse, J, c->Ne); c->nlaunch += 1; return cudaGetLastError();
-    case 17: launch_pdl(k_restrict_fused<T, 17, 9>, nb, 128, 0, c->stream, r_fine, f_coarse, J, c->Ne); c->nlaunch += 1; return cudaGetLastError();
+    case 3: launch_pdl<restrict_fused_body<T, 3, 2>, 128>(k_restrict_fused<T, 3, 2>, nb, 128, 0, c->stream, r_fine, f_coarse, J, c->Ne); c->nlaunch += 1; return cudaGetLastError();
+    case 5: launch_pdl<restrict_fused_body<T, 5, 3>, 128>(k_restrict_fused<T, 5, 3>, nb, 128, 0, c->stream, r_fine, f_coarse, J, c->Ne); c->nlaunch += 1; return cudaGetLastError();
+    case 9: launch_pdl<restrict_fused_body<T, 9, 5>, 128>(k_restrict_fused<T, 9, 5>, nb, 128, 0, c->stream, r_fine, f_coarse, J, c->Ne); c->nlaunch += 1; return cudaGetLastError();
+    case 17: launch_pdl<restrict_fused_body<T, 17, 9>, 128>(k_restrict_fused<T, 17, 9>, nb, 128, 0, c->stream, r_fine, f_coarse, J, c->Ne); c->nlaunch += 1; return cudaGetLastError();
     default: break;
   }
   T* t1 = static_cast<T*>(c->ws.corr);
@@ -234,10 +252,10 @@ cudaError_t launch_prolong(const mg_ctx* c, int l, const T* u_coarse, T* u_fine)
   const T* J = table_of<T>(c) + c->lev[l].J;
   const int nb = fused_blocks(c->Ne);
   switch (nf) {
-    case 3: launch_pdl(k_prolong_fused<T, 3, 2>, nb, 128, 0, c->stream, u_coarse, u_fine, J, c->Ne); c->nlaunch += 1; return cudaGetLastError();
-    case 5: launch_pdl(k_prolong_fused<T, 5, 3>, nb, 128, 0, c->stream, u_coarse, u_fine, J, c->Ne); c->nlaunch += 1; return cudaGetLastError();
-    case 9: launch_pdl(k_prolong_fused<T, 9, 5>, nb, 128, 0, c->stream, u_coarse, u_fine, J, c->Ne); c->nlaunch += 1; return cudaGetLastError();
-    case 17: launch_pdl(k_prolong_fused<T, 17, 9>, nb, 128, 0, c->stream, u_coarse, u_fine, J, c->Ne); c->nlaunch += 1; return cudaGetLastError();
+    case 3: launch_pdl<prolong_fused_body<T, 3, 2>, 128>(k_prolong_fused<T, 3, 2>, nb, 128, 0, c->stream, u_coarse, u_fine, J, c->Ne); c->nlaunch += 1; return cudaGetLastError();
+    case 5: launch_pdl<prolong_fused_body<T, 5, 3>, 128>(k_prolong_fused<T, 5, 3>, nb, 128, 0, c->stream, u_coarse, u_fine, J, c->Ne); c->nlaunch += 1; return cudaGetLastError();
+    case 9: launch_pdl<prolong_fused_body<T, 9, 5>, 128>(k_prolong_fused<T, 9, 5>, nb, 128, 0, c->stream, u_coarse, u_fine, J, c->Ne); c->nlaunch += 1; return cudaGetLastError();
+    case 17: launch_pdl<prolong_fused_body<T, 17, 9>, 128>(k_prolong_fused<T, 17, 9>, nb, 128, 0, c->stream, u_coarse, u_fine, J, c->Ne); c->nlaunch += 1; return cudaGetLastError();
     default: break;
   }
   T* t1 = static_cast<T*>(c->ws.corr);

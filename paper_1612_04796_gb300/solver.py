@@ -270,3 +270,29 @@ class MGSolver:
         self._check(self.lib.mg_get_table(self.ctx, int(level), int(direction), int(what),
                                           buf.ctypes.data_as(ctypes.c_void_p), cap, ctypes.byref(cnt)))
         return buf[:cnt.value].copy()
+
+
+def solve_batch(solvers, fs, us=None, tol=1e-10, maxit=200):
+    """mg_solve_batch: MG-CG solves of several problems (one MGSolver each,
+    distinct) advanced together, every sweep one launch for all of them, on
+    the first solver's stream.  Returns (us, iterations, relative residuals,
+    statuses), one entry per problem; raises only for argument or CUDA
+    errors (per-problem outcomes are in the statuses, 0 = converged)."""
+    n = len(solvers)
+    if n != len(fs):
+        raise ValueError("one right-hand side per solver")
+    for s, f in zip(solvers, fs):
+        s._vec(f, s.L, name="f")
+    us = [s.zeros() for s in solvers] if us is None else [s._vec(u, s.L, name="u") for s, u in zip(solvers, us)]
+    P = ctypes.c_void_p
+    ctxs = (P * n)(*[s.ctx for s in solvers])
+    up = (P * n)(*[_ptr(u) for u in us])
+    fp = (P * n)(*[_ptr(f) for f in fs])
+    its = (ctypes.c_int * n)()
+    rel = (ctypes.c_double * n)()
+    st = (ctypes.c_int * n)()
+    lib = solvers[0].lib
+    solvers[0]._check(lib.mg_solve_batch(ctypes.cast(ctxs, P), n, ctypes.cast(up, P), ctypes.cast(fp, P),
+                                         float(tol), int(maxit), ctypes.cast(its, P), ctypes.cast(rel, P),
+                                         ctypes.cast(st, P)))
+    return us, list(its), list(rel), list(st)
