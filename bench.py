@@ -78,7 +78,15 @@ WORKLOADS["serving512"] = dict(workload="serving stream: 512 solve requests, Poi
                                 "double-float), tol 1e-10, "
                                 "admitted by HBM footprint (smallest work first with aging; MG_SERVING_POLICY=fcfs "
                                 "for first come first served), "
-                                "one context and stream per slot")
+                                "one context and stream per slot; requests of <= 2^20 DOFs and one order admitted "
+                                "together are solved as one batch (MG_SERVING_BATCH=1: no batching)")
+WORKLOADS["batch16_p4"] = dict(workload="16 independent small problems solved together (mg_solve_batch: one launch per "
+                                         "sweep for all): periodic boxes [0,AR]x[0,1]x[0,1], AR ~ U[1,8], n^3 elements "
+                                         "with n in {4,5,6,7,8} (seed 7), P=4, N_O=1, Gaussian f, FP32 V(1,1) in FP64 "
+                                         "PCG (outer A p in double-float), tol 1e-10; compared with the same 16 solves "
+                                         "one after another (mg_solve each)",
+                                problems=16, P=4, sizes=[4, 5, 6, 7, 8], aspect=[1.0, 8.0], seed=7,
+                                overlap_layers=1, precision="mixed", use_cg=True)
 FP32_FLOP_PER_CLK_PER_SM = 256    # 128 FP32 FMA lanes per SM
 
 # bounded sample of the workload for the CPU oracle (same P, overlap, tol; smaller mesh)
@@ -563,6 +571,76 @@ def run_workload(args):
     print(json.dumps(line), flush=True)
 
 
+def run_batch(args):
+    """Many small problems: DOF/s of solving all of them with one batched
+    call (every sweep one grouped launch) against the same solves made one
+    after another on the same stream."""
+    import torch
+
+    import paper_1612_04796_gb300 as pkg
+    from paper_1612_04796_gb300 import inputs
+
+    W = dict(WORKLOADS[args.workload])
+    dev = torch.device("cuda", torch.cuda.current_device())
+    pkg.load_library()
+    rng = np.random.default_rng(W["seed"])
+    probs = []
+    for i in range(W["problems"]):
+        n = int(rng.choice(W["sizes"]))
+        ar = float(rng.uniform(*W["aspect"]))
+        s = pkg.MGSolver((ar, 1.0, 1.0), (n, n, n), W["P"], overlap=W["overlap_layers"], precision=W["precision"],
+                         device=dev, outer_df64=True)
+        b = s.rhs(torch.tensor(inputs.gaussian(s.num_dofs(), W["seed"] * 1000 + i), device=dev))
+        probs.append((s, b, torch.zeros(s.num_dofs(), dtype=torch.float64, device=dev)))
+    dofs = sum(s.num_dofs() for s, _, _ in probs)
+    solvers = [p[0] for p in probs]
+    stream = torch.cuda.current_stream(dev)
+
+    def run(batched, k):
+        ms, its = [], None
+        for _ in range(k):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            e0.record(stream)
+            for _, _, u in probs:
+                u.zero_()
+            if batched:
+                _, its, _, sts = pkg.solve_batch(solvers, [b for _, b, _ in probs], [u for _, _, u in probs],
+                                                 tol=1e-10, maxit=200)
+                assert all(v == 0 for v in sts), sts
+            else:
+                its = [s.solve(b, u, tol=1e-10, maxit=200, use_cg=True)[1] for s, b, u in probs]
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(max(e0.elapsed_time(e1), (time.perf_counter() - t0) * 1e3))
+        return ms, its
+
+    run(True, args.warmup)
+    run(False, args.warmup)
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    ms_b, its_b = run(True, args.steps)
+    ms_s, its_s = run(False, args.steps)
+    clock_info = clocks.stop()
+    assert its_b == its_s
+    u_b = [u.clone() for _, _, u in probs]
+    run(False, 1)
+    identical = all(torch.equal(a, u) for a, (_, _, u) in zip(u_b, probs))
+    tb, ts = statistics.median(ms_b), statistics.median(ms_s)
+    line = {
+        "metric": METRIC, "value": dofs / (tb / 1e3), "unit": "DOF/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": tb, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 multigrid / f64 outer", "data": "synthetic",
+        "config": dict(W, name=args.workload, total_dofs=dofs, dofs_each=[s.num_dofs() for s in solvers],
+                       iterations=its_b, l2="inputs L2-resident (small problems; the point is launch overhead)"),
+        "one_by_one": {"value": dofs / (ts / 1e3), "ms_per_step": ts},
+        "speedup_vs_one_by_one": ts / tb, "bitwise_identical_to_one_by_one": identical, "clocks": clock_info,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_serving(args):
     """The serving stream: throughput (DOFs solved / makespan) and per-request
     latency (arrival to result on the host) percentiles."""
@@ -574,7 +652,8 @@ def run_serving(args):
     slots = int(os.environ.get("MG_SERVING_SLOTS", "8"))
     policy = os.environ.get("MG_SERVING_POLICY", "smallest")
     reqs = request_stream(seed=5, n_requests=n_req, overlap=overlap)
-    srv = Server(slots=slots, keep_solution=False, policy=policy)
+    batch_max = int(os.environ.get("MG_SERVING_BATCH", "16"))
+    srv = Server(slots=slots, keep_solution=False, policy=policy, batch_max=batch_max)
     # warm-up: one small request of every order (module loading, first captures)
     warm = [r for r in request_stream(seed=6, n_requests=64, sizes=(4,)) if True][:8]
     srv.serve(warm, realtime=False)
@@ -597,8 +676,11 @@ def run_serving(args):
                        hbm_budget_gb=srv.budget / 1e9, total_dofs=dofs,
                        admission=policy + (" (aging after %.0f s)" % srv.max_wait
                                            if policy == "smallest" else ""),
-                       outer_operator="double-float (FP32 pairs)" if srv.outer_df64 else "FP64"),
+                       outer_operator="double-float (FP32 pairs)" if srv.outer_df64 else "FP64",
+                       batch_max=srv.batch_max, batch_dofs=srv.batch_dofs),
         "latency": summ, "max_concurrent": srv.max_active,
+        "batched_requests": int(sum(r.batch > 1 for r in res)),
+        "mean_batch": float(np.mean([r.batch for r in res])),
         "iterations": {"median": float(np.median([r.iterations for r in ok])),
                        "max": int(max(r.iterations for r in ok))},
         "max_relres": float(max(r.relres for r in ok)), "clocks": clock_info,
@@ -612,6 +694,8 @@ def main():
         run_reference(args)
     elif args.workload == "serving512":
         run_serving(args)
+    elif args.workload == "batch16_p4":
+        run_batch(args)
     elif args.workload != "cube16_p8" or args.precision is not None or args.cg:
         run_workload(args)
     else:

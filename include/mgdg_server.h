@@ -90,6 +90,14 @@ typedef struct {
   int (*execute)(void* user, long long ticket, const mg_request* req, int slot, int* iterations,
                  double* relres);
   void* execute_user;
+  /* Batching (GPU executor, use_cg = 1): a worker that admits a request of at most
+   * batch_dofs DOFs also admits, in submission order, further waiting
+   * requests of the same order P and tolerance, of at most batch_dofs DOFs,
+   * that fit into the budget, up to batch_max in all, and solves them with
+   * mg_solve_batch (every sweep one launch for the group; results bitwise
+   * those of separate solves).  batch_max 1 = no batching (1 .. 16). */
+  int batch_max;
+  size_t batch_dofs;
 } mg_server_opts;
 
 typedef struct {
@@ -98,6 +106,7 @@ typedef struct {
   double relres;      /* final relative residual */
   double t_submit, t_admit, t_done;  /* seconds since mg_server_create (monotonic clock) */
   int concurrency;    /* requests running when this one was admitted, itself included */
+  int batch;          /* requests solved together with it (mg_solve_batch), itself included */
   int slot;           /* worker that ran it */
   size_t footprint;   /* bytes it held */
   char error[160];    /* message of a failed solve, else empty */
@@ -110,7 +119,7 @@ typedef struct {
 } mg_server_stats;
 
 /* Defaults: 8 slots, budget 0, MG_SCHED_FCFS, max_wait 10 s, device 0, use_cg 1,
- * maxit 400, mg_default_opts, GPU executor. */
+ * maxit 400, mg_default_opts, GPU executor, batch_max 16, batch_dofs 2^20. */
 void mg_server_default_opts(mg_server_opts* o);
 
 /* Start the workers.  MG_EINVAL for a bad option, MG_ECUDA if the device,

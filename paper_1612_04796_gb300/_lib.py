@@ -64,6 +64,8 @@ class MgServerOpts(ctypes.Structure):
         ("opts", MgOpts),
         ("execute", EXECUTE_FN),
         ("execute_user", ctypes.c_void_p),
+        ("batch_max", ctypes.c_int),
+        ("batch_dofs", ctypes.c_size_t),
     ]
 
 
@@ -74,6 +76,7 @@ class MgResult(ctypes.Structure):
         ("relres", ctypes.c_double),
         ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double),
         ("concurrency", ctypes.c_int),
+        ("batch", ctypes.c_int),
         ("slot", ctypes.c_int),
         ("footprint", ctypes.c_size_t),
         ("error", ctypes.c_char * 160),

@@ -564,9 +564,32 @@ struct BatchMember {
   bool active = true;
 };
 
-// Record `step(member)` for every active member, then launch the merged sequence.
+// CUDA graphs of merged half iterations, keyed by the step and the set of
+// active problems; a sequence is captured the second time its key occurs
+// (the active set changes whenever a problem converges).
+struct BatchGraphs {
+  cudaStream_t s = nullptr, cap = nullptr;
+  std::vector<std::pair<uint64_t, cudaGraphExec_t>> execs;
+  std::vector<uint64_t> seen;
+  ~BatchGraphs() {
+    if (!execs.empty()) cudaStreamSynchronize(s);
+    for (auto& g : execs) cudaGraphExecDestroy(g.second);
+    if (cap) cudaStreamDestroy(cap);
+  }
+};
+
+// Record `step(member)` for every active member, then launch the merged
+// sequence (through a cached graph when `graphs` is given).
 template <typename F>
-cudaError_t batch_step(std::vector<BatchMember>& ms, cudaStream_t s, long long* launches, F step) {
+cudaError_t batch_step(std::vector<BatchMember>& ms, cudaStream_t s, long long* launches, F step,
+                       BatchGraphs* graphs = nullptr, int kind = 0) {
+  uint64_t key = (uint64_t)kind << 32;
+  for (int i = 0; i < (int)ms.size(); ++i)
+    if (ms[i].active) key |= 1ull << i;
+  if (graphs) {
+    for (auto& g : graphs->execs)
+      if (g.first == key) return cudaGraphLaunch(g.second, s);
+  }
   std::vector<LaunchRecorder> seqs;
   seqs.reserve(ms.size());
   LaunchRecorder*& rec = launch_recorder();
@@ -579,7 +602,27 @@ cudaError_t batch_step(std::vector<BatchMember>& ms, cudaStream_t s, long long* 
     if (e != cudaSuccess) return e;
   }
   if (seqs.empty()) return cudaSuccess;
-  return launch_merged(seqs, s, launches);
+  const bool capture = graphs && std::find(graphs->seen.begin(), graphs->seen.end(), key) != graphs->seen.end();
+  if (!capture) {
+    if (graphs) graphs->seen.push_back(key);
+    return launch_merged(seqs, s, launches);
+  }
+  cudaError_t e;
+  if (!graphs->cap && (e = cudaStreamCreateWithFlags(&graphs->cap, cudaStreamNonBlocking)) != cudaSuccess) return e;
+  if ((e = cudaStreamBeginCapture(graphs->cap, cudaStreamCaptureModeRelaxed)) != cudaSuccess) return e;
+  const cudaError_t el = launch_merged(seqs, graphs->cap, launches);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t ec = cudaStreamEndCapture(graphs->cap, &graph);
+  if (el != cudaSuccess || ec != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return el != cudaSuccess ? el : ec;
+  }
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return e;
+  graphs->execs.push_back({key, exec});
+  return cudaGraphLaunch(exec, s);
 }
 
 // Host copies of scalar slot `slot` of every active member (one gather
@@ -638,12 +681,14 @@ mg_status solve_batch_impl(std::vector<BatchMember>& ms, cudaStream_t s, double 
   // The cudaMemcpyAsync of cg_start is not a kernel: the first direction runs per problem.
   for (auto& m : ms)
     if (m.active) BCK(cg_start(m.c, m.r, m.z, m.p, m.pdf));
+  BatchGraphs graphs;
+  graphs.s = s;
   for (int it = 1; it <= maxit; ++it) {
     bool any = false;
     for (auto& m : ms) any = any || m.active;
     if (!any) break;
-    BCK(batch_step(ms, s, launches,
-                   [&](BatchMember& m) { return cg_step_a(m.c, m.x, m.p, m.r, m.q, m.pdf, m.qdf); }));
+    BCK(batch_step(
+        ms, s, launches, [&](BatchMember& m) { return cg_step_a(m.c, m.x, m.p, m.r, m.q, m.pdf, m.qdf); }, &graphs, 1));
     BCK(batch_read(ms, kSlotRR, s, v));
     for (int i = 0; i < (int)ms.size(); ++i) {
       BatchMember& m = ms[i];
@@ -660,7 +705,8 @@ mg_status solve_batch_impl(std::vector<BatchMember>& ms, cudaStream_t s, double 
         m.active = false;
       }
     }
-    BCK(batch_step(ms, s, launches, [&](BatchMember& m) { return cg_step_b(m.c, m.p, m.r, m.q, m.z, m.pdf); }));
+    BCK(batch_step(
+        ms, s, launches, [&](BatchMember& m) { return cg_step_b(m.c, m.p, m.r, m.q, m.z, m.pdf); }, &graphs, 2));
   }
   // zero-mean solutions and the tensor-core wait flags
   for (auto& m : ms) m.active = true;

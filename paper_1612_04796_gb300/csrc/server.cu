@@ -93,84 +93,126 @@ void set_error(mg_result& r, const char* what, const char* detail) {
   snprintf(r.error, sizeof(r.error), "%s%s%s", what, detail && *detail ? ": " : "", detail ? detail : "");
 }
 
-// The GPU executor: one solve on the worker's stream with pool memory.
-int gpu_solve(mg_server* s, Job& job, int slot) {
+// One request on the GPU: its context, pool memory (workspace, f, b, u) and
+// the right-hand side assembled, ready for mg_solve / mg_solve_batch.
+struct GpuRun {
+  mg_ctx* ctx = nullptr;
+  void* bufs[4] = {nullptr, nullptr, nullptr, nullptr};  // workspace, f, b, u
+  size_t sizes[4] = {0, 0, 0, 0};
+  int status = MG_OK;
+  double* b() const { return (double*)bufs[2]; }
+  double* u() const { return (double*)bufs[3]; }
+};
+
+void gpu_prepare(mg_server* s, Job& job, int slot, GpuRun& g) {
   const mg_request& q = job.req;
   mg_result& r = job.res;
   cudaStream_t st = s->streams[slot];
   mg_opts o = s->o.opts;
   o.stream = (void*)st;
-  mg_ctx* ctx = nullptr;
-  int status = mg_setup(q.lx, q.ly, q.lz, q.nx, q.ny, q.nz, q.P, q.penalty, q.overlap, &o, &ctx);
-  if (status != MG_OK) {
-    set_error(r, "mg_setup", ctx ? mg_last_error(ctx) : "");
-    if (ctx) mg_destroy(ctx);
-    return status;
+  g.status = mg_setup(q.lx, q.ly, q.lz, q.nx, q.ny, q.nz, q.P, q.penalty, q.overlap, &o, &g.ctx);
+  if (g.status != MG_OK) {
+    set_error(r, "mg_setup", g.ctx ? mg_last_error(g.ctx) : "");
+    return;
   }
-  const size_t n = (size_t)mg_num_dofs(ctx, mg_num_levels(ctx) - 1);
-  size_t ws = 0;
-  mg_workspace_size(ctx, &ws);
-  void* bufs[4] = {nullptr, nullptr, nullptr, nullptr};  // workspace, f, b, u
-  const size_t sizes[4] = {ws, n * sizeof(double), n * sizeof(double), n * sizeof(double)};
-  std::unique_ptr<double[]> fbuf;
+  const size_t n = (size_t)mg_num_dofs(g.ctx, mg_num_levels(g.ctx) - 1);
+  mg_workspace_size(g.ctx, &g.sizes[0]);
+  g.sizes[1] = g.sizes[2] = g.sizes[3] = n * sizeof(double);
   cudaError_t ce = cudaSuccess;
-  for (int i = 0; i < 4 && ce == cudaSuccess; ++i) ce = cudaMallocFromPoolAsync(&bufs[i], sizes[i], s->pool, st);
+  for (int i = 0; i < 4 && ce == cudaSuccess; ++i) ce = cudaMallocFromPoolAsync(&g.bufs[i], g.sizes[i], s->pool, st);
   if (ce != cudaSuccess) {
-    status = ce == cudaErrorMemoryAllocation ? MG_ENOMEM : MG_ECUDA;
+    g.status = ce == cudaErrorMemoryAllocation ? MG_ENOMEM : MG_ECUDA;
     set_error(r, "device allocation", cudaGetErrorString(ce));
+    return;
   }
-  double* d_f = (double*)bufs[1];
-  double* d_b = (double*)bufs[2];
-  double* d_u = (double*)bufs[3];
-  if (status == MG_OK) {
-    status = mg_bind_workspace(ctx, bufs[0], ws);
-    if (status != MG_OK) set_error(r, "mg_bind_workspace", mg_last_error(ctx));
+  g.status = mg_bind_workspace(g.ctx, g.bufs[0], g.sizes[0]);
+  if (g.status != MG_OK) {
+    set_error(r, "mg_bind_workspace", mg_last_error(g.ctx));
+    return;
   }
-  if (status == MG_OK) {
-    const double* src = q.f;
-    if (!src) {
-      fbuf.reset(new (std::nothrow) double[n]);
-      if (!fbuf) {
-        status = MG_ENOMEM;
-        set_error(r, "host buffer of the right-hand side", "");
-      } else {
-        q.fill(q.user, job.ticket, fbuf.get(), n);
-        src = fbuf.get();
-      }
+  std::unique_ptr<double[]> fbuf;
+  const double* src = q.f;
+  if (!src) {
+    fbuf.reset(new (std::nothrow) double[n]);
+    if (!fbuf) {
+      g.status = MG_ENOMEM;
+      set_error(r, "host buffer of the right-hand side", "");
+      return;
     }
-    if (status == MG_OK) {
-      ce = cudaMemcpyAsync(d_f, src, sizes[1], cudaMemcpyHostToDevice, st);
-      if (ce == cudaSuccess) ce = cudaMemsetAsync(d_u, 0, sizes[3], st);
-      if (ce != cudaSuccess) {
-        status = MG_ECUDA;
-        set_error(r, "copy in", cudaGetErrorString(ce));
-      }
-    }
+    q.fill(q.user, job.ticket, fbuf.get(), n);
+    src = fbuf.get();
   }
-  if (status == MG_OK) {
-    status = mg_rhs(ctx, d_f, d_b);
-    if (status != MG_OK) set_error(r, "mg_rhs", mg_last_error(ctx));
+  ce = cudaMemcpyAsync(g.bufs[1], src, g.sizes[1], cudaMemcpyHostToDevice, st);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(g.u(), 0, g.sizes[3], st);
+  if (ce == cudaSuccess && fbuf) ce = cudaStreamSynchronize(st);  // fbuf is released on return
+  if (ce != cudaSuccess) {
+    g.status = MG_ECUDA;
+    set_error(r, "copy in", cudaGetErrorString(ce));
+    return;
   }
-  if (status == MG_OK) {
-    status = mg_solve(ctx, d_u, d_b, q.tol, s->o.maxit, s->o.use_cg, &r.iterations, &r.relres, nullptr);
-    if (status != MG_OK) set_error(r, "mg_solve", mg_last_error(ctx));
-    if ((status == MG_OK || status == MG_ENOCONV) && q.u) {
-      ce = cudaMemcpyAsync(q.u, d_u, sizes[3], cudaMemcpyDeviceToHost, st);
-      if (ce != cudaSuccess) {
-        status = MG_ECUDA;
-        set_error(r, "copy out", cudaGetErrorString(ce));
-      }
+  g.status = mg_rhs(g.ctx, (const double*)g.bufs[1], g.b());
+  if (g.status != MG_OK) set_error(r, "mg_rhs", mg_last_error(g.ctx));
+}
+
+// Copy the solution out, release the memory and the context; the request's status.
+int gpu_finish(mg_server* s, Job& job, int slot, GpuRun& g) {
+  cudaStream_t st = s->streams[slot];
+  if ((g.status == MG_OK || g.status == MG_ENOCONV) && job.req.u) {
+    const cudaError_t ce = cudaMemcpyAsync(job.req.u, g.u(), g.sizes[3], cudaMemcpyDeviceToHost, st);
+    if (ce != cudaSuccess) {
+      g.status = MG_ECUDA;
+      set_error(job.res, "copy out", cudaGetErrorString(ce));
     }
   }
   for (int i = 0; i < 4; ++i)
-    if (bufs[i]) cudaFreeAsync(bufs[i], st);
-  ce = cudaStreamSynchronize(st);
-  if (ce != cudaSuccess && status == MG_OK) {
-    status = MG_ECUDA;
-    set_error(r, "stream", cudaGetErrorString(ce));
+    if (g.bufs[i]) cudaFreeAsync(g.bufs[i], st);
+  const cudaError_t ce = cudaStreamSynchronize(st);
+  if (ce != cudaSuccess && g.status == MG_OK) {
+    g.status = MG_ECUDA;
+    set_error(job.res, "stream", cudaGetErrorString(ce));
   }
-  mg_destroy(ctx);
-  return status;
+  if (g.ctx) mg_destroy(g.ctx);
+  return g.status;
+}
+
+// The GPU executor for one request, or for a group with mg_solve_batch.
+void gpu_solve(mg_server* s, std::vector<std::shared_ptr<Job>>& group, int slot) {
+  const int n = (int)group.size();
+  std::vector<GpuRun> runs(n);
+  for (int i = 0; i < n; ++i) gpu_prepare(s, *group[i], slot, runs[i]);
+  std::vector<int> ok;
+  for (int i = 0; i < n; ++i)
+    if (runs[i].status == MG_OK) ok.push_back(i);
+  if (ok.size() == 1) {
+    Job& j = *group[ok[0]];
+    GpuRun& g = runs[ok[0]];
+    g.status = mg_solve(g.ctx, g.u(), g.b(), j.req.tol, s->o.maxit, s->o.use_cg, &j.res.iterations, &j.res.relres,
+                        nullptr);
+    if (g.status != MG_OK) set_error(j.res, "mg_solve", mg_last_error(g.ctx));
+  } else if (ok.size() > 1) {
+    const int k = (int)ok.size();
+    std::vector<mg_ctx*> ctxs(k);
+    std::vector<double*> us(k);
+    std::vector<const double*> bs(k);
+    std::vector<int> its(k), sts(k);
+    std::vector<double> rel(k);
+    for (int i = 0; i < k; ++i) {
+      ctxs[i] = runs[ok[i]].ctx;
+      us[i] = runs[ok[i]].u();
+      bs[i] = runs[ok[i]].b();
+    }
+    const int st = mg_solve_batch(ctxs.data(), k, us.data(), bs.data(), group[ok[0]]->req.tol, s->o.maxit,
+                                  its.data(), rel.data(), sts.data());
+    for (int i = 0; i < k; ++i) {
+      Job& j = *group[ok[i]];
+      GpuRun& g = runs[ok[i]];
+      j.res.iterations = its[i];
+      j.res.relres = rel[i];
+      g.status = st != MG_OK ? st : sts[i];
+      if (g.status != MG_OK) set_error(j.res, "mg_solve_batch", st != MG_OK ? mg_last_error(ctxs[0]) : "");
+    }
+  }
+  for (int i = 0; i < n; ++i) group[i]->res.status = gpu_finish(s, *group[i], slot, runs[i]);
 }
 
 void worker(mg_server* s, int slot) {
@@ -191,31 +233,53 @@ void worker(mg_server* s, int slot) {
       }
       s->cv_work.wait(lk);
     }
-    s->used += job->footprint;
+    // batching: further waiting requests of the same order and tolerance, all small
+    std::vector<std::shared_ptr<Job>> group{job};
+    if (!s->o.execute && s->o.use_cg && s->o.batch_max > 1 && job->work <= (double)s->o.batch_dofs) {
+      size_t held = s->used + job->footprint;
+      for (auto it = s->waiting.begin(); it != s->waiting.end() && (int)group.size() < s->o.batch_max;) {
+        const Job& c = **it;
+        if (c.req.P == job->req.P && c.req.tol == job->req.tol && c.work <= (double)s->o.batch_dofs &&
+            c.footprint <= s->budget - held) {
+          held += c.footprint;
+          group.push_back(*it);
+          it = s->waiting.erase(it);
+        } else {
+          ++it;
+        }
+      }
+    }
+    const double t_admit = s->now();
+    for (auto& j : group) {
+      s->used += j->footprint;
+      s->running += 1;
+      j->res.t_admit = t_admit;
+      j->res.slot = slot;
+      j->res.batch = (int)group.size();
+    }
     s->peak = std::max(s->peak, s->used);
-    s->running += 1;
     s->max_running = std::max(s->max_running, s->running);
-    job->res.t_admit = s->now();
-    job->res.concurrency = s->running;
-    job->res.slot = slot;
+    for (auto& j : group) j->res.concurrency = s->running;
     lk.unlock();
 
-    int status;
     if (s->o.execute) {
-      status = s->o.execute(s->o.execute_user, job->ticket, &job->req, slot, &job->res.iterations,
-                            &job->res.relres);
+      const int status = s->o.execute(s->o.execute_user, job->ticket, &job->req, slot, &job->res.iterations,
+                                      &job->res.relres);
       if (status != MG_OK && !job->res.error[0]) set_error(job->res, "executor", "");
+      job->res.status = status;
     } else {
-      status = gpu_solve(s, *job, slot);
+      gpu_solve(s, group, slot);
     }
 
     lk.lock();
-    job->res.status = status;
-    job->res.t_done = s->now();
-    job->done = true;
-    s->used -= job->footprint;
-    s->running -= 1;
-    s->completed += 1;
+    const double t_done = s->now();
+    for (auto& j : group) {
+      j->res.t_done = t_done;
+      j->done = true;
+      s->used -= j->footprint;
+      s->running -= 1;
+      s->completed += 1;
+    }
     s->cv_work.notify_all();
     s->cv_done.notify_all();
   }
@@ -223,7 +287,8 @@ void worker(mg_server* s, int slot) {
 
 bool valid_opts(const mg_server_opts* o) {
   return o->slots >= 1 && o->slots <= 256 && (o->policy == MG_SCHED_FCFS || o->policy == MG_SCHED_SMALLEST) &&
-         o->max_wait >= 0.0 && o->maxit >= 1 && (o->use_cg == 0 || o->use_cg == 1) && o->device >= 0;
+         o->max_wait >= 0.0 && o->maxit >= 1 && (o->use_cg == 0 || o->use_cg == 1) && o->device >= 0 &&
+         o->batch_max >= 1 && o->batch_max <= 16;
 }
 
 // The library's sizing of a request (host only), or 0 if mg_setup rejects it.
@@ -256,6 +321,8 @@ void mg_server_default_opts(mg_server_opts* o) {
   o->use_cg = 1;
   o->maxit = 400;
   mg_default_opts(&o->opts);
+  o->batch_max = 16;
+  o->batch_dofs = size_t(1) << 20;
 }
 
 mg_status mg_request_footprint(const mg_request* req, const mg_opts* opts, size_t* bytes) {

@@ -52,6 +52,7 @@ class Result:
         self.t_done = None
         self.error = None
         self.concurrency = 0
+        self.batch = 1
         self.slot = -1
 
     @property
@@ -77,7 +78,9 @@ class Server:
     library's; this class marshals requests in and results out.
 
     Real solves by default: FP32 V-cycle preconditioner inside FP64 inexact
-    PCG, the outer products q = A p in double-float (outer_df64).  Each
+    PCG, the outer products q = A p in double-float (outer_df64); requests of
+    at most ``batch_dofs`` DOFs and the same order are solved in groups of up
+    to ``batch_max`` (mg_solve_batch: one launch per sweep for the group).  Each
     request's nodal right-hand side is drawn from its seed when the runtime
     admits it (the fill callback), so queued requests hold no host buffer.
 
@@ -86,7 +89,8 @@ class Server:
     makes no CUDA call, and ``req.footprint`` (bytes) is the request's size."""
 
     def __init__(self, slots=8, budget_bytes=None, precision="mixed", use_cg=True, device="cuda", keep_solution=True,
-                 outer_df64=True, policy="fcfs", max_wait=10.0, executor=None, maxit=400):
+                 outer_df64=True, policy="fcfs", max_wait=10.0, executor=None, maxit=400, batch_max=16,
+                 batch_dofs=1 << 20):
         from . import _lib
         from .solver import PRECISION
         if policy not in POLICY:
@@ -110,6 +114,9 @@ class Server:
         o.opts.precision = PRECISION[precision]
         o.opts.outer_df64 = 1 if self.outer_df64 else 0
         o.budget = 0 if budget_bytes is None else int(budget_bytes)
+        o.batch_max = int(batch_max)
+        o.batch_dofs = int(batch_dofs)
+        self.batch_max, self.batch_dofs = int(batch_max), int(batch_dofs)
         self._records = {}
         self._next_key = 1
         self._errors = {}
@@ -211,6 +218,7 @@ class Server:
                     res.iterations, res.relres = out.iterations, out.relres
                     res.t_arrival, res.t_admit, res.t_done = out.t_submit, out.t_admit, out.t_done
                     res.concurrency = out.concurrency
+                    res.batch = out.batch
                     res.slot = out.slot
                     if out.status != 0:
                         res.error = self._errors.pop(keys[i], None) or "%s: %s" % (

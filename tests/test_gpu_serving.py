@@ -74,3 +74,22 @@ def test_fp64_standalone_server(mg):
     srv.close()
     assert res.error is None and res.relres <= 1e-10
     assert 10 <= res.iterations <= 13
+
+
+def test_batched_admission_matches_unbatched(mg):
+    """Small requests of one order queued behind a busy slot are admitted
+    together and solved as one batch (mg_solve_batch); every result is
+    bitwise the one of the same server without batching."""
+    from paper_1612_04796_gb300.serving import Request, Server
+    reqs = [Request(i, (1.0 + 0.5 * i, 1.0, 1.0), (4 + i % 3, 4, 5), 4, seed=400 + i) for i in range(7)]
+    plain = Server(slots=1, batch_max=1)
+    ref = plain.serve(reqs, realtime=False)
+    plain.close()
+    batched = Server(slots=1, batch_max=8)
+    got = batched.serve(reqs, realtime=False)
+    batched.close()
+    assert max(r.batch for r in got) > 1 and all(r.batch == 1 for r in ref)
+    for a, b in zip(ref, got):
+        assert a.error is None and b.error is None
+        assert a.iterations == b.iterations and a.relres == b.relres
+        np.testing.assert_array_equal(a.u, b.u)
