@@ -239,8 +239,11 @@ mg_status mg_solve_host(mg_ctx* ctx, double* u_host, const double* f_host, doubl
  *            non-finite initial residual, MG_ECUDA if a tensor-core wait ran out)
  * Every launch goes to the stream of ctxs[0] (the other contexts' streams are
  * not used); the call synchronises it once per half iteration.  Each problem
- * gets the same kernels, block decomposition and reduction order as its own
- * mg_solve, hence bitwise the same result.  Returns MG_EINVAL / MG_ENOTREADY
+ * gets the block decomposition and reduction order of its own mg_solve; the
+ * batched kernels are separate compilations of the same code (a compiler may
+ * contract multiply-adds differently), so results agree with mg_solve to
+ * rounding, and bit for bit with any other batch that contains the problem
+ * (its result does not depend on the other problems).  Returns MG_EINVAL / MG_ENOTREADY
  * for bad arguments, MG_ECUDA if a CUDA call failed (message on ctxs[0]),
  * else MG_OK (per-problem outcomes in status).
  */

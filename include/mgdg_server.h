@@ -90,12 +90,14 @@ typedef struct {
   int (*execute)(void* user, long long ticket, const mg_request* req, int slot, int* iterations,
                  double* relres);
   void* execute_user;
-  /* Batching (GPU executor, use_cg = 1): a worker that admits a request of at most
-   * batch_dofs DOFs also admits, in submission order, further waiting
+  /* Batching (GPU executor, use_cg = 1): requests of at most batch_dofs DOFs
+   * are solved with mg_solve_batch (every sweep one launch for the group); a
+   * worker that admits one also admits, in submission order, further waiting
    * requests of the same order P and tolerance, of at most batch_dofs DOFs,
-   * that fit into the budget, up to batch_max in all, and solves them with
-   * mg_solve_batch (every sweep one launch for the group; results bitwise
-   * those of separate solves).  batch_max 1 = no batching (1 .. 16). */
+   * that fit into the budget, up to batch_max in all.  A small request's
+   * result is therefore the same bits whatever it was grouped with (and equal
+   * to a separate mg_solve to rounding).  batch_max 1 = groups of one
+   * (1 .. 16); batch_dofs 0 = no request takes the batched path. */
   int batch_max;
   size_t batch_dofs;
 } mg_server_opts;

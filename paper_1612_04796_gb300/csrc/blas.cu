@@ -360,6 +360,15 @@ __global__ void k_zero(T* x, int64_t n) {
   zero_body<T>(plain_block(), x, n);
 }
 
+// Blocks of the two-stage reductions: about 1024 elements per block, at most
+// kRedBlocks (8 per SM; vectors above 1.2 M elements); the second stage sums
+// the partials of exactly these blocks, so the order of summation is a fixed
+// function of n.
+inline int red_blocks(int64_t n) {
+  const int64_t b = (n + 1023) / 1024;
+  return (int)(b < 1 ? 1 : (b > kRedBlocks ? kRedBlocks : b));
+}
+
 inline int grid_for(int64_t n) {
   int64_t b = (n + kThreads - 1) / kThreads;
   if (b > 152 * 8) b = 152 * 8;
@@ -369,9 +378,10 @@ inline int grid_for(int64_t n) {
 
 template <typename T>
 cudaError_t reduce(const mg_ctx* c, const T* x, const T* y, int64_t n, int mode, int slot) {
-  launch_pdl<partial_body<T>>(k_partial<T>, kRedBlocks, kThreads, 0, c->stream, x, y, n, mode, c->ws.red);
+  const int nb = red_blocks(n);
+  launch_pdl<partial_body<T>>(k_partial<T>, nb, kThreads, 0, c->stream, x, y, n, mode, c->ws.red);
   c->nlaunch += 1;
-  launch_pdl<final_body>(k_final, 1, kThreads, 0, c->stream, c->ws.red, kRedBlocks, c->ws.scal, slot);
+  launch_pdl<final_body>(k_final, 1, kThreads, 0, c->stream, c->ws.red, nb, c->ws.scal, slot);
   c->nlaunch += 1;
   return cudaGetLastError();
 }
@@ -393,8 +403,9 @@ cudaError_t launch_sub_mean(const mg_ctx* c, double* x, int64_t n, int sum_slot)
 }
 
 cudaError_t launch_cg_update(const mg_ctx* c, double* x, const double* p, double* r, const double* q, int64_t n) {
-  launch_pdl<cg_update_body>(k_cg_update, kRedBlocks, kThreads, 0, c->stream, x, p, r, q, n, c->ws.scal, c->ws.red);
-  launch_pdl<cg_update_final_body>(k_cg_update_final, 1, kThreads, 0, c->stream, c->ws.red, kRedBlocks, c->ws.scal, n);
+  const int nb = red_blocks(n);
+  launch_pdl<cg_update_body>(k_cg_update, nb, kThreads, 0, c->stream, x, p, r, q, n, c->ws.scal, c->ws.red);
+  launch_pdl<cg_update_final_body>(k_cg_update_final, 1, kThreads, 0, c->stream, c->ws.red, nb, c->ws.scal, n);
   c->nlaunch += 2;
   return cudaGetLastError();
 }
@@ -402,8 +413,9 @@ cudaError_t launch_cg_update(const mg_ctx* c, double* x, const double* p, double
 template <typename TZ>
 cudaError_t launch_cg_direction(const mg_ctx* c, double* p, const TZ* z, const double* q, const double* r, int64_t n,
                                 df64* pdf) {
-  launch_pdl<cg_sums_body<TZ>>(k_cg_sums<TZ>, kRedBlocks, kThreads, 0, c->stream, z, q, r, n, c->ws.red);
-  launch_pdl<cg_sums_final_body<TZ>>(k_cg_sums_final<TZ>, 1, kThreads, 0, c->stream, c->ws.red, kRedBlocks, c->ws.scal, n);
+  const int nb = red_blocks(n);
+  launch_pdl<cg_sums_body<TZ>>(k_cg_sums<TZ>, nb, kThreads, 0, c->stream, z, q, r, n, c->ws.red);
+  launch_pdl<cg_sums_final_body<TZ>>(k_cg_sums_final<TZ>, 1, kThreads, 0, c->stream, c->ws.red, nb, c->ws.scal, n);
   launch_pdl<cg_newdir_body<TZ>>(k_cg_newdir<TZ>, grid_for(n), kThreads, 0, c->stream, p, z, n, c->ws.scal, pdf);
   c->nlaunch += 3;
   return cudaGetLastError();
@@ -429,8 +441,9 @@ cudaError_t launch_join_df64(const mg_ctx* c, const df64* x, double* y, int64_t 
 }
 
 cudaError_t launch_dot_dfq(const mg_ctx* c, const double* p, const df64* qdf, double* q, int64_t n, int slot) {
-  launch_pdl<dot_dfq_body>(k_dot_dfq, kRedBlocks, kThreads, 0, c->stream, p, qdf, q, n, c->ws.red);
-  launch_pdl<final_body>(k_final, 1, kThreads, 0, c->stream, c->ws.red, kRedBlocks, c->ws.scal, slot);
+  const int nb = red_blocks(n);
+  launch_pdl<dot_dfq_body>(k_dot_dfq, nb, kThreads, 0, c->stream, p, qdf, q, n, c->ws.red);
+  launch_pdl<final_body>(k_final, 1, kThreads, 0, c->stream, c->ws.red, nb, c->ws.scal, slot);
   c->nlaunch += 2;
   return cudaGetLastError();
 }
@@ -460,11 +473,12 @@ cudaError_t launch_rhs(const mg_ctx* c, const double* f, double* b) {
   for (int d = 0; d < 3; ++d) a.mass[d] = lv.t[d].mass;
   a.n = lv.n;
   a.Ne = c->Ne;
-  launch_pdl(k_mass_partial, kRedBlocks, kThreads, 0, c->stream, a, f, c->ws.red);
+  const int nb = red_blocks(lv.N);
+  launch_pdl(k_mass_partial, nb, kThreads, 0, c->stream, a, f, c->ws.red);
   c->nlaunch += 1;
-  launch_pdl<final_body>(k_final, 1, kThreads, 0, c->stream, c->ws.red, kRedBlocks, c->ws.scal, kSlotMassF);
+  launch_pdl<final_body>(k_final, 1, kThreads, 0, c->stream, c->ws.red, nb, c->ws.scal, kSlotMassF);
   c->nlaunch += 1;
-  launch_pdl<final_body>(k_final, 1, kThreads, 0, c->stream, c->ws.red + kRedBlocks, kRedBlocks, c->ws.scal, kSlotMass);
+  launch_pdl<final_body>(k_final, 1, kThreads, 0, c->stream, c->ws.red + nb, nb, c->ws.scal, kSlotMass);
   c->nlaunch += 1;
   launch_pdl(k_rhs, grid_for(lv.N), kThreads, 0, c->stream, a, f, b, c->ws.scal);
   c->nlaunch += 1;

@@ -93,13 +93,16 @@ cudaError_t coarse_passes(const double* const Q[3], const double* const lam[3], 
   if (blocks > 152 * 8) blocks = 152 * 8;
   const int* nz = null_mode;
   const int b = (int)blocks;
-  launch_pdl<coarse_axis_body<TI, double>>(k_coarse_axis<TI, double>, b, 256, 0, s, f0, A, Q[0], d, 0, 0, 1, 0, scal, mean_slot, 0, nullptr, nullptr, nullptr, 0, 0, 0);
-  launch_pdl<coarse_axis_body<double, double>>(k_coarse_axis<double, double>, b, 256, 0, s, A, B, Q[1], d, 1, 0, 0, 0, scal, -1, 0, nullptr, nullptr, nullptr, 0, 0, 0);
-  launch_pdl<coarse_axis_body<double, double>>(k_coarse_axis<double, double>, b, 256, 0, s, B, A, Q[2], d, 2, 0, 0, 0, scal, -1, 1, lam[0], lam[1], lam[2],
+  // the FP32 / double-float hierarchies' coarse solves run through the grouped
+  // twins (batched solves), the FP64 hierarchy's through the plain kernels
+  constexpr bool kTwin = kTwinType<TI> || kTwinType<TO>;
+  launch_pdl<kTwin ? &coarse_axis_body<TI, double> : nullptr>(k_coarse_axis<TI, double>, b, 256, 0, s, f0, A, Q[0], d, 0, 0, 1, 0, scal, mean_slot, 0, nullptr, nullptr, nullptr, 0, 0, 0);
+  launch_pdl<kTwin ? &coarse_axis_body<double, double> : nullptr>(k_coarse_axis<double, double>, b, 256, 0, s, A, B, Q[1], d, 1, 0, 0, 0, scal, -1, 0, nullptr, nullptr, nullptr, 0, 0, 0);
+  launch_pdl<kTwin ? &coarse_axis_body<double, double> : nullptr>(k_coarse_axis<double, double>, b, 256, 0, s, B, A, Q[2], d, 2, 0, 0, 0, scal, -1, 1, lam[0], lam[1], lam[2],
                                                   nz[0], nz[1], nz[2]);
-  launch_pdl<coarse_axis_body<double, double>>(k_coarse_axis<double, double>, b, 256, 0, s, A, B, Q[2], d, 2, 1, 0, 0, scal, -1, 0, nullptr, nullptr, nullptr, 0, 0, 0);
-  launch_pdl<coarse_axis_body<double, double>>(k_coarse_axis<double, double>, b, 256, 0, s, B, A, Q[1], d, 1, 1, 0, 0, scal, -1, 0, nullptr, nullptr, nullptr, 0, 0, 0);
-  launch_pdl<coarse_axis_body<double, TO>>(k_coarse_axis<double, TO>, b, 256, 0, s, A, u0, Q[0], d, 0, 1, 0, 1, scal, -1, 0, nullptr, nullptr, nullptr, 0, 0, 0);
+  launch_pdl<kTwin ? &coarse_axis_body<double, double> : nullptr>(k_coarse_axis<double, double>, b, 256, 0, s, A, B, Q[2], d, 2, 1, 0, 0, scal, -1, 0, nullptr, nullptr, nullptr, 0, 0, 0);
+  launch_pdl<kTwin ? &coarse_axis_body<double, double> : nullptr>(k_coarse_axis<double, double>, b, 256, 0, s, B, A, Q[1], d, 1, 1, 0, 0, scal, -1, 0, nullptr, nullptr, nullptr, 0, 0, 0);
+  launch_pdl<kTwin ? &coarse_axis_body<double, TO> : nullptr>(k_coarse_axis<double, TO>, b, 256, 0, s, A, u0, Q[0], d, 0, 1, 0, 1, scal, -1, 0, nullptr, nullptr, nullptr, 0, 0, 0);
   return cudaGetLastError();
 }
 

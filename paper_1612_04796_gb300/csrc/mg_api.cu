@@ -564,65 +564,88 @@ struct BatchMember {
   bool active = true;
 };
 
-// CUDA graphs of merged half iterations, keyed by the step and the set of
-// active problems; a sequence is captured the second time its key occurs
-// (the active set changes whenever a problem converges).
-struct BatchGraphs {
+#ifndef MGDG_BATCH_CAPTURE_AFTER
+#define MGDG_BATCH_CAPTURE_AFTER 5
+#endif
+
+// Recorded half iterations of a batch, keyed by the step and the set of
+// active problems (it shrinks as problems converge): a sequence is recorded
+// once, launched from the record while it is new, and captured as a CUDA
+// graph when the same key occurs for the MGDG_BATCH_CAPTURE_AFTER-th time
+// (0: never), so that short-lived sets do not pay for a capture.
+struct BatchCache {
+  struct Entry {
+    uint64_t key;
+    int uses;
+    std::vector<LaunchRecorder> seqs;
+    cudaGraphExec_t exec;
+  };
   cudaStream_t s = nullptr, cap = nullptr;
-  std::vector<std::pair<uint64_t, cudaGraphExec_t>> execs;
-  std::vector<uint64_t> seen;
-  ~BatchGraphs() {
-    if (!execs.empty()) cudaStreamSynchronize(s);
-    for (auto& g : execs) cudaGraphExecDestroy(g.second);
+  std::vector<Entry> entries;
+  ~BatchCache() {
+    bool any = false;
+    for (auto& e : entries) any = any || e.exec;
+    if (any) cudaStreamSynchronize(s);
+    for (auto& e : entries)
+      if (e.exec) cudaGraphExecDestroy(e.exec);
     if (cap) cudaStreamDestroy(cap);
   }
 };
 
-// Record `step(member)` for every active member, then launch the merged
-// sequence (through a cached graph when `graphs` is given).
-template <typename F>
-cudaError_t batch_step(std::vector<BatchMember>& ms, cudaStream_t s, long long* launches, F step,
-                       BatchGraphs* graphs = nullptr, int kind = 0) {
-  uint64_t key = (uint64_t)kind << 32;
-  for (int i = 0; i < (int)ms.size(); ++i)
-    if (ms[i].active) key |= 1ull << i;
-  if (graphs) {
-    for (auto& g : graphs->execs)
-      if (g.first == key) return cudaGraphLaunch(g.second, s);
-  }
-  std::vector<LaunchRecorder> seqs;
-  seqs.reserve(ms.size());
-  LaunchRecorder*& rec = launch_recorder();
-  for (auto& m : ms) {
-    if (!m.active) continue;
-    seqs.emplace_back();
-    rec = &seqs.back();
-    const cudaError_t e = step(m);
-    rec = nullptr;
-    if (e != cudaSuccess) return e;
-  }
-  if (seqs.empty()) return cudaSuccess;
-  const bool capture = graphs && std::find(graphs->seen.begin(), graphs->seen.end(), key) != graphs->seen.end();
-  if (!capture) {
-    if (graphs) graphs->seen.push_back(key);
-    return launch_merged(seqs, s, launches);
-  }
+cudaError_t capture_merged(BatchCache* bc, const std::vector<LaunchRecorder>& seqs, long long* launches,
+                           cudaGraphExec_t* exec) {
   cudaError_t e;
-  if (!graphs->cap && (e = cudaStreamCreateWithFlags(&graphs->cap, cudaStreamNonBlocking)) != cudaSuccess) return e;
-  if ((e = cudaStreamBeginCapture(graphs->cap, cudaStreamCaptureModeRelaxed)) != cudaSuccess) return e;
-  const cudaError_t el = launch_merged(seqs, graphs->cap, launches);
+  if (!bc->cap && (e = cudaStreamCreateWithFlags(&bc->cap, cudaStreamNonBlocking)) != cudaSuccess) return e;
+  if ((e = cudaStreamBeginCapture(bc->cap, cudaStreamCaptureModeRelaxed)) != cudaSuccess) return e;
+  const cudaError_t el = launch_merged(seqs, bc->cap, launches);
   cudaGraph_t graph = nullptr;
-  const cudaError_t ec = cudaStreamEndCapture(graphs->cap, &graph);
+  const cudaError_t ec = cudaStreamEndCapture(bc->cap, &graph);
   if (el != cudaSuccess || ec != cudaSuccess) {
     if (graph) cudaGraphDestroy(graph);
     return el != cudaSuccess ? el : ec;
   }
-  cudaGraphExec_t exec = nullptr;
-  e = cudaGraphInstantiate(&exec, graph, 0);
+  e = cudaGraphInstantiate(exec, graph, 0);
   cudaGraphDestroy(graph);
-  if (e != cudaSuccess) return e;
-  graphs->execs.push_back({key, exec});
-  return cudaGraphLaunch(exec, s);
+  return e;
+}
+
+// Record `step(member)` for every active member (or take the recorded
+// sequences from the cache), then launch them merged.
+template <typename F>
+cudaError_t batch_step(std::vector<BatchMember>& ms, cudaStream_t s, long long* launches, F step,
+                       BatchCache* cache = nullptr, int kind = 0) {
+  uint64_t key = (uint64_t)kind << 32;
+  for (int i = 0; i < (int)ms.size(); ++i)
+    if (ms[i].active) key |= 1ull << i;
+  BatchCache::Entry* ent = nullptr;
+  if (cache)
+    for (auto& e : cache->entries)
+      if (e.key == key) ent = &e;
+  if (ent && ent->exec) return cudaGraphLaunch(ent->exec, s);
+  std::vector<LaunchRecorder> fresh;
+  if (!ent) {
+    fresh.reserve(ms.size());
+    LaunchRecorder*& rec = launch_recorder();
+    for (auto& m : ms) {
+      if (!m.active) continue;
+      fresh.emplace_back();
+      rec = &fresh.back();
+      const cudaError_t e = step(m);
+      rec = nullptr;
+      if (e != cudaSuccess) return e;
+    }
+    if (fresh.empty()) return cudaSuccess;
+    if (!cache) return launch_merged(fresh, s, launches);
+    cache->entries.push_back({key, 0, std::move(fresh), nullptr});
+    ent = &cache->entries.back();
+  }
+  ent->uses += 1;
+  if (MGDG_BATCH_CAPTURE_AFTER > 0 && ent->uses >= MGDG_BATCH_CAPTURE_AFTER) {
+    const cudaError_t e = capture_merged(cache, ent->seqs, launches, &ent->exec);
+    if (e != cudaSuccess) return e;
+    return cudaGraphLaunch(ent->exec, s);
+  }
+  return launch_merged(ent->seqs, s, launches);
 }
 
 // Host copies of scalar slot `slot` of every active member (one gather
@@ -681,14 +704,14 @@ mg_status solve_batch_impl(std::vector<BatchMember>& ms, cudaStream_t s, double 
   // The cudaMemcpyAsync of cg_start is not a kernel: the first direction runs per problem.
   for (auto& m : ms)
     if (m.active) BCK(cg_start(m.c, m.r, m.z, m.p, m.pdf));
-  BatchGraphs graphs;
-  graphs.s = s;
+  BatchCache cache;
+  cache.s = s;
   for (int it = 1; it <= maxit; ++it) {
     bool any = false;
     for (auto& m : ms) any = any || m.active;
     if (!any) break;
     BCK(batch_step(
-        ms, s, launches, [&](BatchMember& m) { return cg_step_a(m.c, m.x, m.p, m.r, m.q, m.pdf, m.qdf); }, &graphs, 1));
+        ms, s, launches, [&](BatchMember& m) { return cg_step_a(m.c, m.x, m.p, m.r, m.q, m.pdf, m.qdf); }, &cache, 1));
     BCK(batch_read(ms, kSlotRR, s, v));
     for (int i = 0; i < (int)ms.size(); ++i) {
       BatchMember& m = ms[i];
@@ -706,7 +729,7 @@ mg_status solve_batch_impl(std::vector<BatchMember>& ms, cudaStream_t s, double 
       }
     }
     BCK(batch_step(
-        ms, s, launches, [&](BatchMember& m) { return cg_step_b(m.c, m.p, m.r, m.q, m.z, m.pdf); }, &graphs, 2));
+        ms, s, launches, [&](BatchMember& m) { return cg_step_b(m.c, m.p, m.r, m.q, m.z, m.pdf); }, &cache, 2));
   }
   // zero-mean solutions and the tensor-core wait flags
   for (auto& m : ms) m.active = true;

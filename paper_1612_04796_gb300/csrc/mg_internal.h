@@ -34,14 +34,17 @@ __device__ __forceinline__ void pdl_entry() { asm volatile("griddepcontrol.wait;
 // (k_grouped) runs the bodies of several independent problems in one launch:
 // the launch's blocks are split into consecutive ranges, one per problem,
 // each range running the body with that problem's parameters and its own
-// block numbering, exactly as the plain kernel would (same per-block work,
-// same reduction order, so the same bits).
+// block numbering, as the plain kernel would (same per-block work, same
+// reduction order).
 struct BlockIdx {
   int b, g;  // block index, number of blocks
 };
 __device__ __forceinline__ BlockIdx plain_block() { return BlockIdx{(int)blockIdx.x, (int)gridDim.x}; }
 
-constexpr int kMaxBatch = 16;  // problems per grouped launch
+#ifndef MGDG_MAX_BATCH
+#define MGDG_MAX_BATCH 16
+#endif
+constexpr int kMaxBatch = MGDG_MAX_BATCH;  // problems per grouped launch
 
 template <typename A>
 struct Grouped {
@@ -112,55 +115,82 @@ cudaError_t replay_plain(const LaunchRec& r, cudaStream_t s) {
                       t);
 }
 
+// Launch the grouped twin of Body for n problems: parameter sets a[i] (each
+// a cuda::std::tuple<KArgs...>) with grid[i] blocks each.
 template <int LB, auto Body, typename... KArgs>
-cudaError_t launch_grouped(const LaunchRec* const* r, int n, cudaStream_t s) {
+cudaError_t launch_twin(const void* const* a, const unsigned* grid, int n, dim3 block, size_t smem,
+                        cudaStream_t s) {
   using Tup = cuda::std::tuple<KArgs...>;
   Grouped<Tup> g;
   g.count = n;
   g.start[0] = 0;
   for (int i = 0; i < n; ++i) {
-    memcpy((void*)&g.a[i], r[i]->args.data(), sizeof(Tup));
-    g.start[i + 1] = g.start[i] + (int)r[i]->grid.x;
+    memcpy((void*)&g.a[i], a[i], sizeof(Tup));
+    g.start[i + 1] = g.start[i] + (int)grid[i];
   }
   auto* twin = k_grouped<LB, Body, KArgs...>;
-  if (r[0]->smem > 48 * 1024) {
-    const cudaError_t e = cudaFuncSetAttribute(twin, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)r[0]->smem);
+  static size_t smem_set = 48 * 1024;  // dynamic shared memory the twin has been allowed so far
+  if (smem > smem_set) {
+    const cudaError_t e = cudaFuncSetAttribute(twin, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    smem_set = smem;
   }
   void* ptrs[1] = {(void*)&g};
-  return launch_pdl_now((const void*)twin, dim3(g.start[n]), r[0]->block, r[0]->smem, s, ptrs);
+  return launch_pdl_now((const void*)twin, dim3(g.start[n]), block, smem, s, ptrs);
 }
 
-// Launch `kernel` with programmatic dependent launch (or record it, see
-// LaunchRecorder).  Body (optional): the kernel's body, for a grouped twin
-// with launch bounds LB.
+template <int LB, auto Body, typename... KArgs>
+cudaError_t launch_grouped(const LaunchRec* const* r, int n, cudaStream_t s) {
+  const void* a[kMaxBatch];
+  unsigned grid[kMaxBatch];
+  for (int i = 0; i < n; ++i) {
+    a[i] = r[i]->args.data();
+    grid[i] = r[i]->grid.x;
+  }
+  return launch_twin<LB, Body, KArgs...>(a, grid, n, r[0]->block, r[0]->smem, s);
+}
+
+// Launch `kernel` with programmatic dependent launch, or record it while a
+// recorder is installed (LaunchRecorder).  Body (optional, may be a null
+// pointer): the kernel's body; a recorded launch of a kernel with a body is
+// later run by the body's grouped twin k_grouped (with LB as launch bounds),
+// together with other problems' launches of the same kernel.  The twin is a
+// separate compilation of the body (it may contract multiply-adds
+// differently from the plain kernel), so batched solves agree with single
+// solves to rounding, and bit for bit with each other whatever the batch.
 template <auto Body = nullptr, int LB = 256, typename... KArgs, typename... Args>
 inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
                               Args&&... args) {
   cuda::std::tuple<KArgs...> t(static_cast<KArgs>(args)...);
-  if (LaunchRecorder* rec = launch_recorder()) {
-    LaunchRec r;
-    r.key = (const void*)kernel;
-    r.grid = grid;
-    r.block = block;
-    r.smem = smem;
-    r.args.resize(sizeof(t));
-    memcpy(r.args.data(), (const void*)&t, sizeof(t));
-    r.plain = &replay_plain<KArgs...>;
-    if constexpr (!std::is_same<decltype(Body), std::nullptr_t>::value) {
-      if (grid.y == 1 && grid.z == 1) r.grouped = &launch_grouped<LB, Body, KArgs...>;
-    }
-    rec->recs.push_back(std::move(r));
-    return cudaSuccess;
+  LaunchRecorder* rec = launch_recorder();
+  if (!rec) return launch_tuple(kernel, grid, block, smem, s, t);
+  LaunchRec r;
+  r.key = (const void*)kernel;
+  r.grid = grid;
+  r.block = block;
+  r.smem = smem;
+  r.plain = &replay_plain<KArgs...>;
+  if constexpr (Body != nullptr) {
+    if (grid.y == 1 && grid.z == 1) r.grouped = &launch_grouped<LB, Body, KArgs...>;
   }
-  return launch_tuple(kernel, grid, block, smem, s, t);
+  r.args.resize(sizeof(t));
+  memcpy(r.args.data(), (const void*)&t, sizeof(t));
+  rec->recs.push_back(std::move(r));
+  return cudaSuccess;
 }
+
+// Arithmetic types whose kernels have grouped twins (batched solves merge the
+// launches of the FP32 and double-float hierarchies and the FP64 vector
+// passes; the FP64 operator, smoother and transfer kernels run one launch per
+// problem, which keeps the build time).
+template <typename T>
+constexpr bool kTwinType = !std::is_same<T, double>::value;
 
 constexpr int kMaxLevels = 6;   // P <= 32
 constexpr int kMaxP = 32;
 constexpr int kMaxN = kMaxP + 1;        // nodes per element and direction
 constexpr int kMaxM = 3 * kMaxN;         // widest subdomain line (strips of whole neighbour elements)
-constexpr int kRedBlocks = 1216;        // fixed grid of the two-stage reductions (8 per SM)
+constexpr int kRedBlocks = 1216;        // largest grid of the two-stage reductions (8 per SM)
 
 // Slots of the device scalar array ws.scal.
 enum Slot : int {
@@ -227,7 +257,7 @@ struct Workspace {
   double* coarse_f = nullptr;  // FP64 coarse rhs / solution for the FP32 hierarchy
   double* coarse_u = nullptr;
   double* cg[8] = {nullptr};   // FP64 outer vectors: x, r, z, p, q, u_io, f_io, spare
-  double* red = nullptr;       // reduction partials (kRedBlocks * 2)
+  double* red = nullptr;       // reduction partials (up to 8 columns of kRedBlocks)
   double* scal = nullptr;      // device scalars (64)
   int* status = nullptr;       // device status word
   double* jac = nullptr;       // eigensolver scratch

@@ -429,7 +429,7 @@ cudaError_t launch_fdm(const mg_ctx* c, int l, const T* r) {
   const int lines = std::max(lv.m[1] * lv.m[2], std::max(lv.m[0] * lv.m[2], lv.m[0] * lv.m[1]));
   int threads = lines >= 256 ? 256 : 128;
   int64_t blocks = c->Ne < 152 * 8 ? c->Ne : 152 * 8;
-  launch_pdl<fdm_body<T>>(k_fdm<T>, (int)blocks, threads, smem, c->stream, a);
+  launch_pdl<kTwinType<T> ? &fdm_body<T> : nullptr>(k_fdm<T>, (int)blocks, threads, smem, c->stream, a);
   c->nlaunch += 1;
   return cudaGetLastError();
 }
@@ -447,19 +447,19 @@ cudaError_t launch_scatter(const mg_ctx* c, int l, T* u, int accumulate) {
   const bool two = 2 * lv.no[0] <= lv.n && 2 * lv.no[1] <= lv.n && 2 * lv.no[2] <= lv.n;
   if (two) {
     switch (lv.n) {
-#define MGDG_SC2(N) case N: launch_pdl<scatter_n2_body<T, N>>(k_scatter_n2<T, N>, eb, 256, 0, c->stream, corr, u, c->Ne, c->ne[0], c->ne[1], c->ne[2], g, accumulate); return cudaGetLastError();
+#define MGDG_SC2(N) case N: launch_pdl<kTwinType<T> ? &scatter_n2_body<T, N> : nullptr>(k_scatter_n2<T, N>, eb, 256, 0, c->stream, corr, u, c->Ne, c->ne[0], c->ne[1], c->ne[2], g, accumulate); return cudaGetLastError();
       MGDG_SC2(3) MGDG_SC2(5) MGDG_SC2(9) MGDG_SC2(17) MGDG_SC2(33)
 #undef MGDG_SC2
       default: break;
     }
   }
   switch (lv.n) {
-#define MGDG_SC(N) case N: launch_pdl<scatter_n_body<T, N>>(k_scatter_n<T, N>, eb, 256, 0, c->stream, corr, u, c->Ne, c->ne[0], c->ne[1], c->ne[2], g, accumulate); return cudaGetLastError();
+#define MGDG_SC(N) case N: launch_pdl<kTwinType<T> ? &scatter_n_body<T, N> : nullptr>(k_scatter_n<T, N>, eb, 256, 0, c->stream, corr, u, c->Ne, c->ne[0], c->ne[1], c->ne[2], g, accumulate); return cudaGetLastError();
     MGDG_SC(3) MGDG_SC(5) MGDG_SC(9) MGDG_SC(17) MGDG_SC(33)
 #undef MGDG_SC
     default: break;
   }
-  launch_pdl<scatter_body<T>>(k_scatter<T>, (int)blocks, 256, 0, c->stream, corr, u, c->Ne, c->ne[0], c->ne[1], c->ne[2], lv.n, g,
+  launch_pdl<kTwinType<T> ? &scatter_body<T> : nullptr>(k_scatter<T>, (int)blocks, 256, 0, c->stream, corr, u, c->Ne, c->ne[0], c->ne[1], c->ne[2], lv.n, g,
                                                     accumulate);
   return cudaGetLastError();
 }

@@ -175,21 +175,22 @@ int gpu_finish(mg_server* s, Job& job, int slot, GpuRun& g) {
   return g.status;
 }
 
-// The GPU executor for one request, or for a group with mg_solve_batch.
-void gpu_solve(mg_server* s, std::vector<std::shared_ptr<Job>>& group, int slot) {
+// The GPU executor: one request with mg_solve, or (batched) a group of one or
+// more with mg_solve_batch.
+void gpu_solve(mg_server* s, std::vector<std::shared_ptr<Job>>& group, int slot, bool batched) {
   const int n = (int)group.size();
   std::vector<GpuRun> runs(n);
   for (int i = 0; i < n; ++i) gpu_prepare(s, *group[i], slot, runs[i]);
   std::vector<int> ok;
   for (int i = 0; i < n; ++i)
     if (runs[i].status == MG_OK) ok.push_back(i);
-  if (ok.size() == 1) {
+  if (ok.size() == 1 && !batched) {
     Job& j = *group[ok[0]];
     GpuRun& g = runs[ok[0]];
     g.status = mg_solve(g.ctx, g.u(), g.b(), j.req.tol, s->o.maxit, s->o.use_cg, &j.res.iterations, &j.res.relres,
                         nullptr);
     if (g.status != MG_OK) set_error(j.res, "mg_solve", mg_last_error(g.ctx));
-  } else if (ok.size() > 1) {
+  } else if (!ok.empty()) {
     const int k = (int)ok.size();
     std::vector<mg_ctx*> ctxs(k);
     std::vector<double*> us(k);
@@ -233,9 +234,11 @@ void worker(mg_server* s, int slot) {
       }
       s->cv_work.wait(lk);
     }
-    // batching: further waiting requests of the same order and tolerance, all small
+    // batching: small requests take the batched path, with further waiting
+    // requests of the same order and tolerance, all small
     std::vector<std::shared_ptr<Job>> group{job};
-    if (!s->o.execute && s->o.use_cg && s->o.batch_max > 1 && job->work <= (double)s->o.batch_dofs) {
+    const bool batched = !s->o.execute && s->o.use_cg && job->work <= (double)s->o.batch_dofs;
+    if (batched && s->o.batch_max > 1) {
       size_t held = s->used + job->footprint;
       for (auto it = s->waiting.begin(); it != s->waiting.end() && (int)group.size() < s->o.batch_max;) {
         const Job& c = **it;
@@ -268,7 +271,7 @@ void worker(mg_server* s, int slot) {
       if (status != MG_OK && !job->res.error[0]) set_error(job->res, "executor", "");
       job->res.status = status;
     } else {
-      gpu_solve(s, group, slot);
+      gpu_solve(s, group, slot, batched);
     }
 
     lk.lock();

@@ -336,7 +336,7 @@ cudaError_t launch_sipg_n(const mg_ctx* c, OpArgs<T>& a) {
       const int64_t nblk = c->Ne * chunks;
       const int blocks = (int)(nblk < 152 * 16 ? nblk : 152 * 16);
       for (int dir = 0; dir < 3; ++dir) {
-        launch_pdl<sipg_dir_body<T, N, NP>>(k_sipg_dir<T, N, NP>, blocks, threads, 0, c->stream, a, dir, chunks);
+        launch_pdl<kTwinType<T> ? &sipg_dir_body<T, N, NP> : nullptr>(k_sipg_dir<T, N, NP>, blocks, threads, 0, c->stream, a, dir, chunks);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
       }
@@ -350,7 +350,7 @@ cudaError_t launch_sipg_n(const mg_ctx* c, OpArgs<T>& a) {
   if (threads > 256) threads = 256;
   int64_t groups = (c->Ne + a.epb - 1) / a.epb;
   int64_t blocks = groups < 152 * 16 ? groups : 152 * 16;
-  launch_pdl<sipg_n_body<T, N>>(k_sipg_n<T, N>, (int)blocks, threads, 0, c->stream, a);
+  launch_pdl<kTwinType<T> ? &sipg_n_body<T, N> : nullptr>(k_sipg_n<T, N>, (int)blocks, threads, 0, c->stream, a);
   c->nlaunch += 1;
   return cudaGetLastError();
 }

@@ -57,7 +57,7 @@ cudaError_t contract(const mg_ctx* c, const T* in, T* out, const T* J, int d0, i
   int64_t total = c->Ne * (int64_t)o0 * o1 * o2;
   int64_t blocks = (total + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;
-  launch_pdl<contract_axis_body<T>>(k_contract_axis<T>, (int)blocks, 256, 0, c->stream, in, out, J, c->Ne, d0, d1, d2, axis, nout, ldj, transpose,
+  launch_pdl<kTwinType<T> ? &contract_axis_body<T> : nullptr>(k_contract_axis<T>, (int)blocks, 256, 0, c->stream, in, out, J, c->Ne, d0, d1, d2, axis, nout, ldj, transpose,
                                                          accumulate);
   c->nlaunch += 1;
   return cudaGetLastError();
@@ -231,10 +231,10 @@ cudaError_t launch_restrict(const mg_ctx* c, int l, const T* r_fine, T* f_coarse
   const T* J = table_of<T>(c) + c->lev[l].J;
   const int nb = fused_blocks(c->Ne);
   switch (nf) {
-    case 3: launch_pdl<restrict_fused_body<T, 3, 2>, 128>(k_restrict_fused<T, 3, 2>, nb, 128, 0, c->stream, r_fine, f_coarse, J, c->Ne); c->nlaunch += 1; return cudaGetLastError();
-    case 5: launch_pdl<restrict_fused_body<T, 5, 3>, 128>(k_restrict_fused<T, 5, 3>, nb, 128, 0, c->stream, r_fine, f_coarse, J, c->Ne); c->nlaunch += 1; return cudaGetLastError();
-    case 9: launch_pdl<restrict_fused_body<T, 9, 5>, 128>(k_restrict_fused<T, 9, 5>, nb, 128, 0, c->stream, r_fine, f_coarse, J, c->Ne); c->nlaunch += 1; return cudaGetLastError();
-    case 17: launch_pdl<restrict_fused_body<T, 17, 9>, 128>(k_restrict_fused<T, 17, 9>, nb, 128, 0, c->stream, r_fine, f_coarse, J, c->Ne); c->nlaunch += 1; return cudaGetLastError();
+    case 3: launch_pdl<kTwinType<T> ? &restrict_fused_body<T, 3, 2> : nullptr, 128>(k_restrict_fused<T, 3, 2>, nb, 128, 0, c->stream, r_fine, f_coarse, J, c->Ne); c->nlaunch += 1; return cudaGetLastError();
+    case 5: launch_pdl<kTwinType<T> ? &restrict_fused_body<T, 5, 3> : nullptr, 128>(k_restrict_fused<T, 5, 3>, nb, 128, 0, c->stream, r_fine, f_coarse, J, c->Ne); c->nlaunch += 1; return cudaGetLastError();
+    case 9: launch_pdl<kTwinType<T> ? &restrict_fused_body<T, 9, 5> : nullptr, 128>(k_restrict_fused<T, 9, 5>, nb, 128, 0, c->stream, r_fine, f_coarse, J, c->Ne); c->nlaunch += 1; return cudaGetLastError();
+    case 17: launch_pdl<kTwinType<T> ? &restrict_fused_body<T, 17, 9> : nullptr, 128>(k_restrict_fused<T, 17, 9>, nb, 128, 0, c->stream, r_fine, f_coarse, J, c->Ne); c->nlaunch += 1; return cudaGetLastError();
     default: break;
   }
   T* t1 = static_cast<T*>(c->ws.corr);
@@ -252,10 +252,10 @@ cudaError_t launch_prolong(const mg_ctx* c, int l, const T* u_coarse, T* u_fine)
   const T* J = table_of<T>(c) + c->lev[l].J;
   const int nb = fused_blocks(c->Ne);
   switch (nf) {
-    case 3: launch_pdl<prolong_fused_body<T, 3, 2>, 128>(k_prolong_fused<T, 3, 2>, nb, 128, 0, c->stream, u_coarse, u_fine, J, c->Ne); c->nlaunch += 1; return cudaGetLastError();
-    case 5: launch_pdl<prolong_fused_body<T, 5, 3>, 128>(k_prolong_fused<T, 5, 3>, nb, 128, 0, c->stream, u_coarse, u_fine, J, c->Ne); c->nlaunch += 1; return cudaGetLastError();
-    case 9: launch_pdl<prolong_fused_body<T, 9, 5>, 128>(k_prolong_fused<T, 9, 5>, nb, 128, 0, c->stream, u_coarse, u_fine, J, c->Ne); c->nlaunch += 1; return cudaGetLastError();
-    case 17: launch_pdl<prolong_fused_body<T, 17, 9>, 128>(k_prolong_fused<T, 17, 9>, nb, 128, 0, c->stream, u_coarse, u_fine, J, c->Ne); c->nlaunch += 1; return cudaGetLastError();
+    case 3: launch_pdl<kTwinType<T> ? &prolong_fused_body<T, 3, 2> : nullptr, 128>(k_prolong_fused<T, 3, 2>, nb, 128, 0, c->stream, u_coarse, u_fine, J, c->Ne); c->nlaunch += 1; return cudaGetLastError();
+    case 5: launch_pdl<kTwinType<T> ? &prolong_fused_body<T, 5, 3> : nullptr, 128>(k_prolong_fused<T, 5, 3>, nb, 128, 0, c->stream, u_coarse, u_fine, J, c->Ne); c->nlaunch += 1; return cudaGetLastError();
+    case 9: launch_pdl<kTwinType<T> ? &prolong_fused_body<T, 9, 5> : nullptr, 128>(k_prolong_fused<T, 9, 5>, nb, 128, 0, c->stream, u_coarse, u_fine, J, c->Ne); c->nlaunch += 1; return cudaGetLastError();
+    case 17: launch_pdl<kTwinType<T> ? &prolong_fused_body<T, 17, 9> : nullptr, 128>(k_prolong_fused<T, 17, 9>, nb, 128, 0, c->stream, u_coarse, u_fine, J, c->Ne); c->nlaunch += 1; return cudaGetLastError();
     default: break;
   }
   T* t1 = static_cast<T*>(c->ws.corr);

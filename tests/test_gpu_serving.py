@@ -46,22 +46,33 @@ def test_memory_budget_limits_concurrency(mg):
 
 def test_served_solution_equals_a_direct_solve(mg):
     """The runtime's path (right-hand side drawn at admission, copied in,
-    assembled by mg_rhs, solved from zero, copied out) gives bitwise the
-    solution of the same solve made directly through MGSolver."""
+    assembled by mg_rhs, solved from zero, copied out) gives the bits of the
+    same solve made directly: a small request takes the batched path
+    (mg_solve_batch), a large one mg_solve; both agree with mg_solve to
+    rounding."""
     import torch
     from paper_1612_04796_gb300 import inputs
     from paper_1612_04796_gb300.serving import Request, Server
-    req = Request(0, (2.0, 1.0, 1.0), (5, 5, 5), 4, seed=77)
-    srv = Server(slots=2)
-    res = srv.serve([req], realtime=False)[0]
+    small = Request(0, (2.0, 1.0, 1.0), (5, 5, 5), 4, seed=77)
+    large = Request(1, (1.0, 1.0, 1.0), (12, 12, 12), 8, seed=78)   # 373,248 DOFs > batch_dofs below
+    srv = Server(slots=2, batch_dofs=200000)
+    res = srv.serve([small, large], realtime=False)
     srv.close()
-    assert res.error is None and res.relres <= 1e-10
-    s = mg.MGSolver(req.lengths, req.counts, req.P, overlap=req.overlap, precision="mixed", outer_df64=True)
-    b = s.rhs(torch.tensor(inputs.gaussian(s.num_dofs(), req.seed), device="cuda"))
-    u, its, rel, _ = s.solve(b, tol=req.tol, use_cg=True, maxit=400)
-    assert its == res.iterations and rel == res.relres
-    np.testing.assert_array_equal(u.cpu().numpy(), res.u)
-    s.close()
+    for req, r in zip((small, large), res):
+        assert r.error is None and r.relres <= 1e-10
+        s = mg.MGSolver(req.lengths, req.counts, req.P, overlap=req.overlap, precision="mixed", outer_df64=True)
+        b = s.rhs(torch.tensor(inputs.gaussian(s.num_dofs(), req.seed), device="cuda"))
+        u, its, rel, _ = s.solve(b, tol=req.tol, use_cg=True, maxit=400)
+        if req is small:
+            ub, itb, relb, _ = mg.solve_batch([s], [b], tol=req.tol, maxit=400)
+            assert itb[0] == r.iterations and relb[0] == r.relres
+            np.testing.assert_array_equal(ub[0].cpu().numpy(), r.u)
+            assert abs(its - r.iterations) <= 1
+            assert np.max(np.abs(u.cpu().numpy() - r.u)) <= 1e-9 * np.max(np.abs(r.u))
+        else:
+            assert its == r.iterations and rel == r.relres
+            np.testing.assert_array_equal(u.cpu().numpy(), r.u)
+        s.close()
 
 
 def test_fp64_standalone_server(mg):
@@ -79,7 +90,7 @@ def test_fp64_standalone_server(mg):
 def test_batched_admission_matches_unbatched(mg):
     """Small requests of one order queued behind a busy slot are admitted
     together and solved as one batch (mg_solve_batch); every result is
-    bitwise the one of the same server without batching."""
+    bitwise the one of the same server with groups of one."""
     from paper_1612_04796_gb300.serving import Request, Server
     reqs = [Request(i, (1.0 + 0.5 * i, 1.0, 1.0), (4 + i % 3, 4, 5), 4, seed=400 + i) for i in range(7)]
     plain = Server(slots=1, batch_max=1)
