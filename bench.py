@@ -79,7 +79,14 @@ WORKLOADS["serving512"] = dict(workload="serving stream: 512 solve requests, Poi
                                 "admitted by HBM footprint (smallest work first with aging; MG_SERVING_POLICY=fcfs "
                                 "for first come first served), "
                                 "one context and stream per slot; requests of <= 2^20 DOFs and one order admitted "
-                                "together are solved as one batch (MG_SERVING_BATCH=1: no batching)")
+                                "together are solved as one batch (MG_SERVING_BATCH=1: groups of one; MG_SERVING_BATCH_DOFS=0: "
+                                "no batched path)")
+WORKLOADS["serving512_small"] = dict(workload="serving stream of small requests only: 512 solve requests, Poisson arrivals at "
+                                     "5000/s (seed 5: the server is saturated), periodic box [0,AR]x[0,1]x[0,1], AR ~ U[1,8], n^3 elements with "
+                                     "n in {4,8}, P in {2,4,8} (1,728 to 373,248 DOFs), N_O=4, Gaussian f, FP32 V(1,1) "
+                                     "in FP64 PCG (outer A p in double-float), tol 1e-10; the regime where launches, "
+                                     "not arithmetic, bound the throughput (MG_SERVING_BATCH_DOFS=0: no batched path)",
+                                     sizes=[4, 8], orders=[2, 4, 8], rate=5000.0)
 WORKLOADS["batch16_p4"] = dict(workload="16 independent small problems solved together (mg_solve_batch: one launch per "
                                          "sweep for all): periodic boxes [0,AR]x[0,1]x[0,1], AR ~ U[1,8], n^3 elements "
                                          "with n in {4,5,6,7,8} (seed 7), P=4, N_O=1, Gaussian f, FP32 V(1,1) in FP64 "
@@ -651,9 +658,12 @@ def run_serving(args):
     overlap = 4 if args.overlap is None else args.overlap
     slots = int(os.environ.get("MG_SERVING_SLOTS", "8"))
     policy = os.environ.get("MG_SERVING_POLICY", "smallest")
-    reqs = request_stream(seed=5, n_requests=n_req, overlap=overlap)
+    W = WORKLOADS[args.workload]
+    reqs = request_stream(seed=5, n_requests=n_req, overlap=overlap, sizes=tuple(W.get("sizes", (4, 8, 16, 24, 32))),
+                          orders=tuple(W.get("orders", (2, 4, 8, 16))), rate=W.get("rate", 200.0))
     batch_max = int(os.environ.get("MG_SERVING_BATCH", "16"))
-    srv = Server(slots=slots, keep_solution=False, policy=policy, batch_max=batch_max)
+    batch_dofs = int(os.environ.get("MG_SERVING_BATCH_DOFS", str(1 << 20)))
+    srv = Server(slots=slots, keep_solution=False, policy=policy, batch_max=batch_max, batch_dofs=batch_dofs)
     # warm-up: one small request of every order (module loading, first captures)
     warm = [r for r in request_stream(seed=6, n_requests=64, sizes=(4,)) if True][:8]
     srv.serve(warm, realtime=False)
@@ -672,7 +682,7 @@ def run_serving(args):
         "metric": METRIC, "value": dofs / makespan, "unit": "DOF/s", "n_gpus": 1, "steps": 1, "warmup": 1,
         "ms_per_step": makespan * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32 multigrid / f64 outer", "data": "synthetic",
-        "config": dict(WORKLOADS["serving512"], name="serving512", requests=len(reqs), slots=slots, overlap_layers=overlap,
+        "config": dict(W, name=args.workload, requests=len(reqs), slots=slots, overlap_layers=overlap,
                        hbm_budget_gb=srv.budget / 1e9, total_dofs=dofs,
                        admission=policy + (" (aging after %.0f s)" % srv.max_wait
                                            if policy == "smallest" else ""),
@@ -692,7 +702,7 @@ def main():
     args = parse_args()
     if args.impl == "reference":
         run_reference(args)
-    elif args.workload == "serving512":
+    elif args.workload in ("serving512", "serving512_small"):
         run_serving(args)
     elif args.workload == "batch16_p4":
         run_batch(args)
