@@ -628,8 +628,12 @@ def run_batch(args):
     run(False, args.warmup)
     clocks = ClockSampler(dev.index)
     clocks.start()
+    lb0 = solvers[0].batch_launches()
     ms_b, its_b = run(True, args.steps)
+    launches_b = solvers[0].batch_launches() - lb0
+    ls0 = sum(s.kernel_launches() for s in solvers)
     ms_s, its_s = run(False, args.steps)
+    launches_s = sum(s.kernel_launches() for s in solvers) - ls0
     clock_info = clocks.stop()
     assert its_b == its_s
     u_b = [u.clone() for _, _, u in probs]
@@ -642,7 +646,8 @@ def run_batch(args):
         "dtype": "f32 multigrid / f64 outer", "data": "synthetic",
         "config": dict(W, name=args.workload, total_dofs=dofs, dofs_each=[s.num_dofs() for s in solvers],
                        iterations=its_b, l2="inputs L2-resident (small problems; the point is launch overhead)"),
-        "one_by_one": {"value": dofs / (ts / 1e3), "ms_per_step": ts},
+        "gpu_launches": launches_b // args.steps,
+        "one_by_one": {"value": dofs / (ts / 1e3), "ms_per_step": ts, "gpu_launches": launches_s // args.steps},
         "speedup_vs_one_by_one": ts / tb, "bitwise_identical_to_one_by_one": identical, "clocks": clock_info,
     }
     print(json.dumps(line), flush=True)

@@ -322,6 +322,11 @@ mg_status mg_coarse_solve_noalloc(double lx, double ly, double lz, int nx, int n
  *   residual, 3 restriction, 4 prolongation, 5 coarse solve.  Synchronises
  *   the stream. */
 long long mg_kernel_launches(const mg_ctx* ctx);
+/* Kernels launched by the mg_solve_batch calls whose first context was ctx
+ * (grouped launches, graph nodes, the gathers of the residual norms and the
+ * per-problem first directions; recorded launches do not count for the
+ * members' mg_kernel_launches). */
+long long mg_batch_launches(const mg_ctx* ctx);
 mg_status mg_profile(mg_ctx* ctx, int enable);
 mg_status mg_profile_result(mg_ctx* ctx, int kind, int level, double* total_ms, long long* count);
 

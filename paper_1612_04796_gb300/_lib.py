@@ -131,6 +131,7 @@ SIGNATURES = {
     "mg_get_table": (_S, [_P, _I, _I, _I, _P, _I, ctypes.POINTER(_I)]),
     "mg_coarse_solve_noalloc": (_S, [_D, _D, _D, _I, _I, _I, _D, _P, _P, _P]),
     "mg_kernel_launches": (_LL, [_P]),
+    "mg_batch_launches": (_LL, [_P]),
     "mg_profile": (_S, [_P, _I]),
     "mg_profile_result": (_S, [_P, _I, _I, ctypes.POINTER(_D), ctypes.POINTER(_LL)]),
     "mg_server_default_opts": (None, [ctypes.POINTER(MgServerOpts)]),

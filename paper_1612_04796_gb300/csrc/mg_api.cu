@@ -579,6 +579,7 @@ struct BatchCache {
     int uses;
     std::vector<LaunchRecorder> seqs;
     cudaGraphExec_t exec;
+    long long nodes;  // kernel launches in the graph
   };
   cudaStream_t s = nullptr, cap = nullptr;
   std::vector<Entry> entries;
@@ -621,7 +622,10 @@ cudaError_t batch_step(std::vector<BatchMember>& ms, cudaStream_t s, long long* 
   if (cache)
     for (auto& e : cache->entries)
       if (e.key == key) ent = &e;
-  if (ent && ent->exec) return cudaGraphLaunch(ent->exec, s);
+  if (ent && ent->exec) {
+    *launches += ent->nodes;
+    return cudaGraphLaunch(ent->exec, s);
+  }
   std::vector<LaunchRecorder> fresh;
   if (!ent) {
     fresh.reserve(ms.size());
@@ -630,19 +634,22 @@ cudaError_t batch_step(std::vector<BatchMember>& ms, cudaStream_t s, long long* 
       if (!m.active) continue;
       fresh.emplace_back();
       rec = &fresh.back();
+      const long long n0 = m.c->nlaunch;  // recorded, not launched for this context
       const cudaError_t e = step(m);
+      m.c->nlaunch = n0;
       rec = nullptr;
       if (e != cudaSuccess) return e;
     }
     if (fresh.empty()) return cudaSuccess;
     if (!cache) return launch_merged(fresh, s, launches);
-    cache->entries.push_back({key, 0, std::move(fresh), nullptr});
+    cache->entries.push_back({key, 0, std::move(fresh), nullptr, 0});
     ent = &cache->entries.back();
   }
   ent->uses += 1;
   if (MGDG_BATCH_CAPTURE_AFTER > 0 && ent->uses >= MGDG_BATCH_CAPTURE_AFTER) {
-    const cudaError_t e = capture_merged(cache, ent->seqs, launches, &ent->exec);
+    const cudaError_t e = capture_merged(cache, ent->seqs, &ent->nodes, &ent->exec);
     if (e != cudaSuccess) return e;
+    *launches += ent->nodes;
     return cudaGraphLaunch(ent->exec, s);
   }
   return launch_merged(ent->seqs, s, launches);
@@ -650,7 +657,8 @@ cudaError_t batch_step(std::vector<BatchMember>& ms, cudaStream_t s, long long* 
 
 // Host copies of scalar slot `slot` of every active member (one gather
 // launch, one copy, one synchronisation).
-cudaError_t batch_read(std::vector<BatchMember>& ms, int slot, cudaStream_t s, std::vector<double>& out) {
+cudaError_t batch_read(std::vector<BatchMember>& ms, int slot, cudaStream_t s, std::vector<double>& out,
+                       long long* launches) {
   const double* src[kMaxBatch];
   int idx[kMaxBatch], n = 0;
   for (int i = 0; i < (int)ms.size(); ++i)
@@ -664,6 +672,7 @@ cudaError_t batch_read(std::vector<BatchMember>& ms, int slot, cudaStream_t s, s
   double host[kMaxBatch];
   cudaError_t e;
   if ((e = launch_gather_scalars(src, n, dst, s)) != cudaSuccess) return e;
+  ++*launches;
   if ((e = cudaMemcpyAsync(host, dst, n * sizeof(double), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
   if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
   for (int k = 0; k < n; ++k) out[idx[k]] = host[k];
@@ -690,7 +699,7 @@ mg_status solve_batch_impl(std::vector<BatchMember>& ms, cudaStream_t s, double 
     if ((e2 = launch_sub_mean(m.c, m.r, N, kSlotSum)) != cudaSuccess) return e2;
     return launch_dot(m.c, m.r, m.r, N, kSlotRR);
   }));
-  BCK(batch_read(ms, kSlotRR, s, v));
+  BCK(batch_read(ms, kSlotRR, s, v, launches));
   for (int i = 0; i < (int)ms.size(); ++i) {
     BatchMember& m = ms[i];
     m.r0 = m.rn = sqrt(v[i]);
@@ -703,7 +712,11 @@ mg_status solve_batch_impl(std::vector<BatchMember>& ms, cudaStream_t s, double 
   }
   // The cudaMemcpyAsync of cg_start is not a kernel: the first direction runs per problem.
   for (auto& m : ms)
-    if (m.active) BCK(cg_start(m.c, m.r, m.z, m.p, m.pdf));
+    if (m.active) {
+      const long long n0 = m.c->nlaunch;
+      BCK(cg_start(m.c, m.r, m.z, m.p, m.pdf));
+      *launches += m.c->nlaunch - n0;
+    }
   BatchCache cache;
   cache.s = s;
   for (int it = 1; it <= maxit; ++it) {
@@ -712,7 +725,7 @@ mg_status solve_batch_impl(std::vector<BatchMember>& ms, cudaStream_t s, double 
     if (!any) break;
     BCK(batch_step(
         ms, s, launches, [&](BatchMember& m) { return cg_step_a(m.c, m.x, m.p, m.r, m.q, m.pdf, m.qdf); }, &cache, 1));
-    BCK(batch_read(ms, kSlotRR, s, v));
+    BCK(batch_read(ms, kSlotRR, s, v, launches));
     for (int i = 0; i < (int)ms.size(); ++i) {
       BatchMember& m = ms[i];
       if (!m.active) continue;
@@ -1217,6 +1230,8 @@ const char* mg_last_error(const mg_ctx* c) {
   if (!c) return "null context";
   return c->err.c_str();
 }
+
+long long mg_batch_launches(const mg_ctx* c) { return c ? c->batch_launches : -1; }
 
 long long mg_kernel_launches(const mg_ctx* c) { return c ? c->nlaunch : -1; }
 

@@ -249,6 +249,10 @@ class MGSolver:
     def kernel_launches(self):
         return int(self.lib.mg_kernel_launches(self.ctx))
 
+    def batch_launches(self):
+        """Kernels launched by the batched solves this solver led (first in the list)."""
+        return int(self.lib.mg_batch_launches(self.ctx))
+
     def profile(self, enable=True):
         self._check(self.lib.mg_profile(self.ctx, int(bool(enable))))
 
