@@ -82,6 +82,86 @@ __device__ __forceinline__ void fdm_bwd(const T (&v)[M], const T* __restrict__ S
   }
 }
 
+// The same two products with the output loop rolled, each output written to
+// out[i * os] as soon as it is formed: the double-float pair arithmetic makes
+// the fully unrolled form too large for the instruction cache (the same
+// operations in the same order, so the same results).
+template <typename T, int M>
+__device__ __forceinline__ void fdm_fwd_rolled(T (&x)[M], const T* __restrict__ S, T* out, int os) {
+  constexpr int h = M / 2, ne = h + 1;
+#pragma unroll
+  for (int a = 0; a < h; ++a) {
+    const T xa = x[a], xb = x[M - 1 - a];
+    x[a] = xa + xb;
+    x[M - 1 - a] = xa - xb;
+  }
+#pragma unroll 1
+  for (int p = 0; p < ne; ++p) {
+    Acc<T> acc;
+    acc.init(S[p], x[0]);
+#pragma unroll
+    for (int a = 1; a <= h; ++a) acc.add(S[a * M + p], x[a]);
+    out[p * os] = acc.get();
+  }
+#pragma unroll 1
+  for (int q = 0; q < h; ++q) {
+    Acc<T> acc;
+    acc.init(S[ne + q], x[M - 1]);
+#pragma unroll
+    for (int a = 1; a < h; ++a) acc.add(S[a * M + ne + q], x[M - 1 - a]);
+    out[(ne + q) * os] = acc.get();
+  }
+}
+
+template <typename T, int M>
+__device__ __forceinline__ void fdm_bwd_rolled(const T (&v)[M], const T* __restrict__ SW, T* out, int os) {
+  constexpr int h = M / 2, ne = h + 1;
+#pragma unroll 1
+  for (int a = 0; a <= h; ++a) {
+    Acc<T> ea;
+    ea.init(SW[a * M], v[0]);
+#pragma unroll
+    for (int p = 1; p < ne; ++p) ea.add(SW[a * M + p], v[p]);
+    const T E = ea.get();
+    if (a < h) {
+      Acc<T> oa;
+      oa.init(SW[a * M + ne], v[ne]);
+#pragma unroll
+      for (int q = 1; q < h; ++q) oa.add(SW[a * M + ne + q], v[ne + q]);
+      const T O = oa.get();
+      out[a * os] = E + O;
+      out[(M - 1 - a) * os] = E - O;
+    } else {
+      out[a * os] = E;
+    }
+  }
+}
+
+// Line transforms of the smoother passes: out[i * os] = (S^T x)_i, resp. (SW v)_i.
+template <typename T, int M>
+__device__ __forceinline__ void line_fwd(T (&x)[M], const T* __restrict__ S, T* out, int os) {
+  if constexpr (std::is_same<T, df64>::value) {
+    fdm_fwd_rolled<T, M>(x, S, out, os);
+  } else {
+    T y[M];
+    fdm_fwd<T, M>(x, S, y);
+#pragma unroll
+    for (int p = 0; p < M; ++p) out[p * os] = y[p];
+  }
+}
+
+template <typename T, int M>
+__device__ __forceinline__ void line_bwd(const T (&v)[M], const T* __restrict__ SW, T* out, int os) {
+  if constexpr (std::is_same<T, df64>::value) {
+    fdm_bwd_rolled<T, M>(v, SW, out, os);
+  } else {
+    T x[M];
+    fdm_bwd<T, M>(v, SW, x);
+#pragma unroll
+    for (int p = 0; p < M; ++p) out[p * os] = x[p];
+  }
+}
+
 // Subdomains per block and whether their tiles fit in shared memory (the
 // last pass always writes the corrections to the global buffer).
 template <typename T, int M>
@@ -129,13 +209,11 @@ __device__ __forceinline__ void fdm_m_body(BlockIdx bi_, FdmArgs<T> a) {
       const int64_t ol = (fdm_wrap(sx - 1, a.nx) + row) * n3 + loc + (n - no);
       const int64_t oc = (sx + row) * n3 + loc - no;
       const int64_t orr = (fdm_wrap(sx + 1, a.nx) + row) * n3 + loc - (no + n);
-      T x[M], y[M];
+      T x[M];
 #pragma unroll
       for (int t = 0; t < M; ++t) x[t] = a.r[(t < no ? ol : (t < no + n ? oc : orr)) + t];
-      fdm_fwd<T, M>(x, sS, y);
       T* tile = (kSmemTile ? sTile + (ln / M2) * M3 : a.corr + s * (int64_t)M3) + M * l2;
-#pragma unroll
-      for (int p = 0; p < M; ++p) tile[p] = y[p];
+      line_fwd<T, M>(x, sS, tile, 1);
     }
     __syncthreads();
     // pass 2: forward, y
@@ -144,12 +222,10 @@ __device__ __forceinline__ void fdm_m_body(BlockIdx bi_, FdmArgs<T> a) {
       if (s >= a.Ne) continue;
       const int l2 = ln % M2;
       T* line = (kSmemTile ? sTile + (ln / M2) * M3 : a.corr + s * (int64_t)M3) + (l2 % M) + M2 * (l2 / M);
-      T x[M], y[M];
+      T x[M];
 #pragma unroll
       for (int t = 0; t < M; ++t) x[t] = line[t * M];
-      fdm_fwd<T, M>(x, sS + M2, y);
-#pragma unroll
-      for (int t = 0; t < M; ++t) line[t * M] = y[t];
+      line_fwd<T, M>(x, sS + M2, line, M);
     }
     __syncthreads();
     // pass 3: forward z, scale by 1 / (lam_x + lam_y + lam_z), backward z
@@ -161,12 +237,16 @@ __device__ __forceinline__ void fdm_m_body(BlockIdx bi_, FdmArgs<T> a) {
       T x[M], y[M];
 #pragma unroll
       for (int t = 0; t < M; ++t) x[t] = line[t * M2];
-      fdm_fwd<T, M>(x, sS + 2 * M2, y);
+      if constexpr (std::is_same<T, df64>::value) {  // through the tile (rolled products)
+        fdm_fwd_rolled<T, M>(x, sS + 2 * M2, line, M2);
 #pragma unroll
-      for (int t = 0; t < M; ++t) y[t] *= dinv[l2 + t * M2];
-      fdm_bwd<T, M>(y, sSW + 2 * M2, x);
+        for (int t = 0; t < M; ++t) y[t] = line[t * M2] * dinv[l2 + t * M2];
+      } else {
+        fdm_fwd<T, M>(x, sS + 2 * M2, y);
 #pragma unroll
-      for (int t = 0; t < M; ++t) line[t * M2] = x[t];
+        for (int t = 0; t < M; ++t) y[t] *= dinv[l2 + t * M2];
+      }
+      line_bwd<T, M>(y, sSW + 2 * M2, line, M2);
     }
     __syncthreads();
     // pass 4: backward, y
@@ -175,12 +255,10 @@ __device__ __forceinline__ void fdm_m_body(BlockIdx bi_, FdmArgs<T> a) {
       if (s >= a.Ne) continue;
       const int l2 = ln % M2;
       T* line = (kSmemTile ? sTile + (ln / M2) * M3 : a.corr + s * (int64_t)M3) + (l2 % M) + M2 * (l2 / M);
-      T x[M], y[M];
+      T y[M];
 #pragma unroll
       for (int t = 0; t < M; ++t) y[t] = line[t * M];
-      fdm_bwd<T, M>(y, sSW + M2, x);
-#pragma unroll
-      for (int t = 0; t < M; ++t) line[t * M] = x[t];
+      line_bwd<T, M>(y, sSW + M2, line, M);
     }
     __syncthreads();
     // pass 5: backward, x (weights folded into SW)
@@ -190,12 +268,10 @@ __device__ __forceinline__ void fdm_m_body(BlockIdx bi_, FdmArgs<T> a) {
       const int l2 = ln % M2;
       const T* line = (kSmemTile ? sTile + (ln / M2) * M3 : a.corr + s * (int64_t)M3) + M * l2;
       T* outl = a.corr + s * (int64_t)M3 + M * l2;
-      T x[M], y[M];
+      T y[M];
 #pragma unroll
       for (int t = 0; t < M; ++t) y[t] = line[t];
-      fdm_bwd<T, M>(y, sSW, x);
-#pragma unroll
-      for (int t = 0; t < M; ++t) outl[t] = x[t];
+      line_bwd<T, M>(y, sSW, outl, 1);
     }
     __syncthreads();
   }

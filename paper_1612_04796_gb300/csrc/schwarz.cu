@@ -321,16 +321,21 @@ __device__ __forceinline__ void scatter_n2_body(BlockIdx bi_, const T* __restric
     cand(i, g.nox, ex, nx, sx, px, &vx);
     cand(j, g.noy, ey, ny, sy, py, &vy);
     cand(k, g.noz, ez, nz, sz, pz, &vz);
+    // offset of (subdomain, position) = the sum of one term per direction
+    int64_t ox[2], oy[2], oz[2];
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+      ox[a] = sx[a] * mxyz + px[a];
+      oy[a] = sy[a] * ((int64_t)nx * mxyz) + (int64_t)g.mx * py[a];
+      oz[a] = sz[a] * ((int64_t)nx * ny * mxyz) + (int64_t)g.mx * g.my * pz[a];
+    }
     T val[8];
 #pragma unroll
     for (int c = 0; c < 2; ++c)
 #pragma unroll
       for (int b = 0; b < 2; ++b)
 #pragma unroll
-        for (int a = 0; a < 2; ++a) {
-          const int64_t sub = sx[a] + (int64_t)nx * (sy[b] + (int64_t)ny * sz[c]);
-          val[a + 2 * (b + 2 * c)] = corr[sub * mxyz + px[a] + g.mx * (py[b] + g.my * pz[c])];
-        }
+        for (int a = 0; a < 2; ++a) val[a + 2 * (b + 2 * c)] = corr[ox[a] + oy[b] + oz[c]];
     T sum = 0;
 #pragma unroll
     for (int c = 0; c < 2; ++c)
