@@ -329,7 +329,7 @@ cudaError_t launch_setup_coarse_tables(const double len[3], const int ne[3], dou
                                        const DirTables t[3], double* scratch, int64_t per_block, int* status,
                                        cudaStream_t s);
 
-// ---- operator (sipg.cu) ----
+// ---- operator (sipg_kernels.cuh, instantiated in sipg_f64.cu / sipg_f32.cu / sipg_df64.cu) ----
 // out = mode==0 ? A u : f - A u, on level l, T = double | float.
 template <typename T>
 cudaError_t launch_sipg(const mg_ctx* c, int l, const T* u, const T* f, T* out, int residual);  // T: double, float, df64
