@@ -26,7 +26,7 @@ __device__ double block_reduce(double v, double* sh) {
 // mode 0: sum x*y   mode 1: sum x   (T = double | float input)
 template <typename T>
 __device__ __forceinline__ void partial_body(BlockIdx bi_, const T* __restrict__ x, const T* __restrict__ y, int64_t n,
-                                                      int mode, double* partial) {
+                                             int mode, double* partial) {
   __shared__ double sh[kThreads];
   double acc = 0.0;
   for (int64_t i = bi_.b * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)bi_.g * blockDim.x)
@@ -37,7 +37,7 @@ __device__ __forceinline__ void partial_body(BlockIdx bi_, const T* __restrict__
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_partial(const T* __restrict__ x, const T* __restrict__ y, int64_t n,
-                                                      int mode, double* partial) {
+                                  int mode, double* partial) {
   pdl_entry();
   partial_body<T>(plain_block(), x, y, n, mode, partial);
 }
@@ -70,8 +70,8 @@ __global__ void k_sub_mean(T* x, int64_t n, const double* scal, int slot) {
 
 // The CG update with the partial sums of the new r and r^2 (columns 0, 1).
 __device__ __forceinline__ void cg_update_body(BlockIdx bi_, double* __restrict__ x, const double* __restrict__ p,
-                                                        double* __restrict__ r, const double* __restrict__ q,
-                                                        int64_t n, double* scal, double* partial) {
+                                               double* __restrict__ r, const double* __restrict__ q, int64_t n,
+                                               double* scal, double* partial) {
   __shared__ double sh[kThreads];
   const double alpha = scal[kSlotRZ] / scal[kSlotPQ];
   if (bi_.b == 0 && threadIdx.x == 0) scal[kSlotAlpha] = alpha;
@@ -93,8 +93,8 @@ __device__ __forceinline__ void cg_update_body(BlockIdx bi_, double* __restrict_
 }
 
 __global__ void __launch_bounds__(kThreads) k_cg_update(double* __restrict__ x, const double* __restrict__ p,
-                                                        double* __restrict__ r, const double* __restrict__ q,
-                                                        int64_t n, double* scal, double* partial) {
+                                  double* __restrict__ r, const double* __restrict__ q, int64_t n, double* scal,
+                                  double* partial) {
   pdl_entry();
   cg_update_body(plain_block(), x, p, r, q, n, scal, partial);
 }
@@ -110,7 +110,7 @@ __device__ void final_columns(const double* partial, int nb, int cols, double* v
 }
 
 __device__ __forceinline__ void cg_update_final_body(BlockIdx bi_, const double* partial, int nb, double* scal,
-                                                              int64_t n) {
+                                                     int64_t n) {
   __shared__ double sh[kThreads];
   double v[2];
   final_columns(partial, nb, 2, v, sh);
@@ -120,8 +120,7 @@ __device__ __forceinline__ void cg_update_final_body(BlockIdx bi_, const double*
   }
 }
 
-__global__ void __launch_bounds__(kThreads) k_cg_update_final(const double* partial, int nb, double* scal,
-                                                              int64_t n) {
+__global__ void __launch_bounds__(kThreads) k_cg_update_final(const double* partial, int nb, double* scal, int64_t n) {
   pdl_entry();
   cg_update_final_body(plain_block(), partial, nb, scal, n);
 }
@@ -137,7 +136,7 @@ __device__ __forceinline__ double z_scale(const double* scal) {
 // preconditioner's scale is applied to the totals).
 template <typename TZ>
 __device__ __forceinline__ void cg_sums_body(BlockIdx bi_, const TZ* __restrict__ zs, const double* __restrict__ q,
-                                                      const double* __restrict__ r, int64_t n, double* partial) {
+                                             const double* __restrict__ r, int64_t n, double* partial) {
   __shared__ double sh[kThreads];
   double a[3] = {0.0, 0.0, 0.0};
   for (int64_t i = bi_.b * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)bi_.g * blockDim.x) {
@@ -155,7 +154,7 @@ __device__ __forceinline__ void cg_sums_body(BlockIdx bi_, const TZ* __restrict_
 
 template <typename TZ>
 __global__ void __launch_bounds__(kThreads) k_cg_sums(const TZ* __restrict__ zs, const double* __restrict__ q,
-                                                      const double* __restrict__ r, int64_t n, double* partial) {
+                                  const double* __restrict__ r, int64_t n, double* partial) {
   pdl_entry();
   cg_sums_body<TZ>(plain_block(), zs, q, r, n, partial);
 }
@@ -163,7 +162,8 @@ __global__ void __launch_bounds__(kThreads) k_cg_sums(const TZ* __restrict__ zs,
 // With z' = z - mean(z): z'.q' = z.q (1^T q = 1^T A p = 0) and
 // z'.r' = z.r - sum(z) sum(r) / n (sum(r) from the update pass).
 template <typename TZ>
-__device__ __forceinline__ void cg_sums_final_body(BlockIdx bi_, const double* partial, int nb, double* scal, int64_t n) {
+__device__ __forceinline__ void cg_sums_final_body(BlockIdx bi_, const double* partial, int nb, double* scal,
+                                                   int64_t n) {
   __shared__ double sh[kThreads];
   double v[3];
   final_columns(partial, nb, 3, v, sh);
@@ -186,8 +186,8 @@ __global__ void __launch_bounds__(kThreads) k_cg_sums_final(const double* partia
 
 // p = (z - mean(z)) + beta p; pdf (if given) receives p split into double-float pairs
 template <typename TZ>
-__device__ __forceinline__ void cg_newdir_body(BlockIdx bi_, double* __restrict__ p, const TZ* __restrict__ zs, int64_t n, const double* scal,
-                            df64* __restrict__ pdf) {
+__device__ __forceinline__ void cg_newdir_body(BlockIdx bi_, double* __restrict__ p, const TZ* __restrict__ zs,
+                                               int64_t n, const double* scal, df64* __restrict__ pdf) {
   const double zsc = z_scale<TZ>(scal), muz = scal[kSlotMuZ], beta = scal[kSlotBeta];
   for (int64_t i = bi_.b * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)bi_.g * blockDim.x) {
     const double v = ((double)zs[i] * zsc - muz) + beta * p[i];
@@ -204,7 +204,8 @@ __global__ void k_cg_newdir(double* __restrict__ p, const TZ* __restrict__ zs, i
 }
 
 // y = x (accumulate = 0) or y += x (accumulate = 1), x double-float, y FP64
-__device__ __forceinline__ void join_df64_body(BlockIdx bi_, const df64* __restrict__ x, double* __restrict__ y, int64_t n, int accumulate) {
+__device__ __forceinline__ void join_df64_body(BlockIdx bi_, const df64* __restrict__ x, double* __restrict__ y,
+                                               int64_t n, int accumulate) {
   for (int64_t i = bi_.b * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)bi_.g * blockDim.x)
     y[i] = accumulate ? y[i] + df_to_double(x[i]) : df_to_double(x[i]);
 }
@@ -214,7 +215,8 @@ __global__ void k_join_df64(const df64* __restrict__ x, double* __restrict__ y, 
   join_df64_body(plain_block(), x, y, n, accumulate);
 }
 
-__device__ __forceinline__ void split_df64_body(BlockIdx bi_, const double* __restrict__ x, df64* __restrict__ y, int64_t n) {
+__device__ __forceinline__ void split_df64_body(BlockIdx bi_, const double* __restrict__ x, df64* __restrict__ y,
+                                                int64_t n) {
   for (int64_t i = bi_.b * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)bi_.g * blockDim.x)
     y[i] = df_from_double(x[i]);
 }
@@ -226,7 +228,7 @@ __global__ void k_split_df64(const double* __restrict__ x, df64* __restrict__ y,
 
 // q = qdf as FP64 and the partial sums of p . q
 __device__ __forceinline__ void dot_dfq_body(BlockIdx bi_, const double* __restrict__ p, const df64* __restrict__ qdf,
-                                                      double* __restrict__ q, int64_t n, double* partial) {
+                                             double* __restrict__ q, int64_t n, double* partial) {
   __shared__ double sh[kThreads];
   double acc = 0.0;
   for (int64_t i = bi_.b * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)bi_.g * blockDim.x) {
@@ -239,12 +241,13 @@ __device__ __forceinline__ void dot_dfq_body(BlockIdx bi_, const double* __restr
 }
 
 __global__ void __launch_bounds__(kThreads) k_dot_dfq(const double* __restrict__ p, const df64* __restrict__ qdf,
-                                                      double* __restrict__ q, int64_t n, double* partial) {
+                                  double* __restrict__ q, int64_t n, double* partial) {
   pdl_entry();
   dot_dfq_body(plain_block(), p, qdf, q, n, partial);
 }
 
-__device__ __forceinline__ void add_body(BlockIdx bi_, double* __restrict__ y, const double* __restrict__ x, int64_t n) {
+__device__ __forceinline__ void add_body(BlockIdx bi_, double* __restrict__ y, const double* __restrict__ x,
+                                         int64_t n) {
   for (int64_t i = bi_.b * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)bi_.g * blockDim.x)
     y[i] += x[i];
 }
@@ -254,8 +257,8 @@ __global__ void k_add(double* __restrict__ y, const double* __restrict__ x, int6
   add_body(plain_block(), y, x, n);
 }
 
-__device__ __forceinline__ void to_f32_body(BlockIdx bi_, const double* __restrict__ x, float* __restrict__ y, int64_t n, const double* scal,
-                         int slot) {
+__device__ __forceinline__ void to_f32_body(BlockIdx bi_, const double* __restrict__ x, float* __restrict__ y,
+                                            int64_t n, const double* scal, int slot) {
   double s = 1.0;
   if (slot >= 0) {
     double nrm = sqrt(scal[slot]);
@@ -265,14 +268,13 @@ __device__ __forceinline__ void to_f32_body(BlockIdx bi_, const double* __restri
     y[i] = (float)(x[i] * s);
 }
 
-__global__ void k_to_f32(const double* __restrict__ x, float* __restrict__ y, int64_t n, const double* scal,
-                         int slot) {
+__global__ void k_to_f32(const double* __restrict__ x, float* __restrict__ y, int64_t n, const double* scal, int slot) {
   pdl_entry();
   to_f32_body(plain_block(), x, y, n, scal, slot);
 }
 
-__device__ __forceinline__ void from_f32_body(BlockIdx bi_, const float* __restrict__ x, double* __restrict__ y, int64_t n, const double* scal,
-                           int slot) {
+__device__ __forceinline__ void from_f32_body(BlockIdx bi_, const float* __restrict__ x, double* __restrict__ y,
+                                              int64_t n, const double* scal, int slot) {
   double s = 1.0;
   if (slot >= 0) {
     double nrm = sqrt(scal[slot]);
@@ -303,8 +305,7 @@ __device__ __forceinline__ double mass_at(const MassArgs& a, int64_t dof) {
 }
 
 // partial sums of M f (slot 0) and M (slot 1)
-__global__ void __launch_bounds__(kThreads) k_mass_partial(MassArgs a, const double* __restrict__ f,
-                                                           double* partial) {
+__global__ void __launch_bounds__(kThreads) k_mass_partial(MassArgs a, const double* __restrict__ f, double* partial) {
   pdl_entry();
   __shared__ double sh[kThreads];
   const int64_t total = a.Ne * a.n * a.n * a.n;
@@ -397,7 +398,8 @@ cudaError_t launch_sum(const mg_ctx* c, const double* x, int64_t n, int slot) {
 }
 
 cudaError_t launch_sub_mean(const mg_ctx* c, double* x, int64_t n, int sum_slot) {
-  launch_pdl<sub_mean_body<double>>(k_sub_mean<double>, grid_for(n), kThreads, 0, c->stream, x, n, c->ws.scal, sum_slot);
+  launch_pdl<sub_mean_body<double>>(k_sub_mean<double>, grid_for(n), kThreads, 0, c->stream, x, n, c->ws.scal,
+                                    sum_slot);
   c->nlaunch += 1;
   return cudaGetLastError();
 }

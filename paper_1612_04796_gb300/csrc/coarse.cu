@@ -40,10 +40,11 @@ __device__ __forceinline__ int64_t eb_index(int gx, int gy, int gz, const Coarse
 // TI / TO: type of the input / output vector (the FP32 hierarchy reads its
 // right-hand side and writes its solution in FP32; intermediates are FP64).
 template <typename TI, typename TO>
-__device__ __forceinline__ void coarse_axis_body(BlockIdx bi_, const TI* __restrict__ in, TO* __restrict__ out, const double* __restrict__ Q,
-                              CoarseDims d, int axis, int backward, int in_eb, int out_eb, const double* scal,
-                              int mean_slot, int scale, const double* lx, const double* ly, const double* lz,
-                              int nx0, int ny0, int nz0) {
+__device__ __forceinline__ void coarse_axis_body(BlockIdx bi_, const TI* __restrict__ in, TO* __restrict__ out,
+                                                 const double* __restrict__ Q, CoarseDims d, int axis, int backward,
+                                                 int in_eb, int out_eb, const double* scal, int mean_slot, int scale,
+                                                 const double* lx, const double* ly, const double* lz, int nx0,
+                                                 int ny0, int nz0) {
   const int Nx = d.Ng[0], Ny = d.Ng[1], Nz = d.Ng[2];
   const int64_t total = (int64_t)Nx * Ny * Nz;
   const int Na = d.Ng[axis];
@@ -76,10 +77,22 @@ __device__ __forceinline__ void coarse_axis_body(BlockIdx bi_, const TI* __restr
 template <typename TI, typename TO>
 __global__ void k_coarse_axis(const TI* __restrict__ in, TO* __restrict__ out, const double* __restrict__ Q,
                               CoarseDims d, int axis, int backward, int in_eb, int out_eb, const double* scal,
-                              int mean_slot, int scale, const double* lx, const double* ly, const double* lz,
-                              int nx0, int ny0, int nz0) {
+                              int mean_slot, int scale, const double* lx, const double* ly, const double* lz, int nx0,
+                              int ny0, int nz0) {
   pdl_entry();
-  coarse_axis_body<TI, TO>(plain_block(), in, out, Q, d, axis, backward, in_eb, out_eb, scal, mean_slot, scale, lx, ly, lz, nx0, ny0, nz0);
+  coarse_axis_body<TI, TO>(plain_block(), in, out, Q, d, axis, backward, in_eb, out_eb, scal, mean_slot, scale, lx, ly,
+                           lz, nx0, ny0, nz0);
+}
+
+// One axis pass (k_coarse_axis, or its grouped twin's body when Twin).
+template <bool Twin, typename TI, typename TO>
+void axis_pass(int blocks, cudaStream_t s, const TI* in, TO* out, const double* Q, const CoarseDims& d, int axis,
+               int backward, int in_eb, int out_eb, const double* scal, int mean_slot, int scale,
+               const double* lx = nullptr, const double* ly = nullptr, const double* lz = nullptr, int nx0 = 0,
+               int ny0 = 0, int nz0 = 0) {
+  launch_pdl<Twin ? &coarse_axis_body<TI, TO> : nullptr>(k_coarse_axis<TI, TO>, blocks, 256, 0, s, in, out, Q, d,
+                                                         axis, backward, in_eb, out_eb, scal, mean_slot, scale, lx,
+                                                         ly, lz, nx0, ny0, nz0);
 }
 
 // The six axis passes: f0 (element-blocked) -> x, y, z forward, scale, z, y, x
@@ -96,13 +109,12 @@ cudaError_t coarse_passes(const double* const Q[3], const double* const lam[3], 
   // the FP32 / double-float hierarchies' coarse solves run through the grouped
   // twins (batched solves), the FP64 hierarchy's through the plain kernels
   constexpr bool kTwin = kTwinType<TI> || kTwinType<TO>;
-  launch_pdl<kTwin ? &coarse_axis_body<TI, double> : nullptr>(k_coarse_axis<TI, double>, b, 256, 0, s, f0, A, Q[0], d, 0, 0, 1, 0, scal, mean_slot, 0, nullptr, nullptr, nullptr, 0, 0, 0);
-  launch_pdl<kTwin ? &coarse_axis_body<double, double> : nullptr>(k_coarse_axis<double, double>, b, 256, 0, s, A, B, Q[1], d, 1, 0, 0, 0, scal, -1, 0, nullptr, nullptr, nullptr, 0, 0, 0);
-  launch_pdl<kTwin ? &coarse_axis_body<double, double> : nullptr>(k_coarse_axis<double, double>, b, 256, 0, s, B, A, Q[2], d, 2, 0, 0, 0, scal, -1, 1, lam[0], lam[1], lam[2],
-                                                  nz[0], nz[1], nz[2]);
-  launch_pdl<kTwin ? &coarse_axis_body<double, double> : nullptr>(k_coarse_axis<double, double>, b, 256, 0, s, A, B, Q[2], d, 2, 1, 0, 0, scal, -1, 0, nullptr, nullptr, nullptr, 0, 0, 0);
-  launch_pdl<kTwin ? &coarse_axis_body<double, double> : nullptr>(k_coarse_axis<double, double>, b, 256, 0, s, B, A, Q[1], d, 1, 1, 0, 0, scal, -1, 0, nullptr, nullptr, nullptr, 0, 0, 0);
-  launch_pdl<kTwin ? &coarse_axis_body<double, TO> : nullptr>(k_coarse_axis<double, TO>, b, 256, 0, s, A, u0, Q[0], d, 0, 1, 0, 1, scal, -1, 0, nullptr, nullptr, nullptr, 0, 0, 0);
+  axis_pass<kTwin>(b, s, f0, A, Q[0], d, 0, 0, 1, 0, scal, mean_slot, 0);
+  axis_pass<kTwin>(b, s, A, B, Q[1], d, 1, 0, 0, 0, scal, -1, 0);
+  axis_pass<kTwin>(b, s, B, A, Q[2], d, 2, 0, 0, 0, scal, -1, 1, lam[0], lam[1], lam[2], nz[0], nz[1], nz[2]);
+  axis_pass<kTwin>(b, s, A, B, Q[2], d, 2, 1, 0, 0, scal, -1, 0);
+  axis_pass<kTwin>(b, s, B, A, Q[1], d, 1, 1, 0, 0, scal, -1, 0);
+  axis_pass<kTwin>(b, s, A, u0, Q[0], d, 0, 1, 0, 1, scal, -1, 0);
   return cudaGetLastError();
 }
 

@@ -230,8 +230,8 @@ __global__ void k_scatter(const T* __restrict__ corr, T* __restrict__ u, int64_t
 // possible covering subdomains visited in the same fixed order (-1, 0, +1 per
 // direction, x fastest) with predicates instead of per-DOF lists.
 template <typename T, int N>
-__device__ __forceinline__ void scatter_n_body(BlockIdx bi_, const T* __restrict__ corr, T* __restrict__ u,
-                                               int64_t Ne, int nx, int ny, int nz, SubShape g, int accumulate) {
+__device__ __forceinline__ void scatter_n_body(BlockIdx bi_, const T* __restrict__ corr, T* __restrict__ u, int64_t Ne,
+                                               int nx, int ny, int nz, SubShape g, int accumulate) {
   constexpr int N3 = N * N * N;
   const int64_t mxyz = (int64_t)g.mx * g.my * g.mz;
   const int64_t total = Ne * N3;
@@ -274,7 +274,7 @@ __device__ __forceinline__ void scatter_n_body(BlockIdx bi_, const T* __restrict
 
 template <typename T, int N>
 __global__ void __launch_bounds__(256) k_scatter_n(const T* __restrict__ corr, T* __restrict__ u, int64_t Ne, int nx,
-                                                   int ny, int nz, SubShape g, int accumulate) {
+                                  int ny, int nz, SubShape g, int accumulate) {
   pdl_entry();
   scatter_n_body<T, N>(plain_block(), corr, u, Ne, nx, ny, nz, g, accumulate);
 }
@@ -285,8 +285,8 @@ __global__ void __launch_bounds__(256) k_scatter_n(const T* __restrict__ corr, T
 // address and its value is replaced by zero), then summed in the same order
 // as k_scatter_n, so the two kernels give identical bits.
 template <typename T, int N>
-__device__ __forceinline__ void scatter_n2_body(BlockIdx bi_, const T* __restrict__ corr, T* __restrict__ u, int64_t Ne,
-                                                    int nx, int ny, int nz, SubShape g, int accumulate) {
+__device__ __forceinline__ void scatter_n2_body(BlockIdx bi_, const T* __restrict__ corr, T* __restrict__ u,
+                                                int64_t Ne, int nx, int ny, int nz, SubShape g, int accumulate) {
   constexpr int N3 = N * N * N;
   const int64_t mxyz = (int64_t)g.mx * g.my * g.mz;
   const int64_t total = Ne * N3;
@@ -349,8 +349,8 @@ __device__ __forceinline__ void scatter_n2_body(BlockIdx bi_, const T* __restric
 }
 
 template <typename T, int N>
-__global__ void __launch_bounds__(256) k_scatter_n2(const T* __restrict__ corr, T* __restrict__ u, int64_t Ne,
-                                                    int nx, int ny, int nz, SubShape g, int accumulate) {
+__global__ void __launch_bounds__(256) k_scatter_n2(const T* __restrict__ corr, T* __restrict__ u, int64_t Ne, int nx,
+                                  int ny, int nz, SubShape g, int accumulate) {
   pdl_entry();
   scatter_n2_body<T, N>(plain_block(), corr, u, Ne, nx, ny, nz, g, accumulate);
 }
@@ -452,20 +452,30 @@ cudaError_t launch_scatter(const mg_ctx* c, int l, T* u, int accumulate) {
   const bool two = 2 * lv.no[0] <= lv.n && 2 * lv.no[1] <= lv.n && 2 * lv.no[2] <= lv.n;
   if (two) {
     switch (lv.n) {
-#define MGDG_SC2(N) case N: launch_pdl<kTwinType<T> ? &scatter_n2_body<T, N> : nullptr>(k_scatter_n2<T, N>, eb, 256, 0, c->stream, corr, u, c->Ne, c->ne[0], c->ne[1], c->ne[2], g, accumulate); return cudaGetLastError();
+#define MGDG_SC2(N)                                                                                           \
+  case N:                                                                                                     \
+    launch_pdl<kTwinType<T> ? &scatter_n2_body<T, N> : nullptr>(k_scatter_n2<T, N>, eb, 256, 0, c->stream, corr, u, \
+                                                                c->Ne, c->ne[0], c->ne[1], c->ne[2], g,          \
+                                                                accumulate);                                     \
+    return cudaGetLastError();
       MGDG_SC2(3) MGDG_SC2(5) MGDG_SC2(9) MGDG_SC2(17) MGDG_SC2(33)
 #undef MGDG_SC2
       default: break;
     }
   }
   switch (lv.n) {
-#define MGDG_SC(N) case N: launch_pdl<kTwinType<T> ? &scatter_n_body<T, N> : nullptr>(k_scatter_n<T, N>, eb, 256, 0, c->stream, corr, u, c->Ne, c->ne[0], c->ne[1], c->ne[2], g, accumulate); return cudaGetLastError();
+#define MGDG_SC(N)                                                                                            \
+  case N:                                                                                                     \
+    launch_pdl<kTwinType<T> ? &scatter_n_body<T, N> : nullptr>(k_scatter_n<T, N>, eb, 256, 0, c->stream, corr, u,   \
+                                                               c->Ne, c->ne[0], c->ne[1], c->ne[2], g,           \
+                                                               accumulate);                                      \
+    return cudaGetLastError();
     MGDG_SC(3) MGDG_SC(5) MGDG_SC(9) MGDG_SC(17) MGDG_SC(33)
 #undef MGDG_SC
     default: break;
   }
-  launch_pdl<kTwinType<T> ? &scatter_body<T> : nullptr>(k_scatter<T>, (int)blocks, 256, 0, c->stream, corr, u, c->Ne, c->ne[0], c->ne[1], c->ne[2], lv.n, g,
-                                                    accumulate);
+  launch_pdl<kTwinType<T> ? &scatter_body<T> : nullptr>(k_scatter<T>, (int)blocks, 256, 0, c->stream, corr, u, c->Ne,
+                                                        c->ne[0], c->ne[1], c->ne[2], lv.n, g, accumulate);
   return cudaGetLastError();
 }
 

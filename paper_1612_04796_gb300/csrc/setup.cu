@@ -325,7 +325,7 @@ __device__ double line_entry(const BasisSmem& sm, const SetupParams& q, int da, 
 }
 
 __global__ void __launch_bounds__(kSetupThreads) k_setup_level(SetupBatch batch, double* tab, double* scratch,
-                                                             int64_t scratch_per_block, int* status) {
+                                  int64_t scratch_per_block, int* status) {
   __shared__ BasisSmem sm;
   const SetupParams q = batch.p[blockIdx.x];
   const int t = threadIdx.x, nt = blockDim.x;

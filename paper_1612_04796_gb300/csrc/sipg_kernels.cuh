@@ -336,7 +336,8 @@ cudaError_t launch_sipg_n(const mg_ctx* c, OpArgs<T>& a) {
       const int64_t nblk = c->Ne * chunks;
       const int blocks = (int)(nblk < 152 * 16 ? nblk : 152 * 16);
       for (int dir = 0; dir < 3; ++dir) {
-        launch_pdl<kTwinType<T> ? &sipg_dir_body<T, N, NP> : nullptr>(k_sipg_dir<T, N, NP>, blocks, threads, 0, c->stream, a, dir, chunks);
+        launch_pdl<kTwinType<T> ? &sipg_dir_body<T, N, NP> : nullptr>(k_sipg_dir<T, N, NP>, blocks, threads, 0,
+                                                                      c->stream, a, dir, chunks);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
       }

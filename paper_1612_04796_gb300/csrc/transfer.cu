@@ -16,8 +16,9 @@ namespace {
 // per-element tensor with extents (d0, d1, d2), x fastest.
 // Mat(o, t) = transpose ? J[t * ldj + o] : J[o * ldj + t].
 template <typename T>
-__device__ __forceinline__ void contract_axis_body(BlockIdx bi_, const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ J, int64_t Ne,
-                                int d0, int d1, int d2, int axis, int nout, int ldj, int transpose, int accumulate) {
+__device__ __forceinline__ void contract_axis_body(BlockIdx bi_, const T* __restrict__ in, T* __restrict__ out,
+                                                   const T* __restrict__ J, int64_t Ne, int d0, int d1, int d2,
+                                                   int axis, int nout, int ldj, int transpose, int accumulate) {
   int o0 = d0, o1 = d1, o2 = d2;
   if (axis == 0) o0 = nout; else if (axis == 1) o1 = nout; else o2 = nout;
   const int64_t in_sz = (int64_t)d0 * d1 * d2, out_sz = (int64_t)o0 * o1 * o2;
@@ -57,8 +58,9 @@ cudaError_t contract(const mg_ctx* c, const T* in, T* out, const T* J, int d0, i
   int64_t total = c->Ne * (int64_t)o0 * o1 * o2;
   int64_t blocks = (total + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;
-  launch_pdl<kTwinType<T> ? &contract_axis_body<T> : nullptr>(k_contract_axis<T>, (int)blocks, 256, 0, c->stream, in, out, J, c->Ne, d0, d1, d2, axis, nout, ldj, transpose,
-                                                         accumulate);
+  launch_pdl<kTwinType<T> ? &contract_axis_body<T> : nullptr>(k_contract_axis<T>, (int)blocks, 256, 0, c->stream, in,
+                                                              out, J, c->Ne, d0, d1, d2, axis, nout, ldj, transpose,
+                                                              accumulate);
   c->nlaunch += 1;
   return cudaGetLastError();
 }
@@ -115,7 +117,7 @@ __device__ void cs_split(Get get, T* AE, T* AO) {
 // intermediates in shared memory.
 template <typename T, int NF, int NC>
 __device__ __forceinline__ void prolong_fused_body(BlockIdx bi_, const T* __restrict__ uc, T* __restrict__ uf,
-                                                       const T* __restrict__ J, int64_t Ne) {
+                                                   const T* __restrict__ J, int64_t Ne) {
   constexpr int nei = (NC + 1) / 2, neo = (NF + 1) / 2;
   __shared__ T sE[neo * nei], sO[(NF / 2) * (NC / 2) + 1];
   __shared__ T sB[NF * NC * NC], sC[NF * NF * NC];
@@ -157,7 +159,7 @@ __device__ __forceinline__ void prolong_fused_body(BlockIdx bi_, const T* __rest
 
 template <typename T, int NF, int NC>
 __global__ void __launch_bounds__(128) k_prolong_fused(const T* __restrict__ uc, T* __restrict__ uf,
-                                                       const T* __restrict__ J, int64_t Ne) {
+                                  const T* __restrict__ J, int64_t Ne) {
   pdl_entry();
   prolong_fused_body<T, NF, NC>(plain_block(), uc, uf, J, Ne);
 }
@@ -165,7 +167,7 @@ __global__ void __launch_bounds__(128) k_prolong_fused(const T* __restrict__ uc,
 // Fused restriction f_c = (J^T (x) J^T (x) J^T) r_f per element.
 template <typename T, int NF, int NC>
 __device__ __forceinline__ void restrict_fused_body(BlockIdx bi_, const T* __restrict__ rf, T* __restrict__ fc,
-                                                        const T* __restrict__ J, int64_t Ne) {
+                                                    const T* __restrict__ J, int64_t Ne) {
   constexpr int nei = (NF + 1) / 2, neo = (NC + 1) / 2;
   __shared__ T sE[neo * nei], sO[(NC / 2) * (NF / 2) + 1];
   __shared__ T sB[NF * NC * NC], sC[NF * NF * NC];
@@ -207,7 +209,7 @@ __device__ __forceinline__ void restrict_fused_body(BlockIdx bi_, const T* __res
 
 template <typename T, int NF, int NC>
 __global__ void __launch_bounds__(128) k_restrict_fused(const T* __restrict__ rf, T* __restrict__ fc,
-                                                        const T* __restrict__ J, int64_t Ne) {
+                                  const T* __restrict__ J, int64_t Ne) {
   pdl_entry();
   restrict_fused_body<T, NF, NC>(plain_block(), rf, fc, J, Ne);
 }
@@ -225,16 +227,31 @@ const df64* table_of<df64>(const mg_ctx* c) { return c->ws.tabdf; }
 
 inline int fused_blocks(int64_t Ne) { return (int)(Ne < 152 * 12 ? Ne : 152 * 12); }
 
+template <typename T, int NF, int NC>
+cudaError_t restrict_fused(const mg_ctx* c, const T* r_fine, T* f_coarse, const T* J) {
+  launch_pdl<kTwinType<T> ? &restrict_fused_body<T, NF, NC> : nullptr, 128>(
+      k_restrict_fused<T, NF, NC>, fused_blocks(c->Ne), 128, 0, c->stream, r_fine, f_coarse, J, c->Ne);
+  c->nlaunch += 1;
+  return cudaGetLastError();
+}
+
+template <typename T, int NF, int NC>
+cudaError_t prolong_fused(const mg_ctx* c, const T* u_coarse, T* u_fine, const T* J) {
+  launch_pdl<kTwinType<T> ? &prolong_fused_body<T, NF, NC> : nullptr, 128>(
+      k_prolong_fused<T, NF, NC>, fused_blocks(c->Ne), 128, 0, c->stream, u_coarse, u_fine, J, c->Ne);
+  c->nlaunch += 1;
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_restrict(const mg_ctx* c, int l, const T* r_fine, T* f_coarse) {
   const int nf = c->lev[l].n, nc = c->lev[l - 1].n;
   const T* J = table_of<T>(c) + c->lev[l].J;
-  const int nb = fused_blocks(c->Ne);
   switch (nf) {
-    case 3: launch_pdl<kTwinType<T> ? &restrict_fused_body<T, 3, 2> : nullptr, 128>(k_restrict_fused<T, 3, 2>, nb, 128, 0, c->stream, r_fine, f_coarse, J, c->Ne); c->nlaunch += 1; return cudaGetLastError();
-    case 5: launch_pdl<kTwinType<T> ? &restrict_fused_body<T, 5, 3> : nullptr, 128>(k_restrict_fused<T, 5, 3>, nb, 128, 0, c->stream, r_fine, f_coarse, J, c->Ne); c->nlaunch += 1; return cudaGetLastError();
-    case 9: launch_pdl<kTwinType<T> ? &restrict_fused_body<T, 9, 5> : nullptr, 128>(k_restrict_fused<T, 9, 5>, nb, 128, 0, c->stream, r_fine, f_coarse, J, c->Ne); c->nlaunch += 1; return cudaGetLastError();
-    case 17: launch_pdl<kTwinType<T> ? &restrict_fused_body<T, 17, 9> : nullptr, 128>(k_restrict_fused<T, 17, 9>, nb, 128, 0, c->stream, r_fine, f_coarse, J, c->Ne); c->nlaunch += 1; return cudaGetLastError();
+    case 3: return restrict_fused<T, 3, 2>(c, r_fine, f_coarse, J);
+    case 5: return restrict_fused<T, 5, 3>(c, r_fine, f_coarse, J);
+    case 9: return restrict_fused<T, 9, 5>(c, r_fine, f_coarse, J);
+    case 17: return restrict_fused<T, 17, 9>(c, r_fine, f_coarse, J);
     default: break;
   }
   T* t1 = static_cast<T*>(c->ws.corr);
@@ -250,12 +267,11 @@ template <typename T>
 cudaError_t launch_prolong(const mg_ctx* c, int l, const T* u_coarse, T* u_fine) {
   const int nf = c->lev[l].n, nc = c->lev[l - 1].n;
   const T* J = table_of<T>(c) + c->lev[l].J;
-  const int nb = fused_blocks(c->Ne);
   switch (nf) {
-    case 3: launch_pdl<kTwinType<T> ? &prolong_fused_body<T, 3, 2> : nullptr, 128>(k_prolong_fused<T, 3, 2>, nb, 128, 0, c->stream, u_coarse, u_fine, J, c->Ne); c->nlaunch += 1; return cudaGetLastError();
-    case 5: launch_pdl<kTwinType<T> ? &prolong_fused_body<T, 5, 3> : nullptr, 128>(k_prolong_fused<T, 5, 3>, nb, 128, 0, c->stream, u_coarse, u_fine, J, c->Ne); c->nlaunch += 1; return cudaGetLastError();
-    case 9: launch_pdl<kTwinType<T> ? &prolong_fused_body<T, 9, 5> : nullptr, 128>(k_prolong_fused<T, 9, 5>, nb, 128, 0, c->stream, u_coarse, u_fine, J, c->Ne); c->nlaunch += 1; return cudaGetLastError();
-    case 17: launch_pdl<kTwinType<T> ? &prolong_fused_body<T, 17, 9> : nullptr, 128>(k_prolong_fused<T, 17, 9>, nb, 128, 0, c->stream, u_coarse, u_fine, J, c->Ne); c->nlaunch += 1; return cudaGetLastError();
+    case 3: return prolong_fused<T, 3, 2>(c, u_coarse, u_fine, J);
+    case 5: return prolong_fused<T, 5, 3>(c, u_coarse, u_fine, J);
+    case 9: return prolong_fused<T, 9, 5>(c, u_coarse, u_fine, J);
+    case 17: return prolong_fused<T, 17, 9>(c, u_coarse, u_fine, J);
     default: break;
   }
   T* t1 = static_cast<T*>(c->ws.corr);
