@@ -6,6 +6,7 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <atomic>
 #include <cuda/std/tuple>
 #include <string>
 #include <type_traits>
@@ -129,11 +130,13 @@ cudaError_t launch_twin(const void* const* a, const unsigned* grid, int n, dim3 
     g.start[i + 1] = g.start[i] + (int)grid[i];
   }
   auto* twin = k_grouped<LB, Body, KArgs...>;
-  static size_t smem_set = 48 * 1024;  // dynamic shared memory the twin has been allowed so far
-  if (smem > smem_set) {
+  static std::atomic<size_t> smem_set{48 * 1024};  // dynamic shared memory the twin is allowed so far
+  if (smem > smem_set.load()) {
     const cudaError_t e = cudaFuncSetAttribute(twin, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    smem_set = smem;
+    size_t cur = smem_set.load();
+    while (cur < smem && !smem_set.compare_exchange_weak(cur, smem)) {
+    }
   }
   void* ptrs[1] = {(void*)&g};
   return launch_pdl_now((const void*)twin, dim3(g.start[n]), block, smem, s, ptrs);

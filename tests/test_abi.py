@@ -128,3 +128,24 @@ def test_max_overlap_rejections(lib):
     assert st == 1 and not ctx.value
     st, ctx = _setup(lib, P=4, counts=(4, 4, 4), lengths=lengths, overlap_mode=3, overlap_frac=0.08)
     assert st == 1 and not ctx.value
+
+
+def test_batch_solve_argument_checks(lib):
+    """mg_solve_batch rejects bad arguments on the host (no CUDA call): no
+    contexts, a count out of range, a context without workspace."""
+    st, ctx = _setup(lib)
+    assert st == 0
+    P = ctypes.c_void_p
+    ctxs = (P * 1)(ctx.value)
+    vec = (P * 1)(P(256))
+    its = (ctypes.c_int * 1)()
+    rel = (ctypes.c_double * 1)()
+    sts = (ctypes.c_int * 1)()
+    args = (ctypes.cast(vec, P), ctypes.cast(vec, P), 1e-10, 10, ctypes.cast(its, P), ctypes.cast(rel, P),
+            ctypes.cast(sts, P))
+    assert lib.mg_solve_batch(None, 1, *args) == 1                       # MG_EINVAL
+    assert lib.mg_solve_batch(ctypes.cast(ctxs, P), 0, *args) == 1
+    assert lib.mg_solve_batch(ctypes.cast(ctxs, P), 17, *args) == 1
+    assert lib.mg_solve_batch(ctypes.cast(ctxs, P), 1, *args) == 5       # MG_ENOTREADY: not bound
+    assert lib.mg_batch_launches(ctx) == 0
+    lib.mg_destroy(ctx)
