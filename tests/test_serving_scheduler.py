@@ -257,3 +257,20 @@ def test_library_footprint_is_host_only(lib):
     fb, fs = srv.footprint(big), srv.footprint(small)
     assert fb > 3 * 8 * big.dofs and fs > 3 * 8 * small.dofs and fb > fs
     srv.close()
+
+
+def test_server_options_are_validated(lib):
+    """mg_server_create rejects bad options on the host (custom executor: no
+    CUDA call): slots, policy, batch size."""
+    fn = _lib.EXECUTE_FN(lambda *a: 0)
+    for field, value in (("slots", 0), ("slots", 257), ("policy", 2), ("batch_max", 0), ("batch_max", 17),
+                         ("maxit", 0), ("max_wait", -1.0)):
+        o = _lib.MgServerOpts()
+        lib.mg_server_default_opts(ctypes.byref(o))
+        o.execute = fn
+        setattr(o, field, value)
+        h = ctypes.c_void_p()
+        assert lib.mg_server_create(ctypes.byref(o), ctypes.byref(h)) == _lib.MG_EINVAL, field
+    o = _lib.MgServerOpts()
+    lib.mg_server_default_opts(ctypes.byref(o))
+    assert (o.slots, o.policy, o.maxit, o.use_cg, o.batch_max, o.batch_dofs) == (8, 0, 400, 1, 16, 1 << 20)
