@@ -17,6 +17,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "mg_internal.h"
 
 using namespace mgdg;
@@ -172,10 +174,22 @@ double read_scalar(mg_ctx* c, int slot, cudaError_t* err) {
 }
 
 // CUDA events around one kernel group when profiling is on (mg_profile).
+// NVTX ranges (tracing): whole solves and every kernel group of the cycle
+// appear by name in a profiler's timeline; without a tool attached the calls
+// return at once.
+const char* const kRangeNames[kProfKinds] = {"smoother FDM", "smoother scatter", "operator", "restriction",
+                                             "prolongation", "coarse solve", "vector pass"};
+
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
+
 struct ProfScope {
   const mg_ctx* c;
   long idx = -1;
-  ProfScope(const mg_ctx* c_, int kind, int level) : c(c_) {
+  NvtxRange range;
+  ProfScope(const mg_ctx* c_, int kind, int level) : c(c_), range(kRangeNames[kind]) {
     if (!c->prof_on) return;
     if (c->prof_used == c->prof.size()) {
       mg_ctx::ProfRec r{kind, level, nullptr, nullptr};
@@ -1128,6 +1142,7 @@ mg_status mg_solve(mg_ctx* c, double* u, const double* f, double tol, int maxit,
   mg_status s = need_ready(c);
   if (s != MG_OK) return s;
   if (!u || !f || u == f || maxit < 0 || !(tol >= 0.0)) return fail(c, MG_EINVAL, "bad arguments");
+  NvtxRange range(use_cg ? "mg_solve MG-CG" : "mg_solve MG");
   return solve_impl(c, u, f, tol, maxit, use_cg ? 1 : 0, iters, relres, history);
 }
 
@@ -1213,7 +1228,11 @@ mg_status mg_solve_batch(mg_ctx* const* ctxs, int count, double* const* u, const
   }
   std::string err;
   long long launches = 0;
-  const mg_status st = solve_batch_impl(ms, s, tol, maxit, &launches, &err);
+  mg_status st;
+  {
+    NvtxRange range("mg_solve_batch");
+    st = solve_batch_impl(ms, s, tol, maxit, &launches, &err);
+  }
   for (int i = 0; i < count; ++i) {
     ctxs[i]->stream = saved[i];
     ctxs[i]->prof_on = prof[i];

@@ -3,6 +3,7 @@
 // solver context and pool memory.  Host code only; the solves call the
 // library's entry points.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 #include <stdio.h>
 #include <string.h>
@@ -179,6 +180,9 @@ int gpu_finish(mg_server* s, Job& job, int slot, GpuRun& g) {
 // more with mg_solve_batch.
 void gpu_solve(mg_server* s, std::vector<std::shared_ptr<Job>>& group, int slot, bool batched) {
   const int n = (int)group.size();
+  char label[64];  // NVTX range of the worker's solve (tracing)
+  snprintf(label, sizeof(label), "serve slot %d: %d request%s", slot, n, n > 1 ? "s" : "");
+  nvtxRangePushA(label);
   std::vector<GpuRun> runs(n);
   for (int i = 0; i < n; ++i) gpu_prepare(s, *group[i], slot, runs[i]);
   std::vector<int> ok;
@@ -214,6 +218,7 @@ void gpu_solve(mg_server* s, std::vector<std::shared_ptr<Job>>& group, int slot,
     }
   }
   for (int i = 0; i < n; ++i) group[i]->res.status = gpu_finish(s, *group[i], slot, runs[i]);
+  nvtxRangePop();
 }
 
 void worker(mg_server* s, int slot) {

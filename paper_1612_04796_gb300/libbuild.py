@@ -64,7 +64,7 @@ def build(force=False, verbose=False, extra_flags=()):
     with concurrent.futures.ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 4)) as ex:
         objs = list(ex.map(compile_one, jobs))
     if force or any(j[2] for j in jobs) or not os.path.exists(LIB):
-        cmd = [cc] + ARCH + ["-shared", "-o", LIB] + objs + ["-lcudart", "-lpthread"]
+        cmd = [cc] + ARCH + ["-shared", "-o", LIB] + objs + ["-lcudart", "-lpthread", "-ldl"]
         res = subprocess.run(cmd, capture_output=True, text=True)
         if res.returncode != 0:
             raise RuntimeError("link failed:\n%s%s" % (res.stdout, res.stderr))
