@@ -566,7 +566,7 @@ mg_status solve_impl(mg_ctx* c, double* u, const double* f, double tol, int maxi
 
 // Batched MG-CG (mg_solve_batch).  Every problem's launches are recorded and
 // merged into grouped launches on the first problem's stream; host
-// synchronisation once per half iteration for all problems together.
+// synchronisation once per iteration for all problems together.
 struct BatchMember {
   mg_ctx* c;
   double *x, *r, *z, *p, *q;
