@@ -238,15 +238,15 @@ mg_status mg_solve_host(mg_ctx* ctx, double* u_host, const double* f_host, doubl
  *            MG_ENOCONV at maxit or on a non-finite residual, MG_EINVAL on a
  *            non-finite initial residual, MG_ECUDA if a tensor-core wait ran out)
  * Every launch goes to the stream of ctxs[0] (the other contexts' streams are
- * not used); the call synchronises it once per iteration (to read the residual
- * norms of all problems together).  Each problem
- * gets the block decomposition and reduction order of its own mg_solve; the
- * batched kernels are separate compilations of the same code (a compiler may
- * contract multiply-adds differently), so results agree with mg_solve to
- * rounding, and bit for bit with any other batch that contains the problem
- * (its result does not depend on the other problems).  Returns MG_EINVAL / MG_ENOTREADY
- * for bad arguments, MG_ECUDA if a CUDA call failed (message on ctxs[0]),
- * else MG_OK (per-problem outcomes in status).
+ * not used); the call synchronises it once per iteration, to read the
+ * residual norms of all problems together.  Each problem gets the block
+ * decomposition and reduction order of its own mg_solve; the batched kernels
+ * are separate compilations of the same code (a compiler may contract
+ * multiply-adds differently), so results agree with mg_solve to rounding, and
+ * bit for bit with any other batch that contains the problem (its result does
+ * not depend on the other problems).  Returns MG_EINVAL / MG_ENOTREADY for bad
+ * arguments, MG_ECUDA if a CUDA call failed (message on ctxs[0]), else MG_OK
+ * (per-problem outcomes in status).
  */
 mg_status mg_solve_batch(mg_ctx* const* ctxs, int count, double* const* u, const double* const* f, double tol,
                          int maxit, int* iters, double* relres, int* status);
