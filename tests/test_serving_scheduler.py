@@ -274,3 +274,11 @@ def test_server_options_are_validated(lib):
     o = _lib.MgServerOpts()
     lib.mg_server_default_opts(ctypes.byref(o))
     assert (o.slots, o.policy, o.maxit, o.use_cg, o.batch_max, o.batch_dofs) == (8, 0, 400, 1, 16, 1 << 20)
+
+
+def test_small_request_stream_shape():
+    """The saturated small-request stream: sizes, orders and arrival rate as asked."""
+    reqs = request_stream(seed=5, n_requests=512, rate=5000.0, sizes=(4, 8), orders=(2, 4, 8))
+    assert {r.counts[0] for r in reqs} <= {4, 8} and {r.P for r in reqs} <= {2, 4, 8}
+    assert max(r.dofs for r in reqs) <= 8 ** 3 * 9 ** 3
+    assert 0.05 < reqs[-1].arrival < 0.2  # ~512 / 5000 per second
