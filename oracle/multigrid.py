@@ -55,7 +55,7 @@ def max_overlap_widths(mesh, frac):
 
 class Level:
     def __init__(self, mesh, P_l, factor, n_o=None, delta_rel=None, smoother=True, profile="quintic",
-                 max_frac=None):
+                 max_frac=None, delta_rule=None):
         self.P = P_l
         self.A = assemble(mesh, P_l, factor)
         self.N = self.A.shape[0]
@@ -67,10 +67,15 @@ class Level:
                 delta = deltas
             else:
                 self.n_o = level_layers(P_l, n_o, delta_rel)
-                if delta_rel is not None:
+                # weight half-width: the strip itself for a geometric overlap,
+                # else (or on request) a node-based reading (layer_delta)
+                rule = delta_rule or ("strip" if delta_rel is not None else "mid")
+                if rule == "strip":
+                    if delta_rel is None:
+                        raise ValueError("the strip reading needs a geometric overlap")
                     delta = min(2.0 * delta_rel, 1.0)
                 else:
-                    delta = layer_delta(P_l, self.n_o)
+                    delta = layer_delta(P_l, self.n_o, rule)
             self.delta = delta
             self.smoother = SchwarzSmoother(self.A, mesh, P_l, self.n_o, delta, profile)
 
@@ -78,14 +83,15 @@ class Level:
 class Hierarchy:
     """All levels of the polynomial multigrid method for one mesh and order P."""
 
-    def __init__(self, mesh, P, factor=2.0, n_o=1, delta_rel=None, profile="quintic", max_frac=None):
+    def __init__(self, mesh, P, factor=2.0, n_o=1, delta_rel=None, profile="quintic", max_frac=None,
+                 delta_rule=None):
         L = int(round(math.log2(P)))
         if 2 ** L != P:
             raise ValueError("P must be a power of two")
         self.mesh = mesh
         self.L = L
         self.levels = [Level(mesh, 2 ** l, factor, n_o, delta_rel, smoother=(l >= 1), profile=profile,
-                             max_frac=max_frac) for l in range(L + 1)]
+                             max_frac=max_frac, delta_rule=delta_rule) for l in range(L + 1)]
         self.I3 = [None] + [interpolation_matrix(2 ** (l - 1), 2 ** l) for l in range(1, L + 1)]
         self.Ne = mesh.num_elements
 

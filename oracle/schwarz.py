@@ -94,21 +94,28 @@ def hat_weight(xi_h, delta, profile="quintic"):
     return 1.0 - quintic(t)
 
 
-def layer_delta(P, n_o):
+def layer_delta(P, n_o, rule="mid"):
     """Overlap half-width (reference units) used for the weights when the
-    overlap is prescribed as N_O node layers.
+    strip holds N_O node layers.
 
-    Reading (parity unpinned for N_O >= 2): the midpoint between the distances
-    of the last included (k = N_O - 1) and the first excluded (k = N_O)
-    neighbour node, capped at 1 (delta_O = dx/2).  Every choice between those two
-    nodes gives the same weights for N_O = 1: face nodes 1/2, the rest of the core
-    1 (this is the only case Table 1 pins, rows 1 vs 3 at P = 4)."""
+    Readings (parity unpinned for N_O >= 2; the definition is deferred to an
+    earlier paper): rule "mid", the midpoint between the distances of the last
+    included (k = N_O - 1) and the first excluded (k = N_O) neighbour node;
+    rule "node", the distance of the last included node, so that the weight
+    function reaches 0 on the outermost node of the subdomain.  Both are capped
+    at 1 (delta_O = dx/2).  Every such choice gives the same weights for
+    N_O = 1: face nodes 1/2, the rest of the core 1 (the only case Table 1
+    pins, rows 1 vs 3 at P = 4)."""
     xi = gll_nodes(P)
     d = 1.0 + xi
     if n_o <= 0:
         return 0.0
     if n_o >= len(d):
         return 1.0
+    if rule == "node":
+        return min(d[n_o - 1], 1.0)
+    if rule != "mid":
+        raise ValueError(rule)
     return min(0.5 * (d[n_o - 1] + d[n_o]), 1.0)
 
 
@@ -215,19 +222,48 @@ class SchwarzSmoother:
             if diff > 1e-13 * ref:
                 raise AssertionError("A_ss differs between subdomains: %g" % diff)
         self.m3 = len(I0)
+        # A_ss is badly scaled at high order (the GLL mass weights span two
+        # orders of magnitude per direction, so its diagonal spans six): the
+        # factorisation is applied to the symmetrically scaled matrix
+        # D A_ss D, D = diag(A_ss)^(-1/2), whose condition number is far
+        # smaller, and every solve ends with iterative refinement steps
+        # x += A_ss^{-1} (r - A_ss x) (plain FP64 residuals).
+        self.dscale = 1.0 / np.sqrt(Ass.diagonal())
+        Dm = sp.diags(self.dscale)
+        Asc = (Dm @ Ass @ Dm).tocsc()
         if self.m3 <= dense_limit:
-            self.chol = sla.cho_factor(Ass.toarray(), lower=True)
+            self.chol = sla.cho_factor(Asc.toarray(), lower=True)
             self.lu = None
         else:
             self.chol = None
-            self.lu = spl.splu(sp.csc_matrix(Ass))
+            self.lu = spl.splu(Asc)
         self.Ass = Ass
 
-    def local_solve(self, rs):
-        """A_ss^{-1} applied to the columns of rs (m^3 x k)."""
-        if self.chol is not None:
-            return sla.cho_solve(self.chol, rs)
-        return self.lu.solve(rs)
+    def _factor_solve(self, rs):
+        b = rs * (self.dscale[:, None] if rs.ndim == 2 else self.dscale)
+        y = sla.cho_solve(self.chol, b) if self.chol is not None else self.lu.solve(b)
+        return y * (self.dscale[:, None] if rs.ndim == 2 else self.dscale)
+
+    def local_solve(self, rs, max_refine=40):
+        """A_ss^{-1} applied to the columns of rs (m^3 x k): a direct solve
+        with the scaled factorisation, then refinement steps while the largest
+        relative residual of the columns still falls by at least half (at
+        P = 32 the first solve leaves a residual of about 2e-2 and the
+        refinement reaches the FP64 rounding level, about 5e-16, in ~15 steps)."""
+        def worst(res):
+            return float(np.max(np.linalg.norm(res, axis=0) / np.maximum(np.linalg.norm(rs, axis=0), 1e-300)))
+
+        x = self._factor_solve(rs)
+        res = rs - self.Ass @ x
+        prev = np.inf
+        for _ in range(max_refine):
+            rel = worst(res)
+            if rel <= 1e-15 or rel > 0.5 * prev:
+                break
+            prev = rel
+            x = x + self._factor_solve(res)
+            res = rs - self.Ass @ x
+        return x
 
     def correction(self, r):
         """sum_s R_s^T (W_s A_ss^{-1} R_s r)."""

@@ -127,3 +127,16 @@ def test_table1_row5_wide_overlap_p4():
     for prof in ("quintic", "linear"):
         got = _rate(4, 6, "MG", delta_rel=0.5, profile=prof)
         assert abs(got - 2.26) <= 0.15 * 2.26, (prof, got)
+
+
+@pytest.mark.parametrize("row,P,col,solver", [(5, 8, 1, "MG"), (6, 4, 0, "MG-CG")])
+def test_table1_wide_overlap_rows(row, P, col, solver):
+    """Table 1 row 5 at P = 8 (MG, delta_O = dx/2: N_O = 2, 3, 5 on levels
+    P_l = 2, 4, 8) and row 6 at P = 4 (MG-CG, N_O = 2, 3), default weights
+    (quintic transition across the strip, half-width = the strip).  These
+    rows have several node layers in the strip, so they test the weight
+    reading beyond N_O = 1.  6^3 mesh (the rate is mesh independent, Section
+    4.1); band 10 percent (the oracle gives 2.85 vs 2.76 and 2.23 vs 2.29)."""
+    ref = TABLE1["rows"][row - 1]
+    got = _rate(P, 6, solver, delta_rel=0.5)
+    assert abs(got - ref["rbar"][col]) <= 0.10 * ref["rbar"][col], (got, ref["rbar"][col])

@@ -134,3 +134,33 @@ def test_subdomain_matrices_translation_invariant_and_spd():
     sm = SchwarzSmoother(A, mesh, P, 2, layer_delta(P, 2), check=10 ** 6)  # checks every subdomain
     ev = np.linalg.eigvalsh(sm.Ass.toarray())
     assert ev[0] > 0
+
+
+@pytest.mark.parametrize("P,n_o", [(8, 3), (16, 1)])
+def test_local_solve_reaches_rounding_level(P, n_o):
+    """The oracle's direct subdomain solve (scaled factorisation plus
+    refinement) solves A_ss x = r_s to the FP64 rounding level: residual
+    below 1e-14 of the right-hand side on every column, at high order where
+    A_ss is badly scaled (Section 3.1, Eq. subproblem)."""
+    mesh = Mesh((1.0, 1.5, 0.7), (3, 3, 3))
+    A = assemble(mesh, P)
+    sm = SchwarzSmoother(A, mesh, P, n_o, layer_delta(P, n_o), check=2)
+    rs = inputs.gaussian(sm.m3 * 3, 60).reshape(sm.m3, 3)
+    x = sm.local_solve(rs)
+    res = np.linalg.norm(rs - sm.Ass @ x, axis=0) / np.linalg.norm(rs, axis=0)
+    assert np.all(res < 1e-14), res
+
+
+def test_layer_delta_readings():
+    """The two node-based readings of the weight half-width: "node" is the
+    distance of the outermost included neighbour node (its weight becomes 0),
+    "mid" lies halfway to the first excluded node; for N_O = 1 both give the
+    same weights (face nodes 1/2)."""
+    from oracle.gll import gll_nodes
+    d = 1.0 + gll_nodes(16)
+    assert layer_delta(16, 3, "node") == pytest.approx(d[2])
+    assert layer_delta(16, 3, "mid") == pytest.approx(0.5 * (d[2] + d[3]))
+    assert hat_weight(1.0 + layer_delta(16, 3, "node"), layer_delta(16, 3, "node")) == 0.0
+    for rule in ("node", "mid"):
+        de, ii, w = subdomain_1d(8, 1, layer_delta(8, 1, rule))
+        np.testing.assert_allclose(w, [0.5] + [0.5] + [1.0] * 7 + [0.5] + [0.5])
