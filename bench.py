@@ -9,8 +9,11 @@ in HBM when timing starts; L2 is flushed (256 MiB write) between steps.
 
 Also reported: the same solves through the host-buffer API (e2e), the
 mixed-precision solver (FP32 V-cycle inside FP64 CG) on the same problem, the
-smoother kernel against its FP64 roofline, and the FP64 CPU oracle timed on
-the host cores on a bounded sample of the workload.
+level kernels against their rooflines (the FP64 / FP32 pipe at the sampled
+clock for the fast diagonalisation, HBM for the residual and the scatter),
+the anisotropic 48x8x8, P = 16 box (mixed MG-CG, N_O = 1, 2, 4; key "c3"),
+the 512-request serving stream (N_O = 1 and 4; key "serving"), and the FP64
+CPU oracle timed on the host cores on a bounded sample of the workload.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mg|reference]
 Multi-GPU (N > 1, launched with torch.distributed.run): every rank solves its
@@ -111,6 +114,8 @@ def parse_args():
     ap.add_argument("--impl", default="mg", choices=["mg", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip e2e / mixed / roofline legs")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the 48x8x8, P=16 (c3) and serving-stream keys of the default line")
     ap.add_argument("--workload", default="cube16_p8", choices=sorted(WORKLOADS))
     ap.add_argument("--overlap", type=int, default=None, help="override N_O of the workload")
     ap.add_argument("--precision", default=None, choices=["fp64", "mixed"], help="override the workload's precision")
@@ -224,10 +229,119 @@ def measured_traffic():
 
 
 def profile_shares(s, total_ms):
+    """Share of the profiled step time of every kernel group; "other" is the
+    rest: launch gaps and the host synchronisations of the stopping test."""
     out = {}
     for kind in s.PROFILE_KINDS:
         ms, _ = s.profile_result(kind)
         out[kind] = round(ms / max(total_ms, 1e-9), 4)
+    out["other"] = round(1.0 - sum(out.values()), 4)
+    return out
+
+
+def clock_mhz(clock_info, pk):
+    """Median SM clock sampled under load (nvidia-smi), else the peaks file's maximum."""
+    v = (clock_info or {}).get("sm_mhz")
+    return (float(v), "median SM clock sampled during the timed steps") if v else \
+        (float(pk.get("sm_max_mhz", 2070.0)), "maximum SM clock (no clock samples)")
+
+
+def fdm_executed_ops(md):
+    """Arithmetic instructions the even/odd fast diagonalisation executes per
+    subdomain of m_x x m_y x m_z: per direction d, m^3 / m_d lines, each
+    transformed forward and backward with (h+1)^2 + h^2 multiply-adds and 2h
+    additions (h = (m_d - 1) / 2); plus m^3 multiplications by 1/(lam sum)."""
+    m3 = md[0] * md[1] * md[2]
+    ops = m3
+    for m in md:
+        h = (m - 1) // 2
+        ops += 2 * (m3 // m) * (2 * h + (h + 1) ** 2 + h * h)
+    return ops
+
+
+def fdm_dense_flop(md):
+    """Dense-equivalent flops of one subdomain solve (6 dense 1D products and
+    the division): 4 (m_x + m_y + m_z) m^3 + m^3 = 12 m^4 + m^3 for a cube."""
+    m3 = md[0] * md[1] * md[2]
+    return 4 * sum(md) * m3 + m3
+
+
+def level_widths(s, lev):
+    n = 2 ** lev + 1
+    return [n + 2 * s.layers(lev, d) for d in range(3)]
+
+
+def fdm_roofline(s, lev, fp64, clk, clk_basis, pk, traffic=None):
+    """Roofline of the smoother's gather + fast diagonalisation on one level,
+    from the CUDA-event durations of its profiled launches.  ALU bound: the
+    achieved rate counts every executed arithmetic instruction of the method
+    as 2 flop (FMA-equivalent) against the pipe's FMA rate at the sampled clock;
+    the dense-equivalent rate (the 12 m^4 + m^3 count) is given beside it."""
+    ms, cnt = s.profile_result("fdm", lev)
+    if not cnt:
+        return None
+    t = ms / cnt / 1e3
+    md = level_widths(s, lev)
+    Ne = int(np.prod(s.counts))
+    per_clk = FP64_FLOP_PER_CLK_PER_SM if fp64 else FP32_FLOP_PER_CLK_PER_SM
+    peak = NUM_SMS * per_clk * clk * 1e6
+    ops = Ne * fdm_executed_ops(md)
+    dense = Ne * fdm_dense_flop(md)
+    vb = 8 if fp64 else 4
+    algo_bytes = vb * (s.num_dofs(lev) + Ne * md[0] * md[1] * md[2])
+    m = md[0] if md[0] == md[1] == md[2] else "x".join(str(v) for v in md)
+    return {
+        "kernel": ("k_fdm_m<double, %s>" % m if fp64 else "k_fdm_c<%s>" % m)
+                  + " (level %d gather + fast diagonalisation)" % lev,
+        "bound": "alu", "achieved": 2.0 * ops / t / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
+        "frac": 2.0 * ops / t / peak, "traffic": traffic,
+        "executed_ops_per_launch": ops, "avg_launch_ms": t * 1e3, "launches_timed": cnt,
+        "dense_equivalent": {"flop_per_launch": dense, "achieved_tflops": dense / t / 1e12,
+                             "frac_of_peak": dense / t / peak},
+        "hbm": {"algorithmic_bytes_per_launch": algo_bytes, "achieved_gbs": algo_bytes / t / 1e9,
+                "frac": algo_bytes / t / 1e9 / float(pk["hbm_gbs"])},
+        "peak_basis": "%s pipe: %d SMs x %d flop/clk (FMA-equivalent) x %.0f MHz (%s); derived, the peaks file has "
+                      "no %s entry" % ("FP64" if fp64 else "FP32", NUM_SMS, per_clk, clk, clk_basis,
+                                       "FP64" if fp64 else "FP32"),
+    }
+
+
+def hbm_roofline(s, kind, lev, bytes_per_launch, name, pk):
+    """HBM roofline of a streaming kernel group: algorithmic bytes per launch
+    over its mean CUDA-event duration, against the measured copy bandwidth."""
+    ms, cnt = s.profile_result(kind, lev)
+    if not cnt:
+        return None
+    t = ms / cnt / 1e3
+    return {"kernel": name, "bound": "hbm", "achieved": bytes_per_launch / t / 1e9, "peak": float(pk["hbm_gbs"]),
+            "unit": "GB/s", "frac": bytes_per_launch / t / 1e9 / float(pk["hbm_gbs"]), "traffic": None,
+            "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_ms": t * 1e3, "launches_timed": cnt}
+
+
+def level_rooflines(s, lev, fp64, clk, clk_basis, pk, traffic=None):
+    """Rooflines of the three level kernels of the smoothing step on level lev
+    (residual, gather + fast diagonalisation, weighted scatter); the first is
+    the dominant one by time."""
+    vb = 8 if fp64 else 4
+    N = s.num_dofs(lev)
+    md = level_widths(s, lev)
+    Ne = int(np.prod(s.counts))
+    tname = "double" if fp64 else "float"
+    out = []
+    r = fdm_roofline(s, lev, fp64, clk, clk_basis, pk, traffic)
+    if r:
+        out.append(r)
+    r = hbm_roofline(s, "sipg", lev, 3 * vb * N, "%s (level %d residual r = f - A u: reads u, f, writes r)"
+                     % ("k_sipg_n<double, %d>" % (2 ** lev + 1) if fp64 else "k_sipg_c<%d>" % (2 ** lev + 1), lev),
+                     pk)
+    if r:
+        out.append(r)
+    r = hbm_roofline(s, "scatter", lev, vb * (Ne * md[0] * md[1] * md[2] + 2 * N),
+                     "k_scatter_e<%s, %d> (level %d weighted scatter: reads the corrections and u, writes u)"
+                     % (tname, 2 ** lev + 1, lev), pk)
+    if r:
+        out.append(r)
+    out.sort(key=lambda d: -d["avg_launch_ms"] * d["launches_timed"])
     return out
 
 
@@ -265,6 +379,14 @@ def sample_text(N, its):
     return ("FP64 oracle (numpy/scipy, assembled SIPG matrix, direct subdomain solves) solving the same problem "
             "class on %dx%dx%d elements, P=%d (%d DOFs, %d V(1,1) cycles to 1e-10), solve time only"
             % (c[0], c[1], c[2], ORACLE_SAMPLE["P"], N, its))
+
+
+def compact_line(line):
+    """An extra configuration's line without the keys the main line already has."""
+    drop = ("metric", "n_gpus", "higher_is_better", "scaling", "vs_baseline", "data", "unit")
+    out = {k: v for k, v in line.items() if k not in drop}
+    out["unit"] = line["unit"]
+    return out
 
 
 def run_reference(args):
@@ -363,26 +485,13 @@ def run_mg(args):
     s.profile(False)
 
     # roofline of the dominant kernel: the smoother's fast diagonalisation on the
-    # fine level, FP64-pipe bound; algorithmic flops per launch = Ne (12 m^4 + m^3)
-    lev = s.L
-    m = s.P + 1 + 2 * s.layers(lev)
-    Ne = int(np.prod(W["elements"]))
-    fdm_ms, fdm_n = s.profile_result("fdm", lev)
-    algo_flop = Ne * (12.0 * m ** 4 + m ** 3)
+    # fine level (FP64-pipe bound), with the other level kernels beside it
     pk, pk_kind = peaks()
-    sm_max = float(pk.get("sm_max_mhz", 2070.0))
-    fp64_peak = NUM_SMS * FP64_FLOP_PER_CLK_PER_SM * sm_max * 1e6
-    achieved = algo_flop / (fdm_ms / fdm_n / 1e3) if fdm_n else None
-    roofline = {
-        "kernel": "k_fdm<double> (fine-level gather + fast diagonalisation)",
-        "bound": "alu", "achieved": achieved / 1e12 if achieved else None, "peak": fp64_peak / 1e12,
-        "unit": "TFLOP/s", "frac": (achieved / fp64_peak) if achieved else None, "traffic": measured_traffic(),
-        "traffic_source": "profiles/fdm_fp64_16x16x16_p8_m11.md (ncu dram__bytes_read+write of one launch)",
-        "algorithmic_flop_per_launch": algo_flop, "launches_timed": fdm_n,
-        "avg_launch_ms": fdm_ms / fdm_n if fdm_n else None,
-        "peak_basis": "FP64 pipe: %d SMs x %d flop/clk x %.0f MHz (derived; %s peaks file has no FP64 entry)"
-                      % (NUM_SMS, FP64_FLOP_PER_CLK_PER_SM, sm_max, pk_kind),
-    }
+    clk, clk_basis = clock_mhz(clock_info, pk)
+    kern = level_rooflines(s, s.L, True, clk, clk_basis, pk, traffic=measured_traffic())
+    roofline = dict(kern[0])
+    roofline["traffic_source"] = "profiles/fdm_fp64_16x16x16_p8_m11.md (ncu dram__bytes_read+write of one launch)"
+    roofline["other_kernels"] = kern[1:]
     roofline["time_share_of_step"] = profile_shares(s, sum(prof_ms))
     roofline["ms_per_step_by_kernel_level"] = profile_levels(s, args.steps)
     roofline["timing"] = ("kernel durations from CUDA events around each kernel group over %d profiled steps of the "
@@ -423,8 +532,11 @@ def run_mg(args):
                 um.zero_()
                 sm_.solve(b, um, tol=W["tol"], use_cg=True)
             barrier()
+            ck = ClockSampler(dev.index)
+            ck.start()
             mix_ms, its_ml = timed_steps(sm_, um, use_cg=True)
             barrier()
+            ck_info = ck.stop()
             sm_.profile(True)
             mix_prof_ms, _ = timed_steps(sm_, um, use_cg=True)
             sm_.profile(False)
@@ -439,7 +551,10 @@ def run_mg(args):
                    "fdm_tensor_cores_by_level": [sm_.fdm_tensor_cores(l) for l in range(1, sm_.L + 1)],
                    "true_relres_fp64": true_rel, "max_rel_diff_vs_fp64_solution": err,
                    "time_share_of_step": profile_shares(sm_, sum(mix_prof_ms)),
-                   "ms_per_step_by_kernel_level": profile_levels(sm_, args.steps)}
+                   "ms_per_step_by_kernel_level": profile_levels(sm_, args.steps), "clocks": ck_info}
+            clk_m, clk_b = clock_mhz(ck_info, pk)
+            kern = level_rooflines(sm_, sm_.L, False, clk_m, clk_b, pk)
+            leg["roofline"] = dict(kern[0], other_kernels=kern[1:])
             sm_.close()
             return leg
 
@@ -451,8 +566,11 @@ def run_mg(args):
             ud.zero_()
             sd.solve(b, ud, tol=W["tol"])
         barrier()
+        ck = ClockSampler(dev.index)
+        ck.start()
         df_ms, its_d = timed_steps(sd, ud, use_cg=False)
         barrier()
+        df_clocks = ck.stop()
         sd.profile(True)
         df_prof_ms, _ = timed_steps(sd, ud, use_cg=False)
         sd.profile(False)
@@ -463,12 +581,23 @@ def run_mg(args):
                         "true_relres_fp64": float(torch.linalg.norm(s.residual(ud, b)) / torch.linalg.norm(b)),
                         "max_rel_diff_vs_fp64_solution": float(torch.max(torch.abs(ud - u)) / torch.max(torch.abs(u))),
                         "time_share_of_step": profile_shares(sd, sum(df_prof_ms)),
-                        "ms_per_step_by_kernel_level": profile_levels(sd, args.steps)}
+                        "ms_per_step_by_kernel_level": profile_levels(sd, args.steps), "clocks": df_clocks}
         sd.close()
 
         line["mixed"] = mixed_leg(args.outer_df64)
         if not args.outer_df64:
             line["mixed_df64"] = mixed_leg(True)
+
+    if not args.no_configs and world == 1:
+        # the metric's own configurations beside the main line: the anisotropic
+        # 48x8x8, P = 16 box (mixed MG-CG, every overlap the configuration
+        # lists) and the 512-request serving stream (N_O = 1 and 4)
+        line["c3"] = {}
+        for no in (1, 2, 4):
+            line["c3"]["n_o_%d" % no] = compact_line(workload_line("box48x8x8_p16", 3, 2, overlap=no))
+        line["serving"] = {}
+        for no in (1, 4):
+            line["serving"]["n_o_%d" % no] = compact_line(serving_line("serving512", no))
 
     if rank == 0 and not args.no_cpu_baseline:
         Ns, ts, _, its_s = oracle_sample_solve()
@@ -481,25 +610,27 @@ def run_mg(args):
         dist.destroy_process_group()
 
 
-def run_workload(args):
-    """One configuration other than the default line: DOF/s of full solves,
-    per-kernel device times, fine-level smoother roofline."""
+def workload_line(name, steps, warmup, overlap=None, precision=None, cg=False, outer_df64=False,
+                  tensor_cores="off"):
+    """One configuration: DOF/s of full solves (inputs resident, L2 flushed
+    between solves), per-kernel device times and the rooflines of the
+    fine-level kernels.  Returns the JSON line as a dict."""
     import torch
 
     import paper_1612_04796_gb300 as pkg
     from paper_1612_04796_gb300 import inputs
 
-    W = dict(WORKLOADS[args.workload])
-    if args.overlap is not None:
-        W["overlap_layers"] = args.overlap
-    if args.precision is not None:
-        W["precision"] = args.precision
-    if args.cg:
+    W = dict(WORKLOADS[name])
+    if overlap is not None:
+        W["overlap_layers"] = overlap
+    if precision is not None:
+        W["precision"] = precision
+    if cg:
         W["use_cg"] = True
     dev = torch.device("cuda", torch.cuda.current_device())
     pkg.load_library()
     extra = {k: W[k] for k in ("overlap_mode", "overlap_frac", "ns_growth") if k in W}
-    extra_mixed = dict(extra, tensor_cores=TC_MODE[args.tensor_cores], outer_df64=args.outer_df64)
+    extra_mixed = dict(extra, tensor_cores=TC_MODE[tensor_cores], outer_df64=outer_df64)
     s = pkg.MGSolver(W["lengths"], W["elements"], W["P"], overlap=W["overlap_layers"], precision=W["precision"],
                      device=dev, **(extra_mixed if W["precision"] == "mixed" else extra))
     s64 = s if W["precision"] == "fp64" else pkg.MGSolver(W["lengths"], W["elements"], W["P"],
@@ -517,7 +648,7 @@ def run_workload(args):
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    def steps(k):
+    def run(k):
         ms, its = [], []
         for step in range(k):
             flush.fill_(step & 0xFF)
@@ -532,49 +663,49 @@ def run_workload(args):
             its.append(it)
         return ms, its
 
-    steps(args.warmup)
+    run(warmup)
     torch.cuda.synchronize()
     clocks = ClockSampler(dev.index)
     clocks.start()
     l0 = s.kernel_launches()
-    ms, its = steps(args.steps)
+    ms, its = run(steps)
     launches = s.kernel_launches() - l0
     clock_info = clocks.stop()
     s.profile(True)
-    prof_ms, _ = steps(args.steps)
+    prof_ms, _ = run(steps)
     s.profile(False)
     true_rel = float(torch.linalg.norm(s64.residual(u, b)) / torch.linalg.norm(b))
     if W["precision"] == "mixed":
-        W["fdm_tensor_cores"] = args.tensor_cores
-        W["outer_operator"] = "double-float (FP32 pairs)" if args.outer_df64 else "FP64"
+        W["fdm_tensor_cores"] = tensor_cores
+        W["outer_operator"] = "double-float (FP32 pairs)" if outer_df64 else "FP64"
         W["fdm_tensor_cores_by_level"] = [s.fdm_tensor_cores(l) for l in range(1, s.L + 1)]
-    lev = s.L
-    md = [s.P + 1 + 2 * s.layers(lev, d) for d in range(3)]
-    m = md[0] if md[0] == md[1] == md[2] else "x".join(str(v) for v in md)
-    Ne = int(np.prod(W["elements"]))
-    fdm_ms, fdm_n = s.profile_result("fdm", lev)
-    mxyz = float(md[0] * md[1] * md[2])
-    algo = Ne * (4.0 * sum(md) * mxyz + mxyz)  # dense-equivalent 1D products, both directions, + division
-    pk, _ = peaks()
-    clk = float(pk.get("sm_max_mhz", 2070.0)) * 1e6
     fp64 = W["precision"] == "fp64"
-    peak = NUM_SMS * (FP64_FLOP_PER_CLK_PER_SM if fp64 else FP32_FLOP_PER_CLK_PER_SM) * clk
-    ach = algo / (fdm_ms / fdm_n / 1e3) if fdm_n else None
+    pk, _ = peaks()
+    clk, clk_basis = clock_mhz(clock_info, pk)
+    kern = level_rooflines(s, s.L, fp64, clk, clk_basis, pk)
+    vb = 8 if fp64 else 4
     line = {
-        "metric": METRIC, "value": N * args.steps / (sum(ms) / 1e3), "unit": "DOF/s", "n_gpus": 1,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": sum(ms) / args.steps, "higher_is_better": True,
+        "metric": METRIC, "value": N * steps / (sum(ms) / 1e3), "unit": "DOF/s", "n_gpus": 1,
+        "steps": steps, "warmup": warmup, "ms_per_step": sum(ms) / steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64" if fp64 else "f32 multigrid / f64 outer",
         "data": "synthetic",
-        "config": dict(W, dofs=N, iterations=int(statistics.median(its)), name=args.workload,
-                       true_relres=true_rel, l2="flushed (256 MiB write) between steps"),
+        "config": dict(W, dofs=N, iterations=int(statistics.median(its)), name=name,
+                       true_relres=true_rel, l2="flushed (256 MiB write) between steps; fine-level vectors "
+                       "%.0f MB each" % (vb * N / 1e6)),
         "gpu_launches": launches, "clocks": clock_info,
-        "roofline": {"kernel": "fine-level smoother (m=%s)" % m, "bound": "alu", "unit": "TFLOP/s",
-                     "achieved": ach / 1e12 if ach else None, "peak": peak / 1e12,
-                     "frac": ach / peak if ach else None, "traffic": None,
-                     "avg_launch_ms": fdm_ms / fdm_n if fdm_n else None,
-                     "time_share_of_step": profile_shares(s, sum(prof_ms)),
-                     "ms_per_step_by_kernel_level": profile_levels(s, args.steps)},
+        "roofline": dict(kern[0], other_kernels=kern[1:], time_share_of_step=profile_shares(s, sum(prof_ms)),
+                         ms_per_step_by_kernel_level=profile_levels(s, steps)),
     }
+    if s64 is not s:
+        s64.close()
+    s.close()
+    return line
+
+
+def run_workload(args):
+    """One configuration other than the default line (`--workload NAME`)."""
+    line = workload_line(args.workload, args.steps, args.warmup, overlap=args.overlap, precision=args.precision,
+                         cg=args.cg, outer_df64=args.outer_df64, tensor_cores=args.tensor_cores)
     print(json.dumps(line), flush=True)
 
 
@@ -653,24 +784,25 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
-def run_serving(args):
+def serving_line(name, overlap=None, n_req=None):
     """The serving stream: throughput (DOFs solved / makespan) and per-request
-    latency (arrival to result on the host) percentiles."""
+    latency (arrival to result on the host) percentiles.  Returns the JSON line
+    as a dict."""
     import torch
 
     from paper_1612_04796_gb300.serving import Server, latency_summary, request_stream
-    n_req = int(os.environ.get("MG_SERVING_REQUESTS", "512"))
-    overlap = 4 if args.overlap is None else args.overlap
+    n_req = int(os.environ.get("MG_SERVING_REQUESTS", "512")) if n_req is None else n_req
+    overlap = 4 if overlap is None else overlap
     slots = int(os.environ.get("MG_SERVING_SLOTS", "8"))
     policy = os.environ.get("MG_SERVING_POLICY", "smallest")
-    W = WORKLOADS[args.workload]
+    W = WORKLOADS[name]
     reqs = request_stream(seed=5, n_requests=n_req, overlap=overlap, sizes=tuple(W.get("sizes", (4, 8, 16, 24, 32))),
                           orders=tuple(W.get("orders", (2, 4, 8, 16))), rate=W.get("rate", 200.0))
     batch_max = int(os.environ.get("MG_SERVING_BATCH", "16"))
     batch_dofs = int(os.environ.get("MG_SERVING_BATCH_DOFS", str(1 << 20)))
     srv = Server(slots=slots, keep_solution=False, policy=policy, batch_max=batch_max, batch_dofs=batch_dofs)
-    # warm-up: one small request of every order (module loading, first captures)
-    warm = [r for r in request_stream(seed=6, n_requests=64, sizes=(4,)) if True][:8]
+    # warm-up: small requests of every order (module loading, first captures)
+    warm = request_stream(seed=6, n_requests=64, sizes=(4,), overlap=overlap)[:8]
     srv.serve(warm, realtime=False)
     torch.cuda.synchronize()
     clocks = ClockSampler(srv.device.index)
@@ -687,7 +819,7 @@ def run_serving(args):
         "metric": METRIC, "value": dofs / makespan, "unit": "DOF/s", "n_gpus": 1, "steps": 1, "warmup": 1,
         "ms_per_step": makespan * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32 multigrid / f64 outer", "data": "synthetic",
-        "config": dict(W, name=args.workload, requests=len(reqs), slots=slots, overlap_layers=overlap,
+        "config": dict(W, name=name, requests=len(reqs), slots=slots, overlap_layers=overlap,
                        hbm_budget_gb=srv.budget / 1e9, total_dofs=dofs,
                        admission=policy + (" (aging after %.0f s)" % srv.max_wait
                                            if policy == "smallest" else ""),
@@ -696,11 +828,17 @@ def run_serving(args):
         "latency": summ, "max_concurrent": srv.max_active,
         "batched_requests": int(sum(r.batch > 1 for r in res)),
         "mean_batch": float(np.mean([r.batch for r in res])),
+        "failed_requests": len(res) - len(ok),
         "iterations": {"median": float(np.median([r.iterations for r in ok])),
                        "max": int(max(r.iterations for r in ok))},
         "max_relres": float(max(r.relres for r in ok)), "clocks": clock_info,
     }
-    print(json.dumps(line), flush=True)
+    srv.close()
+    return line
+
+
+def run_serving(args):
+    print(json.dumps(serving_line(args.workload, args.overlap)), flush=True)
 
 
 def main():

@@ -78,6 +78,16 @@ typedef enum {
   MG_WEIGHT_QUINTIC_NORMALISED = 3  /* one-sided quintic hat normalised to sum to one */
 } mg_weight_profile;
 
+/* Half-width delta (reference units) of the transition of w_H (Fig. wH) when
+ * the strip holds N_O >= 2 node layers; the paper defers the definition to an
+ * earlier paper, so these are readings.  For N_O <= 1 all give the same weights. */
+typedef enum {
+  MG_DELTA_DEFAULT = 0, /* MG_DELTA_MID for MG_OVERLAP_LAYERS, MG_DELTA_STRIP otherwise */
+  MG_DELTA_NODE = 1,    /* the distance of the outermost included neighbour node: its weight is 0 */
+  MG_DELTA_MID = 2,     /* midway between the outermost included and the first excluded node */
+  MG_DELTA_STRIP = 3    /* the strip itself, 2 delta_O / dx (MG_OVERLAP_WIDTH and MG_OVERLAP_MAX only) */
+} mg_weight_delta;
+
 typedef struct {
   int overlap_mode;      /* mg_overlap_mode, default MG_OVERLAP_LAYERS */
   double overlap_frac;   /* delta_O / dx for MG_OVERLAP_WIDTH (0 .. 0.5; paper: 0.08, 0.5),
@@ -96,6 +106,8 @@ typedef struct {
                             arithmetic (pairs of FP32, about 48 significant bits; FP64 vectors,
                             inner products and updates); 0 = FP64 (default) */
   void* stream;          /* cudaStream_t; NULL = default stream */
+  int weight_delta;      /* mg_weight_delta, default MG_DELTA_DEFAULT; MG_OVERLAP_MAX takes only
+                            the default */
 } mg_opts;
 
 /* Fill *o with the defaults above. */
@@ -256,6 +268,12 @@ mg_status mg_solve_batch(mg_ctx* const* ctxs, int count, double* const* u, const
  * preconditioner of MG_DF64).  Uses two of the outer-iteration work vectors. */
 mg_status mg_vcycle_df64(mg_ctx* ctx, double* u, const double* f);
 
+/* mg_smooth_df64 -- nsteps Schwarz steps on level l like mg_smooth (Section 3.1;
+ * FP64 vectors u, f of that level), with the residual, the fast
+ * diagonalisation and the weighted scatter in double-float arithmetic (the
+ * smoother of MG_DF64).  Uses two of the outer-iteration work vectors. */
+mg_status mg_smooth_df64(mg_ctx* ctx, int level, double* u, const double* f, int nsteps);
+
 /* mg_apply_sipg_df64 -- Au = A_l u like mg_apply_sipg (FP64 vectors), with the
  * arithmetic in double-float (about 48 significant bits); the operator of the
  * outer iteration when mg_opts.outer_df64 = 1.  Uses the smoother's
@@ -304,7 +322,11 @@ mg_status mg_get_table(mg_ctx* ctx, int level, int dir, int what, double* host_o
  * failed CUDA call, MG_ENOCONV if an eigensolver hit its sweep limit.
  * The first call on each device looks up the array's device address
  * (cudaGetSymbolAddress, with that device current): make that first call
- * before any stream capture begins.  All calls share the one array, which
+ * before any stream capture begins.  With lazy module loading (the CUDA
+ * default) that first lookup may also load the library's device code on the
+ * device, which is when the array is reserved, so the first call can take
+ * device memory and synchronise; a caller for whom that matters makes one call
+ * at start-up.  Later calls reserve nothing.  All calls share the one array, which
  * keeps the last call's contents: calls that overlap on the GPU (from other
  * streams or other host threads) race on it and must not be issued
  * concurrently.
@@ -319,9 +341,12 @@ mg_status mg_coarse_solve_noalloc(double lx, double ly, double lz, int nx, int n
  *   stream around every kernel group (clearing earlier records); 0 stops.
  * mg_profile_result: summed device time in ms and number of recorded groups
  *   of one kind on one level (level -1: all levels).  kind: 0 smoother fast
- *   diagonalisation (gather + contractions), 1 smoother scatter, 2 operator /
- *   residual, 3 restriction, 4 prolongation, 5 coarse solve.  Synchronises
- *   the stream. */
+ *   diagonalisation (gather + contractions), 1 smoother scatter, 2 level
+ *   operator / residual inside the V-cycle, 3 restriction, 4 prolongation,
+ *   5 coarse solve, 6 vector passes of the outer iteration (inner products,
+ *   updates, mean projections, precision conversions), 7 the outer
+ *   iteration's operator (fine-level residual of MG, q = A p of MG-CG).
+ *   Synchronises the stream. */
 long long mg_kernel_launches(const mg_ctx* ctx);
 /* Kernels launched by the mg_solve_batch calls whose first context was ctx
  * (grouped launches, graph nodes, the gathers of the residual norms and the

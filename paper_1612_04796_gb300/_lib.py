@@ -25,6 +25,7 @@ class MgOpts(ctypes.Structure):
         ("fdm_tensor_cores", ctypes.c_int),
         ("outer_df64", ctypes.c_int),
         ("stream", ctypes.c_void_p),
+        ("weight_delta", ctypes.c_int),
     ]
 
 
@@ -112,6 +113,7 @@ SIGNATURES = {
     "mg_level_fdm_tensor_cores": (_I, [_P, _I]),
     "mg_apply_sipg_df64": (_S, [_P, _I, _P, _P]),
     "mg_vcycle_df64": (_S, [_P, _P, _P]),
+    "mg_smooth_df64": (_S, [_P, _I, _P, _P, _I]),
     "mg_selftest_bounded_wait": (_S, [_P, _I, ctypes.POINTER(ctypes.c_int)]),
     "mg_node_coords": (_S, [_P, _I, _P, _P, _P]),
     "mg_rhs": (_S, [_P, _P, _P]),

@@ -1,0 +1,272 @@
+// FP32 fast-diagonalisation smoother with the 1D factors in the kernel's
+// parameter space (Section 3.1, the subdomain solve
+//   du_s = (Sz(x)Sy(x)Sx) (Lx (+) Ly (+) Lz)^{-1} (Sz^T(x)Sy^T(x)Sx^T) r_s).
+//
+// In FP32 the line products of the shared-memory kernel (fdm_tmpl.cuh) are
+// limited by their loads, not by the FMA pipe: every multiply-add reads its
+// coefficient of S from shared memory.  Here the even/odd halves of the six
+// 1D factors (at most 29.4 KB at m = 35) travel as one __grid_constant__
+// kernel parameter, so with the fully unrolled products of a compile-time
+// width every coefficient is an immediate constant-bank operand of its FMA:
+// the only shared-memory traffic left is the subdomain tile itself.
+//
+// One block takes SPB subdomains: their residual tiles r_s = R_s r are
+// gathered with coalesced loads (x fastest) into shared memory, the five line
+// passes (x forward; y forward; z forward, division by the eigenvalue sums,
+// z backward; y backward; x backward with the weights folded into SW) run in
+// place, and the weighted correction tiles are written back with coalesced
+// stores to the correction buffer, in the layout of the other smoother kernels.
+#include <algorithm>
+#include <atomic>
+
+#include "mg_internal.h"
+
+namespace mgdg {
+namespace {
+
+template <int M>
+struct FdmCShape {
+  static constexpr int h = M / 2, ne = h + 1, ho = h > 0 ? h : 1;
+  static constexpr int M2 = M * M, M3 = M2 * M;
+  static constexpr int spb = M2 >= 256 ? 1 : 256 / M2;     // subdomains per block
+  static constexpr int lines = spb * M2;                     // lines of one pass
+  static constexpr int iters = (lines + 511) / 512;
+  static constexpr int threads = ((lines + iters - 1) / iters + 31) / 32 * 32;
+  static constexpr size_t smem = sizeof(float) * (size_t)spb * M3;
+};
+
+template <int M>
+struct FdmCArgs {
+  using Sh = FdmCShape<M>;
+  const float* r;
+  float* corr;
+  int64_t Ne;
+  int nx, ny, nz, n, no;
+  float lam[3][M];                   // 1D eigenvalues
+  float se[3][Sh::ne * Sh::ne];      // S[a][p], a, p <= h         (forward, even modes)
+  float so[3][Sh::ho * Sh::ho];      // S[a][h+1+q], a, q < h      (forward, odd modes)
+  float we[3][Sh::ne * Sh::ne];      // SW[a][p], a, p <= h        (backward, even modes)
+  float wo[3][Sh::ho * Sh::ho];      // SW[a][h+1+q], a, q < h     (backward, odd modes)
+};
+
+// y = S_d^T x (even modes first), x a reflection-symmetric line.
+template <int M, int D>
+__device__ __forceinline__ void fwd_c(const FdmCArgs<M>& a, const float (&x)[M], float (&y)[M]) {
+  constexpr int h = M / 2, ne = h + 1;
+  float e[ne], o[h > 0 ? h : 1];
+#pragma unroll
+  for (int t = 0; t < h; ++t) {
+    e[t] = x[t] + x[M - 1 - t];
+    o[t] = x[t] - x[M - 1 - t];
+  }
+  e[h] = x[h];
+#pragma unroll
+  for (int p = 0; p < ne; ++p) {
+    float acc = a.se[D][p] * e[0];
+#pragma unroll
+    for (int t = 1; t < ne; ++t) acc = fmaf(a.se[D][t * ne + p], e[t], acc);
+    y[p] = acc;
+  }
+#pragma unroll
+  for (int q = 0; q < h; ++q) {
+    float acc = a.so[D][q] * o[0];
+#pragma unroll
+    for (int t = 1; t < h; ++t) acc = fmaf(a.so[D][t * h + q], o[t], acc);
+    y[ne + q] = acc;
+  }
+}
+
+// x = SW_d v (weights folded into SW).
+template <int M, int D>
+__device__ __forceinline__ void bwd_c(const FdmCArgs<M>& a, const float (&v)[M], float (&x)[M]) {
+  constexpr int h = M / 2, ne = h + 1;
+#pragma unroll
+  for (int t = 0; t <= h; ++t) {
+    float E = a.we[D][t * ne] * v[0];
+#pragma unroll
+    for (int p = 1; p < ne; ++p) E = fmaf(a.we[D][t * ne + p], v[p], E);
+    if (t < h) {
+      float O = a.wo[D][t * h] * v[ne];
+#pragma unroll
+      for (int q = 1; q < h; ++q) O = fmaf(a.wo[D][t * h + q], v[ne + q], O);
+      x[t] = E + O;
+      x[M - 1 - t] = E - O;
+    } else {
+      x[t] = E;
+    }
+  }
+}
+
+__device__ __forceinline__ int fc_wrap(int x, int n) { return x < 0 ? x + n : (x >= n ? x - n : x); }
+
+template <int M>
+__global__ void __launch_bounds__(FdmCShape<M>::threads) k_fdm_c(const __grid_constant__ FdmCArgs<M> a) {
+  pdl_entry();
+  using Sh = FdmCShape<M>;
+  constexpr int M2 = Sh::M2, M3 = Sh::M3, SPB = Sh::spb;
+  extern __shared__ __align__(16) float fc_tile[];  // SPB tiles of M^3, node (i, j, k) at i + M (j + M k)
+  __shared__ int nb[SPB * 27];                      // the 27 elements around each subdomain's core
+  const int n = a.n, no = a.no, n3 = n * n * n;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int64_t s0 = (int64_t)blockIdx.x * SPB; s0 < a.Ne; s0 += (int64_t)gridDim.x * SPB) {
+    const int cnt = (int)(a.Ne - s0 < SPB ? a.Ne - s0 : SPB);
+    for (int i = tid; i < cnt * 27; i += nt) {
+      const int g = i / 27, k = i - g * 27;
+      const int s = (int)(s0 + g), sxy = s / a.nx;  // element indices fit in 32 bits
+      const int sx = s - sxy * a.nx, sy = sxy % a.ny, sz = sxy / a.ny;
+      const int dx = k % 3 - 1, dy = (k / 3) % 3 - 1, dz = k / 9 - 1;
+      nb[i] = fc_wrap(sx + dx, a.nx) + a.nx * (fc_wrap(sy + dy, a.ny) + a.ny * fc_wrap(sz + dz, a.nz));
+    }
+    __syncthreads();
+    // gather r_s = R_s r: x fastest, so a warp reads runs of contiguous values
+    for (int i = tid; i < cnt * M3; i += nt) {
+      const int g = i / M3, k = i - g * M3;
+      const int ia = k % M, ib = (k / M) % M, ic = k / M2;
+      const int dx = ia < no ? 0 : (ia < no + n ? 1 : 2), jx = ia - no + (dx == 0 ? n : (dx == 2 ? -n : 0));
+      const int dy = ib < no ? 0 : (ib < no + n ? 1 : 2), jy = ib - no + (dy == 0 ? n : (dy == 2 ? -n : 0));
+      const int dz = ic < no ? 0 : (ic < no + n ? 1 : 2), jz = ic - no + (dz == 0 ? n : (dz == 2 ? -n : 0));
+      fc_tile[i] = a.r[(int64_t)nb[g * 27 + dx + 3 * (dy + 3 * dz)] * n3 + jx + n * (jy + n * jz)];
+    }
+    __syncthreads();
+    const int lines = cnt * M2;
+    // pass 1: x forward
+    for (int ln = tid; ln < lines; ln += nt) {
+      float* line = fc_tile + (ln / M2) * M3 + M * (ln % M2);
+      float x[M], y[M];
+#pragma unroll
+      for (int t = 0; t < M; ++t) x[t] = line[t];
+      fwd_c<M, 0>(a, x, y);
+#pragma unroll
+      for (int t = 0; t < M; ++t) line[t] = y[t];
+    }
+    __syncthreads();
+    // pass 2: y forward
+    for (int ln = tid; ln < lines; ln += nt) {
+      const int l2 = ln % M2;
+      float* line = fc_tile + (ln / M2) * M3 + (l2 % M) + M2 * (l2 / M);
+      float x[M], y[M];
+#pragma unroll
+      for (int t = 0; t < M; ++t) x[t] = line[t * M];
+      fwd_c<M, 1>(a, x, y);
+#pragma unroll
+      for (int t = 0; t < M; ++t) line[t * M] = y[t];
+    }
+    __syncthreads();
+    // pass 3: z forward, times 1 / (lam_x + lam_y + lam_z), z backward
+    for (int ln = tid; ln < lines; ln += nt) {
+      const int l2 = ln % M2;
+      float* line = fc_tile + (ln / M2) * M3 + l2;
+      const float lxy = a.lam[0][l2 % M] + a.lam[1][l2 / M];
+      float x[M], y[M];
+#pragma unroll
+      for (int t = 0; t < M; ++t) x[t] = line[t * M2];
+      fwd_c<M, 2>(a, x, y);
+#pragma unroll
+      for (int t = 0; t < M; ++t) y[t] *= __frcp_rn(lxy + a.lam[2][t]);
+      bwd_c<M, 2>(a, y, x);
+#pragma unroll
+      for (int t = 0; t < M; ++t) line[t * M2] = x[t];
+    }
+    __syncthreads();
+    // pass 4: y backward
+    for (int ln = tid; ln < lines; ln += nt) {
+      const int l2 = ln % M2;
+      float* line = fc_tile + (ln / M2) * M3 + (l2 % M) + M2 * (l2 / M);
+      float x[M], y[M];
+#pragma unroll
+      for (int t = 0; t < M; ++t) y[t] = line[t * M];
+      bwd_c<M, 1>(a, y, x);
+#pragma unroll
+      for (int t = 0; t < M; ++t) line[t * M] = x[t];
+    }
+    __syncthreads();
+    // pass 5: x backward (weights folded into SW)
+    for (int ln = tid; ln < lines; ln += nt) {
+      float* line = fc_tile + (ln / M2) * M3 + M * (ln % M2);
+      float x[M], y[M];
+#pragma unroll
+      for (int t = 0; t < M; ++t) y[t] = line[t];
+      bwd_c<M, 0>(a, y, x);
+#pragma unroll
+      for (int t = 0; t < M; ++t) line[t] = x[t];
+    }
+    __syncthreads();
+    // the weighted correction tiles, coalesced
+    float* out = a.corr + s0 * M3;
+    for (int i = tid; i < cnt * M3; i += nt) out[i] = fc_tile[i];
+    __syncthreads();
+  }
+}
+
+// Host-side fill of the parameter block from the FP32 tables of level l.
+template <int M>
+cudaError_t launch_fdm_c_m(const mg_ctx* c, int l, const float* r) {
+  using Sh = FdmCShape<M>;
+  constexpr int h = M / 2, ne = h + 1;
+  static_assert(sizeof(FdmCArgs<M>) <= 32000, "parameter block too large");
+  const LevelInfo& lv = c->lev[l];
+  const float* tab = c->tab32_host.data();
+  FdmCArgs<M> a;
+  a.r = r;
+  a.corr = static_cast<float*>(c->ws.corr);
+  a.Ne = c->Ne;
+  a.nx = c->ne[0];
+  a.ny = c->ne[1];
+  a.nz = c->ne[2];
+  a.n = lv.n;
+  a.no = lv.no[0];
+  for (int d = 0; d < 3; ++d) {
+    const float* S = tab + lv.t[d].S;
+    const float* SW = tab + lv.t[d].SW;
+    for (int t = 0; t < M; ++t) a.lam[d][t] = tab[lv.t[d].lam + t];
+    for (int t = 0; t < ne; ++t)
+      for (int p = 0; p < ne; ++p) {
+        a.se[d][t * ne + p] = S[t * M + p];
+        a.we[d][t * ne + p] = SW[t * M + p];
+      }
+    for (int t = 0; t < h; ++t)
+      for (int q = 0; q < h; ++q) {
+        a.so[d][t * h + q] = S[t * M + ne + q];
+        a.wo[d][t * h + q] = SW[t * M + ne + q];
+      }
+  }
+  if (Sh::smem > 48 * 1024) {
+    const cudaError_t e = cudaFuncSetAttribute(k_fdm_c<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::smem);
+    if (e != cudaSuccess) return e;
+  }
+  static std::atomic<int> per_sm_cached{0};  // resident blocks per SM, queried once per width
+  int per_sm = per_sm_cached.load();
+  if (per_sm == 0) {
+    const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fdm_c<M>, Sh::threads, Sh::smem);
+    if (e != cudaSuccess) return e;
+    per_sm = std::max(per_sm, 1);
+    per_sm_cached.store(per_sm);
+  }
+  const int64_t groups = (c->Ne + Sh::spb - 1) / Sh::spb;
+  const int64_t slots = 152LL * per_sm;
+  const int blocks = (int)std::min<int64_t>(groups, slots);
+  launch_pdl(k_fdm_c<M>, blocks, Sh::threads, Sh::smem, c->stream, a);
+  c->nlaunch += 1;
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool fdm_c_applies(const mg_ctx* c, int l) {
+  const LevelInfo& lv = c->lev[l];
+  const int m = lv.m[0];
+  return l >= 1 && m == lv.m[1] && m == lv.m[2] && (m & 1) && m >= 3 && m <= 35 && !c->tab32_host.empty();
+}
+
+cudaError_t launch_fdm_c(const mg_ctx* c, int l, const float* r) {
+  if (!fdm_c_applies(c, l)) return cudaErrorNotSupported;
+  switch (c->lev[l].m[0]) {
+#define MGDG_FC(M) case M: return launch_fdm_c_m<M>(c, l, r);
+    MGDG_FC(3) MGDG_FC(5) MGDG_FC(7) MGDG_FC(9) MGDG_FC(11) MGDG_FC(13) MGDG_FC(15) MGDG_FC(17) MGDG_FC(19)
+    MGDG_FC(21) MGDG_FC(23) MGDG_FC(25) MGDG_FC(27) MGDG_FC(29) MGDG_FC(31) MGDG_FC(33) MGDG_FC(35)
+#undef MGDG_FC
+    default: return cudaErrorNotSupported;
+  }
+}
+
+}  // namespace mgdg

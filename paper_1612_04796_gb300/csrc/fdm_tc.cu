@@ -260,6 +260,7 @@ __global__ void __launch_bounds__(kTcThreads) k_fdm_tc(TcArgs a) {
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
+  __shared__ uint32_t pending_phase;  // phase of the commit a timed-out wait was waiting for
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   float* A = reinterpret_cast<float*>(tc_smem);
   float* B = reinterpret_cast<float*>(tc_smem + a.a_bytes);
@@ -348,6 +349,7 @@ __global__ void __launch_bounds__(kTcThreads) k_fdm_tc(TcArgs a) {
       if (tid == 0 && !tc_wait(mb, phase, a.wait_cycles)) {
         atomicExch(a.status + 1, kDevTimeout);
         abort_flag = 1;
+        pending_phase = phase;
       }
       phase ^= 1u;
       __syncthreads();
@@ -367,6 +369,11 @@ __global__ void __launch_bounds__(kTcThreads) k_fdm_tc(TcArgs a) {
     }
     if (abort_flag) break;
   }
+  // After a timeout with MMAs issued, they may still be writing the tensor
+  // memory about to be freed: one more bounded wait for their commit.  (If it
+  // also runs out, the tensor memory's contents are undefined; the status word
+  // already tells the host, and the solve reports MG_ECUDA.)
+  if (tid == 0 && abort_flag && !a.self_test) tc_wait(mb, pending_phase, a.wait_cycles);
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");

@@ -88,13 +88,15 @@ int layers_from_width(int P, double frac) {
   return cnt;
 }
 
-// Hat-weight half-width for N_O prescribed layers: midpoint between the last
-// included and the first excluded neighbour node, capped at 1.
-double layer_delta(int P, int no) {
+// Hat-weight half-width for a strip of N_O neighbour node layers (reference
+// units, capped at 1): MG_DELTA_MID, midway between the last included and the
+// first excluded neighbour node; MG_DELTA_NODE, the distance of the last
+// included node (its weight becomes 0).
+double layer_delta(int P, int no, int rule) {
   if (no <= 0) return 0.0;
   std::vector<double> x = gll_host(P);
   if (no >= P + 1) return 1.0;
-  double d = 0.5 * ((1.0 + x[no - 1]) + (1.0 + x[no]));
+  double d = rule == MG_DELTA_NODE ? 1.0 + x[no - 1] : 0.5 * ((1.0 + x[no - 1]) + (1.0 + x[no]));
   return d < 1.0 ? d : 1.0;
 }
 
@@ -178,7 +180,7 @@ double read_scalar(mg_ctx* c, int slot, cudaError_t* err) {
 // appear by name in a profiler's timeline; without a tool attached the calls
 // return at once.
 const char* const kRangeNames[kProfKinds] = {"smoother FDM", "smoother scatter", "operator", "restriction",
-                                             "prolongation", "coarse solve", "vector pass"};
+                                             "prolongation", "coarse solve", "vector pass", "outer operator"};
 
 struct NvtxRange {
   explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
@@ -358,16 +360,24 @@ cudaError_t precond(const mg_ctx* c, const double* r, double* z) {
     float* f32 = lvec<float>(c->lev[L].f);
     float* u32 = lvec<float>(c->lev[L].u);
     cudaError_t e;
-    if ((e = launch_to_f32(c, r, f32, N, kSlotRR)) != cudaSuccess) return e;
+    {
+      ProfScope pv(c, kProfVector, L);
+      if ((e = launch_to_f32(c, r, f32, N, kSlotRR)) != cudaSuccess) return e;
+    }
     if ((e = vcycle_t<float>(c, u32, f32, true, false)) != cudaSuccess) return e;
+    ProfScope pv(c, kProfVector, L);
     return launch_from_f32(c, u32, z, N, kSlotRR);
   }
   if (c->opts.precision == MG_DF64) {
     df64* fd = lvec<df64>(c->lev[L].f);
     df64* ud = lvec<df64>(c->lev[L].u);
     cudaError_t e;
-    if ((e = launch_split_df64(c, r, fd, N)) != cudaSuccess) return e;
+    {
+      ProfScope pv(c, kProfVector, L);
+      if ((e = launch_split_df64(c, r, fd, N)) != cudaSuccess) return e;
+    }
     if ((e = vcycle_t<df64>(c, ud, fd, true, false)) != cudaSuccess) return e;
+    ProfScope pv(c, kProfVector, L);
     return launch_join_df64(c, ud, z, N, 0);
   }
   return vcycle_t<double>(c, z, r, true, false);
@@ -432,17 +442,20 @@ cudaError_t cg_step_a(const mg_ctx* c, double* x, double* p, double* r, double* 
   cudaError_t e;
   if (pdf) {
     {
-      ProfScope ps(c, kProfSipg, L);
+      ProfScope ps(c, kProfOuter, L);
       if ((e = launch_sipg<df64>(c, L, pdf, nullptr, qdf, 0)) != cudaSuccess) return e;
     }
+    ProfScope pv(c, kProfVector, L);
     if ((e = launch_dot_dfq(c, p, qdf, q, N, kSlotPQ)) != cudaSuccess) return e;
   } else {
     {
-      ProfScope ps(c, kProfSipg, L);
+      ProfScope ps(c, kProfOuter, L);
       if ((e = launch_sipg<double>(c, L, p, nullptr, q, 0)) != cudaSuccess) return e;
     }
+    ProfScope pv(c, kProfVector, L);
     if ((e = launch_dot(c, p, q, N, kSlotPQ)) != cudaSuccess) return e;
   }
+  ProfScope pv(c, kProfVector, L);
   return launch_cg_update(c, x, p, r, q, N);
 }
 
@@ -455,18 +468,27 @@ cudaError_t cg_step_b(const mg_ctx* c, double* p, double* r, double* q, double* 
   if (c->opts.precision == MG_MIXED) {
     float* f32 = lvec<float>(c->lev[L].f);
     float* u32 = lvec<float>(c->lev[L].u);
-    if ((e = launch_to_f32(c, r, f32, N, kSlotRR)) != cudaSuccess) return e;
+    {
+      ProfScope pv(c, kProfVector, L);
+      if ((e = launch_to_f32(c, r, f32, N, kSlotRR)) != cudaSuccess) return e;
+    }
     if ((e = vcycle_t<float>(c, u32, f32, true, false)) != cudaSuccess) return e;
+    ProfScope pv(c, kProfVector, L);
     return launch_cg_direction<float>(c, p, u32, q, r, N, pdf);
   }
   if (c->opts.precision == MG_DF64) {
     df64* fd = lvec<df64>(c->lev[L].f);
     df64* ud = lvec<df64>(c->lev[L].u);
-    if ((e = launch_split_df64(c, r, fd, N)) != cudaSuccess) return e;
+    {
+      ProfScope pv(c, kProfVector, L);
+      if ((e = launch_split_df64(c, r, fd, N)) != cudaSuccess) return e;
+    }
     if ((e = vcycle_t<df64>(c, ud, fd, true, false)) != cudaSuccess) return e;
+    ProfScope pv(c, kProfVector, L);
     return launch_cg_direction<df64>(c, p, ud, q, r, N, pdf);
   }
   if ((e = vcycle_t<double>(c, z, r, true, false)) != cudaSuccess) return e;
+  ProfScope pv(c, kProfVector, L);
   return launch_cg_direction<double>(c, p, z, q, r, N);
 }
 
@@ -498,14 +520,16 @@ mg_status solve_impl(mg_ctx* c, double* u, const double* f, double tol, int maxi
         if (mixed) {
           double* z = c->ws.cg[2];
           if ((e = precond(c, r, z)) != cudaSuccess) return e;
+          ProfScope pv(c, kProfVector, L);
           if ((e = launch_add(c, u, z, N)) != cudaSuccess) return e;
         } else if ((e = vcycle_t<double>(c, u, f, false, true)) != cudaSuccess) {
           return e;
         }
         {
-          ProfScope ps(c, kProfSipg, L);
+          ProfScope ps(c, kProfOuter, L);
           if ((e = launch_sipg<double>(c, L, u, f, r, 1)) != cudaSuccess) return e;
         }
+        ProfScope pv(c, kProfVector, L);
         return launch_dot(c, r, r, N, kSlotRR);
       }));
       double v = read_scalar(c, kSlotRR, &err);
@@ -792,6 +816,7 @@ void mg_default_opts(mg_opts* o) {
   o->fdm_tensor_cores = 0;
   o->outer_df64 = 0;
   o->stream = nullptr;
+  o->weight_delta = MG_DELTA_DEFAULT;
 }
 
 mg_status mg_setup(double lx, double ly, double lz, int nx, int ny, int nz, int P, double penalty, int overlap,
@@ -809,6 +834,9 @@ mg_status mg_setup(double lx, double ly, double lz, int nx, int ny, int nz, int 
   if (o.fdm_tensor_cores < 0 || o.fdm_tensor_cores > 2) return MG_EINVAL;
   if (o.outer_df64 < 0 || o.outer_df64 > 1) return MG_EINVAL;
   if (o.weight_profile < MG_WEIGHT_QUINTIC || o.weight_profile > MG_WEIGHT_QUINTIC_NORMALISED) return MG_EINVAL;
+  if (o.weight_delta < MG_DELTA_DEFAULT || o.weight_delta > MG_DELTA_STRIP) return MG_EINVAL;
+  if (o.overlap_mode == MG_OVERLAP_LAYERS && o.weight_delta == MG_DELTA_STRIP) return MG_EINVAL;
+  if (o.overlap_mode == MG_OVERLAP_MAX && o.weight_delta != MG_DELTA_DEFAULT) return MG_EINVAL;
   if (o.overlap_mode != MG_OVERLAP_LAYERS && o.overlap_mode != MG_OVERLAP_WIDTH && o.overlap_mode != MG_OVERLAP_MAX)
     return MG_EINVAL;
   if (o.overlap_mode == MG_OVERLAP_WIDTH && !(o.overlap_frac >= 0.0 && o.overlap_frac <= 0.5)) return MG_EINVAL;
@@ -865,8 +893,10 @@ mg_status mg_setup(double lx, double ly, double lz, int nx, int ny, int nz, int 
         const int maxno = lv.P / 2 + 1;
         const int no = (o.overlap_mode == MG_OVERLAP_LAYERS) ? overlap : layers_from_width(lv.P, o.overlap_frac);
         lv.no[d] = std::min(no, maxno);
-        lv.delta[d] = (o.overlap_mode == MG_OVERLAP_LAYERS) ? layer_delta(lv.P, lv.no[d])
-                                                            : std::min(2.0 * o.overlap_frac, 1.0);
+        const bool strip = o.overlap_mode == MG_OVERLAP_WIDTH &&
+                           (o.weight_delta == MG_DELTA_DEFAULT || o.weight_delta == MG_DELTA_STRIP);
+        lv.delta[d] = strip ? std::min(2.0 * o.overlap_frac, 1.0)
+                            : layer_delta(lv.P, lv.no[d], o.weight_delta == MG_DELTA_NODE ? MG_DELTA_NODE : MG_DELTA_MID);
       }
       lv.m[d] = lv.n + 2 * lv.no[d];
     }
@@ -950,6 +980,9 @@ mg_status mg_bind_workspace(mg_ctx* c, void* dptr, size_t bytes) {
   CK(launch_setup(c));
   int st = 0;
   CK(cudaMemcpyAsync(&st, w.status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  c->tab32_host.assign(c->ws.tab_count, 0.0f);
+  CK(cudaMemcpyAsync(c->tab32_host.data(), w.tab32, c->ws.tab_count * sizeof(float), cudaMemcpyDeviceToHost,
+                     c->stream));
   // null mode of the coarse eigenbases: the smallest eigenvalue per direction
   for (int d = 0; d < 3; ++d) {
     std::vector<double> lam(c->Ng[d]);
@@ -985,6 +1018,21 @@ mg_status mg_vcycle_df64(mg_ctx* c, double* u, const double* f) {
   CK(launch_split_df64(c, u, ud, N));
   CK(launch_split_df64(c, f, fd, N));
   CK(vcycle_t<df64>(c, ud, fd, false, false));
+  CK(launch_join_df64(c, ud, u, N, 0));
+  return MG_OK;
+}
+
+mg_status mg_smooth_df64(mg_ctx* c, int level, double* u, const double* f, int nsteps) {
+  mg_status s = need_ready(c);
+  if (s != MG_OK) return s;
+  if (!check_level(c, level, true)) return MG_EINVAL;
+  if (!u || !f || u == f || nsteps < 0) return fail(c, MG_EINVAL, "bad arguments");
+  const int64_t N = c->lev[level].N;
+  df64* ud = reinterpret_cast<df64*>(c->ws.cg[5]);
+  df64* fd = reinterpret_cast<df64*>(c->ws.cg[6]);
+  CK(launch_split_df64(c, u, ud, N));
+  CK(launch_split_df64(c, f, fd, N));
+  for (int k = 0; k < nsteps; ++k) CK(smooth_step<df64>(c, level, ud, fd, false, false));
   CK(launch_join_df64(c, ud, u, N, 0));
   return MG_OK;
 }

@@ -305,6 +305,7 @@ struct mg_ctx {
   std::vector<GraphEntry> graphs;
   cudaStream_t cap_stream = nullptr;
   bool use_graphs = true;
+  std::vector<float> tab32_host;  // host copy of the FP32 tables (kernel parameters of the FP32 smoother)
   mutable bool prof_on = false;
   mutable std::vector<ProfRec> prof;
   mutable size_t prof_used = 0;
@@ -313,8 +314,12 @@ struct mg_ctx {
 namespace mgdg {
 
 // Kernel groups timed by the profiler (mg_profile_result kinds).
+// kProfSipg: the level operators inside the V-cycle; kProfOuter: the outer
+// iteration's fine-level residual or q = A p (FP64 or double-float);
+// kProfVector: the outer iteration's vector passes (inner products, updates,
+// mean projections, FP64 <-> FP32 / double-float conversions).
 enum ProfKind : int { kProfFdm = 0, kProfScatter, kProfSipg, kProfRestrict, kProfProlong, kProfCoarse, kProfVector,
-                      kProfKinds };
+                      kProfOuter, kProfKinds };
 
 // ---- batched execution (batch.cu) ----
 // Launch the recorded sequences of several problems on stream s, merged into
@@ -336,6 +341,10 @@ cudaError_t launch_setup_coarse_tables(const double len[3], const int ne[3], dou
 // out = mode==0 ? A u : f - A u, on level l, T = double | float.
 template <typename T>
 cudaError_t launch_sipg(const mg_ctx* c, int l, const T* u, const T* f, T* out, int residual);  // T: double, float, df64
+// FP32 operator with shared-memory element blocks and the coefficients as kernel
+// parameters (sipg_const.cu): orders 2, 4, 8, 16 on meshes that give every SM a
+// block; cudaErrorNotSupported otherwise.
+cudaError_t launch_sipg_c(const mg_ctx* c, int l, const float* u, const float* f, float* out, int residual);
 
 // ---- smoother (schwarz.cu) ----
 // Corrections of all subdomains from residual r into ws.corr, then
@@ -350,6 +359,10 @@ cudaError_t launch_scatter(const mg_ctx* c, int l, T* u, int accumulate);
 // kernel's first (shortened) wait runs out and it reports kDevTimeout.
 cudaError_t launch_fdm_tc(const mg_ctx* c, int l, const float* r, int self_test = 0);
 bool fdm_tc_fits(const mg_ctx* c, int l);
+// FP32 corrections with the 1D factors as kernel parameters (fdm_const.cu):
+// cubic odd widths 3..35; cudaErrorNotSupported otherwise.
+cudaError_t launch_fdm_c(const mg_ctx* c, int l, const float* r);
+bool fdm_c_applies(const mg_ctx* c, int l);
 
 // ---- transfers (transfer.cu) ----
 template <typename T>

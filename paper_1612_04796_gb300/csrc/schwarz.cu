@@ -355,6 +355,80 @@ __global__ void __launch_bounds__(256) k_scatter_n2(const T* __restrict__ corr, 
   scatter_n2_body<T, N>(plain_block(), corr, u, Ne, nx, ny, nz, g, accumulate);
 }
 
+// k_scatter_n2 with blocks aligned to elements: a block takes EPB whole
+// elements, so the element coordinates and the three per-direction tile
+// offsets of the covering subdomains are formed once per element (in shared
+// memory) instead of once per DOF; each DOF then adds its <= 8 contributions
+// in the order of k_scatter_n / k_scatter_n2 (identical bits).
+template <typename T, int N>
+__global__ void __launch_bounds__(256) k_scatter_e(const T* __restrict__ corr, T* __restrict__ u, int64_t Ne, int nx,
+                                                   int ny, int nz, SubShape g, int accumulate) {
+  pdl_entry();
+  constexpr int N3 = N * N * N, EPB = N3 >= 256 ? 1 : 256 / N3;
+  __shared__ int64_t sb[EPB][3][3];  // [element][direction][offset -1, 0, +1]: that direction's share of the tile offset
+  const int64_t mxyz = (int64_t)g.mx * g.my * g.mz;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int64_t e0 = (int64_t)blockIdx.x * EPB; e0 < Ne; e0 += (int64_t)gridDim.x * EPB) {
+    const int cnt = (int)(Ne - e0 < EPB ? Ne - e0 : EPB);
+    if (tid < cnt) {
+      const int e = (int)(e0 + tid), exy = e / nx;  // element indices fit in 32 bits
+      const int ex = e - exy * nx, ey = exy % ny, ez = exy / ny;
+      for (int o = 0; o < 3; ++o) {
+        sb[tid][0][o] = wrap(ex + o - 1, nx) * mxyz;
+        sb[tid][1][o] = wrap(ey + o - 1, ny) * ((int64_t)nx * mxyz);
+        sb[tid][2][o] = wrap(ez + o - 1, nz) * ((int64_t)nx * ny * mxyz);
+      }
+    }
+    __syncthreads();
+    for (int d = tid; d < cnt * N3; d += nt) {
+      const int ge = EPB == 1 ? 0 : d / N3;
+      const int loc = EPB == 1 ? d : d - ge * N3;
+      const int i = loc % N, j = (loc / N) % N, k = loc / (N * N);
+      // per direction the two candidates in increasing offset (an absent one
+      // repeats the own position and is masked out)
+      int oa[3][2], pa[3][2];
+      bool v[3];
+      const int t3[3] = {i, j, k}, no3[3] = {g.nox, g.noy, g.noz};
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const int t = t3[q], no = no3[q];
+        if (t < no) {
+          oa[q][0] = 0; pa[q][0] = no + N + t; oa[q][1] = 1; pa[q][1] = no + t; v[q] = true;
+        } else if (t >= N - no) {
+          oa[q][0] = 1; pa[q][0] = no + t; oa[q][1] = 2; pa[q][1] = t - (N - no); v[q] = true;
+        } else {
+          oa[q][0] = oa[q][1] = 1; pa[q][0] = pa[q][1] = no + t; v[q] = false;
+        }
+      }
+      int64_t ox[2], oy[2], oz[2];
+#pragma unroll
+      for (int a = 0; a < 2; ++a) {
+        ox[a] = sb[ge][0][oa[0][a]] + pa[0][a];
+        oy[a] = sb[ge][1][oa[1][a]] + (int64_t)g.mx * pa[1][a];
+        oz[a] = sb[ge][2][oa[2][a]] + (int64_t)g.mx * g.my * pa[2][a];
+      }
+      T val[8];
+#pragma unroll
+      for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+          for (int a = 0; a < 2; ++a) val[a + 2 * (b + 2 * c)] = corr[ox[a] + oy[b] + oz[c]];
+      T sum = 0;
+#pragma unroll
+      for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+          for (int a = 0; a < 2; ++a)
+            if ((a == 0 || v[0]) && (b == 0 || v[1]) && (c == 0 || v[2])) sum += val[a + 2 * (b + 2 * c)];
+      const int64_t dof = e0 * N3 + d;
+      u[dof] = accumulate ? u[dof] + sum : sum;
+    }
+    __syncthreads();
+  }
+}
+
 template <typename T>
 const T* table_of(const mg_ctx* c);
 template <>
@@ -372,6 +446,11 @@ cudaError_t launch_fdm(const mg_ctx* c, int l, const T* r) {
   if constexpr (std::is_same<T, float>::value) {
     if (lv.fdm_tc) {
       const cudaError_t e = launch_fdm_tc(c, l, r);
+      if (e != cudaErrorNotSupported) return e;
+    } else if (launch_recorder() == nullptr) {
+      // single solves: the factors as kernel parameters; batched solves keep
+      // the shared-memory kernel, whose body has a grouped twin
+      const cudaError_t e = launch_fdm_c(c, l, r);
       if (e != cudaErrorNotSupported) return e;
     }
   }
@@ -450,6 +529,21 @@ cudaError_t launch_scatter(const mg_ctx* c, int l, T* u, int accumulate) {
   const SubShape g{lv.m[0], lv.m[1], lv.m[2], lv.no[0], lv.no[1], lv.no[2]};
   c->nlaunch += 1;
   const bool two = 2 * lv.no[0] <= lv.n && 2 * lv.no[1] <= lv.n && 2 * lv.no[2] <= lv.n;
+  if (two && launch_recorder() == nullptr) {
+    // single solves: element-aligned blocks (batched solves keep k_scatter_n2, whose body has a twin)
+    const int n3 = lv.n * lv.n * lv.n, epb = n3 >= 256 ? 1 : 256 / n3;
+    const int64_t eblocks = std::min<int64_t>((c->Ne + epb - 1) / epb, 152 * 16);
+    switch (lv.n) {
+#define MGDG_SCE(N)                                                                                           \
+  case N:                                                                                                     \
+    launch_pdl(k_scatter_e<T, N>, (int)eblocks, 256, 0, c->stream, corr, u, c->Ne, c->ne[0], c->ne[1],        \
+               c->ne[2], g, accumulate);                                                                      \
+    return cudaGetLastError();
+      MGDG_SCE(3) MGDG_SCE(5) MGDG_SCE(9) MGDG_SCE(17) MGDG_SCE(33)
+#undef MGDG_SCE
+      default: break;
+    }
+  }
   if (two) {
     switch (lv.n) {
 #define MGDG_SC2(N)                                                                                           \

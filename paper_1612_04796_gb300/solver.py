@@ -14,6 +14,7 @@ from ._lib import MgOpts, load_library
 PRECISION = {"fp64": 0, "mixed": 1, "df64": 2}
 OVERLAP_MODE = {"layers": 0, "width": 1, "max": 2}
 PROFILE = {"quintic": 0, "linear": 1, "quintic_halves": 2, "quintic_normalised": 3}
+WEIGHT_DELTA = {"default": 0, "node": 1, "mid": 2, "strip": 3}
 
 
 class MGError(RuntimeError):
@@ -34,7 +35,7 @@ class MGSolver:
 
     def __init__(self, lengths, counts, P, penalty=2.0, overlap=1, precision="fp64", overlap_mode="layers",
                  overlap_frac=0.08, weight_profile="quintic", ns_pre=1, ns_post=1, ns_growth=1, device="cuda",
-                 stream=None, tensor_cores=False, outer_df64=False):
+                 stream=None, tensor_cores=False, outer_df64=False, weight_delta="default"):
         self.lib = load_library()
         self.device = torch.device(device)
         if self.device.type == "cuda" and self.device.index is None:
@@ -44,6 +45,7 @@ class MGSolver:
         opts.overlap_mode = OVERLAP_MODE[overlap_mode]
         opts.overlap_frac = float(overlap_frac)
         opts.weight_profile = PROFILE[weight_profile]
+        opts.weight_delta = WEIGHT_DELTA[weight_delta]
         opts.ns_pre, opts.ns_post, opts.ns_growth = int(ns_pre), int(ns_post), int(ns_growth)
         opts.precision = PRECISION[precision]
         opts.fdm_tensor_cores = {False: 0, True: 1, "auto": 2}[tensor_cores]
@@ -175,6 +177,14 @@ class MGSolver:
         self._check(self.lib.mg_smooth(self.ctx, level, _ptr(u), _ptr(f), int(nsteps)))
         return u
 
+    def smooth_df64(self, u, f, level=None, nsteps=1):
+        """Schwarz steps on FP64 vectors with double-float arithmetic (mg_smooth_df64)."""
+        level = self.L if level is None else level
+        self._vec(u, level, name="u")
+        self._vec(f, level, name="f")
+        self._check(self.lib.mg_smooth_df64(self.ctx, level, _ptr(u), _ptr(f), int(nsteps)))
+        return u
+
     def restrict_residual(self, u, f, level=None):
         level = self.L if level is None else level
         self._vec(u, level, name="u")
@@ -256,7 +266,8 @@ class MGSolver:
     def profile(self, enable=True):
         self._check(self.lib.mg_profile(self.ctx, int(bool(enable))))
 
-    PROFILE_KINDS = {"fdm": 0, "scatter": 1, "sipg": 2, "restrict": 3, "prolong": 4, "coarse": 5}
+    PROFILE_KINDS = {"fdm": 0, "scatter": 1, "sipg": 2, "restrict": 3, "prolong": 4, "coarse": 5, "vector": 6,
+                     "outer": 7}
 
     def profile_result(self, kind, level=-1):
         """(total ms, number of kernel groups) recorded for one kind / level."""

@@ -47,6 +47,7 @@ def test_defaults(lib):
 @pytest.mark.parametrize("bad", [dict(P=3), dict(P=1), dict(P=64), dict(counts=(2, 4, 4)), dict(counts=(4, 4, 513)),
                                  dict(overlap=-1), dict(lengths=(0.0, 1.0, 1.0)), dict(ns_pre=0, ns_post=0),
                                  dict(precision=7), dict(overlap_mode=1, overlap_frac=0.75),
+                                 dict(weight_delta=4), dict(weight_delta=3), dict(overlap_mode=2, weight_delta=1),
                                  dict(precision=1, fdm_tensor_cores=3)])
 def test_rejects_bad_arguments(lib, bad):
     st, ctx = _setup(lib, **bad)
@@ -149,3 +150,12 @@ def test_batch_solve_argument_checks(lib):
     assert lib.mg_solve_batch(ctypes.cast(ctxs, P), 1, *args) == 5       # MG_ENOTREADY: not bound
     assert lib.mg_batch_launches(ctx) == 0
     lib.mg_destroy(ctx)
+
+
+def test_weight_delta_readings_accepted(lib):
+    """Node-based half-width readings in both overlap modes, the strip reading
+    only for the geometric overlap."""
+    for mode, delta in ((0, 1), (0, 2), (1, 1), (1, 2), (1, 3), (2, 0)):
+        st, ctx = _setup(lib, P=16, overlap=2, overlap_mode=mode, overlap_frac=0.08, weight_delta=delta)
+        assert st == 0, (mode, delta)
+        lib.mg_destroy(ctx)

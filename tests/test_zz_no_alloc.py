@@ -47,6 +47,31 @@ def test_noalloc_coarse_solve_matches_context_entry_point(mg, lengths, counts):
         assert np.max(np.abs(got - want)) / np.max(np.abs(want)) < FP64_TOL
 
 
+def test_noalloc_second_call_takes_no_device_memory(mg):
+    """After a first call (which may load the module and so reserve the
+    array), a further call leaves the device's free memory unchanged."""
+    import torch
+    lib = mg.load_library()
+    lengths, counts = (1.0, 2.0, 1.0), (8, 6, 5)
+    N0 = 8 * counts[0] * counts[1] * counts[2]
+    f0 = torch.tensor(inputs.gaussian(N0, 33), device="cuda")
+    f0 -= f0.mean()
+    u0 = torch.empty_like(f0)
+    stream = torch.cuda.current_stream()
+
+    def call():
+        st = lib.mg_coarse_solve_noalloc(lengths[0], lengths[1], lengths[2], counts[0], counts[1], counts[2], 2.0,
+                                         _ptr(f0), _ptr(u0), ctypes.c_void_p(stream.cuda_stream))
+        torch.cuda.synchronize()
+        assert st == 0
+
+    call()
+    free0, _ = torch.cuda.mem_get_info()
+    call()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+
+
 def test_noalloc_rejects_sizes_beyond_the_maximum(mg):
     import torch
     lib = mg.load_library()
