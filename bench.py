@@ -77,8 +77,8 @@ WORKLOADS = {
 }
 WORKLOADS["serving512"] = dict(workload="serving stream: 512 solve requests, Poisson arrivals at 200/s (seed 5), periodic box "
                                 "[0,AR]x[0,1]x[0,1], AR ~ U[1,8], n^3 elements with n in {4,8,16,24,32}, P in {2,4,8,16}, "
-                                "N_O=4 (default; --overlap), Gaussian f, FP32 V(1,1) in FP64 PCG (outer A p in "
-                                "double-float), tol 1e-10, "
+                                "N_O=4 (default; --overlap), Gaussian f, FP32 V(1,1) in a PCG whose outer iteration runs in "
+                                "double-float (convergence confirmed on the FP64 residual), tol 1e-10, "
                                 "admitted by HBM footprint (smallest work first with aging; MG_SERVING_POLICY=fcfs "
                                 "for first come first served), "
                                 "one context and stream per slot; requests of <= 2^20 DOFs and one order admitted "
@@ -87,7 +87,7 @@ WORKLOADS["serving512"] = dict(workload="serving stream: 512 solve requests, Poi
 WORKLOADS["serving512_small"] = dict(workload="serving stream of small requests only: 512 solve requests, Poisson arrivals at "
                                      "5000/s (seed 5: the server is saturated), periodic box [0,AR]x[0,1]x[0,1], AR ~ U[1,8], n^3 elements with "
                                      "n in {4,8}, P in {2,4,8} (1,728 to 373,248 DOFs), N_O=4, Gaussian f, FP32 V(1,1) "
-                                     "in FP64 PCG (outer A p in double-float), tol 1e-10; the regime where launches, "
+                                     "in PCG (outer iteration in double-float), tol 1e-10; the regime where launches, "
                                      "not arithmetic, bound the throughput (MG_SERVING_BATCH_DOFS=0: no batched path)",
                                      sizes=[4, 8], orders=[2, 4, 8], rate=5000.0)
 WORKLOADS["batch16_p4"] = dict(workload="16 independent small problems solved together (mg_solve_batch: one launch per "
@@ -120,6 +120,9 @@ def parse_args():
     ap.add_argument("--overlap", type=int, default=None, help="override N_O of the workload")
     ap.add_argument("--precision", default=None, choices=["fp64", "mixed"], help="override the workload's precision")
     ap.add_argument("--cg", action="store_true", help="solve the workload with MG-CG instead of its default solver")
+    ap.add_argument("--outer-all", action="store_true",
+                    help="mixed MG-CG runs: the whole outer iteration (vectors, inner products, updates and "
+                         "q = A p) in double-float arithmetic")
     ap.add_argument("--outer-df64", action="store_true",
                     help="mixed runs: outer operator products q = A p in double-float (FP32-pair) arithmetic")
     ap.add_argument("--tensor-cores", default="off", choices=["off", "on", "auto"],
@@ -546,7 +549,9 @@ def run_mg(args):
             leg = {"value": world * N * args.steps / mix_total, "unit": "DOF/s",
                    "ms_per_step": sum(mix_ms) / args.steps, "iterations": its_ml[-1],
                    "solver": "MG-CG: FP32 V(1,1) preconditioner, FP64 inexact PCG",
-                   "outer_operator": "double-float (FP32 pairs, ~48-bit)" if outer_df64 else "FP64",
+                   "outer_operator": {False: "FP64", True: "double-float (FP32 pairs, ~48-bit)",
+                                      "all": "double-float, with the outer vectors, inner products and updates "
+                                             "(FP32 pairs, ~48-bit)"}[outer_df64],
                    "fdm_tensor_cores": args.tensor_cores,
                    "fdm_tensor_cores_by_level": [sm_.fdm_tensor_cores(l) for l in range(1, sm_.L + 1)],
                    "true_relres_fp64": true_rel, "max_rel_diff_vs_fp64_solution": err,
@@ -587,6 +592,7 @@ def run_mg(args):
         line["mixed"] = mixed_leg(args.outer_df64)
         if not args.outer_df64:
             line["mixed_df64"] = mixed_leg(True)
+        line["mixed_df64_all"] = mixed_leg("all")
 
     if not args.no_configs and world == 1:
         # the metric's own configurations beside the main line: the anisotropic
@@ -677,7 +683,8 @@ def workload_line(name, steps, warmup, overlap=None, precision=None, cg=False, o
     true_rel = float(torch.linalg.norm(s64.residual(u, b)) / torch.linalg.norm(b))
     if W["precision"] == "mixed":
         W["fdm_tensor_cores"] = tensor_cores
-        W["outer_operator"] = "double-float (FP32 pairs)" if outer_df64 else "FP64"
+        W["outer_operator"] = {False: "FP64", True: "double-float (FP32 pairs)",
+                               "all": "double-float outer iteration (FP32 pairs)"}[outer_df64]
         W["fdm_tensor_cores_by_level"] = [s.fdm_tensor_cores(l) for l in range(1, s.L + 1)]
     fp64 = W["precision"] == "fp64"
     pk, _ = peaks()
@@ -705,7 +712,8 @@ def workload_line(name, steps, warmup, overlap=None, precision=None, cg=False, o
 def run_workload(args):
     """One configuration other than the default line (`--workload NAME`)."""
     line = workload_line(args.workload, args.steps, args.warmup, overlap=args.overlap, precision=args.precision,
-                         cg=args.cg, outer_df64=args.outer_df64, tensor_cores=args.tensor_cores)
+                         cg=args.cg, outer_df64="all" if args.outer_all else args.outer_df64,
+                         tensor_cores=args.tensor_cores)
     print(json.dumps(line), flush=True)
 
 
@@ -823,7 +831,8 @@ def serving_line(name, overlap=None, n_req=None):
                        hbm_budget_gb=srv.budget / 1e9, total_dofs=dofs,
                        admission=policy + (" (aging after %.0f s)" % srv.max_wait
                                            if policy == "smallest" else ""),
-                       outer_operator="double-float (FP32 pairs)" if srv.outer_df64 else "FP64",
+                       outer_operator={False: "FP64", True: "double-float (FP32 pairs)",
+                                       "all": "double-float outer iteration (FP32 pairs)"}[srv.outer_df64],
                        batch_max=srv.batch_max, batch_dofs=srv.batch_dofs),
         "latency": summ, "max_concurrent": srv.max_active,
         "batched_requests": int(sum(r.batch > 1 for r in res)),

@@ -104,10 +104,16 @@ typedef struct {
                             between contexts) */
   int outer_df64;        /* MG_MIXED with use_cg: 1 = the outer products q = A p in double-float
                             arithmetic (pairs of FP32, about 48 significant bits; FP64 vectors,
-                            inner products and updates); 0 = FP64 (default) */
+                            inner products and updates); 2 = the whole outer iteration in
+                            double-float (vectors x, r, p, q stored as pairs; q = A p, inner
+                            products, updates on the FP32 pipes; the initial residual and the
+                            returned solution FP64); 0 = FP64 (default) */
   void* stream;          /* cudaStream_t; NULL = default stream */
   int weight_delta;      /* mg_weight_delta, default MG_DELTA_DEFAULT; MG_OVERLAP_MAX takes only
                             the default */
+  int autotune;          /* 1 = mg_bind_workspace times the kernel variants of every level's
+                            smoother, operator and scatter (as the hierarchy's arithmetic runs
+                            them) and keeps the fastest; 0 = the fixed defaults (default) */
 } mg_opts;
 
 /* Fill *o with the defaults above. */
@@ -172,6 +178,14 @@ mg_status mg_selftest_bounded_wait(mg_ctx* ctx, int level, int* timed_out);
 /* Kernel of the FP32 smoother contractions on a level after mg_bind_workspace:
  * 1 tensor cores, 0 CUDA cores, -1 bad level. */
 int mg_level_fdm_tensor_cores(const mg_ctx* ctx, int level);
+
+/* Kernel variant of single solves on a level (what mg_opts.autotune chose, or
+ * the default): kind 0 smoother, 1 operator, 2 scatter; returns 0 for the
+ * default kernel (FP32 smoother with the 1D factors as kernel parameters;
+ * FP32 / double-float operator on shared-memory element blocks;
+ * element-aligned scatter), 1 for the alternative (shared-memory smoother,
+ * plain operator, plain scatter), -1 for a bad level or kind. */
+int mg_level_kernel_variant(const mg_ctx* ctx, int level, int kind);
 
 /* Physical coordinates of the nodes of `level` into x, y, z (device, N_l each). */
 mg_status mg_node_coords(mg_ctx* ctx, int level, double* x, double* y, double* z);

@@ -26,6 +26,7 @@ class MgOpts(ctypes.Structure):
         ("outer_df64", ctypes.c_int),
         ("stream", ctypes.c_void_p),
         ("weight_delta", ctypes.c_int),
+        ("autotune", ctypes.c_int),
     ]
 
 
@@ -111,6 +112,7 @@ SIGNATURES = {
     "mg_level_layers": (_I, [_P, _I]),
     "mg_level_layers_dir": (_I, [_P, _I, _I]),
     "mg_level_fdm_tensor_cores": (_I, [_P, _I]),
+    "mg_level_kernel_variant": (_I, [_P, _I, _I]),
     "mg_apply_sipg_df64": (_S, [_P, _I, _P, _P]),
     "mg_vcycle_df64": (_S, [_P, _P, _P]),
     "mg_smooth_df64": (_S, [_P, _I, _P, _P, _I]),

@@ -5,9 +5,10 @@
 // The solver's launch sequence for one problem is recorded (launch_pdl with a
 // recorder installed) instead of launched; the sequences of the problems are
 // then merged: the records of one problem keep their order, and at each step
-// the kernel found at the head of the most sequences is launched once through
-// its grouped twin (k_grouped), every problem getting its own block range and
-// parameters.  Problems of different sizes, aspect ratios and even kernel
+// one kernel found at the heads of the sequences (that of the sequence with
+// the most records left) is launched once through its grouped twin
+// (k_grouped) for every sequence that has it at its head, each problem
+// getting its own block range and parameters.  Problems of different sizes, aspect ratios and even kernel
 // variants (a small mesh takes the direction-split operator) merge as far as
 // their sequences agree.
 #include "mg_internal.h"
@@ -44,17 +45,29 @@ cudaError_t launch_merged(const std::vector<LaunchRecorder>& seqs, cudaStream_t 
   std::vector<size_t> head(B, 0);
   long long n_launch = 0;
   for (;;) {
-    // the kernel at the head of the most sequences (ties: the lowest problem index)
+    // The next kernel: the head of the sequence with the most records left
+    // (ties: the head shared by the most sequences, then the lowest problem
+    // index).  Sequences of different kernel variants differ by inserted
+    // launches (a direction-split operator is three launches where the
+    // element-block operator is one) and share their tails, so serving the
+    // longest remaining sequence first brings them back into step at the
+    // next common kernel instead of leaving one group behind.
     int best = -1, best_count = 0;
+    size_t best_left = 0;
     for (int i = 0; i < B; ++i) {
       if (head[i] >= seqs[i].recs.size()) continue;
       const LaunchRec& r = seqs[i].recs[head[i]];
       int count = 0;
+      size_t left = 0;
       for (int j = 0; j < B; ++j)
-        if (head[j] < seqs[j].recs.size() && same_kernel(seqs[j].recs[head[j]], r)) ++count;
-      if (count > best_count) {
+        if (head[j] < seqs[j].recs.size() && same_kernel(seqs[j].recs[head[j]], r)) {
+          ++count;
+          left = std::max(left, seqs[j].recs.size() - head[j]);
+        }
+      if (left > best_left || (left == best_left && count > best_count)) {
         best = i;
         best_count = count;
+        best_left = left;
       }
     }
     if (best < 0) break;

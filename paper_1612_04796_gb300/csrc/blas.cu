@@ -389,6 +389,20 @@ cudaError_t reduce(const mg_ctx* c, const T* x, const T* y, int64_t n, int mode,
 
 }  // namespace
 
+int reduction_blocks(int64_t n) { return red_blocks(n); }
+
+cudaError_t launch_final_sum(const mg_ctx* c, int nb, int slot) {
+  launch_pdl<final_body>(k_final, 1, kThreads, 0, c->stream, c->ws.red, nb, c->ws.scal, slot);
+  c->nlaunch += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_update_final(const mg_ctx* c, int nb, int64_t n) {
+  launch_pdl<cg_update_final_body>(k_cg_update_final, 1, kThreads, 0, c->stream, c->ws.red, nb, c->ws.scal, n);
+  c->nlaunch += 1;
+  return cudaGetLastError();
+}
+
 cudaError_t launch_dot(const mg_ctx* c, const double* x, const double* y, int64_t n, int slot) {
   return reduce<double>(c, x, y, n, 0, slot);
 }

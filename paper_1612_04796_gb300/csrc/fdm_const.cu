@@ -10,12 +10,13 @@
 // width every coefficient is an immediate constant-bank operand of its FMA:
 // the only shared-memory traffic left is the subdomain tile itself.
 //
-// One block takes SPB subdomains: their residual tiles r_s = R_s r are
-// gathered with coalesced loads (x fastest) into shared memory, the five line
-// passes (x forward; y forward; z forward, division by the eigenvalue sums,
-// z backward; y backward; x backward with the weights folded into SW) run in
-// place, and the weighted correction tiles are written back with coalesced
-// stores to the correction buffer, in the layout of the other smoother kernels.
+// One block takes SPB subdomains, one thread per 1D line and pass: the first
+// pass gathers the x-lines of r_s = R_s r from the element and its
+// neighbours and transforms them into the shared-memory tile, three more run
+// in place (y forward; z forward, division by the eigenvalue sums, z
+// backward; y backward), and the last (x backward, weights folded into SW)
+// writes the weighted correction tile to the correction buffer, in the layout
+// of the other smoother kernels.
 #include <algorithm>
 #include <atomic>
 
@@ -40,9 +41,9 @@ struct FdmCArgs {
   using Sh = FdmCShape<M>;
   const float* r;
   float* corr;
+  const float* dinv;                 // 1 / (lam_x[i] + lam_y[j] + lam_z[k]) at i + M (j + M k)
   int64_t Ne;
   int nx, ny, nz, n, no;
-  float lam[3][M];                   // 1D eigenvalues
   float se[3][Sh::ne * Sh::ne];      // S[a][p], a, p <= h         (forward, even modes)
   float so[3][Sh::ho * Sh::ho];      // S[a][h+1+q], a, q < h      (forward, odd modes)
   float we[3][Sh::ne * Sh::ne];      // SW[a][p], a, p <= h        (backward, even modes)
@@ -105,37 +106,30 @@ __global__ void __launch_bounds__(FdmCShape<M>::threads) k_fdm_c(const __grid_co
   using Sh = FdmCShape<M>;
   constexpr int M2 = Sh::M2, M3 = Sh::M3, SPB = Sh::spb;
   extern __shared__ __align__(16) float fc_tile[];  // SPB tiles of M^3, node (i, j, k) at i + M (j + M k)
-  __shared__ int nb[SPB * 27];                      // the 27 elements around each subdomain's core
   const int n = a.n, no = a.no, n3 = n * n * n;
+  const float* __restrict__ dinv = a.dinv;
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int64_t s0 = (int64_t)blockIdx.x * SPB; s0 < a.Ne; s0 += (int64_t)gridDim.x * SPB) {
-    const int cnt = (int)(a.Ne - s0 < SPB ? a.Ne - s0 : SPB);
-    for (int i = tid; i < cnt * 27; i += nt) {
-      const int g = i / 27, k = i - g * 27;
+    const int lines = (int)(a.Ne - s0 < SPB ? a.Ne - s0 : SPB) * M2;
+    // pass 1: gather the x-lines of r_s = R_s r (left strip, element, right
+    // strip), x forward
+    for (int ln = tid; ln < lines; ln += nt) {
+      const int g = ln / M2, l2 = ln - g * M2, b = l2 % M, c = l2 / M;
       const int s = (int)(s0 + g), sxy = s / a.nx;  // element indices fit in 32 bits
       const int sx = s - sxy * a.nx, sy = sxy % a.ny, sz = sxy / a.ny;
-      const int dx = k % 3 - 1, dy = (k / 3) % 3 - 1, dz = k / 9 - 1;
-      nb[i] = fc_wrap(sx + dx, a.nx) + a.nx * (fc_wrap(sy + dy, a.ny) + a.ny * fc_wrap(sz + dz, a.nz));
-    }
-    __syncthreads();
-    // gather r_s = R_s r: x fastest, so a warp reads runs of contiguous values
-    for (int i = tid; i < cnt * M3; i += nt) {
-      const int g = i / M3, k = i - g * M3;
-      const int ia = k % M, ib = (k / M) % M, ic = k / M2;
-      const int dx = ia < no ? 0 : (ia < no + n ? 1 : 2), jx = ia - no + (dx == 0 ? n : (dx == 2 ? -n : 0));
-      const int dy = ib < no ? 0 : (ib < no + n ? 1 : 2), jy = ib - no + (dy == 0 ? n : (dy == 2 ? -n : 0));
-      const int dz = ic < no ? 0 : (ic < no + n ? 1 : 2), jz = ic - no + (dz == 0 ? n : (dz == 2 ? -n : 0));
-      fc_tile[i] = a.r[(int64_t)nb[g * 27 + dx + 3 * (dy + 3 * dz)] * n3 + jx + n * (jy + n * jz)];
-    }
-    __syncthreads();
-    const int lines = cnt * M2;
-    // pass 1: x forward
-    for (int ln = tid; ln < lines; ln += nt) {
-      float* line = fc_tile + (ln / M2) * M3 + M * (ln % M2);
+      const int dy = b < no ? -1 : (b < no + n ? 0 : 1), iy = b - no + (dy < 0 ? n : (dy > 0 ? -n : 0));
+      const int dz = c < no ? -1 : (c < no + n ? 0 : 1), iz = c - no + (dz < 0 ? n : (dz > 0 ? -n : 0));
+      const int64_t row = (int64_t)a.nx * (fc_wrap(sy + dy, a.ny) + (int64_t)a.ny * fc_wrap(sz + dz, a.nz));
+      const int loc = n * (iy + n * iz);
+      // position t of the line in the left / centre / right element
+      const float* rl = a.r + (fc_wrap(sx - 1, a.nx) + row) * n3 + loc + (n - no);
+      const float* rc = a.r + (sx + row) * n3 + loc - no;
+      const float* rr = a.r + (fc_wrap(sx + 1, a.nx) + row) * n3 + loc - (no + n);
       float x[M], y[M];
 #pragma unroll
-      for (int t = 0; t < M; ++t) x[t] = line[t];
+      for (int t = 0; t < M; ++t) x[t] = __ldg((t < no ? rl : (t < no + n ? rc : rr)) + t);
       fwd_c<M, 0>(a, x, y);
+      float* line = fc_tile + g * M3 + M * l2;
 #pragma unroll
       for (int t = 0; t < M; ++t) line[t] = y[t];
     }
@@ -156,13 +150,12 @@ __global__ void __launch_bounds__(FdmCShape<M>::threads) k_fdm_c(const __grid_co
     for (int ln = tid; ln < lines; ln += nt) {
       const int l2 = ln % M2;
       float* line = fc_tile + (ln / M2) * M3 + l2;
-      const float lxy = a.lam[0][l2 % M] + a.lam[1][l2 / M];
       float x[M], y[M];
 #pragma unroll
       for (int t = 0; t < M; ++t) x[t] = line[t * M2];
       fwd_c<M, 2>(a, x, y);
 #pragma unroll
-      for (int t = 0; t < M; ++t) y[t] *= __frcp_rn(lxy + a.lam[2][t]);
+      for (int t = 0; t < M; ++t) y[t] *= __ldg(dinv + l2 + t * M2);
       bwd_c<M, 2>(a, y, x);
 #pragma unroll
       for (int t = 0; t < M; ++t) line[t * M2] = x[t];
@@ -180,20 +173,18 @@ __global__ void __launch_bounds__(FdmCShape<M>::threads) k_fdm_c(const __grid_co
       for (int t = 0; t < M; ++t) line[t * M] = x[t];
     }
     __syncthreads();
-    // pass 5: x backward (weights folded into SW)
+    // pass 5: x backward (weights folded into SW), straight to the correction buffer
     for (int ln = tid; ln < lines; ln += nt) {
-      float* line = fc_tile + (ln / M2) * M3 + M * (ln % M2);
+      const int g = ln / M2, l2 = ln - g * M2;
+      const float* line = fc_tile + g * M3 + M * l2;
+      float* out = a.corr + (s0 + g) * M3 + M * l2;
       float x[M], y[M];
 #pragma unroll
       for (int t = 0; t < M; ++t) y[t] = line[t];
       bwd_c<M, 0>(a, y, x);
 #pragma unroll
-      for (int t = 0; t < M; ++t) line[t] = x[t];
+      for (int t = 0; t < M; ++t) out[t] = x[t];
     }
-    __syncthreads();
-    // the weighted correction tiles, coalesced
-    float* out = a.corr + s0 * M3;
-    for (int i = tid; i < cnt * M3; i += nt) out[i] = fc_tile[i];
     __syncthreads();
   }
 }
@@ -209,6 +200,7 @@ cudaError_t launch_fdm_c_m(const mg_ctx* c, int l, const float* r) {
   FdmCArgs<M> a;
   a.r = r;
   a.corr = static_cast<float*>(c->ws.corr);
+  a.dinv = c->ws.tab32 + lv.dinv;
   a.Ne = c->Ne;
   a.nx = c->ne[0];
   a.ny = c->ne[1];
@@ -218,7 +210,6 @@ cudaError_t launch_fdm_c_m(const mg_ctx* c, int l, const float* r) {
   for (int d = 0; d < 3; ++d) {
     const float* S = tab + lv.t[d].S;
     const float* SW = tab + lv.t[d].SW;
-    for (int t = 0; t < M; ++t) a.lam[d][t] = tab[lv.t[d].lam + t];
     for (int t = 0; t < ne; ++t)
       for (int p = 0; p < ne; ++p) {
         a.se[d][t * ne + p] = S[t * M + p];

@@ -290,12 +290,7 @@ cudaError_t launch_fdm_m(const FdmArgs<T>& a, int blocks, int threads, size_t /*
     cudaError_t e = cudaFuncSetAttribute(k_fdm_m<T, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  // grouped twin (batched solves) for the FP32 smoother only: the FP64 and
-  // double-float hierarchies are not batched by the serving path
-  if constexpr (std::is_same<T, float>::value)
-    launch_pdl<fdm_m_body<T, M>>(k_fdm_m<T, M>, blocks, threads, smem, s, a);
-  else
-    launch_pdl(k_fdm_m<T, M>, blocks, threads, smem, s, a);
+  launch_pdl<fdm_m_body<T, M>>(k_fdm_m<T, M>, blocks, threads, smem, s, a);  // with its grouped twin
   return cudaGetLastError();
 }
 

@@ -253,7 +253,8 @@ cudaError_t run_graph(mg_ctx* c, int kind, const void* a, const void* b, F body)
   return cudaGraphLaunch(exec, c->stream);
 }
 
-enum GraphKind : int { kGraphMgCycle = 1, kGraphPrecond, kGraphVcycle, kGraphVcycle32, kGraphCgA, kGraphCgB };
+enum GraphKind : int { kGraphMgCycle = 1, kGraphPrecond, kGraphVcycle, kGraphVcycle32, kGraphCgA, kGraphCgB,
+                       kGraphOdfA, kGraphOdfB };
 
 // ---- level vector views ----
 template <typename T>
@@ -418,6 +419,64 @@ cudaError_t choose_fdm_kernels(mg_ctx* c) {
   return e;
 }
 
+// Autotuner (mg_opts.autotune): on every level, time each kernel variant of
+// the smoother, the operator and the scatter as the hierarchy's arithmetic
+// runs them (CUDA events, one warm-up launch and three timed launches each,
+// inputs zeroed), and keep the faster one per (kernel, level).
+template <typename T>
+cudaError_t autotune_levels_t(mg_ctx* c) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  auto timed = [&](auto&& run, float* ms) -> cudaError_t {
+    cudaError_t er;
+    if ((er = run()) != cudaSuccess) return er;
+    if ((er = cudaEventRecord(e0, c->stream)) != cudaSuccess) return er;
+    for (int k = 0; k < 3; ++k)
+      if ((er = run()) != cudaSuccess) return er;
+    if ((er = cudaEventRecord(e1, c->stream)) != cudaSuccess) return er;
+    if ((er = cudaEventSynchronize(e1)) != cudaSuccess) return er;
+    return cudaEventElapsedTime(ms, e0, e1);
+  };
+  for (int l = 1; l <= c->L && e == cudaSuccess; ++l) {
+    LevelInfo& lv = c->lev[l];
+    T* u = lvec<T>(lv.u);
+    T* f = lvec<T>(lv.f);
+    T* r = lvec<T>(lv.r);
+    if ((e = launch_zero<T>(c, u, lv.N)) != cudaSuccess) break;
+    if ((e = launch_zero<T>(c, f, lv.N)) != cudaSuccess) break;
+    float t[2] = {0.f, 0.f};
+    if (std::is_same<T, float>::value && !lv.fdm_tc) {
+      for (int v = 0; v < 2 && e == cudaSuccess; ++v) {
+        lv.fdm_plain = v;
+        e = timed([&]() { return launch_fdm<T>(c, l, f); }, &t[v]);
+      }
+      lv.fdm_plain = t[1] < t[0] ? 1 : 0;
+    }
+    if (!std::is_same<T, double>::value) {
+      for (int v = 0; v < 2 && e == cudaSuccess; ++v) {
+        lv.sipg_plain = v;
+        e = timed([&]() { return launch_sipg<T>(c, l, u, f, r, 1); }, &t[v]);
+      }
+      lv.sipg_plain = t[1] < t[0] ? 1 : 0;
+    }
+    for (int v = 0; v < 2 && e == cudaSuccess; ++v) {
+      lv.scatter_plain = v;
+      e = timed([&]() { return launch_scatter<T>(c, l, u, 0); }, &t[v]);
+    }
+    lv.scatter_plain = t[1] < t[0] ? 1 : 0;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  return e;
+}
+
+cudaError_t autotune_levels(mg_ctx* c) {
+  if (c->opts.precision == MG_MIXED) return autotune_levels_t<float>(c);
+  if (c->opts.precision == MG_DF64) return autotune_levels_t<df64>(c);
+  return autotune_levels_t<double>(c);
+}
+
 // The first direction of the PCG iteration: z = B r projected to zero mean,
 // p = z, rz = r . z (and p in double-float for the outer operator).
 cudaError_t cg_start(const mg_ctx* c, double* r, double* z, double* p, df64* pdf) {
@@ -492,6 +551,97 @@ cudaError_t cg_step_b(const mg_ctx* c, double* p, double* r, double* q, double* 
   return launch_cg_direction<double>(c, p, z, q, r, N);
 }
 
+// ---- MG-CG with the outer iteration in double-float (mg_opts.outer_df64 = 2) ----
+// The outer vectors live in the FP64 work vectors, reinterpreted as df64
+// pairs: x in cg[7], r in cg[1], p in cg[3], q in cg[4], f in cg[0]; the
+// FP32 preconditioner reads lev[L].f and writes lev[L].u.
+bool outer_all_df64(const mg_ctx* c) { return c->opts.outer_df64 == 2 && c->opts.precision == MG_MIXED; }
+
+struct OdfVecs {
+  double* x64;
+  df64 *x, *r, *p, *q;
+  float *f32, *z32;
+};
+
+OdfVecs odf_vecs(const mg_ctx* c) {
+  OdfVecs v;
+  v.x64 = c->ws.cg[7];
+  v.x = reinterpret_cast<df64*>(c->ws.cg[7]);
+  v.r = reinterpret_cast<df64*>(c->ws.cg[1]);
+  v.p = reinterpret_cast<df64*>(c->ws.cg[3]);
+  v.q = reinterpret_cast<df64*>(c->ws.cg[4]);
+  v.f32 = lvec<float>(c->lev[c->L].f);
+  v.z32 = lvec<float>(c->lev[c->L].u);
+  return v;
+}
+
+// The first direction: x (FP64, = u), f and r (FP64, zero mean, scal[Sum]
+// its sum, scal[RR] its square norm) are split into pairs, q = 0, z = B r in
+// FP32, p = z - mean(z), rz = z'.r'.  Launches only.
+cudaError_t odf_start(const mg_ctx* c, const double* u, const double* f) {
+  const int64_t N = c->lev[c->L].N;
+  const OdfVecs v = odf_vecs(c);
+  cudaError_t e;
+  if ((e = launch_split_df64(c, f, reinterpret_cast<df64*>(c->ws.cg[0]), N)) != cudaSuccess) return e;
+  if ((e = cudaMemcpyAsync(v.x64, u, N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream)) != cudaSuccess)
+    return e;
+  if ((e = launch_odf_split(c, v.x64, N)) != cudaSuccess) return e;
+  if ((e = launch_odf_split(c, c->ws.cg[1], N)) != cudaSuccess) return e;
+  if ((e = launch_zero<double>(c, c->ws.cg[4], N)) != cudaSuccess) return e;
+  if ((e = launch_odf_to_f32(c, v.r, v.f32, N)) != cudaSuccess) return e;
+  if ((e = vcycle_t<float>(c, v.z32, v.f32, true, false)) != cudaSuccess) return e;
+  return launch_odf_direction(c, v.p, v.z32, v.q, v.r, N, 1);
+}
+
+// q = A p; alpha; x, r updated; rr; the next preconditioner input.  Launches only.
+cudaError_t odf_step_a(const mg_ctx* c) {
+  const int L = c->L;
+  const int64_t N = c->lev[L].N;
+  const OdfVecs v = odf_vecs(c);
+  cudaError_t e;
+  {
+    ProfScope ps(c, kProfOuter, L);
+    if ((e = launch_sipg<df64>(c, L, v.p, nullptr, v.q, 0)) != cudaSuccess) return e;
+  }
+  ProfScope pv(c, kProfVector, L);
+  return launch_odf_update(c, v.x, v.p, v.r, v.q, v.f32, N);
+}
+
+// The true residual of the iterate (residual replacement): r = f - A x
+// evaluated directly (double-float operator with compensated inner products:
+// its error is a few 2^-48 of |f|, far below the tolerance), written over
+// the recurrence residual, with scal[Sum], scal[RR] (|r - mean(r)|^2).
+// Launches only.  The 48-bit recurrence residual drifts from the true one
+// over many iterations (by about 7 % after 85), so convergence is confirmed
+// on this residual, and a failed check continues from it (odf_replace).
+cudaError_t odf_true_residual(const mg_ctx* c) {
+  const int L = c->L;
+  const int64_t N = c->lev[L].N;
+  const OdfVecs v = odf_vecs(c);
+  cudaError_t e;
+  if ((e = launch_sipg<df64>(c, L, v.x, reinterpret_cast<const df64*>(c->ws.cg[0]), v.r, 1)) != cudaSuccess)
+    return e;
+  return launch_odf_residual_norm(c, v.r, N);
+}
+
+// After a failed check: the next preconditioner input from the replaced
+// residual.  Launches only.
+cudaError_t odf_replace(const mg_ctx* c) {
+  const OdfVecs v = odf_vecs(c);
+  return launch_odf_to_f32(c, v.r, v.f32, c->lev[c->L].N);
+}
+
+// z = B r (FP32 V-cycle), beta, rz, p.  Launches only.
+cudaError_t odf_step_b(const mg_ctx* c) {
+  const int L = c->L;
+  const int64_t N = c->lev[L].N;
+  const OdfVecs v = odf_vecs(c);
+  cudaError_t e;
+  if ((e = vcycle_t<float>(c, v.z32, v.f32, true, false)) != cudaSuccess) return e;
+  ProfScope pv(c, kProfVector, L);
+  return launch_odf_direction(c, v.p, v.z32, v.q, v.r, N, 0);
+}
+
 mg_status solve_impl(mg_ctx* c, double* u, const double* f, double tol, int maxit, int use_cg, int* iters,
                      double* relres, double* history) {
   const int L = c->L;
@@ -545,9 +695,11 @@ mg_status solve_impl(mg_ctx* c, double* u, const double* f, double tol, int maxi
     double* z = c->ws.cg[2];
     double* p = c->ws.cg[3];
     double* q = c->ws.cg[4];
+    const bool odf = outer_all_df64(c);
     CK(launch_sipg<double>(c, L, x, f, r, 1));
     CK(launch_sum(c, r, N, kSlotSum));
     CK(launch_sub_mean(c, r, N, kSlotSum));
+    if (odf) CK(launch_sum(c, r, N, kSlotSum));  // sum(r) of the projected r, used by the first direction
     CK(launch_dot(c, r, r, N, kSlotRR));
     double rr = read_scalar(c, kSlotRR, &err);
     CK(err);
@@ -555,13 +707,42 @@ mg_status solve_impl(mg_ctx* c, double* u, const double* f, double tol, int maxi
     if (history) history[0] = r0;
     if (!std::isfinite(r0)) return fail(c, MG_EINVAL, "initial residual is not finite (NaN or Inf in u or f)");
     converged = r0 == 0.0;
+    if (odf) {
+      // the outer iteration in double-float pairs; x returns to u (FP64) at the end
+      if (!converged) CK(odf_start(c, x, f));
+      bool started = !converged;
+      while (!converged && it < maxit) {
+        ++it;
+        CK(run_graph(c, kGraphOdfA, x, f, [&]() { return odf_step_a(c); }));
+        double v = read_scalar(c, kSlotRR, &err);
+        CK(err);
+        rn = sqrt(v);
+        if (history) history[it] = rn;
+        if (!std::isfinite(rn)) return fail(c, MG_ENOCONV, "residual became non-finite");
+        if (rn <= tol * r0) {
+          // confirm on the true residual of the iterate
+          CK(odf_true_residual(c));
+          double t = read_scalar(c, kSlotRR, &err);
+          CK(err);
+          rn = sqrt(t);
+          if (history) history[it] = rn;
+          if (rn <= tol * r0) {
+            converged = true;
+            break;
+          }
+          CK(odf_replace(c));
+        }
+        CK(run_graph(c, kGraphOdfB, x, f, [&]() { return odf_step_b(c); }));
+      }
+      if (started) CK(launch_join_df64(c, reinterpret_cast<const df64*>(c->ws.cg[7]), x, N, 0));
+    }
     // double-float copies of p and q for the outer operator (mg_opts.outer_df64), in the
     // smoother's correction buffer: written after each preconditioner, read before the next
     const bool df = c->opts.outer_df64 && c->opts.precision != MG_FP64;
     df64* pdf = df ? static_cast<df64*>(c->ws.corr) : nullptr;
     df64* qdf = df ? pdf + N : nullptr;
-    if (!converged) CK(cg_start(c, r, z, p, pdf));
-    while (!converged && it < maxit) {
+    if (!converged && !odf) CK(cg_start(c, r, z, p, pdf));
+    while (!converged && !odf && it < maxit) {
       ++it;
       CK(run_graph(c, kGraphCgA, x, f, [&]() { return cg_step_a(c, x, p, r, q, pdf, qdf); }));
       double v = read_scalar(c, kSlotRR, &err);
@@ -735,6 +916,7 @@ mg_status solve_batch_impl(std::vector<BatchMember>& ms, cudaStream_t s, double 
     if ((e2 = launch_sipg<double>(m.c, m.c->L, m.x, m.f, m.r, 1)) != cudaSuccess) return e2;
     if ((e2 = launch_sum(m.c, m.r, N, kSlotSum)) != cudaSuccess) return e2;
     if ((e2 = launch_sub_mean(m.c, m.r, N, kSlotSum)) != cudaSuccess) return e2;
+    if (outer_all_df64(m.c) && (e2 = launch_sum(m.c, m.r, N, kSlotSum)) != cudaSuccess) return e2;
     return launch_dot(m.c, m.r, m.r, N, kSlotRR);
   }));
   BCK(batch_read(ms, kSlotRR, s, v, launches));
@@ -749,12 +931,20 @@ mg_status solve_batch_impl(std::vector<BatchMember>& ms, cudaStream_t s, double 
     }
   }
   // The cudaMemcpyAsync of cg_start is not a kernel: the first direction runs per problem.
-  for (auto& m : ms)
+  std::vector<bool> odf_started(ms.size(), false);
+  for (int i = 0; i < (int)ms.size(); ++i) {
+    BatchMember& m = ms[i];
     if (m.active) {
       const long long n0 = m.c->nlaunch;
-      BCK(cg_start(m.c, m.r, m.z, m.p, m.pdf));
+      if (outer_all_df64(m.c)) {
+        BCK(odf_start(m.c, m.x, m.f));
+        odf_started[i] = true;
+      } else {
+        BCK(cg_start(m.c, m.r, m.z, m.p, m.pdf));
+      }
       *launches += m.c->nlaunch - n0;
     }
+  }
   BatchCache cache;
   cache.s = s;
   for (int it = 1; it <= maxit; ++it) {
@@ -762,7 +952,11 @@ mg_status solve_batch_impl(std::vector<BatchMember>& ms, cudaStream_t s, double 
     for (auto& m : ms) any = any || m.active;
     if (!any) break;
     BCK(batch_step(
-        ms, s, launches, [&](BatchMember& m) { return cg_step_a(m.c, m.x, m.p, m.r, m.q, m.pdf, m.qdf); }, &cache, 1));
+        ms, s, launches,
+        [&](BatchMember& m) {
+          return outer_all_df64(m.c) ? odf_step_a(m.c) : cg_step_a(m.c, m.x, m.p, m.r, m.q, m.pdf, m.qdf);
+        },
+        &cache, 1));
     BCK(batch_read(ms, kSlotRR, s, v, launches));
     for (int i = 0; i < (int)ms.size(); ++i) {
       BatchMember& m = ms[i];
@@ -772,6 +966,25 @@ mg_status solve_batch_impl(std::vector<BatchMember>& ms, cudaStream_t s, double 
       if (!std::isfinite(m.rn)) {
         m.status = MG_ENOCONV;
         m.active = false;
+      } else if (m.rn <= tol * m.r0 && odf_started[i]) {
+        // double-float recurrence: confirm on the FP64 residual (one problem at a time)
+        const long long n0 = m.c->nlaunch;
+        BCK(odf_true_residual(m.c));
+        *launches += m.c->nlaunch - n0;
+        std::vector<BatchMember> one(1, m);
+        std::vector<double> t;
+        BCK(batch_read(one, kSlotRR, s, t, launches));
+        m.rn = sqrt(t[0]);
+        if (m.rn <= tol * m.r0) {
+          m.active = false;
+        } else if (it == maxit) {
+          m.status = MG_ENOCONV;
+          m.active = false;
+        } else {
+          const long long n1 = m.c->nlaunch;
+          BCK(odf_replace(m.c));
+          *launches += m.c->nlaunch - n1;
+        }
       } else if (m.rn <= tol * m.r0) {
         m.active = false;
       } else if (it == maxit) {
@@ -780,9 +993,19 @@ mg_status solve_batch_impl(std::vector<BatchMember>& ms, cudaStream_t s, double 
       }
     }
     BCK(batch_step(
-        ms, s, launches, [&](BatchMember& m) { return cg_step_b(m.c, m.p, m.r, m.q, m.z, m.pdf); }, &cache, 2));
+        ms, s, launches,
+        [&](BatchMember& m) { return outer_all_df64(m.c) ? odf_step_b(m.c) : cg_step_b(m.c, m.p, m.r, m.q, m.z, m.pdf); },
+        &cache, 2));
   }
-  // zero-mean solutions and the tensor-core wait flags
+  // double-float iterates back to FP64, zero-mean solutions and the tensor-core wait flags
+  for (int i = 0; i < (int)ms.size(); ++i)
+    if (odf_started[i]) {
+      BatchMember& m = ms[i];
+      const int64_t N = m.c->lev[m.c->L].N;
+      const long long n0 = m.c->nlaunch;
+      BCK(launch_join_df64(m.c, reinterpret_cast<const df64*>(m.c->ws.cg[7]), m.x, N, 0));
+      *launches += m.c->nlaunch - n0;
+    }
   for (auto& m : ms) m.active = true;
   BCK(batch_step(ms, s, launches, [&](BatchMember& m) -> cudaError_t {
     const int64_t N = m.c->lev[m.c->L].N;
@@ -817,6 +1040,7 @@ void mg_default_opts(mg_opts* o) {
   o->outer_df64 = 0;
   o->stream = nullptr;
   o->weight_delta = MG_DELTA_DEFAULT;
+  o->autotune = 0;
 }
 
 mg_status mg_setup(double lx, double ly, double lz, int nx, int ny, int nz, int P, double penalty, int overlap,
@@ -832,7 +1056,8 @@ mg_status mg_setup(double lx, double ly, double lz, int nx, int ny, int nz, int 
   if (o.ns_pre < 0 || o.ns_post < 0 || o.ns_growth < 1 || o.ns_pre + o.ns_post < 1) return MG_EINVAL;
   if (o.precision != MG_FP64 && o.precision != MG_MIXED && o.precision != MG_DF64) return MG_EINVAL;
   if (o.fdm_tensor_cores < 0 || o.fdm_tensor_cores > 2) return MG_EINVAL;
-  if (o.outer_df64 < 0 || o.outer_df64 > 1) return MG_EINVAL;
+  if (o.outer_df64 < 0 || o.outer_df64 > 2) return MG_EINVAL;
+  if (o.autotune < 0 || o.autotune > 1) return MG_EINVAL;
   if (o.weight_profile < MG_WEIGHT_QUINTIC || o.weight_profile > MG_WEIGHT_QUINTIC_NORMALISED) return MG_EINVAL;
   if (o.weight_delta < MG_DELTA_DEFAULT || o.weight_delta > MG_DELTA_STRIP) return MG_EINVAL;
   if (o.overlap_mode == MG_OVERLAP_LAYERS && o.weight_delta == MG_DELTA_STRIP) return MG_EINVAL;
@@ -934,6 +1159,7 @@ mg_status mg_setup(double lx, double ly, double lz, int nx, int ny, int nz, int 
     lv.J = (l >= 1) ? tab((int64_t)lv.n * (c->lev[l - 1].n)) : -1;
     lv.u = lv.f = lv.r = nullptr;
     lv.fdm_tc = 0;
+    lv.fdm_plain = lv.sipg_plain = lv.scatter_plain = 0;
   }
   c->ws.tab_count = off;
   c->ws_bytes = make_layout(c).total;
@@ -983,6 +1209,9 @@ mg_status mg_bind_workspace(mg_ctx* c, void* dptr, size_t bytes) {
   c->tab32_host.assign(c->ws.tab_count, 0.0f);
   CK(cudaMemcpyAsync(c->tab32_host.data(), w.tab32, c->ws.tab_count * sizeof(float), cudaMemcpyDeviceToHost,
                      c->stream));
+  c->tabdf_host.assign(c->ws.tab_count, df64(0.f, 0.f));
+  CK(cudaMemcpyAsync(c->tabdf_host.data(), w.tabdf, c->ws.tab_count * sizeof(df64), cudaMemcpyDeviceToHost,
+                     c->stream));
   // null mode of the coarse eigenbases: the smallest eigenvalue per direction
   for (int d = 0; d < 3; ++d) {
     std::vector<double> lam(c->Ng[d]);
@@ -994,6 +1223,12 @@ mg_status mg_bind_workspace(mg_ctx* c, void* dptr, size_t bytes) {
   CK(cudaStreamSynchronize(c->stream));
   if (st != kDevOk) return fail(c, MG_ENOCONV, "setup eigensolver did not converge");
   if (c->opts.precision == MG_MIXED && c->opts.fdm_tensor_cores != 0) CK(choose_fdm_kernels(c));
+  if (c->opts.autotune) {
+    const long long n0 = c->nlaunch;
+    CK(autotune_levels(c));
+    CK(cudaStreamSynchronize(c->stream));
+    c->nlaunch = n0;  // the trial launches are not the solver's
+  }
   c->ready = true;
   return MG_OK;
 }
@@ -1067,6 +1302,17 @@ mg_status mg_selftest_bounded_wait(mg_ctx* c, int level, int* timed_out) {
   CK(cudaStreamSynchronize(c->stream));
   *timed_out = st == kDevTimeout ? 1 : 0;
   return MG_OK;
+}
+
+int mg_level_kernel_variant(const mg_ctx* c, int level, int kind) {
+  if (!c || level < 1 || level > c->L) return -1;
+  const LevelInfo& lv = c->lev[level];
+  switch (kind) {
+    case 0: return lv.fdm_plain;
+    case 1: return lv.sipg_plain;
+    case 2: return lv.scatter_plain;
+    default: return -1;
+  }
 }
 
 int mg_level_fdm_tensor_cores(const mg_ctx* c, int level) {

@@ -182,12 +182,11 @@ inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, s
   return cudaSuccess;
 }
 
-// Arithmetic types whose kernels have grouped twins (batched solves merge the
-// launches of the FP32 and double-float hierarchies and the FP64 vector
-// passes; the FP64 operator, smoother and transfer kernels run one launch per
-// problem, which keeps the build time).
+// Arithmetic types whose kernels have grouped twins: all of them (batched
+// solves merge the launches of the FP64, FP32 and double-float hierarchies
+// and of the vector passes).
 template <typename T>
-constexpr bool kTwinType = !std::is_same<T, double>::value;
+constexpr bool kTwinType = true;
 
 constexpr int kMaxLevels = 6;   // P <= 32
 constexpr int kMaxP = 32;
@@ -240,6 +239,11 @@ struct LevelInfo {
                          // (ru4 = rounded up to a multiple of 4; tensor-core smoother)
   int64_t mass3;         // n^3: mass_x[i] mass_y[j] mass_z[k]
   int fdm_tc;            // FP32 smoother contractions on the tensor cores (1) or CUDA cores (0)
+  // Kernel variants of single solves (mg_opts.autotune picks them by timing):
+  // 1 = the shared-memory FP32 smoother k_fdm_m instead of k_fdm_c; the plain
+  // operator k_sipg_n instead of k_sipg_c; the scatter k_scatter_n2 instead of
+  // the element-aligned k_scatter_e.
+  int fdm_plain, sipg_plain, scatter_plain;
   int64_t J;             // n * n_c interpolation from level l-1 (level >= 1)
   // device vectors (bytes sized for FP64; FP32 code uses the first half)
   void* u;
@@ -305,7 +309,8 @@ struct mg_ctx {
   std::vector<GraphEntry> graphs;
   cudaStream_t cap_stream = nullptr;
   bool use_graphs = true;
-  std::vector<float> tab32_host;  // host copy of the FP32 tables (kernel parameters of the FP32 smoother)
+  std::vector<float> tab32_host;  // host copies of the FP32 and double-float tables (kernel parameters
+  std::vector<mgdg::df64> tabdf_host;  // of the FP32 smoother and the FP32 / double-float operators)
   mutable bool prof_on = false;
   mutable std::vector<ProfRec> prof;
   mutable size_t prof_used = 0;
@@ -341,10 +346,11 @@ cudaError_t launch_setup_coarse_tables(const double len[3], const int ne[3], dou
 // out = mode==0 ? A u : f - A u, on level l, T = double | float.
 template <typename T>
 cudaError_t launch_sipg(const mg_ctx* c, int l, const T* u, const T* f, T* out, int residual);  // T: double, float, df64
-// FP32 operator with shared-memory element blocks and the coefficients as kernel
-// parameters (sipg_const.cu): orders 2, 4, 8, 16 on meshes that give every SM a
-// block; cudaErrorNotSupported otherwise.
+// FP32 / double-float operator with shared-memory element blocks and the
+// coefficients as kernel parameters (sipg_const.cu): orders 2, 4, 8, 16 on
+// meshes that give every SM a block; cudaErrorNotSupported otherwise.
 cudaError_t launch_sipg_c(const mg_ctx* c, int l, const float* u, const float* f, float* out, int residual);
+cudaError_t launch_sipg_c(const mg_ctx* c, int l, const df64* u, const df64* f, df64* out, int residual);
 
 // ---- smoother (schwarz.cu) ----
 // Corrections of all subdomains from residual r into ws.corr, then
@@ -402,6 +408,28 @@ cudaError_t launch_split_df64(const mg_ctx* c, const double* x, df64* y, int64_t
 cudaError_t launch_join_df64(const mg_ctx* c, const df64* x, double* y, int64_t n, int accumulate);
 cudaError_t launch_dot_dfq(const mg_ctx* c, const double* p, const df64* qdf, double* q, int64_t n, int slot);
 cudaError_t launch_add(const mg_ctx* c, double* y, const double* x, int64_t n);  // y += x
+// Blocks of the two-stage reductions for n values, and their second stages
+// over ws.red: the sum of one column into scal[slot]; the CG update's two
+// columns into scal[Sum] and scal[RR] (|r - mean(r)|^2).
+int reduction_blocks(int64_t n);
+cudaError_t launch_final_sum(const mg_ctx* c, int nb, int slot);
+cudaError_t launch_update_final(const mg_ctx* c, int nb, int64_t n);
+
+// ---- outer MG-CG in double-float arithmetic (blas_df.cu; mg_opts.outer_df64 = 2) ----
+// Vectors x, r, p, q stored as df64 pairs, z the FP32 preconditioner output.
+//  update: pq = p . q; alpha = rz / pq; x += alpha p; r -= alpha q;
+//          scal[Sum], scal[RR] of the new r; r32 = r / sqrt(rr_old), scal[Scale] = sqrt(rr_old).
+//  direction: with z' = Scale z - mean: beta = -alpha z'.q / rz (0 if first);
+//          rz = z'.r'; p = z' + beta p (p = z' if first).
+cudaError_t launch_odf_update(const mg_ctx* c, df64* x, const df64* p, df64* r, const df64* q, float* r32,
+                              int64_t n);
+cudaError_t launch_odf_direction(const mg_ctx* c, df64* p, const float* z, const df64* q, const df64* r, int64_t n,
+                                 int first);
+cudaError_t launch_odf_split(const mg_ctx* c, double* v, int64_t n);  // FP64 -> df64, in place
+// scal[Sum] = sum r, scal[RR] = |r - mean(r)|^2 of a double-float vector
+cudaError_t launch_odf_residual_norm(const mg_ctx* c, const df64* r, int64_t n);
+// y = r / sqrt(scal[RR]) (FP32), scal[Scale] = sqrt(scal[RR])
+cudaError_t launch_odf_to_f32(const mg_ctx* c, const df64* r, float* y, int64_t n);
 cudaError_t launch_to_f32(const mg_ctx* c, const double* x, float* y, int64_t n, int norm_slot);
 cudaError_t launch_from_f32(const mg_ctx* c, const float* x, double* y, int64_t n, int norm_slot);
 cudaError_t launch_rhs(const mg_ctx* c, const double* f, double* b);

@@ -447,7 +447,7 @@ cudaError_t launch_fdm(const mg_ctx* c, int l, const T* r) {
     if (lv.fdm_tc) {
       const cudaError_t e = launch_fdm_tc(c, l, r);
       if (e != cudaErrorNotSupported) return e;
-    } else if (launch_recorder() == nullptr) {
+    } else if (launch_recorder() == nullptr && !lv.fdm_plain) {
       // single solves: the factors as kernel parameters; batched solves keep
       // the shared-memory kernel, whose body has a grouped twin
       const cudaError_t e = launch_fdm_c(c, l, r);
@@ -529,7 +529,7 @@ cudaError_t launch_scatter(const mg_ctx* c, int l, T* u, int accumulate) {
   const SubShape g{lv.m[0], lv.m[1], lv.m[2], lv.no[0], lv.no[1], lv.no[2]};
   c->nlaunch += 1;
   const bool two = 2 * lv.no[0] <= lv.n && 2 * lv.no[1] <= lv.n && 2 * lv.no[2] <= lv.n;
-  if (two && launch_recorder() == nullptr) {
+  if (two && launch_recorder() == nullptr && !lv.scatter_plain) {
     // single solves: element-aligned blocks (batched solves keep k_scatter_n2, whose body has a twin)
     const int n3 = lv.n * lv.n * lv.n, epb = n3 >= 256 ? 1 : 256 / n3;
     const int64_t eblocks = std::min<int64_t>((c->Ne + epb - 1) / epb, 152 * 16);

@@ -1,20 +1,22 @@
-// FP32 sum-factorised SIPG operator (Section 2, Eq. A) with shared-memory
-// element blocks and the 1D coefficients in the kernel's parameter space.
+// Sum-factorised SIPG operator (Section 2, Eq. A) in FP32 or double-float
+// arithmetic with shared-memory element blocks and the 1D coefficients in
+// the kernel's parameter space.
 //
 // The plain operator kernel (sipg_kernels.cuh) makes three passes over an
 // element in global memory: every pass reads its lines with a stride and
-// reads and rewrites the output vector.  In FP32 that kernel waits on its
-// loads.  Here a block takes EPB consecutive elements: their blocks of u are
+// reads and rewrites the output vector, and every multiply-add loads its
+// coefficient.  In FP32 and double-float that kernel waits on its loads.  Here a block takes EPB consecutive elements: their blocks of u are
 // loaded once with coalesced loads into shared memory, the x, y and z line
 // products run from there and accumulate in a shared output block, and the
 // last (z) pass applies the mass and forms f - A u with coalesced loads of f
 // and stores of the result.  Only the face terms read the neighbour lines
 // from global memory (L2).  The even/odd line matrices, face vectors, rows of
-// the differentiation matrix and the 1D masses (at most 2.2 KB at n = 17)
-// travel as one __grid_constant__ parameter, so with the compile-time order
-// every coefficient is an immediate constant-bank operand of its FMA.  The
-// arithmetic is that of line_apply_n (the same even/odd form, face terms and
-// order of the three directions).
+// the differentiation matrix and the 1D masses (at most 4.2 KB at n = 17 in
+// double-float) travel as one __grid_constant__ parameter, so with the
+// compile-time order every coefficient is an immediate constant-bank operand.
+// The arithmetic is that of line_apply_n (the same even/odd form, face terms,
+// accumulation (Acc) and order of the three directions); the mass of a node
+// is formed as the product of the three 1D masses.
 #include <algorithm>
 #include <atomic>
 
@@ -23,30 +25,39 @@
 namespace mgdg {
 namespace {
 
-template <int N>
+template <typename T, int N>
 struct SipgCShape {
   static constexpr int ne = (N + 1) / 2, no = N / 2, noo = no > 0 ? no : 1;
   static constexpr int n2 = N * N, n3 = n2 * N;
   static constexpr int epb = n2 >= 256 ? 1 : 256 / n2;  // elements per block
   static constexpr int threads = (epb * n2 + 31) / 32 * 32;
-  static constexpr size_t smem = sizeof(float) * 2 * (size_t)epb * n3;
+  static constexpr size_t smem = sizeof(T) * 2 * (size_t)epb * n3;
 };
 
-template <int N>
+template <typename T, int N>
 struct SipgCArgs {
-  using Sh = SipgCShape<N>;
-  const float* u;
-  const float* f;
-  float* out;
+  using Sh = SipgCShape<T, N>;
+  const T* u;
+  const T* f;
+  T* out;
   int64_t Ne;
   int nx, ny, nz, residual;
-  float ce[3][Sh::ne * Sh::ne];  // even half of M_d^{-1} L_ee
-  float co[3][Sh::noo * Sh::noo];  // odd half
-  float fe[3][Sh::ne], fo[3][Sh::noo];  // face vectors of the even / odd halves
-  float mu[3], g2[3];            // face scalars mu / m_0 and g / (2 m_0)
-  float d0[N], dp[N];            // first and last row of the reference differentiation matrix
-  float mass[3][N];              // 1D masses (h_d / 2) w
+  T ce[3][Sh::ne * Sh::ne];    // even half of M_d^{-1} L_ee
+  T co[3][Sh::noo * Sh::noo];  // odd half
+  T fe[3][Sh::ne], fo[3][Sh::noo];  // face vectors of the even / odd halves
+  T mu[3], g2[3];              // face scalars mu / m_0 and g / (2 m_0)
+  T d0[N], dp[N];              // first and last row of the reference differentiation matrix
+  T mass[3][N];                // 1D masses (h_d / 2) w
 };
+
+template <typename T>
+__device__ __forceinline__ T sc_load(const T* p) {
+  return *p;
+}
+template <>
+__device__ __forceinline__ float sc_load<float>(const float* p) {
+  return __ldg(p);
+}
 
 __device__ __forceinline__ int sc_wrap(int x, int n) { return x < 0 ? x + n : (x >= n ? x - n : x); }
 
@@ -54,39 +65,46 @@ __device__ __forceinline__ int sc_wrap(int x, int n) { return x < 0 ? x + n : (x
 // face terms from the neighbours' lines in global memory, outputs combined
 // into the shared output block (D = 0: store, 1: add) or, for D = 2, into
 // out = residual ? f - M (acc + v) : M (acc + v) in global memory.
-template <int N, int D>
-__device__ __forceinline__ void line_c(const SipgCArgs<N>& a, const float* __restrict__ su, float* so,
-                                       const float* __restrict__ uL, const float* __restrict__ uR, int st,
-                                       float* __restrict__ out, const float* __restrict__ fl, float mpq) {
+template <typename T, int N, int D>
+__device__ __forceinline__ void line_c(const SipgCArgs<T, N>& a, const T* __restrict__ su, T* so,
+                                       const T* __restrict__ uL, const T* __restrict__ uR, int st,
+                                       T* __restrict__ out, const T* __restrict__ fl, T mpq) {
   constexpr int P = N - 1, ne = (N + 1) / 2, no = N / 2;
-  float ev[ne], od[no > 0 ? no : 1];
+  T ev[ne], od[no > 0 ? no : 1];
 #pragma unroll
   for (int t = 0; t < no; ++t) {
-    const float xa = su[t * st], xb = su[(P - t) * st];
+    const T xa = su[t * st], xb = su[(P - t) * st];
     ev[t] = xa + xb;
     od[t] = xa - xb;
   }
   if (N & 1) ev[ne - 1] = su[no * st];
-  const float av = __ldg(uL + P * st), cv = __ldg(uR);
-  float b = a.dp[0] * __ldg(uL), dd = a.d0[0] * cv;
+  const T av = sc_load(uL + P * st), cv = sc_load(uR);
+  Acc<T> ba, da;
+  ba.init(a.dp[0], sc_load(uL));
+  da.init(a.d0[0], cv);
 #pragma unroll
   for (int t = 1; t < N; ++t) {
-    b = fmaf(a.dp[t], __ldg(uL + t * st), b);
-    dd = fmaf(a.d0[t], __ldg(uR + t * st), dd);
+    ba.add(a.dp[t], sc_load(uL + t * st));
+    da.add(a.d0[t], sc_load(uR + t * st));
   }
-  const float s = av + cv, tm = av - cv;
-  const float lo = a.g2[D] * b - a.mu[D] * av;
-  const float hi = -(a.mu[D] * cv + a.g2[D] * dd);
+  const T b = ba.get(), dd = da.get();
+  const T s = av + cv, tm = av - cv;
+  const T lo = a.g2[D] * b - a.mu[D] * av;
+  const T hi = -(a.mu[D] * cv + a.g2[D] * dd);
 #pragma unroll
   for (int i = 0; i < ne; ++i) {
-    float E = a.fe[D][i] * s;
+    Acc<T> ea;
+    ea.init(a.fe[D][i], s);
 #pragma unroll
-    for (int t = 0; t < ne; ++t) E = fmaf(a.ce[D][i * ne + t], ev[t], E);
-    float v0, v1;
+    for (int t = 0; t < ne; ++t) ea.add(a.ce[D][i * ne + t], ev[t]);
+    const T E = ea.get();
+    T v0, v1;
     if (i < no) {
-      float O = a.fo[D][i] * tm;
+      Acc<T> oa;
+      oa.init(a.fo[D][i], tm);
 #pragma unroll
-      for (int t = 0; t < no; ++t) O = fmaf(a.co[D][i * no + t], od[t], O);
+      for (int t = 0; t < no; ++t) oa.add(a.co[D][i * no + t], od[t]);
+      const T O = oa.get();
       v0 = E + O;
       v1 = E - O;
     } else {
@@ -104,29 +122,29 @@ __device__ __forceinline__ void line_c(const SipgCArgs<N>& a, const float* __res
       so[i * st] += v0;
       if (i1 != i) so[i1 * st] += v1;
     } else {
-      const float w0 = mpq * a.mass[2][i] * (so[i * st] + v0);
+      const T w0 = mpq * a.mass[2][i] * (so[i * st] + v0);
       out[i * st] = a.residual ? fl[i * st] - w0 : w0;
       if (i1 != i) {
-        const float w1 = mpq * a.mass[2][i1] * (so[i1 * st] + v1);
+        const T w1 = mpq * a.mass[2][i1] * (so[i1 * st] + v1);
         out[i1 * st] = a.residual ? fl[i1 * st] - w1 : w1;
       }
     }
   }
 }
 
-template <int N>
-__global__ void __launch_bounds__(SipgCShape<N>::threads) k_sipg_c(const __grid_constant__ SipgCArgs<N> a) {
+template <typename T, int N>
+__global__ void __launch_bounds__(SipgCShape<T, N>::threads) k_sipg_c(const __grid_constant__ SipgCArgs<T, N> a) {
   pdl_entry();
-  using Sh = SipgCShape<N>;
+  using Sh = SipgCShape<T, N>;
   constexpr int n2 = Sh::n2, n3 = Sh::n3, EPB = Sh::epb;
-  extern __shared__ __align__(16) float sc_smem[];
-  float* sU = sc_smem;             // EPB element blocks of u
-  float* sO = sc_smem + EPB * n3;  // EPB output blocks (x and y contributions)
+  extern __shared__ __align__(16) unsigned char sc_raw[];
+  T* sU = reinterpret_cast<T*>(sc_raw);  // EPB element blocks of u
+  T* sO = sU + EPB * n3;                 // EPB output blocks (x and y contributions)
   const int tid = threadIdx.x, nt = blockDim.x;
   const int g = tid / n2, l2 = tid - g * n2, p = l2 % N, q = l2 / N;
   for (int64_t e0 = (int64_t)blockIdx.x * EPB; e0 < a.Ne; e0 += (int64_t)gridDim.x * EPB) {
     const int cnt = (int)(a.Ne - e0 < EPB ? a.Ne - e0 : EPB);
-    const float* ub = a.u + e0 * n3;
+    const T* ub = a.u + e0 * n3;
     for (int i = tid; i < cnt * n3; i += nt) sU[i] = ub[i];
     __syncthreads();
     const bool act = g < cnt;
@@ -137,20 +155,21 @@ __global__ void __launch_bounds__(SipgCShape<N>::threads) k_sipg_c(const __grid_
       ey = exy % a.ny;
       ez = exy / a.ny;
     }
-    const float* su = sU + g * n3;
-    float* so = sO + g * n3;
+    const T* su = sU + g * n3;
+    T* so = sO + g * n3;
     if (act) {  // x lines (p, q) = (j, k)
       const int base = N * (p + N * q);
       const int64_t row = (int64_t)a.nx * (ey + (int64_t)a.ny * ez);
-      line_c<N, 0>(a, su + base, so + base, a.u + (sc_wrap(ex - 1, a.nx) + row) * n3 + base,
-                   a.u + (sc_wrap(ex + 1, a.nx) + row) * n3 + base, 1, nullptr, nullptr, 0.f);
+      line_c<T, N, 0>(a, su + base, so + base, a.u + (sc_wrap(ex - 1, a.nx) + row) * n3 + base,
+                      a.u + (sc_wrap(ex + 1, a.nx) + row) * n3 + base, 1, nullptr, nullptr, T(0.f));
     }
     __syncthreads();
     if (act) {  // y lines (p, q) = (i, k)
       const int base = p + n2 * q;
       const int64_t eL = ex + a.nx * (sc_wrap(ey - 1, a.ny) + (int64_t)a.ny * ez);
       const int64_t eR = ex + a.nx * (sc_wrap(ey + 1, a.ny) + (int64_t)a.ny * ez);
-      line_c<N, 1>(a, su + base, so + base, a.u + eL * n3 + base, a.u + eR * n3 + base, N, nullptr, nullptr, 0.f);
+      line_c<T, N, 1>(a, su + base, so + base, a.u + eL * n3 + base, a.u + eR * n3 + base, N, nullptr, nullptr,
+                      T(0.f));
     }
     __syncthreads();
     if (act) {  // z lines (p, q) = (i, j): mass, residual, coalesced stores
@@ -158,20 +177,28 @@ __global__ void __launch_bounds__(SipgCShape<N>::threads) k_sipg_c(const __grid_
       const int64_t exy = ex + (int64_t)a.nx * ey, plane = (int64_t)a.nx * a.ny;
       const int64_t eL = exy + plane * sc_wrap(ez - 1, a.nz), eR = exy + plane * sc_wrap(ez + 1, a.nz);
       const int64_t off = (e0 + g) * n3 + base;
-      line_c<N, 2>(a, su + base, so + base, a.u + eL * n3 + base, a.u + eR * n3 + base, n2, a.out + off,
-                   a.residual ? a.f + off : nullptr, a.mass[0][p] * a.mass[1][q]);
+      line_c<T, N, 2>(a, su + base, so + base, a.u + eL * n3 + base, a.u + eR * n3 + base, n2, a.out + off,
+                      a.residual ? a.f + off : nullptr, a.mass[0][p] * a.mass[1][q]);
     }
     __syncthreads();
   }
 }
 
-template <int N>
-cudaError_t launch_sipg_c_n(const mg_ctx* c, int l, const float* u, const float* f, float* out, int residual) {
-  using Sh = SipgCShape<N>;
+template <typename T>
+const std::vector<T>& host_tables(const mg_ctx* c);
+template <>
+const std::vector<float>& host_tables<float>(const mg_ctx* c) { return c->tab32_host; }
+template <>
+const std::vector<df64>& host_tables<df64>(const mg_ctx* c) { return c->tabdf_host; }
+
+template <typename T, int N>
+cudaError_t launch_sipg_c_n(const mg_ctx* c, int l, const T* u, const T* f, T* out, int residual) {
+  using Sh = SipgCShape<T, N>;
   constexpr int ne = Sh::ne, no = Sh::no;
+  static_assert(sizeof(SipgCArgs<T, N>) <= 32000, "parameter block too large");
   const LevelInfo& lv = c->lev[l];
-  const float* tab = c->tab32_host.data();
-  SipgCArgs<N> a;
+  const T* tab = host_tables<T>(c).data();
+  SipgCArgs<T, N> a;
   a.u = u;
   a.f = f;
   a.out = out;
@@ -195,38 +222,49 @@ cudaError_t launch_sipg_c_n(const mg_ctx* c, int l, const float* u, const float*
     a.dp[i] = tab[lv.t[0].dp + i];
   }
   if (Sh::smem > 48 * 1024) {
-    const cudaError_t e = cudaFuncSetAttribute(k_sipg_c<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::smem);
+    const cudaError_t e =
+        cudaFuncSetAttribute(k_sipg_c<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::smem);
     if (e != cudaSuccess) return e;
   }
-  static std::atomic<int> per_sm_cached{0};  // resident blocks per SM, queried once per order
+  static std::atomic<int> per_sm_cached{0};  // resident blocks per SM, queried once per type and order
   int per_sm = per_sm_cached.load();
   if (per_sm == 0) {
-    const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sipg_c<N>, Sh::threads, Sh::smem);
+    const cudaError_t e =
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sipg_c<T, N>, Sh::threads, Sh::smem);
     if (e != cudaSuccess) return e;
     per_sm = std::max(per_sm, 1);
     per_sm_cached.store(per_sm);
   }
   const int64_t groups = (c->Ne + Sh::epb - 1) / Sh::epb;
   const int blocks = (int)std::min<int64_t>(groups, 152LL * per_sm);
-  launch_pdl(k_sipg_c<N>, blocks, Sh::threads, Sh::smem, c->stream, a);
+  launch_pdl(k_sipg_c<T, N>, blocks, Sh::threads, Sh::smem, c->stream, a);
   c->nlaunch += 1;
   return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_sipg_c_t(const mg_ctx* c, int l, const T* u, const T* f, T* out, int residual) {
+  if (host_tables<T>(c).empty()) return cudaErrorNotSupported;
+  const int n = c->lev[l].n;
+  const int epb = n * n >= 256 ? 1 : 256 / (n * n);
+  if ((c->Ne + epb - 1) / epb < 152) return cudaErrorNotSupported;  // too few blocks: the direction-split kernel
+  switch (n) {
+    case 3: return launch_sipg_c_n<T, 3>(c, l, u, f, out, residual);
+    case 5: return launch_sipg_c_n<T, 5>(c, l, u, f, out, residual);
+    case 9: return launch_sipg_c_n<T, 9>(c, l, u, f, out, residual);
+    case 17: return launch_sipg_c_n<T, 17>(c, l, u, f, out, residual);
+    default: return cudaErrorNotSupported;
+  }
 }
 
 }  // namespace
 
 cudaError_t launch_sipg_c(const mg_ctx* c, int l, const float* u, const float* f, float* out, int residual) {
-  if (c->tab32_host.empty()) return cudaErrorNotSupported;
-  const int n = c->lev[l].n;
-  const int epb = n * n >= 256 ? 1 : 256 / (n * n);
-  if ((c->Ne + epb - 1) / epb < 152) return cudaErrorNotSupported;  // too few blocks: the direction-split kernel
-  switch (n) {
-    case 3: return launch_sipg_c_n<3>(c, l, u, f, out, residual);
-    case 5: return launch_sipg_c_n<5>(c, l, u, f, out, residual);
-    case 9: return launch_sipg_c_n<9>(c, l, u, f, out, residual);
-    case 17: return launch_sipg_c_n<17>(c, l, u, f, out, residual);
-    default: return cudaErrorNotSupported;
-  }
+  return launch_sipg_c_t<float>(c, l, u, f, out, residual);
+}
+
+cudaError_t launch_sipg_c(const mg_ctx* c, int l, const df64* u, const df64* f, df64* out, int residual) {
+  return launch_sipg_c_t<df64>(c, l, u, f, out, residual);
 }
 
 }  // namespace mgdg

@@ -391,10 +391,11 @@ cudaError_t launch_sipg(const mg_ctx* c, int l, const T* u, const T* f, T* out, 
   a.d0 = lv.t[0].d0;
   a.dp = lv.t[0].dp;
   a.mass3 = lv.mass3;
-  if constexpr (std::is_same<T, float>::value) {
-    // single solves: shared-memory element blocks, coefficients as kernel
-    // parameters; batched solves keep the kernels whose bodies have twins
-    if (launch_recorder() == nullptr) {
+  if constexpr (!std::is_same<T, double>::value) {
+    // single solves (FP32, double-float): shared-memory element blocks,
+    // coefficients as kernel parameters; batched solves keep the kernels
+    // whose bodies have twins
+    if (launch_recorder() == nullptr && !lv.sipg_plain) {
       const cudaError_t e = launch_sipg_c(c, l, u, f, out, residual);
       if (e != cudaErrorNotSupported) return e;
     }

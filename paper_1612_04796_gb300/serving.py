@@ -77,8 +77,11 @@ class Server:
     admission, the worker threads, the streams and the device memory are the
     library's; this class marshals requests in and results out.
 
-    Real solves by default: FP32 V-cycle preconditioner inside FP64 inexact
-    PCG, the outer products q = A p in double-float (outer_df64); requests of
+    Real solves by default: FP32 V-cycle preconditioner inside the inexact
+    PCG, whose outer iteration runs in double-float arithmetic (outer_df64 =
+    "all": vectors, inner products, updates and q = A p in FP32 pairs, the
+    convergence confirmed on the FP64 residual; True: only q = A p; False:
+    FP64); requests of
     at most ``batch_dofs`` DOFs and the same order are solved in groups of up
     to ``batch_max`` (mg_solve_batch: one launch per sweep for the group).  Each
     request's nodal right-hand side is drawn from its seed when the runtime
@@ -89,7 +92,7 @@ class Server:
     makes no CUDA call, and ``req.footprint`` (bytes) is the request's size."""
 
     def __init__(self, slots=8, budget_bytes=None, precision="mixed", use_cg=True, device="cuda", keep_solution=True,
-                 outer_df64=True, policy="fcfs", max_wait=10.0, executor=None, maxit=400, batch_max=16,
+                 outer_df64="all", policy="fcfs", max_wait=10.0, executor=None, maxit=400, batch_max=16,
                  batch_dofs=1 << 20):
         from . import _lib
         from .solver import PRECISION
@@ -98,7 +101,7 @@ class Server:
         self._lib = _lib
         self.lib = _lib.load_library()
         self.precision = precision
-        self.outer_df64 = bool(outer_df64) and precision != "fp64"
+        self.outer_df64 = outer_df64 if precision != "fp64" else False
         self.use_cg = use_cg
         self.keep = keep_solution and executor is None
         self.policy = policy
@@ -112,7 +115,7 @@ class Server:
         o.use_cg = 1 if use_cg else 0
         o.maxit = int(maxit)
         o.opts.precision = PRECISION[precision]
-        o.opts.outer_df64 = 1 if self.outer_df64 else 0
+        o.opts.outer_df64 = {False: 0, True: 1, "all": 2}[self.outer_df64]
         o.budget = 0 if budget_bytes is None else int(budget_bytes)
         o.batch_max = int(batch_max)
         o.batch_dofs = int(batch_dofs)

@@ -35,7 +35,7 @@ class MGSolver:
 
     def __init__(self, lengths, counts, P, penalty=2.0, overlap=1, precision="fp64", overlap_mode="layers",
                  overlap_frac=0.08, weight_profile="quintic", ns_pre=1, ns_post=1, ns_growth=1, device="cuda",
-                 stream=None, tensor_cores=False, outer_df64=False, weight_delta="default"):
+                 stream=None, tensor_cores=False, outer_df64=False, weight_delta="default", autotune=False):
         self.lib = load_library()
         self.device = torch.device(device)
         if self.device.type == "cuda" and self.device.index is None:
@@ -46,10 +46,11 @@ class MGSolver:
         opts.overlap_frac = float(overlap_frac)
         opts.weight_profile = PROFILE[weight_profile]
         opts.weight_delta = WEIGHT_DELTA[weight_delta]
+        opts.autotune = 1 if autotune else 0
         opts.ns_pre, opts.ns_post, opts.ns_growth = int(ns_pre), int(ns_post), int(ns_growth)
         opts.precision = PRECISION[precision]
         opts.fdm_tensor_cores = {False: 0, True: 1, "auto": 2}[tensor_cores]
-        opts.outer_df64 = 1 if outer_df64 else 0
+        opts.outer_df64 = {False: 0, True: 1, "all": 2}[outer_df64]
         with torch.cuda.device(self.device):
             self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         opts.stream = ctypes.c_void_p(self.stream.cuda_stream)
@@ -104,6 +105,12 @@ class MGSolver:
     def fdm_tensor_cores(self, level):
         """1 if the FP32 smoother of `level` runs its contractions on the tensor cores."""
         return int(self.lib.mg_level_fdm_tensor_cores(self.ctx, level))
+
+    def kernel_variants(self, level):
+        """Kernel variants of single solves on `level` (mg_level_kernel_variant):
+        {"fdm", "sipg", "scatter"} -> 0 default, 1 alternative."""
+        return {k: int(self.lib.mg_level_kernel_variant(self.ctx, level, i))
+                for i, k in enumerate(("fdm", "sipg", "scatter"))}
 
     def layers(self, level, direction=None):
         """N_O of a level: of the x direction, or of `direction` (0, 1, 2)."""

@@ -48,6 +48,7 @@ def test_defaults(lib):
                                  dict(overlap=-1), dict(lengths=(0.0, 1.0, 1.0)), dict(ns_pre=0, ns_post=0),
                                  dict(precision=7), dict(overlap_mode=1, overlap_frac=0.75),
                                  dict(weight_delta=4), dict(weight_delta=3), dict(overlap_mode=2, weight_delta=1),
+                                 dict(autotune=2), dict(precision=1, outer_df64=3),
                                  dict(precision=1, fdm_tensor_cores=3)])
 def test_rejects_bad_arguments(lib, bad):
     st, ctx = _setup(lib, **bad)
@@ -159,3 +160,13 @@ def test_weight_delta_readings_accepted(lib):
         st, ctx = _setup(lib, P=16, overlap=2, overlap_mode=mode, overlap_frac=0.08, weight_delta=delta)
         assert st == 0, (mode, delta)
         lib.mg_destroy(ctx)
+
+
+def test_kernel_variant_query(lib):
+    st, ctx = _setup(lib, P=8, counts=(4, 4, 4), autotune=1)
+    assert st == 0
+    assert lib.mg_level_kernel_variant(ctx, 0, 0) == -1
+    assert lib.mg_level_kernel_variant(ctx, 3, 3) == -1
+    assert lib.mg_level_kernel_variant(ctx, 4, 0) == -1
+    assert lib.mg_level_kernel_variant(ctx, 3, 0) == 0  # before binding: the defaults
+    lib.mg_destroy(ctx)

@@ -88,3 +88,31 @@ def test_batch_mixed_orders_and_limits(mg):
         mg.solve_batch([a, a], [fa, fa])
     a.close()
     b.close()
+
+
+UNIFORM = [((1.0, 1.0, 1.0), (8, 8, 8)), ((2.0, 1.0, 1.0), (9, 8, 8)), ((1.0, 3.0, 1.0), (8, 10, 8)),
+           ((1.0, 1.0, 1.5), (8, 8, 9))]
+
+
+def test_fp64_batch_takes_one_launch_per_sweep(mg):
+    """An FP64 batch (operator, smoother, scatter, transfers and vector passes
+    all with grouped twins) of meshes that take the same kernel variants
+    launches far fewer kernels than the same solves one by one, with the same
+    iterations."""
+    import torch
+    probs = []
+    for i, (L, n) in enumerate(UNIFORM):
+        s = mg.MGSolver(L, n, 4)
+        probs.append((s, s.rhs(torch.tensor(inputs.gaussian(s.num_dofs(), 400 + i), device="cuda"))))
+    solvers, rhs = [s for s, _ in probs], [b for _, b in probs]
+    l0 = [s.kernel_launches() for s in solvers]
+    its1 = [s.solve(b, tol=1e-10, use_cg=True)[1] for s, b in probs]
+    single = sum(s.kernel_launches() - a for s, a in zip(solvers, l0))
+    b0 = solvers[0].batch_launches()
+    _, its, _, sts = mg.solve_batch(solvers, rhs, tol=1e-10)
+    batched = solvers[0].batch_launches() - b0
+    assert sts == [0] * len(probs)
+    assert all(abs(a - b) <= 1 for a, b in zip(its, its1))
+    assert batched < 0.5 * single, (batched, single)
+    for s in solvers:
+        s.close()

@@ -114,3 +114,64 @@ def test_df64_mgcg_solve(mg):
     assert np.linalg.norm(b - H.A @ u) <= 1.01e-10 * np.linalg.norm(b)
     assert abs(itg - ito) <= 1
     assert rel_err(u, uo) < 1e-8
+
+
+def test_mixed_solve_with_df64_outer_iteration(mg):
+    """The whole outer iteration in double-float (outer_df64 = 2: x, r, p, q
+    stored as FP32 pairs, inner products and updates on the FP32 pipes): the
+    true FP64 residual reaches 1e-10, the iteration count matches the oracle's
+    MG-CG within one, and the solution matches the oracle's to what the
+    tolerance implies (Section 3.2 inexact PCG; 48-bit vectors are far below
+    the 1e-10 target)."""
+    lengths, counts, P = (1.0, 1.0, 1.0), (4, 4, 4), 8
+    s = mg.MGSolver(lengths, counts, P, precision="mixed", outer_df64="all")
+    mesh = Mesh(lengths, counts)
+    H = Hierarchy(mesh, P)
+    b = weak_rhs(mesh, P, inputs.gaussian(H.A.shape[0], 19))
+    uo, ito, _ = solve_mgcg(H, b, tol=1e-10)
+    ug, itg, rel, hg = s.solve(cuda(b), tol=1e-10, use_cg=True)
+    u = ug.cpu().numpy()
+    s.close()
+    assert np.linalg.norm(b - H.A @ u) <= 1.01e-10 * np.linalg.norm(b)
+    assert abs(itg - ito) <= 1
+    assert rel_err(u, uo) < 1e-7
+    assert abs(u.mean()) < 1e-14 * np.abs(u).max()
+
+
+def test_df64_outer_iteration_batched_matches_single(mg):
+    """mg_solve_batch with the double-float outer iteration: every problem
+    converges to the FP64 tolerance and agrees with its single solve to
+    rounding (the grouped kernels are separate compilations)."""
+    import torch
+    probs = [((1.0, 1.0, 1.0), (4, 4, 4), 4, 23), ((2.0, 1.0, 1.0), (5, 4, 4), 4, 24)]
+    single, batch_s, fs = [], [], []
+    for lengths, counts, P, seed in probs:
+        a = mg.MGSolver(lengths, counts, P, precision="mixed", outer_df64="all")
+        f = a.rhs(torch.tensor(inputs.gaussian(a.num_dofs(), seed), device=a.device))
+        single.append(a.solve(f, tol=1e-10, use_cg=True))
+        batch_s.append(mg.MGSolver(lengths, counts, P, precision="mixed", outer_df64="all"))
+        fs.append(f)
+    us, its, rels, sts = mg.solve_batch(batch_s, fs, tol=1e-10)
+    assert sts == [0, 0] and max(rels) <= 1e-10
+    for (u1, it1, _, _), u2, it2 in zip(single, us, its):
+        assert abs(it1 - it2) <= 1
+        assert rel_err(u2.cpu().numpy(), u1.cpu().numpy()) < 1e-9
+
+
+def test_df64_outer_iteration_confirms_on_fp64_residual(mg):
+    """With the outer iteration in 48-bit pairs the recurrence residual drifts
+    from the true one over many iterations; convergence is confirmed on the
+    FP64 residual (and the iteration goes on from it if needed), so the true
+    FP64 residual meets the tolerance.  Anisotropic box (element aspect ratio
+    4), N_O = 1: tens of iterations."""
+    import torch
+    s = mg.MGSolver((16.0, 1.0, 1.0), (16, 4, 4), 8, precision="mixed", outer_df64="all")
+    f = s.rhs(torch.tensor(inputs.gaussian(s.num_dofs(), 25), device=s.device))
+    u, its, rel, hist = s.solve(f, tol=1e-10, use_cg=True)
+    s64 = mg.MGSolver((16.0, 1.0, 1.0), (16, 4, 4), 8)
+    true = float(torch.linalg.norm(s64.residual(u, f)) / torch.linalg.norm(f))
+    s.close()
+    s64.close()
+    assert its > 10
+    assert true <= 1.0e-10 * (1 + 1e-6), (its, true)
+    assert abs(hist[-1] / hist[0] - true) <= 1e-3 * true

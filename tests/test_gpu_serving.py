@@ -60,7 +60,8 @@ def test_served_solution_equals_a_direct_solve(mg):
     srv.close()
     for req, r in zip((small, large), res):
         assert r.error is None and r.relres <= 1e-10
-        s = mg.MGSolver(req.lengths, req.counts, req.P, overlap=req.overlap, precision="mixed", outer_df64=True)
+        s = mg.MGSolver(req.lengths, req.counts, req.P, overlap=req.overlap, precision="mixed",
+                        outer_df64=srv.outer_df64)
         b = s.rhs(torch.tensor(inputs.gaussian(s.num_dofs(), req.seed), device="cuda"))
         u, its, rel, _ = s.solve(b, tol=req.tol, use_cg=True, maxit=400)
         if req is small:
