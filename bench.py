@@ -7,13 +7,17 @@ mean), weak rhs b = M f, standalone V(1,1) multigrid with N_O = 1 node-layer
 overlap, FP64, from u = 0 to ||b - A u|| <= 1e-10 ||b||.  Inputs are resident
 in HBM when timing starts; L2 is flushed (256 MiB write) between steps.
 
-Also reported: the same solves through the host-buffer API (e2e), the
-mixed-precision solver (FP32 V-cycle inside FP64 CG) on the same problem, the
-level kernels against their rooflines (the FP64 / FP32 pipe at the sampled
-clock for the fast diagonalisation, HBM for the residual and the scatter),
-the anisotropic 48x8x8, P = 16 box (mixed MG-CG, N_O = 1, 2, 4; key "c3"),
-the 512-request serving stream (N_O = 1 and 4; key "serving"), and the FP64
-CPU oracle timed on the host cores on a bounded sample of the workload.
+Also reported: the same solves through the host-buffer API (e2e); the
+standalone MG with the multigrid in double-float (df64); the mixed-precision
+solver (FP32 V-cycle inside the outer CG) on the same problem with the outer
+iteration in FP64 (mixed), with q = A p in double-float (mixed_df64) and with
+the whole outer iteration in double-float (mixed_df64_all); the level
+kernels against their rooflines (the FP64 / FP32 pipe at the sampled clock
+for the fast diagonalisation, HBM for the residual and the scatter); the
+anisotropic 48x8x8, P = 16 box (mixed MG-CG, N_O = 1, 2, 4, and N_O = 4 with
+the double-float outer iteration; key "c3"); the 512-request serving stream
+(N_O = 1 and 4, and N_O = 4 without grouped launches; key "serving"); and the
+FP64 CPU oracle timed on the host cores on a bounded sample of the workload.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mg|reference]
 Multi-GPU (N > 1, launched with torch.distributed.run): every rank solves its
@@ -78,7 +82,7 @@ WORKLOADS = {
 WORKLOADS["serving512"] = dict(workload="serving stream: 512 solve requests, Poisson arrivals at 200/s (seed 5), periodic box "
                                 "[0,AR]x[0,1]x[0,1], AR ~ U[1,8], n^3 elements with n in {4,8,16,24,32}, P in {2,4,8,16}, "
                                 "N_O=4 (default; --overlap), Gaussian f, FP32 V(1,1) in a PCG whose outer iteration runs in "
-                                "double-float (convergence confirmed on the FP64 residual), tol 1e-10, "
+                                "double-float (convergence confirmed on the true residual), tol 1e-10, "
                                 "admitted by HBM footprint (smallest work first with aging; MG_SERVING_POLICY=fcfs "
                                 "for first come first served), "
                                 "one context and stream per slot; requests of <= 2^20 DOFs and one order admitted "
@@ -120,6 +124,9 @@ def parse_args():
     ap.add_argument("--overlap", type=int, default=None, help="override N_O of the workload")
     ap.add_argument("--precision", default=None, choices=["fp64", "mixed"], help="override the workload's precision")
     ap.add_argument("--cg", action="store_true", help="solve the workload with MG-CG instead of its default solver")
+    ap.add_argument("--fdm-bf16", action="store_true",
+                    help="mixed runs: the FP32 smoother's contractions with BF16-rounded operands (a precision "
+                         "study of BF16 tensor-core contractions, run on the CUDA cores)")
     ap.add_argument("--outer-all", action="store_true",
                     help="mixed MG-CG runs: the whole outer iteration (vectors, inner products, updates and "
                          "q = A p) in double-float arithmetic")
@@ -597,13 +604,19 @@ def run_mg(args):
     if not args.no_configs and world == 1:
         # the metric's own configurations beside the main line: the anisotropic
         # 48x8x8, P = 16 box (mixed MG-CG, every overlap the configuration
-        # lists) and the 512-request serving stream (N_O = 1 and 4)
+        # lists, outer iteration in FP64 as the configuration states; and N_O = 4
+        # with the double-float outer iteration) and the 512-request serving
+        # stream (N_O = 1 and 4, and N_O = 4 without grouped launches)
         line["c3"] = {}
         for no in (1, 2, 4):
             line["c3"]["n_o_%d" % no] = compact_line(workload_line("box48x8x8_p16", 3, 2, overlap=no))
+        line["c3"]["n_o_4_outer_df64"] = compact_line(workload_line("box48x8x8_p16", 3, 2, overlap=4,
+                                                                    outer_df64="all"))
         line["serving"] = {}
         for no in (1, 4):
             line["serving"]["n_o_%d" % no] = compact_line(serving_line("serving512", no))
+        # the same stream with every request solved on its own (no grouped launches)
+        line["serving"]["n_o_4_unbatched"] = compact_line(serving_line("serving512", 4, batch_dofs=0))
 
     if rank == 0 and not args.no_cpu_baseline:
         Ns, ts, _, its_s = oracle_sample_solve()
@@ -617,7 +630,7 @@ def run_mg(args):
 
 
 def workload_line(name, steps, warmup, overlap=None, precision=None, cg=False, outer_df64=False,
-                  tensor_cores="off"):
+                  tensor_cores="off", fdm_bf16=False):
     """One configuration: DOF/s of full solves (inputs resident, L2 flushed
     between solves), per-kernel device times and the rooflines of the
     fine-level kernels.  Returns the JSON line as a dict."""
@@ -636,7 +649,7 @@ def workload_line(name, steps, warmup, overlap=None, precision=None, cg=False, o
     dev = torch.device("cuda", torch.cuda.current_device())
     pkg.load_library()
     extra = {k: W[k] for k in ("overlap_mode", "overlap_frac", "ns_growth") if k in W}
-    extra_mixed = dict(extra, tensor_cores=TC_MODE[tensor_cores], outer_df64=outer_df64)
+    extra_mixed = dict(extra, tensor_cores=TC_MODE[tensor_cores], outer_df64=outer_df64, fdm_bf16=fdm_bf16)
     s = pkg.MGSolver(W["lengths"], W["elements"], W["P"], overlap=W["overlap_layers"], precision=W["precision"],
                      device=dev, **(extra_mixed if W["precision"] == "mixed" else extra))
     s64 = s if W["precision"] == "fp64" else pkg.MGSolver(W["lengths"], W["elements"], W["P"],
@@ -686,6 +699,7 @@ def workload_line(name, steps, warmup, overlap=None, precision=None, cg=False, o
         W["outer_operator"] = {False: "FP64", True: "double-float (FP32 pairs)",
                                "all": "double-float outer iteration (FP32 pairs)"}[outer_df64]
         W["fdm_tensor_cores_by_level"] = [s.fdm_tensor_cores(l) for l in range(1, s.L + 1)]
+        W["fdm_operands"] = "BF16-rounded (FP32 accumulation)" if fdm_bf16 else "FP32"
     fp64 = W["precision"] == "fp64"
     pk, _ = peaks()
     clk, clk_basis = clock_mhz(clock_info, pk)
@@ -713,7 +727,7 @@ def run_workload(args):
     """One configuration other than the default line (`--workload NAME`)."""
     line = workload_line(args.workload, args.steps, args.warmup, overlap=args.overlap, precision=args.precision,
                          cg=args.cg, outer_df64="all" if args.outer_all else args.outer_df64,
-                         tensor_cores=args.tensor_cores)
+                         tensor_cores=args.tensor_cores, fdm_bf16=args.fdm_bf16)
     print(json.dumps(line), flush=True)
 
 
@@ -792,7 +806,7 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
-def serving_line(name, overlap=None, n_req=None):
+def serving_line(name, overlap=None, n_req=None, batch_dofs=None):
     """The serving stream: throughput (DOFs solved / makespan) and per-request
     latency (arrival to result on the host) percentiles.  Returns the JSON line
     as a dict."""
@@ -807,7 +821,8 @@ def serving_line(name, overlap=None, n_req=None):
     reqs = request_stream(seed=5, n_requests=n_req, overlap=overlap, sizes=tuple(W.get("sizes", (4, 8, 16, 24, 32))),
                           orders=tuple(W.get("orders", (2, 4, 8, 16))), rate=W.get("rate", 200.0))
     batch_max = int(os.environ.get("MG_SERVING_BATCH", "16"))
-    batch_dofs = int(os.environ.get("MG_SERVING_BATCH_DOFS", str(1 << 20)))
+    if batch_dofs is None:
+        batch_dofs = int(os.environ.get("MG_SERVING_BATCH_DOFS", str(1 << 20)))
     srv = Server(slots=slots, keep_solution=False, policy=policy, batch_max=batch_max, batch_dofs=batch_dofs)
     # warm-up: small requests of every order (module loading, first captures)
     warm = request_stream(seed=6, n_requests=64, sizes=(4,), overlap=overlap)[:8]

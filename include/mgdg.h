@@ -114,6 +114,10 @@ typedef struct {
   int autotune;          /* 1 = mg_bind_workspace times the kernel variants of every level's
                             smoother, operator and scatter (as the hierarchy's arithmetic runs
                             them) and keeps the fastest; 0 = the fixed defaults (default) */
+  int fdm_bf16;          /* MG_MIXED, a precision study: 1 = the FP32 smoother of single solves
+                            rounds every line entering a 1D product, and the 1D factors, to BF16
+                            and accumulates in FP32 -- the arithmetic of BF16 tensor-core
+                            contractions, on the CUDA cores; 0 = FP32 operands (default) */
 } mg_opts;
 
 /* Fill *o with the defaults above. */

@@ -55,9 +55,15 @@ __global__ void __launch_bounds__(kThreads) k_final(const double* partial, int n
   final_body(plain_block(), partial, nb, scal, slot);
 }
 
+// Scalars that every thread needs are formed once per block (thread 0,
+// shared memory): on this part a per-thread FP64 division or square root
+// costs as much FP64-pipe time as the pass's per-element arithmetic.
 template <typename T>
 __device__ __forceinline__ void sub_mean_body(BlockIdx bi_, T* x, int64_t n, const double* scal, int slot) {
-  const T mean = (T)(scal[slot] / (double)n);
+  __shared__ double s_mean;
+  if (threadIdx.x == 0) s_mean = scal[slot] / (double)n;
+  __syncthreads();
+  const T mean = (T)s_mean;
   for (int64_t i = bi_.b * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)bi_.g * blockDim.x)
     x[i] -= mean;
 }
@@ -73,8 +79,13 @@ __device__ __forceinline__ void cg_update_body(BlockIdx bi_, double* __restrict_
                                                double* __restrict__ r, const double* __restrict__ q, int64_t n,
                                                double* scal, double* partial) {
   __shared__ double sh[kThreads];
-  const double alpha = scal[kSlotRZ] / scal[kSlotPQ];
-  if (bi_.b == 0 && threadIdx.x == 0) scal[kSlotAlpha] = alpha;
+  __shared__ double s_alpha;
+  if (threadIdx.x == 0) {
+    s_alpha = scal[kSlotRZ] / scal[kSlotPQ];
+    if (bi_.b == 0) scal[kSlotAlpha] = s_alpha;
+  }
+  __syncthreads();
+  const double alpha = s_alpha;
   double s1 = 0.0, s2 = 0.0;
   for (int64_t i = bi_.b * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)bi_.g * blockDim.x) {
     x[i] += alpha * p[i];
@@ -188,7 +199,10 @@ __global__ void __launch_bounds__(kThreads) k_cg_sums_final(const double* partia
 template <typename TZ>
 __device__ __forceinline__ void cg_newdir_body(BlockIdx bi_, double* __restrict__ p, const TZ* __restrict__ zs,
                                                int64_t n, const double* scal, df64* __restrict__ pdf) {
-  const double zsc = z_scale<TZ>(scal), muz = scal[kSlotMuZ], beta = scal[kSlotBeta];
+  __shared__ double s_zsc;
+  if (threadIdx.x == 0) s_zsc = z_scale<TZ>(scal);
+  __syncthreads();
+  const double zsc = s_zsc, muz = scal[kSlotMuZ], beta = scal[kSlotBeta];
   for (int64_t i = bi_.b * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)bi_.g * blockDim.x) {
     const double v = ((double)zs[i] * zsc - muz) + beta * p[i];
     p[i] = v;
@@ -259,11 +273,17 @@ __global__ void k_add(double* __restrict__ y, const double* __restrict__ x, int6
 
 __device__ __forceinline__ void to_f32_body(BlockIdx bi_, const double* __restrict__ x, float* __restrict__ y,
                                             int64_t n, const double* scal, int slot) {
-  double s = 1.0;
-  if (slot >= 0) {
-    double nrm = sqrt(scal[slot]);
-    s = nrm > 0.0 ? 1.0 / nrm : 1.0;
+  __shared__ double s_s;
+  if (threadIdx.x == 0) {
+    double v = 1.0;
+    if (slot >= 0) {
+      const double nrm = sqrt(scal[slot]);
+      v = nrm > 0.0 ? 1.0 / nrm : 1.0;
+    }
+    s_s = v;
   }
+  __syncthreads();
+  const double s = s_s;
   for (int64_t i = bi_.b * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)bi_.g * blockDim.x)
     y[i] = (float)(x[i] * s);
 }
@@ -275,11 +295,17 @@ __global__ void k_to_f32(const double* __restrict__ x, float* __restrict__ y, in
 
 __device__ __forceinline__ void from_f32_body(BlockIdx bi_, const float* __restrict__ x, double* __restrict__ y,
                                               int64_t n, const double* scal, int slot) {
-  double s = 1.0;
-  if (slot >= 0) {
-    double nrm = sqrt(scal[slot]);
-    s = nrm > 0.0 ? nrm : 1.0;
+  __shared__ double s_s;
+  if (threadIdx.x == 0) {
+    double v = 1.0;
+    if (slot >= 0) {
+      const double nrm = sqrt(scal[slot]);
+      v = nrm > 0.0 ? nrm : 1.0;
+    }
+    s_s = v;
   }
+  __syncthreads();
+  const double s = s_s;
   for (int64_t i = bi_.b * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)bi_.g * blockDim.x)
     y[i] = (double)x[i] * s;
 }

@@ -20,6 +20,7 @@ namespace {
 
 constexpr int kT = 256;
 
+// FP64 reduction of a few thousand per-block totals (the second stages).
 __device__ double odf_block_sum(double v, double* sh) {
   const int t = threadIdx.x;
   sh[t] = v;
@@ -33,6 +34,27 @@ __device__ double odf_block_sum(double v, double* sh) {
   return r;
 }
 
+// Block total of one double-float value per thread, in a fixed order:
+// pair additions across each warp (FP32 pipes), then the eight warp totals
+// in FP64 by thread 0 (the only thread that receives the total).  Keeping
+// the per-element and per-thread work off the FP64 pipe is the point: ncu
+// counted a per-thread FP64 tree at 40 % of the FP64 pipe in these passes.
+__device__ double odf_block_total(df64 v, df64* sh) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const df64 w(__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o));
+    v = v + w;
+  }
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += (double)sh[w].hi + (double)sh[w].lo;
+  __syncthreads();
+  return t;
+}
+
 __device__ __forceinline__ Acc<df64> odf_zero() {
   Acc<df64> a;
   a.s = 0.f;
@@ -40,16 +62,15 @@ __device__ __forceinline__ Acc<df64> odf_zero() {
   return a;
 }
 
-__device__ __forceinline__ double odf_value(const Acc<df64>& a) { return (double)a.s + (double)a.c; }
 
 // partial[b] = sum p . q over block b's elements
 __device__ __forceinline__ void odf_dot_body(BlockIdx bi, const df64* __restrict__ p, const df64* __restrict__ q,
                                              int64_t n, double* partial) {
-  __shared__ double sh[kT];
+  __shared__ df64 sh[kT / 32];
   Acc<df64> acc = odf_zero();
   for (int64_t i = bi.b * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)bi.g * blockDim.x)
     acc.add(p[i], q[i]);
-  const double b = odf_block_sum(odf_value(acc), sh);
+  const double b = odf_block_total(acc.get(), sh);
   if (threadIdx.x == 0) partial[bi.b] = b;
 }
 
@@ -65,15 +86,22 @@ __global__ void __launch_bounds__(kT) k_odf_dot(const df64* __restrict__ p, cons
 __device__ __forceinline__ void odf_update_body(BlockIdx bi, df64* __restrict__ x, const df64* __restrict__ p,
                                                 df64* __restrict__ r, const df64* __restrict__ q, int64_t n,
                                                 double* scal, double* partial, float* __restrict__ r32) {
-  __shared__ double sh[kT];
-  const double alpha = scal[kSlotRZ] / scal[kSlotPQ];
-  const double nrm = sqrt(scal[kSlotRR]);
-  const float sc = nrm > 0.0 ? (float)(1.0 / nrm) : 1.f;
-  if (bi.b == 0 && threadIdx.x == 0) {
-    scal[kSlotAlpha] = alpha;
-    scal[kSlotScale] = nrm > 0.0 ? nrm : 1.0;
+  __shared__ df64 sh[kT / 32];
+  __shared__ df64 s_a;
+  __shared__ float s_sc;
+  if (threadIdx.x == 0) {  // the scalars once per block
+    const double alpha = scal[kSlotRZ] / scal[kSlotPQ];
+    const double nrm = sqrt(scal[kSlotRR]);
+    s_a = df64(alpha);
+    s_sc = nrm > 0.0 ? (float)(1.0 / nrm) : 1.f;
+    if (bi.b == 0) {
+      scal[kSlotAlpha] = alpha;
+      scal[kSlotScale] = nrm > 0.0 ? nrm : 1.0;
+    }
   }
-  const df64 a(alpha), na(-alpha);
+  __syncthreads();
+  const df64 a = s_a, na = -s_a;
+  const float sc = s_sc;
   Acc<df64> s1 = odf_zero(), s2 = odf_zero();
   for (int64_t i = bi.b * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)bi.g * blockDim.x) {
     x[i] = x[i] + a * p[i];
@@ -83,8 +111,8 @@ __device__ __forceinline__ void odf_update_body(BlockIdx bi, df64* __restrict__ 
     s2.add(ri, ri);
     r32[i] = __fmul_rn(__fadd_rn(ri.hi, ri.lo), sc);
   }
-  const double b1 = odf_block_sum(odf_value(s1), sh);
-  const double b2 = odf_block_sum(odf_value(s2), sh);
+  const double b1 = odf_block_total(s1.get(), sh);
+  const double b2 = odf_block_total(s2.get(), sh);
   if (threadIdx.x == 0) {
     partial[bi.b] = b1;
     partial[bi.g + bi.b] = b2;
@@ -101,7 +129,7 @@ __global__ void __launch_bounds__(kT) k_odf_update(df64* __restrict__ x, const d
 // Partial sums of z, z.q, z.r (columns 0 .. 2) of the unscaled FP32 z.
 __device__ __forceinline__ void odf_sums_body(BlockIdx bi, const float* __restrict__ z, const df64* __restrict__ q,
                                               const df64* __restrict__ r, int64_t n, double* partial) {
-  __shared__ double sh[kT];
+  __shared__ df64 sh[kT / 32];
   Acc<df64> a0 = odf_zero(), a1 = odf_zero(), a2 = odf_zero();
   for (int64_t i = bi.b * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)bi.g * blockDim.x) {
     const df64 zi(z[i], 0.f);
@@ -109,9 +137,9 @@ __device__ __forceinline__ void odf_sums_body(BlockIdx bi, const float* __restri
     a1.add(zi, q[i]);
     a2.add(zi, r[i]);
   }
-  const double b0 = odf_block_sum(odf_value(a0), sh);
-  const double b1 = odf_block_sum(odf_value(a1), sh);
-  const double b2 = odf_block_sum(odf_value(a2), sh);
+  const double b0 = odf_block_total(a0.get(), sh);
+  const double b1 = odf_block_total(a1.get(), sh);
+  const double b2 = odf_block_total(a2.get(), sh);
   if (threadIdx.x == 0) {
     partial[bi.b] = b0;
     partial[bi.g + bi.b] = b1;
@@ -157,7 +185,14 @@ __global__ void __launch_bounds__(kT) k_odf_sums_final(const double* partial, in
 // p = (s z - mu_z) + beta p (first: p = s z - mu_z), double-float
 __device__ __forceinline__ void odf_newdir_body(BlockIdx bi, df64* __restrict__ p, const float* __restrict__ z,
                                                 int64_t n, const double* scal, int first) {
-  const df64 zsc(scal[kSlotScale]), muz(-scal[kSlotMuZ]), beta(scal[kSlotBeta]);
+  __shared__ df64 s_v[3];
+  if (threadIdx.x == 0) {  // the scalars once per block
+    s_v[0] = df64(scal[kSlotScale]);
+    s_v[1] = df64(-scal[kSlotMuZ]);
+    s_v[2] = df64(scal[kSlotBeta]);
+  }
+  __syncthreads();
+  const df64 zsc = s_v[0], muz = s_v[1], beta = s_v[2];
   for (int64_t i = bi.b * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)bi.g * blockDim.x) {
     const df64 v = df64(z[i], 0.f) * zsc + muz;
     p[i] = first ? v : v + beta * p[i];
@@ -172,15 +207,15 @@ __global__ void __launch_bounds__(kT) k_odf_newdir(df64* __restrict__ p, const f
 
 // Partial sums of r and r.r (columns 0, 1) of a double-float vector.
 __device__ __forceinline__ void odf_rsums_body(BlockIdx bi, const df64* __restrict__ r, int64_t n, double* partial) {
-  __shared__ double sh[kT];
+  __shared__ df64 sh[kT / 32];
   Acc<df64> s1 = odf_zero(), s2 = odf_zero();
   for (int64_t i = bi.b * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)bi.g * blockDim.x) {
     const df64 ri = r[i];
     s1.add(ri);
     s2.add(ri, ri);
   }
-  const double b1 = odf_block_sum(odf_value(s1), sh);
-  const double b2 = odf_block_sum(odf_value(s2), sh);
+  const double b1 = odf_block_total(s1.get(), sh);
+  const double b2 = odf_block_total(s2.get(), sh);
   if (threadIdx.x == 0) {
     partial[bi.b] = b1;
     partial[bi.g + bi.b] = b2;
@@ -208,9 +243,14 @@ __global__ void __launch_bounds__(kT) k_odf_split(double* v, int64_t n) {
 // y = r / sqrt(rr) in FP32 and scal[Scale] = sqrt(rr): the first preconditioner input
 __device__ __forceinline__ void odf_to_f32_body(BlockIdx bi, const df64* __restrict__ r, float* __restrict__ y,
                                                 int64_t n, double* scal) {
-  const double nrm = sqrt(scal[kSlotRR]);
-  const float sc = nrm > 0.0 ? (float)(1.0 / nrm) : 1.f;
-  if (bi.b == 0 && threadIdx.x == 0) scal[kSlotScale] = nrm > 0.0 ? nrm : 1.0;
+  __shared__ float s_sc;
+  if (threadIdx.x == 0) {  // the scale once per block
+    const double nrm = sqrt(scal[kSlotRR]);
+    s_sc = nrm > 0.0 ? (float)(1.0 / nrm) : 1.f;
+    if (bi.b == 0) scal[kSlotScale] = nrm > 0.0 ? nrm : 1.0;
+  }
+  __syncthreads();
+  const float sc = s_sc;
   for (int64_t i = bi.b * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)bi.g * blockDim.x)
     y[i] = __fmul_rn(__fadd_rn(r[i].hi, r[i].lo), sc);
 }

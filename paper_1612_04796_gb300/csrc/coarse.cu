@@ -49,22 +49,36 @@ __device__ __forceinline__ void coarse_axis_body(BlockIdx bi_, const TI* __restr
   const int64_t total = (int64_t)Nx * Ny * Nz;
   const int Na = d.Ng[axis];
   const double shift = mean_slot >= 0 ? scal[mean_slot] / (double)total : 0.0;
-  for (int64_t idx = bi_.b * (int64_t)blockDim.x + threadIdx.x; idx < total;
-       idx += (int64_t)bi_.g * blockDim.x) {
-    int g[3];
-    const int i32 = (int)idx, gyz = i32 / Nx;  // coarse sizes fit in 32 bits
-    g[0] = i32 - gyz * Nx;
-    g[1] = gyz % Ny;
-    g[2] = gyz / Ny;
-    const int o = g[axis];
+  // four lanes per output, each summing every fourth term, combined by
+  // shuffles in a fixed order: four times the threads in flight for these
+  // latency-bound passes
+  const int part = threadIdx.x & 3;
+  const int64_t start = (bi_.b * (int64_t)blockDim.x + threadIdx.x) >> 2;
+  const int64_t stride = ((int64_t)bi_.g * blockDim.x) >> 2;
+  const int64_t rounds = (total + stride - 1) / stride;  // the same for the four lanes of an output
+  for (int64_t k = 0; k < rounds; ++k) {
+    const int64_t idx = start + k * stride;
+    const bool live = idx < total;
+    int g[3] = {0, 0, 0};
     double acc = 0.0;
-    for (int t = 0; t < Na; ++t) {
-      int h[3] = {g[0], g[1], g[2]};
-      h[axis] = t;
-      const int64_t src = in_eb ? eb_index(h[0], h[1], h[2], d) : h[0] + (int64_t)Nx * (h[1] + (int64_t)Ny * h[2]);
-      const double q = backward ? Q[o * Na + t] : Q[t * Na + o];
-      acc += q * ((double)in[src] - shift);
+    if (live) {
+      const int i32 = (int)idx, gyz = i32 / Nx;  // coarse sizes fit in 32 bits
+      g[0] = i32 - gyz * Nx;
+      g[1] = gyz % Ny;
+      g[2] = gyz / Ny;
+      const int o = g[axis];
+      for (int t = part; t < Na; t += 4) {
+        int h[3] = {g[0], g[1], g[2]};
+        h[axis] = t;
+        const int64_t src =
+            in_eb ? eb_index(h[0], h[1], h[2], d) : h[0] + (int64_t)Nx * (h[1] + (int64_t)Ny * h[2]);
+        const double q = backward ? Q[o * Na + t] : Q[t * Na + o];
+        acc += q * ((double)in[src] - shift);
+      }
     }
+    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+    if (!live || part != 0) continue;
     if (scale) {
       if (g[0] == nx0 && g[1] == ny0 && g[2] == nz0) acc = 0.0;
       else acc /= (lx[g[0]] + ly[g[1]] + lz[g[2]]);
@@ -102,7 +116,7 @@ cudaError_t coarse_passes(const double* const Q[3], const double* const lam[3], 
                           const int null_mode[3], const TI* f0, double* A, double* B, TO* u0, const double* scal,
                           int mean_slot, cudaStream_t s) {
   const int64_t N0 = (int64_t)d.Ng[0] * d.Ng[1] * d.Ng[2];
-  int64_t blocks = (N0 + 255) / 256;
+  int64_t blocks = (4 * N0 + 255) / 256;  // four lanes per output
   if (blocks > 152 * 8) blocks = 152 * 8;
   const int* nz = null_mode;
   const int b = (int)blocks;

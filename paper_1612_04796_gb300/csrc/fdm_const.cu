@@ -17,6 +17,8 @@
 // backward; y backward), and the last (x backward, weights folded into SW)
 // writes the weighted correction tile to the correction buffer, in the layout
 // of the other smoother kernels.
+#include <cuda_bf16.h>
+
 #include <algorithm>
 #include <atomic>
 
@@ -100,7 +102,19 @@ __device__ __forceinline__ void bwd_c(const FdmCArgs<M>& a, const float (&v)[M],
 
 __device__ __forceinline__ int fc_wrap(int x, int n) { return x < 0 ? x + n : (x >= n ? x - n : x); }
 
-template <int M>
+// BF16 operand emulation (mg_opts.fdm_bf16): every line entering a 1D
+// product is rounded to BF16 (to nearest even) and the 1D factors were
+// rounded on the host, the products accumulating in FP32 -- the arithmetic of
+// BF16 tensor-core contractions with FP32 accumulation, on the CUDA cores.
+template <bool BF, int M>
+__device__ __forceinline__ void round_line(float (&x)[M]) {
+  if constexpr (BF) {
+#pragma unroll
+    for (int t = 0; t < M; ++t) x[t] = __bfloat162float(__float2bfloat16_rn(x[t]));
+  }
+}
+
+template <int M, bool BF>
 __global__ void __launch_bounds__(FdmCShape<M>::threads) k_fdm_c(const __grid_constant__ FdmCArgs<M> a) {
   pdl_entry();
   using Sh = FdmCShape<M>;
@@ -128,6 +142,7 @@ __global__ void __launch_bounds__(FdmCShape<M>::threads) k_fdm_c(const __grid_co
       float x[M], y[M];
 #pragma unroll
       for (int t = 0; t < M; ++t) x[t] = __ldg((t < no ? rl : (t < no + n ? rc : rr)) + t);
+      round_line<BF>(x);
       fwd_c<M, 0>(a, x, y);
       float* line = fc_tile + g * M3 + M * l2;
 #pragma unroll
@@ -141,6 +156,7 @@ __global__ void __launch_bounds__(FdmCShape<M>::threads) k_fdm_c(const __grid_co
       float x[M], y[M];
 #pragma unroll
       for (int t = 0; t < M; ++t) x[t] = line[t * M];
+      round_line<BF>(x);
       fwd_c<M, 1>(a, x, y);
 #pragma unroll
       for (int t = 0; t < M; ++t) line[t * M] = y[t];
@@ -153,9 +169,11 @@ __global__ void __launch_bounds__(FdmCShape<M>::threads) k_fdm_c(const __grid_co
       float x[M], y[M];
 #pragma unroll
       for (int t = 0; t < M; ++t) x[t] = line[t * M2];
+      round_line<BF>(x);
       fwd_c<M, 2>(a, x, y);
 #pragma unroll
       for (int t = 0; t < M; ++t) y[t] *= __ldg(dinv + l2 + t * M2);
+      round_line<BF>(y);
       bwd_c<M, 2>(a, y, x);
 #pragma unroll
       for (int t = 0; t < M; ++t) line[t * M2] = x[t];
@@ -168,6 +186,7 @@ __global__ void __launch_bounds__(FdmCShape<M>::threads) k_fdm_c(const __grid_co
       float x[M], y[M];
 #pragma unroll
       for (int t = 0; t < M; ++t) y[t] = line[t * M];
+      round_line<BF>(y);
       bwd_c<M, 1>(a, y, x);
 #pragma unroll
       for (int t = 0; t < M; ++t) line[t * M] = x[t];
@@ -181,6 +200,7 @@ __global__ void __launch_bounds__(FdmCShape<M>::threads) k_fdm_c(const __grid_co
       float x[M], y[M];
 #pragma unroll
       for (int t = 0; t < M; ++t) y[t] = line[t];
+      round_line<BF>(y);
       bwd_c<M, 0>(a, y, x);
 #pragma unroll
       for (int t = 0; t < M; ++t) out[t] = x[t];
@@ -190,6 +210,16 @@ __global__ void __launch_bounds__(FdmCShape<M>::threads) k_fdm_c(const __grid_co
 }
 
 // Host-side fill of the parameter block from the FP32 tables of level l.
+inline float round_bf16_host(float v) {
+  // nearest BF16 (ties to even) of a finite FP32 value
+  uint32_t u;
+  memcpy(&u, &v, 4);
+  u += 0x7FFFu + ((u >> 16) & 1u);
+  u &= 0xFFFF0000u;
+  memcpy(&v, &u, 4);
+  return v;
+}
+
 template <int M>
 cudaError_t launch_fdm_c_m(const mg_ctx* c, int l, const float* r) {
   using Sh = FdmCShape<M>;
@@ -221,22 +251,32 @@ cudaError_t launch_fdm_c_m(const mg_ctx* c, int l, const float* r) {
         a.wo[d][t * h + q] = SW[t * M + ne + q];
       }
   }
+  const bool bf = c->opts.fdm_bf16 != 0;
+  if (bf) {
+    for (int d = 0; d < 3; ++d) {
+      for (auto& v : a.se[d]) v = round_bf16_host(v);
+      for (auto& v : a.so[d]) v = round_bf16_host(v);
+      for (auto& v : a.we[d]) v = round_bf16_host(v);
+      for (auto& v : a.wo[d]) v = round_bf16_host(v);
+    }
+  }
+  auto kern = bf ? k_fdm_c<M, true> : k_fdm_c<M, false>;
   if (Sh::smem > 48 * 1024) {
-    const cudaError_t e = cudaFuncSetAttribute(k_fdm_c<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::smem);
+    const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::smem);
     if (e != cudaSuccess) return e;
   }
-  static std::atomic<int> per_sm_cached{0};  // resident blocks per SM, queried once per width
-  int per_sm = per_sm_cached.load();
+  static std::atomic<int> per_sm_cached[2] = {{0}, {0}};  // resident blocks per SM, queried once per variant
+  int per_sm = per_sm_cached[bf].load();
   if (per_sm == 0) {
-    const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fdm_c<M>, Sh::threads, Sh::smem);
+    const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, Sh::threads, Sh::smem);
     if (e != cudaSuccess) return e;
     per_sm = std::max(per_sm, 1);
-    per_sm_cached.store(per_sm);
+    per_sm_cached[bf].store(per_sm);
   }
   const int64_t groups = (c->Ne + Sh::spb - 1) / Sh::spb;
   const int64_t slots = 152LL * per_sm;
   const int blocks = (int)std::min<int64_t>(groups, slots);
-  launch_pdl(k_fdm_c<M>, blocks, Sh::threads, Sh::smem, c->stream, a);
+  launch_pdl(kern, blocks, Sh::threads, Sh::smem, c->stream, a);
   c->nlaunch += 1;
   return cudaGetLastError();
 }

@@ -447,7 +447,7 @@ cudaError_t launch_fdm(const mg_ctx* c, int l, const T* r) {
     if (lv.fdm_tc) {
       const cudaError_t e = launch_fdm_tc(c, l, r);
       if (e != cudaErrorNotSupported) return e;
-    } else if (launch_recorder() == nullptr && !lv.fdm_plain) {
+    } else if (launch_recorder() == nullptr && (!lv.fdm_plain || c->opts.fdm_bf16)) {
       // single solves: the factors as kernel parameters; batched solves keep
       // the shared-memory kernel, whose body has a grouped twin
       const cudaError_t e = launch_fdm_c(c, l, r);

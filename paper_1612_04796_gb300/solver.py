@@ -35,7 +35,8 @@ class MGSolver:
 
     def __init__(self, lengths, counts, P, penalty=2.0, overlap=1, precision="fp64", overlap_mode="layers",
                  overlap_frac=0.08, weight_profile="quintic", ns_pre=1, ns_post=1, ns_growth=1, device="cuda",
-                 stream=None, tensor_cores=False, outer_df64=False, weight_delta="default", autotune=False):
+                 stream=None, tensor_cores=False, outer_df64=False, weight_delta="default", autotune=False,
+                 fdm_bf16=False):
         self.lib = load_library()
         self.device = torch.device(device)
         if self.device.type == "cuda" and self.device.index is None:
@@ -47,6 +48,7 @@ class MGSolver:
         opts.weight_profile = PROFILE[weight_profile]
         opts.weight_delta = WEIGHT_DELTA[weight_delta]
         opts.autotune = 1 if autotune else 0
+        opts.fdm_bf16 = 1 if fdm_bf16 else 0
         opts.ns_pre, opts.ns_post, opts.ns_growth = int(ns_pre), int(ns_post), int(ns_growth)
         opts.precision = PRECISION[precision]
         opts.fdm_tensor_cores = {False: 0, True: 1, "auto": 2}[tensor_cores]
