@@ -15,7 +15,9 @@ the whole outer iteration in double-float (mixed_df64_all); the level
 kernels against their rooflines (the FP64 / FP32 pipe at the sampled clock
 for the fast diagonalisation, HBM for the residual and the scatter); the
 anisotropic 48x8x8, P = 16 box (mixed MG-CG, N_O = 1, 2, 4, and N_O = 4 with
-the double-float outer iteration; key "c3"); the 512-request serving stream
+the double-float outer iteration; key "c3"); the 4^3, P = 32 cube with the
+smoother's contractions on the tensor cores and on the CUDA cores (key "c4");
+the 512-request serving stream
 (N_O = 1 and 4, and N_O = 4 without grouped launches; key "serving"); and the
 FP64 CPU oracle timed on the host cores on a bounded sample of the workload.
 
@@ -75,7 +77,7 @@ WORKLOADS = {
                     lengths=[48.0, 24.0, 1.0], elements=[8, 8, 8], P=16, overlap_layers=1, overlap_mode="max",
                     overlap_frac=0.08, ns_growth=3, rhs="gaussian", seed=3, precision="fp64", use_cg=True),
     "cube4_p32": dict(workload="periodic unit cube, 4^3 elements, P=32 (2,299,968 DOFs), f = 8 random Fourier modes "
-                        "(|k|_inf <= 8, seed 4), FP32 V(1,1) preconditioner (CUDA-core FDM) in FP64 PCG, N_O=1, tol 1e-10",
+                        "(|k|_inf <= 8, seed 4), FP32 V(1,1) preconditioner in FP64 PCG, N_O=1, tol 1e-10",
                lengths=[1.0, 1.0, 1.0], elements=[4, 4, 4], P=32, overlap_layers=1, rhs="fourier", seed=4,
                precision="mixed", use_cg=True),
 }
@@ -102,6 +104,7 @@ WORKLOADS["batch16_p4"] = dict(workload="16 independent small problems solved to
                                 problems=16, P=4, sizes=[4, 5, 6, 7, 8], aspect=[1.0, 8.0], seed=7,
                                 overlap_layers=1, precision="mixed", use_cg=True)
 FP32_FLOP_PER_CLK_PER_SM = 256    # 128 FP32 FMA lanes per SM
+TF32_PER_BF16 = 1.1 / 2.25         # nominal dense tensor rates per GPU
 
 # bounded sample of the workload for the CPU oracle (same P, overlap, tol; smaller mesh)
 ORACLE_SAMPLE = {"elements": [6, 6, 6], "P": 8}
@@ -300,6 +303,20 @@ def fdm_roofline(s, lev, fp64, clk, clk_basis, pk, traffic=None):
     vb = 8 if fp64 else 4
     algo_bytes = vb * (s.num_dofs(lev) + Ne * md[0] * md[1] * md[2])
     m = md[0] if md[0] == md[1] == md[2] else "x".join(str(v) for v in md)
+    if not fp64 and s.fdm_tensor_cores(lev) == 1:
+        # tcgen05 TF32 contractions: the dense count is what the tensor cores
+        # execute (no even/odd split), against the TF32 dense peak
+        tpeak = float(pk["bf16_tflops"]) * TF32_PER_BF16 * 1e12
+        return {
+            "kernel": "k_fdm_tc<%s> (level %d gather + fast diagonalisation on the tensor cores, TF32)" % (m, lev),
+            "bound": "tensor", "achieved": dense / t / 1e12, "peak": tpeak / 1e12, "unit": "TFLOP/s",
+            "frac": dense / t / tpeak, "traffic": traffic, "flop_per_launch": dense,
+            "avg_launch_ms": t * 1e3, "launches_timed": cnt,
+            "hbm": {"algorithmic_bytes_per_launch": algo_bytes, "achieved_gbs": algo_bytes / t / 1e9,
+                    "frac": algo_bytes / t / 1e9 / float(pk["hbm_gbs"])},
+            "peak_basis": "TF32 dense: measured bf16 burst %.1f TFLOP/s x the nominal TF32 / BF16 ratio %.4f "
+                          "(1.1 / 2.25 PFLOP/s)" % (float(pk["bf16_tflops"]), TF32_PER_BF16),
+        }
     return {
         "kernel": ("k_fdm_m<double, %s>" % m if fp64 else "k_fdm_c<%s>" % m)
                   + " (level %d gather + fast diagonalisation)" % lev,
@@ -612,6 +629,13 @@ def run_mg(args):
             line["c3"]["n_o_%d" % no] = compact_line(workload_line("box48x8x8_p16", 3, 2, overlap=no))
         line["c3"]["n_o_4_outer_df64"] = compact_line(workload_line("box48x8x8_p16", 3, 2, overlap=4,
                                                                     outer_df64="all"))
+        # the P = 32 cube: the FP32 smoother's contractions on the tensor cores
+        # where timing at setup prefers them (TF32 inputs, FP32 accumulation), and
+        # on the CUDA cores; outer iteration in double-float
+        line["c4"] = {}
+        for tcm in ("auto", "off"):
+            line["c4"]["tensor_cores_" + tcm] = compact_line(workload_line("cube4_p32", 5, 3, outer_df64="all",
+                                                                           tensor_cores=tcm))
         line["serving"] = {}
         for no in (1, 4):
             line["serving"]["n_o_%d" % no] = compact_line(serving_line("serving512", no))

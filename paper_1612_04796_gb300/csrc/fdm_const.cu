@@ -209,6 +209,146 @@ __global__ void __launch_bounds__(FdmCShape<M>::threads) k_fdm_c(const __grid_co
   }
 }
 
+// ---- the same solve split into three grid-wide kernels ----
+//
+// A level with few subdomains (the 4^3 mesh at P = 32 has 64) gives the
+// one-block-per-subdomain kernel too few blocks to fill 152 SMs.  Its passes
+// are independent across planes of the tile, so they are spread over three
+// kernels with many blocks each, the tile staying in the correction buffer
+// between them (L2-resident at these sizes):
+//   k_fdm_xy: per block SL z-planes (c) of one subdomain: gather the x-lines,
+//             x forward, y forward;
+//   k_fdm_z:  one thread per (i, j) column of every subdomain: z forward,
+//             times 1 / (lam_x + lam_y + lam_z), z backward, in place;
+//   k_fdm_yx: per block SL z-planes: y backward, x backward (weights folded
+//             into SW), the weighted correction written back in place.
+// Every line sees exactly the products of k_fdm_c, in the same order.
+template <int M>
+struct FdmSplitShape {
+  static constexpr int M2 = M * M, M3 = M2 * M;
+  static constexpr int sl = 160 / M < 1 ? 1 : 160 / M;  // planes per block: about 160 threads
+  static constexpr int sl_c = sl < M ? sl : M;
+  static constexpr int threads = (sl_c * M + 31) / 32 * 32;
+  static constexpr int groups = (M + sl_c - 1) / sl_c;        // plane groups per subdomain
+  static constexpr int zt = 256;                               // columns per block of k_fdm_z
+  static constexpr size_t smem = sizeof(float) * (size_t)sl_c * M2;
+};
+
+template <int M, bool BF>
+__global__ void __launch_bounds__(FdmSplitShape<M>::threads) k_fdm_xy(const __grid_constant__ FdmCArgs<M> a) {
+  pdl_entry();
+  using Sh = FdmSplitShape<M>;
+  constexpr int M2 = Sh::M2, SL = Sh::sl_c;
+  extern __shared__ __align__(16) float fs_tile[];  // SL planes, node (p, b) of plane g at g M^2 + p + M b
+  const int n = a.n, no = a.no, n3 = n * n * n;
+  const int64_t s = blockIdx.x / Sh::groups;
+  const int c0 = (int)(blockIdx.x - s * Sh::groups) * SL;
+  const int planes = M - c0 < SL ? M - c0 : SL;
+  const int tid = threadIdx.x;
+  if (s >= a.Ne) return;
+  const int sxy = (int)s / a.nx;
+  const int sx = (int)s - sxy * a.nx, sy = sxy % a.ny, sz = sxy / a.ny;
+  // x-lines (b, c): gather and x forward
+  if (tid < planes * M) {
+    const int g = tid / M, b = tid - g * M, c = c0 + g;
+    const int dy = b < no ? -1 : (b < no + n ? 0 : 1), iy = b - no + (dy < 0 ? n : (dy > 0 ? -n : 0));
+    const int dz = c < no ? -1 : (c < no + n ? 0 : 1), iz = c - no + (dz < 0 ? n : (dz > 0 ? -n : 0));
+    const int64_t row = (int64_t)a.nx * (fc_wrap(sy + dy, a.ny) + (int64_t)a.ny * fc_wrap(sz + dz, a.nz));
+    const int loc = n * (iy + n * iz);
+    const float* rl = a.r + (fc_wrap(sx - 1, a.nx) + row) * n3 + loc + (n - no);
+    const float* rc = a.r + (sx + row) * n3 + loc - no;
+    const float* rr = a.r + (fc_wrap(sx + 1, a.nx) + row) * n3 + loc - (no + n);
+    float x[M], y[M];
+#pragma unroll
+    for (int t = 0; t < M; ++t) x[t] = __ldg((t < no ? rl : (t < no + n ? rc : rr)) + t);
+    round_line<BF>(x);
+    fwd_c<M, 0>(a, x, y);
+    float* line = fs_tile + g * M2 + M * b;
+#pragma unroll
+    for (int t = 0; t < M; ++t) line[t] = y[t];
+  }
+  __syncthreads();
+  // y-lines (p, c): y forward, to plane c of the tile in the correction buffer
+  if (tid < planes * M) {
+    const int g = tid / M, p = tid - g * M;
+    const float* line = fs_tile + g * M2 + p;
+    float* out = a.corr + s * Sh::M3 + (int64_t)(c0 + g) * M2 + p;
+    float x[M], y[M];
+#pragma unroll
+    for (int t = 0; t < M; ++t) x[t] = line[t * M];
+    round_line<BF>(x);
+    fwd_c<M, 1>(a, x, y);
+#pragma unroll
+    for (int t = 0; t < M; ++t) out[t * M] = y[t];
+  }
+}
+
+template <int M, bool BF>
+__global__ void __launch_bounds__(FdmSplitShape<M>::zt) k_fdm_z(const __grid_constant__ FdmCArgs<M> a) {
+  pdl_entry();
+  using Sh = FdmSplitShape<M>;
+  constexpr int M2 = Sh::M2;
+  const int64_t col = (int64_t)blockIdx.x * Sh::zt + threadIdx.x;
+  const int64_t s = col / M2;
+  const int l2 = (int)(col - s * M2);
+  if (s >= a.Ne) return;
+  float* line = a.corr + s * Sh::M3 + l2;
+  float x[M], y[M];
+#pragma unroll
+  for (int t = 0; t < M; ++t) x[t] = line[(int64_t)t * M2];
+  round_line<BF>(x);
+  fwd_c<M, 2>(a, x, y);
+#pragma unroll
+  for (int t = 0; t < M; ++t) y[t] *= __ldg(a.dinv + l2 + t * M2);
+  round_line<BF>(y);
+  bwd_c<M, 2>(a, y, x);
+#pragma unroll
+  for (int t = 0; t < M; ++t) line[(int64_t)t * M2] = x[t];
+}
+
+template <int M, bool BF>
+__global__ void __launch_bounds__(FdmSplitShape<M>::threads) k_fdm_yx(const __grid_constant__ FdmCArgs<M> a) {
+  pdl_entry();
+  using Sh = FdmSplitShape<M>;
+  constexpr int M2 = Sh::M2, SL = Sh::sl_c;
+  extern __shared__ __align__(16) float fs_tile[];
+  const int64_t s = blockIdx.x / Sh::groups;
+  const int c0 = (int)(blockIdx.x - s * Sh::groups) * SL;
+  const int planes = M - c0 < SL ? M - c0 : SL;
+  const int tid = threadIdx.x;
+  if (s >= a.Ne) return;
+  float* plane0 = a.corr + s * Sh::M3 + (int64_t)c0 * M2;
+  // y-lines (p, c): y backward into shared memory
+  if (tid < planes * M) {
+    const int g = tid / M, p = tid - g * M;
+    const float* in = plane0 + g * M2 + p;
+    float* line = fs_tile + g * M2 + p;
+    float x[M], y[M];
+#pragma unroll
+    for (int t = 0; t < M; ++t) y[t] = in[t * M];
+    round_line<BF>(y);
+    bwd_c<M, 1>(a, y, x);
+#pragma unroll
+    for (int t = 0; t < M; ++t) line[t * M] = x[t];
+  }
+  __syncthreads();
+  // x-lines (b, c): x backward, in place in shared memory
+  if (tid < planes * M) {
+    const int g = tid / M, b = tid - g * M;
+    float* line = fs_tile + g * M2 + M * b;
+    float x[M], y[M];
+#pragma unroll
+    for (int t = 0; t < M; ++t) y[t] = line[t];
+    round_line<BF>(y);
+    bwd_c<M, 0>(a, y, x);
+#pragma unroll
+    for (int t = 0; t < M; ++t) line[t] = x[t];
+  }
+  __syncthreads();
+  // the planes are contiguous in the correction tile: coalesced copy out
+  for (int i = tid; i < planes * M2; i += blockDim.x) plane0[i] = fs_tile[i];
+}
+
 // Host-side fill of the parameter block from the FP32 tables of level l.
 inline float round_bf16_host(float v) {
   // nearest BF16 (ties to even) of a finite FP32 value
@@ -221,13 +361,11 @@ inline float round_bf16_host(float v) {
 }
 
 template <int M>
-cudaError_t launch_fdm_c_m(const mg_ctx* c, int l, const float* r) {
-  using Sh = FdmCShape<M>;
+void fill_fdm_c_args(const mg_ctx* c, int l, const float* r, FdmCArgs<M>& a) {
   constexpr int h = M / 2, ne = h + 1;
   static_assert(sizeof(FdmCArgs<M>) <= 32000, "parameter block too large");
   const LevelInfo& lv = c->lev[l];
   const float* tab = c->tab32_host.data();
-  FdmCArgs<M> a;
   a.r = r;
   a.corr = static_cast<float*>(c->ws.corr);
   a.dinv = c->ws.tab32 + lv.dinv;
@@ -251,8 +389,7 @@ cudaError_t launch_fdm_c_m(const mg_ctx* c, int l, const float* r) {
         a.wo[d][t * h + q] = SW[t * M + ne + q];
       }
   }
-  const bool bf = c->opts.fdm_bf16 != 0;
-  if (bf) {
+  if (c->opts.fdm_bf16) {
     for (int d = 0; d < 3; ++d) {
       for (auto& v : a.se[d]) v = round_bf16_host(v);
       for (auto& v : a.so[d]) v = round_bf16_host(v);
@@ -260,6 +397,14 @@ cudaError_t launch_fdm_c_m(const mg_ctx* c, int l, const float* r) {
       for (auto& v : a.wo[d]) v = round_bf16_host(v);
     }
   }
+}
+
+template <int M>
+cudaError_t launch_fdm_c_m(const mg_ctx* c, int l, const float* r) {
+  using Sh = FdmCShape<M>;
+  FdmCArgs<M> a;
+  fill_fdm_c_args<M>(c, l, r, a);
+  const bool bf = c->opts.fdm_bf16 != 0;
   auto kern = bf ? k_fdm_c<M, true> : k_fdm_c<M, false>;
   if (Sh::smem > 48 * 1024) {
     const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::smem);
@@ -281,6 +426,26 @@ cudaError_t launch_fdm_c_m(const mg_ctx* c, int l, const float* r) {
   return cudaGetLastError();
 }
 
+// The three kernels of the split solve, one after another on the stream.
+template <int M>
+cudaError_t launch_fdm_split_m(const mg_ctx* c, int l, const float* r) {
+  using Sh = FdmSplitShape<M>;
+  FdmCArgs<M> a;
+  fill_fdm_c_args<M>(c, l, r, a);
+  const bool bf = c->opts.fdm_bf16 != 0;
+  auto kxy = bf ? k_fdm_xy<M, true> : k_fdm_xy<M, false>;
+  auto kz = bf ? k_fdm_z<M, true> : k_fdm_z<M, false>;
+  auto kyx = bf ? k_fdm_yx<M, true> : k_fdm_yx<M, false>;
+  static_assert(Sh::smem <= 48 * 1024, "plane group exceeds the default shared-memory limit");
+  const int64_t bp = c->Ne * Sh::groups, bz = (c->Ne * Sh::M2 + Sh::zt - 1) / Sh::zt;
+  if (bp > 0x7fffffffLL || bz > 0x7fffffffLL) return cudaErrorNotSupported;
+  launch_pdl(kxy, (int)bp, Sh::threads, Sh::smem, c->stream, a);
+  launch_pdl(kz, (int)bz, Sh::zt, 0, c->stream, a);
+  launch_pdl(kyx, (int)bp, Sh::threads, Sh::smem, c->stream, a);
+  c->nlaunch += 3;
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 bool fdm_c_applies(const mg_ctx* c, int l) {
@@ -289,10 +454,19 @@ bool fdm_c_applies(const mg_ctx* c, int l) {
   return l >= 1 && m == lv.m[1] && m == lv.m[2] && (m & 1) && m >= 3 && m <= 35 && !c->tab32_host.empty();
 }
 
+int fdm_c_default_variant(const mg_ctx* c, int l) {
+  // the split pays for its two extra launches only on wide tiles
+  if (!fdm_c_applies(c, l) || c->lev[l].m[0] < 15) return 0;
+  const int m = c->lev[l].m[0], m2 = m * m;
+  const int64_t spb = m2 >= 256 ? 1 : 256 / m2;  // FdmCShape<m>::spb
+  return (c->Ne + spb - 1) / spb < 152 ? 2 : 0;
+}
+
 cudaError_t launch_fdm_c(const mg_ctx* c, int l, const float* r) {
   if (!fdm_c_applies(c, l)) return cudaErrorNotSupported;
+  const bool split = c->lev[l].fdm_variant == 2;
   switch (c->lev[l].m[0]) {
-#define MGDG_FC(M) case M: return launch_fdm_c_m<M>(c, l, r);
+#define MGDG_FC(M) case M: return split ? launch_fdm_split_m<M>(c, l, r) : launch_fdm_c_m<M>(c, l, r);
     MGDG_FC(3) MGDG_FC(5) MGDG_FC(7) MGDG_FC(9) MGDG_FC(11) MGDG_FC(13) MGDG_FC(15) MGDG_FC(17) MGDG_FC(19)
     MGDG_FC(21) MGDG_FC(23) MGDG_FC(25) MGDG_FC(27) MGDG_FC(29) MGDG_FC(31) MGDG_FC(33) MGDG_FC(35)
 #undef MGDG_FC

@@ -445,13 +445,16 @@ cudaError_t autotune_levels_t(mg_ctx* c) {
     T* r = lvec<T>(lv.r);
     if ((e = launch_zero<T>(c, u, lv.N)) != cudaSuccess) break;
     if ((e = launch_zero<T>(c, f, lv.N)) != cudaSuccess) break;
-    float t[2] = {0.f, 0.f};
+    float t[3] = {0.f, 0.f, 0.f};
     if (std::is_same<T, float>::value && !lv.fdm_tc) {
-      for (int v = 0; v < 2 && e == cudaSuccess; ++v) {
-        lv.fdm_plain = v;
+      const int nv = fdm_c_applies(c, l) ? 3 : 2;
+      int best = 0;
+      for (int v = 0; v < nv && e == cudaSuccess; ++v) {
+        lv.fdm_variant = v;
         e = timed([&]() { return launch_fdm<T>(c, l, f); }, &t[v]);
+        if (t[v] < t[best]) best = v;
       }
-      lv.fdm_plain = t[1] < t[0] ? 1 : 0;
+      lv.fdm_variant = best;
     }
     if (!std::is_same<T, double>::value) {
       for (int v = 0; v < 2 && e == cudaSuccess; ++v) {
@@ -1161,7 +1164,7 @@ mg_status mg_setup(double lx, double ly, double lz, int nx, int ny, int nz, int 
     lv.J = (l >= 1) ? tab((int64_t)lv.n * (c->lev[l - 1].n)) : -1;
     lv.u = lv.f = lv.r = nullptr;
     lv.fdm_tc = 0;
-    lv.fdm_plain = lv.sipg_plain = lv.scatter_plain = 0;
+    lv.fdm_variant = lv.sipg_plain = lv.scatter_plain = 0;
   }
   c->ws.tab_count = off;
   c->ws_bytes = make_layout(c).total;
@@ -1224,6 +1227,8 @@ mg_status mg_bind_workspace(mg_ctx* c, void* dptr, size_t bytes) {
   }
   CK(cudaStreamSynchronize(c->stream));
   if (st != kDevOk) return fail(c, MG_ENOCONV, "setup eigensolver did not converge");
+  if (c->opts.precision == MG_MIXED)
+    for (int l = 1; l <= c->L; ++l) c->lev[l].fdm_variant = fdm_c_default_variant(c, l);
   if (c->opts.precision == MG_MIXED && c->opts.fdm_tensor_cores != 0) CK(choose_fdm_kernels(c));
   if (c->opts.autotune) {
     const long long n0 = c->nlaunch;
@@ -1310,7 +1315,7 @@ int mg_level_kernel_variant(const mg_ctx* c, int level, int kind) {
   if (!c || level < 1 || level > c->L) return -1;
   const LevelInfo& lv = c->lev[level];
   switch (kind) {
-    case 0: return lv.fdm_plain;
+    case 0: return lv.fdm_variant;
     case 1: return lv.sipg_plain;
     case 2: return lv.scatter_plain;
     default: return -1;

@@ -240,10 +240,12 @@ struct LevelInfo {
   int64_t mass3;         // n^3: mass_x[i] mass_y[j] mass_z[k]
   int fdm_tc;            // FP32 smoother contractions on the tensor cores (1) or CUDA cores (0)
   // Kernel variants of single solves (mg_opts.autotune picks them by timing):
-  // 1 = the shared-memory FP32 smoother k_fdm_m instead of k_fdm_c; the plain
+  // fdm_variant 0 = the FP32 smoother k_fdm_c, 1 = the shared-memory k_fdm_m,
+  // 2 = k_fdm_c's passes split over three grid-wide kernels (the default where
+  // k_fdm_c would launch fewer blocks than there are SMs); 1 = the plain
   // operator k_sipg_n instead of k_sipg_c; the scatter k_scatter_n2 instead of
   // the element-aligned k_scatter_e.
-  int fdm_plain, sipg_plain, scatter_plain;
+  int fdm_variant, sipg_plain, scatter_plain;
   int64_t J;             // n * n_c interpolation from level l-1 (level >= 1)
   // device vectors (bytes sized for FP64; FP32 code uses the first half)
   void* u;
@@ -367,8 +369,9 @@ cudaError_t launch_fdm_tc(const mg_ctx* c, int l, const float* r, int self_test 
 bool fdm_tc_fits(const mg_ctx* c, int l);
 // FP32 corrections with the 1D factors as kernel parameters (fdm_const.cu):
 // cubic odd widths 3..35; cudaErrorNotSupported otherwise.
-cudaError_t launch_fdm_c(const mg_ctx* c, int l, const float* r);
+cudaError_t launch_fdm_c(const mg_ctx* c, int l, const float* r);  // k_fdm_c, or split if fdm_variant == 2
 bool fdm_c_applies(const mg_ctx* c, int l);
+int fdm_c_default_variant(const mg_ctx* c, int l);  // 2 where k_fdm_c would leave SMs idle, else 0
 
 // ---- transfers (transfer.cu) ----
 template <typename T>

@@ -356,20 +356,28 @@ __global__ void __launch_bounds__(256) k_scatter_n2(const T* __restrict__ corr, 
 }
 
 // k_scatter_n2 with blocks aligned to elements: a block takes EPB whole
-// elements, so the element coordinates and the three per-direction tile
-// offsets of the covering subdomains are formed once per element (in shared
-// memory) instead of once per DOF; each DOF then adds its <= 8 contributions
-// in the order of k_scatter_n / k_scatter_n2 (identical bits).
+// elements (or, at high order, 1 / cpe of one element, so that a mesh of few
+// elements still gives every SM blocks), so the element coordinates and the
+// three per-direction tile offsets of the covering subdomains are formed once
+// per element (in shared memory) instead of once per DOF; each DOF then adds
+// its <= 8 contributions in the order of k_scatter_n / k_scatter_n2
+// (identical bits).
 template <typename T, int N>
 __global__ void __launch_bounds__(256) k_scatter_e(const T* __restrict__ corr, T* __restrict__ u, int64_t Ne, int nx,
-                                                   int ny, int nz, SubShape g, int accumulate) {
+                                                   int ny, int nz, SubShape g, int accumulate, int cpe) {
   pdl_entry();
   constexpr int N3 = N * N * N, EPB = N3 >= 256 ? 1 : 256 / N3;
   __shared__ int64_t sb[EPB][3][3];  // [element][direction][offset -1, 0, +1]: that direction's share of the tile offset
   const int64_t mxyz = (int64_t)g.mx * g.my * g.mz;
   const int tid = threadIdx.x, nt = blockDim.x;
-  for (int64_t e0 = (int64_t)blockIdx.x * EPB; e0 < Ne; e0 += (int64_t)gridDim.x * EPB) {
+  // work units: EPB elements, or (EPB = 1) the cpe chunks of an element
+  const int chunk = EPB == 1 ? (N3 + cpe - 1) / cpe : N3;
+  const int64_t units = EPB == 1 ? Ne * cpe : (Ne + EPB - 1) / EPB;
+  for (int64_t vb = blockIdx.x; vb < units; vb += gridDim.x) {
+    const int64_t e0 = EPB == 1 ? vb / cpe : vb * EPB;
     const int cnt = (int)(Ne - e0 < EPB ? Ne - e0 : EPB);
+    const int d0 = EPB == 1 ? (int)(vb - e0 * cpe) * chunk : 0;
+    const int d1 = EPB == 1 ? (d0 + chunk < N3 ? d0 + chunk : N3) : cnt * N3;
     if (tid < cnt) {
       const int e = (int)(e0 + tid), exy = e / nx;  // element indices fit in 32 bits
       const int ex = e - exy * nx, ey = exy % ny, ez = exy / ny;
@@ -380,7 +388,7 @@ __global__ void __launch_bounds__(256) k_scatter_e(const T* __restrict__ corr, T
       }
     }
     __syncthreads();
-    for (int d = tid; d < cnt * N3; d += nt) {
+    for (int d = d0 + tid; d < d1; d += nt) {
       const int ge = EPB == 1 ? 0 : d / N3;
       const int loc = EPB == 1 ? d : d - ge * N3;
       const int i = loc % N, j = (loc / N) % N, k = loc / (N * N);
@@ -447,9 +455,10 @@ cudaError_t launch_fdm(const mg_ctx* c, int l, const T* r) {
     if (lv.fdm_tc) {
       const cudaError_t e = launch_fdm_tc(c, l, r);
       if (e != cudaErrorNotSupported) return e;
-    } else if (launch_recorder() == nullptr && (!lv.fdm_plain || c->opts.fdm_bf16)) {
-      // single solves: the factors as kernel parameters; batched solves keep
-      // the shared-memory kernel, whose body has a grouped twin
+    } else if (launch_recorder() == nullptr && (lv.fdm_variant != 1 || c->opts.fdm_bf16)) {
+      // single solves: the factors as kernel parameters (one kernel, or its
+      // passes split over three, fdm_variant 2); batched solves keep the
+      // shared-memory kernel, whose body has a grouped twin
       const cudaError_t e = launch_fdm_c(c, l, r);
       if (e != cudaErrorNotSupported) return e;
     }
@@ -532,12 +541,15 @@ cudaError_t launch_scatter(const mg_ctx* c, int l, T* u, int accumulate) {
   if (two && launch_recorder() == nullptr && !lv.scatter_plain) {
     // single solves: element-aligned blocks (batched solves keep k_scatter_n2, whose body has a twin)
     const int n3 = lv.n * lv.n * lv.n, epb = n3 >= 256 ? 1 : 256 / n3;
-    const int64_t eblocks = std::min<int64_t>((c->Ne + epb - 1) / epb, 152 * 16);
+    // chunks per element (one-element blocks): at least 152 * 8 blocks in all where the
+    // elements alone give fewer, each chunk at least 256 DOFs
+    const int cpe = epb > 1 ? 1 : (int)std::max<int64_t>(1, std::min<int64_t>(n3 / 256, (152 * 8 + c->Ne - 1) / c->Ne));
+    const int64_t eblocks = std::min<int64_t>(epb > 1 ? (c->Ne + epb - 1) / epb : c->Ne * cpe, 152 * 16);
     switch (lv.n) {
 #define MGDG_SCE(N)                                                                                           \
   case N:                                                                                                     \
     launch_pdl(k_scatter_e<T, N>, (int)eblocks, 256, 0, c->stream, corr, u, c->Ne, c->ne[0], c->ne[1],        \
-               c->ne[2], g, accumulate);                                                                      \
+               c->ne[2], g, accumulate, cpe);                                                                 \
     return cudaGetLastError();
       MGDG_SCE(3) MGDG_SCE(5) MGDG_SCE(9) MGDG_SCE(17) MGDG_SCE(33)
 #undef MGDG_SCE

@@ -11,11 +11,14 @@ tests compare every width the large configurations run with the FP64 oracle
   sampled values that tests/golden/make_smoother_wide.py stored from the
   oracle (a direct solve at m = 35 takes minutes and 15 GB).
 
-FP64 and double-float arithmetic, and FP32.  Tolerances (max-norm of the
-difference over the max-norm of the oracle's correction): FP64 1e-12 (the
-FP64 path's bound for one application); double-float 1e-10 (about 48
+FP64 and double-float arithmetic, FP32, and FP32 with the contractions on
+the tensor cores (TF32 inputs, FP32 accumulation).  Tolerances (max-norm of
+the difference over the max-norm of the oracle's correction): FP64 1e-12
+(the FP64 path's bound for one application); double-float 1e-10 (about 48
 significant bits per operation); FP32 1e-5 (contractions of length <= 35 in
-each of six passes, a few hundred FP32 ulps).
+each of six passes, a few hundred FP32 ulps); TF32 2e-2 in the max norm and
+5e-3 in the 2-norm (10 fraction bits per contraction input through six
+passes, as in the tensor-core tests at the smaller widths).
 
 Also: the FP64 multigrid solve of the 6^3, P = 8 problem that bench.py times
 for its CPU baseline (same cycles, same residual history as the oracle), and
@@ -37,7 +40,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LENGTHS = (1.0, 1.5, 0.7)
 COUNTS = (3, 4, 3)
 P16_LAYERS = [0, 1, 2, 4]  # m = 17, 19, 21, 25
-TOL = {"fp64": 1e-12, "df64": 1e-10, "fp32": 1e-5}
+TOL = {"fp64": 1e-12, "df64": 1e-10, "fp32": 1e-5, "tf32": 2e-2}
+TF32_L2 = 5e-3
 
 
 def rel_err(got, ref):
@@ -68,9 +72,12 @@ def p16_case():
 
 def gpu_smooth(mg, arith, lengths, counts, P, no, u, f):
     import torch
-    s = mg.MGSolver(lengths, counts, P, overlap=no)
+    tc = arith == "tf32"
+    s = mg.MGSolver(lengths, counts, P, overlap=no, **(dict(precision="mixed", tensor_cores=True) if tc else {}))
     assert s.layers(s.L) == no
-    if arith == "fp32":
+    if tc:
+        assert s.fdm_tensor_cores(s.L) == 1  # the fine level's tiles fit the tensor-core kernel
+    if arith in ("fp32", "tf32"):
         ut = cuda(u, torch.float32)
         s.smooth(ut, cuda(f, torch.float32))
     elif arith == "df64":
@@ -84,13 +91,16 @@ def gpu_smooth(mg, arith, lengths, counts, P, no, u, f):
     return out
 
 
-@pytest.mark.parametrize("arith", ["fp64", "df64", "fp32"])
+@pytest.mark.parametrize("arith", ["fp64", "df64", "fp32", "tf32"])
 @pytest.mark.parametrize("no", P16_LAYERS)
 def test_smooth_p16_widths(mg, p16_case, no, arith):
     u, f, corr = p16_case
     got = gpu_smooth(mg, arith, LENGTHS, COUNTS, 16, no, u, f)
     err = rel_err(got, corr[no])
     assert err < TOL[arith], (16 + 1 + 2 * no, arith, err)
+    if arith == "tf32":
+        e2 = float(np.linalg.norm(got - corr[no]) / np.linalg.norm(corr[no]))
+        assert e2 < TF32_L2, (16 + 1 + 2 * no, e2)
 
 
 @pytest.fixture(scope="module")
@@ -99,7 +109,7 @@ def m35_golden():
         return json.load(fh)
 
 
-@pytest.mark.parametrize("arith", ["fp64", "df64", "fp32"])
+@pytest.mark.parametrize("arith", ["fp64", "df64", "fp32", "tf32"])
 def test_smooth_m35_matches_stored_oracle(mg, m35_golden, arith):
     g = m35_golden
     c = g["case"]
@@ -113,8 +123,13 @@ def test_smooth_m35_matches_stored_oracle(mg, m35_golden, arith):
     assert err < TOL[arith], (arith, err)
     # the whole correction has the oracle's size (every sampled value agrees, and
     # nothing outside the sample is wildly off)
-    assert abs(np.max(np.abs(got)) / g["correction_max_abs"] - 1.0) < 10 * TOL[arith]
-    assert abs(np.linalg.norm(got) / g["correction_norm2"] - 1.0) < 10 * TOL[arith]
+    size_tol = TF32_L2 if arith == "tf32" else 10 * TOL[arith]
+    assert abs(np.max(np.abs(got)) / g["correction_max_abs"] - 1.0) < max(size_tol, TOL[arith])
+    assert abs(np.linalg.norm(got) / g["correction_norm2"] - 1.0) < size_tol
+    if arith == "tf32":
+        ref = np.asarray(g["value"])
+        e2 = float(np.linalg.norm(got[idx] - ref) / np.linalg.norm(ref))
+        assert e2 < TF32_L2, e2
 
 
 def test_mg_solve_6cube_p8_matches_oracle(mg):

@@ -13,9 +13,11 @@ sums, which dominate the correction, so the error grows with the spread of
 lam_x + lam_y + lam_z: measured 2.7e-2 (2-norm) at AR 48, P = 8; those cases
 allow 6e-2 / 4e-2.  The outer FP64 iteration absorbs this (the solve tests
 below and the AR 48 bench need at most one extra iteration).  Sizes the oracle cannot
-invert densely (m = 35, the 23 x 27 x 51 tiles of the Table 2 "max"
-overlap) are compared with the FP32 CUDA-core kernels, which are
-oracle-pinned at the smaller sizes."""
+invert densely in a test's time (m = 35, the 23 x 27 x 51 tiles of the
+Table 2 "max" overlap) are also compared with the FP32 CUDA-core kernels,
+which are oracle-pinned at every width; m = 35 (two lines per MMA row, the
+pass output filling 480 tensor-memory columns) and m = 17 ... 25 meet the
+oracle in test_gpu_fullwidth.py."""
 import math
 
 import numpy as np
@@ -102,6 +104,7 @@ def test_smooth_large_tiles_match_cuda_cores(mg, kw):
     lengths, counts, P = kw.pop("lengths"), kw.pop("counts"), kw.pop("P")
     s_tc = mg.MGSolver(lengths, counts, P, precision="mixed", tensor_cores=True, **kw)
     s_cc = mg.MGSolver(lengths, counts, P, precision="mixed", tensor_cores=False, **kw)
+    assert s_tc.fdm_tensor_cores(s_tc.L) == 1 and s_cc.fdm_tensor_cores(s_cc.L) == 0
     N = s_tc.num_dofs()
     u = cuda(inputs.gaussian(N, 12), torch.float32)
     f = cuda(inputs.gaussian(N, 13), torch.float32)
@@ -153,3 +156,25 @@ def test_autotuned_kernel_choice_solves(mg):
     u, its, rel, _ = s.solve(b, tol=1e-10, use_cg=True, maxit=100)
     s.close()
     assert rel <= 1e-10 and its < 100
+
+
+def test_p32_solve_with_tensor_cores(mg):
+    """At P = 32 (m = 35) the fine level's contractions run on the tensor cores
+    (two lines per MMA row); the mixed MG-CG solve reaches 1e-10 on the FP64
+    residual in about as many iterations as with the FP32 CUDA-core smoother."""
+    import torch
+    lengths, counts, P = (1.0, 1.0, 1.0), (3, 3, 3), 32
+    res = {}
+    for tc in (True, False):
+        s = mg.MGSolver(lengths, counts, P, precision="mixed", tensor_cores=tc)
+        assert s.fdm_tensor_cores(s.L) == (1 if tc else 0)
+        N = s.num_dofs()
+        f = inputs.gaussian(N, 21)
+        b = s.rhs(cuda(f - f.mean(), torch.float64))
+        u, its, rel, _ = s.solve(b, tol=1e-10, use_cg=True, maxit=60)
+        r = b - s.apply_sipg(u)
+        res[tc] = (its, float(torch.linalg.norm(r) / torch.linalg.norm(b)))
+        s.close()
+    (its_tc, rel_tc), (its_cc, rel_cc) = res[True], res[False]
+    assert rel_tc <= 1.01e-10 and rel_cc <= 1.01e-10, res
+    assert its_tc <= its_cc + 2, res
