@@ -185,14 +185,15 @@ int mg_level_fdm_tensor_cores(const mg_ctx* ctx, int level);
 
 /* Kernel variant of single solves on a level (what mg_opts.autotune chose, or
  * the default): kind 0 smoother, 1 operator, 2 scatter; returns 0 for the
- * kernel with the 1D factors as kernel parameters (FP32 smoother), the
- * FP32 / double-float operator on shared-memory element blocks and the
- * element-aligned scatter; 1 for the alternative (shared-memory smoother,
- * plain operator, plain scatter); for the FP32 smoother 2 for the passes of
- * the parameter-space kernel split over three grid-wide kernels (planes of
- * the tile, then its z-columns, then planes again), the default on cubic
- * levels whose subdomains would fill fewer blocks than the GPU has SMs; -1
- * for a bad level or kind. */
+ * kernels with the 1D coefficients as kernel parameters (FP32 smoother;
+ * FP32 / double-float operator on shared-memory element blocks,
+ * direction-split on meshes of few elements) and the element-aligned
+ * scatter; 1 for the alternative
+ * (shared-memory smoother, plain operator, plain scatter); for the FP32
+ * smoother 2 for the passes of the parameter-space kernel split over three
+ * grid-wide kernels (planes of the tile, then its z-columns, then planes
+ * again), the default on cubic levels whose subdomains would fill fewer
+ * blocks than the GPU has SMs; -1 for a bad level or kind. */
 int mg_level_kernel_variant(const mg_ctx* ctx, int level, int kind);
 
 /* Physical coordinates of the nodes of `level` into x, y, z (device, N_l each). */

@@ -1,13 +1,16 @@
 // Sum-factorised SIPG operator (Section 2, Eq. A) in FP32 or double-float
 // arithmetic with shared-memory element blocks and the 1D coefficients in
-// the kernel's parameter space.
+// the kernel's parameter space.  (In FP64 this form was measured slower than
+// the plain kernel, 248 vs 230 us on the 16^3, P = 8 level: the FP64 pipe,
+// not the coefficient loads, bounds it there, so FP64 keeps the plain kernel.)
 //
 // The plain operator kernel (sipg_kernels.cuh) makes three passes over an
 // element in global memory: every pass reads its lines with a stride and
 // reads and rewrites the output vector, and every multiply-add loads its
-// coefficient.  In FP32 and double-float that kernel waits on its loads.  Here a block takes EPB consecutive elements: their blocks of u are
-// loaded once with coalesced loads into shared memory, the x, y and z line
-// products run from there and accumulate in a shared output block, and the
+// coefficient, so it waits on its loads.  Here a block takes EPB consecutive
+// elements: their blocks of u are loaded once with coalesced loads into
+// shared memory, the x, y and z line products run from there and accumulate
+// in a shared output block, and the
 // last (z) pass applies the mass and forms f - A u with coalesced loads of f
 // and stores of the result.  Only the face terms read the neighbour lines
 // from global memory (L2).  The even/odd line matrices, face vectors, rows of
@@ -65,10 +68,13 @@ __device__ __forceinline__ int sc_wrap(int x, int n) { return x < 0 ? x + n : (x
 // face terms from the neighbours' lines in global memory, outputs combined
 // into the shared output block (D = 0: store, 1: add) or, for D = 2, into
 // out = residual ? f - M (acc + v) : M (acc + v) in global memory.
-template <typename T, int N, int D>
+// SPLIT (the direction-split kernel): su is the line in global memory, the
+// x and y contributions accumulate in out itself (so == out for D < 2; for
+// D = 2 they are read back from out).
+template <typename T, int N, int D, bool SPLIT = false>
 __device__ __forceinline__ void line_c(const SipgCArgs<T, N>& a, const T* __restrict__ su, T* so,
                                        const T* __restrict__ uL, const T* __restrict__ uR, int st,
-                                       T* __restrict__ out, const T* __restrict__ fl, T mpq) {
+                                       T* out, const T* __restrict__ fl, T mpq) {
   constexpr int P = N - 1, ne = (N + 1) / 2, no = N / 2;
   T ev[ne], od[no > 0 ? no : 1];
 #pragma unroll
@@ -122,12 +128,11 @@ __device__ __forceinline__ void line_c(const SipgCArgs<T, N>& a, const T* __rest
       so[i * st] += v0;
       if (i1 != i) so[i1 * st] += v1;
     } else {
-      const T w0 = mpq * a.mass[2][i] * (so[i * st] + v0);
+      const T* acc = SPLIT ? out : so;
+      const T w0 = mpq * a.mass[2][i] * (acc[i * st] + v0);
+      const T w1 = mpq * a.mass[2][i1] * (acc[i1 * st] + v1);
       out[i * st] = a.residual ? fl[i * st] - w0 : w0;
-      if (i1 != i) {
-        const T w1 = mpq * a.mass[2][i1] * (so[i1 * st] + v1);
-        out[i1 * st] = a.residual ? fl[i1 * st] - w1 : w1;
-      }
+      if (i1 != i) out[i1 * st] = a.residual ? fl[i1 * st] - w1 : w1;
     }
   }
 }
@@ -184,6 +189,46 @@ __global__ void __launch_bounds__(SipgCShape<T, N>::threads) k_sipg_c(const __gr
   }
 }
 
+// Direction-split form for meshes with few elements (too few blocks of
+// element blocks to fill the SMs; n = 33 always, whose element block does not
+// fit shared memory): three launches, one thread per line of direction D of
+// every element, the own line read from global memory, the contributions of
+// x and y accumulated in the output vector and the z launch applying the
+// mass and forming f - A u there.  Same arithmetic as k_sipg_c, with the
+// coefficients in the parameter space.
+template <typename T, int N, int D>
+__global__ void __launch_bounds__(256) k_sipg_cd(const __grid_constant__ SipgCArgs<T, N> a) {
+  pdl_entry();
+  constexpr int n2 = N * N, n3 = n2 * N;
+  const int64_t gl = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t e = gl / n2;
+  if (e >= a.Ne) return;
+  const int l2 = (int)(gl - e * n2), p = l2 % N, q = l2 / N;
+  const int e32 = (int)e, exy = e32 / a.nx;  // element indices fit in 32 bits
+  const int ex = e32 - exy * a.nx, ey = exy % a.ny, ez = exy / a.ny;
+  if (D == 0) {  // x lines (p, q) = (j, k)
+    const int base = N * (p + N * q);
+    const int64_t row = (int64_t)a.nx * (ey + (int64_t)a.ny * ez);
+    T* o = a.out + e * n3 + base;
+    line_c<T, N, 0, true>(a, a.u + e * n3 + base, o, a.u + (sc_wrap(ex - 1, a.nx) + row) * n3 + base,
+                          a.u + (sc_wrap(ex + 1, a.nx) + row) * n3 + base, 1, nullptr, nullptr, T(0.f));
+  } else if (D == 1) {  // y lines (p, q) = (i, k)
+    const int base = p + n2 * q;
+    const int64_t eL = ex + a.nx * (sc_wrap(ey - 1, a.ny) + (int64_t)a.ny * ez);
+    const int64_t eR = ex + a.nx * (sc_wrap(ey + 1, a.ny) + (int64_t)a.ny * ez);
+    T* o = a.out + e * n3 + base;
+    line_c<T, N, 1, true>(a, a.u + e * n3 + base, o, a.u + eL * n3 + base, a.u + eR * n3 + base, N, nullptr,
+                          nullptr, T(0.f));
+  } else {  // z lines (p, q) = (i, j): mass, residual
+    const int base = p + N * q;
+    const int64_t exy2 = ex + (int64_t)a.nx * ey, plane = (int64_t)a.nx * a.ny;
+    const int64_t eL = exy2 + plane * sc_wrap(ez - 1, a.nz), eR = exy2 + plane * sc_wrap(ez + 1, a.nz);
+    const int64_t off = e * n3 + base;
+    line_c<T, N, 2, true>(a, a.u + off, nullptr, a.u + eL * n3 + base, a.u + eR * n3 + base, n2, a.out + off,
+                          a.residual ? a.f + off : nullptr, a.mass[0][p] * a.mass[1][q]);
+  }
+}
+
 template <typename T>
 const std::vector<T>& host_tables(const mg_ctx* c);
 template <>
@@ -192,13 +237,12 @@ template <>
 const std::vector<df64>& host_tables<df64>(const mg_ctx* c) { return c->tabdf_host; }
 
 template <typename T, int N>
-cudaError_t launch_sipg_c_n(const mg_ctx* c, int l, const T* u, const T* f, T* out, int residual) {
+void fill_sipg_c_args(const mg_ctx* c, int l, const T* u, const T* f, T* out, int residual, SipgCArgs<T, N>& a) {
   using Sh = SipgCShape<T, N>;
   constexpr int ne = Sh::ne, no = Sh::no;
   static_assert(sizeof(SipgCArgs<T, N>) <= 32000, "parameter block too large");
   const LevelInfo& lv = c->lev[l];
   const T* tab = host_tables<T>(c).data();
-  SipgCArgs<T, N> a;
   a.u = u;
   a.f = f;
   a.out = out;
@@ -221,6 +265,13 @@ cudaError_t launch_sipg_c_n(const mg_ctx* c, int l, const T* u, const T* f, T* o
     a.d0[i] = tab[lv.t[0].d0 + i];
     a.dp[i] = tab[lv.t[0].dp + i];
   }
+}
+
+template <typename T, int N>
+cudaError_t launch_sipg_c_n(const mg_ctx* c, int l, const T* u, const T* f, T* out, int residual) {
+  using Sh = SipgCShape<T, N>;
+  SipgCArgs<T, N> a;
+  fill_sipg_c_args<T, N>(c, l, u, f, out, residual, a);
   if (Sh::smem > 48 * 1024) {
     const cudaError_t e =
         cudaFuncSetAttribute(k_sipg_c<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::smem);
@@ -242,12 +293,32 @@ cudaError_t launch_sipg_c_n(const mg_ctx* c, int l, const T* u, const T* f, T* o
   return cudaGetLastError();
 }
 
+template <typename T, int N>
+cudaError_t launch_sipg_cd_n(const mg_ctx* c, int l, const T* u, const T* f, T* out, int residual) {
+  SipgCArgs<T, N> a;
+  fill_sipg_c_args<T, N>(c, l, u, f, out, residual, a);
+  const int64_t blocks = (c->Ne * (int64_t)(N * N) + 255) / 256;
+  if (blocks > 0x7fffffffLL) return cudaErrorNotSupported;
+  launch_pdl(k_sipg_cd<T, N, 0>, (int)blocks, 256, 0, c->stream, a);
+  launch_pdl(k_sipg_cd<T, N, 1>, (int)blocks, 256, 0, c->stream, a);
+  launch_pdl(k_sipg_cd<T, N, 2>, (int)blocks, 256, 0, c->stream, a);
+  c->nlaunch += 3;
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_sipg_c_t(const mg_ctx* c, int l, const T* u, const T* f, T* out, int residual) {
   if (host_tables<T>(c).empty()) return cudaErrorNotSupported;
   const int n = c->lev[l].n;
   const int epb = n * n >= 256 ? 1 : 256 / (n * n);
-  if ((c->Ne + epb - 1) / epb < 152) return cudaErrorNotSupported;  // too few blocks: the direction-split kernel
+  if (n == 33) return launch_sipg_cd_n<T, 33>(c, l, u, f, out, residual);
+  if ((c->Ne + epb - 1) / epb < 152) {
+    // too few element blocks to fill the SMs: the direction-split form (high
+    // orders; the low ones keep the plain direction-split kernel)
+    if (n == 17) return launch_sipg_cd_n<T, 17>(c, l, u, f, out, residual);
+    if (n == 9) return launch_sipg_cd_n<T, 9>(c, l, u, f, out, residual);
+    return cudaErrorNotSupported;
+  }
   switch (n) {
     case 3: return launch_sipg_c_n<T, 3>(c, l, u, f, out, residual);
     case 5: return launch_sipg_c_n<T, 5>(c, l, u, f, out, residual);

@@ -7,6 +7,8 @@
 // through the smoother's correction buffer as scratch (order 32), or in one
 // fused kernel per element with shared-memory intermediates and even/odd
 // products (orders 2..16).
+#include <type_traits>
+
 #include "mg_internal.h"
 
 namespace mgdg {
@@ -214,6 +216,53 @@ __global__ void __launch_bounds__(128) k_restrict_fused(const T* __restrict__ rf
   restrict_fused_body<T, NF, NC>(plain_block(), rf, fc, J, Ne);
 }
 
+// One-axis contraction with the even / odd halves of the centro-symmetric 1D
+// matrix in the kernel's parameter space (order 32 in FP32, where the fused
+// kernel's element block does not fit shared memory and the generic kernel
+// above reloads a matrix entry for every multiply-add): one thread per line
+// along AXIS of every element, NI inputs in, NO outputs out (added to the
+// output with ACC), the products of cs_matvec.
+template <typename T, int NO, int NI>
+struct TrCArgs {
+  static constexpr int nei = (NI + 1) / 2, hi = NI / 2, neo = (NO + 1) / 2, ho = NO / 2;
+  const T* in;
+  T* out;
+  int64_t Ne;
+  int d0, d1, d2;  // input extents per element, x fastest
+  T ae[neo * nei];
+  T ao[(ho > 0 ? ho : 1) * (hi > 0 ? hi : 1)];
+};
+
+template <typename T, int NO, int NI, int AXIS, bool ACC>
+__global__ void __launch_bounds__(256) k_contract_c(const __grid_constant__ TrCArgs<T, NO, NI> a) {
+  pdl_entry();
+  const int o0 = AXIS == 0 ? NO : a.d0, o1 = AXIS == 1 ? NO : a.d1, o2 = AXIS == 2 ? NO : a.d2;
+  const int nl = AXIS == 0 ? a.d1 * a.d2 : (AXIS == 1 ? a.d0 * a.d2 : a.d0 * a.d1);
+  const int64_t gl = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t e = gl / nl;
+  if (e >= a.Ne) return;
+  const int l = (int)(gl - e * nl);
+  int ib, is, ob, os;
+  if (AXIS == 0) {
+    const int b = l % a.d1, c = l / a.d1;
+    ib = a.d0 * (b + a.d1 * c); is = 1; ob = o0 * (b + o1 * c); os = 1;
+  } else if (AXIS == 1) {
+    const int x = l % a.d0, c = l / a.d0;
+    ib = x + a.d0 * a.d1 * c; is = a.d0; ob = x + o0 * o1 * c; os = o0;
+  } else {
+    const int x = l % a.d0, b = l / a.d0;
+    ib = x + a.d0 * b; is = a.d0 * a.d1; ob = x + o0 * b; os = o0 * o1;
+  }
+  const T* src = a.in + e * ((int64_t)a.d0 * a.d1 * a.d2) + ib;
+  T* dst = a.out + e * ((int64_t)o0 * o1 * o2) + ob;
+  T x[NI], y[NO];
+#pragma unroll
+  for (int t = 0; t < NI; ++t) x[t] = src[t * is];
+  cs_matvec<T, NO, NI>(a.ae, a.ao, x, y);
+#pragma unroll
+  for (int t = 0; t < NO; ++t) dst[t * os] = ACC ? dst[t * os] + y[t] : y[t];
+}
+
 template <typename T>
 const T* table_of(const mg_ctx* c);
 template <>
@@ -226,6 +275,38 @@ const df64* table_of<df64>(const mg_ctx* c) { return c->ws.tabdf; }
 }  // namespace
 
 inline int fused_blocks(int64_t Ne) { return (int)(Ne < 152 * 12 ? Ne : 152 * 12); }
+
+// Halves of A (NO x NI, A[o][t] = J[o NC + t] for the prolongation, J[t NC + o]
+// for the restriction) from the level's FP32 table, as cs_split forms them.
+template <int NO, int NI>
+void fill_trc(const mg_ctx* c, int l, bool transpose, TrCArgs<float, NO, NI>& a) {
+  using A = TrCArgs<float, NO, NI>;
+  const int nc = c->lev[l - 1].n;
+  const float* J = c->tab32_host.data() + c->lev[l].J;
+  auto get = [&](int o, int t) { return transpose ? J[t * nc + o] : J[o * nc + t]; };
+  for (int o = 0; o < A::neo; ++o)
+    for (int t = 0; t < A::nei; ++t)
+      a.ae[o * A::nei + t] = (t < A::hi) ? 0.5f * (get(o, t) + get(o, NI - 1 - t)) : get(o, t);
+  for (int o = 0; o < A::ho; ++o)
+    for (int t = 0; t < A::hi; ++t) a.ao[o * A::hi + t] = 0.5f * (get(o, t) - get(o, NI - 1 - t));
+}
+
+template <int NO, int NI, int AXIS, bool ACC>
+cudaError_t contract_c(const mg_ctx* c, TrCArgs<float, NO, NI>& a, const float* in, float* out, int d0, int d1,
+                       int d2) {
+  a.in = in;
+  a.out = out;
+  a.Ne = c->Ne;
+  a.d0 = d0;
+  a.d1 = d1;
+  a.d2 = d2;
+  const int nl = AXIS == 0 ? d1 * d2 : (AXIS == 1 ? d0 * d2 : d0 * d1);
+  const int64_t blocks = (c->Ne * nl + 255) / 256;
+  launch_pdl(k_contract_c<float, NO, NI, AXIS, ACC>, (int)blocks, 256, 0, c->stream, a);
+  c->nlaunch += 1;
+  return cudaGetLastError();
+}
+
 
 template <typename T, int NF, int NC>
 cudaError_t restrict_fused(const mg_ctx* c, const T* r_fine, T* f_coarse, const T* J) {
@@ -257,6 +338,15 @@ cudaError_t launch_restrict(const mg_ctx* c, int l, const T* r_fine, T* f_coarse
   T* t1 = static_cast<T*>(c->ws.corr);
   T* t2 = t1 + c->Ne * (int64_t)nf * nf * nc;
   cudaError_t e;
+  if constexpr (std::is_same<T, float>::value) {
+    if (nf == 33 && nc == 17 && launch_recorder() == nullptr && !c->tab32_host.empty()) {
+      TrCArgs<float, 17, 33> a;
+      fill_trc<17, 33>(c, l, true, a);
+      if ((e = contract_c<17, 33, 2, false>(c, a, r_fine, t1, nf, nf, nf)) != cudaSuccess) return e;
+      if ((e = contract_c<17, 33, 1, false>(c, a, t1, t2, nf, nf, nc)) != cudaSuccess) return e;
+      return contract_c<17, 33, 0, false>(c, a, t2, f_coarse, nf, nc, nc);
+    }
+  }
   // z: (nf, nf, nf) -> (nf, nf, nc); y: -> (nf, nc, nc); x: -> (nc, nc, nc)
   if ((e = contract<T>(c, r_fine, t1, J, nf, nf, nf, 2, nc, nc, 1, 0)) != cudaSuccess) return e;
   if ((e = contract<T>(c, t1, t2, J, nf, nf, nc, 1, nc, nc, 1, 0)) != cudaSuccess) return e;
@@ -277,6 +367,15 @@ cudaError_t launch_prolong(const mg_ctx* c, int l, const T* u_coarse, T* u_fine)
   T* t1 = static_cast<T*>(c->ws.corr);
   T* t2 = t1 + c->Ne * (int64_t)nf * nc * nc;
   cudaError_t e;
+  if constexpr (std::is_same<T, float>::value) {
+    if (nf == 33 && nc == 17 && launch_recorder() == nullptr && !c->tab32_host.empty()) {
+      TrCArgs<float, 33, 17> a;
+      fill_trc<33, 17>(c, l, false, a);
+      if ((e = contract_c<33, 17, 0, false>(c, a, u_coarse, t1, nc, nc, nc)) != cudaSuccess) return e;
+      if ((e = contract_c<33, 17, 1, false>(c, a, t1, t2, nf, nc, nc)) != cudaSuccess) return e;
+      return contract_c<33, 17, 2, true>(c, a, t2, u_fine, nf, nf, nc);
+    }
+  }
   // x: (nc, nc, nc) -> (nf, nc, nc); y: -> (nf, nf, nc); z: -> (nf, nf, nf), accumulated
   if ((e = contract<T>(c, u_coarse, t1, J, nc, nc, nc, 0, nf, nc, 0, 0)) != cudaSuccess) return e;
   if ((e = contract<T>(c, t1, t2, J, nf, nc, nc, 1, nf, nc, 0, 0)) != cudaSuccess) return e;

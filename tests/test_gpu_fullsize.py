@@ -91,6 +91,29 @@ def test_cube4_p32_operator_sampled(mg):
         assert np.max(np.abs(got - ref)) / np.max(np.abs(ref)) < 1e-12, e
 
 
+@pytest.mark.parametrize("arith", ["fp32", "df64"])
+def test_cube4_p32_operator_sampled_fp32_df64(mg, arith):
+    """The operator of the mixed solve at P = 32 (n = 33 on 64 elements: the
+    direction-split kernels with the 1D coefficients as kernel parameters) in
+    FP32 (the multigrid's residuals; 1e-5 of the element's largest entry) and
+    in double-float (the outer iteration's A p; 1e-12)."""
+    import torch
+    s = mg.MGSolver(CUBE4_P32["lengths"], CUBE4_P32["counts"], CUBE4_P32["P"], precision="mixed",
+                    outer_df64=True)
+    u = inputs.gaussian(s.num_dofs(), 44)
+    if arith == "fp32":
+        u = u.astype(np.float32).astype(np.float64)
+        Au = s.apply_sipg(torch.tensor(u, dtype=torch.float32, device="cuda")).double().cpu().numpy()
+    else:
+        Au = s.apply_sipg_df64(_cuda(u)).cpu().numpy()
+    s.close()
+    n3 = 33 ** 3
+    for e in (0, 37, 63):
+        ref = oracle_operator_at(u, CUBE4_P32["lengths"], CUBE4_P32["counts"], 32, e)
+        got = Au[e * n3:(e + 1) * n3]
+        assert np.max(np.abs(got - ref)) / np.max(np.abs(ref)) < (1e-5 if arith == "fp32" else 1e-12), (e, arith)
+
+
 def test_cube4_p32_mixed_solve_reaches_tolerance(mg):
     """High order (P = 32): FP32 V-cycle inside FP64 CG reaches 1e-10 on the
     true FP64 residual; MG-CG takes about ceil(10 / 0.52) = 20 iterations
@@ -132,3 +155,27 @@ def test_cube16_p8_double_float_solves(cube16, mg):
         its.append(itm)
         sm.close()
     assert its[0] == its[1]
+
+
+@pytest.mark.parametrize("ctx_precision", ["fp64", "mixed"])
+def test_p32_fp32_vcycle_matches_fp64(mg, ctx_precision):
+    """One FP32 V-cycle at P = 32 (3^3 elements; the transfers between the
+    P = 32 and P = 16 levels with the 1D matrix as kernel parameters, and in a
+    mixed context the split smoother and the direction-split operator)
+    against the FP64 V-cycle, whose kernels are separate code: equal to FP32
+    rounding (1e-4 of the largest entry of the result)."""
+    import torch
+    lengths, counts, P = (1.0, 1.5, 0.7), (3, 3, 3), 32
+    s64 = mg.MGSolver(lengths, counts, P)
+    s32 = s64 if ctx_precision == "fp64" else mg.MGSolver(lengths, counts, P, precision="mixed")
+    N = s64.num_dofs()
+    u = inputs.gaussian(N, 45).astype(np.float32).astype(np.float64)
+    f = inputs.gaussian(N, 46).astype(np.float32).astype(np.float64)
+    u64 = s64.vcycle(_cuda(u), _cuda(f)).cpu().numpy()
+    ut = torch.tensor(u, dtype=torch.float32, device="cuda")
+    u32 = s32.vcycle(ut, torch.tensor(f, dtype=torch.float32, device="cuda")).double().cpu().numpy()
+    err = np.max(np.abs(u32 - u64)) / np.max(np.abs(u64))
+    assert err < 1e-4, err
+    if s32 is not s64:
+        s32.close()
+    s64.close()

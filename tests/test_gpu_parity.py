@@ -133,7 +133,7 @@ def test_apply_sipg_all_levels(solver_cache):
         assert rel_err(host(s.apply_sipg(cuda(u), level=l)), A @ u) < FP64_TOL
 
 
-@pytest.mark.parametrize("P", [4, 8])
+@pytest.mark.parametrize("P", [4, 8, 16])  # P = 16 on 60 elements: the direction-split kernels
 def test_apply_sipg_fp32(solver_cache, P):
     import torch
     lengths, counts = (1.0, 1.5, 0.7), (3, 4, 5)
