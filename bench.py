@@ -317,9 +317,14 @@ def fdm_roofline(s, lev, fp64, clk, clk_basis, pk, traffic=None):
             "peak_basis": "TF32 dense: measured bf16 burst %.1f TFLOP/s x the nominal TF32 / BF16 ratio %.4f "
                           "(1.1 / 2.25 PFLOP/s)" % (float(pk["bf16_tflops"]), TF32_PER_BF16),
         }
+    if fp64:
+        kname = "k_fdm_m<double, %s>" % m
+    else:
+        kname = {0: "k_fdm_c<%s>", 1: "k_fdm_m<float, %s>",
+                 2: "k_fdm_xy / k_fdm_z / k_fdm_yx<%s> (split over three kernels)"}.get(
+                     s.kernel_variants(lev)["fdm"], "k_fdm_c<%s>") % m
     return {
-        "kernel": ("k_fdm_m<double, %s>" % m if fp64 else "k_fdm_c<%s>" % m)
-                  + " (level %d gather + fast diagonalisation)" % lev,
+        "kernel": kname + " (level %d gather + fast diagonalisation)" % lev,
         "bound": "alu", "achieved": 2.0 * ops / t / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
         "frac": 2.0 * ops / t / peak, "traffic": traffic,
         "executed_ops_per_launch": ops, "avg_launch_ms": t * 1e3, "launches_timed": cnt,

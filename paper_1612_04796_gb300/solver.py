@@ -110,7 +110,8 @@ class MGSolver:
 
     def kernel_variants(self, level):
         """Kernel variants of single solves on `level` (mg_level_kernel_variant):
-        {"fdm", "sipg", "scatter"} -> 0 default, 1 alternative."""
+        {"fdm", "sipg", "scatter"} -> 0 parameter-space / element-aligned
+        kernels, 1 the alternative, 2 (FP32 smoother) the split form."""
         return {k: int(self.lib.mg_level_kernel_variant(self.ctx, level, i))
                 for i, k in enumerate(("fdm", "sipg", "scatter"))}
 
