@@ -127,9 +127,11 @@ def parse_args():
     ap.add_argument("--overlap", type=int, default=None, help="override N_O of the workload")
     ap.add_argument("--precision", default=None, choices=["fp64", "mixed"], help="override the workload's precision")
     ap.add_argument("--cg", action="store_true", help="solve the workload with MG-CG instead of its default solver")
-    ap.add_argument("--fdm-bf16", action="store_true",
-                    help="mixed runs: the FP32 smoother's contractions with BF16-rounded operands (a precision "
-                         "study of BF16 tensor-core contractions, run on the CUDA cores)")
+    ap.add_argument("--fdm-operands", default="fp32", choices=["fp32", "bf16", "fp8"],
+                    help="mixed runs: the FP32 smoother's contractions with operands rounded to BF16 or to FP8 "
+                         "E4M3 with power-of-two scales per line and per factor column (a precision study of "
+                         "BF16 / FP8 tensor-core contractions, run on the CUDA cores)")
+    ap.add_argument("--fdm-bf16", action="store_true", help="the same as --fdm-operands bf16")
     ap.add_argument("--outer-all", action="store_true",
                     help="mixed MG-CG runs: the whole outer iteration (vectors, inner products, updates and "
                          "q = A p) in double-float arithmetic")
@@ -659,7 +661,7 @@ def run_mg(args):
 
 
 def workload_line(name, steps, warmup, overlap=None, precision=None, cg=False, outer_df64=False,
-                  tensor_cores="off", fdm_bf16=False):
+                  tensor_cores="off", fdm_operands="fp32"):
     """One configuration: DOF/s of full solves (inputs resident, L2 flushed
     between solves), per-kernel device times and the rooflines of the
     fine-level kernels.  Returns the JSON line as a dict."""
@@ -678,7 +680,8 @@ def workload_line(name, steps, warmup, overlap=None, precision=None, cg=False, o
     dev = torch.device("cuda", torch.cuda.current_device())
     pkg.load_library()
     extra = {k: W[k] for k in ("overlap_mode", "overlap_frac", "ns_growth") if k in W}
-    extra_mixed = dict(extra, tensor_cores=TC_MODE[tensor_cores], outer_df64=outer_df64, fdm_bf16=fdm_bf16)
+    extra_mixed = dict(extra, tensor_cores=TC_MODE[tensor_cores], outer_df64=outer_df64,
+                       fdm_operands=fdm_operands)
     s = pkg.MGSolver(W["lengths"], W["elements"], W["P"], overlap=W["overlap_layers"], precision=W["precision"],
                      device=dev, **(extra_mixed if W["precision"] == "mixed" else extra))
     s64 = s if W["precision"] == "fp64" else pkg.MGSolver(W["lengths"], W["elements"], W["P"],
@@ -728,7 +731,9 @@ def workload_line(name, steps, warmup, overlap=None, precision=None, cg=False, o
         W["outer_operator"] = {False: "FP64", True: "double-float (FP32 pairs)",
                                "all": "double-float outer iteration (FP32 pairs)"}[outer_df64]
         W["fdm_tensor_cores_by_level"] = [s.fdm_tensor_cores(l) for l in range(1, s.L + 1)]
-        W["fdm_operands"] = "BF16-rounded (FP32 accumulation)" if fdm_bf16 else "FP32"
+        W["fdm_operands"] = {"fp32": "FP32", "bf16": "BF16-rounded (FP32 accumulation)",
+                             "fp8": "FP8 E4M3-rounded with power-of-two scales per line and per factor "
+                                    "column (FP32 accumulation)"}[fdm_operands]
     fp64 = W["precision"] == "fp64"
     pk, _ = peaks()
     clk, clk_basis = clock_mhz(clock_info, pk)
@@ -756,7 +761,8 @@ def run_workload(args):
     """One configuration other than the default line (`--workload NAME`)."""
     line = workload_line(args.workload, args.steps, args.warmup, overlap=args.overlap, precision=args.precision,
                          cg=args.cg, outer_df64="all" if args.outer_all else args.outer_df64,
-                         tensor_cores=args.tensor_cores, fdm_bf16=args.fdm_bf16)
+                         tensor_cores=args.tensor_cores,
+                         fdm_operands="bf16" if args.fdm_bf16 else args.fdm_operands)
     print(json.dumps(line), flush=True)
 
 

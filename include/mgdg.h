@@ -114,10 +114,13 @@ typedef struct {
   int autotune;          /* 1 = mg_bind_workspace times the kernel variants of every level's
                             smoother, operator and scatter (as the hierarchy's arithmetic runs
                             them) and keeps the fastest; 0 = the fixed defaults (default) */
-  int fdm_bf16;          /* MG_MIXED, a precision study: 1 = the FP32 smoother of single solves
-                            rounds every line entering a 1D product, and the 1D factors, to BF16
-                            and accumulates in FP32 -- the arithmetic of BF16 tensor-core
-                            contractions, on the CUDA cores; 0 = FP32 operands (default) */
+  int fdm_operands;      /* MG_MIXED, a precision study of the FP32 smoother of single solves:
+                            every line entering a 1D product, and the 1D factors, rounded to
+                            1 = BF16, or 2 = FP8 E4M3 after a power-of-two scale per line (data)
+                            or per output index (factors: "scaled eigenbases"), accumulating in
+                            FP32 -- the arithmetic of BF16 / FP8 tensor-core contractions, on
+                            the CUDA cores (the one-kernel smoother); 0 = FP32 operands
+                            (default) */
 } mg_opts;
 
 /* Fill *o with the defaults above. */

@@ -27,7 +27,7 @@ class MgOpts(ctypes.Structure):
         ("stream", ctypes.c_void_p),
         ("weight_delta", ctypes.c_int),
         ("autotune", ctypes.c_int),
-        ("fdm_bf16", ctypes.c_int),
+        ("fdm_operands", ctypes.c_int),
     ]
 
 

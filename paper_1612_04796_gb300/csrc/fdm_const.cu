@@ -18,6 +18,10 @@
 // writes the weighted correction tile to the correction buffer, in the layout
 // of the other smoother kernels.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+
+#include <cmath>
 
 #include <algorithm>
 #include <atomic>
@@ -102,19 +106,36 @@ __device__ __forceinline__ void bwd_c(const FdmCArgs<M>& a, const float (&v)[M],
 
 __device__ __forceinline__ int fc_wrap(int x, int n) { return x < 0 ? x + n : (x >= n ? x - n : x); }
 
-// BF16 operand emulation (mg_opts.fdm_bf16): every line entering a 1D
-// product is rounded to BF16 (to nearest even) and the 1D factors were
-// rounded on the host, the products accumulating in FP32 -- the arithmetic of
-// BF16 tensor-core contractions with FP32 accumulation, on the CUDA cores.
-template <bool BF, int M>
+// Operand emulation for a precision study (mg_opts.fdm_operands): every
+// line entering a 1D product is rounded (OP = 1: to BF16, nearest even;
+// OP = 2: to FP8 E4M3, nearest even, after scaling the line by the power of
+// two that puts its largest magnitude in [224, 448)) and the 1D factors were
+// rounded the same way on the host (FP8: per output index), the products
+// accumulating in FP32 -- the arithmetic of BF16 / FP8 tensor-core
+// contractions with FP32 accumulation and scaled eigenbases, on the CUDA cores.
+template <int OP, int M>
 __device__ __forceinline__ void round_line(float (&x)[M]) {
-  if constexpr (BF) {
+  if constexpr (OP == 1) {
 #pragma unroll
     for (int t = 0; t < M; ++t) x[t] = __bfloat162float(__float2bfloat16_rn(x[t]));
+  } else if constexpr (OP == 2) {
+    float amax = 0.f;
+#pragma unroll
+    for (int t = 0; t < M; ++t) amax = fmaxf(amax, fabsf(x[t]));
+    if (amax > 0.f) {
+      int e;
+      frexpf(amax / 448.f, &e);  // amax / 448 = f 2^e, f in [0.5, 1)
+      const float sc = ldexpf(1.f, e), inv = ldexpf(1.f, -e);
+#pragma unroll
+      for (int t = 0; t < M; ++t) {
+        const __nv_fp8_storage_t q = __nv_cvt_float_to_fp8(x[t] * inv, __NV_SATFINITE, __NV_E4M3);
+        x[t] = __half2float(__half(__nv_cvt_fp8_to_halfraw(q, __NV_E4M3))) * sc;
+      }
+    }
   }
 }
 
-template <int M, bool BF>
+template <int M, int OP>
 __global__ void __launch_bounds__(FdmCShape<M>::threads) k_fdm_c(const __grid_constant__ FdmCArgs<M> a) {
   pdl_entry();
   using Sh = FdmCShape<M>;
@@ -142,7 +163,7 @@ __global__ void __launch_bounds__(FdmCShape<M>::threads) k_fdm_c(const __grid_co
       float x[M], y[M];
 #pragma unroll
       for (int t = 0; t < M; ++t) x[t] = __ldg((t < no ? rl : (t < no + n ? rc : rr)) + t);
-      round_line<BF>(x);
+      round_line<OP>(x);
       fwd_c<M, 0>(a, x, y);
       float* line = fc_tile + g * M3 + M * l2;
 #pragma unroll
@@ -156,7 +177,7 @@ __global__ void __launch_bounds__(FdmCShape<M>::threads) k_fdm_c(const __grid_co
       float x[M], y[M];
 #pragma unroll
       for (int t = 0; t < M; ++t) x[t] = line[t * M];
-      round_line<BF>(x);
+      round_line<OP>(x);
       fwd_c<M, 1>(a, x, y);
 #pragma unroll
       for (int t = 0; t < M; ++t) line[t * M] = y[t];
@@ -169,11 +190,11 @@ __global__ void __launch_bounds__(FdmCShape<M>::threads) k_fdm_c(const __grid_co
       float x[M], y[M];
 #pragma unroll
       for (int t = 0; t < M; ++t) x[t] = line[t * M2];
-      round_line<BF>(x);
+      round_line<OP>(x);
       fwd_c<M, 2>(a, x, y);
 #pragma unroll
       for (int t = 0; t < M; ++t) y[t] *= __ldg(dinv + l2 + t * M2);
-      round_line<BF>(y);
+      round_line<OP>(y);
       bwd_c<M, 2>(a, y, x);
 #pragma unroll
       for (int t = 0; t < M; ++t) line[t * M2] = x[t];
@@ -186,7 +207,7 @@ __global__ void __launch_bounds__(FdmCShape<M>::threads) k_fdm_c(const __grid_co
       float x[M], y[M];
 #pragma unroll
       for (int t = 0; t < M; ++t) y[t] = line[t * M];
-      round_line<BF>(y);
+      round_line<OP>(y);
       bwd_c<M, 1>(a, y, x);
 #pragma unroll
       for (int t = 0; t < M; ++t) line[t * M] = x[t];
@@ -200,7 +221,7 @@ __global__ void __launch_bounds__(FdmCShape<M>::threads) k_fdm_c(const __grid_co
       float x[M], y[M];
 #pragma unroll
       for (int t = 0; t < M; ++t) y[t] = line[t];
-      round_line<BF>(y);
+      round_line<OP>(y);
       bwd_c<M, 0>(a, y, x);
 #pragma unroll
       for (int t = 0; t < M; ++t) out[t] = x[t];
@@ -222,7 +243,8 @@ __global__ void __launch_bounds__(FdmCShape<M>::threads) k_fdm_c(const __grid_co
 //             times 1 / (lam_x + lam_y + lam_z), z backward, in place;
 //   k_fdm_yx: per block SL z-planes: y backward, x backward (weights folded
 //             into SW), the weighted correction written back in place.
-// Every line sees exactly the products of k_fdm_c, in the same order.
+// Every line sees exactly the products of k_fdm_c, in the same order.  (FP32
+// operands only: the operand studies run the one-kernel form.)
 template <int M>
 struct FdmSplitShape {
   static constexpr int M2 = M * M, M3 = M2 * M;
@@ -234,7 +256,7 @@ struct FdmSplitShape {
   static constexpr size_t smem = sizeof(float) * (size_t)sl_c * M2;
 };
 
-template <int M, bool BF>
+template <int M>
 __global__ void __launch_bounds__(FdmSplitShape<M>::threads) k_fdm_xy(const __grid_constant__ FdmCArgs<M> a) {
   pdl_entry();
   using Sh = FdmSplitShape<M>;
@@ -261,7 +283,6 @@ __global__ void __launch_bounds__(FdmSplitShape<M>::threads) k_fdm_xy(const __gr
     float x[M], y[M];
 #pragma unroll
     for (int t = 0; t < M; ++t) x[t] = __ldg((t < no ? rl : (t < no + n ? rc : rr)) + t);
-    round_line<BF>(x);
     fwd_c<M, 0>(a, x, y);
     float* line = fs_tile + g * M2 + M * b;
 #pragma unroll
@@ -276,14 +297,13 @@ __global__ void __launch_bounds__(FdmSplitShape<M>::threads) k_fdm_xy(const __gr
     float x[M], y[M];
 #pragma unroll
     for (int t = 0; t < M; ++t) x[t] = line[t * M];
-    round_line<BF>(x);
     fwd_c<M, 1>(a, x, y);
 #pragma unroll
     for (int t = 0; t < M; ++t) out[t * M] = y[t];
   }
 }
 
-template <int M, bool BF>
+template <int M>
 __global__ void __launch_bounds__(FdmSplitShape<M>::zt) k_fdm_z(const __grid_constant__ FdmCArgs<M> a) {
   pdl_entry();
   using Sh = FdmSplitShape<M>;
@@ -296,17 +316,15 @@ __global__ void __launch_bounds__(FdmSplitShape<M>::zt) k_fdm_z(const __grid_con
   float x[M], y[M];
 #pragma unroll
   for (int t = 0; t < M; ++t) x[t] = line[(int64_t)t * M2];
-  round_line<BF>(x);
   fwd_c<M, 2>(a, x, y);
 #pragma unroll
   for (int t = 0; t < M; ++t) y[t] *= __ldg(a.dinv + l2 + t * M2);
-  round_line<BF>(y);
   bwd_c<M, 2>(a, y, x);
 #pragma unroll
   for (int t = 0; t < M; ++t) line[(int64_t)t * M2] = x[t];
 }
 
-template <int M, bool BF>
+template <int M>
 __global__ void __launch_bounds__(FdmSplitShape<M>::threads) k_fdm_yx(const __grid_constant__ FdmCArgs<M> a) {
   pdl_entry();
   using Sh = FdmSplitShape<M>;
@@ -326,7 +344,6 @@ __global__ void __launch_bounds__(FdmSplitShape<M>::threads) k_fdm_yx(const __gr
     float x[M], y[M];
 #pragma unroll
     for (int t = 0; t < M; ++t) y[t] = in[t * M];
-    round_line<BF>(y);
     bwd_c<M, 1>(a, y, x);
 #pragma unroll
     for (int t = 0; t < M; ++t) line[t * M] = x[t];
@@ -339,7 +356,6 @@ __global__ void __launch_bounds__(FdmSplitShape<M>::threads) k_fdm_yx(const __gr
     float x[M], y[M];
 #pragma unroll
     for (int t = 0; t < M; ++t) y[t] = line[t];
-    round_line<BF>(y);
     bwd_c<M, 0>(a, y, x);
 #pragma unroll
     for (int t = 0; t < M; ++t) line[t] = x[t];
@@ -358,6 +374,37 @@ inline float round_bf16_host(float v) {
   u &= 0xFFFF0000u;
   memcpy(&v, &u, 4);
   return v;
+}
+
+// Nearest FP8 E4M3 value of a finite v (1 sign bit, 4 exponent bits with
+// bias 7, 3 fraction bits: normal values (1 + f/8) 2^(e-7), subnormals
+// f/8 2^-6, largest finite 448), ties to even, saturating at +-448.
+inline double round_e4m3_host(double v) {
+  if (v == 0.0) return v;
+  const double av = std::fabs(v);
+  int e;
+  std::frexp(av, &e);                              // av = g 2^e, g in [0.5, 1): leading bit 2^(e-1)
+  const int lead = std::max(e - 1, -6);            // below 2^-6 the spacing stays that of the subnormals
+  const double q = std::ldexp(1.0, lead - 3);      // spacing of E4M3 values there
+  const double r = std::min(std::nearbyint(av / q) * q, 448.0);  // default rounding: ties to even
+  return std::copysign(r, v);
+}
+
+// Round the rows x cols matrix A (row-major) to E4M3 after scaling each
+// column (by_row = false) or row (true) by the power of two that puts its
+// largest magnitude in [224, 448), then undo the scaling.
+inline void scale_round_e4m3(float* A, int rows, int cols, bool by_row) {
+  const int outer = by_row ? rows : cols, inner = by_row ? cols : rows;
+  for (int o = 0; o < outer; ++o) {
+    auto at = [&](int i) -> float& { return by_row ? A[o * cols + i] : A[i * cols + o]; };
+    double amax = 0.0;
+    for (int i = 0; i < inner; ++i) amax = std::max(amax, std::fabs((double)at(i)));
+    if (amax == 0.0) continue;
+    int e;
+    std::frexp(amax / 448.0, &e);
+    for (int i = 0; i < inner; ++i)
+      at(i) = (float)std::ldexp(round_e4m3_host(std::ldexp((double)at(i), -e)), e);
+  }
 }
 
 template <int M>
@@ -389,12 +436,22 @@ void fill_fdm_c_args(const mg_ctx* c, int l, const float* r, FdmCArgs<M>& a) {
         a.wo[d][t * h + q] = SW[t * M + ne + q];
       }
   }
-  if (c->opts.fdm_bf16) {
+  if (c->opts.fdm_operands == 1) {
     for (int d = 0; d < 3; ++d) {
       for (auto& v : a.se[d]) v = round_bf16_host(v);
       for (auto& v : a.so[d]) v = round_bf16_host(v);
       for (auto& v : a.we[d]) v = round_bf16_host(v);
       for (auto& v : a.wo[d]) v = round_bf16_host(v);
+    }
+  } else if (c->opts.fdm_operands == 2) {
+    // FP8 with a power-of-two scale per output index: the columns p of the
+    // forward halves (se[t ne + p], so[t h + q]) and the rows t of the
+    // backward halves (we[t ne + p], wo[t h + q])
+    for (int d = 0; d < 3; ++d) {
+      scale_round_e4m3(a.se[d], ne, ne, false);
+      scale_round_e4m3(a.so[d], h, h, false);
+      scale_round_e4m3(a.we[d], ne, ne, true);
+      scale_round_e4m3(a.wo[d], h, h, true);
     }
   }
 }
@@ -404,19 +461,19 @@ cudaError_t launch_fdm_c_m(const mg_ctx* c, int l, const float* r) {
   using Sh = FdmCShape<M>;
   FdmCArgs<M> a;
   fill_fdm_c_args<M>(c, l, r, a);
-  const bool bf = c->opts.fdm_bf16 != 0;
-  auto kern = bf ? k_fdm_c<M, true> : k_fdm_c<M, false>;
+  const int op = c->opts.fdm_operands;
+  auto kern = op == 1 ? k_fdm_c<M, 1> : (op == 2 ? k_fdm_c<M, 2> : k_fdm_c<M, 0>);
   if (Sh::smem > 48 * 1024) {
     const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::smem);
     if (e != cudaSuccess) return e;
   }
-  static std::atomic<int> per_sm_cached[2] = {{0}, {0}};  // resident blocks per SM, queried once per variant
-  int per_sm = per_sm_cached[bf].load();
+  static std::atomic<int> per_sm_cached[3] = {{0}, {0}, {0}};  // resident blocks per SM, once per variant
+  int per_sm = per_sm_cached[op].load();
   if (per_sm == 0) {
     const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, Sh::threads, Sh::smem);
     if (e != cudaSuccess) return e;
     per_sm = std::max(per_sm, 1);
-    per_sm_cached[bf].store(per_sm);
+    per_sm_cached[op].store(per_sm);
   }
   const int64_t groups = (c->Ne + Sh::spb - 1) / Sh::spb;
   const int64_t slots = 152LL * per_sm;
@@ -432,10 +489,9 @@ cudaError_t launch_fdm_split_m(const mg_ctx* c, int l, const float* r) {
   using Sh = FdmSplitShape<M>;
   FdmCArgs<M> a;
   fill_fdm_c_args<M>(c, l, r, a);
-  const bool bf = c->opts.fdm_bf16 != 0;
-  auto kxy = bf ? k_fdm_xy<M, true> : k_fdm_xy<M, false>;
-  auto kz = bf ? k_fdm_z<M, true> : k_fdm_z<M, false>;
-  auto kyx = bf ? k_fdm_yx<M, true> : k_fdm_yx<M, false>;
+  auto kxy = k_fdm_xy<M>;
+  auto kz = k_fdm_z<M>;
+  auto kyx = k_fdm_yx<M>;
   static_assert(Sh::smem <= 48 * 1024, "plane group exceeds the default shared-memory limit");
   const int64_t bp = c->Ne * Sh::groups, bz = (c->Ne * Sh::M2 + Sh::zt - 1) / Sh::zt;
   if (bp > 0x7fffffffLL || bz > 0x7fffffffLL) return cudaErrorNotSupported;
@@ -464,7 +520,7 @@ int fdm_c_default_variant(const mg_ctx* c, int l) {
 
 cudaError_t launch_fdm_c(const mg_ctx* c, int l, const float* r) {
   if (!fdm_c_applies(c, l)) return cudaErrorNotSupported;
-  const bool split = c->lev[l].fdm_variant == 2;
+  const bool split = c->lev[l].fdm_variant == 2 && c->opts.fdm_operands == 0;
   switch (c->lev[l].m[0]) {
 #define MGDG_FC(M) case M: return split ? launch_fdm_split_m<M>(c, l, r) : launch_fdm_c_m<M>(c, l, r);
     MGDG_FC(3) MGDG_FC(5) MGDG_FC(7) MGDG_FC(9) MGDG_FC(11) MGDG_FC(13) MGDG_FC(15) MGDG_FC(17) MGDG_FC(19)

@@ -1044,7 +1044,7 @@ void mg_default_opts(mg_opts* o) {
   o->stream = nullptr;
   o->weight_delta = MG_DELTA_DEFAULT;
   o->autotune = 0;
-  o->fdm_bf16 = 0;
+  o->fdm_operands = 0;
 }
 
 mg_status mg_setup(double lx, double ly, double lz, int nx, int ny, int nz, int P, double penalty, int overlap,
@@ -1062,7 +1062,7 @@ mg_status mg_setup(double lx, double ly, double lz, int nx, int ny, int nz, int 
   if (o.fdm_tensor_cores < 0 || o.fdm_tensor_cores > 2) return MG_EINVAL;
   if (o.outer_df64 < 0 || o.outer_df64 > 2) return MG_EINVAL;
   if (o.autotune < 0 || o.autotune > 1) return MG_EINVAL;
-  if (o.fdm_bf16 < 0 || o.fdm_bf16 > 1) return MG_EINVAL;
+  if (o.fdm_operands < 0 || o.fdm_operands > 2) return MG_EINVAL;
   if (o.weight_profile < MG_WEIGHT_QUINTIC || o.weight_profile > MG_WEIGHT_QUINTIC_NORMALISED) return MG_EINVAL;
   if (o.weight_delta < MG_DELTA_DEFAULT || o.weight_delta > MG_DELTA_STRIP) return MG_EINVAL;
   if (o.overlap_mode == MG_OVERLAP_LAYERS && o.weight_delta == MG_DELTA_STRIP) return MG_EINVAL;

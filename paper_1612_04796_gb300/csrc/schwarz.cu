@@ -455,7 +455,7 @@ cudaError_t launch_fdm(const mg_ctx* c, int l, const T* r) {
     if (lv.fdm_tc) {
       const cudaError_t e = launch_fdm_tc(c, l, r);
       if (e != cudaErrorNotSupported) return e;
-    } else if (launch_recorder() == nullptr && (lv.fdm_variant != 1 || c->opts.fdm_bf16)) {
+    } else if (launch_recorder() == nullptr && (lv.fdm_variant != 1 || c->opts.fdm_operands)) {
       // single solves: the factors as kernel parameters (one kernel, or its
       // passes split over three, fdm_variant 2); batched solves keep the
       // shared-memory kernel, whose body has a grouped twin

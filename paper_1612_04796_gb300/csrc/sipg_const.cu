@@ -22,6 +22,7 @@
 // is formed as the product of the three 1D masses.
 #include <algorithm>
 #include <atomic>
+#include <type_traits>
 
 #include "mg_internal.h"
 
@@ -97,7 +98,12 @@ __device__ __forceinline__ void line_c(const SipgCArgs<T, N>& a, const T* __rest
   const T s = av + cv, tm = av - cv;
   const T lo = a.g2[D] * b - a.mu[D] * av;
   const T hi = -(a.mu[D] * cv + a.g2[D] * dd);
-#pragma unroll
+  // double-float at n = 33: the fully unrolled outputs overflow the
+  // instruction cache (the kernel stalled on instruction fetch), so one output
+  // per trip, its products unrolled, the coefficients indexed by the trip
+  // (1.66 vs 2.59 ms per P = 32 solve; in FP32 rolling measured slower)
+  constexpr int kUnroll = (std::is_same<T, df64>::value && N >= 33) ? 1 : ne;
+#pragma unroll kUnroll
   for (int i = 0; i < ne; ++i) {
     Acc<T> ea;
     ea.init(a.fe[D][i], s);

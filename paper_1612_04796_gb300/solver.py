@@ -15,6 +15,7 @@ PRECISION = {"fp64": 0, "mixed": 1, "df64": 2}
 OVERLAP_MODE = {"layers": 0, "width": 1, "max": 2}
 PROFILE = {"quintic": 0, "linear": 1, "quintic_halves": 2, "quintic_normalised": 3}
 WEIGHT_DELTA = {"default": 0, "node": 1, "mid": 2, "strip": 3}
+FDM_OPERANDS = {"fp32": 0, "bf16": 1, "fp8": 2}
 
 
 class MGError(RuntimeError):
@@ -36,7 +37,7 @@ class MGSolver:
     def __init__(self, lengths, counts, P, penalty=2.0, overlap=1, precision="fp64", overlap_mode="layers",
                  overlap_frac=0.08, weight_profile="quintic", ns_pre=1, ns_post=1, ns_growth=1, device="cuda",
                  stream=None, tensor_cores=False, outer_df64=False, weight_delta="default", autotune=False,
-                 fdm_bf16=False):
+                 fdm_bf16=False, fdm_operands="fp32"):
         self.lib = load_library()
         self.device = torch.device(device)
         if self.device.type == "cuda" and self.device.index is None:
@@ -48,7 +49,8 @@ class MGSolver:
         opts.weight_profile = PROFILE[weight_profile]
         opts.weight_delta = WEIGHT_DELTA[weight_delta]
         opts.autotune = 1 if autotune else 0
-        opts.fdm_bf16 = 1 if fdm_bf16 else 0
+        # operand precision study of the FP32 smoother (fdm_bf16=True is fdm_operands="bf16")
+        opts.fdm_operands = FDM_OPERANDS["bf16" if fdm_bf16 else fdm_operands]
         opts.ns_pre, opts.ns_post, opts.ns_growth = int(ns_pre), int(ns_post), int(ns_growth)
         opts.precision = PRECISION[precision]
         opts.fdm_tensor_cores = {False: 0, True: 1, "auto": 2}[tensor_cores]
