@@ -791,7 +791,7 @@ def run_batch(args):
     solvers = [p[0] for p in probs]
     stream = torch.cuda.current_stream(dev)
 
-    def run(batched, k):
+    def run(batched, k, batch_solvers=None):
         ms, its = [], None
         for _ in range(k):
             e0 = torch.cuda.Event(enable_timing=True)
@@ -802,8 +802,8 @@ def run_batch(args):
             for _, _, u in probs:
                 u.zero_()
             if batched:
-                _, its, _, sts = pkg.solve_batch(solvers, [b for _, b, _ in probs], [u for _, _, u in probs],
-                                                 tol=1e-10, maxit=200)
+                _, its, _, sts = pkg.solve_batch(batch_solvers or solvers, [b for _, b, _ in probs],
+                                                 [u for _, _, u in probs], tol=1e-10, maxit=200)
                 assert all(v == 0 for v in sts), sts
             else:
                 its = [s.solve(b, u, tol=1e-10, maxit=200, use_cg=True)[1] for s, b, u in probs]
@@ -819,14 +819,27 @@ def run_batch(args):
     lb0 = solvers[0].batch_launches()
     ms_b, its_b = run(True, args.steps)
     launches_b = solvers[0].batch_launches() - lb0
+    u_b = [u.clone() for _, _, u in probs]  # the batched solutions
     ls0 = sum(s.kernel_launches() for s in solvers)
     ms_s, its_s = run(False, args.steps)
     launches_s = sum(s.kernel_launches() for s in solvers) - ls0
     clock_info = clocks.stop()
     assert its_b == its_s
-    u_b = [u.clone() for _, _, u in probs]
-    run(False, 1)
+    # batched against one by one: the batched kernels are separate compilations
+    # of the same code, equal to rounding (bit for bit where the compiler
+    # contracted alike)
     identical = all(torch.equal(a, u) for a, (_, _, u) in zip(u_b, probs))
+    max_rel_diff = max(float((a - u).abs().max() / u.abs().max()) for a, (_, _, u) in zip(u_b, probs))
+    # the same batch with every grouped launch in persistent form (one wave of
+    # blocks looping over the problems' blocks; the first context's option
+    # decides): a twin of the first problem's context with persistent="always"
+    s0 = solvers[0]
+    sp = pkg.MGSolver(s0.lengths, s0.counts, W["P"], overlap=W["overlap_layers"], precision=W["precision"],
+                      device=dev, outer_df64=True, persistent="always")
+    run(True, args.warmup, [sp] + solvers[1:])
+    ms_p, its_p = run(True, args.steps, [sp] + solvers[1:])
+    identical_p = its_p == its_b and all(torch.equal(a, u) for a, (_, _, u) in zip(u_b, probs))
+    sp.close()
     tb, ts = statistics.median(ms_b), statistics.median(ms_s)
     line = {
         "metric": METRIC, "value": dofs / (tb / 1e3), "unit": "DOF/s", "n_gpus": 1, "steps": args.steps,
@@ -836,7 +849,10 @@ def run_batch(args):
                        iterations=its_b, l2="inputs L2-resident (small problems; the point is launch overhead)"),
         "gpu_launches": launches_b // args.steps,
         "one_by_one": {"value": dofs / (ts / 1e3), "ms_per_step": ts, "gpu_launches": launches_s // args.steps},
-        "speedup_vs_one_by_one": ts / tb, "bitwise_identical_to_one_by_one": identical, "clocks": clock_info,
+        "speedup_vs_one_by_one": ts / tb, "bitwise_identical_to_one_by_one": identical,
+        "max_rel_diff_vs_one_by_one": max_rel_diff, "clocks": clock_info,
+        "persistent_always": {"value": dofs / (statistics.median(ms_p) / 1e3), "ms_per_step": statistics.median(ms_p),
+                              "bitwise_identical_to_batched": identical_p},
     }
     print(json.dumps(line), flush=True)
 

@@ -121,6 +121,10 @@ typedef struct {
                             FP32 -- the arithmetic of BF16 / FP8 tensor-core contractions, on
                             the CUDA cores (the one-kernel smoother); 0 = FP32 operands
                             (default) */
+  int persistent;        /* mg_solve_batch (the first context's value): 0 = a grouped launch with
+                            more blocks than the GPU holds at once runs in persistent form -- one
+                            wave of blocks looping over the problems' blocks (default); 1 = every
+                            grouped launch persistent; 2 = none */
 } mg_opts;
 
 /* Fill *o with the defaults above. */

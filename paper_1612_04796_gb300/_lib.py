@@ -28,6 +28,7 @@ class MgOpts(ctypes.Structure):
         ("weight_delta", ctypes.c_int),
         ("autotune", ctypes.c_int),
         ("fdm_operands", ctypes.c_int),
+        ("persistent", ctypes.c_int),
     ]
 
 

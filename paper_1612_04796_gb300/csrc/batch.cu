@@ -8,7 +8,9 @@
 // one kernel found at the heads of the sequences (that of the sequence with
 // the most records left) is launched once through its grouped twin
 // (k_grouped) for every sequence that has it at its head, each problem
-// getting its own block range and parameters.  Problems of different sizes, aspect ratios and even kernel
+// getting its own block range and parameters; a launch with more blocks than
+// the GPU holds at once runs the persistent form k_grouped_p (a grid of one
+// wave looping over the problems' blocks; mg_opts.persistent).  Problems of different sizes, aspect ratios and even kernel
 // variants (a small mesh takes the direction-split operator) merge as far as
 // their sequences agree.
 #include "mg_internal.h"
@@ -40,7 +42,7 @@ bool same_kernel(const LaunchRec& a, const LaunchRec& b) {
 
 }  // namespace
 
-cudaError_t launch_merged(const std::vector<LaunchRecorder>& seqs, cudaStream_t s, long long* launches) {
+cudaError_t launch_merged(const std::vector<LaunchRecorder>& seqs, cudaStream_t s, long long* launches, int persist) {
   const int B = (int)seqs.size();
   std::vector<size_t> head(B, 0);
   long long n_launch = 0;
@@ -83,7 +85,7 @@ cudaError_t launch_merged(const std::vector<LaunchRecorder>& seqs, cudaStream_t 
     cudaError_t e = cudaSuccess;
     if (ref.grouped) {  // a kernel with a body always runs its twin, also for one problem
       for (int k = 0; k < n && e == cudaSuccess; k += kMaxBatch) {
-        e = ref.grouped(group + k, std::min(kMaxBatch, n - k), s);
+        e = ref.grouped(group + k, std::min(kMaxBatch, n - k), s, persist);
         ++n_launch;
       }
     } else {

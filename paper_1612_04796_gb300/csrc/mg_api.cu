@@ -816,11 +816,11 @@ struct BatchCache {
 };
 
 cudaError_t capture_merged(BatchCache* bc, const std::vector<LaunchRecorder>& seqs, long long* launches,
-                           cudaGraphExec_t* exec) {
+                           cudaGraphExec_t* exec, int persist) {
   cudaError_t e;
   if (!bc->cap && (e = cudaStreamCreateWithFlags(&bc->cap, cudaStreamNonBlocking)) != cudaSuccess) return e;
   if ((e = cudaStreamBeginCapture(bc->cap, cudaStreamCaptureModeRelaxed)) != cudaSuccess) return e;
-  const cudaError_t el = launch_merged(seqs, bc->cap, launches);
+  const cudaError_t el = launch_merged(seqs, bc->cap, launches, persist);
   cudaGraph_t graph = nullptr;
   const cudaError_t ec = cudaStreamEndCapture(bc->cap, &graph);
   if (el != cudaSuccess || ec != cudaSuccess) {
@@ -838,6 +838,7 @@ template <typename F>
 cudaError_t batch_step(std::vector<BatchMember>& ms, cudaStream_t s, long long* launches, F step,
                        BatchCache* cache = nullptr, int kind = 0) {
   uint64_t key = (uint64_t)kind << 32;
+  const int persist = ms.empty() ? 0 : ms[0].c->opts.persistent;  // the first context's choice
   for (int i = 0; i < (int)ms.size(); ++i)
     if (ms[i].active) key |= 1ull << i;
   BatchCache::Entry* ent = nullptr;
@@ -863,18 +864,18 @@ cudaError_t batch_step(std::vector<BatchMember>& ms, cudaStream_t s, long long* 
       if (e != cudaSuccess) return e;
     }
     if (fresh.empty()) return cudaSuccess;
-    if (!cache) return launch_merged(fresh, s, launches);
+    if (!cache) return launch_merged(fresh, s, launches, persist);
     cache->entries.push_back({key, 0, std::move(fresh), nullptr, 0});
     ent = &cache->entries.back();
   }
   ent->uses += 1;
   if (MGDG_BATCH_CAPTURE_AFTER > 0 && ent->uses >= MGDG_BATCH_CAPTURE_AFTER) {
-    const cudaError_t e = capture_merged(cache, ent->seqs, &ent->nodes, &ent->exec);
+    const cudaError_t e = capture_merged(cache, ent->seqs, &ent->nodes, &ent->exec, persist);
     if (e != cudaSuccess) return e;
     *launches += ent->nodes;
     return cudaGraphLaunch(ent->exec, s);
   }
-  return launch_merged(ent->seqs, s, launches);
+  return launch_merged(ent->seqs, s, launches, persist);
 }
 
 // Host copies of scalar slot `slot` of every active member (one gather
@@ -1045,6 +1046,7 @@ void mg_default_opts(mg_opts* o) {
   o->weight_delta = MG_DELTA_DEFAULT;
   o->autotune = 0;
   o->fdm_operands = 0;
+  o->persistent = 0;
 }
 
 mg_status mg_setup(double lx, double ly, double lz, int nx, int ny, int nz, int P, double penalty, int overlap,
@@ -1063,6 +1065,7 @@ mg_status mg_setup(double lx, double ly, double lz, int nx, int ny, int nz, int 
   if (o.outer_df64 < 0 || o.outer_df64 > 2) return MG_EINVAL;
   if (o.autotune < 0 || o.autotune > 1) return MG_EINVAL;
   if (o.fdm_operands < 0 || o.fdm_operands > 2) return MG_EINVAL;
+  if (o.persistent < 0 || o.persistent > 2) return MG_EINVAL;
   if (o.weight_profile < MG_WEIGHT_QUINTIC || o.weight_profile > MG_WEIGHT_QUINTIC_NORMALISED) return MG_EINVAL;
   if (o.weight_delta < MG_DELTA_DEFAULT || o.weight_delta > MG_DELTA_STRIP) return MG_EINVAL;
   if (o.overlap_mode == MG_OVERLAP_LAYERS && o.weight_delta == MG_DELTA_STRIP) return MG_EINVAL;

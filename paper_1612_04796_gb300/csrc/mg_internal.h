@@ -63,6 +63,29 @@ __global__ void __launch_bounds__(LB) k_grouped(const __grid_constant__ Grouped<
   cuda::std::apply([&](const Ps&... ps) { Body(bi, ps...); }, g.a[r]);
 }
 
+// Persistent form of the grouped twin: at most as many blocks as the SMs
+// hold at once, each looping over the launch's virtual blocks (the problem
+// ranges of k_grouped, in increasing order), with a block barrier between two
+// virtual blocks because the bodies reuse their shared memory.  Every virtual
+// block does the work of the same block of k_grouped.  (No body returns
+// before a barrier of its own, so every thread reaches the loop's barrier.)
+template <int LB, auto Body, typename... Ps>
+__global__ void __launch_bounds__(LB) k_grouped_p(const __grid_constant__ Grouped<cuda::std::tuple<Ps...>> g) {
+  pdl_entry();
+  const int total = g.start[g.count];
+  int r = 0;
+  for (int vb = (int)blockIdx.x; vb < total; vb += (int)gridDim.x) {
+    while (r + 1 < g.count && vb >= g.start[r + 1]) ++r;
+    const BlockIdx bi{vb - g.start[r], g.start[r + 1] - g.start[r]};
+    cuda::std::apply([&](const Ps&... ps) { Body(bi, ps...); }, g.a[r]);
+    __syncthreads();
+  }
+}
+
+// Persistent grouped launches (mg_opts.persistent): 0 = where the launch has
+// more blocks than the GPU holds at once, 1 = always, 2 = never.
+enum PersistMode : int { kPersistAuto = 0, kPersistAlways = 1, kPersistNever = 2 };
+
 // One recorded launch: the plain kernel (its identity), the launch shape, its
 // parameters packed as cuda::std::tuple<kernel parameter types...>, how to
 // replay it alone and (if the kernel has a body) how to launch the grouped
@@ -73,7 +96,7 @@ struct LaunchRec {
   size_t smem = 0;
   std::vector<unsigned char> args;
   cudaError_t (*plain)(const LaunchRec&, cudaStream_t) = nullptr;
-  cudaError_t (*grouped)(const LaunchRec* const*, int, cudaStream_t) = nullptr;
+  cudaError_t (*grouped)(const LaunchRec* const*, int, cudaStream_t, int persist) = nullptr;
 };
 
 // While a host thread has a recorder installed, launch_pdl appends to it
@@ -118,9 +141,20 @@ cudaError_t replay_plain(const LaunchRec& r, cudaStream_t s) {
 
 // Launch the grouped twin of Body for n problems: parameter sets a[i] (each
 // a cuda::std::tuple<KArgs...>) with grid[i] blocks each.
+// Allow `kernel` `smem` bytes of dynamic shared memory (once per kernel and size).
+inline cudaError_t allow_smem(const void* kernel, size_t smem, std::atomic<size_t>& smem_set) {
+  if (smem <= smem_set.load()) return cudaSuccess;
+  const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  size_t cur = smem_set.load();
+  while (cur < smem && !smem_set.compare_exchange_weak(cur, smem)) {
+  }
+  return cudaSuccess;
+}
+
 template <int LB, auto Body, typename... KArgs>
-cudaError_t launch_twin(const void* const* a, const unsigned* grid, int n, dim3 block, size_t smem,
-                        cudaStream_t s) {
+cudaError_t launch_twin(const void* const* a, const unsigned* grid, int n, dim3 block, size_t smem, cudaStream_t s,
+                        int persist = kPersistAuto) {
   using Tup = cuda::std::tuple<KArgs...>;
   Grouped<Tup> g;
   g.count = n;
@@ -129,28 +163,46 @@ cudaError_t launch_twin(const void* const* a, const unsigned* grid, int n, dim3 
     memcpy((void*)&g.a[i], a[i], sizeof(Tup));
     g.start[i + 1] = g.start[i] + (int)grid[i];
   }
+  const int total = g.start[n];
+  void* ptrs[1] = {(void*)&g};
+  if (persist != kPersistNever) {
+    auto* ptwin = k_grouped_p<LB, Body, KArgs...>;
+    static std::atomic<size_t> psmem_set{48 * 1024};
+    cudaError_t e = allow_smem((const void*)ptwin, smem, psmem_set);
+    if (e != cudaSuccess) return e;
+    // resident blocks per SM at this block size and shared memory (the largest
+    // size asked for so far; a block count for fewer bytes is a lower bound)
+    static std::atomic<long long> occ_key{-1};
+    static std::atomic<int> occ_val{0};
+    const long long key = (long long)block.x * (1LL << 32) + (long long)smem;
+    int per_sm = occ_key.load() == key ? occ_val.load() : 0;
+    if (per_sm == 0) {
+      if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ptwin, (int)block.x, smem)) != cudaSuccess)
+        return e;
+      per_sm = per_sm > 0 ? per_sm : 1;
+      occ_val.store(per_sm);
+      occ_key.store(key);
+    }
+    const int resident = 152 * per_sm;
+    if (persist == kPersistAlways || total > resident)
+      return launch_pdl_now((const void*)ptwin, dim3(total < resident ? total : resident), block, smem, s, ptrs);
+  }
   auto* twin = k_grouped<LB, Body, KArgs...>;
   static std::atomic<size_t> smem_set{48 * 1024};  // dynamic shared memory the twin is allowed so far
-  if (smem > smem_set.load()) {
-    const cudaError_t e = cudaFuncSetAttribute(twin, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    size_t cur = smem_set.load();
-    while (cur < smem && !smem_set.compare_exchange_weak(cur, smem)) {
-    }
-  }
-  void* ptrs[1] = {(void*)&g};
-  return launch_pdl_now((const void*)twin, dim3(g.start[n]), block, smem, s, ptrs);
+  const cudaError_t e = allow_smem((const void*)twin, smem, smem_set);
+  if (e != cudaSuccess) return e;
+  return launch_pdl_now((const void*)twin, dim3(total), block, smem, s, ptrs);
 }
 
 template <int LB, auto Body, typename... KArgs>
-cudaError_t launch_grouped(const LaunchRec* const* r, int n, cudaStream_t s) {
+cudaError_t launch_grouped(const LaunchRec* const* r, int n, cudaStream_t s, int persist) {
   const void* a[kMaxBatch];
   unsigned grid[kMaxBatch];
   for (int i = 0; i < n; ++i) {
     a[i] = r[i]->args.data();
     grid[i] = r[i]->grid.x;
   }
-  return launch_twin<LB, Body, KArgs...>(a, grid, n, r[0]->block, r[0]->smem, s);
+  return launch_twin<LB, Body, KArgs...>(a, grid, n, r[0]->block, r[0]->smem, s, persist);
 }
 
 // Launch `kernel` with programmatic dependent launch, or record it while a
@@ -331,7 +383,8 @@ enum ProfKind : int { kProfFdm = 0, kProfScatter, kProfSipg, kProfRestrict, kPro
 // ---- batched execution (batch.cu) ----
 // Launch the recorded sequences of several problems on stream s, merged into
 // grouped launches; *launches += the number of launches made.
-cudaError_t launch_merged(const std::vector<LaunchRecorder>& seqs, cudaStream_t s, long long* launches);
+cudaError_t launch_merged(const std::vector<LaunchRecorder>& seqs, cudaStream_t s, long long* launches,
+                          int persist);
 // out[i] = *src[i] (device scalars of up to kMaxBatch problems), one launch.
 cudaError_t launch_gather_scalars(const double* const* src, int n, double* out, cudaStream_t s);
 

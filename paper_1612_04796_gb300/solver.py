@@ -37,7 +37,7 @@ class MGSolver:
     def __init__(self, lengths, counts, P, penalty=2.0, overlap=1, precision="fp64", overlap_mode="layers",
                  overlap_frac=0.08, weight_profile="quintic", ns_pre=1, ns_post=1, ns_growth=1, device="cuda",
                  stream=None, tensor_cores=False, outer_df64=False, weight_delta="default", autotune=False,
-                 fdm_bf16=False, fdm_operands="fp32"):
+                 fdm_bf16=False, fdm_operands="fp32", persistent="auto"):
         self.lib = load_library()
         self.device = torch.device(device)
         if self.device.type == "cuda" and self.device.index is None:
@@ -51,6 +51,7 @@ class MGSolver:
         opts.autotune = 1 if autotune else 0
         # operand precision study of the FP32 smoother (fdm_bf16=True is fdm_operands="bf16")
         opts.fdm_operands = FDM_OPERANDS["bf16" if fdm_bf16 else fdm_operands]
+        opts.persistent = {"auto": 0, "always": 1, "never": 2}[persistent]  # grouped launches of solve_batch
         opts.ns_pre, opts.ns_post, opts.ns_growth = int(ns_pre), int(ns_post), int(ns_growth)
         opts.precision = PRECISION[precision]
         opts.fdm_tensor_cores = {False: 0, True: 1, "auto": 2}[tensor_cores]

@@ -116,3 +116,29 @@ def test_fp64_batch_takes_one_launch_per_sweep(mg):
     assert batched < 0.5 * single, (batched, single)
     for s in solvers:
         s.close()
+
+
+@pytest.mark.parametrize("precision,outer_df64", [("mixed", "all"), ("fp64", False)])
+def test_persistent_grouped_launches(mg, precision, outer_df64):
+    """mg_opts.persistent: every grouped launch as one wave of blocks looping
+    over the problems' blocks (always), or never.  Every virtual block does
+    the work of the same block of the plain grouped launch, so the batch gives
+    the same iterations and the same bits either way; a persistent launch of
+    several waves' worth of blocks is the default (auto) and agrees as well."""
+    import torch
+    res = {}
+    for mode in ("always", "never", "auto"):
+        solvers, rhs = [], []
+        for i, (L, n) in enumerate(SHAPES):
+            s = mg.MGSolver(L, n, 8, precision=precision, outer_df64=outer_df64, persistent=mode)
+            solvers.append(s)
+            rhs.append(s.rhs(torch.tensor(inputs.gaussian(s.num_dofs(), 400 + i), device="cuda")))
+        us, its, rels, sts = mg.solve_batch(solvers, rhs, tol=1e-10, maxit=200)
+        assert all(st == 0 for st in sts) and all(r <= 1e-10 for r in rels)
+        res[mode] = ([u.clone() for u in us], list(its))
+        for s in solvers:
+            s.close()
+    for mode in ("never", "auto"):
+        assert res[mode][1] == res["always"][1], (mode, res[mode][1], res["always"][1])
+        for a, b in zip(res[mode][0], res["always"][0]):
+            assert torch.equal(a, b), mode
