@@ -10,11 +10,14 @@
 // of f_0 onto the range of A_0, and u_0 has zero Euclidean mean -- it is the
 // minimum-norm solution A_0^+ f_0 without separate mean projections (they
 // would change u_0 only at rounding level).  This is a direct solve: no
-// iteration, no tolerance; six launches, one per axis pass.
+// iteration, no tolerance; three launches through shared memory on small
+// coarse grids, else six, one per axis pass.
 //
 // Vectors of level 0 are element-blocked with 2 nodes per direction; the
 // global 1D index along x is 2 ex + i (the same for y, z).  Intermediates are
 // stored in lexicographic order gx + Ngx (gy + Ngy gz).
+#include <atomic>
+
 #include "mg_internal.h"
 
 namespace mgdg {
@@ -98,6 +101,165 @@ __global__ void k_coarse_axis(const TI* __restrict__ in, TO* __restrict__ out, c
                            lz, nx0, ny0, nz0);
 }
 
+// ---- the same solve in three launches, through shared memory ----
+//
+// The contractions along x and y couple only values of one z-plane, those
+// along z only values of one y-slab, so where a plane and a slab fit shared
+// memory the six passes become three kernels, each block holding a plane or
+// a slab: x and y forward per z-plane; z forward, the pseudo-inverse of the
+// eigenvalue sums and z backward per y-slab; y and x backward per z-plane.
+// Each output is one sequential sum over the contracted index.
+struct CoarseFused {
+  const double* Q[3];
+  const double* lam[3];
+  CoarseDims d;
+  int null_mode[3];
+  const double* scal;
+  int mean_slot;
+};
+
+template <typename TI>
+__device__ __forceinline__ void coarse_xy_body(BlockIdx bi_, const TI* __restrict__ in, double* __restrict__ out,
+                                               CoarseFused a) {
+  extern __shared__ __align__(16) double cf_sm[];
+  const int Nx = a.d.Ng[0], Ny = a.d.Ng[1], Nz = a.d.Ng[2], plane = Nx * Ny;
+  double* P = cf_sm;
+  double* T = cf_sm + plane;
+  const double shift =
+      a.mean_slot >= 0 ? a.scal[a.mean_slot] / ((double)plane * Nz) : 0.0;
+  const double* __restrict__ Qx = a.Q[0];
+  const double* __restrict__ Qy = a.Q[1];
+  for (int gz = bi_.b; gz < Nz; gz += bi_.g) {
+    for (int i = threadIdx.x; i < plane; i += blockDim.x) {
+      const int gx = i % Nx, gy = i / Nx;
+      P[i] = (double)in[eb_index(gx, gy, gz, a.d)] - shift;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < plane; i += blockDim.x) {  // x forward
+      const int p = i % Nx, gy = i / Nx;
+      double acc = 0.0;
+      for (int t = 0; t < Nx; ++t) acc += Qx[t * Nx + p] * P[t + Nx * gy];
+      T[i] = acc;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < plane; i += blockDim.x) {  // y forward
+      const int p = i % Nx, q = i / Nx;
+      double acc = 0.0;
+      for (int t = 0; t < Ny; ++t) acc += Qy[t * Ny + q] * T[p + Nx * t];
+      out[i + (int64_t)plane * gz] = acc;
+    }
+    __syncthreads();
+  }
+}
+
+__device__ __forceinline__ void coarse_z_body(BlockIdx bi_, double* __restrict__ A, CoarseFused a) {
+  extern __shared__ __align__(16) double cf_sm[];
+  const int Nx = a.d.Ng[0], Ny = a.d.Ng[1], Nz = a.d.Ng[2], slab = Nx * Nz;
+  double* S = cf_sm;
+  double* V = cf_sm + slab;
+  const double* __restrict__ Qz = a.Q[2];
+  for (int gy = bi_.b; gy < Ny; gy += bi_.g) {
+    for (int i = threadIdx.x; i < slab; i += blockDim.x) {
+      const int gx = i % Nx, gz = i / Nx;
+      S[i] = A[gx + (int64_t)Nx * (gy + (int64_t)Ny * gz)];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < slab; i += blockDim.x) {  // z forward, pseudo-inverse
+      const int gx = i % Nx, r = i / Nx;
+      double acc = 0.0;
+      for (int t = 0; t < Nz; ++t) acc += Qz[t * Nz + r] * S[gx + Nx * t];
+      if (gx == a.null_mode[0] && gy == a.null_mode[1] && r == a.null_mode[2]) acc = 0.0;
+      else acc /= (a.lam[0][gx] + a.lam[1][gy] + a.lam[2][r]);
+      V[i] = acc;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < slab; i += blockDim.x) {  // z backward
+      const int gx = i % Nx, gz = i / Nx;
+      double acc = 0.0;
+      for (int t = 0; t < Nz; ++t) acc += Qz[gz * Nz + t] * V[gx + Nx * t];
+      A[gx + (int64_t)Nx * (gy + (int64_t)Ny * gz)] = acc;
+    }
+    __syncthreads();
+  }
+}
+
+template <typename TO>
+__device__ __forceinline__ void coarse_yx_body(BlockIdx bi_, const double* __restrict__ A, TO* __restrict__ out,
+                                               CoarseFused a) {
+  extern __shared__ __align__(16) double cf_sm[];
+  const int Nx = a.d.Ng[0], Ny = a.d.Ng[1], Nz = a.d.Ng[2], plane = Nx * Ny;
+  double* P = cf_sm;
+  double* T = cf_sm + plane;
+  const double* __restrict__ Qx = a.Q[0];
+  const double* __restrict__ Qy = a.Q[1];
+  for (int gz = bi_.b; gz < Nz; gz += bi_.g) {
+    for (int i = threadIdx.x; i < plane; i += blockDim.x) P[i] = A[i + (int64_t)plane * gz];
+    __syncthreads();
+    for (int i = threadIdx.x; i < plane; i += blockDim.x) {  // y backward
+      const int gx = i % Nx, gy = i / Nx;
+      double acc = 0.0;
+      for (int t = 0; t < Ny; ++t) acc += Qy[gy * Ny + t] * P[gx + Nx * t];
+      T[i] = acc;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < plane; i += blockDim.x) {  // x backward, element-blocked result
+      const int gx = i % Nx, gy = i / Nx;
+      double acc = 0.0;
+      for (int t = 0; t < Nx; ++t) acc += Qx[gx * Nx + t] * T[t + Nx * gy];
+      out[eb_index(gx, gy, gz, a.d)] = (TO)acc;
+    }
+    __syncthreads();
+  }
+}
+
+template <typename TI>
+__global__ void __launch_bounds__(256) k_coarse_xy(const TI* __restrict__ in, double* __restrict__ out,
+                                                   const __grid_constant__ CoarseFused a) {
+  pdl_entry();
+  coarse_xy_body<TI>(plain_block(), in, out, a);
+}
+
+__global__ void __launch_bounds__(256) k_coarse_z(double* __restrict__ A, const __grid_constant__ CoarseFused a) {
+  pdl_entry();
+  coarse_z_body(plain_block(), A, a);
+}
+
+template <typename TO>
+__global__ void __launch_bounds__(256) k_coarse_yx(const double* __restrict__ A, TO* __restrict__ out,
+                                                   const __grid_constant__ CoarseFused a) {
+  pdl_entry();
+  coarse_yx_body<TO>(plain_block(), A, out, a);
+}
+
+// Shared memory of the three kernels (two planes or two slabs of FP64),
+// rounded up to 16 KB so that batched problems of similar coarse grids merge
+// their launches (records merge only at equal shared memory), or 0 where the
+// six-pass form is the faster: grids of more than 8,192 coarse DOFs (one
+// block per plane gives too few blocks there: 1.10 vs 0.63 ms per 16^3
+// FP64 solve), or planes that do not fit.  On small grids the six passes are
+// bound by their launches (16 small problems batched: 22.7 vs 23.9 ms).
+inline size_t coarse_fused_smem(const CoarseDims& d) {
+  if ((int64_t)d.Ng[0] * d.Ng[1] * d.Ng[2] > 8192) return 0;
+  const size_t plane = (size_t)d.Ng[0] * d.Ng[1], slab = (size_t)d.Ng[0] * d.Ng[2];
+  const size_t bytes = 2 * sizeof(double) * (plane > slab ? plane : slab);
+  const size_t step = 16 * 1024, rounded = (bytes + step - 1) / step * step;
+  return rounded <= 96 * 1024 ? rounded : 0;
+}
+
+template <typename TI, typename TO>
+cudaError_t coarse_fused(const CoarseFused& a, const TI* f0, double* A, TO* u0, size_t smem, cudaStream_t s) {
+  static std::atomic<size_t> set_xy{48 * 1024}, set_z{48 * 1024}, set_yx{48 * 1024};
+  cudaError_t e;
+  if ((e = allow_smem((const void*)k_coarse_xy<TI>, smem, set_xy)) != cudaSuccess) return e;
+  if ((e = allow_smem((const void*)k_coarse_z, smem, set_z)) != cudaSuccess) return e;
+  if ((e = allow_smem((const void*)k_coarse_yx<TO>, smem, set_yx)) != cudaSuccess) return e;
+  const int bz = a.d.Ng[2] < 152 * 8 ? a.d.Ng[2] : 152 * 8, by = a.d.Ng[1] < 152 * 8 ? a.d.Ng[1] : 152 * 8;
+  launch_pdl<&coarse_xy_body<TI>>(k_coarse_xy<TI>, bz, 256, smem, s, f0, A, a);
+  launch_pdl<&coarse_z_body>(k_coarse_z, by, 256, smem, s, A, a);
+  launch_pdl<&coarse_yx_body<TO>>(k_coarse_yx<TO>, bz, 256, smem, s, A, u0, a);
+  return cudaGetLastError();
+}
+
 // One axis pass (k_coarse_axis, or its grouped twin's body when Twin).
 template <bool Twin, typename TI, typename TO>
 void axis_pass(int blocks, cudaStream_t s, const TI* in, TO* out, const double* Q, const CoarseDims& d, int axis,
@@ -143,6 +305,20 @@ cudaError_t coarse_solve_t(const mg_ctx* c, const TI* f0, TO* u0) {
   const double* tab = c->ws.tab64;
   const double* Q[3] = {tab + lv.t[0].Q, tab + lv.t[1].Q, tab + lv.t[2].Q};
   const double* lam[3] = {tab + lv.t[0].qlam, tab + lv.t[1].qlam, tab + lv.t[2].qlam};
+  const size_t smem = coarse_fused_smem(d);
+  if (smem > 0) {
+    CoarseFused a;
+    for (int k = 0; k < 3; ++k) {
+      a.Q[k] = Q[k];
+      a.lam[k] = lam[k];
+      a.null_mode[k] = c->coarse_null[k];
+    }
+    a.d = d;
+    a.scal = c->ws.scal;
+    a.mean_slot = -1;
+    c->nlaunch += 3;
+    return coarse_fused<TI, TO>(a, f0, c->ws.coarse_a, u0, smem, c->stream);
+  }
   c->nlaunch += 6;
   return coarse_passes<TI, TO>(Q, lam, d, c->coarse_null, f0, c->ws.coarse_a, c->ws.coarse_b, u0, c->ws.scal, -1,
                                c->stream);
