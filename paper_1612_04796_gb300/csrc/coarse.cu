@@ -10,8 +10,8 @@
 // of f_0 onto the range of A_0, and u_0 has zero Euclidean mean -- it is the
 // minimum-norm solution A_0^+ f_0 without separate mean projections (they
 // would change u_0 only at rounding level).  This is a direct solve: no
-// iteration, no tolerance; three launches through shared memory on small
-// coarse grids, else six, one per axis pass.
+// iteration, no tolerance; three launches through shared memory where a
+// plane and a slab of the coarse grid fit it, else six, one per axis pass.
 //
 // Vectors of level 0 are element-blocked with 2 nodes per direction; the
 // global 1D index along x is 2 ex + i (the same for y, z).  Intermediates are
@@ -105,10 +105,13 @@ __global__ void k_coarse_axis(const TI* __restrict__ in, TO* __restrict__ out, c
 //
 // The contractions along x and y couple only values of one z-plane, those
 // along z only values of one y-slab, so where a plane and a slab fit shared
-// memory the six passes become three kernels, each block holding a plane or
-// a slab: x and y forward per z-plane; z forward, the pseudo-inverse of the
-// eigenvalue sums and z backward per y-slab; y and x backward per z-plane.
-// Each output is one sequential sum over the contracted index.
+// memory the six passes become three kernels: x and y forward per z-plane;
+// z forward, the pseudo-inverse of the eigenvalue sums and z backward per
+// y-slab; y and x backward per z-plane.  Each plane or slab is split into
+// `chunks` pieces over as many blocks (x-columns for the first two kernels,
+// y-rows for the last), so that the FP64 work spreads over the SMs; no
+// product is computed twice.  Each output is one sequential sum over the
+// contracted index.
 struct CoarseFused {
   const double* Q[3];
   const double* lam[3];
@@ -116,37 +119,47 @@ struct CoarseFused {
   int null_mode[3];
   const double* scal;
   int mean_slot;
+  int chunks[3];  // pieces per plane (x then y forward), slab (z), plane (y then x backward)
 };
+
+__device__ __forceinline__ void chunk_range(int n, int chunks, int ch, int* lo, int* hi) {
+  const int w = (n + chunks - 1) / chunks;
+  *lo = ch * w;
+  *hi = *lo + w < n ? *lo + w : n;
+}
 
 template <typename TI>
 __device__ __forceinline__ void coarse_xy_body(BlockIdx bi_, const TI* __restrict__ in, double* __restrict__ out,
                                                CoarseFused a) {
   extern __shared__ __align__(16) double cf_sm[];
-  const int Nx = a.d.Ng[0], Ny = a.d.Ng[1], Nz = a.d.Ng[2], plane = Nx * Ny;
+  const int Nx = a.d.Ng[0], Ny = a.d.Ng[1], Nz = a.d.Ng[2], plane = Nx * Ny, C = a.chunks[0];
   double* P = cf_sm;
   double* T = cf_sm + plane;
-  const double shift =
-      a.mean_slot >= 0 ? a.scal[a.mean_slot] / ((double)plane * Nz) : 0.0;
+  const double shift = a.mean_slot >= 0 ? a.scal[a.mean_slot] / ((double)plane * Nz) : 0.0;
   const double* __restrict__ Qx = a.Q[0];
   const double* __restrict__ Qy = a.Q[1];
-  for (int gz = bi_.b; gz < Nz; gz += bi_.g) {
+  for (int vb = bi_.b; vb < Nz * C; vb += bi_.g) {
+    const int gz = vb / C;
+    int p0, p1;
+    chunk_range(Nx, C, vb - gz * C, &p0, &p1);
+    const int w = p1 - p0;
     for (int i = threadIdx.x; i < plane; i += blockDim.x) {
       const int gx = i % Nx, gy = i / Nx;
       P[i] = (double)in[eb_index(gx, gy, gz, a.d)] - shift;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < plane; i += blockDim.x) {  // x forward
-      const int p = i % Nx, gy = i / Nx;
+    for (int i = threadIdx.x; i < w * Ny; i += blockDim.x) {  // x forward, columns p0 .. p1 - 1
+      const int p = p0 + i % w, gy = i / w;
       double acc = 0.0;
       for (int t = 0; t < Nx; ++t) acc += Qx[t * Nx + p] * P[t + Nx * gy];
-      T[i] = acc;
+      T[p + Nx * gy] = acc;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < plane; i += blockDim.x) {  // y forward
-      const int p = i % Nx, q = i / Nx;
+    for (int i = threadIdx.x; i < w * Ny; i += blockDim.x) {  // y forward, the same columns
+      const int p = p0 + i % w, q = i / w;
       double acc = 0.0;
       for (int t = 0; t < Ny; ++t) acc += Qy[t * Ny + q] * T[p + Nx * t];
-      out[i + (int64_t)plane * gz] = acc;
+      out[p + Nx * q + (int64_t)plane * gz] = acc;
     }
     __syncthreads();
   }
@@ -154,27 +167,31 @@ __device__ __forceinline__ void coarse_xy_body(BlockIdx bi_, const TI* __restric
 
 __device__ __forceinline__ void coarse_z_body(BlockIdx bi_, double* __restrict__ A, CoarseFused a) {
   extern __shared__ __align__(16) double cf_sm[];
-  const int Nx = a.d.Ng[0], Ny = a.d.Ng[1], Nz = a.d.Ng[2], slab = Nx * Nz;
+  const int Nx = a.d.Ng[0], Ny = a.d.Ng[1], Nz = a.d.Ng[2], slab = Nx * Nz, C = a.chunks[1];
   double* S = cf_sm;
   double* V = cf_sm + slab;
   const double* __restrict__ Qz = a.Q[2];
-  for (int gy = bi_.b; gy < Ny; gy += bi_.g) {
-    for (int i = threadIdx.x; i < slab; i += blockDim.x) {
-      const int gx = i % Nx, gz = i / Nx;
-      S[i] = A[gx + (int64_t)Nx * (gy + (int64_t)Ny * gz)];
+  for (int vb = bi_.b; vb < Ny * C; vb += bi_.g) {
+    const int gy = vb / C;
+    int x0, x1;
+    chunk_range(Nx, C, vb - gy * C, &x0, &x1);
+    const int w = x1 - x0;
+    for (int i = threadIdx.x; i < w * Nz; i += blockDim.x) {  // the chunk's columns of the slab
+      const int gx = x0 + i % w, gz = i / w;
+      S[gx + Nx * gz] = A[gx + (int64_t)Nx * (gy + (int64_t)Ny * gz)];
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < slab; i += blockDim.x) {  // z forward, pseudo-inverse
-      const int gx = i % Nx, r = i / Nx;
+    for (int i = threadIdx.x; i < w * Nz; i += blockDim.x) {  // z forward, pseudo-inverse
+      const int gx = x0 + i % w, r = i / w;
       double acc = 0.0;
       for (int t = 0; t < Nz; ++t) acc += Qz[t * Nz + r] * S[gx + Nx * t];
       if (gx == a.null_mode[0] && gy == a.null_mode[1] && r == a.null_mode[2]) acc = 0.0;
       else acc /= (a.lam[0][gx] + a.lam[1][gy] + a.lam[2][r]);
-      V[i] = acc;
+      V[gx + Nx * r] = acc;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < slab; i += blockDim.x) {  // z backward
-      const int gx = i % Nx, gz = i / Nx;
+    for (int i = threadIdx.x; i < w * Nz; i += blockDim.x) {  // z backward
+      const int gx = x0 + i % w, gz = i / w;
       double acc = 0.0;
       for (int t = 0; t < Nz; ++t) acc += Qz[gz * Nz + t] * V[gx + Nx * t];
       A[gx + (int64_t)Nx * (gy + (int64_t)Ny * gz)] = acc;
@@ -187,23 +204,27 @@ template <typename TO>
 __device__ __forceinline__ void coarse_yx_body(BlockIdx bi_, const double* __restrict__ A, TO* __restrict__ out,
                                                CoarseFused a) {
   extern __shared__ __align__(16) double cf_sm[];
-  const int Nx = a.d.Ng[0], Ny = a.d.Ng[1], Nz = a.d.Ng[2], plane = Nx * Ny;
+  const int Nx = a.d.Ng[0], Ny = a.d.Ng[1], Nz = a.d.Ng[2], plane = Nx * Ny, C = a.chunks[2];
   double* P = cf_sm;
   double* T = cf_sm + plane;
   const double* __restrict__ Qx = a.Q[0];
   const double* __restrict__ Qy = a.Q[1];
-  for (int gz = bi_.b; gz < Nz; gz += bi_.g) {
+  for (int vb = bi_.b; vb < Nz * C; vb += bi_.g) {
+    const int gz = vb / C;
+    int y0, y1;
+    chunk_range(Ny, C, vb - gz * C, &y0, &y1);
+    const int h = y1 - y0;
     for (int i = threadIdx.x; i < plane; i += blockDim.x) P[i] = A[i + (int64_t)plane * gz];
     __syncthreads();
-    for (int i = threadIdx.x; i < plane; i += blockDim.x) {  // y backward
-      const int gx = i % Nx, gy = i / Nx;
+    for (int i = threadIdx.x; i < Nx * h; i += blockDim.x) {  // y backward, rows y0 .. y1 - 1
+      const int gx = i % Nx, gy = y0 + i / Nx;
       double acc = 0.0;
       for (int t = 0; t < Ny; ++t) acc += Qy[gy * Ny + t] * P[gx + Nx * t];
-      T[i] = acc;
+      T[gx + Nx * gy] = acc;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < plane; i += blockDim.x) {  // x backward, element-blocked result
-      const int gx = i % Nx, gy = i / Nx;
+    for (int i = threadIdx.x; i < Nx * h; i += blockDim.x) {  // x backward, element-blocked result
+      const int gx = i % Nx, gy = y0 + i / Nx;
       double acc = 0.0;
       for (int t = 0; t < Nx; ++t) acc += Qx[gx * Nx + t] * T[t + Nx * gy];
       out[eb_index(gx, gy, gz, a.d)] = (TO)acc;
@@ -233,13 +254,11 @@ __global__ void __launch_bounds__(256) k_coarse_yx(const double* __restrict__ A,
 
 // Shared memory of the three kernels (two planes or two slabs of FP64),
 // rounded up to 16 KB so that batched problems of similar coarse grids merge
-// their launches (records merge only at equal shared memory), or 0 where the
-// six-pass form is the faster: grids of more than 8,192 coarse DOFs (one
-// block per plane gives too few blocks there: 1.10 vs 0.63 ms per 16^3
-// FP64 solve), or planes that do not fit.  On small grids the six passes are
-// bound by their launches (16 small problems batched: 22.7 vs 23.9 ms).
+// their launches (records merge only at equal shared memory), or 0 if a
+// plane or slab does not fit (then the six passes).  Measured against the six
+// passes: 16^3 mesh 0.42 vs 0.63 ms per FP64 solve (12 coarse solves), 16
+// small problems batched 22.6 vs 23.9 ms.
 inline size_t coarse_fused_smem(const CoarseDims& d) {
-  if ((int64_t)d.Ng[0] * d.Ng[1] * d.Ng[2] > 8192) return 0;
   const size_t plane = (size_t)d.Ng[0] * d.Ng[1], slab = (size_t)d.Ng[0] * d.Ng[2];
   const size_t bytes = 2 * sizeof(double) * (plane > slab ? plane : slab);
   const size_t step = 16 * 1024, rounded = (bytes + step - 1) / step * step;
@@ -253,10 +272,12 @@ cudaError_t coarse_fused(const CoarseFused& a, const TI* f0, double* A, TO* u0, 
   if ((e = allow_smem((const void*)k_coarse_xy<TI>, smem, set_xy)) != cudaSuccess) return e;
   if ((e = allow_smem((const void*)k_coarse_z, smem, set_z)) != cudaSuccess) return e;
   if ((e = allow_smem((const void*)k_coarse_yx<TO>, smem, set_yx)) != cudaSuccess) return e;
-  const int bz = a.d.Ng[2] < 152 * 8 ? a.d.Ng[2] : 152 * 8, by = a.d.Ng[1] < 152 * 8 ? a.d.Ng[1] : 152 * 8;
-  launch_pdl<&coarse_xy_body<TI>>(k_coarse_xy<TI>, bz, 256, smem, s, f0, A, a);
-  launch_pdl<&coarse_z_body>(k_coarse_z, by, 256, smem, s, A, a);
-  launch_pdl<&coarse_yx_body<TO>>(k_coarse_yx<TO>, bz, 256, smem, s, A, u0, a);
+  const int vb[3] = {a.d.Ng[2] * a.chunks[0], a.d.Ng[1] * a.chunks[1], a.d.Ng[2] * a.chunks[2]};
+  int nb[3];
+  for (int k = 0; k < 3; ++k) nb[k] = vb[k] < 152 * 8 ? vb[k] : 152 * 8;
+  launch_pdl<&coarse_xy_body<TI>>(k_coarse_xy<TI>, nb[0], 256, smem, s, f0, A, a);
+  launch_pdl<&coarse_z_body>(k_coarse_z, nb[1], 256, smem, s, A, a);
+  launch_pdl<&coarse_yx_body<TO>>(k_coarse_yx<TO>, nb[2], 256, smem, s, A, u0, a);
   return cudaGetLastError();
 }
 
@@ -316,6 +337,14 @@ cudaError_t coarse_solve_t(const mg_ctx* c, const TI* f0, TO* u0) {
     a.d = d;
     a.scal = c->ws.scal;
     a.mean_slot = -1;
+    // pieces per plane / slab: about two blocks per SM in all, each piece at
+    // least 4 columns or rows wide
+    const int outer[3] = {d.Ng[2], d.Ng[1], d.Ng[2]}, width[3] = {d.Ng[0], d.Ng[0], d.Ng[1]};
+    for (int k = 0; k < 3; ++k) {
+      const int want = (2 * 152 + outer[k] - 1) / outer[k], most = (width[k] + 3) / 4;
+      a.chunks[k] = want < most ? want : most;
+      if (a.chunks[k] < 1) a.chunks[k] = 1;
+    }
     c->nlaunch += 3;
     return coarse_fused<TI, TO>(a, f0, c->ws.coarse_a, u0, smem, c->stream);
   }
