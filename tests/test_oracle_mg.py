@@ -6,6 +6,7 @@ import numpy as np
 import pytest
 import scipy.sparse.linalg as spl
 
+from oracle import multigrid
 from oracle.gll import gll_nodes
 from oracle.multigrid import (Hierarchy, convergence_rate, interpolation_matrix, solve_mg, solve_mgcg,
                               solve_pcg)
@@ -66,18 +67,38 @@ def test_pcg_with_identity_preconditioner_is_textbook_cg():
         np.testing.assert_allclose(x, xs, atol=1e-9 * np.abs(xs).max())
 
 
-def test_pcg_with_jacobi_preconditioner_is_textbook_pcg():
+def pcg_textbook_gaps(pcg):
+    """Eight steps of `pcg` (the oracle's inexact PCG, or a planted variant)
+    and of textbook PCG with the Jacobi preconditioner restricted to the
+    zero-mean subspace, P D^-1 P (P the mean projection), on which the
+    periodic operator is definite; returns (relative residual gap, relative
+    iterate gap, residual reduction of the textbook steps)."""
     mesh = Mesh((1, 1, 1), (3, 3, 3))
     A = assemble(mesh, 2)
     b = weak_rhs(mesh, 2, inputs.gaussian(A.shape[0], 2))
+    b = b - b.mean()
     d = A.diagonal()
-    x, _, _ = solve_pcg(A, b, lambda r: r / d, tol=0.0, maxit=8)
-    M = spl.LinearOperator(A.shape, matvec=lambda r: r / d)
+
+    def proj(v):
+        return v - v.mean()
+
+    x, _, _ = pcg(A, b, lambda r: proj(proj(r) / d), tol=0.0, maxit=8)
+    M = spl.LinearOperator(A.shape, matvec=lambda r: proj(proj(r) / d))
     xs, _ = spl.cg(A, b, rtol=0.0, atol=0.0, maxiter=8, M=M)
-    # the oracle projects r and z to zero mean; Jacobi does not preserve the
-    # mean, so compare the residuals instead of the iterates' constant part
     rx, rs = b - A @ x, b - A @ xs
-    assert np.linalg.norm(rx) == pytest.approx(np.linalg.norm(rs), rel=0.5)
+    return (np.linalg.norm(rx - rs) / np.linalg.norm(rs),
+            np.max(np.abs(proj(x) - proj(xs))) / np.max(np.abs(proj(xs))),
+            np.linalg.norm(rs) / np.linalg.norm(b))
+
+
+def test_pcg_with_jacobi_preconditioner_is_textbook_pcg():
+    """With a fixed symmetric positive definite preconditioner the inexact
+    (Golub-Ye) PCG of Section 3.2 takes the same steps as textbook PCG, so
+    both agree to rounding (a wrong coefficient or sign in the recurrences
+    fails: tests/test_oracle_mutations.py plants one)."""
+    gr, gx, red = pcg_textbook_gaps(multigrid.solve_pcg)
+    assert red < 0.5  # the eight steps did reduce the residual
+    assert gr <= 1e-9 and gx <= 1e-9, (gr, gx)
 
 
 def test_manufactured_solution_solve():

@@ -93,3 +93,19 @@ def test_wrong_max_overlap_normalisation_is_caught(monkeypatch, bad):
     monkeypatch.setattr(schwarz, "normalised_subdomain_1d", bad)
     with pytest.raises(AssertionError):
         tmax.test_partition_of_unity_max_overlap(4, 48, "quintic")
+
+
+def test_wrong_pcg_beta_sign_is_caught(monkeypatch):
+    """The inexact PCG's direction update with a flipped sign of beta (planted
+    in the oracle's code) no longer matches textbook PCG."""
+    import inspect
+
+    from oracle import multigrid
+    from test_oracle_mg import pcg_textbook_gaps
+    src = inspect.getsource(multigrid.solve_pcg)
+    assert "p = z_new + beta * p" in src
+    ns = dict(vars(multigrid))
+    exec(compile(src.replace("p = z_new + beta * p", "p = z_new - beta * p"), "<planted>", "exec"), ns)
+    monkeypatch.setattr(multigrid, "solve_pcg", ns["solve_pcg"])
+    gr, gx, _ = pcg_textbook_gaps(multigrid.solve_pcg)
+    assert gr > 1e-3 or gx > 1e-3, (gr, gx)
