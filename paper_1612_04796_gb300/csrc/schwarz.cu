@@ -411,9 +411,10 @@ __global__ void __launch_bounds__(256) k_scatter_e(const T* __restrict__ corr, T
       const int64_t z0 = cand[ge][2][k][0], z1 = cand[ge][2][k][1];
       const bool vx = x1 != x0, vy = y1 != y0, vz = z1 != z0;
       T sum = 0;
-      if constexpr (std::is_same<T, double>::value) {
-        // FP64: only the contributions that exist are loaded and added (about
-        // 1.8 per node at N_O = 1 instead of eight; the FP64 pipe bounds the
+      if constexpr (!std::is_same<T, float>::value) {
+        // FP64 and double-float: only the contributions that exist are loaded
+        // and added (about 1.8 per node at N_O = 1 instead of eight: the FP64
+        // pipe, or the dozen FP32 operations of a double-float add, bound the
         // masked form), in the same order
         sum += corr[x0 + y0 + z0];
         if (vx) sum += corr[x1 + y0 + z0];
@@ -430,8 +431,8 @@ __global__ void __launch_bounds__(256) k_scatter_e(const T* __restrict__ corr, T
           }
         }
       } else {
-        // FP32 and double-float: the eight loads issued together, the absent
-        // ones masked out of the sum
+        // FP32: the eight loads issued together, the absent ones masked out
+        // of the sum
         const bool v[3] = {vx, vy, vz};
         const int64_t ox[2] = {x0, x1}, oy[2] = {y0, y1}, oz[2] = {z0, z1};
         T val[8];

@@ -5,8 +5,8 @@
 // order-P_l GLL nodes (embedded interpolation).  Both are applied as three
 // one-axis contractions (sum factorisation), one output value per thread,
 // through the smoother's correction buffer as scratch (order 32), or in one
-// fused kernel per element with shared-memory intermediates and even/odd
-// products (orders 2..16).
+// fused kernel with shared-memory intermediates and even/odd products, a few
+// elements per block pass (orders 2..16).
 #include <type_traits>
 
 #include "mg_internal.h"
@@ -115,42 +115,53 @@ __device__ void cs_split(Get get, T* AE, T* AO) {
   }
 }
 
-// Fused prolongation u_f += (J (x) J (x) J) u_c, one element per block pass,
-// intermediates in shared memory.
+// Fused prolongation u_f += (J (x) J (x) J) u_c, TE elements per block pass
+// (enough for the z pass to occupy the block's 256 threads), intermediates in
+// shared memory.
+template <int NF>
+struct TrShape {
+  static constexpr int te = 256 / (NF * NF) > 0 ? 256 / (NF * NF) : 1;  // elements per block pass
+};
+
 template <typename T, int NF, int NC>
 __device__ __forceinline__ void prolong_fused_body(BlockIdx bi_, const T* __restrict__ uc, T* __restrict__ uf,
                                                    const T* __restrict__ J, int64_t Ne) {
-  constexpr int nei = (NC + 1) / 2, neo = (NF + 1) / 2;
+  constexpr int nei = (NC + 1) / 2, neo = (NF + 1) / 2, TE = TrShape<NF>::te;
+  constexpr int nB = NF * NC * NC, nC = NF * NF * NC;
   __shared__ T sE[neo * nei], sO[(NF / 2) * (NC / 2) + 1];
-  __shared__ T sB[NF * NC * NC], sC[NF * NF * NC];
+  __shared__ T sB[TE * nB], sC[TE * nC];
   cs_split<T, NF, NC>([&](int o, int t) { return J[o * NC + t]; }, sE, sO);
   __syncthreads();
-  for (int64_t e = bi_.b; e < Ne; e += bi_.g) {
-    const T* x0 = uc + e * (NC * NC * NC);
-    for (int ln = threadIdx.x; ln < NC * NC; ln += blockDim.x) {  // x: (j,k) lines
+  for (int64_t e0 = (int64_t)bi_.b * TE; e0 < Ne; e0 += (int64_t)bi_.g * TE) {
+    const int cnt = (int)(Ne - e0 < TE ? Ne - e0 : TE);
+    for (int w = threadIdx.x; w < cnt * NC * NC; w += blockDim.x) {  // x: (j,k) lines
+      const int g = w / (NC * NC), ln = w - g * (NC * NC);
+      const T* x0 = uc + (e0 + g) * (NC * NC * NC);
       T x[NC], y[NF];
 #pragma unroll
       for (int t = 0; t < NC; ++t) x[t] = x0[t + NC * ln];
       cs_matvec<T, NF, NC>(sE, sO, x, y);
 #pragma unroll
-      for (int a = 0; a < NF; ++a) sB[a + NF * ln] = y[a];
+      for (int a = 0; a < NF; ++a) sB[g * nB + a + NF * ln] = y[a];
     }
     __syncthreads();
-    for (int ln = threadIdx.x; ln < NF * NC; ln += blockDim.x) {  // y: (a,k) lines
+    for (int w = threadIdx.x; w < cnt * NF * NC; w += blockDim.x) {  // y: (a,k) lines
+      const int g = w / (NF * NC), ln = w - g * (NF * NC);
       const int a = ln % NF, k = ln / NF;
       T x[NC], y[NF];
 #pragma unroll
-      for (int t = 0; t < NC; ++t) x[t] = sB[a + NF * (t + NC * k)];
+      for (int t = 0; t < NC; ++t) x[t] = sB[g * nB + a + NF * (t + NC * k)];
       cs_matvec<T, NF, NC>(sE, sO, x, y);
 #pragma unroll
-      for (int b = 0; b < NF; ++b) sC[a + NF * (b + NF * k)] = y[b];
+      for (int b = 0; b < NF; ++b) sC[g * nC + a + NF * (b + NF * k)] = y[b];
     }
     __syncthreads();
-    T* out = uf + e * (NF * NF * NF);
-    for (int ln = threadIdx.x; ln < NF * NF; ln += blockDim.x) {  // z: (a,b) lines, accumulate
+    for (int w = threadIdx.x; w < cnt * NF * NF; w += blockDim.x) {  // z: (a,b) lines, accumulate
+      const int g = w / (NF * NF), ln = w - g * (NF * NF);
+      T* out = uf + (e0 + g) * (NF * NF * NF);
       T x[NC], y[NF];
 #pragma unroll
-      for (int t = 0; t < NC; ++t) x[t] = sC[ln + NF * NF * t];
+      for (int t = 0; t < NC; ++t) x[t] = sC[g * nC + ln + NF * NF * t];
       cs_matvec<T, NF, NC>(sE, sO, x, y);
 #pragma unroll
       for (int c = 0; c < NF; ++c) out[ln + NF * NF * c] += y[c];
@@ -160,47 +171,52 @@ __device__ __forceinline__ void prolong_fused_body(BlockIdx bi_, const T* __rest
 }
 
 template <typename T, int NF, int NC>
-__global__ void __launch_bounds__(128) k_prolong_fused(const T* __restrict__ uc, T* __restrict__ uf,
+__global__ void __launch_bounds__(256) k_prolong_fused(const T* __restrict__ uc, T* __restrict__ uf,
                                   const T* __restrict__ J, int64_t Ne) {
   pdl_entry();
   prolong_fused_body<T, NF, NC>(plain_block(), uc, uf, J, Ne);
 }
 
-// Fused restriction f_c = (J^T (x) J^T (x) J^T) r_f per element.
+// Fused restriction f_c = (J^T (x) J^T (x) J^T) r_f, TE elements per block pass.
 template <typename T, int NF, int NC>
 __device__ __forceinline__ void restrict_fused_body(BlockIdx bi_, const T* __restrict__ rf, T* __restrict__ fc,
                                                     const T* __restrict__ J, int64_t Ne) {
-  constexpr int nei = (NF + 1) / 2, neo = (NC + 1) / 2;
+  constexpr int nei = (NF + 1) / 2, neo = (NC + 1) / 2, TE = TrShape<NF>::te;
+  constexpr int nB = NF * NC * NC, nC = NF * NF * NC;
   __shared__ T sE[neo * nei], sO[(NC / 2) * (NF / 2) + 1];
-  __shared__ T sB[NF * NC * NC], sC[NF * NF * NC];
+  __shared__ T sB[TE * nB], sC[TE * nC];
   cs_split<T, NC, NF>([&](int o, int t) { return J[t * NC + o]; }, sE, sO);
   __syncthreads();
-  for (int64_t e = bi_.b; e < Ne; e += bi_.g) {
-    const T* x0 = rf + e * (NF * NF * NF);
-    for (int ln = threadIdx.x; ln < NF * NF; ln += blockDim.x) {  // z: (a,b) lines
+  for (int64_t e0 = (int64_t)bi_.b * TE; e0 < Ne; e0 += (int64_t)bi_.g * TE) {
+    const int cnt = (int)(Ne - e0 < TE ? Ne - e0 : TE);
+    for (int w = threadIdx.x; w < cnt * NF * NF; w += blockDim.x) {  // z: (a,b) lines
+      const int g = w / (NF * NF), ln = w - g * (NF * NF);
+      const T* x0 = rf + (e0 + g) * (NF * NF * NF);
       T x[NF], y[NC];
 #pragma unroll
       for (int t = 0; t < NF; ++t) x[t] = x0[ln + NF * NF * t];
       cs_matvec<T, NC, NF>(sE, sO, x, y);
 #pragma unroll
-      for (int k = 0; k < NC; ++k) sC[ln + NF * NF * k] = y[k];
+      for (int k = 0; k < NC; ++k) sC[g * nC + ln + NF * NF * k] = y[k];
     }
     __syncthreads();
-    for (int ln = threadIdx.x; ln < NF * NC; ln += blockDim.x) {  // y: (a,k) lines
+    for (int w = threadIdx.x; w < cnt * NF * NC; w += blockDim.x) {  // y: (a,k) lines
+      const int g = w / (NF * NC), ln = w - g * (NF * NC);
       const int a = ln % NF, k = ln / NF;
       T x[NF], y[NC];
 #pragma unroll
-      for (int t = 0; t < NF; ++t) x[t] = sC[a + NF * (t + NF * k)];
+      for (int t = 0; t < NF; ++t) x[t] = sC[g * nC + a + NF * (t + NF * k)];
       cs_matvec<T, NC, NF>(sE, sO, x, y);
 #pragma unroll
-      for (int j = 0; j < NC; ++j) sB[a + NF * (j + NC * k)] = y[j];
+      for (int j = 0; j < NC; ++j) sB[g * nB + a + NF * (j + NC * k)] = y[j];
     }
     __syncthreads();
-    T* out = fc + e * (NC * NC * NC);
-    for (int ln = threadIdx.x; ln < NC * NC; ln += blockDim.x) {  // x: (j,k) lines
+    for (int w = threadIdx.x; w < cnt * NC * NC; w += blockDim.x) {  // x: (j,k) lines
+      const int g = w / (NC * NC), ln = w - g * (NC * NC);
+      T* out = fc + (e0 + g) * (NC * NC * NC);
       T x[NF], y[NC];
 #pragma unroll
-      for (int t = 0; t < NF; ++t) x[t] = sB[t + NF * ln];
+      for (int t = 0; t < NF; ++t) x[t] = sB[g * nB + t + NF * ln];
       cs_matvec<T, NC, NF>(sE, sO, x, y);
 #pragma unroll
       for (int i = 0; i < NC; ++i) out[i + NC * ln] = y[i];
@@ -210,7 +226,7 @@ __device__ __forceinline__ void restrict_fused_body(BlockIdx bi_, const T* __res
 }
 
 template <typename T, int NF, int NC>
-__global__ void __launch_bounds__(128) k_restrict_fused(const T* __restrict__ rf, T* __restrict__ fc,
+__global__ void __launch_bounds__(256) k_restrict_fused(const T* __restrict__ rf, T* __restrict__ fc,
                                   const T* __restrict__ J, int64_t Ne) {
   pdl_entry();
   restrict_fused_body<T, NF, NC>(plain_block(), rf, fc, J, Ne);
@@ -274,7 +290,11 @@ const df64* table_of<df64>(const mg_ctx* c) { return c->ws.tabdf; }
 
 }  // namespace
 
-inline int fused_blocks(int64_t Ne) { return (int)(Ne < 152 * 12 ? Ne : 152 * 12); }
+template <int NF>
+inline int fused_blocks(int64_t Ne) {
+  const int64_t groups = (Ne + TrShape<NF>::te - 1) / TrShape<NF>::te;
+  return (int)(groups < 152 * 8 ? groups : 152 * 8);
+}
 
 // Halves of A (NO x NI, A[o][t] = J[o NC + t] for the prolongation, J[t NC + o]
 // for the restriction) from the level's FP32 table, as cs_split forms them.
@@ -310,16 +330,16 @@ cudaError_t contract_c(const mg_ctx* c, TrCArgs<float, NO, NI>& a, const float* 
 
 template <typename T, int NF, int NC>
 cudaError_t restrict_fused(const mg_ctx* c, const T* r_fine, T* f_coarse, const T* J) {
-  launch_pdl<kTwinType<T> ? &restrict_fused_body<T, NF, NC> : nullptr, 128>(
-      k_restrict_fused<T, NF, NC>, fused_blocks(c->Ne), 128, 0, c->stream, r_fine, f_coarse, J, c->Ne);
+  launch_pdl<kTwinType<T> ? &restrict_fused_body<T, NF, NC> : nullptr, 256>(
+      k_restrict_fused<T, NF, NC>, fused_blocks<NF>(c->Ne), 256, 0, c->stream, r_fine, f_coarse, J, c->Ne);
   c->nlaunch += 1;
   return cudaGetLastError();
 }
 
 template <typename T, int NF, int NC>
 cudaError_t prolong_fused(const mg_ctx* c, const T* u_coarse, T* u_fine, const T* J) {
-  launch_pdl<kTwinType<T> ? &prolong_fused_body<T, NF, NC> : nullptr, 128>(
-      k_prolong_fused<T, NF, NC>, fused_blocks(c->Ne), 128, 0, c->stream, u_coarse, u_fine, J, c->Ne);
+  launch_pdl<kTwinType<T> ? &prolong_fused_body<T, NF, NC> : nullptr, 256>(
+      k_prolong_fused<T, NF, NC>, fused_blocks<NF>(c->Ne), 256, 0, c->stream, u_coarse, u_fine, J, c->Ne);
   c->nlaunch += 1;
   return cudaGetLastError();
 }
