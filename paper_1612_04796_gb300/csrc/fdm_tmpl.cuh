@@ -166,7 +166,8 @@ __device__ __forceinline__ void line_bwd(const T (&v)[M], const T* __restrict__ 
 // last pass always writes the corrections to the global buffer).
 template <typename T, int M>
 struct FdmShape {
-  static constexpr int spb = M * M >= 128 ? 1 : 128 / (M * M);
+  // subdomains per block: one from m = 11 up; about 256 lines a pass below
+  static constexpr int spb = M * M >= 100 ? 1 : 256 / (M * M);
   static constexpr size_t table_bytes = sizeof(T) * 6 * M * M;
   static constexpr size_t tile_bytes = sizeof(T) * spb * M * M * M;
   static constexpr bool smem_tile = table_bytes + tile_bytes <= 210 * 1024;

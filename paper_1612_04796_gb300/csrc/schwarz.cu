@@ -506,7 +506,7 @@ cudaError_t launch_fdm(const mg_ctx* c, int l, const T* r) {
   if (cubic && (m & 1) && m >= 3 && m <= 35) {
     // compile-time width: several subdomains per block when m^2 is small
     const size_t smem = sizeof(T) * 6 * m2;
-    a.spb = m2 >= 128 ? 1 : 128 / m2;  // must equal FdmShape<T, m>::spb
+    a.spb = m2 >= 100 ? 1 : 256 / m2;  // must equal FdmShape<T, m>::spb
     a.s_in_smem = 1;
     int threads = a.spb * m2;
     threads = threads > 256 ? 256 : (threads + 31) / 32 * 32;
