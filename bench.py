@@ -132,6 +132,9 @@ def parse_args():
                          "E4M3 with power-of-two scales per line and per factor column (a precision study of "
                          "BF16 / FP8 tensor-core contractions, run on the CUDA cores)")
     ap.add_argument("--fdm-bf16", action="store_true", help="the same as --fdm-operands bf16")
+    ap.add_argument("--autotune", action="store_true",
+                    help="--workload runs: time each level's kernel variants at setup and keep the fastest "
+                         "(mg_opts.autotune)")
     ap.add_argument("--outer-all", action="store_true",
                     help="mixed MG-CG runs: the whole outer iteration (vectors, inner products, updates and "
                          "q = A p) in double-float arithmetic")
@@ -661,7 +664,7 @@ def run_mg(args):
 
 
 def workload_line(name, steps, warmup, overlap=None, precision=None, cg=False, outer_df64=False,
-                  tensor_cores="off", fdm_operands="fp32"):
+                  tensor_cores="off", fdm_operands="fp32", autotune=False):
     """One configuration: DOF/s of full solves (inputs resident, L2 flushed
     between solves), per-kernel device times and the rooflines of the
     fine-level kernels.  Returns the JSON line as a dict."""
@@ -680,6 +683,7 @@ def workload_line(name, steps, warmup, overlap=None, precision=None, cg=False, o
     dev = torch.device("cuda", torch.cuda.current_device())
     pkg.load_library()
     extra = {k: W[k] for k in ("overlap_mode", "overlap_frac", "ns_growth") if k in W}
+    extra["autotune"] = autotune
     extra_mixed = dict(extra, tensor_cores=TC_MODE[tensor_cores], outer_df64=outer_df64,
                        fdm_operands=fdm_operands)
     s = pkg.MGSolver(W["lengths"], W["elements"], W["P"], overlap=W["overlap_layers"], precision=W["precision"],
@@ -726,6 +730,8 @@ def workload_line(name, steps, warmup, overlap=None, precision=None, cg=False, o
     prof_ms, _ = run(steps)
     s.profile(False)
     true_rel = float(torch.linalg.norm(s64.residual(u, b)) / torch.linalg.norm(b))
+    W["autotune"] = autotune
+    W["kernel_variants_by_level"] = [s.kernel_variants(l) for l in range(1, s.L + 1)]
     if W["precision"] == "mixed":
         W["fdm_tensor_cores"] = tensor_cores
         W["outer_operator"] = {False: "FP64", True: "double-float (FP32 pairs)",
@@ -762,7 +768,7 @@ def run_workload(args):
     line = workload_line(args.workload, args.steps, args.warmup, overlap=args.overlap, precision=args.precision,
                          cg=args.cg, outer_df64="all" if args.outer_all else args.outer_df64,
                          tensor_cores=args.tensor_cores,
-                         fdm_operands="bf16" if args.fdm_bf16 else args.fdm_operands)
+                         fdm_operands="bf16" if args.fdm_bf16 else args.fdm_operands, autotune=args.autotune)
     print(json.dumps(line), flush=True)
 
 

@@ -199,8 +199,8 @@ int mg_level_fdm_tensor_cores(const mg_ctx* ctx, int level);
  * (shared-memory smoother, plain operator, plain scatter); for the FP32
  * smoother 2 for the passes of the parameter-space kernel split over three
  * grid-wide kernels (planes of the tile, then its z-columns, then planes
- * again), the default on cubic levels whose subdomains would fill fewer
- * blocks than the GPU has SMs; -1 for a bad level or kind. */
+ * again), the default on cubic levels with subdomain width m >= 11; -1 for
+ * a bad level or kind. */
 int mg_level_kernel_variant(const mg_ctx* ctx, int level, int kind);
 
 /* Physical coordinates of the nodes of `level` into x, y, z (device, N_l each). */

@@ -232,11 +232,12 @@ __global__ void __launch_bounds__(FdmCShape<M>::threads) k_fdm_c(const __grid_co
 
 // ---- the same solve split into three grid-wide kernels ----
 //
-// A level with few subdomains (the 4^3 mesh at P = 32 has 64) gives the
-// one-block-per-subdomain kernel too few blocks to fill 152 SMs.  Its passes
-// are independent across planes of the tile, so they are spread over three
-// kernels with many blocks each, the tile staying in the correction buffer
-// between them (L2-resident at these sizes):
+// The passes are independent across planes of the tile, so they can be
+// spread over three kernels with many blocks each, the tile staying in the
+// correction buffer between them: a level with few subdomains (the 4^3 mesh
+// at P = 32 has 64) then fills the 152 SMs, and on every cubic level from
+// m = 11 up it was measured faster than the one-kernel form (the default
+// there):
 //   k_fdm_xy: per block SL z-planes (c) of one subdomain: gather the x-lines,
 //             x forward, y forward;
 //   k_fdm_z:  one thread per (i, j) column of every subdomain: z forward,
@@ -511,11 +512,13 @@ bool fdm_c_applies(const mg_ctx* c, int l) {
 }
 
 int fdm_c_default_variant(const mg_ctx* c, int l) {
-  // the split pays for its two extra launches only on wide tiles
-  if (!fdm_c_applies(c, l) || c->lev[l].m[0] < 15) return 0;
-  const int m = c->lev[l].m[0], m2 = m * m;
-  const int64_t spb = m2 >= 256 ? 1 : 256 / m2;  // FdmCShape<m>::spb
-  return (c->Ne + spb - 1) / spb < 152 ? 2 : 0;
+  // The split form was measured faster at every cubic width from m = 11 up,
+  // also where the one-kernel form fills the SMs (16^3 mesh, m = 11: 0.55 vs
+  // 0.73 ms per mixed solve; 48x8x8 mesh, m = 25: 7.1 vs 10.6 ms): its
+  // kernels keep a plane or a column per thread instead of a whole tile per
+  // block in shared memory.  Below m = 11 its two extra launches cost more
+  // than they save.
+  return fdm_c_applies(c, l) && c->lev[l].m[0] >= 11 ? 2 : 0;
 }
 
 cudaError_t launch_fdm_c(const mg_ctx* c, int l, const float* r) {

@@ -293,8 +293,8 @@ struct LevelInfo {
   int fdm_tc;            // FP32 smoother contractions on the tensor cores (1) or CUDA cores (0)
   // Kernel variants of single solves (mg_opts.autotune picks them by timing):
   // fdm_variant 0 = the FP32 smoother k_fdm_c, 1 = the shared-memory k_fdm_m,
-  // 2 = k_fdm_c's passes split over three grid-wide kernels (the default where
-  // k_fdm_c would launch fewer blocks than there are SMs); 1 = the plain
+  // 2 = k_fdm_c's passes split over three grid-wide kernels (the default on
+  // cubic levels with m >= 11); 1 = the plain
   // operator k_sipg_n instead of k_sipg_c; the scatter k_scatter_n2 instead of
   // the element-aligned k_scatter_e.
   int fdm_variant, sipg_plain, scatter_plain;
@@ -424,7 +424,7 @@ bool fdm_tc_fits(const mg_ctx* c, int l);
 // cubic odd widths 3..35; cudaErrorNotSupported otherwise.
 cudaError_t launch_fdm_c(const mg_ctx* c, int l, const float* r);  // k_fdm_c, or split if fdm_variant == 2
 bool fdm_c_applies(const mg_ctx* c, int l);
-int fdm_c_default_variant(const mg_ctx* c, int l);  // 2 where k_fdm_c would leave SMs idle, else 0
+int fdm_c_default_variant(const mg_ctx* c, int l);  // 2 on cubic levels with m >= 11, else 0
 
 // ---- transfers (transfer.cu) ----
 template <typename T>

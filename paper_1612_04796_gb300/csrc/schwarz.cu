@@ -506,7 +506,14 @@ cudaError_t launch_fdm(const mg_ctx* c, int l, const T* r) {
   if (cubic && (m & 1) && m >= 3 && m <= 35) {
     // compile-time width: several subdomains per block when m^2 is small
     const size_t smem = sizeof(T) * 6 * m2;
-    a.spb = m2 >= 100 ? 1 : 256 / m2;  // must equal FdmShape<T, m>::spb
+    // subdomains per block: FdmShape<T, m>::spb (the shared-memory tile is
+    // sized for it), fewer for single solves on small meshes so that the
+    // blocks still fill the SMs (batched records keep the fixed value: only
+    // launches of equal shape merge)
+    const int spb_max = m2 >= 100 ? 1 : 256 / m2;
+    a.spb = launch_recorder() != nullptr
+                ? spb_max
+                : (int)std::max<int64_t>(1, std::min<int64_t>(spb_max, (c->Ne + 2 * 152 - 1) / (2 * 152)));
     a.s_in_smem = 1;
     int threads = a.spb * m2;
     threads = threads > 256 ? 256 : (threads + 31) / 32 * 32;

@@ -23,7 +23,9 @@ def test_autotuned_solve_matches_default(mg, precision, outer):
         # the FP32 smoother has a third variant (its passes split over three kernels)
         assert v["fdm"] in ((0, 1, 2) if precision == "mixed" else (0, 1)) and v["sipg"] in (0, 1) \
             and v["scatter"] in (0, 1), v
-        assert s0.kernel_variants(l) == {"fdm": 0, "sipg": 0, "scatter": 0}
+        # defaults: the split FP32 smoother from m = 11 up (the P = 8 level here), else 0
+        fdm0 = 2 if precision == "mixed" and l == s0.L else 0
+        assert s0.kernel_variants(l) == {"fdm": fdm0, "sipg": 0, "scatter": 0}
     b = s0.rhs(torch.tensor(inputs.gaussian(s0.num_dofs(), 41), device=s0.device))
     use_cg = precision == "mixed"
     u0, it0, rel0, _ = s0.solve(b, tol=1e-10, use_cg=use_cg)
@@ -36,18 +38,19 @@ def test_autotuned_solve_matches_default(mg, precision, outer):
 
 
 def test_split_smoother_matches_fused(mg):
-    """On the 4^3, P = 32 mesh (64 subdomains) the mixed solver's fine levels
-    default to the FP32 smoother split over three grid-wide kernels; it makes
-    the products of the one-kernel smoother, line by line in the same order,
-    so one smoothing step agrees with it to the last bit (or within an ulp
-    where the compiler contracts differently) at m = 35 and m = 19."""
+    """On the 4^3, P = 32 mesh (64 subdomains) the mixed solver's levels of
+    width m >= 11 default to the FP32 smoother split over three grid-wide
+    kernels; it makes the products of the one-kernel smoother, line by line in
+    the same order, so one smoothing step agrees with it to the last bit (or
+    within an ulp where the compiler contracts differently) at m = 35, 19 and
+    11."""
     import torch
     lengths, counts, P = (1.0, 1.0, 1.0), (4, 4, 4), 32
     sm = mg.MGSolver(lengths, counts, P, precision="mixed")
     s1 = mg.MGSolver(lengths, counts, P)  # FP64 context: FP32 smoothing steps use the one-kernel smoother
-    assert sm.kernel_variants(sm.L)["fdm"] == 2 and sm.kernel_variants(sm.L - 1)["fdm"] == 2
-    assert sm.kernel_variants(sm.L - 2)["fdm"] == 0  # m = 11: 32 blocks, too narrow to pay for the split
-    for lev in (sm.L, sm.L - 1):
+    assert [sm.kernel_variants(l)["fdm"] for l in (sm.L, sm.L - 1, sm.L - 2)] == [2, 2, 2]
+    assert sm.kernel_variants(sm.L - 3)["fdm"] == 0  # m = 7: the one-kernel form
+    for lev in (sm.L, sm.L - 1, sm.L - 2):
         N = sm.num_dofs(lev)
         u = torch.tensor(inputs.gaussian(N, 60 + lev), dtype=torch.float32, device=sm.device)
         f = torch.tensor(inputs.gaussian(N, 70 + lev), dtype=torch.float32, device=sm.device)
