@@ -322,28 +322,39 @@ __global__ void __launch_bounds__(256) k_sipg_dir(OpArgs<T> a, int dir, int chun
   sipg_dir_body<T, N, NP>(plain_block(), a, dir, chunks);
 }
 
+// The three direction launches of the direction-split operator, NP threads per line.
+template <typename T, int N, int NP>
+cudaError_t launch_sipg_dir(const mg_ctx* c, OpArgs<T>& a) {
+  constexpr int n2 = N * N;
+  const int chunks = (n2 * NP + 255) / 256;
+  const int threads = ((n2 * NP + chunks - 1) / chunks + 31) / 32 * 32;
+  const int64_t nblk = c->Ne * chunks;
+  const int blocks = (int)(nblk < 152 * 16 ? nblk : 152 * 16);
+  for (int dir = 0; dir < 3; ++dir) {
+    launch_pdl<kTwinType<T> ? &sipg_dir_body<T, N, NP> : nullptr>(k_sipg_dir<T, N, NP>, blocks, threads, 0,
+                                                                  c->stream, a, dir, chunks);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  c->nlaunch += 3;
+  return cudaSuccess;
+}
+
 template <typename T, int N>
 cudaError_t launch_sipg_n(const mg_ctx* c, OpArgs<T>& a) {
   constexpr int n2 = N * N;
-  // the long lines of high orders are shared by 4 threads (4 times the parallelism on small meshes)
-  constexpr int NP = N >= 17 ? 4 : 1;
   // lines per element and direction spread evenly over <= 256 threads
   const int iters = (n2 + 255) / 256;
   if (iters > 1 || c->Ne < 2 * 152) {
-    const int chunks = (n2 * NP + 255) / 256;
-    const int threads = ((n2 * NP + chunks - 1) / chunks + 31) / 32 * 32;
-    if (c->Ne * chunks < 4 * 152 || iters > 1) {
-      const int64_t nblk = c->Ne * chunks;
-      const int blocks = (int)(nblk < 152 * 16 ? nblk : 152 * 16);
-      for (int dir = 0; dir < 3; ++dir) {
-        launch_pdl<kTwinType<T> ? &sipg_dir_body<T, N, NP> : nullptr>(k_sipg_dir<T, N, NP>, blocks, threads, 0,
-                                                                      c->stream, a, dir, chunks);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-      }
-      c->nlaunch += 3;
-      return cudaSuccess;
-    }
+    // The long lines of high orders are shared by 4 threads on meshes of few
+    // elements (4 times the parallelism).  Every sharing thread repeats the
+    // line's even/odd and face sums, so with enough lines (the 48x8x8, P = 16
+    // mesh has 888k per direction) each line gets one thread.
+    const bool share = N >= 17 && c->Ne * (int64_t)n2 < 152 * 512;
+    const int np = share ? 4 : 1;
+    const int chunks = (n2 * np + 255) / 256;
+    if (c->Ne * chunks < 4 * 152 || iters > 1)
+      return share ? launch_sipg_dir<T, N, (N >= 17 ? 4 : 1)>(c, a) : launch_sipg_dir<T, N, 1>(c, a);
   }
   a.epb = n2 >= 128 ? 1 : 128 / n2;
   int threads = a.epb * n2;

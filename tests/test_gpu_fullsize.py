@@ -91,6 +91,22 @@ def test_cube4_p32_operator_sampled(mg):
         assert np.max(np.abs(got - ref)) / np.max(np.abs(ref)) < 1e-12, e
 
 
+def test_p16_fp64_operator_one_thread_per_line(mg):
+    """The FP64 operator at P = 16 on a mesh with enough lines for one thread
+    per line (8x6x6 elements, 83k lines per direction; the 48x8x8 box runs
+    this form): sampled elements against the oracle, 1e-12."""
+    lengths, counts, P = (1.0, 1.5, 0.7), (8, 6, 6), 16
+    s = mg.MGSolver(lengths, counts, P)
+    u = inputs.gaussian(s.num_dofs(), 47)
+    Au = s.apply_sipg(_cuda(u)).cpu().numpy()
+    s.close()
+    n3 = 17 ** 3
+    for e in (0, 100, 287):
+        ref = oracle_operator_at(u, lengths, counts, 16, e)
+        got = Au[e * n3:(e + 1) * n3]
+        assert np.max(np.abs(got - ref)) / np.max(np.abs(ref)) < 1e-12, e
+
+
 @pytest.mark.parametrize("arith", ["fp32", "df64"])
 def test_cube4_p32_operator_sampled_fp32_df64(mg, arith):
     """The operator of the mixed solve at P = 32 (n = 33 on 64 elements: the
