@@ -20,6 +20,11 @@ The oracle is written to be read against the paper, not to be fast:
                 interpolation, the coarse pseudo-inverse solve, the V-cycle,
                 standalone MG and the inexact preconditioned CG.
 
+Graded meshes (element widths varying along each axis, an extension of the
+paper's uniform grids) go through the same functions: ``sipg.Mesh(widths=...)``
+assembles element by element, and ``schwarz.SchwarzSmoother`` then factors
+every subdomain's own A_ss.
+
 Readings of passages the paper leaves silent, ambiguous or garbled are stated in
 the docstring of the function that adopts them.
 

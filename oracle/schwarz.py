@@ -200,34 +200,18 @@ def subdomain_indices(mesh, P, n_o, delta, profile="quintic"):
     return idx, W
 
 
-class SchwarzSmoother:
-    """u <- u + sum_s R_s^T W_s A_ss^{-1} R_s (f - A u), repeated nsteps times.
+class LocalSolver:
+    """Direct solver of one restricted problem A_ss x = r_s.
 
-    A_ss = A[I_s, I_s] is extracted from the assembled A.  On the uniform
-    periodic mesh it is the same matrix for every s (checked on all subdomains,
-    or a sample of ``check`` of them, to 1e-13 relative), so one factorisation
-    serves all subdomains."""
+    A_ss is badly scaled at high order (the GLL mass weights span two orders
+    of magnitude per direction, so its diagonal spans six): the factorisation
+    is applied to the symmetrically scaled matrix D A_ss D,
+    D = diag(A_ss)^(-1/2), whose condition number is far smaller, and every
+    solve ends with iterative refinement steps x += A_ss^{-1} (r - A_ss x)
+    (plain FP64 residuals)."""
 
-    def __init__(self, A, mesh, P, n_o, delta, profile="quintic", check=64, dense_limit=7000):
-        self.idx, self.W = subdomain_indices(mesh, P, n_o, delta, profile)
-        self.N = A.shape[0]
-        Ns = self.idx.shape[0]
-        I0 = self.idx[0]
-        Ass = A[I0][:, I0]
-        sample = np.arange(Ns) if Ns <= check else np.random.default_rng(0).choice(Ns, check, replace=False)
-        ref = abs(Ass).max()
-        for s in sample:
-            Is = self.idx[s]
-            diff = abs(A[Is][:, Is] - Ass).max()
-            if diff > 1e-13 * ref:
-                raise AssertionError("A_ss differs between subdomains: %g" % diff)
-        self.m3 = len(I0)
-        # A_ss is badly scaled at high order (the GLL mass weights span two
-        # orders of magnitude per direction, so its diagonal spans six): the
-        # factorisation is applied to the symmetrically scaled matrix
-        # D A_ss D, D = diag(A_ss)^(-1/2), whose condition number is far
-        # smaller, and every solve ends with iterative refinement steps
-        # x += A_ss^{-1} (r - A_ss x) (plain FP64 residuals).
+    def __init__(self, Ass, dense_limit=7000):
+        self.m3 = Ass.shape[0]
         self.dscale = 1.0 / np.sqrt(Ass.diagonal())
         Dm = sp.diags(self.dscale)
         Asc = (Dm @ Ass @ Dm).tocsc()
@@ -244,7 +228,7 @@ class SchwarzSmoother:
         y = sla.cho_solve(self.chol, b) if self.chol is not None else self.lu.solve(b)
         return y * (self.dscale[:, None] if rs.ndim == 2 else self.dscale)
 
-    def local_solve(self, rs, max_refine=40):
+    def solve(self, rs, max_refine=40):
         """A_ss^{-1} applied to the columns of rs (m^3 x k): a direct solve
         with the scaled factorisation, then refinement steps until the largest
         relative residual of the columns is below 1e-14 or stops falling by at
@@ -265,10 +249,49 @@ class SchwarzSmoother:
             res = rs - self.Ass @ x
         return x
 
+
+class SchwarzSmoother:
+    """u <- u + sum_s R_s^T W_s A_ss^{-1} R_s (f - A u), repeated nsteps times.
+
+    A_ss = A[I_s, I_s] is extracted from the assembled A.  On the uniform
+    periodic mesh it is the same matrix for every s (checked on all subdomains,
+    or a sample of ``check`` of them, to 1e-13 relative), so one factorisation
+    serves all subdomains.  On a graded mesh (``mesh.graded``) every subdomain
+    has its own A_ss and its own factorisation."""
+
+    def __init__(self, A, mesh, P, n_o, delta, profile="quintic", check=64, dense_limit=7000):
+        self.idx, self.W = subdomain_indices(mesh, P, n_o, delta, profile)
+        self.N = A.shape[0]
+        Ns = self.idx.shape[0]
+        if getattr(mesh, "graded", False):
+            self.solvers = [LocalSolver(A[self.idx[s]][:, self.idx[s]], dense_limit) for s in range(Ns)]
+            self.m3 = self.solvers[0].m3
+            return
+        I0 = self.idx[0]
+        Ass = A[I0][:, I0]
+        sample = np.arange(Ns) if Ns <= check else np.random.default_rng(0).choice(Ns, check, replace=False)
+        ref = abs(Ass).max()
+        for s in sample:
+            Is = self.idx[s]
+            diff = abs(A[Is][:, Is] - Ass).max()
+            if diff > 1e-13 * ref:
+                raise AssertionError("A_ss differs between subdomains: %g" % diff)
+        self.solvers = None
+        self.solver = LocalSolver(Ass, dense_limit)
+        self.m3 = self.solver.m3
+        self.Ass = Ass
+
+    def local_solve(self, rs, max_refine=40):
+        """A_ss^{-1} applied to the columns of rs (uniform meshes: the one A_ss)."""
+        return self.solver.solve(rs, max_refine)
+
     def correction(self, r):
         """sum_s R_s^T (W_s A_ss^{-1} R_s r)."""
         rs = r[self.idx]
-        du = self.local_solve(rs.T).T
+        if self.solvers is None:
+            du = self.local_solve(rs.T).T
+        else:
+            du = np.stack([self.solvers[s].solve(rs[s][:, None])[:, 0] for s in range(len(self.solvers))])
         return np.bincount(self.idx.ravel(), weights=(du * self.W[None, :]).ravel(), minlength=self.N)
 
     def smooth(self, A, u, f, nsteps=1):

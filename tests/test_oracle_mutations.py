@@ -109,3 +109,26 @@ def test_wrong_pcg_beta_sign_is_caught(monkeypatch):
     monkeypatch.setattr(multigrid, "solve_pcg", ns["solve_pcg"])
     gr, gx, _ = pcg_textbook_gaps(multigrid.solve_pcg)
     assert gr > 1e-3 or gx > 1e-3, (gr, gx)
+
+
+def test_graded_face_ignoring_the_neighbour_width_is_caught(monkeypatch):
+    """A face matrix that gives the e+ side the normal derivative scale of e-
+    (one 2/h for both sides) breaks Eq. (A) on a graded mesh."""
+    import test_oracle_graded as tgr
+
+    def one_width(P, h, d, mu, h_plus=None):
+        return _orig_face(P, h, d, mu)
+
+    monkeypatch.setattr(sipg, "face_matrix", one_width)
+    with pytest.raises(AssertionError):
+        tgr.test_graded_kronecker_form_eq_A(2)
+
+
+def test_graded_face_penalty_of_the_mean_width_is_caught(monkeypatch):
+    """Taking the penalty of the mean width of the two elements lets a graded
+    line become indefinite at the uniform threshold."""
+    import test_oracle_graded as tgr
+
+    monkeypatch.setattr(sipg, "face_penalty", lambda P, a, b, factor=2.0: sipg.penalty(P, 0.5 * (a + b), factor))
+    with pytest.raises(AssertionError):
+        tgr.test_face_penalty_of_the_smaller_width_keeps_the_uniform_threshold(4)
