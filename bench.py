@@ -103,6 +103,25 @@ WORKLOADS["batch16_p4"] = dict(workload="16 independent small problems solved to
                                          "one after another (mg_solve each)",
                                 problems=16, P=4, sizes=[4, 5, 6, 7, 8], aspect=[1.0, 8.0], seed=7,
                                 overlap_layers=1, precision="mixed", use_cg=True)
+
+
+def cosine_widths(n, length, amp, phase):
+    """Smoothly graded periodic widths: h_i proportional to
+    1 + amp cos(2 pi (i + 1/2) / n + phase), scaled to sum to `length`
+    (largest / smallest width (1 + amp) / (1 - amp) at most)."""
+    h = 1.0 + amp * np.cos(2.0 * np.pi * (np.arange(n) + 0.5) / n + phase)
+    return h * (length / h.sum())
+
+
+WORKLOADS["graded16_p8"] = dict(workload="graded periodic unit cube: 16^3 elements whose widths follow "
+                                         "1 + 0.6 cos(2 pi (i + 1/2) / 16 + phase) per axis (phases 0, 2 pi/3, "
+                                         "4 pi/3; widths 0.025 to 0.1, ratio 4), P=8 (2,985,984 DOFs), N_O=1, "
+                                         "nodal f ~ N(0,1) seed 2, standalone V(1,1) MG, FP64, tol 1e-10; "
+                                         "per-line eigenbases (graded kernels)",
+                                lengths=[1.0, 1.0, 1.0], elements=[16, 16, 16], P=8, overlap_layers=1,
+                                rhs="gaussian", seed=2, precision="fp64", use_cg=False,
+                                widths=[cosine_widths(16, 1.0, 0.6, 2.0 * np.pi * d / 3.0).tolist()
+                                        for d in range(3)])
 FP32_FLOP_PER_CLK_PER_SM = 256    # 128 FP32 FMA lanes per SM
 TF32_PER_BF16 = 1.1 / 2.25         # nominal dense tensor rates per GPU
 
@@ -303,7 +322,10 @@ def fdm_roofline(s, lev, fp64, clk, clk_basis, pk, traffic=None):
     Ne = int(np.prod(s.counts))
     per_clk = FP64_FLOP_PER_CLK_PER_SM if fp64 else FP32_FLOP_PER_CLK_PER_SM
     peak = NUM_SMS * per_clk * clk * 1e6
-    ops = Ne * fdm_executed_ops(md)
+    graded = getattr(s, "widths", None) is not None
+    # graded meshes: whole 1D products (a subdomain line has no reflection
+    # symmetry), 2 m^3 m_d multiply-adds per direction and m^3 divisions
+    ops = Ne * (sum(2 * int(np.prod(md)) * m for m in md) + int(np.prod(md)) if graded else fdm_executed_ops(md))
     dense = Ne * fdm_dense_flop(md)
     vb = 8 if fp64 else 4
     algo_bytes = vb * (s.num_dofs(lev) + Ne * md[0] * md[1] * md[2])
@@ -322,7 +344,9 @@ def fdm_roofline(s, lev, fp64, clk, clk_basis, pk, traffic=None):
             "peak_basis": "TF32 dense: measured bf16 burst %.1f TFLOP/s x the nominal TF32 / BF16 ratio %.4f "
                           "(1.1 / 2.25 PFLOP/s)" % (float(pk["bf16_tflops"]), TF32_PER_BF16),
         }
-    if fp64:
+    if graded:
+        kname = "k_gfdm<%s> (m = %s, per-line eigenbases)" % ("double" if fp64 else "float", m)
+    elif fp64:
         kname = "k_fdm_m<double, %s>" % m
     else:
         kname = {0: "k_fdm_c<%s>", 1: "k_fdm_m<float, %s>",
@@ -368,9 +392,12 @@ def level_rooflines(s, lev, fp64, clk, clk_basis, pk, traffic=None):
     r = fdm_roofline(s, lev, fp64, clk, clk_basis, pk, traffic)
     if r:
         out.append(r)
+    if getattr(s, "widths", None) is not None:
+        oname = "k_gsipg<%s, %d>" % (tname, 2 ** lev + 1)
+    else:
+        oname = "k_sipg_n<double, %d>" % (2 ** lev + 1) if fp64 else "k_sipg_c<%d>" % (2 ** lev + 1)
     r = hbm_roofline(s, "sipg", lev, 3 * vb * N, "%s (level %d residual r = f - A u: reads u, f, writes r)"
-                     % ("k_sipg_n<double, %d>" % (2 ** lev + 1) if fp64 else "k_sipg_c<%d>" % (2 ** lev + 1), lev),
-                     pk)
+                     % (oname, lev), pk)
     if r:
         out.append(r)
     r = hbm_roofline(s, "scatter", lev, vb * (Ne * md[0] * md[1] * md[2] + 2 * N),
@@ -646,6 +673,11 @@ def run_mg(args):
         for tcm in ("auto", "off"):
             line["c4"]["tensor_cores_" + tcm] = compact_line(workload_line("cube4_p32", 5, 3, outer_df64="all",
                                                                            tensor_cores=tcm))
+        # a graded mesh (element widths varying smoothly by a factor 4 along
+        # every axis) of the 16^3, P = 8 size: FP64 MG and mixed MG-CG
+        line["graded"] = {"fp64_mg": compact_line(workload_line("graded16_p8", 5, 3)),
+                          "mixed_mgcg": compact_line(workload_line("graded16_p8", 5, 3, precision="mixed",
+                                                                   cg=True))}
         line["serving"] = {}
         for no in (1, 4):
             line["serving"]["n_o_%d" % no] = compact_line(serving_line("serving512", no))
@@ -686,6 +718,10 @@ def workload_line(name, steps, warmup, overlap=None, precision=None, cg=False, o
     extra["autotune"] = autotune
     extra_mixed = dict(extra, tensor_cores=TC_MODE[tensor_cores], outer_df64=outer_df64,
                        fdm_operands=fdm_operands)
+    if "widths" in W:
+        extra["widths"] = W["widths"]
+        extra_mixed = {k: v for k, v in extra_mixed.items() if k not in ("tensor_cores", "fdm_operands")}
+        extra_mixed["widths"] = W["widths"]
     s = pkg.MGSolver(W["lengths"], W["elements"], W["P"], overlap=W["overlap_layers"], precision=W["precision"],
                      device=dev, **(extra_mixed if W["precision"] == "mixed" else extra))
     s64 = s if W["precision"] == "fp64" else pkg.MGSolver(W["lengths"], W["elements"], W["P"],
@@ -745,12 +781,15 @@ def workload_line(name, steps, warmup, overlap=None, precision=None, cg=False, o
     clk, clk_basis = clock_mhz(clock_info, pk)
     kern = level_rooflines(s, s.L, fp64, clk, clk_basis, pk)
     vb = 8 if fp64 else 4
+    if "widths" in W:
+        W["element_widths"] = {"min": min(min(w) for w in W["widths"]), "max": max(max(w) for w in W["widths"])}
     line = {
         "metric": METRIC, "value": N * steps / (sum(ms) / 1e3), "unit": "DOF/s", "n_gpus": 1,
         "steps": steps, "warmup": warmup, "ms_per_step": sum(ms) / steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64" if fp64 else "f32 multigrid / f64 outer",
         "data": "synthetic",
-        "config": dict(W, dofs=N, iterations=int(statistics.median(its)), name=name,
+        "config": dict({k: v for k, v in W.items() if k != "widths"}, dofs=N,
+                       iterations=int(statistics.median(its)), name=name,
                        true_relres=true_rel, l2="flushed (256 MiB write) between steps; fine-level vectors "
                        "%.0f MB each" % (vb * N / 1e6)),
         "gpu_launches": launches, "clocks": clock_info,

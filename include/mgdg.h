@@ -154,6 +154,33 @@ void mg_default_opts(mg_opts* o);
 mg_status mg_setup(double lx, double ly, double lz, int nx, int ny, int nz, int P, double penalty,
                    int overlap, const mg_opts* opts, mg_ctx** out);
 
+/*
+ * mg_setup_graded -- mg_setup for a graded mesh: element widths that vary
+ * along each axis of the periodic box, the mesh staying a tensor product
+ * (element (ex, ey, ez) is hx[ex] x hy[ey] x hz[ez]; its first corner lies at
+ * the sums of the widths before it).  The paper's grids are uniform
+ * (Section 4); the same form (Section 2, Eq. ip) applies element by element,
+ * so Eq. (A) keeps its Kronecker structure with per-element 1D factors and
+ * every subdomain of Section 3.1 gets the eigenbases of its own three lines.
+ *   hx, hy, hz   host arrays of nx, ny, nz widths (> 0, finite); copied
+ *   nx, ny, nz   3 .. 256 (the coarse eigenproblems are solved whole)
+ *   penalty      as in mg_setup, per face: mu = penalty P_l (P_l+1) / (2 h_min)
+ *                with h_min the smaller width of the face's two elements
+ *                (the uniform threshold stays the coercivity threshold)
+ *   P, overlap, opts, out   as in mg_setup
+ * Supported: MG_FP64 and MG_MIXED, MG_OVERLAP_LAYERS, no tensor cores, no
+ * double-float outer iteration, no autotuning, no operand study; anything
+ * else returns MG_EINVAL, as do the double-float entry points and
+ * mg_solve_batch on such a context.  All other calls work as on a uniform
+ * mesh (mg_node_coords gives the graded coordinates, mg_rhs the graded mass).
+ * No CUDA call is made.
+ */
+mg_status mg_setup_graded(const double* hx, const double* hy, const double* hz, int nx, int ny, int nz, int P,
+                          double penalty, int overlap, const mg_opts* opts, mg_ctx** out);
+
+/* 1 if ctx describes a graded mesh (mg_setup_graded), else 0 (host only). */
+int mg_is_graded(const mg_ctx* ctx);
+
 /* Bytes of device workspace the context needs (256-byte aligned base required). */
 mg_status mg_workspace_size(const mg_ctx* ctx, size_t* bytes);
 
@@ -328,6 +355,20 @@ mg_status mg_vcycle_f32(mg_ctx* ctx, float* u, const float* f);
  * fails with MG_EINVAL if capacity is too small.
  */
 mg_status mg_get_table(mg_ctx* ctx, int level, int dir, int what, double* host_out, int capacity, int* count);
+
+/*
+ * mg_get_line_table -- graded meshes: copy a table of element line `line`
+ * (0 .. n_dir - 1) of level l, direction dir to host memory.  what:
+ *   0 mass diag (h_line / 2) w (n)
+ *   1 rows of the line's element in the 1D matrix L: blocks L[e][e-1],
+ *     L[e][e], L[e][e+1] (3 n*n, each row-major)
+ *   2 eigenvalues Lambda of the subdomain line centred on the element (m; l >= 1)
+ *   3 its eigenvectors S (m*m, S[a*m + p] = entry a of eigenvector p, S^T M_s S = I)
+ * The eigenpairs come in no particular order.  MG_EINVAL on a uniform mesh,
+ * for a missing table, or if capacity is too small.
+ */
+mg_status mg_get_line_table(mg_ctx* ctx, int level, int dir, int line, int what, double* host_out, int capacity,
+                            int* count);
 
 /*
  * mg_coarse_solve_noalloc -- allocation-free variant of mg_coarse_solve.  The

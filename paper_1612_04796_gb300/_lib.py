@@ -135,6 +135,9 @@ SIGNATURES = {
     "mg_smooth_f32": (_S, [_P, _I, _P, _P, _I]),
     "mg_vcycle_f32": (_S, [_P, _P, _P]),
     "mg_get_table": (_S, [_P, _I, _I, _I, _P, _I, ctypes.POINTER(_I)]),
+    "mg_setup_graded": (_S, [_P, _P, _P, _I, _I, _I, _I, _D, _I, ctypes.POINTER(MgOpts), ctypes.POINTER(_P)]),
+    "mg_is_graded": (_I, [_P]),
+    "mg_get_line_table": (_S, [_P, _I, _I, _I, _I, _P, _I, ctypes.POINTER(_I)]),
     "mg_coarse_solve_noalloc": (_S, [_D, _D, _D, _I, _I, _I, _D, _P, _P, _P]),
     "mg_kernel_launches": (_LL, [_P]),
     "mg_batch_launches": (_LL, [_P]),

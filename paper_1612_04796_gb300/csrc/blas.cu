@@ -509,6 +509,7 @@ cudaError_t launch_from_f32(const mg_ctx* c, const float* x, double* y, int64_t 
 }
 
 cudaError_t launch_rhs(const mg_ctx* c, const double* f, double* b) {
+  if (c->graded) return launch_grhs(c, f, b);
   const LevelInfo& lv = c->lev[c->L];
   MassArgs a;
   a.tab = c->ws.tab64;
@@ -531,6 +532,7 @@ cudaError_t launch_rhs(const mg_ctx* c, const double* f, double* b) {
 }
 
 cudaError_t launch_coords(const mg_ctx* c, int l, double* x, double* y, double* z) {
+  if (c->graded) return launch_gcoords(c, l, x, y, z);
   const LevelInfo& lv = c->lev[l];
   launch_pdl(k_coords, grid_for(lv.N), kThreads, 0, c->stream, c->ws.tab64, lv.t[0].nodes, lv.n, c->Ne, c->ne[0], c->ne[1],
                                                         lv.h[0], lv.h[1], lv.h[2], x, y, z);

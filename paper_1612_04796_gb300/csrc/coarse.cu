@@ -355,7 +355,21 @@ cudaError_t coarse_solve_t(const mg_ctx* c, const TI* f0, TO* u0) {
 
 }  // namespace
 
+// Graded mesh: the level-0 mass is not a multiple of I, so the eigenbases are
+// not orthogonal to the constants in the Euclidean sense.  Dropping the
+// constant mode then neither projects f0 onto the range of A_0 nor gives the
+// zero-mean solution: both become explicit passes (f0 - mean(f0) into the
+// FP64 scratch coarse_f, and u0 - mean(u0) at the end).
+template <typename T>
+cudaError_t graded_coarse_solve(const mg_ctx* c, const T* f0, T* u0) {
+  cudaError_t e = launch_gcenter<T>(c, f0, c->ws.coarse_f);
+  if (e == cudaSuccess) e = coarse_solve_t<double, T>(c, c->ws.coarse_f, u0);
+  if (e == cudaSuccess) e = launch_gmean_zero<T>(c, u0);
+  return e;
+}
+
 cudaError_t launch_coarse_solve(const mg_ctx* c, const double* f0, double* u0) {
+  if (c->graded) return graded_coarse_solve<double>(c, f0, u0);
   return coarse_solve_t<double, double>(c, f0, u0);
 }
 
@@ -377,6 +391,7 @@ cudaError_t launch_coarse_solve_df64(const mg_ctx* c, const df64* f0, df64* u0) 
 cudaError_t launch_coarse_solve_f32(const mg_ctx* c, const float* f0, float* u0) {
   // The coarsest solve of the FP32 hierarchy runs in FP64: the first pass
   // reads the FP32 right-hand side, the last writes the FP32 solution.
+  if (c->graded) return graded_coarse_solve<float>(c, f0, u0);
   return coarse_solve_t<float, float>(c, f0, u0);
 }
 

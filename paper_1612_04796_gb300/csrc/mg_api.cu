@@ -105,8 +105,8 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 // ---- workspace layout ----
 struct Layout {
   size_t tab64, tab32, tabdf, lev_u[kMaxLevels], lev_f[kMaxLevels], lev_r[kMaxLevels], corr, ca, cb, cf, cu, cg[8], red,
-      scal, status, jac, total;
-  int64_t jac_count;
+      scal, status, jac, gjac, total;
+  int64_t jac_count, gjac_line, gjac_coarse;
 };
 
 Layout make_layout(const mg_ctx* c) {
@@ -146,6 +146,20 @@ Layout make_layout(const mg_ctx* c) {
   int64_t per_block = 4 * (int64_t)nmax * nmax + 4 * nmax + 64;
   ly.jac_count = per_block * 3 * (c->L + 1);
   ly.jac = take(ly.jac_count * sizeof(double));
+  ly.gjac = 0;
+  ly.gjac_line = ly.gjac_coarse = 0;
+  if (c->graded) {
+    // one block per element line of every level (C, V: m^2 each, M: m) and
+    // one per coarse direction (Ng^2, Ng^2, Ng)
+    int mmax = 1, ngmax = 1;
+    for (int l = 1; l <= c->L; ++l)
+      for (int d = 0; d < 3; ++d) mmax = std::max(mmax, c->lev[l].m[d]);
+    for (int d = 0; d < 3; ++d) ngmax = std::max(ngmax, c->Ng[d]);
+    ly.gjac_line = 2 * (int64_t)mmax * mmax + mmax + 32;
+    ly.gjac_coarse = 2 * (int64_t)ngmax * ngmax + ngmax + 32;
+    const int64_t lines = (int64_t)(c->L + 1) * (c->ne[0] + c->ne[1] + c->ne[2]);
+    ly.gjac = take((lines * ly.gjac_line + 3 * ly.gjac_coarse) * sizeof(double));
+  }
   ly.total = off;
   return ly;
 }
@@ -1175,6 +1189,96 @@ mg_status mg_setup(double lx, double ly, double lz, int nx, int ny, int nz, int 
   return MG_OK;
 }
 
+mg_status mg_setup_graded(const double* hx, const double* hy, const double* hz, int nx, int ny, int nz, int P,
+                          double penalty, int overlap, const mg_opts* opts, mg_ctx** out) {
+  if (!out) return MG_EINVAL;
+  *out = nullptr;
+  if (!hx || !hy || !hz || nx < 3 || ny < 3 || nz < 3 || nx > 256 || ny > 256 || nz > 256) return MG_EINVAL;
+  const double* hs[3] = {hx, hy, hz};
+  const int ns[3] = {nx, ny, nz};
+  double len[3];
+  for (int d = 0; d < 3; ++d) {
+    len[d] = 0.0;
+    for (int e = 0; e < ns[d]; ++e) {
+      if (!(hs[d][e] > 0.0) || !std::isfinite(hs[d][e])) return MG_EINVAL;
+      len[d] += hs[d][e];
+    }
+  }
+  mg_opts o;
+  mg_default_opts(&o);
+  if (opts) o = *opts;
+  // graded meshes run the FP64 or the FP32 hierarchy on node-layer overlaps,
+  // with the fixed kernels
+  if (o.precision != MG_FP64 && o.precision != MG_MIXED) return MG_EINVAL;
+  if (o.overlap_mode != MG_OVERLAP_LAYERS || o.fdm_tensor_cores != 0 || o.outer_df64 != 0 || o.autotune != 0 ||
+      o.fdm_operands != 0)
+    return MG_EINVAL;
+  mg_ctx* c = nullptr;
+  const mg_status st = mg_setup(len[0], len[1], len[2], nx, ny, nz, P, penalty, overlap, &o, &c);
+  if (st != MG_OK) return st;
+  c->graded = true;
+  int64_t off = c->ws.tab_count;
+  auto tab = [&](int64_t count) {
+    int64_t o2 = off;
+    off += (count + 31) / 32 * 32;
+    return o2;
+  };
+  for (int d = 0; d < 3; ++d) {
+    c->wid[d].assign(hs[d], hs[d] + ns[d]);
+    c->org[d].assign(ns[d], 0.0);
+    for (int e = 1; e < ns[d]; ++e) c->org[d][e] = c->org[d][e - 1] + c->wid[d][e - 1];
+    c->gwid[d] = tab(ns[d]);
+    c->gorg[d] = tab(ns[d]);
+  }
+  for (int l = 0; l <= c->L; ++l) {
+    LevelInfo& lv = c->lev[l];
+    for (int d = 0; d < 3; ++d) {
+      DirTables& t = lv.t[d];
+      const int64_t nd = ns[d], n = lv.n, m = lv.m[d];
+      t.gblk = tab(nd * 3 * n * n);
+      t.gmass = tab(nd * n);
+      if (l >= 1) {
+        t.gS = tab(nd * m * m);
+        t.gSW = tab(nd * m * m);
+        t.glam = tab(nd * m);
+      }
+    }
+  }
+  c->ws.tab_count = off;
+  c->ws_bytes = make_layout(c).total;
+  *out = c;
+  return MG_OK;
+}
+
+mg_status mg_get_line_table(mg_ctx* c, int level, int dir, int line, int what, double* host_out, int capacity,
+                            int* count) {
+  mg_status s = need_ready(c);
+  if (s != MG_OK) return s;
+  if (!c->graded) return fail(c, MG_EINVAL, "not a graded mesh");
+  if (!check_level(c, level, false) || dir < 0 || dir > 2 || line < 0 || line >= c->ne[dir] || !host_out || !count)
+    return fail(c, MG_EINVAL, "bad arguments");
+  const LevelInfo& lv = c->lev[level];
+  const DirTables& t = lv.t[dir];
+  const int64_t n = lv.n, m = lv.m[dir];
+  int64_t off = -1, cnt = 0;
+  switch (what) {
+    case 0: off = t.gmass; cnt = n; break;
+    case 1: off = t.gblk; cnt = 3 * n * n; break;
+    case 2: off = t.glam; cnt = m; break;
+    case 3: off = t.gS; cnt = m * m; break;
+    default: return fail(c, MG_EINVAL, "unknown table");
+  }
+  if (off < 0) return fail(c, MG_EINVAL, "table not present on this level");
+  if (cnt > capacity) return fail(c, MG_EINVAL, "capacity too small");
+  CK(cudaMemcpyAsync(host_out, c->ws.tab64 + off + cnt * line, cnt * sizeof(double), cudaMemcpyDeviceToHost,
+                     c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  *count = (int)cnt;
+  return MG_OK;
+}
+
+int mg_is_graded(const mg_ctx* c) { return c && c->graded ? 1 : 0; }
+
 mg_status mg_workspace_size(const mg_ctx* c, size_t* bytes) {
   if (!c || !bytes) return MG_EINVAL;
   *bytes = c->ws_bytes;
@@ -1209,7 +1313,19 @@ mg_status mg_bind_workspace(mg_ctx* c, void* dptr, size_t bytes) {
   w.status = reinterpret_cast<int*>(b + ly.status);
   w.jac = reinterpret_cast<double*>(b + ly.jac);
   w.jac_count = ly.jac_count;
+  w.gjac = c->graded ? reinterpret_cast<double*>(b + ly.gjac) : nullptr;
+  w.gjac_line = ly.gjac_line;
+  w.gjac_coarse = ly.gjac_coarse;
   CK(cudaMemsetAsync(w.status, 0, 256, c->stream));
+  if (c->graded) {
+    // element widths and left ends per direction, read by the setup kernels
+    for (int d = 0; d < 3; ++d) {
+      CK(cudaMemcpyAsync(w.tab64 + c->gwid[d], c->wid[d].data(), c->ne[d] * sizeof(double), cudaMemcpyHostToDevice,
+                         c->stream));
+      CK(cudaMemcpyAsync(w.tab64 + c->gorg[d], c->org[d].data(), c->ne[d] * sizeof(double), cudaMemcpyHostToDevice,
+                         c->stream));
+    }
+  }
   CK(cudaMemsetAsync(w.scal, 0, kNumSlots * sizeof(double), c->stream));
   CK(launch_setup(c));
   int st = 0;
@@ -1255,6 +1371,7 @@ int mg_level_layers(const mg_ctx* c, int level) { return mg_level_layers_dir(c, 
 mg_status mg_vcycle_df64(mg_ctx* c, double* u, const double* f) {
   mg_status s = need_ready(c);
   if (s != MG_OK) return s;
+  if (c->graded) return fail(c, MG_EINVAL, "double-float kernels are not built for graded meshes");
   if (!u || !f || u == f) return fail(c, MG_EINVAL, "null or aliased vector");
   const int L = c->L;
   const int64_t N = c->lev[L].N;
@@ -1285,6 +1402,7 @@ mg_status mg_smooth_df64(mg_ctx* c, int level, double* u, const double* f, int n
 mg_status mg_apply_sipg_df64(mg_ctx* c, int level, const double* u, double* Au) {
   mg_status s = need_ready(c);
   if (s != MG_OK) return s;
+  if (c->graded) return fail(c, MG_EINVAL, "double-float kernels are not built for graded meshes");
   if (!check_level(c, level, false)) return MG_EINVAL;
   if (!u || !Au || u == Au) return fail(c, MG_EINVAL, "null or aliased vector");
   const int64_t N = c->lev[level].N;
@@ -1505,6 +1623,7 @@ mg_status mg_solve_batch(mg_ctx* const* ctxs, int count, double* const* u, const
     for (int j = 0; j < i; ++j)
       if (ctxs[j] == ctxs[i]) return fail(ctxs[0], MG_EINVAL, "a context appears twice in the batch");
     if (!ctxs[i]->ready) return fail(ctxs[0], MG_ENOTREADY, "workspace not bound");
+    if (ctxs[i]->graded) return fail(ctxs[0], MG_EINVAL, "graded meshes are solved one at a time");
   }
   mg_ctx* c0 = ctxs[0];
   const cudaStream_t s = c0->stream;

@@ -277,6 +277,12 @@ struct DirTables {
   int64_t ce, co, fe, fo, fsc;
   int64_t S, SW, lam, w;                      // m*m, m*m, m, m  (level >= 1)
   int64_t Q, qlam;                            // Ng*Ng, Ng       (level 0)
+  // Graded meshes (-1 on uniform ones), per element line e of this direction
+  // (n_d lines): gblk + 3 n^2 e: the rows of element e of the 1D matrix L,
+  // blocks L[e][e-1], L[e][e], L[e][e+1] (n x n, row-major); gmass + n e:
+  // (h_e / 2) w; level >= 1: gS / gSW + m^2 e, glam + m e: the eigenbasis of
+  // the subdomain line centred on element e (SW with the weights folded in).
+  int64_t gblk = -1, gmass = -1, gS = -1, gSW = -1, glam = -1;
 };
 
 struct LevelInfo {
@@ -323,6 +329,8 @@ struct Workspace {
   int* status = nullptr;       // device status word
   double* jac = nullptr;       // eigensolver scratch
   int64_t jac_count = 0;
+  double* gjac = nullptr;      // graded meshes: eigensolver scratch of the element lines
+  int64_t gjac_line = 0, gjac_coarse = 0;  // doubles per line block, per coarse block
 };
 
 }  // namespace mgdg
@@ -339,6 +347,11 @@ struct mg_ctx {
   mgdg::LevelInfo lev[mgdg::kMaxLevels];
   int Ng[3];               // coarse 1D sizes 2 n_d
   int coarse_null[3];      // index of the constant eigenvector per direction
+  // Graded mesh (mg_setup_graded): element widths per direction, and the
+  // table offsets of the widths and of the elements' left ends.
+  bool graded = false;
+  std::vector<double> wid[3], org[3];
+  int64_t gwid[3] = {-1, -1, -1}, gorg[3] = {-1, -1, -1};
   mgdg::Workspace ws;
   size_t ws_bytes;
   bool ready;
@@ -396,6 +409,26 @@ cudaError_t launch_setup(mg_ctx* c);
 cudaError_t launch_setup_coarse_tables(const double len[3], const int ne[3], double penalty, double* tab,
                                        const DirTables t[3], double* scratch, int64_t per_block, int* status,
                                        cudaStream_t s);
+
+// ---- graded meshes (setup.cu, graded.cu) ----
+// Tables of the element lines of every level and the graded coarse eigenbases.
+cudaError_t launch_setup_graded(mg_ctx* c);
+// out = A u (residual 0) or f - A u on level l from the per-line blocks.
+template <typename T>
+cudaError_t launch_gsipg(const mg_ctx* c, int l, const T* u, const T* f, T* out, int residual);
+// Subdomain corrections (gather + fast diagonalisation with per-line
+// eigenbases) into ws.corr, in the layout of launch_fdm.
+template <typename T>
+cudaError_t launch_gfdm(const mg_ctx* c, int l, const T* r);
+// u0 -= mean(u0) on level 0 (on a graded mesh the coarse solve's M-orthonormal
+// eigenbases give a solution whose Euclidean mean is not zero).
+template <typename T>
+cudaError_t launch_gmean_zero(const mg_ctx* c, T* u0);
+// out = f0 - mean(f0) in FP64 (level 0): the projection onto the range of A_0.
+template <typename T>
+cudaError_t launch_gcenter(const mg_ctx* c, const T* f0, double* out);
+cudaError_t launch_grhs(const mg_ctx* c, const double* f, double* b);
+cudaError_t launch_gcoords(const mg_ctx* c, int l, double* x, double* y, double* z);
 
 // ---- operator (sipg_kernels.cuh, instantiated in sipg_f64.cu / sipg_f32.cu / sipg_df64.cu) ----
 // out = mode==0 ? A u : f - A u, on level l, T = double | float.

@@ -470,6 +470,12 @@ const df64* table_of<df64>(const mg_ctx* c) { return c->ws.tabdf; }
 
 template <typename T>
 cudaError_t launch_fdm(const mg_ctx* c, int l, const T* r) {
+  if (c->graded) {
+    if constexpr (std::is_same<T, double>::value || std::is_same<T, float>::value)
+      return launch_gfdm<T>(c, l, r);
+    else
+      return cudaErrorNotSupported;
+  }
   const LevelInfo& lv = c->lev[l];
   if constexpr (std::is_same<T, float>::value) {
     if (lv.fdm_tc) {

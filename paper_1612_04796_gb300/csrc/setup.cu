@@ -496,6 +496,200 @@ __global__ void k_cast_tables(const double* src, float* dst, df64* dst_df, int64
   }
 }
 
+// ---- graded meshes: one eigenbasis per element line ----
+//
+// Element e of a line of widths h has the 1D matrix rows (Section 2, Eq. ip in
+// one dimension, each element with its own g = 2/h, each face with the
+// penalty of its smaller neighbour):
+//   L[e][e]   = (2/h_e) K + mu_r e_P e_P^T - (1/h_e)(e_P D_P + D_P^T e_P^T)
+//                         + mu_l e_0 e_0^T + (1/h_e)(e_0 D_0 + D_0^T e_0^T)
+//   L[e][e+1] = -mu_r e_P e_0^T - (1/h_{e+1}) e_P D_0 + (1/h_e) D_P^T e_0^T
+//   L[e][e-1] = -mu_l e_0 e_P^T + (1/h_{e-1}) e_0 D_P - (1/h_e) D_0^T e_P^T
+// with K = D^T diag(w) D, D_0 / D_P the first / last row of D, mu_l / mu_r
+// the penalties of the left / right face.  A subdomain line is not
+// reflection-symmetric any more, so its generalised eigenproblem is solved
+// whole (no even/odd split).
+
+struct GradedLine {
+  int level, dir, P, n, m, no, nd, first;  // first: index of the line's first block
+  DirTables t;
+  int64_t wid;                             // widths of the n_d elements (table offset)
+  double pen;                              // penalty factor
+};
+
+struct GradedBatch {
+  int count;                               // entries used
+  GradedLine g[kMaxLevels * 3];
+  int coarse_first;                        // first block of the three coarse blocks
+  int Ng[3];
+  DirTables tc[3];                         // level-0 tables (Q, qlam)
+  int64_t wid[3];
+  double pen;
+};
+
+// Entry (i, j) of the row block of an element of width h0 with neighbours of
+// widths hm (left) and hp (right); column element offset db in {-1, 0, 1}.
+__device__ double graded_entry(const double* D, const double* K, int n, double hm, double h0, double hp,
+                               double mu_l, double mu_r, int db, int i, int j) {
+  const int P = n - 1;
+  double v = 0.0;
+  if (db == 0) {
+    v = (2.0 / h0) * K[i * n + j];
+    if (i == P && j == P) v += mu_r;
+    if (i == 0 && j == 0) v += mu_l;
+    if (i == P) v -= D[P * n + j] / h0;
+    if (j == P) v -= D[P * n + i] / h0;
+    if (i == 0) v += D[0 * n + j] / h0;
+    if (j == 0) v += D[0 * n + i] / h0;
+  } else if (db == 1) {
+    if (i == P && j == 0) v -= mu_r;
+    if (i == P) v -= D[0 * n + j] / hp;
+    if (j == 0) v += D[P * n + i] / h0;
+  } else if (db == -1) {
+    if (i == 0 && j == P) v -= mu_l;
+    if (i == 0) v += D[P * n + j] / hm;
+    if (j == P) v -= D[0 * n + i] / h0;
+  }
+  return v;
+}
+
+__device__ __forceinline__ double face_mu(double pen, int P, double a, double b) {
+  return pen * P * (P + 1.0) / (2.0 * fmin(a, b));
+}
+
+// Symmetric generalised eigenproblem L S = M S Lambda (M diagonal > 0), the
+// whole m x m problem by Jacobi.  C (m*m) holds L on entry and is overwritten;
+// V: m*m scratch.  S[a][p] = entry a of eigenvector p, S^T M S = I.
+__device__ bool gen_eig_full(double* C, const double* M, int m, double* V, double* S, double* lam, double* sh_red,
+                             int* sh_p, int* sh_q, double* sh_c, double* sh_s) {
+  const int t = threadIdx.x, nt = blockDim.x;
+  for (int idx = t; idx < m * m; idx += nt) C[idx] /= sqrt(M[idx / m] * M[idx % m]);
+  __syncthreads();
+  const bool ok = jacobi(C, V, m, sh_red, sh_p, sh_q, sh_c, sh_s);
+  for (int idx = t; idx < m * m; idx += nt) S[idx] = V[idx] / sqrt(M[idx / m]);
+  for (int p = t; p < m; p += nt) lam[p] = C[p * m + p];
+  __syncthreads();
+  return ok;
+}
+
+struct GradedSmem {
+  double x[kMaxN], w[kMaxN], D[kMaxN * kMaxN], K[kMaxN * kMaxN];
+  double red[kSetupThreads];
+  int sp[kSetupThreads], sq[kSetupThreads];
+  double sc[kSetupThreads], ss[kSetupThreads];
+};
+
+__device__ void graded_basis(int P, GradedSmem& sm) {
+  const int t = threadIdx.x, nt = blockDim.x, n = P + 1;
+  if (t == 0) gll_nodes_dev(P, sm.x);
+  __syncthreads();
+  for (int i = t; i < n; i += nt) {
+    const double lp = legendre_value(P, sm.x[i]);
+    sm.w[i] = 2.0 / (P * (P + 1.0) * lp * lp);
+  }
+  for (int idx = t; idx < n * n; idx += nt) {
+    const int i = idx / n, j = idx % n;
+    double v;
+    if (i != j) v = legendre_value(P, sm.x[i]) / (legendre_value(P, sm.x[j]) * (sm.x[i] - sm.x[j]));
+    else if (i == 0) v = -P * (P + 1.0) / 4.0;
+    else if (i == P) v = P * (P + 1.0) / 4.0;
+    else v = 0.0;
+    sm.D[idx] = v;
+  }
+  __syncthreads();
+  for (int idx = t; idx < n * n; idx += nt) {
+    const int i = idx / n, j = idx % n;
+    double k = 0.0;
+    for (int a = 0; a < n; ++a) k += sm.w[a] * sm.D[a * n + i] * sm.D[a * n + j];
+    sm.K[idx] = k;
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kSetupThreads) k_setup_graded(GradedBatch b, double* tab, double* scratch,
+                                                                int64_t per_line, int64_t per_coarse, int* status) {
+  __shared__ GradedSmem sm;
+  const int t = threadIdx.x, nt = blockDim.x;
+  const int blk = blockIdx.x;
+  if (blk >= b.coarse_first) {
+    // periodic coarse line of the P = 1 level: Ng = 2 n_d nodes, index 2 e + i
+    const int d = blk - b.coarse_first;
+    const int Ng = b.Ng[d], nd = Ng / 2;
+    graded_basis(1, sm);
+    double* C = scratch + per_line * b.coarse_first + per_coarse * d;
+    double* V = C + (int64_t)Ng * Ng;
+    double* M = V + (int64_t)Ng * Ng;
+    const double* h = tab + b.wid[d];
+    for (int idx = t; idx < Ng * Ng; idx += nt) {
+      const int r = idx / Ng, c = idx % Ng;
+      const int er = r / 2, ir = r % 2, ec = c / 2, ic = c % 2;
+      int db = ec - er;
+      if (db == nd - 1) db = -1;
+      if (db == -(nd - 1)) db = 1;
+      double v = 0.0;
+      if (db >= -1 && db <= 1) {
+        const double hm = h[(er + nd - 1) % nd], h0 = h[er], hp = h[(er + 1) % nd];
+        v = graded_entry(sm.D, sm.K, 2, hm, h0, hp, face_mu(b.pen, 1, hm, h0), face_mu(b.pen, 1, h0, hp), db, ir,
+                         ic);
+      }
+      C[idx] = v;
+    }
+    for (int r = t; r < Ng; r += nt) M[r] = 0.5 * h[r / 2] * sm.w[r % 2];
+    __syncthreads();
+    const bool ok = gen_eig_full(C, M, Ng, V, tab + b.tc[d].Q, tab + b.tc[d].qlam, sm.red, sm.sp, sm.sq, sm.sc,
+                                 sm.ss);
+    if (!ok && t == 0) atomicExch(status, kDevNoConv);
+    return;
+  }
+  int gi = 0;
+  while (gi + 1 < b.count && blk >= b.g[gi + 1].first) ++gi;
+  const GradedLine& g = b.g[gi];
+  const int e = blk - g.first, nd = g.nd, n = g.n, P = g.P, m = g.m, no = g.no;
+  graded_basis(P, sm);
+  const double* h = tab + g.wid;
+  // widths of the elements e-2 .. e+2 and the penalties of the four faces between them
+  double hw[5], mu[4];
+  for (int k = 0; k < 5; ++k) hw[k] = h[((e + k - 2) % nd + nd) % nd];
+  for (int k = 0; k < 4; ++k) mu[k] = face_mu(g.pen, P, hw[k], hw[k + 1]);
+  // rows of element e: L[e][e-1], L[e][e], L[e][e+1]; mass (h_e / 2) w
+  double* blk3 = tab + g.t.gblk + (int64_t)e * 3 * n * n;
+  for (int idx = t; idx < 3 * n * n; idx += nt) {
+    const int db = idx / (n * n) - 1, i = (idx / n) % n, j = idx % n;
+    blk3[idx] = graded_entry(sm.D, sm.K, n, hw[1], hw[2], hw[3], mu[1], mu[2], db, i, j);
+  }
+  for (int i = t; i < n; i += nt) tab[g.t.gmass + (int64_t)e * n + i] = 0.5 * hw[2] * sm.w[i];
+  if (g.level == 0) return;
+  // subdomain line centred on e: last `no` nodes of e-1, element e, first `no` nodes of e+1
+  double* C = scratch + per_line * blk;
+  double* V = C + (int64_t)m * m;
+  double* M = V + (int64_t)m * m;
+  auto node_of = [&](int a, int* de, int* ii) {
+    if (a < no) { *de = -1; *ii = n - no + a; }
+    else if (a < no + n) { *de = 0; *ii = a - no; }
+    else { *de = 1; *ii = a - no - n; }
+  };
+  for (int idx = t; idx < m * m; idx += nt) {
+    int a = idx / m, c = idx % m, da, ia, dc, ic;
+    node_of(a, &da, &ia);
+    node_of(c, &dc, &ic);
+    // row element e + da: widths hw[1 + da .. 3 + da], faces mu[1 + da], mu[2 + da]
+    C[idx] = graded_entry(sm.D, sm.K, n, hw[1 + da], hw[2 + da], hw[3 + da], mu[1 + da], mu[2 + da], dc - da, ia,
+                          ic);
+  }
+  for (int a = t; a < m; a += nt) {
+    int da, ia;
+    node_of(a, &da, &ia);
+    M[a] = 0.5 * hw[2 + da] * sm.w[ia];
+  }
+  __syncthreads();
+  double* S = tab + g.t.gS + (int64_t)e * m * m;
+  const bool ok = gen_eig_full(C, M, m, V, S, tab + g.t.glam + (int64_t)e * m, sm.red, sm.sp, sm.sq, sm.sc, sm.ss);
+  if (!ok && t == 0) atomicExch(status, kDevNoConv);
+  // weights in reference coordinates: the level's table w, folded into SW
+  double* SW = tab + g.t.gSW + (int64_t)e * m * m;
+  for (int idx = t; idx < m * m; idx += nt) SW[idx] = tab[g.t.w + idx / m] * S[idx];
+}
+
 }  // namespace
 
 cudaError_t launch_setup_coarse_tables(const double len[3], const int ne[3], double penalty, double* tab,
@@ -577,7 +771,43 @@ cudaError_t launch_setup(mg_ctx* c) {
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
+  if (c->graded && (e = launch_setup_graded(c)) != cudaSuccess) return e;
   k_cast_tables<<<256, 256, 0, s>>>(c->ws.tab64, c->ws.tab32, c->ws.tabdf, c->ws.tab_count);
+  c->nlaunch += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_setup_graded(mg_ctx* c) {
+  GradedBatch b;
+  b.count = 0;
+  int blocks = 0;
+  for (int l = 0; l <= c->L; ++l) {
+    const LevelInfo& lv = c->lev[l];
+    for (int d = 0; d < 3; ++d) {
+      GradedLine& g = b.g[b.count++];
+      g.level = l;
+      g.dir = d;
+      g.P = lv.P;
+      g.n = lv.n;
+      g.m = lv.m[d];
+      g.no = lv.no[d];
+      g.nd = c->ne[d];
+      g.first = blocks;
+      g.t = lv.t[d];
+      g.wid = c->gwid[d];
+      g.pen = c->penalty;
+      blocks += c->ne[d];
+    }
+  }
+  b.coarse_first = blocks;
+  for (int d = 0; d < 3; ++d) {
+    b.Ng[d] = c->Ng[d];
+    b.tc[d] = c->lev[0].t[d];
+    b.wid[d] = c->gwid[d];
+  }
+  b.pen = c->penalty;
+  k_setup_graded<<<blocks + 3, kSetupThreads, 0, c->stream>>>(b, c->ws.tab64, c->ws.gjac, c->ws.gjac_line,
+                                                               c->ws.gjac_coarse, c->ws.status);
   c->nlaunch += 1;
   return cudaGetLastError();
 }

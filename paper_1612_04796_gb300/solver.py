@@ -32,12 +32,15 @@ class MGSolver:
     """Polynomial multigrid for the SIPG Poisson problem on a periodic box.
 
     lengths (lx, ly, lz), counts (nx, ny, nz), order P (power of two), penalty
-    mu/mu_min (paper: 2), overlap N_O node layers; see include/mgdg.h."""
+    mu/mu_min (paper: 2), overlap N_O node layers; see include/mgdg.h.
+    widths: three sequences of element widths for a graded mesh
+    (mg_setup_graded); lengths and counts are then taken from them and may be
+    None."""
 
     def __init__(self, lengths, counts, P, penalty=2.0, overlap=1, precision="fp64", overlap_mode="layers",
                  overlap_frac=0.08, weight_profile="quintic", ns_pre=1, ns_post=1, ns_growth=1, device="cuda",
                  stream=None, tensor_cores=False, outer_df64=False, weight_delta="default", autotune=False,
-                 fdm_bf16=False, fdm_operands="fp32", persistent="auto"):
+                 fdm_bf16=False, fdm_operands="fp32", persistent="auto", widths=None):
         self.lib = load_library()
         self.device = torch.device(device)
         if self.device.type == "cuda" and self.device.index is None:
@@ -61,11 +64,22 @@ class MGSolver:
         opts.stream = ctypes.c_void_p(self.stream.cuda_stream)
         self.opts = opts
         ctx = ctypes.c_void_p()
-        st = self.lib.mg_setup(float(lengths[0]), float(lengths[1]), float(lengths[2]), int(counts[0]),
-                               int(counts[1]), int(counts[2]), int(P), float(penalty), int(overlap),
-                               ctypes.byref(opts), ctypes.byref(ctx))
-        if st != 0:
-            raise MGError(st, "mg_setup rejected the arguments")
+        if widths is not None:
+            self.widths = tuple(np.ascontiguousarray(w, dtype=np.float64) for w in widths)
+            counts = tuple(len(w) for w in self.widths)
+            lengths = tuple(float(w.sum()) for w in self.widths)
+            hp = [w.ctypes.data_as(ctypes.c_void_p) for w in self.widths]
+            st = self.lib.mg_setup_graded(hp[0], hp[1], hp[2], int(counts[0]), int(counts[1]), int(counts[2]), int(P),
+                                          float(penalty), int(overlap), ctypes.byref(opts), ctypes.byref(ctx))
+            if st != 0:
+                raise MGError(st, "mg_setup_graded rejected the arguments")
+        else:
+            self.widths = None
+            st = self.lib.mg_setup(float(lengths[0]), float(lengths[1]), float(lengths[2]), int(counts[0]),
+                                   int(counts[1]), int(counts[2]), int(P), float(penalty), int(overlap),
+                                   ctypes.byref(opts), ctypes.byref(ctx))
+            if st != 0:
+                raise MGError(st, "mg_setup rejected the arguments")
         self.ctx = ctx
         self.P = int(P)
         self.lengths = tuple(float(v) for v in lengths)
@@ -297,6 +311,15 @@ class MGSolver:
         cnt = ctypes.c_int()
         self._check(self.lib.mg_get_table(self.ctx, int(level), int(direction), int(what),
                                           buf.ctypes.data_as(ctypes.c_void_p), cap, ctypes.byref(cnt)))
+        return buf[:cnt.value].copy()
+
+    def get_line_table(self, level, direction, line, what):
+        """Copy a table of one element line of a graded mesh (see mg_get_line_table)."""
+        cap = 1 << 16
+        buf = np.zeros(cap)
+        cnt = ctypes.c_int()
+        self._check(self.lib.mg_get_line_table(self.ctx, int(level), int(direction), int(line), int(what),
+                                               buf.ctypes.data_as(ctypes.c_void_p), cap, ctypes.byref(cnt)))
         return buf[:cnt.value].copy()
 
 

@@ -170,3 +170,53 @@ def test_kernel_variant_query(lib):
     assert lib.mg_level_kernel_variant(ctx, 4, 0) == -1
     assert lib.mg_level_kernel_variant(ctx, 3, 0) == 0  # before binding: the defaults
     lib.mg_destroy(ctx)
+
+
+def _setup_graded(lib, widths, P=4, overlap=1, **kw):
+    import numpy as np
+    opts = MgOpts()
+    lib.mg_default_opts(ctypes.byref(opts))
+    for k, v in kw.items():
+        setattr(opts, k, v)
+    ws = [np.ascontiguousarray(w, dtype=np.float64) for w in widths]
+    ctx = ctypes.c_void_p()
+    st = lib.mg_setup_graded(*(w.ctypes.data_as(ctypes.c_void_p) for w in ws), len(ws[0]), len(ws[1]), len(ws[2]),
+                             P, 2.0, overlap, ctypes.byref(opts), ctypes.byref(ctx))
+    return st, ctx
+
+
+def test_graded_setup_host_validation(lib):
+    """mg_setup_graded: valid widths give a context flagged as graded whose
+    workspace holds the per-line tables (more than the uniform context of the
+    same counts); invalid widths, sizes and unsupported options are refused
+    before any CUDA call."""
+    w = [[0.2, 0.5, 0.3], [0.4, 0.4, 0.2, 0.5], [1.0, 2.0, 0.5]]
+    st, ctx = _setup_graded(lib, w, P=8)
+    assert st == 0 and lib.mg_is_graded(ctx) == 1
+    gsize = ctypes.c_size_t()
+    assert lib.mg_workspace_size(ctx, ctypes.byref(gsize)) == 0
+    assert lib.mg_num_dofs(ctx, 3) == 36 * 729
+    st2, uctx = _setup(lib, P=8, counts=(3, 4, 3))
+    usize = ctypes.c_size_t()
+    assert st2 == 0 and lib.mg_is_graded(uctx) == 0
+    lib.mg_workspace_size(uctx, ctypes.byref(usize))
+    assert gsize.value > usize.value
+    buf = (ctypes.c_double * 16)()
+    cnt = ctypes.c_int()
+    assert lib.mg_get_line_table(ctx, 3, 0, 0, 0, buf, 16, ctypes.byref(cnt)) == 5  # MG_ENOTREADY
+    lib.mg_destroy(ctx)
+    lib.mg_destroy(uctx)
+    bad = [
+        ([[0.2, -0.5, 0.3], w[1], w[2]], {}),
+        ([[0.2, float("nan"), 0.3], w[1], w[2]], {}),
+        ([[0.5, 0.5], w[1], w[2]], {}),
+        ([[0.01] * 257, w[1], w[2]], {}),
+        (w, {"precision": 2}),
+        (w, {"overlap_mode": 1}),
+        (w, {"precision": 1, "fdm_tensor_cores": 1}),
+        (w, {"precision": 1, "outer_df64": 1}),
+        (w, {"autotune": 1}),
+    ]
+    for widths, kw in bad:
+        st, c = _setup_graded(lib, widths, **kw)
+        assert st == 1 and not c.value, (widths if not kw else kw)
