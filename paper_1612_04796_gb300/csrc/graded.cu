@@ -403,6 +403,8 @@ cudaError_t launch_gsipg(const mg_ctx* c, int l, const T* u, const T* f, T* out,
 
 template <typename T>
 cudaError_t launch_gfdm(const mg_ctx* c, int l, const T* r) {
+  const cudaError_t ef = launch_gfdm_fixed<T>(c, l, r);
+  if (ef != cudaErrorNotSupported) return ef;
   const LevelInfo& lv = c->lev[l];
   GFdmArgs<T> a;
   a.tab = gtable<T>(c);

@@ -420,6 +420,10 @@ cudaError_t launch_gsipg(const mg_ctx* c, int l, const T* u, const T* f, T* out,
 // eigenbases) into ws.corr, in the layout of launch_fdm.
 template <typename T>
 cudaError_t launch_gfdm(const mg_ctx* c, int l, const T* r);
+// The same with compile-time widths (graded_fdm.cu): cubic odd m <= 25;
+// cudaErrorNotSupported otherwise.
+template <typename T>
+cudaError_t launch_gfdm_fixed(const mg_ctx* c, int l, const T* r);
 // u0 -= mean(u0) on level 0 (on a graded mesh the coarse solve's M-orthonormal
 // eigenbases give a solution whose Euclidean mean is not zero).
 template <typename T>
