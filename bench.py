@@ -17,7 +17,8 @@ for the fast diagonalisation, HBM for the residual and the scatter); the
 anisotropic 48x8x8, P = 16 box (mixed MG-CG, N_O = 1, 2, 4, and N_O = 4 with
 the double-float outer iteration; key "c3"); the 4^3, P = 32 cube with the
 smoother's contractions on the tensor cores and on the CUDA cores (key "c4");
-the 512-request serving stream
+a graded 16^3, P = 8 mesh (element widths varying by a factor 4 along every
+axis: FP64 MG and mixed MG-CG; key "graded"); the 512-request serving stream
 (N_O = 1 and 4, and N_O = 4 without grouped launches; key "serving"); and the
 FP64 CPU oracle timed on the host cores on a bounded sample of the workload.
 

@@ -114,6 +114,130 @@ __global__ void __launch_bounds__(256) k_gsipg(GOpArgs<T> a) {
   }
 }
 
+// The same operator with each element staged in shared memory: one block per
+// element (grid-stride), its n^3 values of u, the nine n x n row blocks of its
+// three lines and its masses loaded once; the diagonal-block products read
+// shared memory, the coupling terms the neighbours' values in global memory.
+template <typename T, int N>
+__global__ void __launch_bounds__(256) k_gsipg_s(GOpArgs<T> a) {
+  pdl_entry();
+  constexpr int N2 = N * N, N3 = N2 * N, P = N - 1;
+  extern __shared__ __align__(16) unsigned char gs_raw[];
+  T* su = reinterpret_cast<T*>(gs_raw);  // N^3
+  T* sB = su + N3;                       // [dir][block][N^2]: L[e][e-1], L[e][e], L[e][e+1]
+  T* sm = sB + 9 * N2;                   // [dir][N]
+  for (int64_t e = blockIdx.x; e < a.Ne; e += gridDim.x) {
+    const int e32 = (int)e, exy = e32 / a.nx;
+    const int ex = e32 - exy * a.nx, ey = exy % a.ny, ez = exy / a.ny;
+    const int64_t bo[3] = {a.blk[0] + (int64_t)ex * 3 * N2, a.blk[1] + (int64_t)ey * 3 * N2,
+                           a.blk[2] + (int64_t)ez * 3 * N2};
+    const int64_t mo[3] = {a.mass[0] + (int64_t)ex * N, a.mass[1] + (int64_t)ey * N, a.mass[2] + (int64_t)ez * N};
+    __syncthreads();  // the previous element's values are no longer read
+    for (int q = threadIdx.x; q < N3; q += blockDim.x) su[q] = a.u[e * N3 + q];
+    for (int q = threadIdx.x; q < 9 * N2; q += blockDim.x) {
+      const int d = q / (3 * N2);
+      sB[q] = a.tab[(d == 0 ? bo[0] : (d == 1 ? bo[1] : bo[2])) + (q - d * 3 * N2)];
+    }
+    for (int q = threadIdx.x; q < 3 * N; q += blockDim.x) {
+      const int d = q / N;
+      sm[q] = a.tab[(d == 0 ? mo[0] : (d == 1 ? mo[1] : mo[2])) + (q - d * N)];
+    }
+    __syncthreads();
+    const int64_t rowy = (int64_t)a.nx * (ey + (int64_t)a.ny * ez);
+    const int64_t exl = (gwrap(ex - 1, a.nx) + rowy) * N3, exr = (gwrap(ex + 1, a.nx) + rowy) * N3;
+    const int64_t ezrow = (int64_t)a.nx * a.ny * ez;
+    const int64_t eyl = (ex + (int64_t)a.nx * gwrap(ey - 1, a.ny) + ezrow) * N3;
+    const int64_t eyr = (ex + (int64_t)a.nx * gwrap(ey + 1, a.ny) + ezrow) * N3;
+    const int64_t exy0 = ex + (int64_t)a.nx * ey, plane = (int64_t)a.nx * a.ny;
+    const int64_t ezl = (exy0 + plane * gwrap(ez - 1, a.nz)) * N3, ezr = (exy0 + plane * gwrap(ez + 1, a.nz)) * N3;
+    for (int q = threadIdx.x; q < N3; q += blockDim.x) {
+      const int i = q % N, j = (q / N) % N, k = q / N2;
+      T sx, sy, sz;
+      {  // x lines: stride 1, base N (j + N k)
+        const T* Bm = sB;
+        const T* B0 = sB + N2;
+        const T* Bp = sB + 2 * N2;
+        const int b = N * (j + N * k);
+        T acc = 0;
+#pragma unroll
+        for (int t = 0; t < N; ++t) acc += B0[i * N + t] * su[b + t];
+        if (i == 0) {
+#pragma unroll
+          for (int t = 0; t < N; ++t) acc += Bm[t] * a.u[exl + b + t];
+        } else {
+          acc += Bm[i * N + P] * a.u[exl + b + P];
+        }
+        if (i == P) {
+#pragma unroll
+          for (int t = 0; t < N; ++t) acc += Bp[P * N + t] * a.u[exr + b + t];
+        } else {
+          acc += Bp[i * N] * a.u[exr + b];
+        }
+        sx = acc;
+      }
+      {  // y lines: stride N, base i + N^2 k
+        const T* Bm = sB + 3 * N2;
+        const T* B0 = sB + 4 * N2;
+        const T* Bp = sB + 5 * N2;
+        const int b = i + N2 * k;
+        T acc = 0;
+#pragma unroll
+        for (int t = 0; t < N; ++t) acc += B0[j * N + t] * su[b + t * N];
+        if (j == 0) {
+#pragma unroll
+          for (int t = 0; t < N; ++t) acc += Bm[t] * a.u[eyl + b + t * N];
+        } else {
+          acc += Bm[j * N + P] * a.u[eyl + b + P * N];
+        }
+        if (j == P) {
+#pragma unroll
+          for (int t = 0; t < N; ++t) acc += Bp[P * N + t] * a.u[eyr + b + t * N];
+        } else {
+          acc += Bp[j * N] * a.u[eyr + b];
+        }
+        sy = acc;
+      }
+      {  // z lines: stride N^2, base i + N j
+        const T* Bm = sB + 6 * N2;
+        const T* B0 = sB + 7 * N2;
+        const T* Bp = sB + 8 * N2;
+        const int b = i + N * j;
+        T acc = 0;
+#pragma unroll
+        for (int t = 0; t < N; ++t) acc += B0[k * N + t] * su[b + t * N2];
+        if (k == 0) {
+#pragma unroll
+          for (int t = 0; t < N; ++t) acc += Bm[t] * a.u[ezl + b + t * N2];
+        } else {
+          acc += Bm[k * N + P] * a.u[ezl + b + P * N2];
+        }
+        if (k == P) {
+#pragma unroll
+          for (int t = 0; t < N; ++t) acc += Bp[P * N + t] * a.u[ezr + b + t * N2];
+        } else {
+          acc += Bp[k * N] * a.u[ezr + b];
+        }
+        sz = acc;
+      }
+      const T mx = sm[i], my = sm[N + j], mz = sm[2 * N + k];
+      const T au = sx * my * mz + sy * mx * mz + sz * mx * my;
+      const int64_t dof = e * N3 + q;
+      a.out[dof] = a.residual ? a.f[dof] - au : au;
+    }
+  }
+}
+
+template <typename T, int N>
+cudaError_t launch_gsipg_s(const mg_ctx* c, const GOpArgs<T>& a) {
+  constexpr size_t smem = sizeof(T) * (N * N * N + 9 * N * N + 3 * N);
+  static std::atomic<size_t> smem_set{48 * 1024};
+  const cudaError_t e = allow_smem((const void*)k_gsipg_s<T, N>, smem, smem_set);
+  if (e != cudaSuccess) return e;
+  const int blocks = (int)std::min<int64_t>(a.Ne, 152 * 8);
+  launch_pdl(k_gsipg_s<T, N>, blocks, 256, smem, c->stream, a);
+  return cudaGetLastError();
+}
+
 template <typename T>
 struct GFdmArgs {
   const T* tab;
@@ -255,6 +379,7 @@ __global__ void __launch_bounds__(1024) k_gmean_zero(T* u, int64_t n) {
   pdl_entry();
   __shared__ double sh[1024];
   double s = 0.0;
+#pragma unroll 8
   for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += (double)u[i];
   sh[threadIdx.x] = s;
   __syncthreads();
@@ -272,6 +397,7 @@ __global__ void __launch_bounds__(1024) k_gcenter(const T* __restrict__ f, doubl
   pdl_entry();
   __shared__ double sh[1024];
   double s = 0.0;
+#pragma unroll 8
   for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += (double)f[i];
   sh[threadIdx.x] = s;
   __syncthreads();
@@ -389,6 +515,12 @@ cudaError_t launch_gsipg(const mg_ctx* c, int l, const T* u, const T* f, T* out,
   }
   const int blocks = ggrid(lv.N, 256);
   c->nlaunch += 1;
+  switch (lv.n) {
+    case 5: return launch_gsipg_s<T, 5>(c, a);
+    case 9: return launch_gsipg_s<T, 9>(c, a);
+    case 17: return launch_gsipg_s<T, 17>(c, a);
+    default: break;
+  }
   switch (lv.n) {
     case 2: launch_pdl(k_gsipg<T, 2>, blocks, 256, 0, c->stream, a); break;
     case 3: launch_pdl(k_gsipg<T, 3>, blocks, 256, 0, c->stream, a); break;

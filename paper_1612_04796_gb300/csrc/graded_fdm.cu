@@ -47,33 +47,91 @@ struct GFdmMArgs {
 template <typename T, int M>
 struct GShape {
   static constexpr int spb = M * M >= 100 ? 1 : 256 / (M * M);
-  static constexpr size_t table_vals = 6 * M * M + 3 * M;  // per subdomain: S, SW, lam of three lines
+  // row stride of the staged factors: FP32 rows padded to a multiple of four
+  // (zeros) for 16-byte shared-memory loads, FP64 rows unpadded
+  static constexpr int RS = std::is_same<T, float>::value ? (M + 3) / 4 * 4 : M;
+  static constexpr int MR = M * RS;                                  // one staged factor
+  static constexpr size_t table_vals = 6 * MR + (3 * M + 3) / 4 * 4;  // per subdomain: S, SW, lam of three lines
   static constexpr size_t table_bytes = sizeof(T) * spb * table_vals;
   static constexpr size_t tile_bytes = sizeof(T) * spb * M * M * M;
   static constexpr bool smem_tile = table_bytes + tile_bytes <= 200 * 1024;
   static constexpr size_t smem = table_bytes + (smem_tile ? tile_bytes : 0);
 };
 
+// y_p = sum_a S[a][p] x_a (S staged with row stride RS)
+template <typename T, int M>
+__device__ __forceinline__ void gfwd_reg(const T (&x)[M], const T* __restrict__ S, T (&y)[M]) {
+  constexpr int RS = GShape<T, M>::RS;
+  if constexpr (std::is_same<T, float>::value) {
+    // four outputs per 16-byte load of a factor row
+#pragma unroll
+    for (int g = 0; g < RS / 4; ++g) {
+      float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int a = 0; a < M; ++a) {
+        const float4 s4 = *reinterpret_cast<const float4*>(S + a * RS + 4 * g);
+        acc.x += s4.x * x[a];
+        acc.y += s4.y * x[a];
+        acc.z += s4.z * x[a];
+        acc.w += s4.w * x[a];
+      }
+      y[4 * g] = acc.x;
+      if (4 * g + 1 < M) y[4 * g + 1 < M ? 4 * g + 1 : 0] = acc.y;
+      if (4 * g + 2 < M) y[4 * g + 2 < M ? 4 * g + 2 : 0] = acc.z;
+      if (4 * g + 3 < M) y[4 * g + 3 < M ? 4 * g + 3 : 0] = acc.w;
+    }
+  } else {
+#pragma unroll
+    for (int p = 0; p < M; ++p) {
+      T acc = S[p] * x[0];
+#pragma unroll
+      for (int a = 1; a < M; ++a) acc += S[a * RS + p] * x[a];
+      y[p] = acc;
+    }
+  }
+}
+
 // y_p = sum_a S[a][p] x_a, written to out[p * os]
 template <typename T, int M>
 __device__ __forceinline__ void gfwd(const T (&x)[M], const T* __restrict__ S, T* out, int os) {
+  if constexpr (std::is_same<T, float>::value) {
+    T y[M];
+    gfwd_reg<T, M>(x, S, y);
 #pragma unroll
-  for (int p = 0; p < M; ++p) {
-    T acc = S[p] * x[0];
+    for (int p = 0; p < M; ++p) out[p * os] = y[p];
+  } else {
+    // each output stored as soon as it is formed (fewer live registers)
 #pragma unroll
-    for (int a = 1; a < M; ++a) acc += S[a * M + p] * x[a];
-    out[p * os] = acc;
+    for (int p = 0; p < M; ++p) {
+      T acc = S[p] * x[0];
+#pragma unroll
+      for (int a = 1; a < M; ++a) acc += S[a * M + p] * x[a];
+      out[p * os] = acc;
+    }
   }
 }
 
 // x_a = sum_p SW[a][p] v_p, written to out[a * os]
 template <typename T, int M>
 __device__ __forceinline__ void gbwd(const T (&v)[M], const T* __restrict__ SW, T* out, int os) {
+  constexpr int RS = GShape<T, M>::RS;
 #pragma unroll
   for (int a = 0; a < M; ++a) {
-    T acc = SW[a * M] * v[0];
+    T acc = 0;
+    if constexpr (std::is_same<T, float>::value) {
 #pragma unroll
-    for (int p = 1; p < M; ++p) acc += SW[a * M + p] * v[p];
+      for (int g = 0; g < RS / 4; ++g) {
+        const float4 s4 = *reinterpret_cast<const float4*>(SW + a * RS + 4 * g);
+        acc += s4.x * v[4 * g];
+        if (4 * g + 1 < M) acc += s4.y * v[4 * g + 1 < M ? 4 * g + 1 : 0];
+        if (4 * g + 2 < M) acc += s4.z * v[4 * g + 2 < M ? 4 * g + 2 : 0];
+        if (4 * g + 3 < M) acc += s4.w * v[4 * g + 3 < M ? 4 * g + 3 : 0];
+      }
+    } else {
+      acc = SW[a * RS] * v[0];
+#pragma unroll
+      for (int p = 1; p < M; ++p) acc += SW[a * RS + p] * v[p];
+    }
     out[a * os] = acc;
   }
 }
@@ -82,10 +140,11 @@ template <typename T, int M>
 __global__ void __launch_bounds__(256) k_gfdm_m(GFdmMArgs<T> a) {
   pdl_entry();
   constexpr int M2 = M * M, M3 = M2 * M;
+  constexpr int RS = GShape<T, M>::RS, MR = GShape<T, M>::MR;
   constexpr int TV = (int)GShape<T, M>::table_vals;
   constexpr bool kSmemTile = GShape<T, M>::smem_tile;
   extern __shared__ __align__(16) unsigned char gm_raw[];
-  T* sTab = reinterpret_cast<T*>(gm_raw);  // spb x (S[3], SW[3], lam[3])
+  T* sTab = reinterpret_cast<T*>(gm_raw);  // spb x (S[3], SW[3] with row stride RS, lam[3])
   T* sTile = sTab + a.spb * TV;            // spb M^3 (if kSmemTile)
   const int n = a.n, no = a.no, n3 = n * n * n, spb = a.spb;
   const int lines = spb * M2;
@@ -97,15 +156,18 @@ __global__ void __launch_bounds__(256) k_gfdm_m(GFdmMArgs<T> a) {
       if (s >= a.Ne) continue;
       const int s32 = (int)s, sxy = s32 / a.nx;
       const int lx = s32 - sxy * a.nx, ly = sxy % a.ny, lz = sxy / a.ny;
-      T v;
-      if (q < 6 * M2) {
-        const int d = q / (2 * M2), r = q - d * 2 * M2;
+      T v = 0;
+      if (q < 6 * MR) {
+        const int d = q / (2 * MR), r = q - d * 2 * MR;
+        const int wsw = r >= MR, rr = r - wsw * MR, row = rr / RS, col = rr - row * RS;
         const int64_t ld = d == 0 ? lx : (d == 1 ? ly : lz);
-        const int64_t o = r < M2 ? (d == 0 ? a.S[0] : (d == 1 ? a.S[1] : a.S[2])) + ld * M2 + r
-                                 : (d == 0 ? a.SW[0] : (d == 1 ? a.SW[1] : a.SW[2])) + ld * M2 + r - M2;
-        v = a.tab[o];
-      } else {
-        const int d = (q - 6 * M2) / M, r = (q - 6 * M2) - d * M;
+        if (col < M) {
+          const int64_t base = wsw ? (d == 0 ? a.SW[0] : (d == 1 ? a.SW[1] : a.SW[2]))
+                                   : (d == 0 ? a.S[0] : (d == 1 ? a.S[1] : a.S[2]));
+          v = a.tab[base + ld * M2 + row * M + col];
+        }
+      } else if (q < 6 * MR + 3 * M) {
+        const int d = (q - 6 * MR) / M, r = (q - 6 * MR) - d * M;
         const int64_t ld = d == 0 ? lx : (d == 1 ? ly : lz);
         v = a.tab[(d == 0 ? a.lam[0] : (d == 1 ? a.lam[1] : a.lam[2])) + ld * M + r];
       }
@@ -145,7 +207,7 @@ __global__ void __launch_bounds__(256) k_gfdm_m(GFdmMArgs<T> a) {
       T x[M];
 #pragma unroll
       for (int t = 0; t < M; ++t) x[t] = line[t * M];
-      gfwd<T, M>(x, sTab + k * TV + 2 * M2, line, M);
+      gfwd<T, M>(x, sTab + k * TV + 2 * MR, line, M);
     }
     __syncthreads();
     // pass 3: forward along z, divide by lam_x + lam_y + lam_z, backward along z
@@ -155,20 +217,16 @@ __global__ void __launch_bounds__(256) k_gfdm_m(GFdmMArgs<T> a) {
       if (s >= a.Ne) continue;
       const int l2 = ln - k * M2;
       const T* tb = sTab + k * TV;
-      const T* lam = tb + 6 * M2;
+      const T* lam = tb + 6 * MR;
       const T lxy = lam[l2 % M] + lam[M + l2 / M];
       T* line = (kSmemTile ? sTile + k * M3 : a.corr + s * (int64_t)M3) + l2;
       T x[M], y[M];
 #pragma unroll
       for (int t = 0; t < M; ++t) x[t] = line[t * M2];
+      gfwd_reg<T, M>(x, tb + 4 * MR, y);
 #pragma unroll
-      for (int p = 0; p < M; ++p) {
-        T acc = tb[4 * M2 + p] * x[0];
-#pragma unroll
-        for (int q = 1; q < M; ++q) acc += tb[4 * M2 + q * M + p] * x[q];
-        y[p] = acc / (lxy + lam[2 * M + p]);
-      }
-      gbwd<T, M>(y, tb + 5 * M2, line, M2);
+      for (int p = 0; p < M; ++p) y[p] = y[p] / (lxy + lam[2 * M + p]);
+      gbwd<T, M>(y, tb + 5 * MR, line, M2);
     }
     __syncthreads();
     // pass 4: backward along y
@@ -181,7 +239,7 @@ __global__ void __launch_bounds__(256) k_gfdm_m(GFdmMArgs<T> a) {
       T v[M];
 #pragma unroll
       for (int t = 0; t < M; ++t) v[t] = line[t * M];
-      gbwd<T, M>(v, sTab + k * TV + 3 * M2, line, M);
+      gbwd<T, M>(v, sTab + k * TV + 3 * MR, line, M);
     }
     __syncthreads();
     // pass 5: backward along x (weights folded into SW), into the correction buffer
@@ -194,7 +252,7 @@ __global__ void __launch_bounds__(256) k_gfdm_m(GFdmMArgs<T> a) {
       T v[M];
 #pragma unroll
       for (int t = 0; t < M; ++t) v[t] = line[t];
-      gbwd<T, M>(v, sTab + k * TV + M2, a.corr + s * (int64_t)M3 + M * l2, 1);
+      gbwd<T, M>(v, sTab + k * TV + MR, a.corr + s * (int64_t)M3 + M * l2, 1);
     }
     __syncthreads();
   }

@@ -229,14 +229,15 @@ def test_graded_smooth_many_subdomains_per_block(gsolver):
     assert rel_err(host(ut) - u, ref) < FP64_TOL
 
 
-def test_graded_smooth_fp32(gsolver):
+@pytest.mark.parametrize("P,overlap", [(4, 1), (8, 2)])
+def test_graded_smooth_fp32(gsolver, P, overlap):
     import torch
     widths = mesh_widths((3, 4, 3))
-    P = 4
-    s = gsolver(widths, P, 1)
+    s = gsolver(widths, P, overlap)
     mesh = Mesh(widths=widths)
     A = assemble(mesh, P)
-    sm = SchwarzSmoother(A, mesh, P, 1, layer_delta(P, 1))
+    no = s.layers(s.L)
+    sm = SchwarzSmoother(A, mesh, P, no, layer_delta(P, no))
     u = inputs.gaussian(A.shape[0], 8).astype(np.float32).astype(np.float64)
     f = weak_rhs(mesh, P, inputs.gaussian(A.shape[0], 9)).astype(np.float32).astype(np.float64)
     ref = sm.correction(f - A @ u)
@@ -314,6 +315,23 @@ def test_graded_mixed_precision_reaches_fp64_tolerance(gsolver):
     assert rel_err(u, uo) < 1e-7
 
 
+def test_graded_vcycle_fp32(gsolver):
+    """The FP32 hierarchy's V-cycle on a graded mesh equals the FP64 oracle's
+    cycle to FP32 accuracy."""
+    import torch
+    widths = mesh_widths((3, 3, 4))
+    P = 8
+    s = gsolver(widths, P, 1, precision="mixed")
+    mesh = Mesh(widths=widths)
+    H = Hierarchy(mesh, P, n_o=1)
+    u = inputs.gaussian(H.A.shape[0], 30).astype(np.float32).astype(np.float64)
+    f = weak_rhs(mesh, P, inputs.gaussian(H.A.shape[0], 31)).astype(np.float32).astype(np.float64)
+    ref = H.vcycle(u, f)
+    ut = cuda(u, torch.float32)
+    s.vcycle(ut, cuda(f, torch.float32))
+    assert rel_err(host(ut), ref) < 1e-4
+
+
 def test_equal_widths_match_the_uniform_path(mg):
     """A graded context with equal widths runs the graded kernels; its V-cycle
     equals the uniform context's to rounding."""
@@ -365,3 +383,22 @@ def test_graded_rejects_unsupported_options(mg):
             mg.MGSolver(None, None, 4, widths=widths, **kw)
     with pytest.raises(mg.MGError):
         mg.MGSolver(None, None, 4, widths=[np.array([0.5, -0.1, 0.6]), widths[1], widths[2]])
+
+
+def test_graded_largest_line_count(gsolver):
+    """n_x = 256, the largest element count along a graded axis (the coarse
+    eigenproblem of that axis, 512 x 512, is solved whole in one block):
+    coarse solve and V-cycle at P = 2 equal the oracle's."""
+    widths = [graded_widths(256, 8.0, 2.0, 80), graded_widths(3, 1.0, 2.0, 81), graded_widths(3, 0.5, 2.0, 82)]
+    P = 2
+    s = gsolver(widths, P)
+    mesh = Mesh(widths=widths)
+    H = Hierarchy(mesh, P)
+    f0 = inputs.gaussian(H.levels[0].N, 27)
+    got = host(s.coarse_solve(cuda(f0)))
+    assert rel_err(got, H.coarse_solve(f0)) < 1e-10
+    u = inputs.gaussian(H.A.shape[0], 28)
+    f = weak_rhs(mesh, P, inputs.gaussian(H.A.shape[0], 29))
+    ut = cuda(u)
+    s.vcycle(ut, cuda(f))
+    assert rel_err(host(ut), H.vcycle(u, f)) < 1e-10
