@@ -18,7 +18,8 @@ anisotropic 48x8x8, P = 16 box (mixed MG-CG, N_O = 1, 2, 4, and N_O = 4 with
 the double-float outer iteration; key "c3"); the 4^3, P = 32 cube with the
 smoother's contractions on the tensor cores and on the CUDA cores (key "c4");
 a graded 16^3, P = 8 mesh (element widths varying by a factor 4 along every
-axis: FP64 MG and mixed MG-CG; key "graded"); the 512-request serving stream
+axis: FP64 MG and mixed MG-CG, with the outer iteration in FP64 and in
+double-float; key "graded"); the 512-request serving stream
 (N_O = 1 and 4, and N_O = 4 without grouped launches; key "serving"); and the
 FP64 CPU oracle timed on the host cores on a bounded sample of the workload.
 
@@ -678,7 +679,10 @@ def run_mg(args):
         # every axis) of the 16^3, P = 8 size: FP64 MG and mixed MG-CG
         line["graded"] = {"fp64_mg": compact_line(workload_line("graded16_p8", 5, 3)),
                           "mixed_mgcg": compact_line(workload_line("graded16_p8", 5, 3, precision="mixed",
-                                                                   cg=True))}
+                                                                   cg=True)),
+                          "mixed_mgcg_outer_df64": compact_line(workload_line("graded16_p8", 5, 3,
+                                                                              precision="mixed", cg=True,
+                                                                              outer_df64="all"))}
         line["serving"] = {}
         for no in (1, 4):
             line["serving"]["n_o_%d" % no] = compact_line(serving_line("serving512", no))

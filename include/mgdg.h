@@ -168,10 +168,10 @@ mg_status mg_setup(double lx, double ly, double lz, int nx, int ny, int nz, int 
  *                with h_min the smaller width of the face's two elements
  *                (the uniform threshold stays the coercivity threshold)
  *   P, overlap, opts, out   as in mg_setup
- * Supported: MG_FP64 and MG_MIXED, MG_OVERLAP_LAYERS, no tensor cores, no
- * double-float outer iteration, no autotuning, no operand study; anything
- * else returns MG_EINVAL, as do the double-float entry points and
- * mg_solve_batch on such a context.  All other calls work as on a uniform
+ * Supported: MG_FP64 and MG_MIXED (any outer_df64), MG_OVERLAP_LAYERS; no
+ * tensor cores, no autotuning, no operand study: anything else returns
+ * MG_EINVAL, as do mg_vcycle_df64, mg_smooth_df64 (the double-float
+ * multigrid) and mg_solve_batch on such a context.  All other calls work as on a uniform
  * mesh (mg_node_coords gives the graded coordinates, mg_rhs the graded mass).
  * No CUDA call is made.
  */

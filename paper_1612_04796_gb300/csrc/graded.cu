@@ -34,6 +34,8 @@ template <>
 const double* gtable<double>(const mg_ctx* c) { return c->ws.tab64; }
 template <>
 const float* gtable<float>(const mg_ctx* c) { return c->ws.tab32; }
+template <>
+const df64* gtable<df64>(const mg_ctx* c) { return c->ws.tabdf; }
 
 __device__ __forceinline__ int gwrap(int x, int n) { return x < 0 ? x + n : (x >= n ? x - n : x); }
 
@@ -58,22 +60,23 @@ __device__ __forceinline__ T line_product(const T* __restrict__ B, const T* __re
   const T* Bm = B;              // L[e][e-1]
   const T* B0 = B + N * N;      // L[e][e]
   const T* Bp = B + 2 * N * N;  // L[e][e+1]
-  T s = 0;
+  Acc<T> s;
+  s.init(B0[i * N], u[bc]);
 #pragma unroll
-  for (int t = 0; t < N; ++t) s += B0[i * N + t] * u[bc + t * st];
+  for (int t = 1; t < N; ++t) s.add(B0[i * N + t], u[bc + t * st]);
   if (i == 0) {
 #pragma unroll
-    for (int t = 0; t < N; ++t) s += Bm[t] * u[bl + t * st];
+    for (int t = 0; t < N; ++t) s.add(Bm[t], u[bl + t * st]);
   } else {
-    s += Bm[i * N + P] * u[bl + P * st];
+    s.add(Bm[i * N + P], u[bl + P * st]);
   }
   if (i == P) {
 #pragma unroll
-    for (int t = 0; t < N; ++t) s += Bp[P * N + t] * u[br + t * st];
+    for (int t = 0; t < N; ++t) s.add(Bp[P * N + t], u[br + t * st]);
   } else {
-    s += Bp[i * N] * u[br];
+    s.add(Bp[i * N], u[br]);
   }
-  return s;
+  return s.get();
 }
 
 template <typename T, int N>
@@ -114,6 +117,9 @@ __global__ void __launch_bounds__(256) k_gsipg(GOpArgs<T> a) {
   }
 }
 
+// (Inner products through Acc<T>: a multiply-add chain in FP64 / FP32, the
+// compensated double-float dot product for df64, the outer operator of the
+// mixed solve with the outer iteration in double-float.)
 // The same operator with each element staged in shared memory: one block per
 // element (grid-stride), its n^3 values of u, the nine n x n row blocks of its
 // three lines and its masses loaded once; the diagonal-block products read
@@ -158,66 +164,69 @@ __global__ void __launch_bounds__(256) k_gsipg_s(GOpArgs<T> a) {
         const T* B0 = sB + N2;
         const T* Bp = sB + 2 * N2;
         const int b = N * (j + N * k);
-        T acc = 0;
+        Acc<T> acc;
+        acc.init(B0[i * N], su[b]);
 #pragma unroll
-        for (int t = 0; t < N; ++t) acc += B0[i * N + t] * su[b + t];
+        for (int t = 1; t < N; ++t) acc.add(B0[i * N + t], su[b + t]);
         if (i == 0) {
 #pragma unroll
-          for (int t = 0; t < N; ++t) acc += Bm[t] * a.u[exl + b + t];
+          for (int t = 0; t < N; ++t) acc.add(Bm[t], a.u[exl + b + t]);
         } else {
-          acc += Bm[i * N + P] * a.u[exl + b + P];
+          acc.add(Bm[i * N + P], a.u[exl + b + P]);
         }
         if (i == P) {
 #pragma unroll
-          for (int t = 0; t < N; ++t) acc += Bp[P * N + t] * a.u[exr + b + t];
+          for (int t = 0; t < N; ++t) acc.add(Bp[P * N + t], a.u[exr + b + t]);
         } else {
-          acc += Bp[i * N] * a.u[exr + b];
+          acc.add(Bp[i * N], a.u[exr + b]);
         }
-        sx = acc;
+        sx = acc.get();
       }
       {  // y lines: stride N, base i + N^2 k
         const T* Bm = sB + 3 * N2;
         const T* B0 = sB + 4 * N2;
         const T* Bp = sB + 5 * N2;
         const int b = i + N2 * k;
-        T acc = 0;
+        Acc<T> acc;
+        acc.init(B0[j * N], su[b]);
 #pragma unroll
-        for (int t = 0; t < N; ++t) acc += B0[j * N + t] * su[b + t * N];
+        for (int t = 1; t < N; ++t) acc.add(B0[j * N + t], su[b + t * N]);
         if (j == 0) {
 #pragma unroll
-          for (int t = 0; t < N; ++t) acc += Bm[t] * a.u[eyl + b + t * N];
+          for (int t = 0; t < N; ++t) acc.add(Bm[t], a.u[eyl + b + t * N]);
         } else {
-          acc += Bm[j * N + P] * a.u[eyl + b + P * N];
+          acc.add(Bm[j * N + P], a.u[eyl + b + P * N]);
         }
         if (j == P) {
 #pragma unroll
-          for (int t = 0; t < N; ++t) acc += Bp[P * N + t] * a.u[eyr + b + t * N];
+          for (int t = 0; t < N; ++t) acc.add(Bp[P * N + t], a.u[eyr + b + t * N]);
         } else {
-          acc += Bp[j * N] * a.u[eyr + b];
+          acc.add(Bp[j * N], a.u[eyr + b]);
         }
-        sy = acc;
+        sy = acc.get();
       }
       {  // z lines: stride N^2, base i + N j
         const T* Bm = sB + 6 * N2;
         const T* B0 = sB + 7 * N2;
         const T* Bp = sB + 8 * N2;
         const int b = i + N * j;
-        T acc = 0;
+        Acc<T> acc;
+        acc.init(B0[k * N], su[b]);
 #pragma unroll
-        for (int t = 0; t < N; ++t) acc += B0[k * N + t] * su[b + t * N2];
+        for (int t = 1; t < N; ++t) acc.add(B0[k * N + t], su[b + t * N2]);
         if (k == 0) {
 #pragma unroll
-          for (int t = 0; t < N; ++t) acc += Bm[t] * a.u[ezl + b + t * N2];
+          for (int t = 0; t < N; ++t) acc.add(Bm[t], a.u[ezl + b + t * N2]);
         } else {
-          acc += Bm[k * N + P] * a.u[ezl + b + P * N2];
+          acc.add(Bm[k * N + P], a.u[ezl + b + P * N2]);
         }
         if (k == P) {
 #pragma unroll
-          for (int t = 0; t < N; ++t) acc += Bp[P * N + t] * a.u[ezr + b + t * N2];
+          for (int t = 0; t < N; ++t) acc.add(Bp[P * N + t], a.u[ezr + b + t * N2]);
         } else {
-          acc += Bp[k * N] * a.u[ezr + b];
+          acc.add(Bp[k * N], a.u[ezr + b]);
         }
-        sz = acc;
+        sz = acc.get();
       }
       const T mx = sm[i], my = sm[N + j], mz = sm[2 * N + k];
       const T au = sx * my * mz + sy * mx * mz + sz * mx * my;
@@ -612,6 +621,7 @@ cudaError_t launch_gcoords(const mg_ctx* c, int l, double* x, double* y, double*
 
 template cudaError_t launch_gsipg<double>(const mg_ctx*, int, const double*, const double*, double*, int);
 template cudaError_t launch_gsipg<float>(const mg_ctx*, int, const float*, const float*, float*, int);
+template cudaError_t launch_gsipg<df64>(const mg_ctx*, int, const df64*, const df64*, df64*, int);
 template cudaError_t launch_gfdm<double>(const mg_ctx*, int, const double*);
 template cudaError_t launch_gfdm<float>(const mg_ctx*, int, const float*);
 template cudaError_t launch_gmean_zero<double>(const mg_ctx*, double*);

@@ -1207,11 +1207,10 @@ mg_status mg_setup_graded(const double* hx, const double* hy, const double* hz, 
   mg_opts o;
   mg_default_opts(&o);
   if (opts) o = *opts;
-  // graded meshes run the FP64 or the FP32 hierarchy on node-layer overlaps,
-  // with the fixed kernels
+  // graded meshes run the FP64 or the FP32 hierarchy (with the FP64 or the
+  // double-float outer iteration) on node-layer overlaps, with the fixed kernels
   if (o.precision != MG_FP64 && o.precision != MG_MIXED) return MG_EINVAL;
-  if (o.overlap_mode != MG_OVERLAP_LAYERS || o.fdm_tensor_cores != 0 || o.outer_df64 != 0 || o.autotune != 0 ||
-      o.fdm_operands != 0)
+  if (o.overlap_mode != MG_OVERLAP_LAYERS || o.fdm_tensor_cores != 0 || o.autotune != 0 || o.fdm_operands != 0)
     return MG_EINVAL;
   mg_ctx* c = nullptr;
   const mg_status st = mg_setup(len[0], len[1], len[2], nx, ny, nz, P, penalty, overlap, &o, &c);
@@ -1371,7 +1370,7 @@ int mg_level_layers(const mg_ctx* c, int level) { return mg_level_layers_dir(c, 
 mg_status mg_vcycle_df64(mg_ctx* c, double* u, const double* f) {
   mg_status s = need_ready(c);
   if (s != MG_OK) return s;
-  if (c->graded) return fail(c, MG_EINVAL, "double-float kernels are not built for graded meshes");
+  if (c->graded) return fail(c, MG_EINVAL, "the double-float multigrid is not built for graded meshes");
   if (!u || !f || u == f) return fail(c, MG_EINVAL, "null or aliased vector");
   const int L = c->L;
   const int64_t N = c->lev[L].N;
@@ -1387,6 +1386,7 @@ mg_status mg_vcycle_df64(mg_ctx* c, double* u, const double* f) {
 mg_status mg_smooth_df64(mg_ctx* c, int level, double* u, const double* f, int nsteps) {
   mg_status s = need_ready(c);
   if (s != MG_OK) return s;
+  if (c->graded) return fail(c, MG_EINVAL, "the double-float multigrid is not built for graded meshes");
   if (!check_level(c, level, true)) return MG_EINVAL;
   if (!u || !f || u == f || nsteps < 0) return fail(c, MG_EINVAL, "bad arguments");
   const int64_t N = c->lev[level].N;
@@ -1402,7 +1402,6 @@ mg_status mg_smooth_df64(mg_ctx* c, int level, double* u, const double* f, int n
 mg_status mg_apply_sipg_df64(mg_ctx* c, int level, const double* u, double* Au) {
   mg_status s = need_ready(c);
   if (s != MG_OK) return s;
-  if (c->graded) return fail(c, MG_EINVAL, "double-float kernels are not built for graded meshes");
   if (!check_level(c, level, false)) return MG_EINVAL;
   if (!u || !Au || u == Au) return fail(c, MG_EINVAL, "null or aliased vector");
   const int64_t N = c->lev[level].N;

@@ -380,12 +380,7 @@ const df64* table_of<df64>(const mg_ctx* c) { return c->ws.tabdf; }
 
 template <typename T>
 cudaError_t launch_sipg(const mg_ctx* c, int l, const T* u, const T* f, T* out, int residual) {
-  if (c->graded) {
-    if constexpr (std::is_same<T, double>::value || std::is_same<T, float>::value)
-      return launch_gsipg<T>(c, l, u, f, out, residual);
-    else
-      return cudaErrorNotSupported;
-  }
+  if (c->graded) return launch_gsipg<T>(c, l, u, f, out, residual);
   const LevelInfo& lv = c->lev[l];
   OpArgs<T> a;
   a.tab = table_of<T>(c);

@@ -214,7 +214,6 @@ def test_graded_setup_host_validation(lib):
         (w, {"precision": 2}),
         (w, {"overlap_mode": 1}),
         (w, {"precision": 1, "fdm_tensor_cores": 1}),
-        (w, {"precision": 1, "outer_df64": 1}),
         (w, {"autotune": 1}),
     ]
     for widths, kw in bad:

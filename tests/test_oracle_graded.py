@@ -228,3 +228,18 @@ def test_graded_mg_and_mgcg_converge_like_the_uniform_mesh():
         its[name] = (it_mg, it_cg)
     assert its["graded"][0] <= its["uniform"][0] + 2, its
     assert its["graded"][1] <= its["uniform"][1] + 2, its
+
+
+@pytest.mark.parametrize("graded,P,n_o", [(True, 4, 1), (True, 4, 2), (False, 4, 2), (True, 8, 1)])
+def test_kron_fdm_correction_equals_direct_schwarz_correction(graded, P, n_o):
+    """The fast-diagonalisation form of the smoother's correction (used where
+    direct subdomain solves take too long) equals the direct solves of
+    SchwarzSmoother on graded and uniform meshes."""
+    from oracle.schwarz import SchwarzSmoother, kron_fdm_correction
+    mesh = small_graded_mesh(seed=13, counts=(3, 4, 3), ratio=3.0) if graded else Mesh((1.0, 2.0, 0.5), (3, 4, 3))
+    A = assemble(mesh, P)
+    delta = layer_delta(P, n_o)
+    r = np.random.default_rng(P + n_o).standard_normal(A.shape[0])
+    ref = SchwarzSmoother(A, mesh, P, n_o, delta).correction(r)
+    got = kron_fdm_correction(mesh, P, n_o, delta, r)
+    assert np.max(np.abs(got - ref)) <= 1e-10 * np.max(np.abs(ref))
