@@ -382,40 +382,38 @@ __global__ void __launch_bounds__(256) k_gfdm(GFdmArgs<T> a) {
   }
 }
 
-// u0 -= mean(u0): one block (level 0 holds 8 values per element).
+// Mean removal on level 0 in two launches: per-block partial sums of x into
+// red[0 .. nb), then out = x - (sum of the partials, in block order) / n,
+// every block adding the nb partials itself.
 template <typename T>
-__global__ void __launch_bounds__(1024) k_gmean_zero(T* u, int64_t n) {
+__global__ void __launch_bounds__(256) k_gsum_partial(const T* __restrict__ x, int64_t n, double* __restrict__ red) {
   pdl_entry();
-  __shared__ double sh[1024];
+  __shared__ double sh[256];
   double s = 0.0;
-#pragma unroll 8
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += (double)u[i];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    s += (double)x[i];
   sh[threadIdx.x] = s;
   __syncthreads();
   for (int w = blockDim.x / 2; w > 0; w >>= 1) {
     if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
     __syncthreads();
   }
-  const double mean = sh[0] / (double)n;
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) u[i] = (T)((double)u[i] - mean);
+  if (threadIdx.x == 0) red[blockIdx.x] = sh[0];
 }
 
-// out = f - mean(f) in FP64: one block (level 0).
-template <typename T>
-__global__ void __launch_bounds__(1024) k_gcenter(const T* __restrict__ f, double* __restrict__ out, int64_t n) {
+template <typename TI, typename TO>
+__global__ void __launch_bounds__(256) k_gsub_mean(const TI* x, TO* out, int64_t n, const double* __restrict__ red,
+                                                   int nb) {
   pdl_entry();
-  __shared__ double sh[1024];
-  double s = 0.0;
-#pragma unroll 8
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += (double)f[i];
-  sh[threadIdx.x] = s;
-  __syncthreads();
-  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-    if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
-    __syncthreads();
+  __shared__ double mean;
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int q = 0; q < nb; ++q) s += red[q];
+    mean = s / (double)n;
   }
-  const double mean = sh[0] / (double)n;
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) out[i] = (double)f[i] - mean;
+  __syncthreads();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (TO)((double)x[i] - mean);
 }
 
 struct GMassArgs {
@@ -577,17 +575,26 @@ cudaError_t launch_gfdm(const mg_ctx* c, int l, const T* r) {
   return cudaGetLastError();
 }
 
+// Blocks of the level-0 mean removals: about 2,048 values per block, at most 64.
+inline int gmean_blocks(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(64, (n + 2047) / 2048)); }
+
 template <typename T>
 cudaError_t launch_gmean_zero(const mg_ctx* c, T* u0) {
-  launch_pdl(k_gmean_zero<T>, 1, 1024, 0, c->stream, u0, c->lev[0].N);
-  c->nlaunch += 1;
+  const int64_t n = c->lev[0].N;
+  const int nb = gmean_blocks(n);
+  launch_pdl(k_gsum_partial<T>, nb, 256, 0, c->stream, (const T*)u0, n, c->ws.red);
+  launch_pdl(k_gsub_mean<T, T>, nb, 256, 0, c->stream, (const T*)u0, u0, n, (const double*)c->ws.red, nb);
+  c->nlaunch += 2;
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_gcenter(const mg_ctx* c, const T* f0, double* out) {
-  launch_pdl(k_gcenter<T>, 1, 1024, 0, c->stream, f0, out, c->lev[0].N);
-  c->nlaunch += 1;
+  const int64_t n = c->lev[0].N;
+  const int nb = gmean_blocks(n);
+  launch_pdl(k_gsum_partial<T>, nb, 256, 0, c->stream, f0, n, c->ws.red);
+  launch_pdl(k_gsub_mean<T, double>, nb, 256, 0, c->stream, f0, out, n, (const double*)c->ws.red, nb);
+  c->nlaunch += 2;
   return cudaGetLastError();
 }
 

@@ -212,6 +212,28 @@ def test_graded_smooth_fp64(gsolver, P, overlap):
     assert rel_err(host(u1t) - u1, ref2) < FP64_TOL
 
 
+@pytest.mark.parametrize("P,overlap,dtype", [(16, 5, "fp64"), (32, 1, "fp64"), (16, 5, "fp32")])
+def test_graded_smooth_full_widths(gsolver, P, overlap, dtype):
+    """The widest graded subdomains (m = 27 at P = 16, N_O = 5; m = 35 at
+    P = 32), beyond the compile-time widths, on a graded 3^3 mesh: one
+    smoothing step from u = 0 against the oracle's fast-diagonalisation form
+    of the correction (pinned to the direct subdomain solves)."""
+    import torch
+    from oracle.schwarz import kron_fdm_correction
+    widths = mesh_widths((3, 3, 3), ratio=3.0)
+    s = gsolver(widths, P, overlap)
+    mesh = Mesh(widths=widths)
+    no = s.layers(s.L)
+    assert 2 * no + P + 1 > 25
+    N = s.num_dofs()
+    f = inputs.gaussian(N, 33)
+    ref = kron_fdm_correction(mesh, P, no, layer_delta(P, no), f)
+    tdt = torch.float64 if dtype == "fp64" else torch.float32
+    ut = torch.zeros(N, dtype=tdt, device="cuda")
+    s.smooth(ut, cuda(f, tdt))
+    assert rel_err(host(ut), ref) < (FP64_TOL if dtype == "fp64" else 1e-4)
+
+
 def test_graded_smooth_many_subdomains_per_block(gsolver):
     """11^3 elements at P = 2: more subdomains than the smoother launches
     blocks, so every block transforms several subdomains in turn."""
@@ -332,6 +354,32 @@ def test_graded_vcycle_fp32(gsolver):
     assert rel_err(host(ut), ref) < 1e-4
 
 
+def test_graded_apply_sipg_df64(gsolver):
+    """The double-float operator (the outer operator of the mixed solve with
+    a double-float outer iteration) on a graded mesh: about 48 significant
+    bits against the FP64 oracle."""
+    widths = mesh_widths((3, 4, 5))
+    P = 8
+    s = gsolver(widths, P, precision="mixed", outer_df64=True)
+    A = assemble(Mesh(widths=widths), P)
+    u = inputs.gaussian(A.shape[0], 32)
+    assert rel_err(host(s.apply_sipg_df64(cuda(u))), A @ u) < 1e-12
+
+
+@pytest.mark.parametrize("outer", [True, "all"])
+def test_graded_mixed_with_double_float_outer_iteration(gsolver, outer):
+    widths = [graded_widths(4, 1.0, 2.5, 40 + d) for d in range(3)]
+    P = 8
+    s = gsolver(widths, P, precision="mixed", outer_df64=outer)
+    mesh = Mesh(widths=widths)
+    A = assemble(mesh, P)
+    b = weak_rhs(mesh, P, inputs.gaussian(A.shape[0], 19))
+    ug, itg, rel, _ = s.solve(cuda(b), tol=1e-10, use_cg=True)
+    u = host(ug)
+    assert np.linalg.norm(b - A @ u) <= 1.01e-10 * np.linalg.norm(b)
+    assert itg <= 14
+
+
 def test_equal_widths_match_the_uniform_path(mg):
     """A graded context with equal widths runs the graded kernels; its V-cycle
     equals the uniform context's to rounding."""
@@ -378,7 +426,7 @@ def test_graded_full_size_solve(gsolver):
 def test_graded_rejects_unsupported_options(mg):
     widths = mesh_widths((3, 3, 3))
     for kw in ({"precision": "df64"}, {"precision": "mixed", "tensor_cores": True}, {"overlap_mode": "width"},
-               {"precision": "mixed", "outer_df64": True}, {"autotune": True}):
+               {"autotune": True}):
         with pytest.raises(mg.MGError):
             mg.MGSolver(None, None, 4, widths=widths, **kw)
     with pytest.raises(mg.MGError):
