@@ -1345,7 +1345,7 @@ mg_status mg_bind_workspace(mg_ctx* c, void* dptr, size_t bytes) {
   }
   CK(cudaStreamSynchronize(c->stream));
   if (st != kDevOk) return fail(c, MG_ENOCONV, "setup eigensolver did not converge");
-  if (c->opts.precision == MG_MIXED)
+  if (c->opts.precision == MG_MIXED && !c->graded)  // graded meshes have their own smoother kernels
     for (int l = 1; l <= c->L; ++l) c->lev[l].fdm_variant = fdm_c_default_variant(c, l);
   if (c->opts.precision == MG_MIXED && c->opts.fdm_tensor_cores != 0) CK(choose_fdm_kernels(c));
   if (c->opts.autotune) {
