@@ -122,15 +122,23 @@ __global__ void __launch_bounds__(256) k_gsipg(GOpArgs<T> a) {
 // mixed solve with the outer iteration in double-float.)
 // The same operator with each element staged in shared memory: one block per
 // element (grid-stride), its n^3 values of u, the nine n x n row blocks of its
-// three lines and its masses loaded once; the diagonal-block products read
-// shared memory, the coupling terms the neighbours' values in global memory.
+// three lines and its masses loaded once.  Phase A (every DOF, no branch):
+// the diagonal-block products from shared memory plus, per direction and
+// side, the coupling column that every row has (L[e][e-1] column P times the
+// left neighbour's face value, L[e][e+1] column 0 times the right one's).
+// Phases x, y, z: the rest of the two face rows of each direction (row 0 of
+// L[e][e-1] and row P of L[e][e+1], the neighbour's whole line), one thread
+// per face node, added to the face DOFs in shared memory (each phase touches
+// every DOF at most once; a barrier between phases).  Splitting the face rows
+// off keeps the warps of phase A from running the face loops of a few lanes.
 template <typename T, int N>
 __global__ void __launch_bounds__(256) k_gsipg_s(GOpArgs<T> a) {
   pdl_entry();
   constexpr int N2 = N * N, N3 = N2 * N, P = N - 1;
   extern __shared__ __align__(16) unsigned char gs_raw[];
   T* su = reinterpret_cast<T*>(gs_raw);  // N^3
-  T* sB = su + N3;                       // [dir][block][N^2]: L[e][e-1], L[e][e], L[e][e+1]
+  T* sau = su + N3;                      // N^3: A u of the element
+  T* sB = sau + N3;                      // [dir][block][N^2]: L[e][e-1], L[e][e], L[e][e+1]
   T* sm = sB + 9 * N2;                   // [dir][N]
   for (int64_t e = blockIdx.x; e < a.Ne; e += gridDim.x) {
     const int e32 = (int)e, exy = e32 / a.nx;
@@ -156,89 +164,80 @@ __global__ void __launch_bounds__(256) k_gsipg_s(GOpArgs<T> a) {
     const int64_t eyr = (ex + (int64_t)a.nx * gwrap(ey + 1, a.ny) + ezrow) * N3;
     const int64_t exy0 = ex + (int64_t)a.nx * ey, plane = (int64_t)a.nx * a.ny;
     const int64_t ezl = (exy0 + plane * gwrap(ez - 1, a.nz)) * N3, ezr = (exy0 + plane * gwrap(ez + 1, a.nz)) * N3;
+    // phase A
     for (int q = threadIdx.x; q < N3; q += blockDim.x) {
       const int i = q % N, j = (q / N) % N, k = q / N2;
       T sx, sy, sz;
       {  // x lines: stride 1, base N (j + N k)
-        const T* Bm = sB;
-        const T* B0 = sB + N2;
-        const T* Bp = sB + 2 * N2;
         const int b = N * (j + N * k);
         Acc<T> acc;
-        acc.init(B0[i * N], su[b]);
+        acc.init(sB[N2 + i * N], su[b]);
 #pragma unroll
-        for (int t = 1; t < N; ++t) acc.add(B0[i * N + t], su[b + t]);
-        if (i == 0) {
-#pragma unroll
-          for (int t = 0; t < N; ++t) acc.add(Bm[t], a.u[exl + b + t]);
-        } else {
-          acc.add(Bm[i * N + P], a.u[exl + b + P]);
-        }
-        if (i == P) {
-#pragma unroll
-          for (int t = 0; t < N; ++t) acc.add(Bp[P * N + t], a.u[exr + b + t]);
-        } else {
-          acc.add(Bp[i * N], a.u[exr + b]);
-        }
+        for (int t = 1; t < N; ++t) acc.add(sB[N2 + i * N + t], su[b + t]);
+        acc.add(sB[i * N + P], a.u[exl + b + P]);
+        acc.add(sB[2 * N2 + i * N], a.u[exr + b]);
         sx = acc.get();
       }
       {  // y lines: stride N, base i + N^2 k
-        const T* Bm = sB + 3 * N2;
-        const T* B0 = sB + 4 * N2;
-        const T* Bp = sB + 5 * N2;
         const int b = i + N2 * k;
         Acc<T> acc;
-        acc.init(B0[j * N], su[b]);
+        acc.init(sB[4 * N2 + j * N], su[b]);
 #pragma unroll
-        for (int t = 1; t < N; ++t) acc.add(B0[j * N + t], su[b + t * N]);
-        if (j == 0) {
-#pragma unroll
-          for (int t = 0; t < N; ++t) acc.add(Bm[t], a.u[eyl + b + t * N]);
-        } else {
-          acc.add(Bm[j * N + P], a.u[eyl + b + P * N]);
-        }
-        if (j == P) {
-#pragma unroll
-          for (int t = 0; t < N; ++t) acc.add(Bp[P * N + t], a.u[eyr + b + t * N]);
-        } else {
-          acc.add(Bp[j * N], a.u[eyr + b]);
-        }
+        for (int t = 1; t < N; ++t) acc.add(sB[4 * N2 + j * N + t], su[b + t * N]);
+        acc.add(sB[3 * N2 + j * N + P], a.u[eyl + b + P * N]);
+        acc.add(sB[5 * N2 + j * N], a.u[eyr + b]);
         sy = acc.get();
       }
       {  // z lines: stride N^2, base i + N j
-        const T* Bm = sB + 6 * N2;
-        const T* B0 = sB + 7 * N2;
-        const T* Bp = sB + 8 * N2;
         const int b = i + N * j;
         Acc<T> acc;
-        acc.init(B0[k * N], su[b]);
+        acc.init(sB[7 * N2 + k * N], su[b]);
 #pragma unroll
-        for (int t = 1; t < N; ++t) acc.add(B0[k * N + t], su[b + t * N2]);
-        if (k == 0) {
-#pragma unroll
-          for (int t = 0; t < N; ++t) acc.add(Bm[t], a.u[ezl + b + t * N2]);
-        } else {
-          acc.add(Bm[k * N + P], a.u[ezl + b + P * N2]);
-        }
-        if (k == P) {
-#pragma unroll
-          for (int t = 0; t < N; ++t) acc.add(Bp[P * N + t], a.u[ezr + b + t * N2]);
-        } else {
-          acc.add(Bp[k * N], a.u[ezr + b]);
-        }
+        for (int t = 1; t < N; ++t) acc.add(sB[7 * N2 + k * N + t], su[b + t * N2]);
+        acc.add(sB[6 * N2 + k * N + P], a.u[ezl + b + P * N2]);
+        acc.add(sB[8 * N2 + k * N], a.u[ezr + b]);
         sz = acc.get();
       }
       const T mx = sm[i], my = sm[N + j], mz = sm[2 * N + k];
-      const T au = sx * my * mz + sy * mx * mz + sz * mx * my;
+      sau[q] = sx * my * mz + sy * mx * mz + sz * mx * my;
+    }
+    // phases x, y, z: face rows; task f < 2 N^2: side = f / N^2 (0: row 0 with the
+    // left neighbour, 1: row P with the right one), (p, r) = the other two indices
+#pragma unroll 1
+    for (int d = 0; d < 3; ++d) {
+      __syncthreads();
+      for (int f = threadIdx.x; f < 2 * N2; f += blockDim.x) {
+        const int side = f / N2, pr = f - side * N2, p0 = pr % N, r0 = pr / N;
+        const int st = d == 0 ? 1 : (d == 1 ? N : N2);
+        // DOF of the face node and the base of its line
+        const int base = d == 0 ? N * pr : (d == 1 ? p0 + N2 * r0 : pr);
+        const int row = side == 0 ? 0 : P;
+        const int64_t nb = d == 0 ? (side == 0 ? exl : exr) : (d == 1 ? (side == 0 ? eyl : eyr) : (side == 0 ? ezl : ezr));
+        // L[e][e-1] row 0 without its column P, or L[e][e+1] row P without its column 0
+        const T* B = sB + d * 3 * N2 + (side == 0 ? 0 : 2 * N2) + row * N;
+        const int t0 = side == 0 ? 0 : 1;
+        Acc<T> acc;
+        acc.init(B[t0], a.u[nb + base + t0 * st]);
+#pragma unroll
+        for (int t = 1; t < N - 1; ++t) acc.add(B[t0 + t], a.u[nb + base + (t0 + t) * st]);
+        // mass weights of the two other directions at the face node
+        const T mo1 = d == 0 ? sm[N + p0] : sm[p0];
+        const T mo2 = d == 2 ? sm[N + r0] : sm[2 * N + r0];
+        const int q = base + row * st;
+        sau[q] += acc.get() * mo1 * mo2;
+      }
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < N3; q += blockDim.x) {
       const int64_t dof = e * N3 + q;
-      a.out[dof] = a.residual ? a.f[dof] - au : au;
+      a.out[dof] = a.residual ? a.f[dof] - sau[q] : sau[q];
     }
   }
 }
 
 template <typename T, int N>
 cudaError_t launch_gsipg_s(const mg_ctx* c, const GOpArgs<T>& a) {
-  constexpr size_t smem = sizeof(T) * (N * N * N + 9 * N * N + 3 * N);
+  constexpr size_t smem = sizeof(T) * (2 * N * N * N + 9 * N * N + 3 * N);
   static std::atomic<size_t> smem_set{48 * 1024};
   const cudaError_t e = allow_smem((const void*)k_gsipg_s<T, N>, smem, smem_set);
   if (e != cudaSuccess) return e;
