@@ -219,3 +219,24 @@ def test_graded_setup_host_validation(lib):
     for widths, kw in bad:
         st, c = _setup_graded(lib, widths, **kw)
         assert st == 1 and not c.value, (widths if not kw else kw)
+
+
+def test_bench_graded_workload_widths():
+    """The graded bench workload: smooth periodic widths summing to the box
+    length, largest / smallest at most (1 + 0.6) / (1 - 0.6) = 4, neighbouring
+    widths within a factor 1.35, accepted by mg_setup_graded."""
+    import numpy as np
+
+    import bench
+    W = bench.WORKLOADS["graded16_p8"]
+    assert len(W["widths"]) == 3
+    for d, w in enumerate(W["widths"]):
+        w = np.asarray(w)
+        assert len(w) == W["elements"][d]
+        assert abs(w.sum() - W["lengths"][d]) < 1e-14
+        assert w.max() / w.min() <= 4.0 + 1e-12
+        assert np.max(np.maximum(w / np.roll(w, 1), np.roll(w, 1) / w)) < 1.35
+    lib = pkg.load_library()
+    st, ctx = _setup_graded(lib, W["widths"], P=W["P"], overlap=W["overlap_layers"])
+    assert st == 0
+    lib.mg_destroy(ctx)
