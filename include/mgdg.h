@@ -171,9 +171,10 @@ mg_status mg_setup(double lx, double ly, double lz, int nx, int ny, int nz, int 
  * Supported: MG_FP64 and MG_MIXED (any outer_df64), MG_OVERLAP_LAYERS; no
  * tensor cores, no autotuning, no operand study: anything else returns
  * MG_EINVAL, as do mg_vcycle_df64, mg_smooth_df64 (the double-float
- * multigrid) and mg_solve_batch on such a context.  All other calls work as on a uniform
- * mesh (mg_node_coords gives the graded coordinates, mg_rhs the graded mass).
- * No CUDA call is made.
+ * multigrid) and mg_solve_batch on such a context.  All other calls work as
+ * on a uniform mesh (mg_node_coords gives the graded coordinates, mg_rhs the
+ * graded mass; mg_get_line_table the per-line tables).  No CUDA call is made;
+ * mg_bind_workspace copies the widths to the device and builds the tables.
  */
 mg_status mg_setup_graded(const double* hx, const double* hy, const double* hz, int nx, int ny, int nz, int P,
                           double penalty, int overlap, const mg_opts* opts, mg_ctx** out);
