@@ -252,11 +252,12 @@ class ClockSampler:
                 "samples": len(sm), "power_w_max": max(power)}
 
 
-def measured_traffic():
-    """DRAM bytes per launch of the fine-level smoother from the committed ncu
-    capture, or None if the kernel source changed since it was taken."""
+def measured_traffic(record="fdm_fp64_16x16x16_p8_m11.json"):
+    """DRAM bytes per launch of a fine-level smoother from a committed ncu
+    capture (profiles/<record>), or None if the kernel source changed since
+    it was taken."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "fdm_fp64_16x16x16_p8_m11.json")
+    path = os.path.join(ROOT, "profiles", record)
     if not os.path.exists(path):
         return None
     with open(path) as fh:
@@ -784,7 +785,11 @@ def workload_line(name, steps, warmup, overlap=None, precision=None, cg=False, o
     fp64 = W["precision"] == "fp64"
     pk, _ = peaks()
     clk, clk_basis = clock_mhz(clock_info, pk)
-    kern = level_rooflines(s, s.L, fp64, clk, clk_basis, pk)
+    traffic = measured_traffic("gfdm_fp64_graded16_p8_m11.json") if name == "graded16_p8" and fp64 else None
+    kern = level_rooflines(s, s.L, fp64, clk, clk_basis, pk, traffic=traffic)
+    for k in kern:
+        if traffic is not None and k["kernel"].startswith("k_gfdm"):
+            k["traffic_source"] = "profiles/gfdm_fp64_graded16_p8_m11.md (ncu dram__bytes_read+write of one launch)"
     vb = 8 if fp64 else 4
     if "widths" in W:
         W["element_widths"] = {"min": min(min(w) for w in W["widths"]), "max": max(max(w) for w in W["widths"])}
